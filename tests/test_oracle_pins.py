@@ -1,0 +1,276 @@
+"""Pins of the FP64 oracle against what the paper and mathematics fix.
+
+Each test checks the oracle against something other than itself: closed
+forms of the sums, the paper's own analytic test (f == 1, Sec. 3.1),
+textbook constants, library routines for special cases, and brute-force
+dense solves at small N.  A plausible slip in the oracle (a dropped 1/N, a
+wrong sign in G, an uncompensated y - x_k, a swapped index in Eq. p8) fails
+at least one of them.
+"""
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import workloads
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden_lines(name):
+    with open(os.path.join(GOLDEN, name)) as fh:
+        return [ln.split() for ln in fh if ln.strip() and not ln.startswith("#")]
+
+
+# ------------------------------------------------------------- exact constants
+
+def test_pi_fixed_matches_textbook_hex(orc):
+    hexdigits = _golden_lines("pi_hex.txt")[0][0]
+    nbits = 4 * len(hexdigits)
+    frac = orc.PI_FIXED - (3 << orc._PI_BITS)
+    assert frac >> (orc._PI_BITS - nbits) == int(hexdigits, 16)
+    assert float(Fraction(orc.PI_FIXED, 1 << orc._PI_BITS)) == math.pi
+
+
+def test_bernoulli_matches_as64_table(orc):
+    B = orc.bernoulli(20)
+    for two_m, num, den in _golden_lines("bernoulli_as64.txt"):
+        assert B[int(two_m)] == Fraction(int(num), int(den))
+    assert all(B[k] == 0 for k in range(3, 21, 2))
+
+
+def _pi_frac():
+    from oracle import PI_FIXED, _PI_BITS
+    return Fraction(PI_FIXED, 1 << _PI_BITS)
+
+
+def test_bernoulli_bound_eq12(orc):
+    """|B_2m| < 2 (2m)! / ((2 pi)^2m (1 - 2^(1-2m)))  (Eq. 12)."""
+    B = orc.bernoulli(80)
+    pi = _pi_frac()
+    for m in range(1, 41):
+        bound = Fraction(2 * math.factorial(2 * m)) / ((2 * pi) ** (2 * m) * (1 - Fraction(2) ** (1 - 2 * m)))
+        assert abs(B[2 * m]) < bound
+
+
+def _cot_series_tail(B, q, t):
+    """2 sum_{m>q} |B_2m| t^(2m-1)/(2m)! (200 terms, exact coefficients)."""
+    s = 0.0
+    for m in range(q + 1, q + 60):
+        s += float(abs(B[2 * m]) / math.factorial(2 * m)) * t ** (2 * m - 1)
+    return 2.0 * s
+
+
+@pytest.mark.parametrize("q", [2, 4, 8, 11, 14, 20])
+def test_series_eq10_eq11_truncation(orc, q):
+    """Eq. 10 truncated after q terms differs from cot(t/2) by < 2 eps_q on |t|<=pi,
+    Eq. 11 (the tan series) by < 2 * (2 eps_q) on |t|<=pi/2  (Eq. p14)."""
+    B = orc.bernoulli(2 * q + 130)
+    eps_q = 2.0 ** (1 - 2 * q) / (3 * math.pi * (1 - 2.0 ** (-2 * q - 1)))
+    ts = np.linspace(0.25, math.pi, 200)
+    worst1 = worst2 = 0.0
+    for t in ts:
+        s1 = 2.0 / t - 2.0 * sum(float(abs(B[2 * m]) / math.factorial(2 * m)) * t ** (2 * m - 1)
+                                  for m in range(1, q + 1))
+        worst1 = max(worst1, abs(1.0 / math.tan(t / 2) - s1))
+        t2 = t / 2
+        s2 = -2.0 * sum(float((2 ** (2 * m) - 1) * abs(B[2 * m]) / math.factorial(2 * m)) * t2 ** (2 * m - 1)
+                        for m in range(1, q + 1))
+        worst2 = max(worst2, abs(-math.tan(t2 / 2) - s2))
+    # the series themselves (and the bound) hold: the residual is the tail
+    assert worst1 < 2 * eps_q + 1e-13
+    assert worst2 < 2 * 2 * eps_q + 1e-13
+    # the bound is not vacuous: the tail at t = pi is within a factor ~2 of it
+    assert _cot_series_tail(B, q, math.pi) > 0.3 * eps_q
+
+
+# ------------------------------------------------------------- forward sums
+
+def _exact_expi(m, y):
+    """e^{i m y} with m*y reduced mod 2 pi in exact rational arithmetic."""
+    pi = _pi_frac()
+    a = Fraction(m) * Fraction(y)
+    r = a - 2 * pi * math.floor(a / (2 * pi))
+    r = float(r)
+    return complex(math.cos(r), math.sin(r))
+
+
+@pytest.mark.parametrize("N", [8, 256, 1 << 16])
+def test_nudft_reproduces_single_mode(orc, N):
+    """c = e_m gives g_j = e^{i m y_j} exactly (band-limited series, Eq. p1)."""
+    y = workloads.points("uniform", 64 if N < 65536 else 8, seed=3)
+    for m in sorted({0, 1, N // 3, N - 1}):
+        c = np.zeros(N, complex)
+        c[m] = 1.0
+        g = orc.nudft_fwd(c, y)
+        ref = np.array([_exact_expi(m, v) for v in y])
+        assert np.abs(g - ref).max() < 4e-16 * max(1, 8)
+
+
+@pytest.mark.parametrize("L", [3, 6, 10, 12])
+def test_kernel_form_constant_function(orc, L):
+    """The paper's analytic test (Sec. 3.1): f == 1 gives g_j = 1 exactly, for
+    random y and for y on or next to grid points (Eq. p4 with the 1/N of p5)."""
+    N = 1 << L
+    y = workloads.points("uniform", 200, seed=L)
+    k = np.arange(0, N, max(1, N // 16))
+    xk = k * (2 * math.pi / N)
+    near = np.concatenate([xk, np.nextafter(xk, 10.0), np.nextafter(xk[1:], -10.0)])
+    y = np.concatenate([y, near, [0.0]])
+    y = y[(y >= 0) & (y < 2 * math.pi)]
+    g = orc.kernel_fwd(np.ones(N, complex), y)
+    assert np.abs(g - 1.0).max() < 1e-14
+
+
+@pytest.mark.parametrize("N", [16, 1024, 4096])
+def test_cot_sum_closed_form(orc, N):
+    """sum_k cot((y - 2 pi k/N)/2) = N cot(N y/2): pins G and the compensated
+    difference y - x_k, including y within an ulp of a grid point."""
+    y = workloads.points("uniform", 100, seed=N)
+    k = np.arange(1, N, max(1, N // 8))
+    xk = k * (2 * math.pi / N)
+    y = np.concatenate([y, np.nextafter(xk, 10.0), np.nextafter(xk, -10.0)])
+    h = orc.cot_sum(np.ones(N), y)
+    ref = N / np.tan(N * y / 2)  # N*y exact for N = 2^L
+    assert np.all(np.abs(h - ref) <= 1e-13 * np.maximum(np.abs(ref), N))
+
+
+@pytest.mark.parametrize("N,M", [(64, 50), (1024, 300), (4096, 64)])
+def test_two_forward_routes_agree(orc, N, M):
+    """Direct NUDFT (Eq. p1) and the factored kernel form (Eq. p2/p4) agree."""
+    c = workloads.coeffs(N, seed=N)
+    y = workloads.points("uniform", M, seed=M)
+    g1 = orc.nufft_fwd(c, y, route="nudft")
+    g2 = orc.nufft_fwd(c, y, route="kernel")
+    assert orc.rel_l2(g2, g1) < 1e-13
+
+
+@pytest.mark.parametrize("N", [8, 32, 64])
+def test_dense_kernel_matrix(orc, N):
+    """Columns of the factored form equal the geometric sum of Eq. p2 and the
+    Dirichlet closed form (reading c1: F_j carries the 1/N)."""
+    M = 40
+    y = workloads.points("uniform", M, seed=N + 1)
+    K = np.empty((M, N), complex)
+    for k in range(N):
+        e = np.zeros(N, complex)
+        e[k] = 1.0
+        K[:, k] = orc.kernel_fwd(e, y)
+    x = 2 * np.pi * np.arange(N) / N
+    n = np.arange(N)
+    Kp2 = np.exp(1j * (y[:, None, None] - x[None, :, None]) * n[None, None, :]).sum(-1) / N
+    assert np.abs(K - Kp2).max() < 1e-13
+    t = y[:, None] - x[None, :]
+    Kd = np.exp(1j * (N - 1) * t / 2) * np.sin(N * t / 2) / np.sin(t / 2) / N
+    assert np.abs(K - Kd).max() < 1e-12
+
+
+def test_adjoint_dot_product(orc):
+    """<A c, g> = <c, A^H g> for the direct forward and adjoint, and the
+    factored adjoint route agrees with the direct one."""
+    N, M = 512, 300
+    c = workloads.coeffs(N, seed=5)
+    g = workloads.samples(M, seed=6)
+    y = workloads.points("uniform", M, seed=7)
+    Ac = orc.nudft_fwd(c, y)
+    Ahg = orc.nudft_adj(g, y, N)
+    lhs, rhs = np.vdot(g, Ac), np.vdot(Ahg, c)
+    assert abs(lhs - rhs) / abs(lhs) < 1e-13
+    assert orc.rel_l2(orc.nufft_adj(g, y, N, route="kernel"), Ahg) < 1e-13
+
+
+def test_fft_matches_dft_and_numpy(orc):
+    for N in (8, 64, 1024):
+        x = workloads.coeffs(N, seed=N)
+        assert orc.rel_l2(orc.fft(x, -1), np.fft.fft(x)) < 1e-14
+        assert orc.rel_l2(orc.fft(x, +1), np.fft.ifft(x) * N) < 1e-14
+        assert orc.rel_l2(orc.dft(x, -1), np.fft.fft(x)) < 1e-14
+
+
+# ------------------------------------------------------------- inverse
+
+@pytest.mark.parametrize("N", [16, 256])
+def test_logsin_equispaced_closed_form(orc, N):
+    """y_l = 2 pi l/N + phi: prod_l 2 sin((x - y_l)/2) = +-2 sin(N (x - phi)/2)
+    and prod_{l!=j} 2 sin((y_j - y_l)/2) = +-N, which pin the log-sums and the
+    sign counts behind C_k and D_j (Eq. p8)."""
+    phi = 0.37 * 2 * math.pi / N
+    y = 2 * math.pi * np.arange(N) / N + phi
+    lamC, nC = orc.logsin_C(y, N)
+    assert np.abs(lamC - math.log(2 * abs(math.sin(N * phi / 2)))).max() < 1e-12
+    assert np.array_equal(nC, N - np.arange(N))
+    lamD, nD = orc.logsin_D(y)
+    assert np.abs(lamD + math.log(N)).max() < 1e-12
+    assert np.array_equal(nD, N - 1 - np.arange(N))
+
+
+@pytest.mark.parametrize("N,jit", [(32, 0.1), (128, 0.1), (256, 0.1), (64, 0.4)])
+def test_inverse_round_trip_and_dense_solve(orc, N, jit):
+    """At M = N the Lagrange form (Eq. p6, p8) inverts the forward transform:
+    inufft(nudft_fwd(c)) = c, equal to a dense LU solve of A c = g."""
+    y = workloads.points("jitter", N, N, seed=N, jitter=jit)
+    c = workloads.coeffs(N, seed=N + 3)
+    g = orc.nudft_fwd(c, y)
+    c2 = orc.inufft(g, y, N)
+    A = np.exp(1j * np.outer(y, np.arange(N)))
+    cs = np.linalg.solve(A, g)
+    tol = 1e-12 if jit <= 0.1 else 1e-10
+    assert orc.rel_l2(c2, c) < tol
+    assert orc.rel_l2(c2, cs) < tol
+
+
+def test_inverse_exact_hit(orc):
+    """y_0 = 0 = x_0 exactly: C_0 = 0 and f_0 = g_0 (reading c7)."""
+    N = 64
+    y = workloads.points("jitter", N, N, seed=9, jitter=0.1)
+    y[0] = 0.0
+    c = workloads.coeffs(N, seed=1)
+    g = orc.nudft_fwd(c, y)
+    f = orc.inverse_f(g, y, N)
+    assert f[0] == g[0]
+    assert orc.rel_l2(orc.fft(f, -1) / N, c) < 1e-12
+
+
+# ------------------------------------------------------------- exact grid / binning
+
+def test_exact_grid_generic_points(orc):
+    N, B = 1 << 12, 1 << 7
+    y = workloads.points("uniform", 500, seed=11)
+    leaf, k0, delta = orc.exact_grid(y, N, B)
+    Y = y * N / (2 * math.pi)
+    assert np.abs((k0 + delta) - Y).max() < 1e-9
+    assert np.array_equal(leaf, np.floor((k0 + delta) / (N // B)).astype(np.int64) % B)
+    assert np.all(np.abs(delta) <= 0.5)
+
+
+def test_exact_grid_boundaries_and_hits(orc):
+    N, B = 1 << 10, 1 << 5
+    s = N // B
+    b = np.arange(B)
+    edge = b * (2 * math.pi / B)
+    below = np.nextafter(edge[1:], -10.0)
+    above = np.nextafter(edge, 10.0)
+    y = np.concatenate([[0.0], below, above])
+    leaf, k0, delta = orc.exact_grid(y, N, B)
+    assert leaf[0] == 0 and k0[0] == 0 and delta[0] == 0.0
+    # one ulp below a leaf edge lies in the leaf to the left, one above in the leaf
+    assert np.array_equal(leaf[1:B], b[:-1])
+    assert np.array_equal(leaf[B:], b)
+    # the nearest grid point of an edge is the edge's grid index, |delta| tiny
+    assert np.array_equal(k0[1:B], (b[1:] * s) % N)
+    assert np.abs(delta[1:]).max() < 1e-12
+
+
+def test_binning_is_stable_counting_sort(orc):
+    N, B = 1 << 10, 1 << 6
+    y = workloads.points("clustered", 3000, seed=4)
+    perm, start, leaf = orc.binning(y, N, B)
+    assert np.array_equal(np.sort(perm), np.arange(y.size))
+    assert np.all(np.diff(leaf[perm]) >= 0)
+    for bb in range(B):
+        seg = perm[start[bb]:start[bb + 1]]
+        assert np.all(np.diff(seg) > 0)
+        assert np.all(leaf[seg] == bb)
+    assert start[0] == 0 and start[-1] == y.size
