@@ -1,0 +1,405 @@
+#!/usr/bin/env python
+"""Benchmark of the FMM-based NUFFT / INUFFT on GB300.
+
+Workload (one step): forward NUFFT c -> g followed by the square inverse
+g -> c on N = M = 2^20 complex128 data, y_j a 40 % jittered grid
+(2 pi j/N + U(-0.4, 0.4) 2 pi/N), mixed precision at eps = 1e-6 (FP32 far
+and near field, FP64 F_j / C_k / D_j / FFT).  The plan (binning, F_j, the
+C_k / D_j log-sums) is built once, outside the timed region, as the paper
+separates setting the data structure from evaluation (Sec. 3.3).
+
+metric: non-uniform points per second, 2 M points per step (M through the
+forward and M through the inverse).  The same step is also timed in the
+plain FP64 path at eps = 1e-12 and reported under "fp64".
+
+Multi-GPU (torchrun, N > 1): replicas only -- the transform has no exchange
+step here, each rank runs the full workload on its own GPU; value is the
+points of all ranks divided by the slowest rank's time.
+
+--impl reference times the FP64 CPU oracle (the definition, O(N M)) on the
+host cores for a bounded sample of targets of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads  # noqa: E402
+
+N_LOG2 = 20
+EPS_MIXED = 1e-6
+EPS_FP64 = 1e-12
+JITTER = 0.4
+METRIC = "NUFFT points/s (forward + square inverse, N=M=2^20, mixed eps=1e-6)"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (median SM clock, reasons)."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- roofline model
+
+def stage_work(stage: str, N: int, M: int, info: dict, prec: int):
+    """Algorithmic work of one launch sequence of a stage for one transform:
+    (flops, bytes, bound).  Counted from the method, not from the code:
+    targets: near field (3s-1) pairs x 4 flops (2 complex-real FMA) + far
+    field p complex-real FMA + regular part 2q complex-real FMA, per target;
+    bytes: read y-data (k0, delta, perm: 16 B) + F, E (32 B) + write g (16 B)."""
+    L, p, q = info["lmax"], info["p"], info["q"]
+    s = N >> L
+    B = 1 << L
+    csz = 16
+    if stage == "targets":
+        flops = M * ((3 * s - 1) * 4 + p * 4 + 2 * q * 4)
+        byts = M * (16 + 32 + csz) + B * p * (8 if prec else 16) + N * csz
+        return flops, byts
+    if stage == "fft":
+        return 5 * N * N_LOG2, 2 * N * csz * 2  # two passes, read + write
+    if stage == "m2l":
+        nb = 2 * B
+        return nb * (3 * p * p * 4 + p * p * 2), nb * p * (8 if prec else 16) * 3
+    if stage == "p2m":
+        pm = max(p, 2 * q + 1)
+        return N * pm * 4, N * csz + B * pm * (8 if prec else 16)
+    return 0, 0
+
+
+def fp32_peak_tflops(peaks):
+    # 152 SMs x 128 FP32 lanes x 2 flops (FMA) x max SM clock
+    return 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+
+
+# ---------------------------------------------------------------- our arm
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_1611_09379_gb300 as nf
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+
+    N = M = 1 << N_LOG2
+    y = workloads.points("jitter", M, N, seed=1234, jitter=JITTER)
+    c = workloads.coeffs(N, seed=99)
+    yd = torch.from_numpy(y).to(dev)
+    cd = torch.from_numpy(c).to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    results = {}
+    for tag, prec, eps in (("mixed", nf.MIXED, EPS_MIXED), ("fp64", nf.FP64, EPS_FP64)):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        plan = nf.Plan(N, yd, eps=eps, prec=prec, inverse=True)
+        torch.cuda.synchronize(dev)
+        t_plan = time.perf_counter() - t0
+        g = torch.empty(M, dtype=torch.complex128, device=dev)
+        c2 = torch.empty(N, dtype=torch.complex128, device=dev)
+
+        def step():
+            plan.forward(cd, out=g)
+            plan.inverse(g, out=c2)
+
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize(dev)
+        plan.profile(True)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        with ClockSampler(local) as clk:
+            for i in range(args.steps):
+                flush.zero_()  # L2 flush outside the timed events
+                ev[i][0].record(stream)
+                step()
+                ev[i][1].record(stream)
+            torch.cuda.synchronize(dev)
+        if ws > 1:
+            dist.barrier()
+        ms = [a.elapsed_time(b) for a, b in ev]
+        stats = plan.stats()
+        # accuracy on sampled targets (oracle definition), outside the timing
+        results[tag] = {"ms": ms, "stats": stats, "info": plan.info(), "t_plan_s": t_plan,
+                        "clocks": clk.summary(), "g": g, "c2": c2}
+        # e2e through the public API with host buffers (pinned), copies timed
+        if tag == "mixed":
+            hc = torch.from_numpy(c).pin_memory()
+            hg = torch.empty(M, dtype=torch.complex128).pin_memory()
+            hc2 = torch.empty(N, dtype=torch.complex128).pin_memory()
+            dc = torch.empty(N, dtype=torch.complex128, device=dev)
+            e2e_ms = []
+            for i in range(args.warmup + args.steps):
+                flush.zero_()
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                dc.copy_(hc, non_blocking=True)
+                plan.forward(dc, out=g)
+                hg.copy_(g, non_blocking=True)
+                plan.inverse(g, out=c2)
+                hc2.copy_(c2, non_blocking=True)
+                b.record(stream)
+                torch.cuda.synchronize(dev)
+                if i >= args.warmup:
+                    e2e_ms.append(a.elapsed_time(b))
+            results[tag]["e2e_ms"] = e2e_ms
+            results[tag]["e2e_bytes"] = (N * 16, M * 16 + N * 16)
+        plan.close()
+
+    # max over ranks of the timed totals
+    def ranks_max(x):
+        if ws == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    mx = results["mixed"]
+    ms_step = ranks_max(sum(mx["ms"]) / len(mx["ms"]))
+    value = ws * 2 * M / (ms_step / 1e3)
+    fp = results["fp64"]
+    ms_fp64 = ranks_max(sum(fp["ms"]) / len(fp["ms"]))
+    e2e_ms = ranks_max(sum(mx["e2e_ms"]) / len(mx["e2e_ms"]))
+
+    if rank != 0:
+        if ws > 1:
+            dist.destroy_process_group()
+        return
+
+    # accuracy (sampled 1024 targets / 512 coefficients against the oracle)
+    acc = {}
+    try:
+        import oracle
+        idx = workloads.sample_index(M, 1024)
+        gref = oracle.nudft_fwd(c, y, idx)
+        for tag in ("mixed", "fp64"):
+            gh = results[tag]["g"].cpu().numpy()
+            c2h = results[tag]["c2"].cpu().numpy()
+            acc[tag] = {"fwd_rel_l2_sampled": oracle.rel_l2(gh[idx], gref),
+                        "inv_roundtrip_rel_l2": oracle.rel_l2(c2h, c)}
+    except Exception as e:  # accuracy is reported, not gating
+        acc["error"] = repr(e)
+
+    peaks, peak_src = _peaks()
+    stats = mx["stats"]
+    steps = args.steps
+    launches = int(sum(v[1] for v in stats.values()))
+    # dominant stage and its roofline
+    per = {k: v[0] / steps for k, v in stats.items()}
+    dom = max(per, key=per.get)
+    info = mx["info"]
+    fl, by = stage_work(dom, N, M, info, 1)
+    nseq = 2  # forward + inverse per step
+    t_dom = per[dom] / 1e3
+    if dom == "fft":
+        achieved = by * nseq / t_dom / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s"}
+    else:
+        achieved = fl * nseq / t_dom / 1e12
+        pk = fp32_peak_tflops(peaks)
+        roof = {"bound": "alu", "achieved": achieved, "peak": pk, "unit": "TFLOP/s"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    roof["kernel_stage"] = dom
+    roof["peak_source"] = (f"{peak_src}: " + ("MEASURED_PEAKS hbm_gbs" if roof["bound"] == "hbm" else
+                                             "152 SM x 128 FP32 lanes x 2 x sm_max_mhz"))
+
+    # cpu baseline: the oracle (direct forward definition) on sampled targets
+    cpu = None
+    if not args.no_cpu_baseline:
+        cpu = cpu_oracle_sample(c, y, budget_s=args.cpu_seconds)
+
+    out = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "points/s",
+        "n_gpus": ws,
+        "steps": steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32+f64 (mixed)",
+        "data": "synthetic: y jittered grid (U(-0.4,0.4)), c iid N(0,1) complex128",
+        "config": {"workload": "forward + square inverse NUFFT, N=M=2^20, complex128, jittered y, "
+                               "mixed eps=1e-6 (configs[1])",
+                   "N": N, "M": M, "eps": EPS_MIXED, "lmax": info["lmax"], "p": info["p"],
+                   "q": info["q"], "l2": "flushed (512 MiB write) between timed steps",
+                   "parallelism": "replicas" if ws > 1 else "1 gpu",
+                   "plan_s": mx["t_plan_s"]},
+        "stages_ms_per_step": {k: round(v, 5) for k, v in per.items()},
+        "fp64": {"eps": EPS_FP64, "ms_per_step": ms_fp64, "value": ws * 2 * M / (ms_fp64 / 1e3),
+                 "params": fp["info"], "stages_ms_per_step":
+                     {k: round(v[0] / steps, 5) for k, v in fp["stats"].items()},
+                 "plan_s": fp["t_plan_s"]},
+        "accuracy": acc,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": ws * 2 * M / (e2e_ms / 1e3), "unit": "points/s",
+                "h2d_bytes_per_step": mx["e2e_bytes"][0], "d2h_bytes_per_step": mx["e2e_bytes"][1]},
+        "gpu_launches": launches,
+        "clocks": mx["clocks"],
+    }
+    print(json.dumps(out))
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def cpu_oracle_sample(c, y, budget_s: float = 15.0):
+    import oracle
+    probe = workloads.sample_index(y.size, 16, seed=7)
+    t0 = time.perf_counter()
+    oracle.nudft_fwd(c, y, probe)
+    per_target = max((time.perf_counter() - t0) / probe.size, 1e-6)
+    k = int(min(max(16, budget_s / per_target), 8192))
+    idx = workloads.sample_index(y.size, k, seed=11)
+    t0 = time.perf_counter()
+    oracle.nudft_fwd(c, y, idx)
+    dt = time.perf_counter() - t0
+    return {"value": idx.size / dt, "unit": "points/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"direct forward NUDFT (Eq. p1, O(N) per target) on {idx.size} sampled targets of "
+                      f"the N=M=2^20 workload, {dt:.1f} s; the inverse oracle needs all O(N^2) "
+                      f"log-sums and is not sampled"}
+
+
+# ---------------------------------------------------------------- reference arm (the oracle)
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    N = M = 1 << N_LOG2
+    y = workloads.points("jitter", M, N, seed=1234, jitter=JITTER)
+    c = workloads.coeffs(N, seed=99)
+    per_step = 64  # targets per step: a bounded sample of the workload
+    times = []
+    for i in range(args.warmup + args.steps):
+        idx = workloads.sample_index(M, per_step, seed=100 + i)
+        t0 = time.perf_counter()
+        oracle.nudft_fwd(c, y, idx)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+    ms = 1e3 * sum(times) / len(times)
+    value = per_step / (ms / 1e3)
+    out = {
+        "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (same seeds as the GPU arm)",
+        "impl": "reference",
+        "config": {"workload": "forward + square inverse NUFFT, N=M=2^20, complex128, jittered y, "
+                               "mixed eps=1e-6 (configs[1])", "N": N, "M": M},
+        "cpu_baseline": {"value": value, "unit": "points/s", "cores": oracle.num_threads(),
+                         "kind": "oracle",
+                         "sample": f"direct forward NUDFT on {per_step} sampled targets per step"},
+        "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,204 @@
+/*
+ * nufft.h - C ABI of the GB300 (sm_103a) FMM-based NUFFT / INUFFT library.
+ *
+ * Method: Gumerov & Duraiswami, "Fast Multipole Method based filtering of
+ * non-uniformly sampled data".  A 2 pi-periodic band-limited function
+ *     f(x) = sum_{n=0}^{N-1} c_n e^{i n x}                        (Eq. p1)
+ * is sampled on the uniform grid x_k = 2 pi k / N (f_k) and at M non-uniform
+ * points y_j in [0, 2 pi) (g_j).  The library computes
+ *   forward  (problem (i), Sec. 2):   c_n -> g_j = f(y_j)
+ *            via f = IDFT(c) and g_j = F_j sum_k G(y_j - x_k) f_k   (Eq. p4, p5)
+ *   adjoint:                          g_j -> c'_n = sum_j e^{-i n y_j} g_j
+ *   inverse  (problem (ii), M = N):   g_j -> c_n with f(y_j) = g_j
+ *            via f_k = C_k sum_j G(x_k - y_j) D_j g_j             (Eq. p6, p8)
+ * where G(t) = 1/(e^{it} - 1) = -(1 + i cot(t/2))/2, and every matrix-vector
+ * product with G runs through a multilevel FMM on the circle (Sec. 2.1-2.3).
+ *
+ * Conventions for every call below
+ *   - Data pointers marked [device] are CUDA device pointers owned by the
+ *     caller; [host] pointers are ordinary host memory.  The library never
+ *     frees or retains caller pointers beyond the call.
+ *   - Complex data are interleaved (re, im).  Element type: complex128
+ *     (2 x double) unless the plan was created with NUFFT_IO_C64, then
+ *     complex64 (2 x float).
+ *   - Frequencies are one-sided, n = 0..N-1 (Eq. p1).
+ *   - N must be a power of two, 8 <= N <= 2^26; 1 <= M <= 2^27.
+ *   - y_j must be finite and in [0, 2 pi) (binary64 2 pi excluded).
+ *   - All work is enqueued on the plan's CUDA stream and is asynchronous;
+ *     a return of NUFFT_OK means the work was enqueued without error.
+ *     Calls that must inspect device results (plan creation validates y)
+ *     synchronise the stream and say so.
+ *   - Every function returns a nufft_status; it never aborts the process.
+ */
+#ifndef NUFFT_GB300_H
+#define NUFFT_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  NUFFT_OK = 0,
+  NUFFT_EINVAL = 1,     /* bad argument: N not a power of two, y out of range, ... */
+  NUFFT_ENOMEM = 2,     /* device or host allocation failed */
+  NUFFT_ECUDA = 3,      /* a CUDA runtime call or kernel launch failed */
+  NUFFT_EILLCOND = 4,   /* inverse coefficients out of range / duplicate points */
+  NUFFT_ENOTCONV = 5,   /* iterative solve did not reach the tolerance */
+  NUFFT_ETIMEOUT = 6,   /* a bounded device-side wait gave up */
+  NUFFT_ENOTSUP = 7     /* combination of options not supported */
+} nufft_status;
+
+/* Arithmetic of the FMM (the far field: P2M, M2M, M2L, L2L, L2P and the
+ * level-2 regular part).  F_j, C_k, D_j and the near-field singular pair are
+ * always formed in FP64. */
+typedef enum {
+  NUFFT_FP64 = 0,   /* everything in binary64; target rel. L2 error ~ eps (1e-12) */
+  NUFFT_MIXED = 1   /* far field and near field in binary32 (FP64 F_j and
+                       singular pair); target rel. L2 error ~ eps (1e-6) */
+} nufft_prec;
+
+/* plan flags */
+#define NUFFT_IO_C64 0x1u        /* caller data are complex64 instead of complex128 */
+#define NUFFT_WANT_INVERSE 0x2u  /* precompute C_k, D_j (Eq. p8) for exec_inv (M == N) */
+
+/* Opaque plan: the "data structure" of the paper (Sec. 3.3): the binned point
+ * set, F_j, optionally C_k / D_j, the expansion workspace and the FMM
+ * operators.  Owns its device memory. */
+typedef struct nufft_plan_s *nufft_plan;
+
+/* FMM parameters.  Any field <= 0 is chosen automatically:
+ *   lmax: tree depth, default max(2, log2 N - 5) (Sec. 3.2, l* = 5)
+ *   p:    1/t MLFMM truncation number, q: regular-series truncation number,
+ *         both from Eq. 18.2 with the fraction read as 10/(3 pi eps)
+ * Constraints: 2 <= lmax <= log2 N, 4 <= p <= 64, 2 <= q <= 32. */
+typedef struct {
+  int lmax;
+  int p;
+  int q;
+} nufft_params;
+
+/* ---------------------------------------------------------------- host only */
+
+/* Human-readable text for a status code (static storage). */
+const char *nufft_strerror(int status);
+
+/* Library version as 10000*major + 100*minor + patch. */
+int nufft_version(void);
+
+/* Parameter choice of a plan without creating it (no GPU needed).
+ * in/out: *params (fields <= 0 are filled in).  Returns NUFFT_EINVAL for an
+ * invalid N, M, eps or prec.  eps must lie in [1e-15, 1e-1]. */
+int nufft_choose_params(int64_t N, int64_t M, double eps, int prec,
+                        nufft_params *params);
+
+/* ---------------------------------------------------------------- plans */
+
+/* Build a plan: validate y, bin it into the 2^lmax leaves of the binary tree
+ * on the circle by a stable counting sort (Sec. 2.1, "setting the data
+ * structure", Sec. 3.3), precompute F_j (Eq. p5) and, with
+ * NUFFT_WANT_INVERSE, the log-sums behind C_k and D_j (Eq. p8).
+ *   out     [host]   receives the plan
+ *   N, M             grid size (power of two) and number of points
+ *   y       [device] M binary64 points in [0, 2 pi); read during the call only
+ *   eps              requested accuracy in [1e-15, 1e-1]
+ *   prec             nufft_prec
+ *   params  [host]   optional overrides (NULL = automatic)
+ *   flags            NUFFT_IO_C64 | NUFFT_WANT_INVERSE
+ *   stream           cudaStream_t to run on (NULL = legacy default stream)
+ * Synchronises the stream (it reads back validation flags).  Errors:
+ * EINVAL (bad sizes / eps / y), EILLCOND (inverse requested with duplicate
+ * points or coefficients outside the exponent range), ENOMEM, ECUDA. */
+int nufft_plan_create(nufft_plan *out, int64_t N, int64_t M, const double *y,
+                      double eps, int prec, const nufft_params *params,
+                      unsigned flags, void *stream);
+
+/* Release the plan and its device memory (synchronises its stream). */
+int nufft_plan_destroy(nufft_plan plan);
+
+/* Report the parameters in use (any output pointer may be NULL). */
+int nufft_plan_info(nufft_plan plan, int *lmax, int *p, int *q);
+
+/* Copy the plan's binned point set (the stable counting sort of Sec. 2.1)
+ * into caller buffers, for inspection and tests.  Any pointer may be NULL.
+ *   perm       [device] int32[M]   original index of the i-th sorted point
+ *   leaf_start [device] int32[B+1] first sorted index of each leaf, B = 2^lmax
+ *   k0         [device] int32[M]   nearest grid index round(y N / 2 pi) mod N
+ *   delta      [device] double[M]  y N / (2 pi) - round(y N / 2 pi)
+ * Asynchronous on the plan's stream. */
+int nufft_plan_points(nufft_plan plan, int32_t *perm, int32_t *leaf_start,
+                      int32_t *k0, double *delta);
+
+/* Copy the inverse coefficients of a plan made with NUFFT_WANT_INVERSE.
+ * With lamC_k = sum_l log|2 sin((x_k - y_l)/2)|, lamD_j = -sum_{l!=j}
+ * log|2 sin((y_j - y_l)/2)|, nC_k = #{l: y_l > x_k}, nD_j = #{l: y_l > y_j}:
+ *   Ct     [device] double[N]   (-1)^(k + nC_k) e^{lamC_k + Lambda} / N
+ *                               (0 where a point sits exactly on x_k)
+ *   Dt     [device] double2[M]  (-1)^nD_j e^{lamD_j - Lambda} i e^{-i N y_j/2}
+ *                               (sorted point order, see nufft_plan_points)
+ *   Lambda [host]   the common scale, the midpoint of the range of lamD
+ * so that N Ct_k Dt_j = C_k D_j of Eq. p8.  Any pointer may be NULL.
+ * Synchronises the stream when Lambda is requested. */
+int nufft_plan_inverse_coeffs(nufft_plan plan, double *Ct, double *Dt, double *Lambda);
+
+/* Change the stream later calls are enqueued on. */
+int nufft_plan_set_stream(nufft_plan plan, void *stream);
+
+/* Forward NUFFT (problem (i)): g_j = sum_n c_n e^{i n y_j}.
+ *   c [device] N coefficients, g [device] M outputs (original point order).
+ * c and g must not overlap.  Asynchronous. */
+int nufft_plan_exec_fwd(nufft_plan plan, const void *c, void *g);
+
+/* Adjoint NUFFT: c_n = sum_j e^{-i n y_j} g_j (conjugate transpose of the
+ * forward map; the FMM runs with sources and targets exchanged, Sec. 2.1).
+ *   g [device] M inputs, c [device] N outputs.  Asynchronous. */
+int nufft_plan_exec_adj(nufft_plan plan, const void *g, void *c);
+
+/* Square inverse NUFFT (problem (ii), M == N): the unique band-limited c
+ * with sum_n c_n e^{i n y_j} = g_j, by the Lagrange form Eq. p6 / p8
+ * followed by the DFT of Eq. p1.  Needs NUFFT_WANT_INVERSE.
+ *   g [device] M inputs, c [device] N outputs.  Asynchronous. */
+int nufft_plan_exec_inv(nufft_plan plan, const void *g, void *c);
+
+/* ---------------------------------------------------------------- profiling */
+
+/* Stages of an evaluation, for nufft_plan_stats. */
+enum {
+  NUFFT_STAGE_FFT = 0,      /* c_n <-> f_k (Eq. p1) */
+  NUFFT_STAGE_P2M = 1,      /* charges + leaf multipoles */
+  NUFFT_STAGE_M2M = 2,      /* upward pass */
+  NUFFT_STAGE_LEVEL2 = 3,   /* regular-part coefficients (Eq. p20) */
+  NUFFT_STAGE_M2L = 4,      /* M2L + L2L, levels 3..lmax */
+  NUFFT_STAGE_TARGETS = 5,  /* L2P + near field + regular part + F_j / C_k */
+  NUFFT_STAGE_OTHER = 6,    /* type conversions */
+  NUFFT_NSTAGES = 7
+};
+
+/* Enable (1) or disable (0) per-stage timing: when enabled, every exec call
+ * records CUDA events around each stage on the plan's stream.  Enabling
+ * resets the accumulated times and launch counts. */
+int nufft_plan_profile(nufft_plan plan, int enable);
+
+/* Accumulated device time (ms, from the CUDA events) and kernel launches per
+ * stage since profiling was last enabled.  stage_ms [host] double[NUFFT_NSTAGES],
+ * launches [host] int64[NUFFT_NSTAGES]; either may be NULL.  Synchronises the
+ * stream.  Launch counts are kept even when timing is disabled. */
+int nufft_plan_stats(nufft_plan plan, double *stage_ms, int64_t *launches);
+
+/* ---------------------------------------------------------------- one-shot */
+
+/* Plan + exec + destroy in one call, with the paper's argument order
+ * (nufft_fwd(c_n, N, y_j, M, eps) -> g_j).  All data pointers [device].
+ * Synchronises the stream. */
+int nufft_fwd(const void *c, int64_t N, const double *y, int64_t M, double eps,
+              int prec, unsigned flags, void *g, void *stream);
+int nufft_adj(const void *g, const double *y, int64_t M, int64_t N, double eps,
+              int prec, unsigned flags, void *c, void *stream);
+int inufft(const void *g, const double *y, int64_t M, int64_t N, double eps,
+           int prec, unsigned flags, void *c, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NUFFT_GB300_H */

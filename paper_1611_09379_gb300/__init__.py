@@ -1,0 +1,275 @@
+"""Python binding of the GB300 FMM-based NUFFT / INUFFT library (libnufft_gb300.so).
+
+Argument marshalling only: every step of every transform runs in the CUDA
+kernels behind the C ABI of ``include/nufft.h``.  PyTorch supplies device
+memory and streams.  There is no CPU fallback: if the shared library has not
+been built (``paper_1611_09379_gb300.build.build()``), importing raises.
+
+    import torch, paper_1611_09379_gb300 as nf
+    y = torch.rand(M, dtype=torch.float64, device="cuda") * 2 * math.pi
+    plan = nf.Plan(N, y, eps=1e-12, prec=nf.FP64)
+    g = plan.forward(c)            # g_j = sum_n c_n e^{i n y_j}
+    c2 = plan.adjoint(g)           # c2_n = sum_j e^{-i n y_j} g_j
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libnufft_gb300.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        "libnufft_gb300.so is missing: build it with "
+        "`python -m paper_1611_09379_gb300.build` (nvcc, sm_103a)")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+OK, EINVAL, ENOMEM, ECUDA, EILLCOND, ENOTCONV, ETIMEOUT, ENOTSUP = range(8)
+STAGES = ("fft", "p2m", "m2m", "level2", "m2l", "targets", "other")
+FP64, MIXED = 0, 1
+IO_C64 = 0x1
+WANT_INVERSE = 0x2
+
+# every symbol declared in include/nufft.h
+SYMBOLS = [
+    "nufft_strerror", "nufft_version", "nufft_choose_params", "nufft_plan_create",
+    "nufft_plan_destroy", "nufft_plan_info", "nufft_plan_points", "nufft_plan_inverse_coeffs",
+    "nufft_plan_set_stream", "nufft_plan_profile", "nufft_plan_stats",
+    "nufft_plan_exec_fwd",
+    "nufft_plan_exec_adj", "nufft_plan_exec_inv", "nufft_fwd", "nufft_adj", "inufft",
+]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("lmax", ctypes.c_int), ("p", ctypes.c_int), ("q", ctypes.c_int)]
+
+
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_lib.nufft_strerror.restype = ctypes.c_char_p
+_lib.nufft_strerror.argtypes = [ctypes.c_int]
+_lib.nufft_version.restype = ctypes.c_int
+_lib.nufft_choose_params.argtypes = [_I64, _I64, ctypes.c_double, ctypes.c_int, ctypes.POINTER(Params)]
+_lib.nufft_plan_create.argtypes = [ctypes.POINTER(_P), _I64, _I64, _P, ctypes.c_double, ctypes.c_int,
+                                   ctypes.POINTER(Params), ctypes.c_uint, _P]
+_lib.nufft_plan_destroy.argtypes = [_P]
+_lib.nufft_plan_info.argtypes = [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                 ctypes.POINTER(ctypes.c_int)]
+_lib.nufft_plan_set_stream.argtypes = [_P, _P]
+_lib.nufft_plan_points.argtypes = [_P, _P, _P, _P, _P]
+_lib.nufft_plan_profile.argtypes = [_P, ctypes.c_int]
+_lib.nufft_plan_stats.argtypes = [_P, _P, _P]
+_lib.nufft_plan_inverse_coeffs.argtypes = [_P, _P, _P, ctypes.POINTER(ctypes.c_double)]
+for _n in ("nufft_plan_exec_fwd", "nufft_plan_exec_adj", "nufft_plan_exec_inv"):
+    getattr(_lib, _n).argtypes = [_P, _P, _P]
+for _n in ("nufft_fwd",):
+    getattr(_lib, _n).argtypes = [_P, _I64, _P, _I64, ctypes.c_double, ctypes.c_int, ctypes.c_uint, _P, _P]
+for _n in ("nufft_adj", "inufft"):
+    getattr(_lib, _n).argtypes = [_P, _P, _I64, _I64, ctypes.c_double, ctypes.c_int, ctypes.c_uint, _P, _P]
+for _n in SYMBOLS:
+    if _n not in ("nufft_strerror", "nufft_version"):
+        getattr(_lib, _n).restype = ctypes.c_int
+
+
+class NufftError(RuntimeError):
+    def __init__(self, code: int, where: str = ""):
+        self.code = code
+        msg = _lib.nufft_strerror(code).decode()
+        super().__init__(f"{where}: {msg} (status {code})" if where else msg)
+
+
+def _check(rc: int, where: str):
+    if rc != OK:
+        raise NufftError(rc, where)
+
+
+def strerror(code: int) -> str:
+    return _lib.nufft_strerror(code).decode()
+
+
+def version() -> int:
+    return _lib.nufft_version()
+
+
+def choose_params(N: int, M: int, eps: float, prec: int = FP64, lmax: int = 0, p: int = 0, q: int = 0):
+    """(lmax, p, q) the library would use (host only, no GPU needed)."""
+    prm = Params(lmax, p, q)
+    _check(_lib.nufft_choose_params(N, M, eps, prec, ctypes.byref(prm)), "nufft_choose_params")
+    return prm.lmax, prm.p, prm.q
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_handle(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return _P(s.cuda_stream)
+
+
+def _dev_ptr(t, dtype, n, what):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{what} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{what} must have dtype {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{what} must be contiguous")
+    if t.numel() != n:
+        raise ValueError(f"{what} must have {n} elements, got {t.numel()}")
+    return _P(t.data_ptr())
+
+
+class Plan:
+    """A transform plan: the binned point set and FMM workspace (Sec. 3.3).
+
+    N: grid size (power of two); y: CUDA float64 tensor of M points in [0, 2 pi).
+    prec: FP64 or MIXED; io: 'c128' or 'c64' element type of c and g;
+    inverse=True precomputes C_k, D_j for :meth:`inverse` (needs M == N).
+    lmax / p / q override the automatic parameters (0 = automatic).
+    """
+
+    def __init__(self, N: int, y, eps: float = 1e-12, prec: int = FP64, io: str = "c128",
+                 inverse: bool = False, lmax: int = 0, p: int = 0, q: int = 0, stream=None):
+        torch = _torch()
+        self.N = int(N)
+        self.M = int(y.numel())
+        self.prec = prec
+        self.io = io
+        self.cdtype = torch.complex64 if io == "c64" else torch.complex128
+        flags = (IO_C64 if io == "c64" else 0) | (WANT_INVERSE if inverse else 0)
+        self._stream = stream
+        h = _P()
+        prm = Params(lmax, p, q)
+        yp = _dev_ptr(y, torch.float64, self.M, "y")
+        _check(_lib.nufft_plan_create(ctypes.byref(h), self.N, self.M, yp, eps, prec,
+                                      ctypes.byref(prm), flags, _stream_handle(stream)),
+               "nufft_plan_create")
+        self._h = h
+        self.device = y.device
+
+    def info(self):
+        a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(_lib.nufft_plan_info(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+               "nufft_plan_info")
+        return {"lmax": a.value, "p": b.value, "q": c.value}
+
+    def points(self):
+        """The binned point set: (perm, leaf_start, k0, delta) as CUDA tensors."""
+        torch = _torch()
+        B = 1 << self.info()["lmax"]
+        perm = torch.empty(self.M, dtype=torch.int32, device=self.device)
+        start = torch.empty(B + 1, dtype=torch.int32, device=self.device)
+        k0 = torch.empty(self.M, dtype=torch.int32, device=self.device)
+        delta = torch.empty(self.M, dtype=torch.float64, device=self.device)
+        _check(_lib.nufft_plan_points(self._h, _P(perm.data_ptr()), _P(start.data_ptr()),
+                                      _P(k0.data_ptr()), _P(delta.data_ptr())), "nufft_plan_points")
+        return perm, start, k0, delta
+
+    def inverse_coeffs(self):
+        """(Ct, Dt, Lambda): C_k e^Lambda / N and D_j e^-Lambda / 2 (sorted points)."""
+        torch = _torch()
+        Ct = torch.empty(self.N, dtype=torch.float64, device=self.device)
+        Dt = torch.empty(self.M, dtype=torch.complex128, device=self.device)
+        lam = ctypes.c_double()
+        _check(_lib.nufft_plan_inverse_coeffs(self._h, _P(Ct.data_ptr()), _P(Dt.data_ptr()),
+                                              ctypes.byref(lam)), "nufft_plan_inverse_coeffs")
+        return Ct, Dt, lam.value
+
+    def profile(self, enable: bool = True):
+        """Enable per-stage CUDA-event timing (resets the accumulated stats)."""
+        _check(_lib.nufft_plan_profile(self._h, 1 if enable else 0), "nufft_plan_profile")
+
+    def stats(self):
+        """{stage: (ms, launches)} accumulated since profile() (synchronises)."""
+        ms = (ctypes.c_double * len(STAGES))()
+        nl = (ctypes.c_int64 * len(STAGES))()
+        _check(_lib.nufft_plan_stats(self._h, ctypes.cast(ms, _P), ctypes.cast(nl, _P)),
+               "nufft_plan_stats")
+        return {name: (ms[i], nl[i]) for i, name in enumerate(STAGES)}
+
+    def set_stream(self, stream):
+        self._stream = stream
+        _check(_lib.nufft_plan_set_stream(self._h, _stream_handle(stream)), "nufft_plan_set_stream")
+
+    def _out(self, n, out):
+        torch = _torch()
+        if out is None:
+            out = torch.empty(n, dtype=self.cdtype, device=self.device)
+        return out
+
+    def forward(self, c, out=None):
+        """g_j = sum_n c_n e^{i n y_j} (asynchronous on the plan's stream)."""
+        g = self._out(self.M, out)
+        _check(_lib.nufft_plan_exec_fwd(self._h, _dev_ptr(c, self.cdtype, self.N, "c"),
+                                        _dev_ptr(g, self.cdtype, self.M, "g")), "nufft_plan_exec_fwd")
+        return g
+
+    def adjoint(self, g, out=None):
+        """c_n = sum_j e^{-i n y_j} g_j."""
+        c = self._out(self.N, out)
+        _check(_lib.nufft_plan_exec_adj(self._h, _dev_ptr(g, self.cdtype, self.M, "g"),
+                                        _dev_ptr(c, self.cdtype, self.N, "c")), "nufft_plan_exec_adj")
+        return c
+
+    def inverse(self, g, out=None):
+        """Band-limited c with sum_n c_n e^{i n y_j} = g_j (M == N, Eq. p6/p8)."""
+        c = self._out(self.N, out)
+        _check(_lib.nufft_plan_exec_inv(self._h, _dev_ptr(g, self.cdtype, self.M, "g"),
+                                        _dev_ptr(c, self.cdtype, self.N, "c")), "nufft_plan_exec_inv")
+        return c
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.nufft_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def _oneshot(fn, a, b, c, d, eps, prec, io, out, stream, name):
+    flags = IO_C64 if io == "c64" else 0
+    _check(fn(a, b, c, d, eps, prec, flags, out, _stream_handle(stream)), name)
+
+
+def nufft_fwd(c, N: int, y, M: int, eps: float, prec: int = FP64, io: str = "c128", stream=None):
+    """One-shot forward transform in the paper's argument order: nufft_fwd(c_n, N, y_j, M, eps)."""
+    torch = _torch()
+    cd = torch.complex64 if io == "c64" else torch.complex128
+    g = torch.empty(M, dtype=cd, device=y.device)
+    _oneshot(_lib.nufft_fwd, _dev_ptr(c, cd, N, "c"), N, _dev_ptr(y, torch.float64, M, "y"), M, eps,
+             prec, io, _P(g.data_ptr()), stream, "nufft_fwd")
+    return g
+
+
+def nufft_adj(g, y, M: int, N: int, eps: float, prec: int = FP64, io: str = "c128", stream=None):
+    torch = _torch()
+    cd = torch.complex64 if io == "c64" else torch.complex128
+    c = torch.empty(N, dtype=cd, device=y.device)
+    _oneshot(_lib.nufft_adj, _dev_ptr(g, cd, M, "g"), _dev_ptr(y, torch.float64, M, "y"), M, N, eps,
+             prec, io, _P(c.data_ptr()), stream, "nufft_adj")
+    return c
+
+
+def inufft(g, y, M: int, N: int, eps: float, prec: int = FP64, io: str = "c128", stream=None):
+    """One-shot square inverse: inufft(g_j, y_j, M, N, eps) -> c_n (M == N)."""
+    torch = _torch()
+    cd = torch.complex64 if io == "c64" else torch.complex128
+    c = torch.empty(N, dtype=cd, device=y.device)
+    _oneshot(_lib.inufft, _dev_ptr(g, cd, M, "g"), _dev_ptr(y, torch.float64, M, "y"), M, N, eps,
+             prec, io, _P(c.data_ptr()), stream, "inufft")
+    return c

@@ -1,0 +1,137 @@
+// Internal definitions shared by the CUDA translation units of the library.
+//
+// Coordinates.  Every point lives in "grid units" Y = y N / (2 pi), so the
+// uniform grid x_k = 2 pi k / N sits at the integers.  A non-uniform point is
+// stored as its nearest grid index k0 (int) plus an offset delta in
+// [-1/2, 1/2] (binary64, relative precision of delta itself), formed from
+// y with a double-double product.  Distances between a point and grid
+// points, t = (k0 - k) + delta, then keep full relative precision down to
+// the exact hit, which the kernel G(t) of Eq. p5 needs near its pole.
+//
+// Tree.  Level l has 2^l arcs (boxes) of W_l = N / 2^l grid units
+// (Sec. 2.1); leaves are level L = lmax with s = N / 2^L grid points each.
+// Box i at level l has centre (i + 1/2) W_l.  Expansions are scaled by the
+// box width so the translation operators do not depend on the level.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+#include "../../include/nufft.h"
+
+namespace nufft {
+
+constexpr double kTwoPiHi = 6.283185307179586;          // fl(2 pi)
+constexpr double kTwoPiLo = 2.4492935982947064e-16;     // 2 pi - fl(2 pi)
+constexpr double kInvTwoPiHi = 0.15915494309189535;     // fl(1/(2 pi))
+constexpr double kInvTwoPiLo = -9.839338337591243e-18;  // 1/(2 pi) - fl(1/(2 pi))
+constexpr double kInvPi = 0.3183098861837907;           // fl(1/pi)
+constexpr double kPi = 3.141592653589793;
+
+// box offset of level l (>= 2) in the per-level concatenated arrays
+__host__ __device__ inline int64_t level_off(int l) { return (int64_t(1) << l) - 4; }
+
+template <class T> struct cplx_t;
+template <> struct cplx_t<double> { using type = double2; };
+template <> struct cplx_t<float> { using type = float2; };
+template <class T> using cplx = typename cplx_t<T>::type;
+
+template <class T> __host__ __device__ inline cplx<T> mk(T a, T b) { cplx<T> r; r.x = a; r.y = b; return r; }
+template <class V> __host__ __device__ inline V cadd(V a, V b) { a.x += b.x; a.y += b.y; return a; }
+template <class V> __host__ __device__ inline V csub(V a, V b) { a.x -= b.x; a.y -= b.y; return a; }
+template <class V> __host__ __device__ inline V cmul(V a, V b) {
+  V r; r.x = a.x * b.x - a.y * b.y; r.y = a.x * b.y + a.y * b.x; return r;
+}
+template <class V, class S> __host__ __device__ inline V cscale(V a, S s) { a.x *= s; a.y *= s; return a; }
+template <class V> __host__ __device__ inline V cconj(V a) { a.y = -a.y; return a; }
+
+__device__ inline double2 to_d2(float2 a) { return make_double2(a.x, a.y); }
+__device__ inline double2 to_d2(double2 a) { return a; }
+template <class T> __device__ inline cplx<T> from_d2(double2 a);
+template <> __device__ inline double2 from_d2<double>(double2 a) { return a; }
+template <> __device__ inline float2 from_d2<float>(double2 a) { return make_float2((float)a.x, (float)a.y); }
+
+// Sizes and pointers of one FMM evaluation, passed by value to kernels.
+struct TreeDims {
+  int64_t N;   // grid size (power of two)
+  int L;       // leaf level
+  int s;       // grid points per leaf = N >> L
+  int p;       // 1/t expansion length
+  int q;       // regular-series truncation number
+  int pm;      // multipole length kept (max(p, 2q + 1))
+};
+
+// Device-side error word (set by kernels, read back by the host).
+enum DevStatus : int {
+  kDevOk = 0,
+  kDevBadPoint = 1,     // y not finite or outside [0, 2 pi)
+  kDevSegTooLarge = 2,  // a leaf held more points than the segment sort supports
+  kDevIllCond = 4,      // duplicate points / exponent range in the inverse
+};
+
+}  // namespace nufft
+
+// One kernel's FMM operator set (device pointers): the cot kernel's 1/t
+// operators or the log kernel's (inverse coefficients).
+struct FmmOps {
+  const void* m2l = nullptr;   // [4][p][p]
+  const void* l2l = nullptr;   // [2][p][p]
+  const double* reg = nullptr; // [4][nq][nq] level-2 weights and shifts
+  int nq = 0;                  // number of level-2 polynomial coefficients
+  double c1 = 0, c2 = 0;       // constants per unit charge in Omega_1 / Omega_2
+  int log_kernel = 0;          // adds M_0 log W_l in M2L
+  const double* leaf_shift = nullptr;  // moments subtracted from every leaf
+};
+
+// Per-stage event timing of a plan (see nufft_plan_profile).
+struct StageProf {
+  static constexpr int kMaxPairs = 4096;
+  int enabled = 0;
+  int npairs = 0;
+  cudaEvent_t ev[2 * kMaxPairs] = {};
+  int stage[kMaxPairs] = {};
+  double ms[NUFFT_NSTAGES] = {};
+  int64_t launches[NUFFT_NSTAGES] = {};
+  int open_stage = -1;
+};
+
+// The plan object behind the opaque handle of nufft.h.
+struct nufft_plan_s {
+  int64_t N = 0, M = 0;
+  int L = 0, B = 0, s = 0, p = 0, q = 0, pm = 0;
+  int prec = 0;
+  unsigned flags = 0;
+  double eps = 0;
+  cudaStream_t stream = nullptr;
+  // non-uniform point set, sorted by leaf (stable by original index)
+  int32_t *perm = nullptr;        // [M] original index of sorted point
+  int32_t *leaf_start = nullptr;  // [B+1]
+  int32_t *k0 = nullptr;          // [M] nearest grid index (sorted order)
+  double *delta = nullptr;        // [M] offset in grid units (sorted order)
+  double2 *F = nullptr;           // [M] F_j = (e^{i N y_j} - 1)/N, Eq. p5
+  double2 *E = nullptr;           // [M] e^{i pi delta} sin(pi delta)/(pi delta)
+  // inverse coefficients (Eq. p8), scaled by a common factor
+  double2 *Dt = nullptr;          // [M] D_j e^{-Lambda}
+  double *Ct = nullptr;           // [N] real C_k e^{+Lambda}
+  double *Lambda = nullptr;       // [1] common scale of C and D
+  // FMM workspace
+  void *mexp = nullptr;    // [levels 2..L][box][pm] complex (T)
+  void *lexp = nullptr;    // [levels 3..L][box][p] complex (T)
+  void *charge = nullptr;  // [max(N, M)] complex (T): charges in sorted order
+  double2 *grid = nullptr; // [N] complex128 work vector on the grid
+  double2 *grid2 = nullptr;// [N] complex128 FFT ping-pong buffer
+  double2 *lvl2 = nullptr; // [4*2q + 1] level-2 polynomial coefficients D_l, then Q
+  // operators (device copies, in T)
+  void *op_m2m = nullptr;  // [2][pm][pm]  transposed: [sigma][k][m]
+  void *op_m2l = nullptr;  // [4][p][p]    transposed: [d][m][n], d = -3,-2,2,3
+  void *op_l2l = nullptr;  // [2][p][p]    transposed: [sigma][n'][n]
+  void *op_p2m = nullptr;  // [s][pm] powers rho_o^m of the uniform grid in a leaf
+  double *op_reg = nullptr;// [2][2q][2q] level-2 weights W1, W2 (FP64)
+  double2 *fft_tw = nullptr; // FFT twiddle tables
+  int fft_tw_lo_bits = 0;
+  int *status = nullptr;   // device error word
+  int *seg_overflow = nullptr;
+  StageProf *prof = nullptr;
+};
+
+// Bracket the launches of one stage (no-ops unless profiling is enabled).
+void prof_begin(nufft_plan_s* pl, int stage);
+void prof_end(nufft_plan_s* pl, int launches);

@@ -1,0 +1,181 @@
+// Stockham auto-sort FFT for the c_n <-> f_k step (Eq. p1, Sec. 2):
+//   out_n = sum_k in_k e^{sign 2 pi i n k / N},  N = 2^L, no scaling.
+// Each pass is one radix-R Stockham iteration,
+//   a_r = in[j + r N/R] * w^{sign r (j mod Ns) / (Ns R)},  A = DFT_R(a),
+//   out[(j/Ns) Ns R + (j mod Ns) + r' Ns] = A_r',
+// with the size-R DFT done in shared memory by a CTA for J adjacent j (so
+// the strided global reads and writes move J contiguous elements).  Passes
+// multiply Ns by R until it reaches N.  Twiddles come from two small tables,
+// w^{m/N} = T_hi[m >> b] * T_lo[m & (2^b - 1)], filled once per plan with
+// sincospi of exact arguments.
+#include "common.cuh"
+
+namespace nufft {
+
+constexpr int kFftSmemElems = 4096;  // R * J complex elements staged per CTA
+
+__global__ void k_fft_tables(double2* __restrict__ tw, int64_t N, int lo_bits) {
+  int64_t nlo = int64_t(1) << lo_bits, nhi = N >> lo_bits;
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double s, c;
+  if (i < nlo) {
+    sincospi(2.0 * (double)i / (double)N, &s, &c);
+    tw[i] = make_double2(c, s);
+  } else if (i < nlo + nhi) {
+    int64_t h = i - nlo;
+    // 2 h 2^b / N reduced mod 2 exactly (all powers of two)
+    sincospi(2.0 * (double)(h << lo_bits) / (double)N, &s, &c);
+    tw[i] = make_double2(c, s);
+  }
+}
+
+// e^{sign 2 pi i m / N}, 0 <= m < N
+__device__ inline double2 twiddle(const double2* __restrict__ tw, int64_t m, int lo_bits,
+                                  int sign) {
+  int64_t nlo = int64_t(1) << lo_bits;
+  double2 a = tw[m & (nlo - 1)], b = tw[nlo + (m >> lo_bits)];
+  double2 r = cmul(a, b);
+  if (sign < 0) r.y = -r.y;
+  return r;
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_fft_pass(const cplx<T>* __restrict__ in,
+                                                  cplx<T>* __restrict__ out, int64_t N,
+                                                  int logR, int64_t Ns, int J, int sign,
+                                                  const double2* __restrict__ tw,
+                                                  int lo_bits) {
+  extern __shared__ unsigned char smraw[];
+  cplx<T>* sm = reinterpret_cast<cplx<T>*>(smraw);     // [R][J]
+  const int R = 1 << logR;
+  cplx<T>* twR = sm + R * J;                           // [R/2] e^{sign 2 pi i m / R}
+  const int64_t NR = N >> logR;
+  const int64_t j0 = (int64_t)blockIdx.x * J;
+  const int nth = blockDim.x;
+
+  for (int m = threadIdx.x; m < R / 2; m += nth)
+    twR[m] = from_d2<T>(twiddle(tw, (int64_t)m * (N >> logR), lo_bits, sign));
+
+  // load with pass twiddle into bit-reversed position
+  for (int e = threadIdx.x; e < R * J; e += nth) {
+    int r = e / J, jj = e - r * J;
+    int64_t j = j0 + jj;
+    double2 v = to_d2(in[j + (int64_t)r * NR]);
+    int64_t jm = j % Ns;
+    if (jm != 0 && r != 0) {
+      // w^{r jm / (Ns R)} = e^{2 pi i m / N} with m = r jm (N / (Ns R))
+      int64_t m = ((int64_t)r * jm) * (N / (Ns << logR));
+      v = cmul(v, twiddle(tw, m & (N - 1), lo_bits, sign));
+    }
+    int rb = __brev(r) >> (32 - logR);
+    if (logR == 0) rb = 0;
+    sm[rb * J + jj] = from_d2<T>(v);
+  }
+  __syncthreads();
+  // radix-2 decimation-in-time butterflies
+  for (int h = 1; h < R; h <<= 1) {
+    int stride = R / (2 * h);
+    for (int e = threadIdx.x; e < (R / 2) * J; e += nth) {
+      int bf = e / J, jj = e - bf * J;
+      int grp = bf / h, pos = bf - grp * h;
+      int i0 = grp * 2 * h + pos, i1 = i0 + h;
+      cplx<T> w = twR[pos * stride];
+      cplx<T> a = sm[i0 * J + jj], b = cmul(sm[i1 * J + jj], w);
+      sm[i0 * J + jj] = cadd(a, b);
+      sm[i1 * J + jj] = csub(a, b);
+    }
+    __syncthreads();
+  }
+  // store: out[(j/Ns) Ns R + j%Ns + r Ns]
+  for (int e = threadIdx.x; e < R * J; e += nth) {
+    int r, jj;
+    if (Ns >= J) { r = e / J; jj = e - r * J; }   // J contiguous per r
+    else { jj = e / R; r = e - jj * R; }          // Ns == 1 case: R contiguous per j
+    int64_t j = j0 + jj;
+    int64_t jm = j % Ns;
+    int64_t dst = (j / Ns) * Ns * R + jm + (int64_t)r * Ns;
+    out[dst] = sm[r * J + jj];
+  }
+}
+
+}  // namespace nufft
+
+using namespace nufft;
+
+int fft_lo_bits(int64_t N) {
+  int L = 0;
+  while ((int64_t(1) << L) < N) ++L;
+  return (L + 1) / 2;
+}
+
+size_t fft_table_elems(int64_t N) {
+  int b = fft_lo_bits(N);
+  return (size_t)(int64_t(1) << b) + (size_t)(N >> b);
+}
+
+int fft_init_tables(double2* tw, int64_t N, cudaStream_t st) {
+  int b = fft_lo_bits(N);
+  int64_t n = (int64_t(1) << b) + (N >> b);
+  k_fft_tables<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(tw, N, b);
+  return cudaGetLastError() == cudaSuccess ? NUFFT_OK : NUFFT_ECUDA;
+}
+
+// Split L into passes of at most 10 bits, as evenly as possible.
+static int fft_plan_passes(int L, int* logR) {
+  int np = (L + 9) / 10;
+  if (np == 0) np = 1;
+  int base = L / np, extra = L % np;
+  for (int i = 0; i < np; ++i) logR[i] = base + (i < extra ? 1 : 0);
+  return np;
+}
+
+int fft_num_passes(int64_t N) {
+  int L = 0;
+  while ((int64_t(1) << L) < N) ++L;
+  int logR[8];
+  return fft_plan_passes(L, logR);
+}
+
+// out = FFT(in); buf is a scratch vector of N elements.  in may equal buf.
+// The result lands in out (in is not modified unless in == buf).
+template <class T>
+int fft_run(const cplx<T>* in, cplx<T>* out, cplx<T>* buf, int64_t N, int sign,
+            const double2* tw, cudaStream_t st) {
+  int L = 0;
+  while ((int64_t(1) << L) < N) ++L;
+  int logR[8];
+  int np = fft_plan_passes(L, logR);
+  // ping-pong so the last pass writes `out`
+  const cplx<T>* src = in;
+  int64_t Ns = 1;
+  int b = fft_lo_bits(N);
+  for (int i = 0; i < np; ++i) {
+    cplx<T>* dst = ((np - 1 - i) % 2 == 0) ? out : buf;
+    int R = 1 << logR[i];
+    int J = kFftSmemElems / R;
+    if (J > (int)(N >> logR[i])) J = (int)(N >> logR[i]);
+    if (J < 1) J = 1;
+    size_t smem = (size_t)(R * J + R / 2) * sizeof(cplx<T>);
+    unsigned grid = (unsigned)((N >> logR[i]) / J);
+    k_fft_pass<T><<<grid, 256, smem, st>>>(src, dst, N, logR[i], Ns, J, sign, tw, b);
+    src = dst;
+    Ns <<= logR[i];
+  }
+  return cudaGetLastError() == cudaSuccess ? NUFFT_OK : NUFFT_ECUDA;
+}
+
+int fft_configure() {
+  size_t big = (size_t)(kFftSmemElems + 512) * sizeof(double2);
+  if (cudaFuncSetAttribute(k_fft_pass<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)big) != cudaSuccess)
+    return NUFFT_ECUDA;
+  if (cudaFuncSetAttribute(k_fft_pass<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)big) != cudaSuccess)
+    return NUFFT_ECUDA;
+  return NUFFT_OK;
+}
+
+template int fft_run<double>(const double2*, double2*, double2*, int64_t, int, const double2*,
+                             cudaStream_t);
+template int fft_run<float>(const float2*, float2*, float2*, int64_t, int, const double2*,
+                            cudaStream_t);

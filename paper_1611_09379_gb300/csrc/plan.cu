@@ -1,0 +1,495 @@
+// Host implementation of the C ABI declared in include/nufft.h: parameter
+// choice (Eq. 18, 18.2, 25), construction of the FMM operators, plan
+// lifecycle and the exec entry points.
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "common.cuh"
+
+using namespace nufft;
+
+// kernels and drivers from the other translation units
+size_t setup_tmp_bytes(int64_t M, int64_t B);
+int setup_points(nufft_plan_s* pl, const double* y, void* tmp);
+int fft_init_tables(double2* tw, int64_t N, cudaStream_t st);
+size_t fft_table_elems(int64_t N);
+int fft_configure();
+int fft_num_passes(int64_t N);
+template <class T>
+int fft_run(const cplx<T>* in, cplx<T>* out, cplx<T>* buf, int64_t N, int sign, const double2* tw,
+            cudaStream_t st);
+template <class T> int fmm_configure();
+template <class T> int fmm_forward(nufft_plan_s* pl, void* g);
+template <class T> int fmm_to_grid(nufft_plan_s* pl, const void* g, int inverse);
+int inverse_precompute(nufft_plan_s* pl, void* tmp, size_t tmp_bytes);
+size_t inverse_tmp_bytes(const nufft_plan_s* pl);
+int convert_c128_to_c64(const double2* in, float2* out, int64_t n, cudaStream_t st);
+int convert_c64_to_c128(const float2* in, double2* out, int64_t n, cudaStream_t st);
+
+namespace {
+
+int ilog2(int64_t n) {
+  int L = 0;
+  while ((int64_t(1) << L) < n) ++L;
+  return L;
+}
+
+bool is_pow2(int64_t n) { return n > 0 && (n & (n - 1)) == 0; }
+
+// zeta(s) for even s >= 2 by Euler-Maclaurin summation (K = 64, three
+// correction terms; the remainder is below 1e-30).
+long double zeta_even(int s) {
+  const int K = 64;
+  long double sum = 0;
+  for (int k = 1; k < K; ++k) sum += powl((long double)k, -(long double)s);
+  long double Kl = K;
+  sum += powl(Kl, 1.0L - s) / (s - 1) + 0.5L * powl(Kl, -(long double)s);
+  // + B2/2! s K^{-s-1} + B4/4! s(s+1)(s+2) K^{-s-3} + B6/6! s..(s+4) K^{-s-5}
+  long double t1 = (1.0L / 6.0L) / 2.0L * s * powl(Kl, -(long double)s - 1);
+  long double t2 = (-1.0L / 30.0L) / 24.0L * s * (s + 1.0L) * (s + 2.0L) * powl(Kl, -(long double)s - 3);
+  long double t3 = (1.0L / 42.0L) / 720.0L * s * (s + 1.0L) * (s + 2.0L) * (s + 3.0L) * (s + 4.0L) *
+                   powl(Kl, -(long double)s - 5);
+  return sum + t1 + t2 + t3;
+}
+
+struct Binom {
+  std::vector<long double> c;
+  int n;
+  explicit Binom(int nmax) : c((size_t)(nmax + 1) * (nmax + 1), 0.0L), n(nmax) {
+    for (int i = 0; i <= nmax; ++i) {
+      c[(size_t)i * (nmax + 1)] = 1;
+      for (int k = 1; k <= i; ++k)
+        c[(size_t)i * (nmax + 1) + k] = c[(size_t)(i - 1) * (nmax + 1) + k - 1] +
+                                         (k <= i - 1 ? c[(size_t)(i - 1) * (nmax + 1) + k] : 0);
+    }
+  }
+  long double operator()(int i, int k) const {
+    return (k < 0 || k > i) ? 0 : c[(size_t)i * (n + 1) + k];
+  }
+};
+
+thread_local int g_configured = 0;
+
+int configure_once() {
+  if (g_configured) return NUFFT_OK;
+  int rc = fft_configure();
+  if (!rc) rc = fmm_configure<double>();
+  if (!rc) rc = fmm_configure<float>();
+  if (!rc) g_configured = 1;
+  return rc;
+}
+
+template <class T>
+std::vector<T> cast_vec(const std::vector<long double>& v) {
+  std::vector<T> r(v.size());
+  for (size_t i = 0; i < v.size(); ++i) r[i] = (T)v[i];
+  return r;
+}
+
+int upload(void** dst, const void* src, size_t bytes) {
+  if (cudaMalloc(dst, bytes) != cudaSuccess) return NUFFT_ENOMEM;
+  if (cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice) != cudaSuccess) return NUFFT_ECUDA;
+  return NUFFT_OK;
+}
+
+// Build the translation operators (level independent, scaled form) and
+// the level-2 weights; upload in the plan's arithmetic type.
+int build_operators(nufft_plan_s* pl) {
+  const int p = pl->p, pm = pl->pm, q = pl->q, Q2 = 2 * q, s = pl->s;
+  Binom C(2 * 64 + 2);
+  // M2M [sigma][k][m]
+  std::vector<long double> m2m((size_t)2 * pm * pm, 0.0L);
+  for (int sg = 0; sg < 2; ++sg) {
+    long double sig = sg ? 0.25L : -0.25L;
+    for (int m = 0; m < pm; ++m)
+      for (int k = 0; k <= m; ++k)
+        m2m[(size_t)sg * pm * pm + (size_t)k * pm + m] =
+            C(m, k) * powl(0.5L, k) * powl(sig, m - k);
+  }
+  // M2L [d][m][n], d = -3, -2, 2, 3
+  const int dval[4] = {-3, -2, 2, 3};
+  std::vector<long double> m2l((size_t)4 * p * p, 0.0L);
+  for (int t = 0; t < 4; ++t)
+    for (int m = 0; m < p; ++m)
+      for (int n = 0; n < p; ++n) {
+        long double v = C(m + n, n) * powl((long double)dval[t], -(long double)(m + n + 1));
+        if ((m + 1) & 1) v = -v;  // (-1)^(m+1)
+        m2l[(size_t)t * p * p + (size_t)m * p + n] = v;
+      }
+  // L2L [sigma][n'][n]
+  std::vector<long double> l2l((size_t)2 * p * p, 0.0L);
+  for (int sg = 0; sg < 2; ++sg) {
+    long double sig = sg ? 0.25L : -0.25L;
+    for (int n = 0; n < p; ++n)
+      for (int k = n; k < p; ++k)
+        l2l[(size_t)sg * p * p + (size_t)k * p + n] =
+            0.5L * C(k, n) * powl(0.5L, n) * powl(sig, k - n);
+  }
+  // P2M table for the uniform grid: rho_o = o/s - 1/2
+  std::vector<long double> rp((size_t)s * pm);
+  for (int o = 0; o < s; ++o) {
+    long double rho = (long double)o / s - 0.5L, pw = 1;
+    for (int m = 0; m < pm; ++m) { rp[(size_t)o * pm + m] = pw; pw *= rho; }
+  }
+  // level-2 weights W1, W2 [l][i], shifts S-, S+ [i][r]
+  std::vector<double> reg((size_t)4 * Q2 * Q2, 0.0);
+  for (int l = 0; l < Q2; ++l)
+    for (int i = 0; i < Q2; ++i) {
+      if (((i + l) & 1) == 0) continue;
+      int m = (i + l + 1) / 2;
+      if (m < 1 || m > q) continue;
+      long double z = zeta_even(2 * m);
+      long double am = 2.0L * z * powl(0.25L, m);
+      long double bm = 2.0L * z * (1.0L - powl(0.25L, m));
+      reg[(size_t)l * Q2 + i] = (double)(C(2 * m - 1, l) * am);
+      reg[(size_t)Q2 * Q2 + (size_t)l * Q2 + i] = (double)(C(2 * m - 1, l) * bm);
+    }
+  for (int i = 0; i < Q2; ++i)
+    for (int r = 0; r <= i; ++r) {
+      long double c = C(i, r) * powl(0.5L, i - r);
+      reg[(size_t)2 * Q2 * Q2 + (size_t)i * Q2 + r] = (double)(((i - r) & 1) ? -c : c);
+      reg[(size_t)3 * Q2 * Q2 + (size_t)i * Q2 + r] = (double)c;
+    }
+  int rc;
+  if (pl->prec == NUFFT_FP64) {
+    auto a = cast_vec<double>(m2m), b = cast_vec<double>(m2l), c = cast_vec<double>(l2l),
+         d = cast_vec<double>(rp);
+    if ((rc = upload(&pl->op_m2m, a.data(), a.size() * 8))) return rc;
+    if ((rc = upload(&pl->op_m2l, b.data(), b.size() * 8))) return rc;
+    if ((rc = upload(&pl->op_l2l, c.data(), c.size() * 8))) return rc;
+    if ((rc = upload(&pl->op_p2m, d.data(), d.size() * 8))) return rc;
+  } else {
+    auto a = cast_vec<float>(m2m), b = cast_vec<float>(m2l), c = cast_vec<float>(l2l),
+         d = cast_vec<float>(rp);
+    if ((rc = upload(&pl->op_m2m, a.data(), a.size() * 4))) return rc;
+    if ((rc = upload(&pl->op_m2l, b.data(), b.size() * 4))) return rc;
+    if ((rc = upload(&pl->op_l2l, c.data(), c.size() * 4))) return rc;
+    if ((rc = upload(&pl->op_p2m, d.data(), d.size() * 4))) return rc;
+  }
+  return upload((void**)&pl->op_reg, reg.data(), reg.size() * 8);
+}
+
+void free_plan(nufft_plan_s* pl) {
+  void* ptrs[] = {pl->perm, pl->leaf_start, pl->k0, pl->delta, pl->F, pl->E, pl->Dt, pl->Ct,
+                  pl->Lambda, pl->mexp, pl->lexp, pl->charge, pl->grid, pl->grid2, pl->lvl2,
+                  pl->op_m2m, pl->op_m2l, pl->op_l2l, pl->op_p2m, pl->op_reg, pl->fft_tw,
+                  pl->status, pl->seg_overflow};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (pl->prof) {
+    for (cudaEvent_t e : pl->prof->ev)
+      if (e) cudaEventDestroy(e);
+    delete pl->prof;
+  }
+  delete pl;
+}
+
+template <class X>
+int dalloc(X** p, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  return cudaMalloc((void**)p, bytes) == cudaSuccess ? NUFFT_OK : NUFFT_ENOMEM;
+}
+
+}  // namespace
+
+void prof_begin(nufft_plan_s* pl, int stage) {
+  StageProf* pf = pl->prof;
+  if (!pf) return;
+  pf->open_stage = stage;
+  if (!pf->enabled || pf->npairs >= StageProf::kMaxPairs) return;
+  cudaEvent_t& e = pf->ev[2 * pf->npairs];
+  if (!e && cudaEventCreate(&e) != cudaSuccess) { e = nullptr; return; }
+  cudaEventRecord(e, pl->stream);
+}
+
+void prof_end(nufft_plan_s* pl, int launches) {
+  StageProf* pf = pl->prof;
+  if (!pf || pf->open_stage < 0) return;
+  pf->launches[pf->open_stage] += launches;
+  if (pf->enabled && pf->npairs < StageProf::kMaxPairs && pf->ev[2 * pf->npairs]) {
+    cudaEvent_t& e = pf->ev[2 * pf->npairs + 1];
+    if (e || cudaEventCreate(&e) == cudaSuccess) {
+      cudaEventRecord(e, pl->stream);
+      pf->stage[pf->npairs++] = pf->open_stage;
+    }
+  }
+  pf->open_stage = -1;
+}
+
+extern "C" {
+
+int nufft_plan_profile(nufft_plan pl, int enable) {
+  if (!pl || !pl->prof) return NUFFT_EINVAL;
+  StageProf* pf = pl->prof;
+  pf->enabled = enable ? 1 : 0;
+  pf->npairs = 0;
+  for (int i = 0; i < NUFFT_NSTAGES; ++i) { pf->ms[i] = 0; pf->launches[i] = 0; }
+  return NUFFT_OK;
+}
+
+int nufft_plan_stats(nufft_plan pl, double* stage_ms, int64_t* launches) {
+  if (!pl || !pl->prof) return NUFFT_EINVAL;
+  StageProf* pf = pl->prof;
+  if (cudaStreamSynchronize(pl->stream) != cudaSuccess) return NUFFT_ECUDA;
+  for (int i = 0; i < pf->npairs; ++i) {
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, pf->ev[2 * i], pf->ev[2 * i + 1]) != cudaSuccess)
+      return NUFFT_ECUDA;
+    pf->ms[pf->stage[i]] += ms;
+  }
+  pf->npairs = 0;
+  for (int i = 0; i < NUFFT_NSTAGES; ++i) {
+    if (stage_ms) stage_ms[i] = pf->ms[i];
+    if (launches) launches[i] = pf->launches[i];
+  }
+  return NUFFT_OK;
+}
+
+
+const char* nufft_strerror(int status) {
+  switch (status) {
+    case NUFFT_OK: return "success";
+    case NUFFT_EINVAL: return "invalid argument";
+    case NUFFT_ENOMEM: return "out of memory";
+    case NUFFT_ECUDA: return "CUDA error";
+    case NUFFT_EILLCOND: return "inverse is ill-conditioned (duplicate points or exponent range)";
+    case NUFFT_ENOTCONV: return "iteration did not converge";
+    case NUFFT_ETIMEOUT: return "device wait timed out";
+    case NUFFT_ENOTSUP: return "unsupported option combination";
+    default: return "unknown status";
+  }
+}
+
+int nufft_version(void) { return 100; }
+
+int nufft_choose_params(int64_t N, int64_t M, double eps, int prec, nufft_params* prm) {
+  if (!prm) return NUFFT_EINVAL;
+  if (!is_pow2(N) || N < 8 || N > (int64_t(1) << 26)) return NUFFT_EINVAL;
+  if (M < 1 || M > (int64_t(1) << 27)) return NUFFT_EINVAL;
+  if (!(eps >= 1e-15 && eps <= 1e-1)) return NUFFT_EINVAL;
+  if (prec != NUFFT_FP64 && prec != NUFFT_MIXED) return NUFFT_EINVAL;
+  if (prec == NUFFT_MIXED && eps < 1e-7) return NUFFT_EINVAL;
+  int LN = ilog2(N);
+  int L = prm->lmax;
+  if (L <= 0) {
+    // Eq. 25 with the empirical l* = 5 of Sec. 3.2: log2 sqrt(N M) - 5
+    double lopt = 0.5 * std::log2((double)N * (double)M) - 5.0;
+    L = (int)std::lround(lopt);
+    if (L < 2) L = 2;
+    if (L > LN) L = LN;
+  }
+  if (L < 2 || L > LN || L > 24) return NUFFT_EINVAL;
+  // Eq. 18.2 with the fraction of Eq. 18 solved for eps: 10 / (3 pi eps)
+  double r = 10.0 / (3.0 * M_PI * eps);
+  int q = prm->q, p = prm->p;
+  if (q <= 0) {
+    q = (int)std::ceil(0.5 * std::log2(r));
+    if (q < 2) q = 2;
+  }
+  if (p <= 0) {
+    p = (int)std::ceil(1.0 + std::log(r) / std::log(3.0) + L / std::log2(3.0));
+    if (p < 4) p = 4;
+  }
+  if (q < 2 || q > 32 || p < 4 || p > 64) return NUFFT_EINVAL;
+  prm->lmax = L;
+  prm->p = p;
+  prm->q = q;
+  return NUFFT_OK;
+}
+
+int nufft_plan_create(nufft_plan* out, int64_t N, int64_t M, const double* y, double eps,
+                      int prec, const nufft_params* params, unsigned flags, void* stream) {
+  if (!out || !y) return NUFFT_EINVAL;
+  *out = nullptr;
+  nufft_params prm{0, 0, 0};
+  if (params) prm = *params;
+  int rc = nufft_choose_params(N, M, eps, prec, &prm);
+  if (rc) return rc;
+  if ((flags & NUFFT_WANT_INVERSE) && M != N) return NUFFT_EINVAL;
+  if ((rc = configure_once())) return rc;
+  nufft_plan_s* pl = new (std::nothrow) nufft_plan_s();
+  if (!pl) return NUFFT_ENOMEM;
+  pl->prof = new (std::nothrow) StageProf();
+  if (!pl->prof) { delete pl; return NUFFT_ENOMEM; }
+  pl->N = N; pl->M = M; pl->L = prm.lmax; pl->B = 1 << prm.lmax; pl->s = (int)(N >> prm.lmax);
+  pl->p = prm.p; pl->q = prm.q; pl->pm = prm.p > 2 * prm.q + 1 ? prm.p : 2 * prm.q + 1;
+  pl->prec = prec; pl->flags = flags; pl->eps = eps;
+  pl->stream = (cudaStream_t)stream;
+  const int64_t B = pl->B;
+  const size_t csz = prec == NUFFT_FP64 ? sizeof(double2) : sizeof(float2);
+  const int64_t nm = (int64_t(2) << pl->L) - 4, nl = (int64_t(2) << pl->L) - 8;
+  int64_t big = N > M ? N : M;
+  if ((rc = dalloc(&pl->perm, M * 4)) || (rc = dalloc(&pl->leaf_start, (B + 1) * 4)) ||
+      (rc = dalloc(&pl->k0, M * 4)) || (rc = dalloc(&pl->delta, M * 8)) ||
+      (rc = dalloc(&pl->F, M * 16)) || (rc = dalloc(&pl->E, M * 16)) ||
+      (rc = dalloc(&pl->mexp, nm * pl->pm * csz)) ||
+      (rc = dalloc(&pl->lexp, (nl > 0 ? nl : 1) * pl->p * csz)) ||
+      (rc = dalloc(&pl->charge, big * csz)) || (rc = dalloc(&pl->grid, N * 16)) ||
+      (rc = dalloc(&pl->grid2, N * 16)) || (rc = dalloc(&pl->lvl2, (8 * pl->q + 1) * 16)) ||
+      (rc = dalloc(&pl->fft_tw, fft_table_elems(N) * 16)) || (rc = dalloc(&pl->status, 16))) {
+    free_plan(pl);
+    return rc;
+  }
+  if ((rc = build_operators(pl))) { free_plan(pl); return rc; }
+  cudaStream_t st = pl->stream;
+  if (cudaMemsetAsync(pl->status, 0, 16, st) != cudaSuccess) { free_plan(pl); return NUFFT_ECUDA; }
+  if ((rc = fft_init_tables(pl->fft_tw, N, st))) { free_plan(pl); return rc; }
+  size_t tb = setup_tmp_bytes(M, B);
+  if (flags & NUFFT_WANT_INVERSE) {
+    size_t ib = inverse_tmp_bytes(pl);
+    if (ib > tb) tb = ib;
+  }
+  void* tmp = nullptr;
+  if (cudaMalloc(&tmp, tb) != cudaSuccess) { free_plan(pl); return NUFFT_ENOMEM; }
+  rc = setup_points(pl, y, tmp);
+  if (!rc && (flags & NUFFT_WANT_INVERSE)) rc = inverse_precompute(pl, tmp, tb);
+  int hstat = 0;
+  if (!rc) {
+    if (cudaMemcpyAsync(&hstat, pl->status, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      rc = NUFFT_ECUDA;
+  }
+  cudaFree(tmp);
+  if (!rc && (hstat & kDevBadPoint)) rc = NUFFT_EINVAL;
+  if (!rc && (hstat & kDevSegTooLarge)) rc = NUFFT_EINVAL;
+  if (!rc && (hstat & kDevIllCond)) rc = NUFFT_EILLCOND;
+  if (rc) { free_plan(pl); return rc; }
+  *out = pl;
+  return NUFFT_OK;
+}
+
+int nufft_plan_destroy(nufft_plan pl) {
+  if (!pl) return NUFFT_EINVAL;
+  cudaStreamSynchronize(pl->stream);
+  free_plan(pl);
+  return NUFFT_OK;
+}
+
+int nufft_plan_info(nufft_plan pl, int* lmax, int* p, int* q) {
+  if (!pl) return NUFFT_EINVAL;
+  if (lmax) *lmax = pl->L;
+  if (p) *p = pl->p;
+  if (q) *q = pl->q;
+  return NUFFT_OK;
+}
+
+int nufft_plan_points(nufft_plan pl, int32_t* perm, int32_t* leaf_start, int32_t* k0,
+                      double* delta) {
+  if (!pl) return NUFFT_EINVAL;
+  cudaStream_t st = pl->stream;
+  auto cp = [&](void* dst, const void* src, size_t bytes) {
+    return !dst || cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, st) == cudaSuccess;
+  };
+  if (!cp(perm, pl->perm, pl->M * 4) || !cp(leaf_start, pl->leaf_start, (pl->B + 1) * 4) ||
+      !cp(k0, pl->k0, pl->M * 4) || !cp(delta, pl->delta, pl->M * 8))
+    return NUFFT_ECUDA;
+  return NUFFT_OK;
+}
+
+int nufft_plan_inverse_coeffs(nufft_plan pl, double* Ct, double* Dt, double* Lambda) {
+  if (!pl || !pl->Ct) return NUFFT_EINVAL;
+  cudaStream_t st = pl->stream;
+  if (Ct && cudaMemcpyAsync(Ct, pl->Ct, pl->N * 8, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+    return NUFFT_ECUDA;
+  if (Dt && cudaMemcpyAsync(Dt, pl->Dt, pl->M * 16, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+    return NUFFT_ECUDA;
+  if (Lambda) {
+    if (cudaMemcpyAsync(Lambda, pl->Lambda, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return NUFFT_ECUDA;
+  }
+  return NUFFT_OK;
+}
+
+int nufft_plan_set_stream(nufft_plan pl, void* stream) {
+  if (!pl) return NUFFT_EINVAL;
+  pl->stream = (cudaStream_t)stream;
+  return NUFFT_OK;
+}
+
+int nufft_plan_exec_fwd(nufft_plan pl, const void* c, void* g) {
+  if (!pl || !c || !g) return NUFFT_EINVAL;
+  int rc;
+  const double2* cin = (const double2*)c;
+  if (pl->flags & NUFFT_IO_C64) {
+    prof_begin(pl, NUFFT_STAGE_OTHER);
+    rc = convert_c64_to_c128((const float2*)c, pl->grid2, pl->N, pl->stream);
+    prof_end(pl, 1);
+    if (rc) return rc;
+    cin = pl->grid2;
+  }
+  // f_k = sum_n c_n e^{+2 pi i n k/N}  (Eq. p1, unscaled inverse DFT)
+  prof_begin(pl, NUFFT_STAGE_FFT);
+  rc = fft_run<double>(cin, pl->grid, pl->grid2, pl->N, +1, pl->fft_tw, pl->stream);
+  prof_end(pl, fft_num_passes(pl->N));
+  if (rc) return rc;
+  return pl->prec == NUFFT_FP64 ? fmm_forward<double>(pl, g) : fmm_forward<float>(pl, g);
+}
+
+static int grid_to_coeffs(nufft_plan_s* pl, void* c) {
+  int rc;
+  // c'_n = sum_k u_k e^{-2 pi i n k/N}
+  if (pl->flags & NUFFT_IO_C64) {
+    prof_begin(pl, NUFFT_STAGE_FFT);
+    rc = fft_run<double>(pl->grid, pl->grid, pl->grid2, pl->N, -1, pl->fft_tw, pl->stream);
+    prof_end(pl, fft_num_passes(pl->N));
+    if (rc) return rc;
+    prof_begin(pl, NUFFT_STAGE_OTHER);
+    rc = convert_c128_to_c64(pl->grid, (float2*)c, pl->N, pl->stream);
+    prof_end(pl, 1);
+    return rc;
+  }
+  prof_begin(pl, NUFFT_STAGE_FFT);
+  rc = fft_run<double>(pl->grid, (double2*)c, pl->grid2, pl->N, -1, pl->fft_tw, pl->stream);
+  prof_end(pl, fft_num_passes(pl->N));
+  return rc;
+}
+
+int nufft_plan_exec_adj(nufft_plan pl, const void* g, void* c) {
+  if (!pl || !c || !g) return NUFFT_EINVAL;
+  int rc = pl->prec == NUFFT_FP64 ? fmm_to_grid<double>(pl, g, 0) : fmm_to_grid<float>(pl, g, 0);
+  if (rc) return rc;
+  return grid_to_coeffs(pl, c);
+}
+
+int nufft_plan_exec_inv(nufft_plan pl, const void* g, void* c) {
+  if (!pl || !c || !g) return NUFFT_EINVAL;
+  if (!(pl->flags & NUFFT_WANT_INVERSE) || !pl->Ct) return NUFFT_EINVAL;
+  int rc = pl->prec == NUFFT_FP64 ? fmm_to_grid<double>(pl, g, 1) : fmm_to_grid<float>(pl, g, 1);
+  if (rc) return rc;
+  return grid_to_coeffs(pl, c);  // the 1/N of Eq. p1 is folded into C_k
+}
+
+static int one_shot(int which, const void* in, int64_t N, const double* y, int64_t M, double eps,
+                    int prec, unsigned flags, void* out, void* stream) {
+  nufft_plan pl = nullptr;
+  if (which == 2) flags |= NUFFT_WANT_INVERSE;
+  int rc = nufft_plan_create(&pl, N, M, y, eps, prec, nullptr, flags, stream);
+  if (rc) return rc;
+  if (which == 0) rc = nufft_plan_exec_fwd(pl, in, out);
+  else if (which == 1) rc = nufft_plan_exec_adj(pl, in, out);
+  else rc = nufft_plan_exec_inv(pl, in, out);
+  if (!rc && cudaStreamSynchronize(pl->stream) != cudaSuccess) rc = NUFFT_ECUDA;
+  nufft_plan_destroy(pl);
+  return rc;
+}
+
+int nufft_fwd(const void* c, int64_t N, const double* y, int64_t M, double eps, int prec,
+              unsigned flags, void* g, void* stream) {
+  return one_shot(0, c, N, y, M, eps, prec, flags, g, stream);
+}
+
+int nufft_adj(const void* g, const double* y, int64_t M, int64_t N, double eps, int prec,
+              unsigned flags, void* c, void* stream) {
+  return one_shot(1, g, N, y, M, eps, prec, flags, c, stream);
+}
+
+int inufft(const void* g, const double* y, int64_t M, int64_t N, double eps, int prec,
+           unsigned flags, void* c, void* stream) {
+  return one_shot(2, g, N, y, M, eps, prec, flags, c, stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,94 @@
+"""Host-side checks of the C ABI (no GPU): the library loads and exports every
+symbol include/nufft.h declares; parameter choice (Eq. 18.2 with reading c5,
+Eq. 25 with l* = 5) and argument validation; the double-double constants."""
+import os
+import re
+from fractions import Fraction
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def nf():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1611_09379_gb300 as nf
+    return nf
+
+
+def _declared_symbols():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        txt = open(os.path.join(ROOT, "include", fn)).read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b([A-Za-z_]\w*)\s*\(", txt, flags=re.M):
+            if m.group(1) not in ("if", "defined"):
+                names.add(m.group(1))
+    return names
+
+
+def test_library_exports_every_declared_symbol(nf):
+    import ctypes
+    lib = ctypes.CDLL(nf.LIB_PATH)
+    declared = _declared_symbols()
+    assert len(declared) >= 14
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert declared == set(nf.SYMBOLS)
+
+
+def test_choose_params_matches_eq18_2_reading(nf):
+    # reading c5: q = ceil(1/2 log2(10/(3 pi eps))), p = ceil(1 + log3(...) + lmax/log2 3)
+    assert nf.choose_params(1 << 20, 1 << 20, 1e-12) == (15, 36, 20)
+    assert nf.choose_params(1 << 20, 1 << 20, 1e-6, nf.MIXED) == (15, 24, 11)
+    assert nf.choose_params(1 << 12, 1 << 12, 1e-12) == (7, 31, 20)
+    assert nf.choose_params(1 << 24, 1 << 24, 1e-6, nf.MIXED) == (19, 26, 11)
+    assert nf.choose_params(1 << 16, 1 << 16, 1e-8) == (11, 25, 14)
+    # small N clamps lmax to 2
+    assert nf.choose_params(8, 8, 1e-6)[0] == 2
+    # explicit overrides are kept
+    assert nf.choose_params(1 << 12, 1 << 12, 1e-6, nf.FP64, lmax=4, p=10, q=5) == (4, 10, 5)
+
+
+@pytest.mark.parametrize("args", [
+    (1000, 1000, 1e-6, 0),      # N not a power of two
+    (4, 4, 1e-6, 0),            # N < 8
+    (1 << 10, 0, 1e-6, 0),      # M < 1
+    (1 << 10, 10, 1e-16, 0),    # eps below 1e-15
+    (1 << 10, 10, 0.5, 0),      # eps above 1e-1
+    (1 << 10, 10, 1e-6, 7),     # unknown precision
+    (1 << 10, 10, 1e-9, 1),     # mixed precision cannot reach 1e-9
+])
+def test_choose_params_rejects(nf, args):
+    with pytest.raises(nf.NufftError) as e:
+        nf.choose_params(*args)
+    assert e.value.code == nf.EINVAL
+
+
+def test_lmax_override_bounds(nf):
+    with pytest.raises(nf.NufftError):
+        nf.choose_params(1 << 10, 1 << 10, 1e-6, nf.FP64, lmax=11)
+    with pytest.raises(nf.NufftError):
+        nf.choose_params(1 << 10, 1 << 10, 1e-6, nf.FP64, p=65)
+
+
+def test_strerror_and_version(nf):
+    assert nf.strerror(0) == "success"
+    assert "invalid" in nf.strerror(nf.EINVAL)
+    assert nf.version() >= 100
+
+
+def test_double_double_constants_are_exact(orc):
+    """fl(1/(2pi)) + lo and fl(2pi) + lo in the CUDA sources equal the exact
+    values to 2^-106 relative (checked against the oracle's 480-bit pi)."""
+    src = open(os.path.join(ROOT, "paper_1611_09379_gb300", "csrc", "common.cuh")).read()
+    val = dict(re.findall(r"constexpr double (k\w+) = ([-\d.e+]+);", src))
+    pi = Fraction(orc.PI_FIXED, 1 << orc._PI_BITS)
+    for hi, lo, exact in (("kInvTwoPiHi", "kInvTwoPiLo", 1 / (2 * pi)), ("kTwoPiHi", "kTwoPiLo", 2 * pi)):
+        s = Fraction(float(val[hi])) + Fraction(float(val[lo]))
+        assert abs(s - exact) / exact < Fraction(1, 2 ** 104)
+        assert float(val[hi]) == float(exact)
