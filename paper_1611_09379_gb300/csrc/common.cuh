@@ -108,16 +108,25 @@ struct nufft_plan_s {
   double *delta = nullptr;        // [M] offset in grid units (sorted order)
   double2 *F = nullptr;           // [M] F_j = (e^{i N y_j} - 1)/N, Eq. p5
   double2 *E = nullptr;           // [M] e^{i pi delta} sin(pi delta)/(pi delta)
+  // FP32 copies for the mixed path (rounded from the FP64 values)
+  float *delta_f = nullptr;       // [M]
+  float2 *Ff = nullptr, *Ef = nullptr;  // [M]
+  float2 *lvl2f = nullptr;        // level-2 coefficients
   // inverse coefficients (Eq. p8), scaled by a common factor
   double2 *Dt = nullptr;          // [M] D_j e^{-Lambda}
-  double *Ct = nullptr;           // [N] real C_k e^{+Lambda}
+  double *Ct = nullptr;           // [N] real C_k e^{+Lambda} / N
+  float *Ctf = nullptr;           // [N] FP32 copy (mixed path)
   double *Lambda = nullptr;       // [1] common scale of C and D
   // FMM workspace
   void *mexp = nullptr;    // [levels 2..L][box][pm] complex (T)
   void *lexp = nullptr;    // [levels 3..L][box][p] complex (T)
   void *charge = nullptr;  // [max(N, M)] complex (T): charges in sorted order
-  double2 *grid = nullptr; // [N] complex128 work vector on the grid
-  double2 *grid2 = nullptr;// [N] complex128 FFT ping-pong buffer
+  void *selft = nullptr;   // [M] complex (T): nearest-pair terms of the adjoint / inverse
+  void *srcrec = nullptr;  // [M] packed (k0, delta, charge) records: 16 B (FP32) / 32 B (FP64)
+  double2 *grid = nullptr; // [N] work vector on the grid (complex128 storage; used
+                           //     as complex64 by the mixed path)
+  double2 *grid2 = nullptr;// [N] FFT scratch
+  double2 *grid3 = nullptr;// [N] second FFT scratch (three or more passes)
   double2 *lvl2 = nullptr; // [4*2q + 1] level-2 polynomial coefficients D_l, then Q
   // operators (device copies, in T)
   void *op_m2m = nullptr;  // [2][pm][pm]  transposed: [sigma][k][m]
@@ -126,6 +135,7 @@ struct nufft_plan_s {
   void *op_p2m = nullptr;  // [s][pm] powers rho_o^m of the uniform grid in a leaf
   double *op_reg = nullptr;// [2][2q][2q] level-2 weights W1, W2 (FP64)
   double2 *fft_tw = nullptr; // FFT twiddle tables
+  float2 *fft_tw_f = nullptr;
   int fft_tw_lo_bits = 0;
   int *status = nullptr;   // device error word
   int *seg_overflow = nullptr;

@@ -29,22 +29,39 @@ __global__ void k_fft_tables(double2* __restrict__ tw, int64_t N, int lo_bits) {
   }
 }
 
-// e^{sign 2 pi i m / N}, 0 <= m < N
-__device__ inline double2 twiddle(const double2* __restrict__ tw, int64_t m, int lo_bits,
-                                  int sign) {
+// e^{sign 2 pi i m / N}, 0 <= m < N, from the two tables
+template <class T>
+__device__ inline cplx<T> twiddle_t(const cplx<T>* __restrict__ tw, int64_t m, int lo_bits,
+                                    int sign) {
   int64_t nlo = int64_t(1) << lo_bits;
-  double2 a = tw[m & (nlo - 1)], b = tw[nlo + (m >> lo_bits)];
-  double2 r = cmul(a, b);
+  cplx<T> a = tw[m & (nlo - 1)], b = tw[nlo + (m >> lo_bits)];
+  cplx<T> r = cmul(a, b);
   if (sign < 0) r.y = -r.y;
   return r;
 }
 
+// in / out element type chosen at run time (uniform branch): complex128 when
+// *_f64 != 0, complex64 otherwise; arithmetic in T.
 template <class T>
-__global__ void __launch_bounds__(256) k_fft_pass(const cplx<T>* __restrict__ in,
-                                                  cplx<T>* __restrict__ out, int64_t N,
+__device__ inline cplx<T> load_c(const void* p, int64_t i, int f64) {
+  if (f64) {
+    double2 v = reinterpret_cast<const double2*>(p)[i];
+    return mk<T>((T)v.x, (T)v.y);
+  }
+  float2 v = reinterpret_cast<const float2*>(p)[i];
+  return mk<T>((T)v.x, (T)v.y);
+}
+template <class T>
+__device__ inline void store_c(void* p, int64_t i, int f64, cplx<T> v) {
+  if (f64) reinterpret_cast<double2*>(p)[i] = make_double2((double)v.x, (double)v.y);
+  else reinterpret_cast<float2*>(p)[i] = make_float2((float)v.x, (float)v.y);
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_fft_pass(const void* __restrict__ in, int in_f64,
+                                                  void* __restrict__ out, int out_f64, int64_t N,
                                                   int logR, int64_t Ns, int J, int sign,
-                                                  const double2* __restrict__ tw,
-                                                  int lo_bits) {
+                                                  const cplx<T>* __restrict__ tw, int lo_bits) {
   extern __shared__ unsigned char smraw[];
   cplx<T>* sm = reinterpret_cast<cplx<T>*>(smraw);     // [R][J]
   const int R = 1 << logR;
@@ -54,22 +71,22 @@ __global__ void __launch_bounds__(256) k_fft_pass(const cplx<T>* __restrict__ in
   const int nth = blockDim.x;
 
   for (int m = threadIdx.x; m < R / 2; m += nth)
-    twR[m] = from_d2<T>(twiddle(tw, (int64_t)m * (N >> logR), lo_bits, sign));
+    twR[m] = twiddle_t<T>(tw, (int64_t)m * (N >> logR), lo_bits, sign);
 
   // load with pass twiddle into bit-reversed position
+  const int64_t tstep = N / (Ns << logR);
   for (int e = threadIdx.x; e < R * J; e += nth) {
     int r = e / J, jj = e - r * J;
     int64_t j = j0 + jj;
-    double2 v = to_d2(in[j + (int64_t)r * NR]);
-    int64_t jm = j % Ns;
+    cplx<T> v = load_c<T>(in, j + (int64_t)r * NR, in_f64);
+    int64_t jm = j & (Ns - 1);
     if (jm != 0 && r != 0) {
       // w^{r jm / (Ns R)} = e^{2 pi i m / N} with m = r jm (N / (Ns R))
-      int64_t m = ((int64_t)r * jm) * (N / (Ns << logR));
-      v = cmul(v, twiddle(tw, m & (N - 1), lo_bits, sign));
+      int64_t m = ((int64_t)r * jm) * tstep;
+      v = cmul(v, twiddle_t<T>(tw, m & (N - 1), lo_bits, sign));
     }
-    int rb = __brev(r) >> (32 - logR);
-    if (logR == 0) rb = 0;
-    sm[rb * J + jj] = from_d2<T>(v);
+    int rb = logR ? (int)(__brev((unsigned)r) >> (32 - logR)) : 0;
+    sm[rb * J + jj] = v;
   }
   __syncthreads();
   // radix-2 decimation-in-time butterflies
@@ -90,12 +107,17 @@ __global__ void __launch_bounds__(256) k_fft_pass(const cplx<T>* __restrict__ in
   for (int e = threadIdx.x; e < R * J; e += nth) {
     int r, jj;
     if (Ns >= J) { r = e / J; jj = e - r * J; }   // J contiguous per r
-    else { jj = e / R; r = e - jj * R; }          // Ns == 1 case: R contiguous per j
+    else { jj = e / R; r = e - jj * R; }          // small Ns: R contiguous per j
     int64_t j = j0 + jj;
-    int64_t jm = j % Ns;
+    int64_t jm = j & (Ns - 1);
     int64_t dst = (j / Ns) * Ns * R + jm + (int64_t)r * Ns;
-    out[dst] = sm[r * J + jj];
+    store_c<T>(out, dst, out_f64, sm[r * J + jj]);
   }
+}
+
+__global__ void k_tw_to_float(const double2* __restrict__ a, float2* __restrict__ b, int64_t n) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) b[i] = make_float2((float)a[i].x, (float)a[i].y);
 }
 
 }  // namespace nufft
@@ -113,10 +135,12 @@ size_t fft_table_elems(int64_t N) {
   return (size_t)(int64_t(1) << b) + (size_t)(N >> b);
 }
 
-int fft_init_tables(double2* tw, int64_t N, cudaStream_t st) {
+// tw: double2 tables, twf: float2 copy (may be null)
+int fft_init_tables(double2* tw, float2* twf, int64_t N, cudaStream_t st) {
   int b = fft_lo_bits(N);
   int64_t n = (int64_t(1) << b) + (N >> b);
   k_fft_tables<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(tw, N, b);
+  if (twf) k_tw_to_float<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(tw, twf, n);
   return cudaGetLastError() == cudaSuccess ? NUFFT_OK : NUFFT_ECUDA;
 }
 
@@ -136,29 +160,37 @@ int fft_num_passes(int64_t N) {
   return fft_plan_passes(L, logR);
 }
 
-// out = FFT(in); buf is a scratch vector of N elements.  in may equal buf.
-// The result lands in out (in is not modified unless in == buf).
+// out = FFT(in) in arithmetic T; in / out are complex128 (f64 = 1) or
+// complex64.  Intermediate passes alternate between the scratch vectors buf
+// and buf2 (N cplx<T> each; buf2 is used only with three or more passes), so
+// they keep T precision and never touch `out`.  `in` is only read.
 template <class T>
-int fft_run(const cplx<T>* in, cplx<T>* out, cplx<T>* buf, int64_t N, int sign,
-            const double2* tw, cudaStream_t st) {
+int fft_run(const void* in, int in_f64, void* out, int out_f64, cplx<T>* buf, cplx<T>* buf2,
+            int64_t N, int sign, const cplx<T>* tw, cudaStream_t st) {
   int L = 0;
   while ((int64_t(1) << L) < N) ++L;
   int logR[8];
   int np = fft_plan_passes(L, logR);
-  // ping-pong so the last pass writes `out`
-  const cplx<T>* src = in;
-  int64_t Ns = 1;
+  if (np >= 3 && !buf2) return NUFFT_EINVAL;
   int b = fft_lo_bits(N);
+  const int tf64 = sizeof(T) == 8;
+  const void* src = in;
+  int src_f64 = in_f64;
+  int64_t Ns = 1;
   for (int i = 0; i < np; ++i) {
-    cplx<T>* dst = ((np - 1 - i) % 2 == 0) ? out : buf;
+    bool last = (i == np - 1);
+    void* dst = last ? out : (void*)((i & 1) ? buf2 : buf);
+    int dst_f64 = last ? out_f64 : tf64;
     int R = 1 << logR[i];
     int J = kFftSmemElems / R;
     if (J > (int)(N >> logR[i])) J = (int)(N >> logR[i]);
     if (J < 1) J = 1;
     size_t smem = (size_t)(R * J + R / 2) * sizeof(cplx<T>);
     unsigned grid = (unsigned)((N >> logR[i]) / J);
-    k_fft_pass<T><<<grid, 256, smem, st>>>(src, dst, N, logR[i], Ns, J, sign, tw, b);
+    k_fft_pass<T><<<grid, 256, smem, st>>>(src, src_f64, dst, dst_f64, N, logR[i], Ns, J, sign,
+                                           tw, b);
     src = dst;
+    src_f64 = dst_f64;
     Ns <<= logR[i];
   }
   return cudaGetLastError() == cudaSuccess ? NUFFT_OK : NUFFT_ECUDA;
@@ -175,7 +207,7 @@ int fft_configure() {
   return NUFFT_OK;
 }
 
-template int fft_run<double>(const double2*, double2*, double2*, int64_t, int, const double2*,
-                             cudaStream_t);
-template int fft_run<float>(const float2*, float2*, float2*, int64_t, int, const double2*,
-                            cudaStream_t);
+template int fft_run<double>(const void*, int, void*, int, double2*, double2*, int64_t, int,
+                             const double2*, cudaStream_t);
+template int fft_run<float>(const void*, int, void*, int, float2*, float2*, int64_t, int,
+                            const float2*, cudaStream_t);

@@ -26,35 +26,32 @@ namespace nufft {
 // Uniform sources (the grid): every leaf holds s points at the same relative
 // positions, so the leaf moments are a product with the table rho_o^m.
 template <class T>
-__global__ void k_p2m_uniform(TreeDims d, const double2* __restrict__ q,
+__global__ void k_p2m_uniform(TreeDims d, const cplx<T>* __restrict__ q,
                               const T* __restrict__ rp, cplx<T>* __restrict__ mleaf) {
   int64_t B = int64_t(1) << d.L;
   int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (tid >= B * d.pm) return;
   int64_t b = tid / d.pm;
   int m = (int)(tid - b * d.pm);
-  const double2* qb = q + b * d.s;
+  const cplx<T>* qb = q + b * d.s;
   T ar = 0, ai = 0;
   for (int o = 0; o < d.s; ++o) {
-    double2 v = qb[o];
+    cplx<T> v = qb[o];
     T w = rp[o * d.pm + m];
-    ar += (T)v.x * w;
-    ai += (T)v.y * w;
+    ar = fma(v.x, w, ar);
+    ai = fma(v.y, w, ai);
   }
   mleaf[b * d.pm + m] = mk<T>(ar, ai);
 }
 
-// Leaf-relative data of a sorted non-uniform point.
-__device__ inline void point_local(int32_t k0, double delta, int64_t N, int s, int64_t* leaf,
-                                   int64_t* o) {
-  int64_t fl = (delta < 0.0) ? (int64_t)k0 - 1 : (int64_t)k0;
-  fl = (fl + N) % N;
-  int64_t b = fl / s;
-  int64_t off = (int64_t)k0 - b * s;  // in [0, s] up to a period
-  if (off < -(N >> 1)) off += N;
-  if (off > (N >> 1)) off -= N;
+// Leaf index and offset of a point from its grid coordinates (int32: N <= 2^26):
+// leaf = floor((k0 + delta)/s) mod 2^L, o = k0 - leaf s in [0, s].
+__device__ inline void point_local(int k0, double delta, int N, int s, int* leaf, int* o) {
+  int fl = (delta < 0.0) ? k0 - 1 : k0;
+  fl &= (N - 1);
+  int b = fl / s;
   *leaf = b;
-  *o = off;
+  *o = (k0 - b * s) & (N - 1);
 }
 
 // Non-uniform sources: one warp per leaf; a chunk of 32 sources writes
@@ -75,6 +72,7 @@ __global__ void __launch_bounds__(128) k_p2m_nonuniform(TreeDims d,
   int64_t b = blockIdx.x * WPB + warp;
   if (b >= B) return;
   int32_t a = start[b], e = start[b + 1];
+  const int N = (int)d.N;
   for (int mc = 0; mc < d.pm; mc += 32) {
     T accr = 0, acci = 0;
     for (int c0 = a; c0 < e; c0 += 32) {
@@ -82,8 +80,8 @@ __global__ void __launch_bounds__(128) k_p2m_nonuniform(TreeDims d,
       cplx<T> q = mk<T>(0, 0);
       T rho = 0;
       if (i < e) {
-        int64_t lb, o;
-        point_local(k0[i], delta[i], d.N, d.s, &lb, &o);
+        int lb, o;
+        point_local(k0[i], delta[i], N, d.s, &lb, &o);
         rho = (T)(((double)o + delta[i]) / (double)d.s - 0.5);
         q = charge[i];
       }
@@ -115,92 +113,220 @@ __global__ void k_leaf_shift(int64_t B, int pm, const double* __restrict__ shift
   mleaf[tid].x -= (T)shift[m];
 }
 
-// ---------------------------------------------------------------- M2M
+// ---------------------------------------------------------------- upward pass (M2M)
 
-// level lc (children) -> lc - 1.  op: [2][pm][pm], op[sg][k][m] (transposed).
+// M2M of one parent box: M'_m = sum_{k<=m} A_-[m][k] M(left)_k + A_+[m][k] M(right)_k,
+// A in shared memory as [sigma][k][m].
 template <class T>
-__global__ void k_m2m(TreeDims d, int lc, const T* __restrict__ op, cplx<T>* __restrict__ mexp) {
-  extern __shared__ unsigned char smraw[];
-  T* A = reinterpret_cast<T*>(smraw);
-  int pm = d.pm;
-  for (int i = threadIdx.x; i < 2 * pm * pm; i += blockDim.x) A[i] = op[i];
-  __syncthreads();
-  int64_t np = int64_t(1) << (lc - 1);
-  int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (tid >= np * pm) return;
-  int64_t ip = tid / pm;
-  int m = (int)(tid - ip * pm);
-  const cplx<T>* c0 = mexp + (level_off(lc) + 2 * ip) * pm;
-  const cplx<T>* c1 = c0 + pm;
+__device__ inline cplx<T> m2m_one(const T* __restrict__ A, int pm, int m,
+                                  const cplx<T>* __restrict__ c0, const cplx<T>* __restrict__ c1) {
   T ar = 0, ai = 0;
   for (int k = 0; k <= m; ++k) {
     T w0 = A[k * pm + m], w1 = A[pm * pm + k * pm + m];
     cplx<T> x0 = c0[k], x1 = c1[k];
-    ar += w0 * x0.x + w1 * x1.x;
-    ai += w0 * x0.y + w1 * x1.y;
+    ar = fma(w0, x0.x, fma(w1, x1.x, ar));
+    ai = fma(w0, x0.y, fma(w1, x1.y, ai));
   }
-  mexp[(level_off(lc - 1) + ip) * pm + m] = mk<T>(ar, ai);
+  return mk<T>(ar, ai);
 }
 
-// ---------------------------------------------------------------- M2L + L2L
-
-// Level l (3..L): L[l][i] = L2L(L[l-1][i/2]) + sum_{d in IL(i)} T_d M[l][i+d].
-// Interaction list (children of the parent's neighbours that are not
-// neighbours): even i: d in {-2, +2, +3}; odd i: {-3, -2, +2}; box indices
-// periodic mod 2^l, displacement unwrapped.  op_m2l [4][p][p] = T_d^T for
-// d = -3, -2, +2, +3; op_l2l [2][p][p] transposed.
-// For the log kernel (lw != 0) the constant term also receives
-// M_0 log W_l of each interacting box, W_l the box width in grid units.
+// Subtree upward pass: one CTA per box at level lt; its 2^(lb - lt) descendants
+// at level lb are reduced level by level in shared memory, every level's
+// multipoles written to global memory (M2L needs them all).
 template <class T>
-__global__ void k_m2l_l2l(TreeDims d, int l, const T* __restrict__ op_m2l,
-                          const T* __restrict__ op_l2l, const cplx<T>* __restrict__ mexp,
-                          cplx<T>* __restrict__ lexp, double lw) {
+__global__ void __launch_bounds__(512) k_up_sub(TreeDims d, int lb, int lt, const T* __restrict__ op,
+                                                cplx<T>* __restrict__ mexp) {
   extern __shared__ unsigned char smraw[];
-  T* Tm = reinterpret_cast<T*>(smraw);  // 4 p^2
-  T* Tl = Tm + 4 * d.p * d.p;           // 2 p^2
-  int p = d.p, pm = d.pm;
-  for (int i = threadIdx.x; i < 4 * p * p; i += blockDim.x) Tm[i] = op_m2l[i];
-  if (l > 3)
-    for (int i = threadIdx.x; i < 2 * p * p; i += blockDim.x) Tl[i] = op_l2l[i];
+  const int pm = d.pm;
+  T* A = reinterpret_cast<T*>(smraw);
+  cplx<T>* cur = reinterpret_cast<cplx<T>*>(A + 2 * pm * pm);
+  const int depth = lb - lt;
+  cplx<T>* nxt = cur + (pm << depth);
+  for (int i = threadIdx.x; i < 2 * pm * pm; i += blockDim.x) A[i] = op[i];
+  const int64_t b0 = (int64_t)blockIdx.x << depth;  // first box at level lb
+  const cplx<T>* src = mexp + (level_off(lb) + b0) * pm;
+  for (int i = threadIdx.x; i < (pm << depth); i += blockDim.x) cur[i] = src[i];
   __syncthreads();
-  int64_t nb = int64_t(1) << l;
-  int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (tid >= nb * p) return;
-  int64_t i = tid / p;
-  int n = (int)(tid - i * p);
-  const cplx<T>* ml = mexp + level_off(l) * pm;
+  for (int lev = lb; lev > lt; --lev) {
+    const int np = 1 << (lev - 1 - lt);  // parents in this subtree
+    cplx<T>* dst = mexp + (level_off(lev - 1) + ((int64_t)blockIdx.x << (lev - 1 - lt))) * pm;
+    for (int e = threadIdx.x; e < np * pm; e += blockDim.x) {
+      int ip = e / pm, m = e - ip * pm;
+      cplx<T> v = m2m_one<T>(A, pm, m, cur + 2 * ip * pm, cur + (2 * ip + 1) * pm);
+      nxt[e] = v;
+      dst[e] = v;
+    }
+    __syncthreads();
+    cplx<T>* t = cur; cur = nxt; nxt = t;
+  }
+}
+
+// Top of the upward pass in one CTA: levels lb -> 2 (2^lb <= 32 boxes) in
+// shared memory, every level written to global memory.
+template <class T>
+__global__ void __launch_bounds__(512) k_up_top(TreeDims d, int lb, const T* __restrict__ op,
+                                                cplx<T>* __restrict__ mexp) {
+  extern __shared__ unsigned char smraw[];
+  const int pm = d.pm;
+  T* A = reinterpret_cast<T*>(smraw);
+  cplx<T>* cur = reinterpret_cast<cplx<T>*>(A + 2 * pm * pm);  // [2^lb * pm]
+  cplx<T>* nxt = cur + (pm << lb);                             // [2^(lb-1) * pm]
+  for (int i = threadIdx.x; i < 2 * pm * pm; i += blockDim.x) A[i] = op[i];
+  const cplx<T>* src = mexp + level_off(lb) * pm;
+  for (int i = threadIdx.x; i < (pm << lb); i += blockDim.x) cur[i] = src[i];
+  __syncthreads();
+  for (int lev = lb; lev > 2; --lev) {
+    const int np = 1 << (lev - 1);
+    cplx<T>* par = mexp + level_off(lev - 1) * pm;
+    for (int e = threadIdx.x; e < np * pm; e += blockDim.x) {
+      int ip = e / pm, m = e - ip * pm;
+      cplx<T> v = m2m_one<T>(A, pm, m, cur + 2 * ip * pm, cur + (2 * ip + 1) * pm);
+      nxt[e] = v;
+      par[e] = v;
+    }
+    __syncthreads();
+    cplx<T>* t = cur; cur = nxt; nxt = t;
+  }
+}
+
+// ---------------------------------------------------------------- downward pass (M2L + L2L)
+
+// One output L[l][i][n]: sum over the interaction list (even i: d in
+// {-2, +2, +3}; odd i: {-3, -2, +2}; slots 0:-3 1:-2 2:+2 3:+3) plus the L2L
+// of the parent.  Tm: [4][p][p] as [slot][m][n]; Tl: [2][p][p] as
+// [sigma][n'][n]; msrc(off) returns the multipole vector of box i + off;
+// lw (log kernel only) adds M_0 log W_l per interacting box.
+template <class T, class MSrc>
+__device__ inline cplx<T> m2l_one(const T* __restrict__ Tm, const T* __restrict__ Tl, int p, int n,
+                                  int odd, MSrc msrc, const cplx<T>* __restrict__ lpar, T lw) {
   T ar = 0, ai = 0;
-  int odd = (int)(i & 1);
-  // offsets and operator slots: slot 0:-3, 1:-2, 2:+2, 3:+3
-  int offs[3] = {odd ? -3 : -2, odd ? -2 : 2, odd ? 2 : 3};
-  int slot[3] = {odd ? 0 : 1, odd ? 1 : 2, odd ? 2 : 3};
 #pragma unroll
   for (int t = 0; t < 3; ++t) {
-    int64_t src = (i + offs[t] + nb) & (nb - 1);
-    const cplx<T>* mv = ml + src * pm;
-    const T* Tt = Tm + slot[t] * p * p;
+    const int off = odd ? (t == 0 ? -3 : (t == 1 ? -2 : 2)) : (t == 0 ? -2 : (t == 1 ? 2 : 3));
+    const int slot = odd ? t : t + 1;
+    const cplx<T>* mv = msrc(off);
+    const T* Tt = Tm + slot * p * p + n;
     for (int m = 0; m < p; ++m) {
-      T w = Tt[m * p + n];
+      T w = Tt[m * p];
       cplx<T> x = mv[m];
-      ar += w * x.x;
-      ai += w * x.y;
+      ar = fma(w, x.x, ar);
+      ai = fma(w, x.y, ai);
     }
-    if (lw != 0.0 && n == 0) {
-      ar += (T)lw * mv[0].x;
-      ai += (T)lw * mv[0].y;
+    if (n == 0 && lw != (T)0) {
+      ar = fma(lw, mv[0].x, ar);
+      ai = fma(lw, mv[0].y, ai);
     }
   }
-  if (l > 3) {
-    const cplx<T>* lp = lexp + (level_off(l - 1) - 4 + (i >> 1)) * p;
-    const T* Tt = Tl + odd * p * p;
+  if (lpar) {
+    const T* Tt = Tl + odd * p * p + n;
     for (int k = n; k < p; ++k) {
-      T w = Tt[k * p + n];
-      cplx<T> x = lp[k];
-      ar += w * x.x;
-      ai += w * x.y;
+      T w = Tt[k * p];
+      cplx<T> x = lpar[k];
+      ar = fma(w, x.x, ar);
+      ai = fma(w, x.y, ai);
     }
   }
-  lexp[(level_off(l) - 4 + i) * p + n] = mk<T>(ar, ai);
+  return mk<T>(ar, ai);
+}
+
+// log W_l of the log kernel (0 for the cot kernel's 1/t expansions)
+__device__ inline double level_logw(int log_kernel, int log2N, int l) {
+  return log_kernel ? (double)(log2N - l) * 0.6931471805599453 : 0.0;
+}
+
+// Top of the downward pass in one CTA: levels 3..lt (2^lt <= 32 boxes), each
+// level's multipoles and the locals staged in shared memory.
+template <class T>
+__global__ void __launch_bounds__(512) k_down_top(TreeDims d, int lt, const T* __restrict__ op_m2l,
+                                                  const T* __restrict__ op_l2l,
+                                                  const cplx<T>* __restrict__ mexp,
+                                                  cplx<T>* __restrict__ lexp, int log_kernel,
+                                                  int log2N) {
+  extern __shared__ unsigned char smraw[];
+  const int p = d.p, pm = d.pm;
+  const int nmax = 1 << lt;
+  T* Tm = reinterpret_cast<T*>(smraw);
+  T* Tl = Tm + 4 * p * p;
+  cplx<T>* Ms = reinterpret_cast<cplx<T>*>(Tl + 2 * p * p);  // [nmax * p]
+  cplx<T>* La = Ms + nmax * p;                               // [nmax * p]
+  cplx<T>* Lb = La + nmax * p;                               // [nmax * p]
+  for (int i = threadIdx.x; i < 4 * p * p; i += blockDim.x) Tm[i] = op_m2l[i];
+  for (int i = threadIdx.x; i < 2 * p * p; i += blockDim.x) Tl[i] = op_l2l[i];
+  cplx<T>* par = La;
+  cplx<T>* cur = Lb;
+  for (int l = 3; l <= lt; ++l) {
+    const int nb = 1 << l;
+    const cplx<T>* ml = mexp + level_off(l) * pm;
+    __syncthreads();
+    for (int e = threadIdx.x; e < nb * p; e += blockDim.x) {
+      int i = e / p, m = e - i * p;
+      Ms[e] = ml[(int64_t)i * pm + m];
+    }
+    __syncthreads();
+    const T lw = (T)level_logw(log_kernel, log2N, l);
+    cplx<T>* lout = lexp + (level_off(l) - 4) * p;
+    for (int e = threadIdx.x; e < nb * p; e += blockDim.x) {
+      int i = e / p, n = e - i * p;
+      auto msrc = [&](int off) { return Ms + ((i + off + nb) & (nb - 1)) * p; };
+      cplx<T> v = m2l_one<T>(Tm, Tl, p, n, i & 1, msrc, l > 3 ? par + (i >> 1) * p : nullptr, lw);
+      cur[e] = v;
+      lout[e] = v;
+    }
+    cplx<T>* t = par; par = cur; cur = t;
+  }
+}
+
+// Subtree downward pass: one CTA per box at level lt (whose local expansion
+// is in global memory); levels lt+1..lb of its 2^(lb-lt) descendants are
+// formed in shared memory: the multipoles of the boxes and their +-3
+// neighbours are staged per level, the parents' locals stay on chip.  Only
+// level lb is written back.
+template <class T>
+__global__ void __launch_bounds__(512) k_down_sub(TreeDims d, int lt, int lb,
+                                                  const T* __restrict__ op_m2l,
+                                                  const T* __restrict__ op_l2l,
+                                                  const cplx<T>* __restrict__ mexp,
+                                                  cplx<T>* __restrict__ lexp, int log_kernel,
+                                                  int log2N) {
+  extern __shared__ unsigned char smraw[];
+  const int p = d.p, pm = d.pm;
+  const int depth = lb - lt;
+  T* Tm = reinterpret_cast<T*>(smraw);
+  T* Tl = Tm + 4 * p * p;
+  cplx<T>* Ms = reinterpret_cast<cplx<T>*>(Tl + 2 * p * p);  // [(2^depth + 6) * p]
+  cplx<T>* La = Ms + ((1 << depth) + 6) * p;                 // [2^depth * p]
+  cplx<T>* Lb = La + (p << depth);                           // [2^depth * p]
+  for (int i = threadIdx.x; i < 4 * p * p; i += blockDim.x) Tm[i] = op_m2l[i];
+  for (int i = threadIdx.x; i < 2 * p * p; i += blockDim.x) Tl[i] = op_l2l[i];
+  // root local expansion
+  const cplx<T>* lroot = lexp + (level_off(lt) - 4 + blockIdx.x) * (int64_t)p;
+  for (int i = threadIdx.x; i < p; i += blockDim.x) La[i] = lroot[i];
+  cplx<T>* par = La;
+  cplx<T>* cur = Lb;
+  for (int l = lt + 1; l <= lb; ++l) {
+    const int nbx = 1 << (l - lt);          // boxes of this subtree at level l
+    const int nb = 1 << l;
+    const int c0 = blockIdx.x << (l - lt);  // first box
+    const cplx<T>* ml = mexp + level_off(l) * pm;
+    __syncthreads();  // previous level finished with Ms
+    for (int e = threadIdx.x; e < (nbx + 6) * p; e += blockDim.x) {
+      int bi = e / p, m = e - bi * p;
+      int box = (c0 - 3 + bi + nb) & (nb - 1);
+      Ms[e] = ml[(int64_t)box * pm + m];
+    }
+    __syncthreads();
+    const T lw = (T)level_logw(log_kernel, log2N, l);
+    for (int e = threadIdx.x; e < nbx * p; e += blockDim.x) {
+      int bi = e / p, n = e - bi * p;
+      auto msrc = [&](int off) { return Ms + (bi + 3 + off) * p; };
+      cur[e] = m2l_one<T>(Tm, Tl, p, n, (c0 + bi) & 1, msrc, par + (bi >> 1) * p, lw);
+    }
+    cplx<T>* t = par; par = cur; cur = t;
+  }
+  __syncthreads();
+  // par holds level lb
+  cplx<T>* dst = lexp + (level_off(lb) - 4 + ((int64_t)blockIdx.x << depth)) * p;
+  for (int i = threadIdx.x; i < (p << depth); i += blockDim.x) dst[i] = par[i];
 }
 
 // ---------------------------------------------------------------- level 2
@@ -214,11 +340,12 @@ __global__ void k_m2l_l2l(TreeDims d, int l, const T* __restrict__ op_m2l,
 // the cot kernel W1[l][i] = C(2m-1,l) a_m, W2[l][i] = C(2m-1,l) b_m with
 // i = 2m-1-l, a_m = 2 zeta(2m)/4^m, b_m = (4^m - 1) a_m (and the caller
 // scales by -2/pi); the log kernel uses its own W and the constants.
-// op: [4][nq][nq] = W1, W2, S-, S+.  out: [4][nq] then Q = sum of charges.
-// One CTA.
+// op: [4][nq][nq] = W1, W2, S-, S+.  out: [4][nq] then Q = sum of charges,
+// in FP64 and (outf, optional) rounded to FP32.  One CTA.
 template <class T>
 __global__ void k_level2(TreeDims d, int nq, const double* __restrict__ op, double c1, double c2,
-                         const cplx<T>* __restrict__ mexp, double2* __restrict__ out) {
+                         const cplx<T>* __restrict__ mexp, double2* __restrict__ out,
+                         float2* __restrict__ outf) {
   __shared__ double2 mu[4][66];
   __shared__ double2 A1[4][66];
   const cplx<T>* m2 = mexp;  // level 2 sits at offset 0
@@ -257,11 +384,13 @@ __global__ void k_level2(TreeDims d, int nq, const double* __restrict__ op, doub
       acc = cadd(acc, cscale(mu[n2][0], c2));
     }
     out[n * nq + l] = acc;
+    if (outf) outf[n * nq + l] = make_float2((float)acc.x, (float)acc.y);
   }
   if (threadIdx.x == 0) {
     double2 qs = make_double2(0, 0);
     for (int a = 0; a < 4; ++a) qs = cadd(qs, to_d2(m2[a * d.pm]));
     out[4 * nq] = qs;
+    if (outf) outf[4 * nq] = make_float2((float)qs.x, (float)qs.y);
   }
 }
 
@@ -278,28 +407,42 @@ __device__ inline cplx<T> horner(const cplx<T>* __restrict__ c, int n, T u) {
   return acc;
 }
 
-__device__ inline double2 horner_d(const double2* __restrict__ c, int n, double u) {
-  double2 acc = c[n - 1];
-  for (int k = n - 2; k >= 0; --k) {
-    acc.x = fma(acc.x, u, c[k].x);
-    acc.y = fma(acc.y, u, c[k].y);
-  }
-  return acc;
-}
-
 template <class V> __device__ inline void store_out(V* p, double2 v);
 template <> __device__ inline void store_out<double2>(double2* p, double2 v) { *p = v; }
 template <> __device__ inline void store_out<float2>(float2* p, double2 v) {
   *p = make_float2((float)v.x, (float)v.y);
 }
+template <class V> __device__ inline void store_out_f(V* p, float2 v);
+template <> __device__ inline void store_out_f<double2>(double2* p, float2 v) {
+  *p = make_double2(v.x, v.y);
+}
+template <> __device__ inline void store_out_f<float2>(float2* p, float2 v) { *p = v; }
 
-// near-field accumulation: FP64, or FP32 partial sums folded into FP64 every
-// 16 terms so the rounding of a long FP32 sum stays at the 1e-7 level.
+// Exact conversion of a small integer (|D| < 2^22) to T: for FP32 through
+// the bit pattern of 1.5 * 2^23 + D (an integer add and one subtraction,
+// no conversion instruction).
+__device__ inline float int_to_t(int D, float) {
+  return __int_as_float(0x4B400000 + D) - 12582912.0f;
+}
+__device__ inline double int_to_t(int D, double) { return (double)D; }
+
+// 1/t: FP32 reciprocal on the special-function unit (rcp.approx, 1 ulp), or
+// FP64 division.
+__device__ inline float rcp_t(float t) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(t));
+  return r;
+}
+__device__ inline double rcp_t(double t) { return 1.0 / t; }
+
+// Near-field accumulation of q / t.  FP64 path: FP64 throughout.  FP32 path:
+// FP32 partial sums of up to 16 terms folded into a compensated (Kahan) FP32
+// total, so a sum of ~100 terms stays at the 1e-7 level without FP64
+// instructions.  Callers add terms in chunks and call fold() between them.
 template <class T> struct NearAcc;
 template <> struct NearAcc<double> {
   double2 s = make_double2(0, 0);
-  __device__ inline void add(double2 q, double t) {
-    double r = 1.0 / t;
+  __device__ inline void add_r(double2 q, double r) {
     s.x = fma(q.x, r, s.x);
     s.y = fma(q.y, r, s.y);
   }
@@ -307,21 +450,23 @@ template <> struct NearAcc<double> {
   __device__ inline double2 get() const { return s; }
 };
 template <> struct NearAcc<float> {
-  double2 s = make_double2(0, 0);
-  float2 f = make_float2(0, 0);
-  int cnt = 0;
-  __device__ inline void add(double2 q, double t) {
-    float r = __fdividef(1.0f, (float)t);
-    f.x = fmaf((float)q.x, r, f.x);
-    f.y = fmaf((float)q.y, r, f.y);
-    if (++cnt == 16) fold();
+  float2 f = make_float2(0, 0), s = make_float2(0, 0), c = make_float2(0, 0);
+  __device__ inline static void kahan(float& sum, float& comp, float v) {
+    float y = v - comp;
+    float t = sum + y;
+    comp = (t - sum) - y;
+    sum = t;
+  }
+  __device__ inline void add_r(float2 q, float r) {
+    f.x = fmaf(q.x, r, f.x);
+    f.y = fmaf(q.y, r, f.y);
   }
   __device__ inline void fold() {
-    s.x += f.x; s.y += f.y;
+    kahan(s.x, c.x, f.x);
+    kahan(s.y, c.y, f.y);
     f = make_float2(0, 0);
-    cnt = 0;
   }
-  __device__ inline double2 get() { fold(); return s; }
+  __device__ inline float2 get() { fold(); return s; }
 };
 
 // ---------------------------------------------------------------- forward targets
@@ -332,50 +477,63 @@ template <> struct NearAcc<float> {
 //          - (2/pi) sum_l D^(arc)_l uhat^l
 // where the pair (y_j, x_k0) enters through E_j (its singular 2/t part in
 // closed form) and through Q and the regular polynomial like every source.
+// All arithmetic in T (F_j, E_j were formed in FP64 at plan time).
 template <class T, class VO>
 __global__ void __launch_bounds__(256) k_targets_fwd(
-    TreeDims d, int64_t M, const int32_t* __restrict__ k0s, const double* __restrict__ dels,
-    const int32_t* __restrict__ perm, const double2* __restrict__ F,
-    const double2* __restrict__ E, const double2* __restrict__ fgrid,
-    const cplx<T>* __restrict__ lexp, const double2* __restrict__ lvl2, VO* __restrict__ g) {
-  int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    TreeDims d, int M, const int32_t* __restrict__ k0s, const double* __restrict__ dels,
+    const int32_t* __restrict__ perm, const cplx<T>* __restrict__ F,
+    const cplx<T>* __restrict__ E, const cplx<T>* __restrict__ fgrid,
+    const cplx<T>* __restrict__ lexp, const cplx<T>* __restrict__ lvl2, VO* __restrict__ g) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= M) return;
-  const int64_t N = d.N;
+  const int N = (int)d.N;
   const int s = d.s;
-  int32_t k0 = k0s[j];
+  int k0 = k0s[j];
   double dl = dels[j];
-  int64_t b, o;
+  int b, o;
   point_local(k0, dl, N, s, &b, &o);
+  const T dt = (T)dl;
   // far field (local expansion of the leaf)
-  T u = (T)(((double)o + dl) / (double)s - 0.5);
-  const cplx<T>* Lb = lexp + (level_off(d.L) - 4 + b) * d.p;
-  double2 far = (d.L >= 3) ? to_d2(horner<T>(Lb, d.p, u)) : make_double2(0, 0);
-  // near field: leaves b-1, b, b+1 (periodic, unwrapped displacement)
-  NearAcc<T> acc;
-  int64_t base = b * s - s;
-  for (int64_t r = -s; r < 2 * s; ++r) {
-    if (r == o) continue;
-    int64_t k = (base + (r + s) + N) & (N - 1);
-    double t = (double)(o - r) + dl;
-    acc.add(fgrid[k], t);
+  cplx<T> far = mk<T>(0, 0);
+  if (d.L >= 3) {
+    T u = ((T)o + dt) * (T)(1.0 / s) - (T)0.5;
+    far = horner<T>(lexp + ((int64_t)(level_off(d.L) - 4) + b) * d.p, d.p, u);
   }
-  double2 nr = acc.get();
+  // near field: leaves b-1, b, b+1 (periodic, unwrapped displacement); the
+  // pair with the nearest grid point (D = 0) is masked, E_j carries it
+  NearAcc<T> acc;
+  const int B = 1 << d.L;
+  for (int nb = -1; nb <= 1; ++nb) {
+    const cplx<T>* q = fgrid + (int64_t)((b + nb + B) & (B - 1)) * s;
+    const int D0 = o - nb * s;  // D = D0 - o' for the o'-th point of the leaf
+    for (int c0 = 0; c0 < s; c0 += 16) {
+      const int cn = s - c0 < 16 ? s - c0 : 16;
+#pragma unroll 16
+      for (int u = 0; u < cn; ++u) {
+        const int D = D0 - c0 - u;
+        T r = rcp_t(int_to_t(D, T()) + dt);
+        acc.add_r(q[c0 + u], D == 0 ? (T)0 : r);
+      }
+      acc.fold();
+    }
+  }
+  cplx<T> nr = acc.get();
+  const int base = b * s;
   // regular part, arc n = b >> (L-2), uhat = (y - x_c)/pi
-  int Q2 = 2 * d.q;  // cot kernel: degree 2q-1
-  int64_t arc = b >> (d.L - 2);
-  int64_t I = b * s + o - arc * (N >> 2) - (N >> 3);
-  double uh = ((double)I + dl) * (2.0 / (double)N);
-  double2 reg = horner_d(lvl2 + arc * Q2, Q2, uh);
-  double2 Qs = lvl2[4 * Q2];
-  double cN = (double)N * kInvPi;
-  double hr = cN * (far.x / (double)s + nr.x) - 2.0 * kInvPi * reg.x;
-  double hi = cN * (far.y / (double)s + nr.y) - 2.0 * kInvPi * reg.y;
-  // Q + i h'
-  double2 w = make_double2(Qs.x - hi, Qs.y + hr);
-  double2 Fj = F[j];
-  double2 res = cscale(cmul(Fj, w), -0.5);
+  const int Q2 = 2 * d.q;  // cot kernel: degree 2q-1
+  int arc = b >> (d.L - 2);
+  int I = base + o - arc * (N >> 2) - (N >> 3);
+  T uh = ((T)I + dt) * (T)(2.0 / (double)N);
+  cplx<T> reg = horner<T>(lvl2 + arc * Q2, Q2, uh);
+  cplx<T> Qs = lvl2[4 * Q2];
+  const T cN = (T)((double)N * kInvPi), ts = (T)(1.0 / s), c2 = (T)(2.0 * kInvPi);
+  T hr = cN * fma(far.x, ts, nr.x) - c2 * reg.x;
+  T hi = cN * fma(far.y, ts, nr.y) - c2 * reg.y;
+  // g = E f_k0 - (F/2)(Q + i h')
+  cplx<T> w = mk<T>(Qs.x - hi, Qs.y + hr);
+  cplx<T> res = cscale(cmul(F[j], w), (T)-0.5);
   res = cadd(res, cmul(E[j], fgrid[k0]));
-  store_out<VO>(g + perm[j], res);
+  store_out<VO>(g + perm[j], to_d2(res));
 }
 
 // ---------------------------------------------------------------- adjoint / inverse targets
@@ -394,74 +552,144 @@ __global__ void k_charges(int64_t M, const int32_t* __restrict__ perm,
   charge[i] = from_d2<T>(cmul(c, gv));
 }
 
+// The pair (y_j, x_k0) of each source j with its nearest grid point, one
+// thread per sorted source (uniform work, so the FP64 arithmetic of the
+// inverse does not diverge inside a warp):
+//   adjoint: conj(E_j) g_j, the closed form of the pair's 2/t part (and
+//            conj(F_j) G(x_k0 - y_j) -> 1 at an exact hit);
+//   inverse: the pair's 2/t part times the target factor,
+//            Ct_k0 (i/2) (N/pi) q_j / delta_j, formed in FP64 (finite, as Ct_k0
+//            carries sin((x_k0 - y_j)/2)); g_j / N at an exact hit, where
+//            Ct_k0 = 0 removes every other term.
+template <class T, class VI>
+__global__ void k_self_terms(int M, int inverse, int N, const int32_t* __restrict__ k0s,
+                             const double* __restrict__ dels, const int32_t* __restrict__ perm,
+                             const cplx<T>* __restrict__ E, const cplx<T>* __restrict__ charge,
+                             const VI* __restrict__ gin, const double* __restrict__ Ct,
+                             cplx<T>* __restrict__ st) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= M) return;
+  if (!inverse) {
+    st[i] = cmul(cconj(E[i]), from_d2<T>(to_d2(gin[perm[i]])));
+    return;
+  }
+  double d = dels[i];
+  double2 v;
+  if (d == 0.0) {
+    v = cscale(to_d2(gin[perm[i]]), 1.0 / (double)N);
+  } else {
+    double2 q = to_d2(charge[i]);
+    double w = Ct[k0s[i]] * (0.5 * (double)N * kInvPi) / d;
+    v = make_double2(-q.y * w, q.x * w);
+  }
+  st[i] = from_d2<T>(v);
+}
+
 // One thread per grid point k (Eq. p4 transposed, Eq. p6):
 //   h_k = sum_j q_j cot((x_k - y_j)/2)   by the same FMM, then
-//   adjoint: u_k = sum_{j: k0_j = k} conj(E_j) g_j - (Q + i h'_k)/2  (h' without
-//            those pairs' 2/t part)
-//   inverse: f_k/N = Ct_k (-(Q + i h_k)/2), or g_j/N when y_j = x_k exactly
-//            (Ct_k = C_k e^Lambda / N carries the 1/N of Eq. p1).
-template <class T, class VI>
+//   adjoint: u_k   = -(Q + i h'_k)/2 + sum_{j: k0_j = k} st_j
+//   inverse: f_k/N = Ct_k (-(Q + i h'_k)/2) + sum_{j: k0_j = k} st_j
+// where h' leaves out the 2/t part of the pairs with k0_j = k (their st_j
+// terms above); Ct_k = C_k e^Lambda / N carries the 1/N of Eq. p1.  All
+// arithmetic in T (Ct in FP32 for the mixed path).  dl_t: delta in T.
+// Packed source record for the adjoint / inverse near field: grid index k0,
+// offset delta and charge q in one 16-byte (FP32) or 32-byte (FP64) load.
+template <class T> struct SrcRec;
+template <> struct SrcRec<float> { float4 v; };
+template <> struct SrcRec<double> { double4_32a v; };
+
+template <class T>
+__device__ inline void rec_unpack(const SrcRec<T>& r, int* k0, T* dl, cplx<T>* q);
+template <>
+__device__ inline void rec_unpack<float>(const SrcRec<float>& r, int* k0, float* dl, float2* q) {
+  *k0 = __float_as_int(r.v.x);
+  *dl = r.v.y;
+  *q = make_float2(r.v.z, r.v.w);
+}
+template <>
+__device__ inline void rec_unpack<double>(const SrcRec<double>& r, int* k0, double* dl,
+                                          double2* q) {
+  *k0 = (int)__double_as_longlong(r.v.x);
+  *dl = r.v.y;
+  *q = make_double2(r.v.z, r.v.w);
+}
+
+template <class T>
+__global__ void k_pack_sources(int M, const int32_t* __restrict__ k0s, const double* __restrict__ dels,
+                               const cplx<T>* __restrict__ charge, SrcRec<T>* __restrict__ rec) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= M) return;
+  cplx<T> q = charge[i];
+  SrcRec<T> r;
+  if constexpr (sizeof(T) == 4)
+    r.v = make_float4(__int_as_float(k0s[i]), (float)dels[i], q.x, q.y);
+  else
+    r.v = make_double4_32a(__longlong_as_double((long long)k0s[i]), dels[i], q.x, q.y);
+  rec[i] = r;
+}
+
+// One thread per grid point k (Eq. p4 transposed, Eq. p6):
+//   h_k = sum_j q_j cot((x_k - y_j)/2)   by the same FMM, then
+//   adjoint: u_k   = -(Q + i h'_k)/2 + sum_{j: k0_j = k} st_j
+//   inverse: f_k/N = Ct_k (-(Q + i h'_k)/2) + sum_{j: k0_j = k} st_j
+// where h' leaves out the 2/t part of the pairs with k0_j = k (their st_j
+// terms above); Ct_k = C_k e^Lambda / N carries the 1/N of Eq. p1.  All
+// arithmetic in T (Ct in FP32 for the mixed path).
+template <class T>
 __global__ void __launch_bounds__(256) k_targets_grid(
     TreeDims d, int inverse, const int32_t* __restrict__ start,
-    const int32_t* __restrict__ k0s, const double* __restrict__ dels,
-    const int32_t* __restrict__ perm, const double2* __restrict__ E,
-    const cplx<T>* __restrict__ charge, const VI* __restrict__ gin,
-    const cplx<T>* __restrict__ lexp, const double2* __restrict__ lvl2,
-    const double* __restrict__ Ct, double2* __restrict__ out) {
-  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t N = d.N;
+    const SrcRec<T>* __restrict__ rec, const cplx<T>* __restrict__ st,
+    const cplx<T>* __restrict__ lexp, const cplx<T>* __restrict__ lvl2,
+    const T* __restrict__ Ct, cplx<T>* __restrict__ out) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int N = (int)d.N;
   if (k >= N) return;
   const int s = d.s;
-  const int64_t B = int64_t(1) << d.L;
-  int64_t b = k / s, o = k - b * s;
-  T u = (T)((double)o / (double)s - 0.5);
-  const cplx<T>* Lb = lexp + (level_off(d.L) - 4 + b) * d.p;
-  double2 far = (d.L >= 3) ? to_d2(horner<T>(Lb, d.p, u)) : make_double2(0, 0);
+  const int B = 1 << d.L;
+  int b = k / s, o = k - b * s;
+  cplx<T> far = mk<T>(0, 0);
+  if (d.L >= 3) {
+    T u = (T)o * (T)(1.0 / s) - (T)0.5;
+    far = horner<T>(lexp + ((int64_t)(level_off(d.L) - 4) + b) * d.p, d.p, u);
+  }
   NearAcc<T> acc;
-  double2 self = make_double2(0, 0);
-  int hit = -1;
-  NearAcc<double> accd;  // inverse: pairs with k0_j = k in FP64
+  cplx<T> self = mk<T>(0, 0);
   for (int nb = -1; nb <= 1; ++nb) {
-    int64_t bb = (b + nb + B) & (B - 1);
-    int32_t a = start[bb], e = start[bb + 1];
-    for (int32_t i = a; i < e; ++i) {
-      // k0_i relative to leaf b's origin, unwrapped through the known leaf
-      // offset nb (k0_i lies in [bb s, bb s + s] modulo N)
-      int64_t rel = (int64_t)nb * s + (((int64_t)k0s[i] - bb * s + N) & (N - 1));
-      int64_t D = o - rel;
-      double di = dels[i];
+    int bb = (b + nb + B) & (B - 1);
+    int a = start[bb], e = start[bb + 1];
+    // D = o - (nb s + ((k0_i - bb s) mod N)): k0_i relative to leaf b's
+    // origin, unwrapped through the known leaf offset nb
+    const int D0 = o - nb * s, sub = bb * s;
+    int cnt = 0;
+    for (int i = a; i < e; ++i) {
+      int k0;
+      T dl;
+      cplx<T> q;
+      rec_unpack<T>(rec[i], &k0, &dl, &q);
+      int D = D0 - ((k0 - sub) & (N - 1));
+      T r = rcp_t(int_to_t(D, T()) - dl);
       if (D == 0) {
-        if (inverse) {
-          if (di == 0.0) hit = i;
-          else accd.add(to_d2(charge[i]), -di);
-        } else {
-          self = cadd(self, cmul(cconj(E[i]), to_d2(gin[perm[i]])));
-        }
-        continue;
+        self = cadd(self, st[i]);
+        r = (T)0;
       }
-      acc.add(to_d2(charge[i]), (double)D - di);
+      acc.add_r(q, r);
+      if (++cnt == 16) { acc.fold(); cnt = 0; }
     }
+    acc.fold();
   }
-  double2 nr = acc.get();
-  if (inverse) nr = cadd(nr, accd.get());
-  int Q2 = 2 * d.q;
-  int64_t arc = b >> (d.L - 2);
-  int64_t I = k - arc * (N >> 2) - (N >> 3);
-  double uh = (double)I * (2.0 / (double)N);
-  double2 reg = horner_d(lvl2 + arc * Q2, Q2, uh);
-  double2 Qs = lvl2[4 * Q2];
-  double cN = (double)N * kInvPi;
-  double hr = cN * (far.x / (double)s + nr.x) - 2.0 * kInvPi * reg.x;
-  double hi = cN * (far.y / (double)s + nr.y) - 2.0 * kInvPi * reg.y;
-  double2 res = make_double2(-0.5 * (Qs.x - hi), -0.5 * (Qs.y + hr));
-  if (inverse) {
-    res = cscale(res, Ct[k]);
-    // exact hit: f_k = g_j; Ct carries the 1/N of the final DFT, so apply it here too
-    if (hit >= 0) res = cscale(to_d2(gin[perm[hit]]), 1.0 / (double)N);
-  } else {
-    res = cadd(res, self);
-  }
-  out[k] = res;
+  cplx<T> nr = acc.get();
+  const int Q2 = 2 * d.q;
+  int arc = b >> (d.L - 2);
+  int I = k - arc * (N >> 2) - (N >> 3);
+  T uh = (T)I * (T)(2.0 / (double)N);
+  cplx<T> reg = horner<T>(lvl2 + arc * Q2, Q2, uh);
+  cplx<T> Qs = lvl2[4 * Q2];
+  const T cN = (T)((double)N * kInvPi), ts = (T)(1.0 / s), c2 = (T)(2.0 * kInvPi);
+  T hr = cN * fma(far.x, ts, nr.x) - c2 * reg.x;
+  T hi = cN * fma(far.y, ts, nr.y) - c2 * reg.y;
+  cplx<T> res = mk<T>((T)-0.5 * (Qs.x - hi), (T)-0.5 * (Qs.y + hr));
+  if (inverse) res = cscale(res, Ct[k]);
+  out[k] = cadd(res, self);
 }
 
 }  // namespace nufft
@@ -472,23 +700,43 @@ using namespace nufft;
 
 static inline unsigned nblk(int64_t n, int th) { return (unsigned)((n + th - 1) / th); }
 
+// persistent grids: at most kPersistCtas CTAs, each looping over its share
+// tree passes: levels <= kTopLevel (at most 32 boxes) run in one CTA, finer
+// levels in subtrees of at most kSubDepth levels (64 boxes) per CTA
+static constexpr int kTopLevel = 5;
+static constexpr int kSubDepth = 6;
+static constexpr size_t kSmemBudget = 220 * 1024;
+
+template <class T>
+static size_t up_sub_smem(int pm, int depth) {
+  return (size_t)2 * pm * pm * sizeof(T) + (size_t)3 * ((size_t)pm << depth) / 2 * sizeof(cplx<T>);
+}
+template <class T>
+static size_t down_sub_smem(int p, int depth) {
+  size_t nbx = (size_t)1 << depth;
+  return (size_t)6 * p * p * sizeof(T) + (nbx + 6 + 2 * nbx) * p * sizeof(cplx<T>);
+}
+
 template <class T>
 int fmm_configure() {
-  int big = 200 * 1024;
-  if (cudaFuncSetAttribute(k_m2l_l2l<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big) !=
-      cudaSuccess)
-    return NUFFT_ECUDA;
-  if (cudaFuncSetAttribute(k_m2m<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big) !=
-      cudaSuccess)
+  int big = 220 * 1024;
+  if (cudaFuncSetAttribute(k_up_sub<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(k_up_top<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(k_down_top<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(k_down_sub<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big) !=
+          cudaSuccess)
     return NUFFT_ECUDA;
   return NUFFT_OK;
 }
 
 // Upward pass + far field + level-2 coefficients for charges already laid out
-// (uniform: on the grid in `grid`; non-uniform: sorted in plan->charge).
+// (uniform: on the grid, `charge` = the grid samples; non-uniform: sorted).
 template <class T>
 int fmm_upward_downward(nufft_plan_s* pl, const FmmOps& ops, bool uniform_sources,
-                        const cplx<T>* charge, double2* lvl2) {
+                        const cplx<T>* charge, double2* lvl2, float2* lvl2f) {
   cudaStream_t st = pl->stream;
   TreeDims d{pl->N, pl->L, pl->s, pl->p, pl->q, pl->pm};
   int64_t B = pl->B;
@@ -497,7 +745,7 @@ int fmm_upward_downward(nufft_plan_s* pl, const FmmOps& ops, bool uniform_source
   cplx<T>* mleaf = mexp + level_off(pl->L) * pl->pm;
   prof_begin(pl, NUFFT_STAGE_P2M);
   if (uniform_sources) {
-    k_p2m_uniform<T><<<nblk(B * pl->pm, 256), 256, 0, st>>>(d, pl->grid, (const T*)pl->op_p2m,
+    k_p2m_uniform<T><<<nblk(B * pl->pm, 256), 256, 0, st>>>(d, charge, (const T*)pl->op_p2m,
                                                            mleaf);
   } else {
     constexpr int WPB = P2mWarps<T>::value;
@@ -507,25 +755,59 @@ int fmm_upward_downward(nufft_plan_s* pl, const FmmOps& ops, bool uniform_source
   if (ops.leaf_shift)
     k_leaf_shift<T><<<nblk(B * pl->pm, 256), 256, 0, st>>>(B, pl->pm, ops.leaf_shift, mleaf);
   prof_end(pl, ops.leaf_shift ? 2 : 1);
+  // upward: subtrees of up to kSubDepth levels down to level kTopLevel, then one CTA
   prof_begin(pl, NUFFT_STAGE_M2M);
-  size_t sm_m2m = (size_t)2 * pl->pm * pl->pm * sizeof(T);
-  for (int lc = pl->L; lc >= 3; --lc) {
-    int64_t np = int64_t(1) << (lc - 1);
-    k_m2m<T><<<nblk(np * pl->pm, 256), 256, sm_m2m, st>>>(d, lc, (const T*)pl->op_m2m, mexp);
+  const int pm = pl->pm, p = pl->p, L = pl->L;
+  int nl = 0;
+  int lev = L;
+  while (lev > kTopLevel) {
+    int dep = kSubDepth;
+    while (dep > 1 && up_sub_smem<T>(pm, dep) > kSmemBudget) --dep;
+    int lt = lev - dep > kTopLevel ? lev - dep : kTopLevel;
+    k_up_sub<T><<<1u << lt, 512, up_sub_smem<T>(pm, lev - lt), st>>>(d, lev, lt,
+                                                                     (const T*)pl->op_m2m, mexp);
+    ++nl;
+    lev = lt;
   }
-  prof_end(pl, pl->L - 2);
+  if (lev > 2) {
+    size_t sm = (size_t)2 * pm * pm * sizeof(T) + (size_t)3 * ((size_t)pm << lev) / 2 * sizeof(cplx<T>);
+    k_up_top<T><<<1, 512, sm, st>>>(d, lev, (const T*)pl->op_m2m, mexp);
+    ++nl;
+  }
+  prof_end(pl, nl);
   prof_begin(pl, NUFFT_STAGE_LEVEL2);
-  k_level2<T><<<1, 256, 0, st>>>(d, ops.nq, ops.reg, ops.c1, ops.c2, mexp, lvl2);
+  k_level2<T><<<1, 256, 0, st>>>(d, ops.nq, ops.reg, ops.c1, ops.c2, mexp, lvl2, lvl2f);
   prof_end(pl, 1);
+  // downward: levels 3..kTopLevel in one CTA, then subtrees; the chunks are
+  // cut from the finest level up so the costly fine levels get the most CTAs
   prof_begin(pl, NUFFT_STAGE_M2L);
-  size_t sm_m2l = (size_t)6 * pl->p * pl->p * sizeof(T);
-  for (int l = 3; l <= pl->L; ++l) {
-    int64_t nb = int64_t(1) << l;
-    double lw = ops.log_kernel ? std::log((double)(pl->N >> l)) : 0.0;
-    k_m2l_l2l<T><<<nblk(nb * pl->p, 256), 256, sm_m2l, st>>>(d, l, (const T*)ops.m2l,
-                                                            (const T*)ops.l2l, mexp, lexp, lw);
+  nl = 0;
+  int log2N = 0;
+  while ((int64_t(1) << log2N) < pl->N) ++log2N;
+  if (L >= 3) {
+    int top = L < kTopLevel ? L : kTopLevel;
+    auto top_smem = [&](int t) {
+      return (size_t)6 * p * p * sizeof(T) + (size_t)3 * ((size_t)p << t) * sizeof(cplx<T>);
+    };
+    while (top > 3 && top_smem(top) > kSmemBudget) --top;
+    size_t smt = top_smem(top);
+    k_down_top<T><<<1, 512, smt, st>>>(
+        d, top, (const T*)ops.m2l, (const T*)ops.l2l, mexp, lexp, ops.log_kernel, log2N);
+    ++nl;
+    int dep = kSubDepth;
+    while (dep > 1 && down_sub_smem<T>(p, dep) > kSmemBudget) --dep;
+    int cuts[32], nc = 0;
+    for (int lb = L; lb > top; lb -= dep) cuts[nc++] = lb;
+    int lt = top;
+    for (int c = nc - 1; c >= 0; --c) {
+      int lb = cuts[c];
+      k_down_sub<T><<<1u << lt, 512, down_sub_smem<T>(p, lb - lt), st>>>(
+          d, lt, lb, (const T*)ops.m2l, (const T*)ops.l2l, mexp, lexp, ops.log_kernel, log2N);
+      ++nl;
+      lt = lb;
+    }
   }
-  prof_end(pl, pl->L >= 3 ? pl->L - 2 : 0);
+  prof_end(pl, nl);
   return cudaGetLastError() == cudaSuccess ? NUFFT_OK : NUFFT_ECUDA;
 }
 
@@ -538,55 +820,81 @@ static FmmOps cot_ops(nufft_plan_s* pl) {
   return o;
 }
 
-// forward: grid samples f in pl->grid (complex128) -> g (original order)
+// the plan's per-point data in the arithmetic type T
+template <class T> struct PlanT;
+template <> struct PlanT<double> {
+  static const double2* F(nufft_plan_s* pl) { return pl->F; }
+  static const double2* E(nufft_plan_s* pl) { return pl->E; }
+  static const double* dl(nufft_plan_s* pl) { return pl->delta; }
+  static const double2* lvl2(nufft_plan_s* pl) { return pl->lvl2; }
+  static const double* Ct(nufft_plan_s* pl) { return pl->Ct; }
+};
+template <> struct PlanT<float> {
+  static const float2* F(nufft_plan_s* pl) { return pl->Ff; }
+  static const float2* E(nufft_plan_s* pl) { return pl->Ef; }
+  static const float* dl(nufft_plan_s* pl) { return pl->delta_f; }
+  static const float2* lvl2(nufft_plan_s* pl) { return pl->lvl2f; }
+  static const float* Ct(nufft_plan_s* pl) { return pl->Ctf; }
+};
+
+// forward: grid samples f (cplx<T>, in pl->grid) -> g (original order)
 template <class T>
 int fmm_forward(nufft_plan_s* pl, void* g) {
-  int rc = fmm_upward_downward<T>(pl, cot_ops(pl), true, nullptr, pl->lvl2);
+  const cplx<T>* f = (const cplx<T>*)pl->grid;
+  int rc = fmm_upward_downward<T>(pl, cot_ops(pl), true, f, pl->lvl2,
+                                  sizeof(T) == 4 ? pl->lvl2f : nullptr);
   if (rc) return rc;
   TreeDims d{pl->N, pl->L, pl->s, pl->p, pl->q, pl->pm};
-  cplx<T>* lexp = (cplx<T>*)pl->lexp;
+  const cplx<T>* lexp = (const cplx<T>*)pl->lexp;
   prof_begin(pl, NUFFT_STAGE_TARGETS);
   if (pl->flags & NUFFT_IO_C64)
     k_targets_fwd<T, float2><<<nblk(pl->M, 256), 256, 0, pl->stream>>>(
-        d, pl->M, pl->k0, pl->delta, pl->perm, pl->F, pl->E, pl->grid, lexp, pl->lvl2,
-        (float2*)g);
+        d, (int)pl->M, pl->k0, pl->delta, pl->perm, PlanT<T>::F(pl), PlanT<T>::E(pl), f, lexp,
+        PlanT<T>::lvl2(pl), (float2*)g);
   else
     k_targets_fwd<T, double2><<<nblk(pl->M, 256), 256, 0, pl->stream>>>(
-        d, pl->M, pl->k0, pl->delta, pl->perm, pl->F, pl->E, pl->grid, lexp, pl->lvl2,
-        (double2*)g);
+        d, (int)pl->M, pl->k0, pl->delta, pl->perm, PlanT<T>::F(pl), PlanT<T>::E(pl), f, lexp,
+        PlanT<T>::lvl2(pl), (double2*)g);
   prof_end(pl, 1);
   return cudaGetLastError() == cudaSuccess ? NUFFT_OK : NUFFT_ECUDA;
 }
 
-// adjoint / inverse: samples g (original order) -> values on the grid in pl->grid
+// adjoint / inverse: samples g (original order) -> values on the grid
+// (cplx<T>, in pl->grid)
 template <class T>
 int fmm_to_grid(nufft_plan_s* pl, const void* g, int inverse) {
   cudaStream_t st = pl->stream;
   bool c64 = (pl->flags & NUFFT_IO_C64) != 0;
   const double2* coef = inverse ? pl->Dt : pl->F;
+  cplx<T>* charge = (cplx<T>*)pl->charge;
   prof_begin(pl, NUFFT_STAGE_P2M);
   if (c64)
     k_charges<T, float2><<<nblk(pl->M, 256), 256, 0, st>>>(pl->M, pl->perm, coef, !inverse,
-                                                          (const float2*)g, (cplx<T>*)pl->charge);
+                                                          (const float2*)g, charge);
   else
     k_charges<T, double2><<<nblk(pl->M, 256), 256, 0, st>>>(pl->M, pl->perm, coef, !inverse,
-                                                           (const double2*)g, (cplx<T>*)pl->charge);
+                                                           (const double2*)g, charge);
   prof_end(pl, 1);
-  int rc = fmm_upward_downward<T>(pl, cot_ops(pl), false, (const cplx<T>*)pl->charge, pl->lvl2);
+  int rc = fmm_upward_downward<T>(pl, cot_ops(pl), false, charge, pl->lvl2,
+                                  sizeof(T) == 4 ? pl->lvl2f : nullptr);
   if (rc) return rc;
   TreeDims d{pl->N, pl->L, pl->s, pl->p, pl->q, pl->pm};
+  cplx<T>* st_ = (cplx<T>*)pl->selft;
   prof_begin(pl, NUFFT_STAGE_TARGETS);
   if (c64)
-    k_targets_grid<T, float2><<<nblk(pl->N, 256), 256, 0, st>>>(
-        d, inverse, pl->leaf_start, pl->k0, pl->delta, pl->perm, pl->E,
-        (const cplx<T>*)pl->charge, (const float2*)g, (const cplx<T>*)pl->lexp, pl->lvl2, pl->Ct,
-        pl->grid);
+    k_self_terms<T, float2><<<nblk(pl->M, 256), 256, 0, st>>>(
+        (int)pl->M, inverse, (int)pl->N, pl->k0, pl->delta, pl->perm, PlanT<T>::E(pl), charge,
+        (const float2*)g, pl->Ct, st_);
   else
-    k_targets_grid<T, double2><<<nblk(pl->N, 256), 256, 0, st>>>(
-        d, inverse, pl->leaf_start, pl->k0, pl->delta, pl->perm, pl->E,
-        (const cplx<T>*)pl->charge, (const double2*)g, (const cplx<T>*)pl->lexp, pl->lvl2,
-        pl->Ct, pl->grid);
-  prof_end(pl, 1);
+    k_self_terms<T, double2><<<nblk(pl->M, 256), 256, 0, st>>>(
+        (int)pl->M, inverse, (int)pl->N, pl->k0, pl->delta, pl->perm, PlanT<T>::E(pl), charge,
+        (const double2*)g, pl->Ct, st_);
+  SrcRec<T>* rec = (SrcRec<T>*)pl->srcrec;
+  k_pack_sources<T><<<nblk(pl->M, 256), 256, 0, st>>>((int)pl->M, pl->k0, pl->delta, charge, rec);
+  k_targets_grid<T><<<nblk(pl->N, 256), 256, 0, st>>>(
+      d, inverse, pl->leaf_start, rec, st_, (const cplx<T>*)pl->lexp, PlanT<T>::lvl2(pl),
+      PlanT<T>::Ct(pl), (cplx<T>*)pl->grid);
+  prof_end(pl, 3);
   return cudaGetLastError() == cudaSuccess ? NUFFT_OK : NUFFT_ECUDA;
 }
 
@@ -597,4 +905,4 @@ template int fmm_forward<float>(nufft_plan_s*, void*);
 template int fmm_to_grid<double>(nufft_plan_s*, const void*, int);
 template int fmm_to_grid<float>(nufft_plan_s*, const void*, int);
 template int fmm_upward_downward<double>(nufft_plan_s*, const FmmOps&, bool, const double2*,
-                                         double2*);
+                                         double2*, float2*);

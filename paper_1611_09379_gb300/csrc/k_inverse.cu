@@ -25,18 +25,9 @@ using namespace nufft;
 
 template <class T>
 int fmm_upward_downward(nufft_plan_s* pl, const FmmOps& ops, bool uniform_sources,
-                        const cplx<T>* charge, double2* lvl2);
+                        const cplx<T>* charge, double2* lvl2, float2* lvl2f);
 
 namespace {
-
-__global__ void k_c128_to_c64(const double2* __restrict__ in, float2* __restrict__ out, int64_t n) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < n) out[i] = make_float2((float)in[i].x, (float)in[i].y);
-}
-__global__ void k_c64_to_c128(const float2* __restrict__ in, double2* __restrict__ out, int64_t n) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < n) out[i] = make_double2(in[i].x, in[i].y);
-}
 
 __global__ void k_fill_ones(double2* __restrict__ q, int64_t n) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -210,27 +201,36 @@ __global__ void k_lambda(const double* __restrict__ lamD, int64_t M, double* __r
 
 constexpr double kExpLimit = 700.0;
 
+// Ctf (optional): FP32 copy for the mixed path, whose exponent limit elim
+// keeps C_k e^Lambda / N inside the FP32 range.
 __global__ void k_assemble_C(const double* __restrict__ lamC, const int32_t* __restrict__ nC,
-                             int64_t N, const double* __restrict__ Lam, double* __restrict__ Ct,
+                             int64_t N, const double* __restrict__ Lam, double elim,
+                             double* __restrict__ Ct, float* __restrict__ Ctf,
                              int* __restrict__ status) {
   int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (k >= N) return;
   double l = lamC[k];
-  if (l == -INFINITY) { Ct[k] = 0.0; return; }
-  double e = l + *Lam;
-  if (!(fabs(e) < kExpLimit)) atomicOr(status, kDevIllCond);
-  double sg = ((k + nC[k]) & 1) ? -1.0 : 1.0;
-  Ct[k] = sg * exp(e) / (double)N;  // with the 1/N of Eq. p1
+  double v = 0.0;
+  if (l != -INFINITY) {
+    double e = l + *Lam;
+    if (!(fabs(e) < elim)) atomicOr(status, kDevIllCond);
+    double sg = ((k + nC[k]) & 1) ? -1.0 : 1.0;
+    v = sg * exp(e) / (double)N;  // with the 1/N of Eq. p1
+  }
+  Ct[k] = v;
+  if (Ctf) Ctf[k] = (float)v;
 }
 
+// elim: largest |exponent| of D_j e^{-Lambda} (the mixed path forms the
+// charges D_j g_j in FP32, so it allows less than FP64 range).
 __global__ void k_assemble_D(const double* __restrict__ lamD, const int32_t* __restrict__ nD,
                              const int32_t* __restrict__ k0s, const double* __restrict__ dels,
-                             int64_t M, const double* __restrict__ Lam, double2* __restrict__ Dt,
-                             int* __restrict__ status) {
+                             int64_t M, const double* __restrict__ Lam, double elim,
+                             double2* __restrict__ Dt, int* __restrict__ status) {
   int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= M) return;
   double e = lamD[j] - *Lam;
-  if (!(fabs(e) < kExpLimit)) atomicOr(status, kDevIllCond);
+  if (!(fabs(e) < elim)) atomicOr(status, kDevIllCond);
   double mag = exp(e);
   if ((nD[j] + k0s[j]) & 1) mag = -mag;
   double sn, cs;
@@ -299,16 +299,6 @@ TmpLayout layout(const nufft_plan_s* pl) {
 
 }  // namespace
 
-int convert_c128_to_c64(const double2* in, float2* out, int64_t n, cudaStream_t st) {
-  k_c128_to_c64<<<nblk(n, 256), 256, 0, st>>>(in, out, n);
-  return cudaGetLastError() == cudaSuccess ? NUFFT_OK : NUFFT_ECUDA;
-}
-
-int convert_c64_to_c128(const float2* in, double2* out, int64_t n, cudaStream_t st) {
-  k_c64_to_c128<<<nblk(n, 256), 256, 0, st>>>(in, out, n);
-  return cudaGetLastError() == cudaSuccess ? NUFFT_OK : NUFFT_ECUDA;
-}
-
 size_t inverse_tmp_bytes(const nufft_plan_s* pl) { return layout(pl).total; }
 
 int inverse_precompute(nufft_plan_s* pl, void* tmp, size_t tmp_bytes) {
@@ -321,6 +311,8 @@ int inverse_precompute(nufft_plan_s* pl, void* tmp, size_t tmp_bytes) {
   if (cudaMalloc((void**)&pl->Ct, N * 8) != cudaSuccess) return NUFFT_ENOMEM;
   if (cudaMalloc((void**)&pl->Dt, M * 16) != cudaSuccess) return NUFFT_ENOMEM;
   if (cudaMalloc((void**)&pl->Lambda, 8) != cudaSuccess) return NUFFT_ENOMEM;
+  if (pl->prec != NUFFT_FP64 && cudaMalloc((void**)&pl->Ctf, N * 4) != cudaSuccess)
+    return NUFFT_ENOMEM;
   // ---- operators of the log kernel (host, long double)
   Bin C(2 * 64 + 2);
   std::vector<double> m2m((size_t)2 * pm * pm, 0.0), m2l((size_t)4 * p * p, 0.0),
@@ -394,7 +386,7 @@ int inverse_precompute(nufft_plan_s* pl, void* tmp, size_t tmp_bytes) {
   ops.c2 = std::log(2.0);
   ops.log_kernel = 1;
   ops.leaf_shift = (const double*)(base + t.shift);
-  int rc = fmm_upward_downward<double>(&sh, ops, false, ones, lvl2);
+  int rc = fmm_upward_downward<double>(&sh, ops, false, ones, lvl2, nullptr);
   if (rc) return rc;
   TreeDims d{N, pl->L, s, p, q, pm};
   double* lamC = (double*)(base + t.lamC);
@@ -408,7 +400,9 @@ int inverse_precompute(nufft_plan_s* pl, void* tmp, size_t tmp_bytes) {
   k_logsum_pts<<<nblk(M, 128), 128, 0, st>>>(d, pl->leaf_start, pl->k0, pl->delta, lexp, lvl2, M,
                                              lamD, nD, pl->status);
   k_lambda<<<1, 1024, 0, st>>>(lamD, M, Lam);
-  k_assemble_C<<<nblk(N, 256), 256, 0, st>>>(lamC, nC, N, Lam, pl->Ct, pl->status);
-  k_assemble_D<<<nblk(M, 256), 256, 0, st>>>(lamD, nD, pl->k0, pl->delta, M, Lam, pl->Dt, pl->status);
+  double elim = pl->prec == NUFFT_FP64 ? kExpLimit : 60.0;
+  k_assemble_C<<<nblk(N, 256), 256, 0, st>>>(lamC, nC, N, Lam, elim, pl->Ct, pl->Ctf, pl->status);
+  k_assemble_D<<<nblk(M, 256), 256, 0, st>>>(lamD, nD, pl->k0, pl->delta, M, Lam, elim, pl->Dt,
+                                             pl->status);
   return cudaGetLastError() == cudaSuccess ? NUFFT_OK : NUFFT_ECUDA;
 }

@@ -151,7 +151,9 @@ __global__ void k_segment_sort(int32_t* __restrict__ perm, const int32_t* __rest
 __global__ void k_points_finalize(const int32_t* __restrict__ perm, int64_t M, int64_t N,
                                   const int32_t* __restrict__ k0o, const double* __restrict__ delo,
                                   int32_t* __restrict__ k0s, double* __restrict__ dels,
-                                  double2* __restrict__ F, double2* __restrict__ E) {
+                                  double2* __restrict__ F, double2* __restrict__ E,
+                                  float* __restrict__ dels_f, float2* __restrict__ Ff,
+                                  float2* __restrict__ Ef) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= M) return;
   int32_t j = perm[i];
@@ -164,6 +166,11 @@ __global__ void k_points_finalize(const int32_t* __restrict__ perm, int64_t M, i
   F[i] = make_double2(-2.0 * sn * sn * invN, 2.0 * cs * sn * invN);
   double sinc = (d == 0.0) ? 1.0 : sn / (kPi * d);
   E[i] = make_double2(cs * sinc, sn * sinc);
+  if (dels_f) {  // FP32 copies for the mixed path
+    dels_f[i] = (float)d;
+    Ff[i] = make_float2((float)F[i].x, (float)F[i].y);
+    Ef[i] = make_float2((float)(cs * sinc), (float)(sn * sinc));
+  }
 }
 
 }  // namespace nufft
@@ -204,6 +211,6 @@ int setup_points(nufft_plan_s* pl, const double* y, void* tmp) {
   k_scatter<<<(unsigned)gb, th, 0, st>>>(leafo, M, cursor, pl->perm);
   k_segment_sort<<<(unsigned)B, 256, 0, st>>>(pl->perm, pl->leaf_start, pl->status);
   k_points_finalize<<<(unsigned)gb, th, 0, st>>>(pl->perm, M, N, k0o, delo, pl->k0, pl->delta,
-                                                 pl->F, pl->E);
+                                                 pl->F, pl->E, pl->delta_f, pl->Ff, pl->Ef);
   return cudaGetLastError() == cudaSuccess ? NUFFT_OK : NUFFT_ECUDA;
 }

@@ -14,20 +14,18 @@ using namespace nufft;
 // kernels and drivers from the other translation units
 size_t setup_tmp_bytes(int64_t M, int64_t B);
 int setup_points(nufft_plan_s* pl, const double* y, void* tmp);
-int fft_init_tables(double2* tw, int64_t N, cudaStream_t st);
+int fft_init_tables(double2* tw, float2* twf, int64_t N, cudaStream_t st);
 size_t fft_table_elems(int64_t N);
 int fft_configure();
 int fft_num_passes(int64_t N);
 template <class T>
-int fft_run(const cplx<T>* in, cplx<T>* out, cplx<T>* buf, int64_t N, int sign, const double2* tw,
-            cudaStream_t st);
+int fft_run(const void* in, int in_f64, void* out, int out_f64, cplx<T>* buf, cplx<T>* buf2,
+            int64_t N, int sign, const cplx<T>* tw, cudaStream_t st);
 template <class T> int fmm_configure();
 template <class T> int fmm_forward(nufft_plan_s* pl, void* g);
 template <class T> int fmm_to_grid(nufft_plan_s* pl, const void* g, int inverse);
 int inverse_precompute(nufft_plan_s* pl, void* tmp, size_t tmp_bytes);
 size_t inverse_tmp_bytes(const nufft_plan_s* pl);
-int convert_c128_to_c64(const double2* in, float2* out, int64_t n, cudaStream_t st);
-int convert_c64_to_c128(const float2* in, double2* out, int64_t n, cudaStream_t st);
 
 namespace {
 
@@ -173,10 +171,11 @@ int build_operators(nufft_plan_s* pl) {
 }
 
 void free_plan(nufft_plan_s* pl) {
-  void* ptrs[] = {pl->perm, pl->leaf_start, pl->k0, pl->delta, pl->F, pl->E, pl->Dt, pl->Ct,
-                  pl->Lambda, pl->mexp, pl->lexp, pl->charge, pl->grid, pl->grid2, pl->lvl2,
-                  pl->op_m2m, pl->op_m2l, pl->op_l2l, pl->op_p2m, pl->op_reg, pl->fft_tw,
-                  pl->status, pl->seg_overflow};
+  void* ptrs[] = {pl->perm, pl->leaf_start, pl->k0, pl->delta, pl->F, pl->E, pl->delta_f,
+                  pl->Ff, pl->Ef, pl->lvl2f, pl->Dt, pl->Ct, pl->Ctf, pl->selft, pl->srcrec, pl->Lambda, pl->mexp, pl->lexp,
+                  pl->charge, pl->grid, pl->grid2, pl->grid3, pl->lvl2, pl->op_m2m, pl->op_m2l,
+                  pl->op_l2l, pl->op_p2m, pl->op_reg, pl->fft_tw, pl->fft_tw_f, pl->status,
+                  pl->seg_overflow};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (pl->prof) {
@@ -327,16 +326,26 @@ int nufft_plan_create(nufft_plan* out, int64_t N, int64_t M, const double* y, do
       (rc = dalloc(&pl->F, M * 16)) || (rc = dalloc(&pl->E, M * 16)) ||
       (rc = dalloc(&pl->mexp, nm * pl->pm * csz)) ||
       (rc = dalloc(&pl->lexp, (nl > 0 ? nl : 1) * pl->p * csz)) ||
-      (rc = dalloc(&pl->charge, big * csz)) || (rc = dalloc(&pl->grid, N * 16)) ||
+      (rc = dalloc(&pl->charge, big * csz)) || (rc = dalloc(&pl->selft, M * csz)) ||
+      (rc = dalloc(&pl->srcrec, M * 2 * csz)) ||
+      (rc = dalloc(&pl->grid, N * 16)) ||
       (rc = dalloc(&pl->grid2, N * 16)) || (rc = dalloc(&pl->lvl2, (8 * pl->q + 1) * 16)) ||
       (rc = dalloc(&pl->fft_tw, fft_table_elems(N) * 16)) || (rc = dalloc(&pl->status, 16))) {
+    free_plan(pl);
+    return rc;
+  }
+  if (fft_num_passes(N) >= 3 && (rc = dalloc(&pl->grid3, N * 16))) { free_plan(pl); return rc; }
+  if (prec == NUFFT_MIXED &&
+      ((rc = dalloc(&pl->delta_f, M * 4)) || (rc = dalloc(&pl->Ff, M * 8)) ||
+       (rc = dalloc(&pl->Ef, M * 8)) || (rc = dalloc(&pl->lvl2f, (8 * pl->q + 1) * 8)) ||
+       (rc = dalloc(&pl->fft_tw_f, fft_table_elems(N) * 8)))) {
     free_plan(pl);
     return rc;
   }
   if ((rc = build_operators(pl))) { free_plan(pl); return rc; }
   cudaStream_t st = pl->stream;
   if (cudaMemsetAsync(pl->status, 0, 16, st) != cudaSuccess) { free_plan(pl); return NUFFT_ECUDA; }
-  if ((rc = fft_init_tables(pl->fft_tw, N, st))) { free_plan(pl); return rc; }
+  if ((rc = fft_init_tables(pl->fft_tw, pl->fft_tw_f, N, st))) { free_plan(pl); return rc; }
   size_t tb = setup_tmp_bytes(M, B);
   if (flags & NUFFT_WANT_INVERSE) {
     size_t ib = inverse_tmp_bytes(pl);
@@ -410,42 +419,36 @@ int nufft_plan_set_stream(nufft_plan pl, void* stream) {
   return NUFFT_OK;
 }
 
+// c_n <-> grid with the FFT of the plan's arithmetic (FP64, or FP32 for the
+// mixed path); caller data complex128 or complex64.
+static int fft_plan(nufft_plan_s* pl, const void* in, int in_f64, void* out, int out_f64,
+                    int sign) {
+  prof_begin(pl, NUFFT_STAGE_FFT);
+  int rc;
+  if (pl->prec == NUFFT_FP64)
+    rc = fft_run<double>(in, in_f64, out, out_f64, pl->grid2, pl->grid3, pl->N, sign,
+                         pl->fft_tw, pl->stream);
+  else
+    rc = fft_run<float>(in, in_f64, out, out_f64, (float2*)pl->grid2, (float2*)pl->grid3, pl->N,
+                        sign, pl->fft_tw_f, pl->stream);
+  prof_end(pl, fft_num_passes(pl->N));
+  return rc;
+}
+
 int nufft_plan_exec_fwd(nufft_plan pl, const void* c, void* g) {
   if (!pl || !c || !g) return NUFFT_EINVAL;
-  int rc;
-  const double2* cin = (const double2*)c;
-  if (pl->flags & NUFFT_IO_C64) {
-    prof_begin(pl, NUFFT_STAGE_OTHER);
-    rc = convert_c64_to_c128((const float2*)c, pl->grid2, pl->N, pl->stream);
-    prof_end(pl, 1);
-    if (rc) return rc;
-    cin = pl->grid2;
-  }
+  const int io64 = (pl->flags & NUFFT_IO_C64) ? 0 : 1;
+  const int t64 = pl->prec == NUFFT_FP64;
   // f_k = sum_n c_n e^{+2 pi i n k/N}  (Eq. p1, unscaled inverse DFT)
-  prof_begin(pl, NUFFT_STAGE_FFT);
-  rc = fft_run<double>(cin, pl->grid, pl->grid2, pl->N, +1, pl->fft_tw, pl->stream);
-  prof_end(pl, fft_num_passes(pl->N));
+  int rc = fft_plan(pl, c, io64, pl->grid, t64, +1);
   if (rc) return rc;
   return pl->prec == NUFFT_FP64 ? fmm_forward<double>(pl, g) : fmm_forward<float>(pl, g);
 }
 
 static int grid_to_coeffs(nufft_plan_s* pl, void* c) {
-  int rc;
   // c'_n = sum_k u_k e^{-2 pi i n k/N}
-  if (pl->flags & NUFFT_IO_C64) {
-    prof_begin(pl, NUFFT_STAGE_FFT);
-    rc = fft_run<double>(pl->grid, pl->grid, pl->grid2, pl->N, -1, pl->fft_tw, pl->stream);
-    prof_end(pl, fft_num_passes(pl->N));
-    if (rc) return rc;
-    prof_begin(pl, NUFFT_STAGE_OTHER);
-    rc = convert_c128_to_c64(pl->grid, (float2*)c, pl->N, pl->stream);
-    prof_end(pl, 1);
-    return rc;
-  }
-  prof_begin(pl, NUFFT_STAGE_FFT);
-  rc = fft_run<double>(pl->grid, (double2*)c, pl->grid2, pl->N, -1, pl->fft_tw, pl->stream);
-  prof_end(pl, fft_num_passes(pl->N));
-  return rc;
+  const int io64 = (pl->flags & NUFFT_IO_C64) ? 0 : 1;
+  return fft_plan(pl, pl->grid, pl->prec == NUFFT_FP64, c, io64, -1);
 }
 
 int nufft_plan_exec_adj(nufft_plan pl, const void* g, void* c) {
