@@ -198,6 +198,25 @@ int nufft_adj(const void *g, const double *y, int64_t M, int64_t N, double eps,
 int inufft(const void *g, const double *y, int64_t M, int64_t N, double eps,
            int prec, unsigned flags, void *c, void *stream);
 
+/* ---------------------------------------------------------------- no allocation */
+
+/* nufft_fwd without any memory allocation.  The paper has no counterpart:
+ * this serves callers that cannot allocate device memory when they need a
+ * transform -- applications whose device memory belongs to a pool allocator
+ * or a fixed budget, and latency-critical loops where cudaMalloc / cudaFree
+ * (which may synchronise the device) are not acceptable.
+ * Same arguments, result and accuracy as nufft_fwd (automatic parameters;
+ * flags: 0 or NUFFT_IO_C64), but every work buffer lives in one fixed
+ * 16 MiB device array compiled into the library, held by every GPU that loads
+ * it until the process exits.  Limits: N <= 2^16 and M <= 2^16; larger sizes
+ * return NUFFT_EINVAL and do nothing.
+ * The first call on a device looks up the array's device address and must run
+ * with that device current; make it before any stream capture.  Calls share
+ * the array and overwrite its contents; calls whose GPU work overlaps (other
+ * streams, other threads) race on it.  Synchronises the stream. */
+int nufft_fwd_noalloc(const void *c, int64_t N, const double *y, int64_t M,
+                      double eps, int prec, unsigned flags, void *g, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -39,6 +39,7 @@ SYMBOLS = [
     "nufft_plan_set_stream", "nufft_plan_profile", "nufft_plan_stats",
     "nufft_plan_exec_fwd",
     "nufft_plan_exec_adj", "nufft_plan_exec_inv", "nufft_fwd", "nufft_adj", "inufft",
+    "nufft_fwd_noalloc",
 ]
 
 
@@ -64,7 +65,7 @@ _lib.nufft_plan_stats.argtypes = [_P, _P, _P]
 _lib.nufft_plan_inverse_coeffs.argtypes = [_P, _P, _P, ctypes.POINTER(ctypes.c_double)]
 for _n in ("nufft_plan_exec_fwd", "nufft_plan_exec_adj", "nufft_plan_exec_inv"):
     getattr(_lib, _n).argtypes = [_P, _P, _P]
-for _n in ("nufft_fwd",):
+for _n in ("nufft_fwd", "nufft_fwd_noalloc"):
     getattr(_lib, _n).argtypes = [_P, _I64, _P, _I64, ctypes.c_double, ctypes.c_int, ctypes.c_uint, _P, _P]
 for _n in ("nufft_adj", "inufft"):
     getattr(_lib, _n).argtypes = [_P, _P, _I64, _I64, ctypes.c_double, ctypes.c_int, ctypes.c_uint, _P, _P]
@@ -273,3 +274,17 @@ def inufft(g, y, M: int, N: int, eps: float, prec: int = FP64, io: str = "c128",
     _oneshot(_lib.inufft, _dev_ptr(g, cd, M, "g"), _dev_ptr(y, torch.float64, M, "y"), M, N, eps,
              prec, io, _P(c.data_ptr()), stream, "inufft")
     return c
+
+
+def nufft_fwd_noalloc(c, N: int, y, M: int, eps: float, prec: int = FP64, io: str = "c128",
+                      out=None, stream=None):
+    """nufft_fwd without memory allocation inside the library (N, M <= 2^16):
+    all work buffers live in a fixed device array of the library.  The output
+    tensor is the caller's (``out``), so callers that must not allocate pass
+    one they own."""
+    torch = _torch()
+    cd = torch.complex64 if io == "c64" else torch.complex128
+    g = out if out is not None else torch.empty(M, dtype=cd, device=y.device)
+    _oneshot(_lib.nufft_fwd_noalloc, _dev_ptr(c, cd, N, "c"), N, _dev_ptr(y, torch.float64, M, "y"),
+             M, eps, prec, io, _dev_ptr(g, cd, M, "g"), stream, "nufft_fwd_noalloc")
+    return g

@@ -53,19 +53,20 @@ long double zeta_even(int s) {
   return sum + t1 + t2 + t3;
 }
 
+// binomial coefficients C(i, k), 0 <= k <= i <= kBinomMax, in a fixed table
+constexpr int kBinomMax = 2 * 64 + 2;
 struct Binom {
-  std::vector<long double> c;
-  int n;
-  explicit Binom(int nmax) : c((size_t)(nmax + 1) * (nmax + 1), 0.0L), n(nmax) {
-    for (int i = 0; i <= nmax; ++i) {
-      c[(size_t)i * (nmax + 1)] = 1;
-      for (int k = 1; k <= i; ++k)
-        c[(size_t)i * (nmax + 1) + k] = c[(size_t)(i - 1) * (nmax + 1) + k - 1] +
-                                         (k <= i - 1 ? c[(size_t)(i - 1) * (nmax + 1) + k] : 0);
+  long double c[(kBinomMax + 1) * (kBinomMax + 1)];
+  Binom() {
+    const int n = kBinomMax;
+    for (int i = 0; i <= n; ++i) {
+      c[i * (n + 1)] = 1;
+      for (int k = 1; k <= n; ++k)
+        c[i * (n + 1) + k] = (k > i) ? 0 : c[(i - 1) * (n + 1) + k - 1] + c[(i - 1) * (n + 1) + k];
     }
   }
   long double operator()(int i, int k) const {
-    return (k < 0 || k > i) ? 0 : c[(size_t)i * (n + 1) + k];
+    return (k < 0 || k > i) ? 0 : c[i * (kBinomMax + 1) + k];
   }
 };
 
@@ -93,13 +94,19 @@ int upload(void** dst, const void* src, size_t bytes) {
   return NUFFT_OK;
 }
 
-// Build the translation operators (level independent, scaled form) and
-// the level-2 weights; upload in the plan's arithmetic type.
-int build_operators(nufft_plan_s* pl) {
+}  // namespace
+
+int plan_configure() { return configure_once(); }
+
+// The translation operators (level independent, scaled form) and the
+// level-2 weights of a plan, written into caller arrays of sizes
+// m2m 2 pm^2, m2l 4 p^2, l2l 2 p^2, rp s pm, reg 4 (2q)^2 (every entry set).
+void make_operator_tables(const nufft_plan_s* pl, long double* m2m, long double* m2l,
+                          long double* l2l, long double* rp, double* reg) {
   const int p = pl->p, pm = pl->pm, q = pl->q, Q2 = 2 * q, s = pl->s;
-  Binom C(2 * 64 + 2);
+  static const Binom C;
   // M2M [sigma][k][m]
-  std::vector<long double> m2m((size_t)2 * pm * pm, 0.0L);
+  for (size_t i = 0; i < (size_t)2 * pm * pm; ++i) m2m[i] = 0.0L;
   for (int sg = 0; sg < 2; ++sg) {
     long double sig = sg ? 0.25L : -0.25L;
     for (int m = 0; m < pm; ++m)
@@ -109,7 +116,6 @@ int build_operators(nufft_plan_s* pl) {
   }
   // M2L [d][m][n], d = -3, -2, 2, 3
   const int dval[4] = {-3, -2, 2, 3};
-  std::vector<long double> m2l((size_t)4 * p * p, 0.0L);
   for (int t = 0; t < 4; ++t)
     for (int m = 0; m < p; ++m)
       for (int n = 0; n < p; ++n) {
@@ -118,7 +124,7 @@ int build_operators(nufft_plan_s* pl) {
         m2l[(size_t)t * p * p + (size_t)m * p + n] = v;
       }
   // L2L [sigma][n'][n]
-  std::vector<long double> l2l((size_t)2 * p * p, 0.0L);
+  for (size_t i = 0; i < (size_t)2 * p * p; ++i) l2l[i] = 0.0L;
   for (int sg = 0; sg < 2; ++sg) {
     long double sig = sg ? 0.25L : -0.25L;
     for (int n = 0; n < p; ++n)
@@ -127,13 +133,12 @@ int build_operators(nufft_plan_s* pl) {
             0.5L * C(k, n) * powl(0.5L, n) * powl(sig, k - n);
   }
   // P2M table for the uniform grid: rho_o = o/s - 1/2
-  std::vector<long double> rp((size_t)s * pm);
   for (int o = 0; o < s; ++o) {
     long double rho = (long double)o / s - 0.5L, pw = 1;
     for (int m = 0; m < pm; ++m) { rp[(size_t)o * pm + m] = pw; pw *= rho; }
   }
   // level-2 weights W1, W2 [l][i], shifts S-, S+ [i][r]
-  std::vector<double> reg((size_t)4 * Q2 * Q2, 0.0);
+  for (size_t i = 0; i < (size_t)4 * Q2 * Q2; ++i) reg[i] = 0.0;
   for (int l = 0; l < Q2; ++l)
     for (int i = 0; i < Q2; ++i) {
       if (((i + l) & 1) == 0) continue;
@@ -151,6 +156,17 @@ int build_operators(nufft_plan_s* pl) {
       reg[(size_t)2 * Q2 * Q2 + (size_t)i * Q2 + r] = (double)(((i - r) & 1) ? -c : c);
       reg[(size_t)3 * Q2 * Q2 + (size_t)i * Q2 + r] = (double)c;
     }
+}
+
+namespace {
+
+// Build the operators of a plan and upload them in the plan's arithmetic type.
+int build_operators(nufft_plan_s* pl) {
+  const int p = pl->p, pm = pl->pm, q = pl->q, Q2 = 2 * q, s = pl->s;
+  std::vector<long double> m2m((size_t)2 * pm * pm), m2l((size_t)4 * p * p),
+      l2l((size_t)2 * p * p), rp((size_t)s * pm);
+  std::vector<double> reg((size_t)4 * Q2 * Q2);
+  make_operator_tables(pl, m2m.data(), m2l.data(), l2l.data(), rp.data(), reg.data());
   int rc;
   if (pl->prec == NUFFT_FP64) {
     auto a = cast_vec<double>(m2m), b = cast_vec<double>(m2l), c = cast_vec<double>(l2l),
