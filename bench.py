@@ -325,9 +325,42 @@ def run_ours(args):
         "gpu_launches": launches,
         "clocks": mx["clocks"],
     }
+    if args.lsq:
+        out["inufft_lsq"] = run_lsq()
     print(json.dumps(out))
     if ws > 1:
         dist.destroy_process_group()
+
+
+def run_lsq(maxit: int = 60000):
+    """Least-squares INUFFT (N = 2^16, M = 2^18, 1:100 contrast, complex128):
+    CG to a 1e-8 residual with plain weights and with the shipped learned
+    density compensation; plan and weights outside the timed solve."""
+    import torch
+
+    import paper_1611_09379_gb300 as nf
+    from paper_1611_09379_gb300 import dcf
+    N, M = 1 << 16, 1 << 18
+    y = workloads.points("contrast", M, seed=1234)
+    c_true = workloads.coeffs(N, seed=99)
+    plan = nf.Plan(N, torch.from_numpy(y).cuda(), eps=1e-10)
+    g = plan.forward(torch.from_numpy(c_true).cuda())
+    mlp = dcf.load()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    w = dcf.weights(plan, mlp)
+    torch.cuda.synchronize()
+    t_w = time.perf_counter() - t0
+    out = {"workload": "least-squares INUFFT N=2^16 M=2^18 1:100 contrast (configs[3])",
+           "tol": 1e-8, "plan": plan.info(), "weights_s": t_w}
+    for name, ww in (("learned", w), ("plain", None)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        c, it, res = plan.solve_lsq(g, ww, tol=1e-8, maxit=maxit, check=False)
+        torch.cuda.synchronize()
+        out[name] = {"iterations": it, "residual": res, "solve_s": time.perf_counter() - t0}
+    plan.close()
+    return out
 
 
 def cpu_oracle_sample(c, y, budget_s: float = 15.0):
@@ -392,7 +425,13 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--lsq", action="store_true",
+                    help="also run the least-squares INUFFT, learned vs plain CG (~2.5 min)")
+    ap.add_argument("--lsq-only", action="store_true", help="only the least-squares comparison")
     args = ap.parse_args()
+    if args.lsq_only:
+        print(json.dumps({"inufft_lsq": run_lsq()}))
+        return
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

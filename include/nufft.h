@@ -161,6 +161,70 @@ int nufft_plan_exec_adj(nufft_plan plan, const void *g, void *c);
  *   g [device] M inputs, c [device] N outputs.  Asynchronous. */
 int nufft_plan_exec_inv(nufft_plan plan, const void *g, void *c);
 
+/* Least-squares INUFFT for M > N (problem (ii) of Sec. 2 with more samples
+ * than coefficients; the paper states the problem, the CG solver is this
+ * library's): c = argmin sum_j w_j |sum_n c_n e^{i n y_j} - g_j|^2, by
+ * conjugate gradients on A^H W A c = A^H W g, A_jn = e^{i n y_j}, each
+ * product being one forward and one adjoint FMM of the plan.
+ *   g      [device] M samples (complex128, original point order)
+ *   w      [device] float[M] positive weights (original order), NULL = 1
+ *   tol    stop when ||A^H W (g - A c)|| / ||A^H W g|| <= tol (CG residual)
+ *   maxit  iteration cap
+ *   c      [device] N coefficients out (complex128)
+ *   iters, resid [host] iterations used and final relative residual (may be NULL)
+ * Needs a complex128 plan; use NUFFT_FP64 for tolerances below ~1e-6.  Work
+ * vectors (4N + M complex) are allocated by the plan on first use.  Reads the
+ * residual every few iterations (synchronises).  Returns NUFFT_ENOTCONV when
+ * maxit is reached first (c then holds the last iterate). */
+int nufft_plan_solve_lsq(nufft_plan plan, const void *g, const float *w, double tol,
+                         int maxit, void *c, int *iters, double *resid);
+
+/* ---------------------------------------------------------------- learned weights */
+
+/* Density-compensation features of a plan's points, for the learned weights
+ * of nufft_plan_solve_lsq: in periodic position order, the 8 gaps around
+ * each point (ranks r-4..r+4), as log(gap M / N) with the gap in grid units
+ * (scale free).  feat [device] float[M][8], original point order.
+ * Synchronises the stream. */
+int nufft_plan_dcf_features(nufft_plan plan, float *feat);
+
+/* Training data for the network below.  y [device] double[S][M]: S point sets,
+ * each sorted ascending in [0, 2 pi).
+ * nufft_dcf_features_sorted: feat [device] float[S*M][8], the features above.
+ * nufft_dcf_targets: logw [device] float[S*M] = log(w / mean w) (floored at
+ *   log 1e-4) for the weights of the equations sum_j |D_N(y_i - y_j)|^2 w_j = N
+ *   (D_N(t) = sum_{n<N} e^{int}), which make A^H W A closest to the identity in
+ *   Frobenius norm, found by `iters` multiplicative fixed-point steps
+ *   w_i <- w_i N / sum_j |D_N(y_i - y_j)|^2 w_j (they keep w positive; a direct
+ *   solve is ill-conditioned and gives signed weights).  M <= 1024.
+ * Both asynchronous. */
+int nufft_dcf_features_sorted(const double *y, int64_t S, int64_t M, float *feat, void *stream);
+int nufft_dcf_targets(const double *y, int64_t S, int64_t M, int64_t N, int iters,
+                      float *logw, void *stream);
+
+/* A density-compensation network w = softplus(MLP(feat)), MLP 8 -> 64 -> 64 -> 1
+ * with GELU hidden layers; 4801 parameters laid out W1[64][8] b1[64]
+ * W2[64][64] b2[64] W3[64] b3.  FP32 master weights for training; inference
+ * uses the weights rounded to BF16 with FP32 accumulation.  The paper has no
+ * learned component; it serves the least-squares solve above. */
+typedef struct nufft_mlp_s *nufft_mlp;
+int nufft_mlp_create(nufft_mlp *out);   /* all parameters zero */
+int nufft_mlp_destroy(nufft_mlp mlp);
+int nufft_mlp_num_params(void);
+/* host float[4801]; reset_optimizer != 0 clears the Adam state */
+int nufft_mlp_set_params(nufft_mlp mlp, const float *params, int reset_optimizer);
+int nufft_mlp_get_params(nufft_mlp mlp, float *params);
+/* w [device] float[n] = softplus(MLP(feat [device] float[n][8])); asynchronous */
+int nufft_mlp_infer(nufft_mlp mlp, const float *feat, int64_t n, float *w, void *stream);
+/* gradient of mean_i (log w_i - target_i)^2 w.r.t. the FP32 parameters:
+ * grad [host] float[4801] and loss [host] (either may be NULL; synchronises
+ * when one is given).  target [device] float[n] = log of the desired weights. */
+int nufft_mlp_grad(nufft_mlp mlp, const float *feat, const float *target, int64_t n,
+                   float *grad, float *loss, void *stream);
+/* one Adam step (lr) on that loss; loss [host] optional (synchronises) */
+int nufft_mlp_train_step(nufft_mlp mlp, const float *feat, const float *target, int64_t n,
+                         float lr, float *loss, void *stream);
+
 /* ---------------------------------------------------------------- profiling */
 
 /* Stages of an evaluation, for nufft_plan_stats. */

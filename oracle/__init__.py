@@ -18,6 +18,8 @@ What it computes (each a definition evaluated directly, see oracle.c):
 * ``exact_grid``  leaf index, nearest grid index k0 and offset delta of
                   y_j * N / (2 pi), in exact rational arithmetic   (Sec. 2.1)
 * ``bernoulli``   exact Bernoulli numbers B_0..B_n                 (Eq. 10-12)
+* ``lsq_dense``   c = argmin ||A c - g||, A_jn = e^{i n y_j}, by a dense
+                  least-squares solve (LAPACK through numpy) for small N
 
 Parity unpinned: none of the routines above; the paper's plotted values
 (Figs. comp1, comp4-comp6) are absent from the text and nothing here
@@ -313,6 +315,31 @@ def bernoulli(nmax: int):
     if nmax >= 1:
         out[1] = -out[1]
     return out
+
+
+# ---------------------------------------------------------------- least squares
+
+def nudft_matrix(y, N: int) -> np.ndarray:
+    """A_jn = e^{i n y_j} (M x N) with the phase n*y_j rounded once in FP64
+    (error below N * 2^-50, i.e. under 1e-12 for N <= 1024)."""
+    y = np.asarray(y, dtype=np.float64)
+    n = np.arange(N, dtype=np.float64)
+    return np.exp(1j * np.multiply.outer(y, n))
+
+
+def lsq_dense(g, y, N: int, w=None) -> np.ndarray:
+    """Weighted least squares argmin sum_j w_j |(A c)_j - g_j|^2 by a dense solve
+    (problem (ii) of Sec. 2 for M > N); N <= 1024."""
+    if N > 1024:
+        raise ValueError("dense least squares is for N <= 1024")
+    A = nudft_matrix(y, N)
+    g = np.asarray(g, dtype=np.complex128)
+    if w is not None:
+        sw = np.sqrt(np.asarray(w, dtype=np.float64))
+        A = A * sw[:, None]
+        g = g * sw
+    c, *_ = np.linalg.lstsq(A, g, rcond=None)
+    return c
 
 
 # ---------------------------------------------------------------- error norms

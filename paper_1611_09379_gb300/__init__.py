@@ -39,7 +39,10 @@ SYMBOLS = [
     "nufft_plan_set_stream", "nufft_plan_profile", "nufft_plan_stats",
     "nufft_plan_exec_fwd",
     "nufft_plan_exec_adj", "nufft_plan_exec_inv", "nufft_fwd", "nufft_adj", "inufft",
-    "nufft_fwd_noalloc",
+    "nufft_fwd_noalloc", "nufft_plan_solve_lsq", "nufft_plan_dcf_features",
+    "nufft_dcf_features_sorted", "nufft_dcf_targets", "nufft_mlp_create", "nufft_mlp_destroy",
+    "nufft_mlp_num_params", "nufft_mlp_set_params", "nufft_mlp_get_params", "nufft_mlp_infer",
+    "nufft_mlp_grad", "nufft_mlp_train_step",
 ]
 
 
@@ -61,6 +64,18 @@ _lib.nufft_plan_info.argtypes = [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTE
 _lib.nufft_plan_set_stream.argtypes = [_P, _P]
 _lib.nufft_plan_points.argtypes = [_P, _P, _P, _P, _P]
 _lib.nufft_plan_profile.argtypes = [_P, ctypes.c_int]
+_lib.nufft_plan_dcf_features.argtypes = [_P, _P]
+_lib.nufft_dcf_features_sorted.argtypes = [_P, _I64, _I64, _P, _P]
+_lib.nufft_dcf_targets.argtypes = [_P, _I64, _I64, _I64, ctypes.c_int, _P, _P]
+_lib.nufft_mlp_create.argtypes = [ctypes.POINTER(_P)]
+_lib.nufft_mlp_destroy.argtypes = [_P]
+_lib.nufft_mlp_set_params.argtypes = [_P, _P, ctypes.c_int]
+_lib.nufft_mlp_get_params.argtypes = [_P, _P]
+_lib.nufft_mlp_infer.argtypes = [_P, _P, _I64, _P, _P]
+_lib.nufft_mlp_grad.argtypes = [_P, _P, _P, _I64, _P, _P, _P]
+_lib.nufft_mlp_train_step.argtypes = [_P, _P, _P, _I64, ctypes.c_float, _P, _P]
+_lib.nufft_plan_solve_lsq.argtypes = [_P, _P, _P, ctypes.c_double, ctypes.c_int, _P,
+                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
 _lib.nufft_plan_stats.argtypes = [_P, _P, _P]
 _lib.nufft_plan_inverse_coeffs.argtypes = [_P, _P, _P, ctypes.POINTER(ctypes.c_double)]
 for _n in ("nufft_plan_exec_fwd", "nufft_plan_exec_adj", "nufft_plan_exec_inv"):
@@ -224,6 +239,30 @@ class Plan:
                                         _dev_ptr(c, self.cdtype, self.N, "c")), "nufft_plan_exec_inv")
         return c
 
+    def solve_lsq(self, g, w=None, tol: float = 1e-8, maxit: int = 500, out=None, check=True):
+        """Least-squares coefficients c = argmin sum_j w_j |(A c)_j - g_j|^2 by CG on
+        the normal equations.  Returns (c, iterations, relative residual); raises
+        on non-convergence unless check=False."""
+        torch = _torch()
+        c = self._out(self.N, out)
+        wp = None
+        if w is not None:
+            wp = _dev_ptr(w, torch.float32, self.M, "w")
+        it, res = ctypes.c_int(), ctypes.c_double()
+        rc = _lib.nufft_plan_solve_lsq(self._h, _dev_ptr(g, self.cdtype, self.M, "g"), wp, tol, maxit,
+                                       _dev_ptr(c, self.cdtype, self.N, "c"), ctypes.byref(it),
+                                       ctypes.byref(res))
+        if rc != OK and (check or rc != ENOTCONV):
+            raise NufftError(rc, "nufft_plan_solve_lsq")
+        return c, it.value, res.value
+
+    def dcf_features(self):
+        """Density-compensation features of the points: float32 [M, 8] (original order)."""
+        torch = _torch()
+        feat = torch.empty(self.M, 8, dtype=torch.float32, device=self.device)
+        _check(_lib.nufft_plan_dcf_features(self._h, _P(feat.data_ptr())), "nufft_plan_dcf_features")
+        return feat
+
     def close(self):
         if getattr(self, "_h", None):
             _lib.nufft_plan_destroy(self._h)
@@ -288,3 +327,94 @@ def nufft_fwd_noalloc(c, N: int, y, M: int, eps: float, prec: int = FP64, io: st
     _oneshot(_lib.nufft_fwd_noalloc, _dev_ptr(c, cd, N, "c"), N, _dev_ptr(y, torch.float64, M, "y"),
              M, eps, prec, io, _dev_ptr(g, cd, M, "g"), stream, "nufft_fwd_noalloc")
     return g
+
+
+def dcf_features_sorted(y_sorted, stream=None):
+    """Features of S sorted point sets (float64 CUDA tensor [S, M]): float32 [S*M, 8]."""
+    torch = _torch()
+    S, M = y_sorted.shape
+    feat = torch.empty(S * M, 8, dtype=torch.float32, device=y_sorted.device)
+    _check(_lib.nufft_dcf_features_sorted(_dev_ptr(y_sorted, torch.float64, S * M, "y"), S, M,
+                                          _P(feat.data_ptr()), _stream_handle(stream)),
+           "nufft_dcf_features_sorted")
+    return feat
+
+
+def dcf_targets(y_sorted, N: int, iters: int = 300, stream=None):
+    """log(w / mean w) of the fixed-point density-compensation weights, float32 [S*M]."""
+    torch = _torch()
+    S, M = y_sorted.shape
+    out = torch.empty(S * M, dtype=torch.float32, device=y_sorted.device)
+    _check(_lib.nufft_dcf_targets(_dev_ptr(y_sorted, torch.float64, S * M, "y"), S, M, N, iters,
+                                  _P(out.data_ptr()), _stream_handle(stream)), "nufft_dcf_targets")
+    return out
+
+
+class MLP:
+    """The density-compensation network (8 -> 64 -> 64 -> 1, GELU, softplus) of the library."""
+
+    NPARAM = None
+
+    def __init__(self, params=None):
+        h = _P()
+        _check(_lib.nufft_mlp_create(ctypes.byref(h)), "nufft_mlp_create")
+        self._h = h
+        MLP.NPARAM = _lib.nufft_mlp_num_params()
+        if params is not None:
+            self.set_params(params)
+
+    def set_params(self, params, reset_optimizer=True):
+        import numpy as np
+        a = np.ascontiguousarray(params, dtype=np.float32)
+        if a.size != MLP.NPARAM:
+            raise ValueError(f"expected {MLP.NPARAM} parameters")
+        _check(_lib.nufft_mlp_set_params(self._h, a.ctypes.data_as(_P), 1 if reset_optimizer else 0),
+               "nufft_mlp_set_params")
+
+    def get_params(self):
+        import numpy as np
+        a = np.empty(MLP.NPARAM, np.float32)
+        _check(_lib.nufft_mlp_get_params(self._h, a.ctypes.data_as(_P)), "nufft_mlp_get_params")
+        return a
+
+    def infer(self, feat, out=None, stream=None):
+        torch = _torch()
+        n = feat.shape[0]
+        w = out if out is not None else torch.empty(n, dtype=torch.float32, device=feat.device)
+        _check(_lib.nufft_mlp_infer(self._h, _dev_ptr(feat, torch.float32, n * 8, "feat"), n,
+                                    _dev_ptr(w, torch.float32, n, "w"), _stream_handle(stream)),
+               "nufft_mlp_infer")
+        return w
+
+    def grad(self, feat, target, stream=None):
+        import numpy as np
+        torch = _torch()
+        n = feat.shape[0]
+        g = np.empty(MLP.NPARAM, np.float32)
+        loss = ctypes.c_float()
+        _check(_lib.nufft_mlp_grad(self._h, _dev_ptr(feat, torch.float32, n * 8, "feat"),
+                                   _dev_ptr(target, torch.float32, n, "target"), n, g.ctypes.data_as(_P),
+                                   ctypes.cast(ctypes.byref(loss), _P), _stream_handle(stream)),
+               "nufft_mlp_grad")
+        return g, loss.value
+
+    def train_step(self, feat, target, lr, want_loss=False, stream=None):
+        torch = _torch()
+        n = feat.shape[0]
+        loss = ctypes.c_float()
+        _check(_lib.nufft_mlp_train_step(self._h, _dev_ptr(feat, torch.float32, n * 8, "feat"),
+                                         _dev_ptr(target, torch.float32, n, "target"), n, lr,
+                                         ctypes.cast(ctypes.byref(loss), _P) if want_loss else None,
+                                         _stream_handle(stream)), "nufft_mlp_train_step")
+        return loss.value if want_loss else None
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.nufft_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

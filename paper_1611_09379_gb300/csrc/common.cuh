@@ -140,6 +140,7 @@ struct nufft_plan_s {
   int *status = nullptr;   // device error word
   int *seg_overflow = nullptr;
   StageProf *prof = nullptr;
+  void *lsq_work = nullptr;  // CG work vectors (created on first least-squares solve)
 };
 
 // Bracket the launches of one stage (no-ops unless profiling is enabled).

@@ -191,7 +191,7 @@ void free_plan(nufft_plan_s* pl) {
                   pl->Ff, pl->Ef, pl->lvl2f, pl->Dt, pl->Ct, pl->Ctf, pl->selft, pl->srcrec, pl->Lambda, pl->mexp, pl->lexp,
                   pl->charge, pl->grid, pl->grid2, pl->grid3, pl->lvl2, pl->op_m2m, pl->op_m2l,
                   pl->op_l2l, pl->op_p2m, pl->op_reg, pl->fft_tw, pl->fft_tw_f, pl->status,
-                  pl->seg_overflow};
+                  pl->seg_overflow, pl->lsq_work};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (pl->prof) {

@@ -274,3 +274,23 @@ def test_binning_is_stable_counting_sort(orc):
         assert np.all(np.diff(seg) > 0)
         assert np.all(leaf[seg] == bb)
     assert start[0] == 0 and start[-1] == y.size
+
+
+# ------------------------------------------------------------- density-compensation network
+
+def test_mlp_oracle_gradient_matches_finite_differences():
+    """The FP64 reference gradient of the DCF network equals central finite
+    differences of its loss (pins the hand-written chain rule)."""
+    from oracle import mlp
+    rng = np.random.default_rng(0)
+    p = rng.standard_normal(mlp.NPARAM) * 0.3
+    X = rng.standard_normal((40, 8))
+    t = rng.standard_normal(40)
+    g, _ = mlp.grad(p, X, t)
+    for k in list(range(0, 512, 97)) + [512, 600, 4000, 4672, 4700, 4736, 4799, 4800]:
+        h = 1e-6
+        pp, pm = p.copy(), p.copy()
+        pp[k] += h
+        pm[k] -= h
+        fd = (mlp.loss(pp, X, t) - mlp.loss(pm, X, t)) / (2 * h)
+        assert abs(fd - g[k]) <= 1e-6 * max(1.0, abs(g[k])), k
