@@ -69,14 +69,19 @@ typedef enum {
 typedef struct nufft_plan_s *nufft_plan;
 
 /* FMM parameters.  Any field <= 0 is chosen automatically:
- *   lmax: tree depth, default max(2, log2 N - 5) (Sec. 3.2, l* = 5)
+ *   lmax: tree depth, default max(2, round(log2 sqrt(N M)) - 5) (Eq. 25 with
+ *         the empirical l* = 5 of Sec. 3.2)
  *   p:    1/t MLFMM truncation number, q: regular-series truncation number,
  *         both from Eq. 18.2 with the fraction read as 10/(3 pi eps)
- * Constraints: 2 <= lmax <= log2 N, 4 <= p <= 64, 2 <= q <= 32. */
+ *   batch: number of signals sharing the point set (default 1); exec calls
+ *         then take [batch][N] coefficients and [batch][M] samples
+ * Constraints: 2 <= lmax <= log2 N, 4 <= p <= 64, 2 <= q <= 32,
+ * batch <= 4096. */
 typedef struct {
   int lmax;
   int p;
   int q;
+  int batch;
 } nufft_params;
 
 /* ---------------------------------------------------------------- host only */
@@ -146,19 +151,20 @@ int nufft_plan_inverse_coeffs(nufft_plan plan, double *Ct, double *Dt, double *L
 int nufft_plan_set_stream(nufft_plan plan, void *stream);
 
 /* Forward NUFFT (problem (i)): g_j = sum_n c_n e^{i n y_j}.
- *   c [device] N coefficients, g [device] M outputs (original point order).
+ *   c [device] batch x N coefficients, g [device] batch x M outputs (original
+ *   point order), signal-major.
  * c and g must not overlap.  Asynchronous. */
 int nufft_plan_exec_fwd(nufft_plan plan, const void *c, void *g);
 
 /* Adjoint NUFFT: c_n = sum_j e^{-i n y_j} g_j (conjugate transpose of the
  * forward map; the FMM runs with sources and targets exchanged, Sec. 2.1).
- *   g [device] M inputs, c [device] N outputs.  Asynchronous. */
+ *   g [device] batch x M inputs, c [device] batch x N outputs.  Asynchronous. */
 int nufft_plan_exec_adj(nufft_plan plan, const void *g, void *c);
 
 /* Square inverse NUFFT (problem (ii), M == N): the unique band-limited c
  * with sum_n c_n e^{i n y_j} = g_j, by the Lagrange form Eq. p6 / p8
  * followed by the DFT of Eq. p1.  Needs NUFFT_WANT_INVERSE.
- *   g [device] M inputs, c [device] N outputs.  Asynchronous. */
+ *   g [device] batch x M inputs, c [device] batch x N outputs.  Asynchronous. */
 int nufft_plan_exec_inv(nufft_plan plan, const void *g, void *c);
 
 /* Least-squares INUFFT for M > N (problem (ii) of Sec. 2 with more samples
@@ -172,7 +178,8 @@ int nufft_plan_exec_inv(nufft_plan plan, const void *g, void *c);
  *   maxit  iteration cap
  *   c      [device] N coefficients out (complex128)
  *   iters, resid [host] iterations used and final relative residual (may be NULL)
- * Needs a complex128 plan; use NUFFT_FP64 for tolerances below ~1e-6.  Work
+ * Needs a complex128 plan with batch 1; use NUFFT_FP64 for tolerances below
+ * ~1e-6.  Work
  * vectors (4N + M complex) are allocated by the plan on first use.  Reads the
  * residual every few iterations (synchronises).  Returns NUFFT_ENOTCONV when
  * maxit is reached first (c then holds the last iterate). */

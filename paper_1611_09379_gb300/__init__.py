@@ -47,7 +47,8 @@ SYMBOLS = [
 
 
 class Params(ctypes.Structure):
-    _fields_ = [("lmax", ctypes.c_int), ("p", ctypes.c_int), ("q", ctypes.c_int)]
+    _fields_ = [("lmax", ctypes.c_int), ("p", ctypes.c_int), ("q", ctypes.c_int),
+                ("batch", ctypes.c_int)]
 
 
 _P = ctypes.c_void_p
@@ -111,7 +112,7 @@ def version() -> int:
 
 def choose_params(N: int, M: int, eps: float, prec: int = FP64, lmax: int = 0, p: int = 0, q: int = 0):
     """(lmax, p, q) the library would use (host only, no GPU needed)."""
-    prm = Params(lmax, p, q)
+    prm = Params(lmax, p, q, 1)
     _check(_lib.nufft_choose_params(N, M, eps, prec, ctypes.byref(prm)), "nufft_choose_params")
     return prm.lmax, prm.p, prm.q
 
@@ -147,20 +148,23 @@ class Plan:
     prec: FP64 or MIXED; io: 'c128' or 'c64' element type of c and g;
     inverse=True precomputes C_k, D_j for :meth:`inverse` (needs M == N).
     lmax / p / q override the automatic parameters (0 = automatic).
+    batch: signals sharing the points; exec calls take [batch, N] / [batch, M].
     """
 
     def __init__(self, N: int, y, eps: float = 1e-12, prec: int = FP64, io: str = "c128",
-                 inverse: bool = False, lmax: int = 0, p: int = 0, q: int = 0, stream=None):
+                 inverse: bool = False, lmax: int = 0, p: int = 0, q: int = 0, batch: int = 1,
+                 stream=None):
         torch = _torch()
         self.N = int(N)
         self.M = int(y.numel())
         self.prec = prec
         self.io = io
         self.cdtype = torch.complex64 if io == "c64" else torch.complex128
+        self.batch = int(batch)
         flags = (IO_C64 if io == "c64" else 0) | (WANT_INVERSE if inverse else 0)
         self._stream = stream
         h = _P()
-        prm = Params(lmax, p, q)
+        prm = Params(lmax, p, q, self.batch)
         yp = _dev_ptr(y, torch.float64, self.M, "y")
         _check(_lib.nufft_plan_create(ctypes.byref(h), self.N, self.M, yp, eps, prec,
                                       ctypes.byref(prm), flags, _stream_handle(stream)),
@@ -215,28 +219,32 @@ class Plan:
     def _out(self, n, out):
         torch = _torch()
         if out is None:
-            out = torch.empty(n, dtype=self.cdtype, device=self.device)
+            shape = (n,) if self.batch == 1 else (self.batch, n)
+            out = torch.empty(shape, dtype=self.cdtype, device=self.device)
         return out
 
     def forward(self, c, out=None):
         """g_j = sum_n c_n e^{i n y_j} (asynchronous on the plan's stream)."""
         g = self._out(self.M, out)
-        _check(_lib.nufft_plan_exec_fwd(self._h, _dev_ptr(c, self.cdtype, self.N, "c"),
-                                        _dev_ptr(g, self.cdtype, self.M, "g")), "nufft_plan_exec_fwd")
+        B = self.batch
+        _check(_lib.nufft_plan_exec_fwd(self._h, _dev_ptr(c, self.cdtype, B * self.N, "c"),
+                                        _dev_ptr(g, self.cdtype, B * self.M, "g")), "nufft_plan_exec_fwd")
         return g
 
     def adjoint(self, g, out=None):
         """c_n = sum_j e^{-i n y_j} g_j."""
         c = self._out(self.N, out)
-        _check(_lib.nufft_plan_exec_adj(self._h, _dev_ptr(g, self.cdtype, self.M, "g"),
-                                        _dev_ptr(c, self.cdtype, self.N, "c")), "nufft_plan_exec_adj")
+        B = self.batch
+        _check(_lib.nufft_plan_exec_adj(self._h, _dev_ptr(g, self.cdtype, B * self.M, "g"),
+                                        _dev_ptr(c, self.cdtype, B * self.N, "c")), "nufft_plan_exec_adj")
         return c
 
     def inverse(self, g, out=None):
         """Band-limited c with sum_n c_n e^{i n y_j} = g_j (M == N, Eq. p6/p8)."""
         c = self._out(self.N, out)
-        _check(_lib.nufft_plan_exec_inv(self._h, _dev_ptr(g, self.cdtype, self.M, "g"),
-                                        _dev_ptr(c, self.cdtype, self.N, "c")), "nufft_plan_exec_inv")
+        B = self.batch
+        _check(_lib.nufft_plan_exec_inv(self._h, _dev_ptr(g, self.cdtype, B * self.M, "g"),
+                                        _dev_ptr(c, self.cdtype, B * self.N, "c")), "nufft_plan_exec_inv")
         return c
 
     def solve_lsq(self, g, w=None, tol: float = 1e-8, maxit: int = 500, out=None, check=True):

@@ -57,6 +57,9 @@ struct TreeDims {
   int p;       // 1/t expansion length
   int q;       // regular-series truncation number
   int pm;      // multipole length kept (max(p, 2q + 1))
+  int64_t mstride = 0;  // per-signal strides (batched plans; blockIdx.y = signal)
+  int64_t lstride = 0;  //   multipoles, locals (complex elements)
+  int64_t M_ = 0;       //   and points (charges per signal)
 };
 
 // Device-side error word (set by kernels, read back by the host).
@@ -98,6 +101,7 @@ struct nufft_plan_s {
   int64_t N = 0, M = 0;
   int L = 0, B = 0, s = 0, p = 0, q = 0, pm = 0;
   int prec = 0;
+  int batch = 1;        // signals sharing the point set
   unsigned flags = 0;
   double eps = 0;
   cudaStream_t stream = nullptr;
@@ -122,7 +126,7 @@ struct nufft_plan_s {
   void *lexp = nullptr;    // [levels 3..L][box][p] complex (T)
   void *charge = nullptr;  // [max(N, M)] complex (T): charges in sorted order
   void *selft = nullptr;   // [M] complex (T): nearest-pair terms of the adjoint / inverse
-  void *srcrec = nullptr;  // [M] packed (k0, delta, charge) records: 16 B (FP32) / 32 B (FP64)
+  void *srcpos = nullptr;  // [M] packed (k0, delta) source positions: 8 B (FP32) / 16 B (FP64)
   double2 *grid = nullptr; // [N] work vector on the grid (complex128 storage; used
                            //     as complex64 by the mixed path)
   double2 *grid2 = nullptr;// [N] FFT scratch

@@ -69,6 +69,9 @@ __global__ void __launch_bounds__(256) k_fft_pass(const void* __restrict__ in, i
   const int64_t NR = N >> logR;
   const int64_t j0 = (int64_t)blockIdx.x * J;
   const int nth = blockDim.x;
+  // signal blockIdx.y of a batch: vectors at stride N elements
+  in = (const char*)in + (size_t)blockIdx.y * N * (in_f64 ? 16 : 8);
+  out = (char*)out + (size_t)blockIdx.y * N * (out_f64 ? 16 : 8);
 
   for (int m = threadIdx.x; m < R / 2; m += nth)
     twR[m] = twiddle_t<T>(tw, (int64_t)m * (N >> logR), lo_bits, sign);
@@ -160,13 +163,13 @@ int fft_num_passes(int64_t N) {
   return fft_plan_passes(L, logR);
 }
 
-// out = FFT(in) in arithmetic T; in / out are complex128 (f64 = 1) or
-// complex64.  Intermediate passes alternate between the scratch vectors buf
-// and buf2 (N cplx<T> each; buf2 is used only with three or more passes), so
+// out = FFT(in) in arithmetic T for `batch` signals of N elements each
+// (signal-major); in / out are complex128 (f64 = 1) or complex64.  Intermediate passes alternate between the scratch vectors buf
+// and buf2 (batch x N cplx<T> each; buf2 is used only with three or more passes), so
 // they keep T precision and never touch `out`.  `in` is only read.
 template <class T>
 int fft_run(const void* in, int in_f64, void* out, int out_f64, cplx<T>* buf, cplx<T>* buf2,
-            int64_t N, int sign, const cplx<T>* tw, cudaStream_t st) {
+            int64_t N, int batch, int sign, const cplx<T>* tw, cudaStream_t st) {
   int L = 0;
   while ((int64_t(1) << L) < N) ++L;
   int logR[8];
@@ -187,8 +190,8 @@ int fft_run(const void* in, int in_f64, void* out, int out_f64, cplx<T>* buf, cp
     if (J < 1) J = 1;
     size_t smem = (size_t)(R * J + R / 2) * sizeof(cplx<T>);
     unsigned grid = (unsigned)((N >> logR[i]) / J);
-    k_fft_pass<T><<<grid, 256, smem, st>>>(src, src_f64, dst, dst_f64, N, logR[i], Ns, J, sign,
-                                           tw, b);
+    k_fft_pass<T><<<dim3(grid, (unsigned)batch), 256, smem, st>>>(src, src_f64, dst, dst_f64, N,
+                                                                  logR[i], Ns, J, sign, tw, b);
     src = dst;
     src_f64 = dst_f64;
     Ns <<= logR[i];
@@ -207,7 +210,7 @@ int fft_configure() {
   return NUFFT_OK;
 }
 
-template int fft_run<double>(const void*, int, void*, int, double2*, double2*, int64_t, int,
+template int fft_run<double>(const void*, int, void*, int, double2*, double2*, int64_t, int, int,
                              const double2*, cudaStream_t);
-template int fft_run<float>(const void*, int, void*, int, float2*, float2*, int64_t, int,
+template int fft_run<float>(const void*, int, void*, int, float2*, float2*, int64_t, int, int,
                             const float2*, cudaStream_t);

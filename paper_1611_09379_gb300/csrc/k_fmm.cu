@@ -31,6 +31,8 @@ __global__ void k_p2m_uniform(TreeDims d, const cplx<T>* __restrict__ q,
   int64_t B = int64_t(1) << d.L;
   int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (tid >= B * d.pm) return;
+  q += blockIdx.y * d.N;
+  mleaf += blockIdx.y * d.mstride;
   int64_t b = tid / d.pm;
   int m = (int)(tid - b * d.pm);
   const cplx<T>* qb = q + b * d.s;
@@ -71,6 +73,8 @@ __global__ void __launch_bounds__(128) k_p2m_nonuniform(TreeDims d,
   int64_t B = int64_t(1) << d.L;
   int64_t b = blockIdx.x * WPB + warp;
   if (b >= B) return;
+  charge += blockIdx.y * d.M_;
+  mleaf += blockIdx.y * d.mstride;
   int32_t a = start[b], e = start[b + 1];
   const int N = (int)d.N;
   for (int mc = 0; mc < d.pm; mc += 32) {
@@ -143,6 +147,7 @@ __global__ void __launch_bounds__(512) k_up_sub(TreeDims d, int lb, int lt, cons
   const int depth = lb - lt;
   cplx<T>* nxt = cur + (pm << depth);
   for (int i = threadIdx.x; i < 2 * pm * pm; i += blockDim.x) A[i] = op[i];
+  mexp += blockIdx.y * d.mstride;
   const int64_t b0 = (int64_t)blockIdx.x << depth;  // first box at level lb
   const cplx<T>* src = mexp + (level_off(lb) + b0) * pm;
   for (int i = threadIdx.x; i < (pm << depth); i += blockDim.x) cur[i] = src[i];
@@ -172,6 +177,7 @@ __global__ void __launch_bounds__(512) k_up_top(TreeDims d, int lb, const T* __r
   cplx<T>* cur = reinterpret_cast<cplx<T>*>(A + 2 * pm * pm);  // [2^lb * pm]
   cplx<T>* nxt = cur + (pm << lb);                             // [2^(lb-1) * pm]
   for (int i = threadIdx.x; i < 2 * pm * pm; i += blockDim.x) A[i] = op[i];
+  mexp += blockIdx.y * d.mstride;
   const cplx<T>* src = mexp + level_off(lb) * pm;
   for (int i = threadIdx.x; i < (pm << lb); i += blockDim.x) cur[i] = src[i];
   __syncthreads();
@@ -252,6 +258,8 @@ __global__ void __launch_bounds__(512) k_down_top(TreeDims d, int lt, const T* _
   cplx<T>* Lb = La + nmax * p;                               // [nmax * p]
   for (int i = threadIdx.x; i < 4 * p * p; i += blockDim.x) Tm[i] = op_m2l[i];
   for (int i = threadIdx.x; i < 2 * p * p; i += blockDim.x) Tl[i] = op_l2l[i];
+  mexp += blockIdx.y * d.mstride;
+  lexp += blockIdx.y * d.lstride;
   cplx<T>* par = La;
   cplx<T>* cur = Lb;
   for (int l = 3; l <= lt; ++l) {
@@ -298,6 +306,8 @@ __global__ void __launch_bounds__(512) k_down_sub(TreeDims d, int lt, int lb,
   cplx<T>* Lb = La + (p << depth);                           // [2^depth * p]
   for (int i = threadIdx.x; i < 4 * p * p; i += blockDim.x) Tm[i] = op_m2l[i];
   for (int i = threadIdx.x; i < 2 * p * p; i += blockDim.x) Tl[i] = op_l2l[i];
+  mexp += blockIdx.y * d.mstride;
+  lexp += blockIdx.y * d.lstride;
   // root local expansion
   const cplx<T>* lroot = lexp + (level_off(lt) - 4 + blockIdx.x) * (int64_t)p;
   for (int i = threadIdx.x; i < p; i += blockDim.x) La[i] = lroot[i];
@@ -348,7 +358,9 @@ __global__ void k_level2(TreeDims d, int nq, const double* __restrict__ op, doub
                          float2* __restrict__ outf) {
   __shared__ double2 mu[4][66];
   __shared__ double2 A1[4][66];
-  const cplx<T>* m2 = mexp;  // level 2 sits at offset 0
+  const cplx<T>* m2 = mexp + blockIdx.x * d.mstride;  // level 2 sits at offset 0
+  out += blockIdx.x * (4 * nq + 1);
+  if (outf) outf += blockIdx.x * (4 * nq + 1);
   for (int e = threadIdx.x; e < 4 * nq; e += blockDim.x) {
     int a = e / nq, i = e - a * nq;
     double2 v = to_d2(m2[a * d.pm + i]);
@@ -471,14 +483,17 @@ template <> struct NearAcc<float> {
 
 // ---------------------------------------------------------------- forward targets
 
-// One thread per sorted target j (Eq. p4, p5, p20):
+// One thread per sorted target j and group of G signals (Eq. p4, p5, p20):
 //   g_j = E_j f_{k0} - (F_j/2) (Q + i h'_j),
 //   h'_j = (N/pi) [ (1/s) sum_n L_n u^n + sum_{near, k != k0} f_k / t ]
 //          - (2/pi) sum_l D^(arc)_l uhat^l
 // where the pair (y_j, x_k0) enters through E_j (its singular 2/t part in
 // closed form) and through Q and the regular polynomial like every source.
-// All arithmetic in T (F_j, E_j were formed in FP64 at plan time).
-template <class T, class VO>
+// The near-field reciprocals 1/t depend on the points only and are shared by
+// the G signals.  All arithmetic in T (F_j, E_j were formed in FP64 at plan
+// time).  Signal g of the group: blockIdx.y * G + g; per-signal strides N
+// (grid), M (output), d.lstride (locals), 4 (2q) + 1 (level-2 coefficients).
+template <class T, class VO, int G>
 __global__ void __launch_bounds__(256) k_targets_fwd(
     TreeDims d, int M, const int32_t* __restrict__ k0s, const double* __restrict__ dels,
     const int32_t* __restrict__ perm, const cplx<T>* __restrict__ F,
@@ -488,20 +503,16 @@ __global__ void __launch_bounds__(256) k_targets_fwd(
   if (j >= M) return;
   const int N = (int)d.N;
   const int s = d.s;
+  const int sig0 = blockIdx.y * G;
+  fgrid += (int64_t)sig0 * N;
   int k0 = k0s[j];
   double dl = dels[j];
   int b, o;
   point_local(k0, dl, N, s, &b, &o);
   const T dt = (T)dl;
-  // far field (local expansion of the leaf)
-  cplx<T> far = mk<T>(0, 0);
-  if (d.L >= 3) {
-    T u = ((T)o + dt) * (T)(1.0 / s) - (T)0.5;
-    far = horner<T>(lexp + ((int64_t)(level_off(d.L) - 4) + b) * d.p, d.p, u);
-  }
   // near field: leaves b-1, b, b+1 (periodic, unwrapped displacement); the
   // pair with the nearest grid point (D = 0) is masked, E_j carries it
-  NearAcc<T> acc;
+  NearAcc<T> acc[G];
   const int B = 1 << d.L;
   for (int nb = -1; nb <= 1; ++nb) {
     const cplx<T>* q = fgrid + (int64_t)((b + nb + B) & (B - 1)) * s;
@@ -512,40 +523,56 @@ __global__ void __launch_bounds__(256) k_targets_fwd(
       for (int u = 0; u < cn; ++u) {
         const int D = D0 - c0 - u;
         T r = rcp_t(int_to_t(D, T()) + dt);
-        acc.add_r(q[c0 + u], D == 0 ? (T)0 : r);
+        r = D == 0 ? (T)0 : r;
+#pragma unroll
+        for (int gg = 0; gg < G; ++gg) acc[gg].add_r(q[(int64_t)gg * N + c0 + u], r);
       }
-      acc.fold();
+#pragma unroll
+      for (int gg = 0; gg < G; ++gg) acc[gg].fold();
     }
   }
-  cplx<T> nr = acc.get();
   const int base = b * s;
-  // regular part, arc n = b >> (L-2), uhat = (y - x_c)/pi
   const int Q2 = 2 * d.q;  // cot kernel: degree 2q-1
-  int arc = b >> (d.L - 2);
-  int I = base + o - arc * (N >> 2) - (N >> 3);
-  T uh = ((T)I + dt) * (T)(2.0 / (double)N);
-  cplx<T> reg = horner<T>(lvl2 + arc * Q2, Q2, uh);
-  cplx<T> Qs = lvl2[4 * Q2];
+  const int arc = b >> (d.L - 2);
+  const int I = base + o - arc * (N >> 2) - (N >> 3);
+  const T uh = ((T)I + dt) * (T)(2.0 / (double)N);
+  const T u = ((T)o + dt) * (T)(1.0 / s) - (T)0.5;
   const T cN = (T)((double)N * kInvPi), ts = (T)(1.0 / s), c2 = (T)(2.0 * kInvPi);
-  T hr = cN * fma(far.x, ts, nr.x) - c2 * reg.x;
-  T hi = cN * fma(far.y, ts, nr.y) - c2 * reg.y;
-  // g = E f_k0 - (F/2)(Q + i h')
-  cplx<T> w = mk<T>(Qs.x - hi, Qs.y + hr);
-  cplx<T> res = cscale(cmul(F[j], w), (T)-0.5);
-  res = cadd(res, cmul(E[j], fgrid[k0]));
-  store_out<VO>(g + perm[j], to_d2(res));
+  const cplx<T> Fj = F[j], Ej = E[j];
+  const int pj = perm[j];
+#pragma unroll
+  for (int gg = 0; gg < G; ++gg) {
+    const int sig = sig0 + gg;
+    cplx<T> far = mk<T>(0, 0);
+    if (d.L >= 3)
+      far = horner<T>(lexp + sig * d.lstride + ((int64_t)(level_off(d.L) - 4) + b) * d.p, d.p, u);
+    const cplx<T>* l2 = lvl2 + (int64_t)sig * (4 * Q2 + 1);
+    cplx<T> reg = horner<T>(l2 + arc * Q2, Q2, uh);
+    cplx<T> Qs = l2[4 * Q2];
+    cplx<T> nr = acc[gg].get();
+    T hr = cN * fma(far.x, ts, nr.x) - c2 * reg.x;
+    T hi = cN * fma(far.y, ts, nr.y) - c2 * reg.y;
+    // g = E f_k0 - (F/2)(Q + i h')
+    cplx<T> w = mk<T>(Qs.x - hi, Qs.y + hr);
+    cplx<T> res = cscale(cmul(Fj, w), (T)-0.5);
+    res = cadd(res, cmul(Ej, fgrid[(int64_t)gg * N + k0]));
+    store_out<VO>(g + (int64_t)sig * M + pj, to_d2(res));
+  }
 }
 
 // ---------------------------------------------------------------- adjoint / inverse targets
 
 // Charges in sorted order: adjoint q_i = conj(F_i) g_perm(i);
 // inverse q_i = Dt_i g_perm(i) (Eq. p6: D_j g_j, scaled by e^{-Lambda}).
+// Signal blockIdx.y: samples and charges at stride M.
 template <class T, class VI>
 __global__ void k_charges(int64_t M, const int32_t* __restrict__ perm,
                           const double2* __restrict__ coef, int conj_coef,
                           const VI* __restrict__ gin, cplx<T>* __restrict__ charge) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= M) return;
+  gin += blockIdx.y * M;
+  charge += blockIdx.y * M;
   double2 c = coef[i];
   if (conj_coef) c.y = -c.y;
   double2 gv = to_d2(gin[perm[i]]);
@@ -553,8 +580,8 @@ __global__ void k_charges(int64_t M, const int32_t* __restrict__ perm,
 }
 
 // The pair (y_j, x_k0) of each source j with its nearest grid point, one
-// thread per sorted source (uniform work, so the FP64 arithmetic of the
-// inverse does not diverge inside a warp):
+// thread per sorted source and signal (uniform work, so the FP64 arithmetic
+// of the inverse does not diverge inside a warp):
 //   adjoint: conj(E_j) g_j, the closed form of the pair's 2/t part (and
 //            conj(F_j) G(x_k0 - y_j) -> 1 at an exact hit);
 //   inverse: the pair's 2/t part times the target factor,
@@ -569,6 +596,9 @@ __global__ void k_self_terms(int M, int inverse, int N, const int32_t* __restric
                              cplx<T>* __restrict__ st) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= M) return;
+  gin += (int64_t)blockIdx.y * M;
+  charge += (int64_t)blockIdx.y * M;
+  st += (int64_t)blockIdx.y * M;
   if (!inverse) {
     st[i] = cmul(cconj(E[i]), from_d2<T>(to_d2(gin[perm[i]])));
     return;
@@ -585,75 +615,52 @@ __global__ void k_self_terms(int M, int inverse, int N, const int32_t* __restric
   st[i] = from_d2<T>(v);
 }
 
-// One thread per grid point k (Eq. p4 transposed, Eq. p6):
-//   h_k = sum_j q_j cot((x_k - y_j)/2)   by the same FMM, then
-//   adjoint: u_k   = -(Q + i h'_k)/2 + sum_{j: k0_j = k} st_j
-//   inverse: f_k/N = Ct_k (-(Q + i h'_k)/2) + sum_{j: k0_j = k} st_j
-// where h' leaves out the 2/t part of the pairs with k0_j = k (their st_j
-// terms above); Ct_k = C_k e^Lambda / N carries the 1/N of Eq. p1.  All
-// arithmetic in T (Ct in FP32 for the mixed path).  dl_t: delta in T.
-// Packed source record for the adjoint / inverse near field: grid index k0,
-// offset delta and charge q in one 16-byte (FP32) or 32-byte (FP64) load.
-template <class T> struct SrcRec;
-template <> struct SrcRec<float> { float4 v; };
-template <> struct SrcRec<double> { double4_32a v; };
+// Packed source position for the adjoint / inverse near field: grid index k0
+// and offset delta in one 8-byte (FP32) or 16-byte (FP64) load, shared by all
+// signals.
+template <class T> struct SrcPos;
+template <> struct SrcPos<float> { int k0; float dl; };
+template <> struct SrcPos<double> { long long k0; double dl; };
 
 template <class T>
-__device__ inline void rec_unpack(const SrcRec<T>& r, int* k0, T* dl, cplx<T>* q);
-template <>
-__device__ inline void rec_unpack<float>(const SrcRec<float>& r, int* k0, float* dl, float2* q) {
-  *k0 = __float_as_int(r.v.x);
-  *dl = r.v.y;
-  *q = make_float2(r.v.z, r.v.w);
-}
-template <>
-__device__ inline void rec_unpack<double>(const SrcRec<double>& r, int* k0, double* dl,
-                                          double2* q) {
-  *k0 = (int)__double_as_longlong(r.v.x);
-  *dl = r.v.y;
-  *q = make_double2(r.v.z, r.v.w);
-}
-
-template <class T>
-__global__ void k_pack_sources(int M, const int32_t* __restrict__ k0s, const double* __restrict__ dels,
-                               const cplx<T>* __restrict__ charge, SrcRec<T>* __restrict__ rec) {
+__global__ void k_pack_positions(int M, const int32_t* __restrict__ k0s,
+                                 const double* __restrict__ dels, SrcPos<T>* __restrict__ pos) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= M) return;
-  cplx<T> q = charge[i];
-  SrcRec<T> r;
-  if constexpr (sizeof(T) == 4)
-    r.v = make_float4(__int_as_float(k0s[i]), (float)dels[i], q.x, q.y);
-  else
-    r.v = make_double4_32a(__longlong_as_double((long long)k0s[i]), dels[i], q.x, q.y);
-  rec[i] = r;
+  SrcPos<T> r;
+  r.k0 = k0s[i];
+  r.dl = (T)dels[i];
+  pos[i] = r;
 }
 
-// One thread per grid point k (Eq. p4 transposed, Eq. p6):
+// One thread per grid point k and group of G signals (Eq. p4 transposed, Eq. p6):
 //   h_k = sum_j q_j cot((x_k - y_j)/2)   by the same FMM, then
 //   adjoint: u_k   = -(Q + i h'_k)/2 + sum_{j: k0_j = k} st_j
 //   inverse: f_k/N = Ct_k (-(Q + i h'_k)/2) + sum_{j: k0_j = k} st_j
 // where h' leaves out the 2/t part of the pairs with k0_j = k (their st_j
-// terms above); Ct_k = C_k e^Lambda / N carries the 1/N of Eq. p1.  All
-// arithmetic in T (Ct in FP32 for the mixed path).
-template <class T>
+// terms above); Ct_k = C_k e^Lambda / N carries the 1/N of Eq. p1.  The
+// reciprocals 1/t are shared by the G signals.  All arithmetic in T (Ct in
+// FP32 for the mixed path).
+template <class T, int G>
 __global__ void __launch_bounds__(256) k_targets_grid(
     TreeDims d, int inverse, const int32_t* __restrict__ start,
-    const SrcRec<T>* __restrict__ rec, const cplx<T>* __restrict__ st,
-    const cplx<T>* __restrict__ lexp, const cplx<T>* __restrict__ lvl2,
-    const T* __restrict__ Ct, cplx<T>* __restrict__ out) {
+    const SrcPos<T>* __restrict__ pos, const cplx<T>* __restrict__ charge,
+    const cplx<T>* __restrict__ st, const cplx<T>* __restrict__ lexp,
+    const cplx<T>* __restrict__ lvl2, const T* __restrict__ Ct, cplx<T>* __restrict__ out) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   const int N = (int)d.N;
   if (k >= N) return;
+  const int64_t M = d.M_;
+  const int sig0 = blockIdx.y * G;
+  charge += sig0 * M;
+  st += sig0 * M;
   const int s = d.s;
   const int B = 1 << d.L;
   int b = k / s, o = k - b * s;
-  cplx<T> far = mk<T>(0, 0);
-  if (d.L >= 3) {
-    T u = (T)o * (T)(1.0 / s) - (T)0.5;
-    far = horner<T>(lexp + ((int64_t)(level_off(d.L) - 4) + b) * d.p, d.p, u);
-  }
-  NearAcc<T> acc;
-  cplx<T> self = mk<T>(0, 0);
+  NearAcc<T> acc[G];
+  cplx<T> self[G];
+#pragma unroll
+  for (int gg = 0; gg < G; ++gg) self[gg] = mk<T>(0, 0);
   for (int nb = -1; nb <= 1; ++nb) {
     int bb = (b + nb + B) & (B - 1);
     int a = start[bb], e = start[bb + 1];
@@ -662,34 +669,47 @@ __global__ void __launch_bounds__(256) k_targets_grid(
     const int D0 = o - nb * s, sub = bb * s;
     int cnt = 0;
     for (int i = a; i < e; ++i) {
-      int k0;
-      T dl;
-      cplx<T> q;
-      rec_unpack<T>(rec[i], &k0, &dl, &q);
-      int D = D0 - ((k0 - sub) & (N - 1));
-      T r = rcp_t(int_to_t(D, T()) - dl);
+      const SrcPos<T> ps = pos[i];
+      int D = D0 - (((int)ps.k0 - sub) & (N - 1));
+      T r = rcp_t(int_to_t(D, T()) - ps.dl);
       if (D == 0) {
-        self = cadd(self, st[i]);
+#pragma unroll
+        for (int gg = 0; gg < G; ++gg) self[gg] = cadd(self[gg], st[gg * M + i]);
         r = (T)0;
       }
-      acc.add_r(q, r);
-      if (++cnt == 16) { acc.fold(); cnt = 0; }
+#pragma unroll
+      for (int gg = 0; gg < G; ++gg) acc[gg].add_r(charge[gg * M + i], r);
+      if (++cnt == 16) {
+#pragma unroll
+        for (int gg = 0; gg < G; ++gg) acc[gg].fold();
+        cnt = 0;
+      }
     }
-    acc.fold();
+#pragma unroll
+    for (int gg = 0; gg < G; ++gg) acc[gg].fold();
   }
-  cplx<T> nr = acc.get();
   const int Q2 = 2 * d.q;
-  int arc = b >> (d.L - 2);
-  int I = k - arc * (N >> 2) - (N >> 3);
-  T uh = (T)I * (T)(2.0 / (double)N);
-  cplx<T> reg = horner<T>(lvl2 + arc * Q2, Q2, uh);
-  cplx<T> Qs = lvl2[4 * Q2];
+  const int arc = b >> (d.L - 2);
+  const int I = k - arc * (N >> 2) - (N >> 3);
+  const T uh = (T)I * (T)(2.0 / (double)N);
+  const T u = (T)o * (T)(1.0 / s) - (T)0.5;
   const T cN = (T)((double)N * kInvPi), ts = (T)(1.0 / s), c2 = (T)(2.0 * kInvPi);
-  T hr = cN * fma(far.x, ts, nr.x) - c2 * reg.x;
-  T hi = cN * fma(far.y, ts, nr.y) - c2 * reg.y;
-  cplx<T> res = mk<T>((T)-0.5 * (Qs.x - hi), (T)-0.5 * (Qs.y + hr));
-  if (inverse) res = cscale(res, Ct[k]);
-  out[k] = cadd(res, self);
+#pragma unroll
+  for (int gg = 0; gg < G; ++gg) {
+    const int sig = sig0 + gg;
+    cplx<T> far = mk<T>(0, 0);
+    if (d.L >= 3)
+      far = horner<T>(lexp + sig * d.lstride + ((int64_t)(level_off(d.L) - 4) + b) * d.p, d.p, u);
+    const cplx<T>* l2 = lvl2 + (int64_t)sig * (4 * Q2 + 1);
+    cplx<T> reg = horner<T>(l2 + arc * Q2, Q2, uh);
+    cplx<T> Qs = l2[4 * Q2];
+    cplx<T> nr = acc[gg].get();
+    T hr = cN * fma(far.x, ts, nr.x) - c2 * reg.x;
+    T hi = cN * fma(far.y, ts, nr.y) - c2 * reg.y;
+    cplx<T> res = mk<T>((T)-0.5 * (Qs.x - hi), (T)-0.5 * (Qs.y + hr));
+    if (inverse) res = cscale(res, Ct[k]);
+    out[(int64_t)sig * N + k] = cadd(res, self[gg]);
+  }
 }
 
 }  // namespace nufft
@@ -732,25 +752,36 @@ int fmm_configure() {
   return NUFFT_OK;
 }
 
+TreeDims dims_of(const nufft_plan_s* pl) {
+  TreeDims d{pl->N, pl->L, pl->s, pl->p, pl->q, pl->pm};
+  d.mstride = ((int64_t(2) << pl->L) - 4) * pl->pm;
+  int64_t nl = (int64_t(2) << pl->L) - 8;
+  d.lstride = (nl > 0 ? nl : 1) * pl->p;
+  d.M_ = pl->M;
+  return d;
+}
+
 // Upward pass + far field + level-2 coefficients for charges already laid out
-// (uniform: on the grid, `charge` = the grid samples; non-uniform: sorted).
+// (uniform: on the grid, `charge` = the grid samples; non-uniform: sorted);
+// all signals of the plan at once (grid y = signal).
 template <class T>
 int fmm_upward_downward(nufft_plan_s* pl, const FmmOps& ops, bool uniform_sources,
                         const cplx<T>* charge, double2* lvl2, float2* lvl2f) {
   cudaStream_t st = pl->stream;
-  TreeDims d{pl->N, pl->L, pl->s, pl->p, pl->q, pl->pm};
+  const TreeDims d = dims_of(pl);
+  const unsigned nsig = (unsigned)pl->batch;
   int64_t B = pl->B;
   cplx<T>* mexp = (cplx<T>*)pl->mexp;
   cplx<T>* lexp = (cplx<T>*)pl->lexp;
   cplx<T>* mleaf = mexp + level_off(pl->L) * pl->pm;
   prof_begin(pl, NUFFT_STAGE_P2M);
   if (uniform_sources) {
-    k_p2m_uniform<T><<<nblk(B * pl->pm, 256), 256, 0, st>>>(d, charge, (const T*)pl->op_p2m,
-                                                           mleaf);
+    k_p2m_uniform<T><<<dim3(nblk(B * pl->pm, 256), nsig), 256, 0, st>>>(
+        d, charge, (const T*)pl->op_p2m, mleaf);
   } else {
     constexpr int WPB = P2mWarps<T>::value;
-    k_p2m_nonuniform<T><<<nblk(B, WPB), 32 * WPB, 0, st>>>(d, pl->leaf_start, pl->k0, pl->delta,
-                                                           charge, mleaf);
+    k_p2m_nonuniform<T><<<dim3(nblk(B, WPB), nsig), 32 * WPB, 0, st>>>(
+        d, pl->leaf_start, pl->k0, pl->delta, charge, mleaf);
   }
   if (ops.leaf_shift)
     k_leaf_shift<T><<<nblk(B * pl->pm, 256), 256, 0, st>>>(B, pl->pm, ops.leaf_shift, mleaf);
@@ -764,19 +795,19 @@ int fmm_upward_downward(nufft_plan_s* pl, const FmmOps& ops, bool uniform_source
     int dep = kSubDepth;
     while (dep > 1 && up_sub_smem<T>(pm, dep) > kSmemBudget) --dep;
     int lt = lev - dep > kTopLevel ? lev - dep : kTopLevel;
-    k_up_sub<T><<<1u << lt, 512, up_sub_smem<T>(pm, lev - lt), st>>>(d, lev, lt,
-                                                                     (const T*)pl->op_m2m, mexp);
+    k_up_sub<T><<<dim3(1u << lt, nsig), 512, up_sub_smem<T>(pm, lev - lt), st>>>(
+        d, lev, lt, (const T*)pl->op_m2m, mexp);
     ++nl;
     lev = lt;
   }
   if (lev > 2) {
     size_t sm = (size_t)2 * pm * pm * sizeof(T) + (size_t)3 * ((size_t)pm << lev) / 2 * sizeof(cplx<T>);
-    k_up_top<T><<<1, 512, sm, st>>>(d, lev, (const T*)pl->op_m2m, mexp);
+    k_up_top<T><<<dim3(1, nsig), 512, sm, st>>>(d, lev, (const T*)pl->op_m2m, mexp);
     ++nl;
   }
   prof_end(pl, nl);
   prof_begin(pl, NUFFT_STAGE_LEVEL2);
-  k_level2<T><<<1, 256, 0, st>>>(d, ops.nq, ops.reg, ops.c1, ops.c2, mexp, lvl2, lvl2f);
+  k_level2<T><<<nsig, 256, 0, st>>>(d, ops.nq, ops.reg, ops.c1, ops.c2, mexp, lvl2, lvl2f);
   prof_end(pl, 1);
   // downward: levels 3..kTopLevel in one CTA, then subtrees; the chunks are
   // cut from the finest level up so the costly fine levels get the most CTAs
@@ -791,7 +822,7 @@ int fmm_upward_downward(nufft_plan_s* pl, const FmmOps& ops, bool uniform_source
     };
     while (top > 3 && top_smem(top) > kSmemBudget) --top;
     size_t smt = top_smem(top);
-    k_down_top<T><<<1, 512, smt, st>>>(
+    k_down_top<T><<<dim3(1, nsig), 512, smt, st>>>(
         d, top, (const T*)ops.m2l, (const T*)ops.l2l, mexp, lexp, ops.log_kernel, log2N);
     ++nl;
     int dep = kSubDepth;
@@ -801,7 +832,7 @@ int fmm_upward_downward(nufft_plan_s* pl, const FmmOps& ops, bool uniform_source
     int lt = top;
     for (int c = nc - 1; c >= 0; --c) {
       int lb = cuts[c];
-      k_down_sub<T><<<1u << lt, 512, down_sub_smem<T>(p, lb - lt), st>>>(
+      k_down_sub<T><<<dim3(1u << lt, nsig), 512, down_sub_smem<T>(p, lb - lt), st>>>(
           d, lt, lb, (const T*)ops.m2l, (const T*)ops.l2l, mexp, lexp, ops.log_kernel, log2N);
       ++nl;
       lt = lb;
@@ -825,75 +856,87 @@ template <class T> struct PlanT;
 template <> struct PlanT<double> {
   static const double2* F(nufft_plan_s* pl) { return pl->F; }
   static const double2* E(nufft_plan_s* pl) { return pl->E; }
-  static const double* dl(nufft_plan_s* pl) { return pl->delta; }
   static const double2* lvl2(nufft_plan_s* pl) { return pl->lvl2; }
   static const double* Ct(nufft_plan_s* pl) { return pl->Ct; }
 };
 template <> struct PlanT<float> {
   static const float2* F(nufft_plan_s* pl) { return pl->Ff; }
   static const float2* E(nufft_plan_s* pl) { return pl->Ef; }
-  static const float* dl(nufft_plan_s* pl) { return pl->delta_f; }
   static const float2* lvl2(nufft_plan_s* pl) { return pl->lvl2f; }
   static const float* Ct(nufft_plan_s* pl) { return pl->Ctf; }
 };
 
-// forward: grid samples f (cplx<T>, in pl->grid) -> g (original order)
+template <class T, class VO, int G>
+static void launch_targets_fwd(nufft_plan_s* pl, const TreeDims& d, const cplx<T>* f, void* g) {
+  dim3 grid(nblk(pl->M, 256), (unsigned)(pl->batch / G));
+  k_targets_fwd<T, VO, G><<<grid, 256, 0, pl->stream>>>(
+      d, (int)pl->M, pl->k0, pl->delta, pl->perm, PlanT<T>::F(pl), PlanT<T>::E(pl), f,
+      (const cplx<T>*)pl->lexp, PlanT<T>::lvl2(pl), (VO*)g);
+}
+
+// forward: grid samples f (cplx<T>, in pl->grid, [batch][N]) -> g ([batch][M], original order)
 template <class T>
 int fmm_forward(nufft_plan_s* pl, void* g) {
   const cplx<T>* f = (const cplx<T>*)pl->grid;
   int rc = fmm_upward_downward<T>(pl, cot_ops(pl), true, f, pl->lvl2,
                                   sizeof(T) == 4 ? pl->lvl2f : nullptr);
   if (rc) return rc;
-  TreeDims d{pl->N, pl->L, pl->s, pl->p, pl->q, pl->pm};
-  const cplx<T>* lexp = (const cplx<T>*)pl->lexp;
+  const TreeDims d = dims_of(pl);
+  const bool g4 = (pl->batch % 4) == 0;
   prof_begin(pl, NUFFT_STAGE_TARGETS);
-  if (pl->flags & NUFFT_IO_C64)
-    k_targets_fwd<T, float2><<<nblk(pl->M, 256), 256, 0, pl->stream>>>(
-        d, (int)pl->M, pl->k0, pl->delta, pl->perm, PlanT<T>::F(pl), PlanT<T>::E(pl), f, lexp,
-        PlanT<T>::lvl2(pl), (float2*)g);
-  else
-    k_targets_fwd<T, double2><<<nblk(pl->M, 256), 256, 0, pl->stream>>>(
-        d, (int)pl->M, pl->k0, pl->delta, pl->perm, PlanT<T>::F(pl), PlanT<T>::E(pl), f, lexp,
-        PlanT<T>::lvl2(pl), (double2*)g);
+  if (pl->flags & NUFFT_IO_C64) {
+    if (g4) launch_targets_fwd<T, float2, 4>(pl, d, f, g);
+    else launch_targets_fwd<T, float2, 1>(pl, d, f, g);
+  } else {
+    if (g4) launch_targets_fwd<T, double2, 4>(pl, d, f, g);
+    else launch_targets_fwd<T, double2, 1>(pl, d, f, g);
+  }
   prof_end(pl, 1);
   return cudaGetLastError() == cudaSuccess ? NUFFT_OK : NUFFT_ECUDA;
 }
 
-// adjoint / inverse: samples g (original order) -> values on the grid
-// (cplx<T>, in pl->grid)
+// adjoint / inverse: samples g ([batch][M], original order) -> values on the
+// grid (cplx<T>, in pl->grid, [batch][N])
 template <class T>
 int fmm_to_grid(nufft_plan_s* pl, const void* g, int inverse) {
   cudaStream_t st = pl->stream;
   bool c64 = (pl->flags & NUFFT_IO_C64) != 0;
   const double2* coef = inverse ? pl->Dt : pl->F;
   cplx<T>* charge = (cplx<T>*)pl->charge;
+  const unsigned nsig = (unsigned)pl->batch;
+  const dim3 gm(nblk(pl->M, 256), nsig);
   prof_begin(pl, NUFFT_STAGE_P2M);
   if (c64)
-    k_charges<T, float2><<<nblk(pl->M, 256), 256, 0, st>>>(pl->M, pl->perm, coef, !inverse,
-                                                          (const float2*)g, charge);
+    k_charges<T, float2><<<gm, 256, 0, st>>>(pl->M, pl->perm, coef, !inverse, (const float2*)g,
+                                            charge);
   else
-    k_charges<T, double2><<<nblk(pl->M, 256), 256, 0, st>>>(pl->M, pl->perm, coef, !inverse,
-                                                           (const double2*)g, charge);
+    k_charges<T, double2><<<gm, 256, 0, st>>>(pl->M, pl->perm, coef, !inverse, (const double2*)g,
+                                             charge);
   prof_end(pl, 1);
   int rc = fmm_upward_downward<T>(pl, cot_ops(pl), false, charge, pl->lvl2,
                                   sizeof(T) == 4 ? pl->lvl2f : nullptr);
   if (rc) return rc;
-  TreeDims d{pl->N, pl->L, pl->s, pl->p, pl->q, pl->pm};
-  cplx<T>* st_ = (cplx<T>*)pl->selft;
+  const TreeDims d = dims_of(pl);
+  cplx<T>* stt = (cplx<T>*)pl->selft;
+  SrcPos<T>* pos = (SrcPos<T>*)pl->srcpos;
   prof_begin(pl, NUFFT_STAGE_TARGETS);
   if (c64)
-    k_self_terms<T, float2><<<nblk(pl->M, 256), 256, 0, st>>>(
-        (int)pl->M, inverse, (int)pl->N, pl->k0, pl->delta, pl->perm, PlanT<T>::E(pl), charge,
-        (const float2*)g, pl->Ct, st_);
+    k_self_terms<T, float2><<<gm, 256, 0, st>>>((int)pl->M, inverse, (int)pl->N, pl->k0,
+                                               pl->delta, pl->perm, PlanT<T>::E(pl), charge,
+                                               (const float2*)g, pl->Ct, stt);
   else
-    k_self_terms<T, double2><<<nblk(pl->M, 256), 256, 0, st>>>(
-        (int)pl->M, inverse, (int)pl->N, pl->k0, pl->delta, pl->perm, PlanT<T>::E(pl), charge,
-        (const double2*)g, pl->Ct, st_);
-  SrcRec<T>* rec = (SrcRec<T>*)pl->srcrec;
-  k_pack_sources<T><<<nblk(pl->M, 256), 256, 0, st>>>((int)pl->M, pl->k0, pl->delta, charge, rec);
-  k_targets_grid<T><<<nblk(pl->N, 256), 256, 0, st>>>(
-      d, inverse, pl->leaf_start, rec, st_, (const cplx<T>*)pl->lexp, PlanT<T>::lvl2(pl),
-      PlanT<T>::Ct(pl), (cplx<T>*)pl->grid);
+    k_self_terms<T, double2><<<gm, 256, 0, st>>>((int)pl->M, inverse, (int)pl->N, pl->k0,
+                                                pl->delta, pl->perm, PlanT<T>::E(pl), charge,
+                                                (const double2*)g, pl->Ct, stt);
+  k_pack_positions<T><<<nblk(pl->M, 256), 256, 0, st>>>((int)pl->M, pl->k0, pl->delta, pos);
+  if (pl->batch % 4 == 0)
+    k_targets_grid<T, 4><<<dim3(nblk(pl->N, 256), nsig / 4), 256, 0, st>>>(
+        d, inverse, pl->leaf_start, pos, charge, stt, (const cplx<T>*)pl->lexp,
+        PlanT<T>::lvl2(pl), PlanT<T>::Ct(pl), (cplx<T>*)pl->grid);
+  else
+    k_targets_grid<T, 1><<<dim3(nblk(pl->N, 256), nsig), 256, 0, st>>>(
+        d, inverse, pl->leaf_start, pos, charge, stt, (const cplx<T>*)pl->lexp,
+        PlanT<T>::lvl2(pl), PlanT<T>::Ct(pl), (cplx<T>*)pl->grid);
   prof_end(pl, 3);
   return cudaGetLastError() == cudaSuccess ? NUFFT_OK : NUFFT_ECUDA;
 }

@@ -117,7 +117,7 @@ int dot(nufft_plan_s* pl, const double2* a, const double2* b, int64_t n, double2
 extern "C" int nufft_plan_solve_lsq(nufft_plan pl, const void* g, const float* w, double tol,
                                     int maxit, void* c, int* iters, double* resid) {
   if (!pl || !g || !c || maxit < 1 || !(tol > 0.0)) return NUFFT_EINVAL;
-  if (pl->flags & NUFFT_IO_C64) return NUFFT_ENOTSUP;
+  if ((pl->flags & NUFFT_IO_C64) || pl->batch != 1) return NUFFT_ENOTSUP;
   const int64_t N = pl->N, M = pl->M;
   cudaStream_t st = pl->stream;
   // work vectors, created on first use and kept by the plan

@@ -20,7 +20,7 @@ int fft_configure();
 int fft_num_passes(int64_t N);
 template <class T>
 int fft_run(const void* in, int in_f64, void* out, int out_f64, cplx<T>* buf, cplx<T>* buf2,
-            int64_t N, int sign, const cplx<T>* tw, cudaStream_t st);
+            int64_t N, int batch, int sign, const cplx<T>* tw, cudaStream_t st);
 template <class T> int fmm_configure();
 template <class T> int fmm_forward(nufft_plan_s* pl, void* g);
 template <class T> int fmm_to_grid(nufft_plan_s* pl, const void* g, int inverse);
@@ -188,7 +188,7 @@ int build_operators(nufft_plan_s* pl) {
 
 void free_plan(nufft_plan_s* pl) {
   void* ptrs[] = {pl->perm, pl->leaf_start, pl->k0, pl->delta, pl->F, pl->E, pl->delta_f,
-                  pl->Ff, pl->Ef, pl->lvl2f, pl->Dt, pl->Ct, pl->Ctf, pl->selft, pl->srcrec, pl->Lambda, pl->mexp, pl->lexp,
+                  pl->Ff, pl->Ef, pl->lvl2f, pl->Dt, pl->Ct, pl->Ctf, pl->selft, pl->srcpos, pl->Lambda, pl->mexp, pl->lexp,
                   pl->charge, pl->grid, pl->grid2, pl->grid3, pl->lvl2, pl->op_m2m, pl->op_m2l,
                   pl->op_l2l, pl->op_p2m, pl->op_reg, pl->fft_tw, pl->fft_tw_f, pl->status,
                   pl->seg_overflow, pl->lsq_work};
@@ -309,9 +309,12 @@ int nufft_choose_params(int64_t N, int64_t M, double eps, int prec, nufft_params
     if (p < 4) p = 4;
   }
   if (q < 2 || q > 32 || p < 4 || p > 64) return NUFFT_EINVAL;
+  int batch = prm->batch <= 0 ? 1 : prm->batch;
+  if (batch > 4096) return NUFFT_EINVAL;
   prm->lmax = L;
   prm->p = p;
   prm->q = q;
+  prm->batch = batch;
   return NUFFT_OK;
 }
 
@@ -319,11 +322,12 @@ int nufft_plan_create(nufft_plan* out, int64_t N, int64_t M, const double* y, do
                       int prec, const nufft_params* params, unsigned flags, void* stream) {
   if (!out || !y) return NUFFT_EINVAL;
   *out = nullptr;
-  nufft_params prm{0, 0, 0};
+  nufft_params prm{0, 0, 0, 0};
   if (params) prm = *params;
   int rc = nufft_choose_params(N, M, eps, prec, &prm);
   if (rc) return rc;
   if ((flags & NUFFT_WANT_INVERSE) && M != N) return NUFFT_EINVAL;
+  const int64_t nb = prm.batch;
   if ((rc = configure_once())) return rc;
   nufft_plan_s* pl = new (std::nothrow) nufft_plan_s();
   if (!pl) return NUFFT_ENOMEM;
@@ -331,7 +335,7 @@ int nufft_plan_create(nufft_plan* out, int64_t N, int64_t M, const double* y, do
   if (!pl->prof) { delete pl; return NUFFT_ENOMEM; }
   pl->N = N; pl->M = M; pl->L = prm.lmax; pl->B = 1 << prm.lmax; pl->s = (int)(N >> prm.lmax);
   pl->p = prm.p; pl->q = prm.q; pl->pm = prm.p > 2 * prm.q + 1 ? prm.p : 2 * prm.q + 1;
-  pl->prec = prec; pl->flags = flags; pl->eps = eps;
+  pl->prec = prec; pl->flags = flags; pl->eps = eps; pl->batch = (int)nb;
   pl->stream = (cudaStream_t)stream;
   const int64_t B = pl->B;
   const size_t csz = prec == NUFFT_FP64 ? sizeof(double2) : sizeof(float2);
@@ -340,20 +344,20 @@ int nufft_plan_create(nufft_plan* out, int64_t N, int64_t M, const double* y, do
   if ((rc = dalloc(&pl->perm, M * 4)) || (rc = dalloc(&pl->leaf_start, (B + 1) * 4)) ||
       (rc = dalloc(&pl->k0, M * 4)) || (rc = dalloc(&pl->delta, M * 8)) ||
       (rc = dalloc(&pl->F, M * 16)) || (rc = dalloc(&pl->E, M * 16)) ||
-      (rc = dalloc(&pl->mexp, nm * pl->pm * csz)) ||
-      (rc = dalloc(&pl->lexp, (nl > 0 ? nl : 1) * pl->p * csz)) ||
-      (rc = dalloc(&pl->charge, big * csz)) || (rc = dalloc(&pl->selft, M * csz)) ||
-      (rc = dalloc(&pl->srcrec, M * 2 * csz)) ||
-      (rc = dalloc(&pl->grid, N * 16)) ||
-      (rc = dalloc(&pl->grid2, N * 16)) || (rc = dalloc(&pl->lvl2, (8 * pl->q + 1) * 16)) ||
+      (rc = dalloc(&pl->mexp, nb * nm * pl->pm * csz)) ||
+      (rc = dalloc(&pl->lexp, nb * (nl > 0 ? nl : 1) * pl->p * csz)) ||
+      (rc = dalloc(&pl->charge, nb * big * csz)) || (rc = dalloc(&pl->selft, nb * M * csz)) ||
+      (rc = dalloc(&pl->srcpos, M * csz)) ||
+      (rc = dalloc(&pl->grid, nb * N * 16)) ||
+      (rc = dalloc(&pl->grid2, nb * N * 16)) || (rc = dalloc(&pl->lvl2, nb * (8 * pl->q + 1) * 16)) ||
       (rc = dalloc(&pl->fft_tw, fft_table_elems(N) * 16)) || (rc = dalloc(&pl->status, 16))) {
     free_plan(pl);
     return rc;
   }
-  if (fft_num_passes(N) >= 3 && (rc = dalloc(&pl->grid3, N * 16))) { free_plan(pl); return rc; }
+  if (fft_num_passes(N) >= 3 && (rc = dalloc(&pl->grid3, nb * N * 16))) { free_plan(pl); return rc; }
   if (prec == NUFFT_MIXED &&
       ((rc = dalloc(&pl->delta_f, M * 4)) || (rc = dalloc(&pl->Ff, M * 8)) ||
-       (rc = dalloc(&pl->Ef, M * 8)) || (rc = dalloc(&pl->lvl2f, (8 * pl->q + 1) * 8)) ||
+       (rc = dalloc(&pl->Ef, M * 8)) || (rc = dalloc(&pl->lvl2f, nb * (8 * pl->q + 1) * 8)) ||
        (rc = dalloc(&pl->fft_tw_f, fft_table_elems(N) * 8)))) {
     free_plan(pl);
     return rc;
@@ -442,11 +446,11 @@ static int fft_plan(nufft_plan_s* pl, const void* in, int in_f64, void* out, int
   prof_begin(pl, NUFFT_STAGE_FFT);
   int rc;
   if (pl->prec == NUFFT_FP64)
-    rc = fft_run<double>(in, in_f64, out, out_f64, pl->grid2, pl->grid3, pl->N, sign,
+    rc = fft_run<double>(in, in_f64, out, out_f64, pl->grid2, pl->grid3, pl->N, pl->batch, sign,
                          pl->fft_tw, pl->stream);
   else
     rc = fft_run<float>(in, in_f64, out, out_f64, (float2*)pl->grid2, (float2*)pl->grid3, pl->N,
-                        sign, pl->fft_tw_f, pl->stream);
+                        pl->batch, sign, pl->fft_tw_f, pl->stream);
   prof_end(pl, fft_num_passes(pl->N));
   return rc;
 }
