@@ -325,11 +325,78 @@ def run_ours(args):
         "gpu_launches": launches,
         "clocks": mx["clocks"],
     }
+    if not args.no_batched:
+        out["batched"] = run_batched()
     if args.lsq:
         out["inufft_lsq"] = run_lsq()
     print(json.dumps(out))
     if ws > 1:
         dist.destroy_process_group()
+
+
+def _timed(fn, flush, stream, steps, warmup):
+    import torch
+    for _ in range(warmup):
+        fn()
+    ms = []
+    for _ in range(steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    return sum(ms) / len(ms)
+
+
+def run_batched(steps: int = 5, warmup: int = 3):
+    """Batched workloads (configs[2]), eps = 1e-6, mixed precision, complex64:
+    (i) 64 signals sharing one uniform point set, N = M = 2^18, one batched
+    forward; (ii) 256 independent forward transforms, N = M = 2^U with U
+    uniform in {10..16}, own uniform points each, one CUDA graph launch."""
+    import torch
+
+    import paper_1611_09379_gb300 as nf
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    out = {}
+    N = M = 1 << 18
+    B = 64
+    y = workloads.points("uniform", M, seed=1234)
+    rng = workloads.rng(5)
+    C = (rng.standard_normal((B, N)) + 1j * rng.standard_normal((B, N))).astype(np.complex64)
+    plan = nf.Plan(N, torch.from_numpy(y).cuda(), eps=1e-6, prec=nf.MIXED, io="c64", batch=B)
+    Cd = torch.from_numpy(C).cuda()
+    G = torch.empty((B, M), dtype=torch.complex64, device="cuda")
+    ms = _timed(lambda: plan.forward(Cd, out=G), flush, stream, steps, warmup)
+    acc = None
+    try:
+        import oracle
+        idx = workloads.sample_index(M, 256)
+        Gh = G.cpu().numpy()
+        acc = max(oracle.rel_l2(Gh[b][idx], oracle.nudft_fwd(C[b].astype(complex), y, idx)) for b in (0, 31, 63))
+    except Exception as e:
+        acc = repr(e)
+    out["signals64"] = {"N": N, "M": M, "batch": B, "ms": ms, "value": B * M / (ms / 1e3),
+                        "unit": "points/s", "params": plan.info(), "fwd_rel_l2_sampled_max": acc}
+    plan.close()
+    U = workloads.rng(6).integers(10, 17, size=256)
+    Ns = [1 << int(u) for u in U]
+    ys = [torch.from_numpy(workloads.points("uniform", n, seed=1000 + i)).cuda() for i, n in enumerate(Ns)]
+    cs = [torch.from_numpy(workloads.coeffs(n, seed=2000 + i).astype(np.complex64)).cuda()
+          for i, n in enumerate(Ns)]
+    gs = [torch.empty(n, dtype=torch.complex64, device="cuda") for n in Ns]
+    t0 = time.perf_counter()
+    multi = nf.Multi(Ns, ys, eps=1e-6, prec=nf.MIXED, io="c64")
+    t_plan = time.perf_counter() - t0
+    ms = _timed(lambda: multi.forward(cs, gs), flush, stream, steps, warmup)
+    out["uneven256"] = {"count": 256, "points": int(sum(Ns)), "ms": ms,
+                        "value": sum(Ns) / (ms / 1e3), "unit": "points/s", "plan_s": t_plan,
+                        "launch": "one CUDA graph (16 forked streams)"}
+    multi.close()
+    return out
 
 
 def run_lsq(maxit: int = 60000):
@@ -428,6 +495,7 @@ def main():
     ap.add_argument("--lsq", action="store_true",
                     help="also run the least-squares INUFFT, learned vs plain CG (~2.5 min)")
     ap.add_argument("--lsq-only", action="store_true", help="only the least-squares comparison")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched workloads")
     args = ap.parse_args()
     if args.lsq_only:
         print(json.dumps({"inufft_lsq": run_lsq()}))

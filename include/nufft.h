@@ -257,6 +257,26 @@ int nufft_plan_profile(nufft_plan plan, int enable);
  * stream.  Launch counts are kept even when timing is disabled. */
 int nufft_plan_stats(nufft_plan plan, double *stage_ms, int64_t *launches);
 
+/* ---------------------------------------------------------------- uneven batches */
+
+/* Many independent forward transforms of uneven sizes, each with its own grid
+ * size N[i], point count M[i] and points y[i] ([device] double[M[i]]), run as
+ * one CUDA graph launch: every transform's kernel chain is captured on one of
+ * several forked streams (independent transforms overlap) and the
+ * instantiated graph is replayed while the caller's buffers stay the same.
+ * The paper treats one transform at a time; this groups many.
+ * nufft_multi_create builds one plan per transform (same eps, prec, flags;
+ * NUFFT_WANT_INVERSE not supported) and synchronises the stream.
+ * nufft_multi_exec_fwd: c[i] [device] N[i] coefficients, g[i] [device] M[i]
+ * outputs; captures a new graph when the pointers differ from the previous
+ * call's, then launches it on the stream (asynchronous). */
+typedef struct nufft_multi_s *nufft_multi;
+int nufft_multi_create(nufft_multi *out, int count, const int64_t *N, const int64_t *M,
+                       const double *const *y, double eps, int prec, unsigned flags,
+                       void *stream);
+int nufft_multi_exec_fwd(nufft_multi multi, const void *const *c, void *const *g);
+int nufft_multi_destroy(nufft_multi multi);
+
 /* ---------------------------------------------------------------- one-shot */
 
 /* Plan + exec + destroy in one call, with the paper's argument order

@@ -42,7 +42,8 @@ SYMBOLS = [
     "nufft_fwd_noalloc", "nufft_plan_solve_lsq", "nufft_plan_dcf_features",
     "nufft_dcf_features_sorted", "nufft_dcf_targets", "nufft_mlp_create", "nufft_mlp_destroy",
     "nufft_mlp_num_params", "nufft_mlp_set_params", "nufft_mlp_get_params", "nufft_mlp_infer",
-    "nufft_mlp_grad", "nufft_mlp_train_step",
+    "nufft_mlp_grad", "nufft_mlp_train_step", "nufft_multi_create", "nufft_multi_exec_fwd",
+    "nufft_multi_destroy",
 ]
 
 
@@ -65,6 +66,10 @@ _lib.nufft_plan_info.argtypes = [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTE
 _lib.nufft_plan_set_stream.argtypes = [_P, _P]
 _lib.nufft_plan_points.argtypes = [_P, _P, _P, _P, _P]
 _lib.nufft_plan_profile.argtypes = [_P, ctypes.c_int]
+_lib.nufft_multi_create.argtypes = [ctypes.POINTER(_P), ctypes.c_int, _P, _P, _P, ctypes.c_double,
+                                    ctypes.c_int, ctypes.c_uint, _P]
+_lib.nufft_multi_exec_fwd.argtypes = [_P, _P, _P]
+_lib.nufft_multi_destroy.argtypes = [_P]
 _lib.nufft_plan_dcf_features.argtypes = [_P, _P]
 _lib.nufft_dcf_features_sorted.argtypes = [_P, _I64, _I64, _P, _P]
 _lib.nufft_dcf_targets.argtypes = [_P, _I64, _I64, _I64, ctypes.c_int, _P, _P]
@@ -419,6 +424,50 @@ class MLP:
     def close(self):
         if getattr(self, "_h", None):
             _lib.nufft_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Multi:
+    """Independent forward transforms of uneven sizes run as one CUDA graph launch.
+
+    ys: list of CUDA float64 point tensors; Ns: grid sizes.  forward(cs, gs)
+    takes lists of coefficient / output tensors (captures a graph the first
+    time and whenever the tensors change, then replays it)."""
+
+    def __init__(self, Ns, ys, eps: float = 1e-6, prec: int = MIXED, io: str = "c64", stream=None):
+        import numpy as np
+        torch = _torch()
+        self.Ns = [int(n) for n in Ns]
+        self.Ms = [int(y.numel()) for y in ys]
+        self._ys = list(ys)  # kept alive for the call
+        self.cdtype = torch.complex64 if io == "c64" else torch.complex128
+        n = len(self.Ns)
+        Na = np.array(self.Ns, dtype=np.int64)
+        Ma = np.array(self.Ms, dtype=np.int64)
+        yp = (ctypes.c_void_p * n)(*[_dev_ptr(y, torch.float64, m, "y").value for y, m in zip(ys, self.Ms)])
+        h = _P()
+        _check(_lib.nufft_multi_create(ctypes.byref(h), n, Na.ctypes.data_as(_P), Ma.ctypes.data_as(_P),
+                                       ctypes.cast(yp, _P), eps, prec, IO_C64 if io == "c64" else 0,
+                                       _stream_handle(stream)), "nufft_multi_create")
+        self._h = h
+
+    def forward(self, cs, gs):
+        n = len(self.Ns)
+        cp = (ctypes.c_void_p * n)(*[_dev_ptr(c, self.cdtype, N, "c").value for c, N in zip(cs, self.Ns)])
+        gp = (ctypes.c_void_p * n)(*[_dev_ptr(g, self.cdtype, M, "g").value for g, M in zip(gs, self.Ms)])
+        _check(_lib.nufft_multi_exec_fwd(self._h, ctypes.cast(cp, _P), ctypes.cast(gp, _P)),
+               "nufft_multi_exec_fwd")
+        return gs
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.nufft_multi_destroy(self._h)
             self._h = None
 
     def __del__(self):
