@@ -75,13 +75,20 @@ typedef struct nufft_plan_s *nufft_plan;
  *         both from Eq. 18.2 with the fraction read as 10/(3 pi eps)
  *   batch: number of signals sharing the point set (default 1); exec calls
  *         then take [batch][N] coefficients and [batch][M] samples
+ *   tc_level: first tree level whose M2L + L2L (Sec. 2.1) runs as a dense
+ *         GEMM on the tensor cores (three TF32 passes, FP32 accumulation;
+ *         NUFFT_MIXED with p <= 28 only); coarser levels use the FP32 SIMT
+ *         kernels.  0 = automatic (the finest levels holding at least 2048
+ *         parent boxes over all signals), -1 = never.  Reported back as -1
+ *         when no level qualifies.
  * Constraints: 2 <= lmax <= log2 N, 4 <= p <= 64, 2 <= q <= 32,
- * batch <= 4096. */
+ * batch <= 4096, tc_level -1, 0 or in [4, 30]. */
 typedef struct {
   int lmax;
   int p;
   int q;
   int batch;
+  int tc_level;
 } nufft_params;
 
 /* ---------------------------------------------------------------- host only */
@@ -97,6 +104,48 @@ int nufft_version(void);
  * invalid N, M, eps or prec.  eps must lie in [1e-15, 1e-1]. */
 int nufft_choose_params(int64_t N, int64_t M, double eps, int prec,
                         nufft_params *params);
+
+/* ---------------------------------------------------------------- autotuner */
+
+/* Exec calls an autotuning run times together (bit mask). */
+#define NUFFT_OP_FWD 0x1u  /* nufft_plan_exec_fwd */
+#define NUFFT_OP_ADJ 0x2u  /* nufft_plan_exec_adj */
+#define NUFFT_OP_INV 0x4u  /* nufft_plan_exec_inv (needs M == N) */
+
+/* One candidate of an autotuning run. */
+typedef struct {
+  nufft_params params;  /* resolved parameters of the candidate */
+  double ms;            /* median time of one pass of the exec sequence */
+  double err;           /* relative L2 difference to the FP64 reference */
+  int accepted;         /* 1 for the returned choice */
+} nufft_tune_trial;
+
+/* Empirical choice of lmax, p, q and tc_level for one point set (no
+ * counterpart in the paper, which fixes lmax by the cost balance of Eq.
+ * 23-25 with l* = 5 and p, q by the error bound of Eq. 18.2).  Times the
+ * exec sequence `ops` (NUFFT_OP_* mask) on probe data for 10 to 40 candidate
+ * parameter sets, each through a plan of its own, and returns the fastest
+ * whose result lies within max(eps / 4, 1.5 x the formula parameters' error)
+ * of the FP64 FMM at eps = 1e-15 (relative L2 over all outputs).  Search:
+ * lmax in {l0 - 1, l0, l0 + 1}; p lowered in steps of 2 and q in steps of 1
+ * while accurate; for NUFFT_MIXED every tc_level from max(4, lmax - 9) to
+ * lmax and -1.
+ *   N, M, y [device], eps, prec, flags (0 or NUFFT_IO_C64), batch: as for
+ *          nufft_plan_create (y is read during the call only)
+ *   ops    NUFFT_OP_FWD | NUFFT_OP_ADJ | NUFFT_OP_INV (INV needs M == N)
+ *   reps   timed repetitions per candidate (>= 1; one untimed run first)
+ *   best   [host] receives the chosen parameters (pass them to
+ *          nufft_plan_create)
+ *   trials [host] optional log of up to max_trials candidates in the order
+ *          tried; n_trials [host, optional] receives the number tried
+ * Synchronous on `stream`; allocates probe and reference buffers of
+ * (batch x max(N, M)) complex values for the duration of the call.  Errors:
+ * as nufft_plan_create (EILLCOND for an inverse on duplicate points), EINVAL
+ * for a bad ops mask / reps / batch. */
+int nufft_autotune(int64_t N, int64_t M, const double *y, double eps, int prec,
+                   unsigned flags, int batch, unsigned ops, int reps,
+                   nufft_params *best, nufft_tune_trial *trials, int max_trials,
+                   int *n_trials, void *stream);
 
 /* ---------------------------------------------------------------- plans */
 
@@ -124,6 +173,15 @@ int nufft_plan_destroy(nufft_plan plan);
 
 /* Report the parameters in use (any output pointer may be NULL). */
 int nufft_plan_info(nufft_plan plan, int *lmax, int *p, int *q);
+
+/* All parameters of the plan (the resolved nufft_params).  out [host]. */
+int nufft_plan_params(nufft_plan plan, nufft_params *out);
+
+/* Wait for the plan's stream and read its device status word: returns
+ * NUFFT_ETIMEOUT if a kernel's bounded wait on the tensor cores gave up since
+ * the last call (its outputs are then invalid; the word is cleared), else
+ * NUFFT_OK.  Exec calls never block, so they cannot report this themselves. */
+int nufft_plan_sync(nufft_plan plan);
 
 /* Copy the plan's binned point set (the stable counting sort of Sec. 2.1)
  * into caller buffers, for inspection and tests.  Any pointer may be NULL.

@@ -35,7 +35,8 @@ WANT_INVERSE = 0x2
 # every symbol declared in include/nufft.h
 SYMBOLS = [
     "nufft_strerror", "nufft_version", "nufft_choose_params", "nufft_plan_create",
-    "nufft_plan_destroy", "nufft_plan_info", "nufft_plan_points", "nufft_plan_inverse_coeffs",
+    "nufft_plan_destroy", "nufft_plan_info", "nufft_plan_params", "nufft_plan_sync",
+    "nufft_plan_points", "nufft_plan_inverse_coeffs",
     "nufft_plan_set_stream", "nufft_plan_profile", "nufft_plan_stats",
     "nufft_plan_exec_fwd",
     "nufft_plan_exec_adj", "nufft_plan_exec_inv", "nufft_fwd", "nufft_adj", "inufft",
@@ -43,14 +44,21 @@ SYMBOLS = [
     "nufft_dcf_features_sorted", "nufft_dcf_targets", "nufft_mlp_create", "nufft_mlp_destroy",
     "nufft_mlp_num_params", "nufft_mlp_set_params", "nufft_mlp_get_params", "nufft_mlp_infer",
     "nufft_mlp_grad", "nufft_mlp_train_step", "nufft_multi_create", "nufft_multi_exec_fwd",
-    "nufft_multi_destroy",
+    "nufft_multi_destroy", "nufft_autotune",
 ]
 
 
 class Params(ctypes.Structure):
     _fields_ = [("lmax", ctypes.c_int), ("p", ctypes.c_int), ("q", ctypes.c_int),
-                ("batch", ctypes.c_int)]
+                ("batch", ctypes.c_int), ("tc_level", ctypes.c_int)]
 
+
+class TuneTrial(ctypes.Structure):
+    _fields_ = [("params", Params), ("ms", ctypes.c_double), ("err", ctypes.c_double),
+                ("accepted", ctypes.c_int)]
+
+
+OP_FWD, OP_ADJ, OP_INV = 0x1, 0x2, 0x4
 
 _P = ctypes.c_void_p
 _I64 = ctypes.c_int64
@@ -63,6 +71,8 @@ _lib.nufft_plan_create.argtypes = [ctypes.POINTER(_P), _I64, _I64, _P, ctypes.c_
 _lib.nufft_plan_destroy.argtypes = [_P]
 _lib.nufft_plan_info.argtypes = [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                  ctypes.POINTER(ctypes.c_int)]
+_lib.nufft_plan_params.argtypes = [_P, ctypes.POINTER(Params)]
+_lib.nufft_plan_sync.argtypes = [_P]
 _lib.nufft_plan_set_stream.argtypes = [_P, _P]
 _lib.nufft_plan_points.argtypes = [_P, _P, _P, _P, _P]
 _lib.nufft_plan_profile.argtypes = [_P, ctypes.c_int]
@@ -83,6 +93,10 @@ _lib.nufft_mlp_train_step.argtypes = [_P, _P, _P, _I64, ctypes.c_float, _P, _P]
 _lib.nufft_plan_solve_lsq.argtypes = [_P, _P, _P, ctypes.c_double, ctypes.c_int, _P,
                                       ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
 _lib.nufft_plan_stats.argtypes = [_P, _P, _P]
+_lib.nufft_autotune.argtypes = [_I64, _I64, _P, ctypes.c_double, ctypes.c_int, ctypes.c_uint,
+                                ctypes.c_int, ctypes.c_uint, ctypes.c_int, ctypes.POINTER(Params),
+                                ctypes.POINTER(TuneTrial), ctypes.c_int,
+                                ctypes.POINTER(ctypes.c_int), _P]
 _lib.nufft_plan_inverse_coeffs.argtypes = [_P, _P, _P, ctypes.POINTER(ctypes.c_double)]
 for _n in ("nufft_plan_exec_fwd", "nufft_plan_exec_adj", "nufft_plan_exec_inv"):
     getattr(_lib, _n).argtypes = [_P, _P, _P]
@@ -117,9 +131,17 @@ def version() -> int:
 
 def choose_params(N: int, M: int, eps: float, prec: int = FP64, lmax: int = 0, p: int = 0, q: int = 0):
     """(lmax, p, q) the library would use (host only, no GPU needed)."""
-    prm = Params(lmax, p, q, 1)
+    prm = Params(lmax, p, q, 1, 0)
     _check(_lib.nufft_choose_params(N, M, eps, prec, ctypes.byref(prm)), "nufft_choose_params")
     return prm.lmax, prm.p, prm.q
+
+
+def choose_params_full(N: int, M: int, eps: float, prec: int = FP64, lmax: int = 0, p: int = 0,
+                       q: int = 0, batch: int = 1, tc_level: int = 0) -> dict:
+    """Every resolved parameter (host only), as a dict."""
+    prm = Params(lmax, p, q, batch, tc_level)
+    _check(_lib.nufft_choose_params(N, M, eps, prec, ctypes.byref(prm)), "nufft_choose_params")
+    return {"lmax": prm.lmax, "p": prm.p, "q": prm.q, "batch": prm.batch, "tc_level": prm.tc_level}
 
 
 def _torch():
@@ -154,11 +176,13 @@ class Plan:
     inverse=True precomputes C_k, D_j for :meth:`inverse` (needs M == N).
     lmax / p / q override the automatic parameters (0 = automatic).
     batch: signals sharing the points; exec calls take [batch, N] / [batch, M].
+    tc_level: first tree level whose M2L runs on the tensor cores (MIXED only;
+    0 = automatic, -1 = never).
     """
 
     def __init__(self, N: int, y, eps: float = 1e-12, prec: int = FP64, io: str = "c128",
                  inverse: bool = False, lmax: int = 0, p: int = 0, q: int = 0, batch: int = 1,
-                 stream=None):
+                 tc_level: int = 0, stream=None):
         torch = _torch()
         self.N = int(N)
         self.M = int(y.numel())
@@ -169,7 +193,7 @@ class Plan:
         flags = (IO_C64 if io == "c64" else 0) | (WANT_INVERSE if inverse else 0)
         self._stream = stream
         h = _P()
-        prm = Params(lmax, p, q, self.batch)
+        prm = Params(lmax, p, q, self.batch, tc_level)
         yp = _dev_ptr(y, torch.float64, self.M, "y")
         _check(_lib.nufft_plan_create(ctypes.byref(h), self.N, self.M, yp, eps, prec,
                                       ctypes.byref(prm), flags, _stream_handle(stream)),
@@ -182,6 +206,18 @@ class Plan:
         _check(_lib.nufft_plan_info(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
                "nufft_plan_info")
         return {"lmax": a.value, "p": b.value, "q": c.value}
+
+    def params(self):
+        """Every resolved parameter of the plan (lmax, p, q, batch, tc_level)."""
+        prm = Params()
+        _check(_lib.nufft_plan_params(self._h, ctypes.byref(prm)), "nufft_plan_params")
+        return {"lmax": prm.lmax, "p": prm.p, "q": prm.q, "batch": prm.batch,
+                "tc_level": prm.tc_level}
+
+    def sync(self):
+        """Wait for the plan's stream; raises NufftError(ETIMEOUT) if a bounded
+        device wait gave up since the last call (outputs then invalid)."""
+        _check(_lib.nufft_plan_sync(self._h), "nufft_plan_sync")
 
     def points(self):
         """The binned point set: (perm, leaf_start, k0, delta) as CUDA tensors."""

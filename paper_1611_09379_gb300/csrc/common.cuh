@@ -68,6 +68,7 @@ enum DevStatus : int {
   kDevBadPoint = 1,     // y not finite or outside [0, 2 pi)
   kDevSegTooLarge = 2,  // a leaf held more points than the segment sort supports
   kDevIllCond = 4,      // duplicate points / exponent range in the inverse
+  kDevTimeout = 8,      // a bounded wait (tensor-core barrier) gave up
 };
 
 }  // namespace nufft
@@ -138,6 +139,8 @@ struct nufft_plan_s {
   void *op_l2l = nullptr;  // [2][p][p]    transposed: [sigma][n'][n]
   void *op_p2m = nullptr;  // [s][pm] powers rho_o^m of the uniform grid in a leaf
   double *op_reg = nullptr;// [2][2q][2q] level-2 weights W1, W2 (FP64)
+  float *op_tc = nullptr;  // tensor-core M2L + L2L operator (hi, lo), kernel layout
+  int tc_level = -1;       // first level on the tensor cores (-1: none)
   double2 *fft_tw = nullptr; // FFT twiddle tables
   float2 *fft_tw_f = nullptr;
   int fft_tw_lo_bits = 0;

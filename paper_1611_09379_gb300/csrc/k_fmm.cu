@@ -17,6 +17,8 @@
 //   L2L  parent -> child: L'_k = 1/2 sum_n C(n,k) 2^-k (sigma/4)^(n-k) L_n
 #include <cmath>
 
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace nufft {
@@ -737,6 +739,9 @@ static size_t down_sub_smem(int p, int depth) {
   return (size_t)6 * p * p * sizeof(T) + (nbx + 6 + 2 * nbx) * p * sizeof(cplx<T>);
 }
 
+int m2l_tc_level(const TreeDims& d, int l, int nsig, const float* bops, const float2* mexp,
+                 float2* lexp, int* status, cudaStream_t st);
+
 template <class T>
 int fmm_configure() {
   int big = 220 * 1024;
@@ -825,10 +830,15 @@ int fmm_upward_downward(nufft_plan_s* pl, const FmmOps& ops, bool uniform_source
     k_down_top<T><<<dim3(1, nsig), 512, smt, st>>>(
         d, top, (const T*)ops.m2l, (const T*)ops.l2l, mexp, lexp, ops.log_kernel, log2N);
     ++nl;
+    // levels lc..L as one tensor-core GEMM each (FP32 data, cot kernel only)
+    int lc = L + 1;
+    if constexpr (std::is_same<T, float>::value)
+      if (!ops.log_kernel && pl->op_tc && pl->tc_level >= 4 && pl->tc_level <= L)
+        lc = pl->tc_level > top + 1 ? pl->tc_level : top + 1;
     int dep = kSubDepth;
     while (dep > 1 && down_sub_smem<T>(p, dep) > kSmemBudget) --dep;
     int cuts[32], nc = 0;
-    for (int lb = L; lb > top; lb -= dep) cuts[nc++] = lb;
+    for (int lb = lc - 1; lb > top; lb -= dep) cuts[nc++] = lb;
     int lt = top;
     for (int c = nc - 1; c >= 0; --c) {
       int lb = cuts[c];
@@ -836,6 +846,14 @@ int fmm_upward_downward(nufft_plan_s* pl, const FmmOps& ops, bool uniform_source
           d, lt, lb, (const T*)ops.m2l, (const T*)ops.l2l, mexp, lexp, ops.log_kernel, log2N);
       ++nl;
       lt = lb;
+    }
+    if constexpr (std::is_same<T, float>::value) {
+      for (int l = lc; l <= L; ++l) {
+        int rc = m2l_tc_level(d, l, (int)nsig, pl->op_tc, (const float2*)mexp, (float2*)lexp,
+                              pl->status, st);
+        if (rc) return rc;
+        ++nl;
+      }
     }
   }
   prof_end(pl, nl);

@@ -22,6 +22,10 @@ template <class T>
 int fft_run(const void* in, int in_f64, void* out, int out_f64, cplx<T>* buf, cplx<T>* buf2,
             int64_t N, int batch, int sign, const cplx<T>* tw, cudaStream_t st);
 template <class T> int fmm_configure();
+bool m2l_tc_supported(int p);
+size_t m2l_tc_table_floats(int p);
+void m2l_tc_table(int p, const long double* m2l, const long double* l2l, float* out);
+int m2l_tc_configure();
 template <class T> int fmm_forward(nufft_plan_s* pl, void* g);
 template <class T> int fmm_to_grid(nufft_plan_s* pl, const void* g, int inverse);
 int inverse_precompute(nufft_plan_s* pl, void* tmp, size_t tmp_bytes);
@@ -77,6 +81,7 @@ int configure_once() {
   int rc = fft_configure();
   if (!rc) rc = fmm_configure<double>();
   if (!rc) rc = fmm_configure<float>();
+  if (!rc) rc = m2l_tc_configure();
   if (!rc) g_configured = 1;
   return rc;
 }
@@ -183,6 +188,11 @@ int build_operators(nufft_plan_s* pl) {
     if ((rc = upload(&pl->op_l2l, c.data(), c.size() * 4))) return rc;
     if ((rc = upload(&pl->op_p2m, d.data(), d.size() * 4))) return rc;
   }
+  if (pl->tc_level >= 4) {
+    std::vector<float> tc(m2l_tc_table_floats(p));
+    m2l_tc_table(p, m2l.data(), l2l.data(), tc.data());
+    if ((rc = upload((void**)&pl->op_tc, tc.data(), tc.size() * 4))) return rc;
+  }
   return upload((void**)&pl->op_reg, reg.data(), reg.size() * 8);
 }
 
@@ -191,7 +201,7 @@ void free_plan(nufft_plan_s* pl) {
                   pl->Ff, pl->Ef, pl->lvl2f, pl->Dt, pl->Ct, pl->Ctf, pl->selft, pl->srcpos, pl->Lambda, pl->mexp, pl->lexp,
                   pl->charge, pl->grid, pl->grid2, pl->grid3, pl->lvl2, pl->op_m2m, pl->op_m2l,
                   pl->op_l2l, pl->op_p2m, pl->op_reg, pl->fft_tw, pl->fft_tw_f, pl->status,
-                  pl->seg_overflow, pl->lsq_work};
+                  pl->seg_overflow, pl->lsq_work, pl->op_tc};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (pl->prof) {
@@ -311,10 +321,21 @@ int nufft_choose_params(int64_t N, int64_t M, double eps, int prec, nufft_params
   if (q < 2 || q > 32 || p < 4 || p > 64) return NUFFT_EINVAL;
   int batch = prm->batch <= 0 ? 1 : prm->batch;
   if (batch > 4096) return NUFFT_EINVAL;
+  int tc = prm->tc_level;
+  if (tc != -1 && tc != 0 && (tc < 4 || tc > 30)) return NUFFT_EINVAL;
+  if (prec != NUFFT_MIXED || !m2l_tc_supported(p)) tc = -1;
+  if (tc == 0) {
+    // finest levels with at least 2048 parents over all signals (32 tiles)
+    tc = -1;
+    for (int l = 6; l <= L; ++l)
+      if ((int64_t(1) << (l - 1)) * batch >= 2048) { tc = l; break; }
+  }
+  if (tc > L) tc = -1;
   prm->lmax = L;
   prm->p = p;
   prm->q = q;
   prm->batch = batch;
+  prm->tc_level = tc;
   return NUFFT_OK;
 }
 
@@ -322,7 +343,7 @@ int nufft_plan_create(nufft_plan* out, int64_t N, int64_t M, const double* y, do
                       int prec, const nufft_params* params, unsigned flags, void* stream) {
   if (!out || !y) return NUFFT_EINVAL;
   *out = nullptr;
-  nufft_params prm{0, 0, 0, 0};
+  nufft_params prm{0, 0, 0, 0, 0};
   if (params) prm = *params;
   int rc = nufft_choose_params(N, M, eps, prec, &prm);
   if (rc) return rc;
@@ -336,6 +357,7 @@ int nufft_plan_create(nufft_plan* out, int64_t N, int64_t M, const double* y, do
   pl->N = N; pl->M = M; pl->L = prm.lmax; pl->B = 1 << prm.lmax; pl->s = (int)(N >> prm.lmax);
   pl->p = prm.p; pl->q = prm.q; pl->pm = prm.p > 2 * prm.q + 1 ? prm.p : 2 * prm.q + 1;
   pl->prec = prec; pl->flags = flags; pl->eps = eps; pl->batch = (int)nb;
+  pl->tc_level = prm.tc_level;
   pl->stream = (cudaStream_t)stream;
   const int64_t B = pl->B;
   const size_t csz = prec == NUFFT_FP64 ? sizeof(double2) : sizeof(float2);
@@ -402,6 +424,33 @@ int nufft_plan_info(nufft_plan pl, int* lmax, int* p, int* q) {
   if (lmax) *lmax = pl->L;
   if (p) *p = pl->p;
   if (q) *q = pl->q;
+  return NUFFT_OK;
+}
+
+int nufft_plan_params(nufft_plan pl, nufft_params* out) {
+  if (!pl || !out) return NUFFT_EINVAL;
+  out->lmax = pl->L;
+  out->p = pl->p;
+  out->q = pl->q;
+  out->batch = pl->batch;
+  out->tc_level = pl->tc_level;
+  return NUFFT_OK;
+}
+
+int nufft_plan_sync(nufft_plan pl) {
+  if (!pl) return NUFFT_EINVAL;
+  cudaStream_t st = pl->stream;
+  int h = 0;
+  if (cudaMemcpyAsync(&h, pl->status, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return NUFFT_ECUDA;
+  if (h & kDevTimeout) {
+    const int keep = h & ~kDevTimeout;
+    if (cudaMemcpyAsync(pl->status, &keep, 4, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return NUFFT_ECUDA;
+    return NUFFT_ETIMEOUT;
+  }
   return NUFFT_OK;
 }
 

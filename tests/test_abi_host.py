@@ -92,3 +92,56 @@ def test_double_double_constants_are_exact(orc):
         s = Fraction(float(val[hi])) + Fraction(float(val[lo]))
         assert abs(s - exact) / exact < Fraction(1, 2 ** 104)
         assert float(val[hi]) == float(exact)
+
+
+def test_tc_level_choice(nf):
+    """Automatic first tensor-core level: the finest levels with >= 2048
+    parent boxes over all signals; FP64 plans and large p never use it."""
+    d = nf.choose_params_full(1 << 20, 1 << 20, 1e-6, nf.MIXED)
+    assert d["lmax"] == 15 and d["tc_level"] == 12
+    assert nf.choose_params_full(1 << 20, 1 << 20, 1e-12, nf.FP64)["tc_level"] == -1
+    b = nf.choose_params_full(1 << 18, 1 << 18, 1e-6, nf.MIXED, batch=64)
+    assert b["lmax"] == 13 and b["tc_level"] == 6
+    assert nf.choose_params_full(1 << 12, 1 << 12, 1e-6, nf.MIXED)["tc_level"] == -1  # lmax 7
+    assert nf.choose_params_full(1 << 20, 1 << 20, 1e-6, nf.MIXED, tc_level=-1)["tc_level"] == -1
+    assert nf.choose_params_full(1 << 20, 1 << 20, 1e-6, nf.MIXED, tc_level=9)["tc_level"] == 9
+    assert nf.choose_params_full(1 << 20, 1 << 20, 1e-6, nf.MIXED, tc_level=20)["tc_level"] == -1
+    # p above the kernel's limit (28): no tensor-core levels
+    assert nf.choose_params_full(1 << 20, 1 << 20, 1e-6, nf.MIXED, p=30)["tc_level"] == -1
+    for bad in (1, 2, 3, 31, -2):
+        with pytest.raises(nf.NufftError):
+            nf.choose_params_full(1 << 20, 1 << 20, 1e-6, nf.MIXED, tc_level=bad)
+
+
+def test_autotune_rejects_bad_arguments(nf):
+    """Argument checks come before any device work."""
+    import ctypes
+    best = nf.Params()
+    n = ctypes.c_int(0)
+    lib = nf._lib
+    # null points, empty op mask, unknown op bit, reps < 1, inverse with M != N
+    assert lib.nufft_autotune(1024, 1024, None, 1e-6, 1, 0, 1, 1, 3, ctypes.byref(best), None, 0,
+                              ctypes.byref(n), None) == nf.EINVAL
+    fake = ctypes.c_void_p(16)  # never dereferenced: the checks fail first
+    assert lib.nufft_autotune(1024, 1024, fake, 1e-6, 1, 0, 1, 0, 3, ctypes.byref(best), None, 0,
+                              None, None) == nf.EINVAL
+    assert lib.nufft_autotune(1024, 1024, fake, 1e-6, 1, 0, 1, 8, 3, ctypes.byref(best), None, 0,
+                              None, None) == nf.EINVAL
+    assert lib.nufft_autotune(1024, 1024, fake, 1e-6, 1, 0, 1, 1, 0, ctypes.byref(best), None, 0,
+                              None, None) == nf.EINVAL
+    assert lib.nufft_autotune(1024, 2048, fake, 1e-6, 1, 0, 1, 4, 3, ctypes.byref(best), None, 0,
+                              None, None) == nf.EINVAL
+    assert lib.nufft_autotune(1000, 1024, fake, 1e-6, 1, 0, 1, 1, 3, ctypes.byref(best), None, 0,
+                              None, None) == nf.EINVAL
+
+
+def test_tune_table_roundtrip(tmp_path):
+    from paper_1611_09379_gb300 import tune
+    assert tune.ops_mask("fwd+inv") == 5 and tune.ops_mask(("adj",)) == 2 and tune.ops_mask(3) == 3
+    k1 = tune.key(1 << 20, 1 << 20, 1e-6, 1, "c128", 1, "fwd+inv", "jitter")
+    k2 = tune.key(1 << 20, 1 << 20, 1e-6, 1, "c128", 1, "fwd", "jitter")
+    assert k1 != k2
+    path = str(tmp_path / "table.json")
+    assert tune.load_table(path) == {}
+    tune.save_table({k1: {"params": {"lmax": 15}}}, path)
+    assert tune.load_table(path)[k1]["params"]["lmax"] == 15
