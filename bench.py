@@ -153,6 +153,7 @@ def run_ours(args):
     import torch.distributed as dist
 
     import paper_1611_09379_gb300 as nf
+    from paper_1611_09379_gb300 import tune
 
     ws, rank, local = _dist()
     if ws > 1:
@@ -169,10 +170,25 @@ def run_ours(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
     results = {}
+    tuning = {}
     for tag, prec, eps in (("mixed", nf.MIXED, EPS_MIXED), ("fp64", nf.FP64, EPS_FP64)):
+        prm = {}
+        if not args.no_tune:
+            # empirical l_max, p, q, tc_level for this point set (outside the timing,
+            # like the plan: Sec. 3.3 separates setting up from evaluating)
+            ent = tune.autotune(N, yd, eps, prec=prec, ops="fwd+inv", reps=5, tag="jitter0.4")
+            prm = {k: ent["params"][k] for k in ("lmax", "p", "q", "tc_level")}
+            chosen = [t for t in ent["trials"] if t["accepted"]]
+            tuning[tag] = {"params": ent["params"], "seconds": ent["seconds"],
+                           "from_table": ent["from_table"],
+                           "formula_params": ent["trials"][0]["params"] if ent["trials"] else None,
+                           "formula_ms": ent["trials"][0]["ms"] if ent["trials"] else None,
+                           "tuned_ms": chosen[0]["ms"] if chosen else None,
+                           "tuned_err_vs_fp64_fmm": chosen[0]["err"] if chosen else None,
+                           "candidates": len(ent["trials"])}
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        plan = nf.Plan(N, yd, eps=eps, prec=prec, inverse=True)
+        plan = nf.Plan(N, yd, eps=eps, prec=prec, inverse=True, **prm)
         torch.cuda.synchronize(dev)
         t_plan = time.perf_counter() - t0
         g = torch.empty(M, dtype=torch.complex128, device=dev)
@@ -203,7 +219,7 @@ def run_ours(args):
         ms = [a.elapsed_time(b) for a, b in ev]
         stats = plan.stats()
         # accuracy on sampled targets (oracle definition), outside the timing
-        results[tag] = {"ms": ms, "stats": stats, "info": plan.info(), "t_plan_s": t_plan,
+        results[tag] = {"ms": ms, "stats": stats, "info": plan.params(), "t_plan_s": t_plan,
                         "clocks": clk.summary(), "g": g, "c2": c2}
         # e2e through the public API with host buffers (pinned), copies timed
         if tag == "mixed":
@@ -309,7 +325,9 @@ def run_ours(args):
         "config": {"workload": "forward + square inverse NUFFT, N=M=2^20, complex128, jittered y, "
                                "mixed eps=1e-6",
                    "N": N, "M": M, "eps": EPS_MIXED, "lmax": info["lmax"], "p": info["p"],
-                   "q": info["q"], "l2": "flushed (512 MiB write) between timed steps",
+                   "q": info["q"], "tc_level": info.get("tc_level"),
+                   "params": "autotuned (nufft_autotune)" if tuning else "Eq. 18.2 / 25 formulas",
+                   "l2": "flushed (512 MiB write) between timed steps",
                    "parallelism": "replicas" if ws > 1 else "1 gpu",
                    "plan_s": mx["t_plan_s"]},
         "stages_ms_per_step": {k: round(v, 5) for k, v in per.items()},
@@ -318,6 +336,7 @@ def run_ours(args):
                      {k: round(v[0] / steps, 5) for k, v in fp["stats"].items()},
                  "plan_s": fp["t_plan_s"]},
         "accuracy": acc,
+        "tuning": tuning or None,
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": {"value": ws * 2 * M / (e2e_ms / 1e3), "unit": "points/s",
@@ -326,7 +345,7 @@ def run_ours(args):
         "clocks": mx["clocks"],
     }
     if not args.no_batched:
-        out["batched"] = run_batched()
+        out["batched"] = run_batched(tune_params=not args.no_tune)
     if args.lsq:
         out["inufft_lsq"] = run_lsq()
     print(json.dumps(out))
@@ -351,7 +370,7 @@ def _timed(fn, flush, stream, steps, warmup):
     return sum(ms) / len(ms)
 
 
-def run_batched(steps: int = 5, warmup: int = 3):
+def run_batched(steps: int = 5, warmup: int = 3, tune_params: bool = True):
     """Batched workloads, eps = 1e-6, mixed precision, complex64:
     (i) 64 signals sharing one uniform point set, N = M = 2^18, one batched
     forward; (ii) 256 independent forward transforms, N = M = 2^U with U
@@ -367,10 +386,21 @@ def run_batched(steps: int = 5, warmup: int = 3):
     y = workloads.points("uniform", M, seed=1234)
     rng = workloads.rng(5)
     C = (rng.standard_normal((B, N)) + 1j * rng.standard_normal((B, N))).astype(np.complex64)
-    plan = nf.Plan(N, torch.from_numpy(y).cuda(), eps=1e-6, prec=nf.MIXED, io="c64", batch=B)
+    yd = torch.from_numpy(y).cuda()
+    prm, tuned = {}, None
+    if tune_params:
+        from paper_1611_09379_gb300 import tune
+        ent = tune.autotune(N, yd, 1e-6, prec=nf.MIXED, io="c64", batch=B, ops="fwd", reps=3,
+                            tag="uniform")
+        prm = {k: ent["params"][k] for k in ("lmax", "p", "q", "tc_level")}
+        tuned = {"seconds": ent["seconds"], "formula_ms": ent["trials"][0]["ms"],
+                 "formula_params": ent["trials"][0]["params"]}
+    plan = nf.Plan(N, yd, eps=1e-6, prec=nf.MIXED, io="c64", batch=B, **prm)
     Cd = torch.from_numpy(C).cuda()
     G = torch.empty((B, M), dtype=torch.complex64, device="cuda")
+    plan.profile(True)
     ms = _timed(lambda: plan.forward(Cd, out=G), flush, stream, steps, warmup)
+    stages = {k: round(v[0] / (steps + warmup), 5) for k, v in plan.stats().items()}
     acc = None
     try:
         import oracle
@@ -380,7 +410,8 @@ def run_batched(steps: int = 5, warmup: int = 3):
     except Exception as e:
         acc = repr(e)
     out["signals64"] = {"N": N, "M": M, "batch": B, "ms": ms, "value": B * M / (ms / 1e3),
-                        "unit": "points/s", "params": plan.info(), "fwd_rel_l2_sampled_max": acc}
+                        "unit": "points/s", "params": plan.params(), "tuning": tuned,
+                        "stages_ms": stages, "fwd_rel_l2_sampled_max": acc}
     plan.close()
     U = workloads.rng(6).integers(10, 17, size=256)
     Ns = [1 << int(u) for u in U]
@@ -496,6 +527,8 @@ def main():
                     help="also run the least-squares INUFFT, learned vs plain CG (~2.5 min)")
     ap.add_argument("--lsq-only", action="store_true", help="only the least-squares comparison")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched workloads")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="use the formula parameters (Eq. 18.2, 25) instead of the autotuner's")
     ap.add_argument("--batched-only", action="store_true",
                     help="only the batched workloads (steps / warmup as given)")
     args = ap.parse_args()
@@ -505,7 +538,7 @@ def main():
     if args.warmup < 3:
         args.warmup = 3
     if args.batched_only:
-        print(json.dumps({"batched": run_batched(args.steps, args.warmup)}))
+        print(json.dumps({"batched": run_batched(args.steps, args.warmup, not args.no_tune)}))
         return
     if args.impl == "reference":
         run_reference(args)

@@ -77,7 +77,7 @@ typedef struct nufft_plan_s *nufft_plan;
  *         then take [batch][N] coefficients and [batch][M] samples
  *   tc_level: first tree level whose M2L + L2L (Sec. 2.1) runs as a dense
  *         GEMM on the tensor cores (three TF32 passes, FP32 accumulation;
- *         NUFFT_MIXED with p <= 28 only); coarser levels use the FP32 SIMT
+ *         NUFFT_MIXED with p <= 24 only); coarser levels use the FP32 SIMT
  *         kernels.  0 = automatic (the finest levels holding at least 2048
  *         parent boxes over all signals), -1 = never.  Reported back as -1
  *         when no level qualifies.
@@ -116,7 +116,7 @@ int nufft_choose_params(int64_t N, int64_t M, double eps, int prec,
 typedef struct {
   nufft_params params;  /* resolved parameters of the candidate */
   double ms;            /* median time of one pass of the exec sequence */
-  double err;           /* relative L2 difference to the FP64 reference */
+  double err;           /* largest relative L2 error over the outputs */
   int accepted;         /* 1 for the returned choice */
 } nufft_tune_trial;
 
@@ -125,8 +125,10 @@ typedef struct {
  * 23-25 with l* = 5 and p, q by the error bound of Eq. 18.2).  Times the
  * exec sequence `ops` (NUFFT_OP_* mask) on probe data for 10 to 40 candidate
  * parameter sets, each through a plan of its own, and returns the fastest
- * whose result lies within max(eps / 4, 1.5 x the formula parameters' error)
- * of the FP64 FMM at eps = 1e-15 (relative L2 over all outputs).  Search:
+ * whose every output has a relative L2 error of at most max(eps / 4, 1.5 x
+ * the formula parameters' error): forward and adjoint against the FP64 FMM
+ * at eps = 1e-15, the inverse (when timed with the forward) as the round
+ * trip inv(fwd(c)) against the probe coefficients c.  Search:
  * lmax in {l0 - 1, l0, l0 + 1}; p lowered in steps of 2 and q in steps of 1
  * while accurate; for NUFFT_MIXED every tc_level from max(4, lmax - 9) to
  * lmax and -1.

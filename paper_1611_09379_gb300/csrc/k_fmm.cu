@@ -485,53 +485,116 @@ template <> struct NearAcc<float> {
 
 // ---------------------------------------------------------------- forward targets
 
+// Packed source position for the adjoint / inverse near field: grid index k0
+// and offset delta in one 8-byte (FP32) or 16-byte (FP64) load, shared by all
+// signals.
+template <class T> struct SrcPos;
+template <> struct SrcPos<float> { int k0; float dl; };
+template <> struct SrcPos<double> { long long k0; double dl; };
+
+// Targets per CTA and the capacity of the staged near-field windows.
+constexpr int kTgtThreads = 256;
+template <class T, int G> struct NearCap {
+  // forward: grid samples per signal; adjoint / inverse: sources per chunk
+  static constexpr int fwd = (sizeof(T) == 4 ? 2048 : 1024) / G;
+  static constexpr int grid = (sizeof(T) == 4 ? 1024 : 512) / G;
+  static constexpr size_t fwd_bytes = (size_t)fwd * G * sizeof(cplx<T>);
+  static constexpr size_t grid_bytes = (size_t)grid * (1 + 2 * G) * sizeof(cplx<T>);
+};
+
+// Near-field sum of one target over a staged window in chunks of 16 terms
+// folded into the compensated total (NearAcc).  `term(i, acc)` adds term i.
+template <class T, int G, class Term>
+__device__ inline void near_window(int lo, int hi, NearAcc<T>* acc, Term term) {
+  for (int i = lo; i < hi; i += 16) {
+    const int n = hi - i < 16 ? hi - i : 16;
+#pragma unroll
+    for (int u = 0; u < 16; ++u)
+      if (u < n) term(i + u);
+#pragma unroll
+    for (int gg = 0; gg < G; ++gg) acc[gg].fold();
+  }
+}
+
 // One thread per sorted target j and group of G signals (Eq. p4, p5, p20):
 //   g_j = E_j f_{k0} - (F_j/2) (Q + i h'_j),
 //   h'_j = (N/pi) [ (1/s) sum_n L_n u^n + sum_{near, k != k0} f_k / t ]
 //          - (2/pi) sum_l D^(arc)_l uhat^l
 // where the pair (y_j, x_k0) enters through E_j (its singular 2/t part in
 // closed form) and through Q and the regular polynomial like every source.
-// The near-field reciprocals 1/t depend on the points only and are shared by
-// the G signals.  All arithmetic in T (F_j, E_j were formed in FP64 at plan
+// Near field: the CTA's 256 targets (sorted, so in leaves bl..bh) draw on the
+// grid samples of leaves bl-1..bh+1, staged once in shared memory; a target
+// in leaf b reads the 3s samples of leaves b-1, b, b+1 from there, with
+// t = (D + delta), D = k0 - k an exact integer in T.  The reciprocals 1/t
+// depend on the points only and are shared by the G signals.  A CTA whose
+// window exceeds the capacity (sparse targets) reads the samples from global
+// memory instead.  All arithmetic in T (F_j, E_j were formed in FP64 at plan
 // time).  Signal g of the group: blockIdx.y * G + g; per-signal strides N
 // (grid), M (output), d.lstride (locals), 4 (2q) + 1 (level-2 coefficients).
 template <class T, class VO, int G>
-__global__ void __launch_bounds__(256) k_targets_fwd(
+__global__ void __launch_bounds__(kTgtThreads) k_targets_fwd(
     TreeDims d, int M, const int32_t* __restrict__ k0s, const double* __restrict__ dels,
     const int32_t* __restrict__ perm, const cplx<T>* __restrict__ F,
     const cplx<T>* __restrict__ E, const cplx<T>* __restrict__ fgrid,
     const cplx<T>* __restrict__ lexp, const cplx<T>* __restrict__ lvl2, VO* __restrict__ g) {
-  int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= M) return;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cplx<T>* sf = reinterpret_cast<cplx<T>*>(smraw);  // [G][window]
+  __shared__ int s_lo, s_hi;
   const int N = (int)d.N;
   const int s = d.s;
   const int sig0 = blockIdx.y * G;
   fgrid += (int64_t)sig0 * N;
-  int k0 = k0s[j];
-  double dl = dels[j];
-  int b, o;
-  point_local(k0, dl, N, s, &b, &o);
-  const T dt = (T)dl;
-  // near field: leaves b-1, b, b+1 (periodic, unwrapped displacement); the
-  // pair with the nearest grid point (D = 0) is masked, E_j carries it
-  NearAcc<T> acc[G];
-  const int B = 1 << d.L;
-  for (int nb = -1; nb <= 1; ++nb) {
-    const cplx<T>* q = fgrid + (int64_t)((b + nb + B) & (B - 1)) * s;
-    const int D0 = o - nb * s;  // D = D0 - o' for the o'-th point of the leaf
-    for (int c0 = 0; c0 < s; c0 += 16) {
-      const int cn = s - c0 < 16 ? s - c0 : 16;
-#pragma unroll 16
-      for (int u = 0; u < cn; ++u) {
-        const int D = D0 - c0 - u;
-        T r = rcp_t(int_to_t(D, T()) + dt);
-        r = D == 0 ? (T)0 : r;
+  const int j0 = blockIdx.x * kTgtThreads;
+  const int j = j0 + threadIdx.x;
+  const bool act = j < M;
+  const int jl = (j0 + kTgtThreads < M ? j0 + kTgtThreads : M) - 1;
+  int k0 = 0, b = 0, o = 0;
+  double dl = 0;
+  if (act) {
+    k0 = k0s[j];
+    dl = dels[j];
+    point_local(k0, dl, N, s, &b, &o);
+  }
+  if (threadIdx.x == 0) s_lo = b;
+  if (j == jl) s_hi = b;
+  __syncthreads();
+  const int bl = s_lo, bh = s_hi;
+  const int nwin = (bh - bl + 3) * s;  // samples of leaves bl-1 .. bh+1
+  const bool staged = nwin <= NearCap<T, G>::fwd;
+  // (targets are sorted by leaf, so b lies in [bl, bh]; checked all the same)
+  if (staged) {
+    const int base = (bl - 1) * s;
+    for (int e = threadIdx.x; e < nwin; e += kTgtThreads) {
+      const int k = (base + e + N) & (N - 1);
 #pragma unroll
-        for (int gg = 0; gg < G; ++gg) acc[gg].add_r(q[(int64_t)gg * N + c0 + u], r);
-      }
-#pragma unroll
-      for (int gg = 0; gg < G; ++gg) acc[gg].fold();
+      for (int gg = 0; gg < G; ++gg) sf[gg * nwin + e] = fgrid[(int64_t)gg * N + k];
     }
+  }
+  __syncthreads();
+  if (!act) return;
+  const T dt = (T)dl;
+  NearAcc<T> acc[G];
+  // c-th sample of the target's 3 leaves: D = k0 - k = (o + s) - c
+  const T D0 = (T)(o + s);
+  if (staged && b >= bl && b <= bh) {
+    const cplx<T>* w = sf + (b - bl) * s;  // leaf b - 1 of the window
+    near_window<T, G>(0, 3 * s, acc, [&](int c) {
+      const T t0 = D0 - (T)c;
+      T r = rcp_t(t0 + dt);
+      r = t0 == (T)0 ? (T)0 : r;  // the pair with x_k0: E_j carries it
+#pragma unroll
+      for (int gg = 0; gg < G; ++gg) acc[gg].add_r(w[gg * nwin + c], r);
+    });
+  } else {
+    const int base = (b - 1) * s;
+    near_window<T, G>(0, 3 * s, acc, [&](int c) {
+      const T t0 = D0 - (T)c;
+      T r = rcp_t(t0 + dt);
+      r = t0 == (T)0 ? (T)0 : r;
+      const int k = (base + c + N) & (N - 1);
+#pragma unroll
+      for (int gg = 0; gg < G; ++gg) acc[gg].add_r(fgrid[(int64_t)gg * N + k], r);
+    });
   }
   const int base = b * s;
   const int Q2 = 2 * d.q;  // cot kernel: degree 2q-1
@@ -555,8 +618,8 @@ __global__ void __launch_bounds__(256) k_targets_fwd(
     T hr = cN * fma(far.x, ts, nr.x) - c2 * reg.x;
     T hi = cN * fma(far.y, ts, nr.y) - c2 * reg.y;
     // g = E f_k0 - (F/2)(Q + i h')
-    cplx<T> w = mk<T>(Qs.x - hi, Qs.y + hr);
-    cplx<T> res = cscale(cmul(Fj, w), (T)-0.5);
+    cplx<T> wv = mk<T>(Qs.x - hi, Qs.y + hr);
+    cplx<T> res = cscale(cmul(Fj, wv), (T)-0.5);
     res = cadd(res, cmul(Ej, fgrid[(int64_t)gg * N + k0]));
     store_out<VO>(g + (int64_t)sig * M + pj, to_d2(res));
   }
@@ -617,12 +680,6 @@ __global__ void k_self_terms(int M, int inverse, int N, const int32_t* __restric
   st[i] = from_d2<T>(v);
 }
 
-// Packed source position for the adjoint / inverse near field: grid index k0
-// and offset delta in one 8-byte (FP32) or 16-byte (FP64) load, shared by all
-// signals.
-template <class T> struct SrcPos;
-template <> struct SrcPos<float> { int k0; float dl; };
-template <> struct SrcPos<double> { long long k0; double dl; };
 
 template <class T>
 __global__ void k_pack_positions(int M, const int32_t* __restrict__ k0s,
@@ -640,56 +697,114 @@ __global__ void k_pack_positions(int M, const int32_t* __restrict__ k0s,
 //   adjoint: u_k   = -(Q + i h'_k)/2 + sum_{j: k0_j = k} st_j
 //   inverse: f_k/N = Ct_k (-(Q + i h'_k)/2) + sum_{j: k0_j = k} st_j
 // where h' leaves out the 2/t part of the pairs with k0_j = k (their st_j
-// terms above); Ct_k = C_k e^Lambda / N carries the 1/N of Eq. p1.  The
-// reciprocals 1/t are shared by the G signals.  All arithmetic in T (Ct in
-// FP32 for the mixed path).
+// terms above); Ct_k = C_k e^Lambda / N carries the 1/N of Eq. p1.
+// Near field: the CTA's 256 grid points lie in leaves bl..bh; the sources of
+// leaves bl-1..bh+1 (consecutive in sorted order, leaf by leaf) are staged
+// in shared memory in chunks, each with its position x relative to the
+// CTA's first grid point kb (an exact integer in T, unwrapped through its
+// leaf slot) and offset delta, its charges and self terms.  A grid point in
+// leaf b sums over the sources of leaves b-1, b, b+1: t = (k - kb - x) -
+// delta with the first difference exact.  The reciprocals 1/t are shared by
+// the G signals.  All arithmetic in T (Ct in FP32 for the mixed path).
 template <class T, int G>
-__global__ void __launch_bounds__(256) k_targets_grid(
+__global__ void __launch_bounds__(kTgtThreads) k_targets_grid(
     TreeDims d, int inverse, const int32_t* __restrict__ start,
     const SrcPos<T>* __restrict__ pos, const cplx<T>* __restrict__ charge,
     const cplx<T>* __restrict__ st, const cplx<T>* __restrict__ lexp,
     const cplx<T>* __restrict__ lvl2, const T* __restrict__ Ct, cplx<T>* __restrict__ out) {
-  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  constexpr int CAP = NearCap<T, G>::grid;
+  constexpr int kMaxSlots = kTgtThreads + 3;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cplx<T>* srel = reinterpret_cast<cplx<T>*>(smraw);  // [CAP] (x, delta)
+  cplx<T>* sq = srel + CAP;                            // [G][CAP] charges
+  cplx<T>* sst = sq + G * CAP;                         // [G][CAP] self terms
+  __shared__ int s_off[kMaxSlots + 1];                 // window offsets of the leaf slots
   const int N = (int)d.N;
-  if (k >= N) return;
   const int64_t M = d.M_;
   const int sig0 = blockIdx.y * G;
   charge += sig0 * M;
   st += sig0 * M;
   const int s = d.s;
   const int B = 1 << d.L;
-  int b = k / s, o = k - b * s;
+  const int kb = blockIdx.x * kTgtThreads;
+  const int k = kb + threadIdx.x;
+  const bool act = k < N;
+  const int bl = kb / s;
+  const int bh = ((kb + kTgtThreads < N ? kb + kTgtThreads : N) - 1) / s;
+  const int nslot = bh - bl + 3;  // leaves bl-1 .. bh+1 (<= kMaxSlots)
+  // slot sizes, then their offsets in the window (one warp, shuffle scan)
+  if (threadIdx.x < 32) {
+    int carry = 0;
+    for (int c0 = 0; c0 < nslot; c0 += 32) {
+      const int js = c0 + threadIdx.x;
+      int cnt = 0;
+      if (js < nslot) {
+        const int bb = (bl - 1 + js + B) & (B - 1);
+        cnt = start[bb + 1] - start[bb];
+      }
+      int v = cnt;
+#pragma unroll
+      for (int sh = 1; sh < 32; sh <<= 1) {
+        int n = __shfl_up_sync(0xffffffffu, v, sh);
+        if ((int)threadIdx.x >= sh) v += n;
+      }
+      if (js < nslot) s_off[js + 1] = carry + v;
+      carry += __shfl_sync(0xffffffffu, v, 31);
+    }
+    if (threadIdx.x == 0) s_off[0] = 0;
+  }
+  __syncthreads();
+  const int total = s_off[nslot];
+  const int b = act ? k / s : bl;
+  const int wlo = s_off[b - bl], whi = s_off[b - bl + 3];  // this point's 3 leaves
+  const T kf = (T)(k - kb);
   NearAcc<T> acc[G];
   cplx<T> self[G];
 #pragma unroll
   for (int gg = 0; gg < G; ++gg) self[gg] = mk<T>(0, 0);
-  for (int nb = -1; nb <= 1; ++nb) {
-    int bb = (b + nb + B) & (B - 1);
-    int a = start[bb], e = start[bb + 1];
-    // D = o - (nb s + ((k0_i - bb s) mod N)): k0_i relative to leaf b's
-    // origin, unwrapped through the known leaf offset nb
-    const int D0 = o - nb * s, sub = bb * s;
-    int cnt = 0;
-    for (int i = a; i < e; ++i) {
-      const SrcPos<T> ps = pos[i];
-      int D = D0 - (((int)ps.k0 - sub) & (N - 1));
-      T r = rcp_t(int_to_t(D, T()) - ps.dl);
-      if (D == 0) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int c0 = 0; c0 < total; c0 += CAP) {
+    const int c1 = total - c0 < CAP ? total : c0 + CAP;
+    __syncthreads();  // the previous chunk is consumed
+    // stage: warp w copies slots w, w + 8, ... (their part inside [c0, c1))
+    for (int js = warp; js < nslot; js += kTgtThreads / 32) {
+      const int lo = s_off[js] > c0 ? s_off[js] : c0;
+      const int hi = s_off[js + 1] < c1 ? s_off[js + 1] : c1;
+      if (lo >= hi) continue;
+      const int bu = bl - 1 + js;  // unwrapped leaf of the slot
+      const int bb = (bu + B) & (B - 1);
+      const int g0 = start[bb] - s_off[js];  // global index of window index e: g0 + e
+      for (int e = lo + lane; e < hi; e += 32) {
+        const int gi = g0 + e;
+        const SrcPos<T> ps = pos[gi];
+        const int xu = bu * s + (((int)ps.k0 - bb * s) & (N - 1)) - kb;
+        srel[e - c0] = mk<T>((T)xu, ps.dl);
 #pragma unroll
-        for (int gg = 0; gg < G; ++gg) self[gg] = cadd(self[gg], st[gg * M + i]);
-        r = (T)0;
-      }
-#pragma unroll
-      for (int gg = 0; gg < G; ++gg) acc[gg].add_r(charge[gg * M + i], r);
-      if (++cnt == 16) {
-#pragma unroll
-        for (int gg = 0; gg < G; ++gg) acc[gg].fold();
-        cnt = 0;
+        for (int gg = 0; gg < G; ++gg) {
+          sq[gg * CAP + e - c0] = charge[gg * M + gi];
+          sst[gg * CAP + e - c0] = st[gg * M + gi];
+        }
       }
     }
+    __syncthreads();
+    const int lo = (wlo > c0 ? wlo : c0) - c0, hi = (whi < c1 ? whi : c1) - c0;
+    if (act && lo < hi) {
+      near_window<T, G>(lo, hi, acc, [&](int i) {
+        const cplx<T> rp = srel[i];
+        const T t0 = kf - rp.x;
+        T r = rcp_t(t0 - rp.y);
+        if (t0 == (T)0) {  // k0_j = k: the pair's self term replaces it
+          r = (T)0;
 #pragma unroll
-    for (int gg = 0; gg < G; ++gg) acc[gg].fold();
+          for (int gg = 0; gg < G; ++gg) self[gg] = cadd(self[gg], sst[gg * CAP + i]);
+        }
+#pragma unroll
+        for (int gg = 0; gg < G; ++gg) acc[gg].add_r(sq[gg * CAP + i], r);
+      });
+    }
   }
+  if (!act) return;
+  const int o = k - b * s;
   const int Q2 = 2 * d.q;
   const int arc = b >> (d.L - 2);
   const int I = k - arc * (N >> 2) - (N >> 3);
@@ -886,8 +1001,8 @@ template <> struct PlanT<float> {
 
 template <class T, class VO, int G>
 static void launch_targets_fwd(nufft_plan_s* pl, const TreeDims& d, const cplx<T>* f, void* g) {
-  dim3 grid(nblk(pl->M, 256), (unsigned)(pl->batch / G));
-  k_targets_fwd<T, VO, G><<<grid, 256, 0, pl->stream>>>(
+  dim3 grid(nblk(pl->M, kTgtThreads), (unsigned)(pl->batch / G));
+  k_targets_fwd<T, VO, G><<<grid, kTgtThreads, NearCap<T, G>::fwd_bytes, pl->stream>>>(
       d, (int)pl->M, pl->k0, pl->delta, pl->perm, PlanT<T>::F(pl), PlanT<T>::E(pl), f,
       (const cplx<T>*)pl->lexp, PlanT<T>::lvl2(pl), (VO*)g);
 }
@@ -948,11 +1063,13 @@ int fmm_to_grid(nufft_plan_s* pl, const void* g, int inverse) {
                                                 (const double2*)g, pl->Ct, stt);
   k_pack_positions<T><<<nblk(pl->M, 256), 256, 0, st>>>((int)pl->M, pl->k0, pl->delta, pos);
   if (pl->batch % 4 == 0)
-    k_targets_grid<T, 4><<<dim3(nblk(pl->N, 256), nsig / 4), 256, 0, st>>>(
+    k_targets_grid<T, 4><<<dim3(nblk(pl->N, kTgtThreads), nsig / 4), kTgtThreads,
+                           NearCap<T, 4>::grid_bytes, st>>>(
         d, inverse, pl->leaf_start, pos, charge, stt, (const cplx<T>*)pl->lexp,
         PlanT<T>::lvl2(pl), PlanT<T>::Ct(pl), (cplx<T>*)pl->grid);
   else
-    k_targets_grid<T, 1><<<dim3(nblk(pl->N, 256), nsig), 256, 0, st>>>(
+    k_targets_grid<T, 1><<<dim3(nblk(pl->N, kTgtThreads), nsig), kTgtThreads,
+                           NearCap<T, 1>::grid_bytes, st>>>(
         d, inverse, pl->leaf_start, pos, charge, stt, (const cplx<T>*)pl->lexp,
         PlanT<T>::lvl2(pl), PlanT<T>::Ct(pl), (cplx<T>*)pl->grid);
   prof_end(pl, 3);

@@ -43,7 +43,6 @@ constexpr int kTcParents = 64;   // parents per tile
 constexpr int kTcRows = 128;     // MMA M (parents x {re, im})
 constexpr int kTcThreads = 256;  // 8 warps
 constexpr int kTcTmemCols = 64;  // accumulator columns allocated (>= Npad)
-constexpr int kMaxGrp = 36;      // kpad / 4 for p <= 28
 constexpr long long kSpinLimit = 1ll << 26;   // iteration cap besides the time limit
 constexpr uint64_t kWaitNs = 1000000000ull;  // 1 s
 
@@ -170,10 +169,65 @@ __device__ inline void split_tf32(float x, float& hi, float& lo) {
   lo = x - hi;
 }
 
-// Shared memory: A_hi, A_lo [128 x kpad], B_hi, B_lo [npad x kpad] (the
-// order of the device table), then the mbarriers and the TMEM address.
-__host__ __device__ inline size_t tc_smem_floats(int p) {
-  return (size_t)2 * kTcRows * tc_kpad(p) + (size_t)2 * tc_npad(p) * tc_kpad(p);
+// Shared-memory plan of the kernel (byte offsets; the MMA operands start on
+// 1024-byte boundaries, the rest on 128-byte ones):
+// A_hi, A_lo [128 x kpad] f32; B_hi, B_lo [npad x kpad] f32 (the order of
+// the device table); raw multipoles [132 boxes][pm] and raw parent locals
+// [64][p] (complex, as in global memory); result staging [64][4p + 1] f32;
+// three mbarriers and the TMEM address.
+struct TcSmem {
+  size_t a_hi, a_lo, b, raw_m, raw_l, stage, bars, total;
+};
+__host__ __device__ inline size_t tc_align(size_t x) { return (x + 1023) & ~size_t(1023); }
+__host__ __device__ inline size_t tc_align16(size_t x) { return (x + 127) & ~size_t(127); }
+__host__ __device__ inline TcSmem tc_smem(int p, int pm) {
+  const size_t kpad = tc_kpad(p), npad = tc_npad(p);
+  TcSmem m;
+  m.a_hi = 0;
+  m.a_lo = tc_align(m.a_hi + (size_t)kTcRows * kpad * 4);
+  m.b = tc_align(m.a_lo + (size_t)kTcRows * kpad * 4);
+  m.raw_m = tc_align(m.b + (size_t)2 * npad * kpad * 4);
+  m.raw_l = tc_align16(m.raw_m + (size_t)(2 * kTcParents + 4) * pm * 8);
+  m.stage = tc_align16(m.raw_l + (size_t)kTcParents * p * 8);
+  m.bars = tc_align16(m.stage + (size_t)kTcParents * (4 * p + 1) * 4);
+  m.total = m.bars + 64;
+  return m;
+}
+
+// One tile = parents P0 .. P0 + nval - 1 of one signal at level l - 1.
+struct TcTile {
+  int sig, P0, nval;
+};
+__device__ inline TcTile tc_tile(int t, int tiles_per_sig, int npar) {
+  TcTile r;
+  r.sig = t / tiles_per_sig;
+  r.P0 = (t - r.sig * tiles_per_sig) * kTcParents;
+  r.nval = npar - r.P0 < kTcParents ? npar - r.P0 : kTcParents;
+  return r;
+}
+
+// Issue the bulk copies of a tile's raw operands (one thread): multipole
+// boxes 2 P0 - 2 .. 2 P0 + 2 nval + 1 (periodic: up to three segments, each
+// starting at an even box, so every copy is 16-byte aligned and a multiple
+// of 16 bytes) and the parents' locals.  Completion on `bar`.
+__device__ inline void tc_issue_raw(const TreeDims& d, int l, const TcTile& tl,
+                                    const float2* mexp, const float2* lexp, uint32_t raw_m,
+                                    uint32_t raw_l, uint32_t bar) {
+  const int pm = d.pm, p = d.p;
+  const int nb = 1 << l;
+  const int nbox = 2 * tl.nval + 4;
+  const float2* ml = mexp + tl.sig * d.mstride + level_off(l) * pm;
+  const float2* lp = lexp + tl.sig * d.lstride + (level_off(l - 1) - 4 + (int64_t)tl.P0) * p;
+  const uint32_t bytes = (uint32_t)((size_t)nbox * pm * 8 + (size_t)tl.nval * p * 8);
+  mbar_expect_tx(bar, bytes);
+  int b = 0;
+  while (b < nbox) {
+    const int box = (2 * tl.P0 - 2 + b + nb) & (nb - 1);
+    const int len = nbox - b < nb - box ? nbox - b : nb - box;
+    bulk_g2s(raw_m + (uint32_t)(b * pm * 8), ml + (int64_t)box * pm, (uint32_t)(len * pm * 8), bar);
+    b += len;
+  }
+  bulk_g2s(raw_l, lp, (uint32_t)(tl.nval * p * 8), bar);
 }
 
 __global__ void __launch_bounds__(kTcThreads, 1)
@@ -182,20 +236,30 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   extern __shared__ __align__(1024) unsigned char smraw[];
   const int p = d.p, pm = d.pm;
   const int kpad = tc_kpad(p), npad = tc_npad(p);
-  float* Ahi = reinterpret_cast<float*>(smraw);
-  float* Alo = Ahi + kTcRows * kpad;
-  float* Bhi = Alo + kTcRows * kpad;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(Bhi + 2 * npad * kpad);  // [0] B load, [1] MMA
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2);
+  const TcSmem so = tc_smem(p, pm);
+  float* Ahi = reinterpret_cast<float*>(smraw + so.a_hi);
+  float* Alo = reinterpret_cast<float*>(smraw + so.a_lo);
+  float* Bhi = reinterpret_cast<float*>(smraw + so.b);
+  const float2* rawM = reinterpret_cast<const float2*>(smraw + so.raw_m);
+  const float2* rawL = reinterpret_cast<const float2*>(smraw + so.raw_l);
+  float* S = reinterpret_cast<float*>(smraw + so.stage);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smraw + so.bars);  // B load, MMA, raw
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 3);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const uint32_t bar_b = smem_u32(&bars[0]), bar_mma = smem_u32(&bars[1]);
+  const uint32_t bar_b = smem_u32(&bars[0]), bar_mma = smem_u32(&bars[1]),
+                 bar_raw = smem_u32(&bars[2]);
+  const uint32_t raw_m_u = smem_u32(smraw + so.raw_m), raw_l_u = smem_u32(smraw + so.raw_l);
 
-  // A starts at zero (its K padding stays zero); barriers; B by one bulk copy
-  for (int i = tid; i < 2 * kTcRows * kpad; i += kTcThreads) Ahi[i] = 0.f;
-  const uint32_t bbytes = (uint32_t)(2 * npad * kpad * sizeof(float));
+  const int nb = 1 << l;
+  const int npar = nb >> 1;
+  const int tiles_per_sig = (npar + kTcParents - 1) / kTcParents;
+  const int ntiles = tiles_per_sig * nsig;
+  const int G = gridDim.x;
+
   if (tid == 0) {
     mbar_init(bar_b, 1);
     mbar_init(bar_mma, 1);
+    mbar_init(bar_raw, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -205,83 +269,99 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  fence_async_smem();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
   int ok = 1;
   if (tid == 0) {
+    const uint32_t bbytes = (uint32_t)(2 * npad * kpad * sizeof(float));
     mbar_expect_tx(bar_b, bbytes);
     bulk_g2s(smem_u32(Bhi), bops, bbytes, bar_b);
+    if ((int)blockIdx.x < ntiles)
+      tc_issue_raw(d, l, tc_tile(blockIdx.x, tiles_per_sig, npar), mexp, lexp, raw_m_u, raw_l_u,
+                   bar_raw);
     ok = mbar_wait(bar_b, 0) ? 1 : 0;
   }
   ok = __syncthreads_and(ok);
 
-  const int nb = 1 << l;
-  const int npar = nb >> 1;
-  const int tiles_per_sig = (npar + kTcParents - 1) / kTcParents;
-  const int ntiles = tiles_per_sig * nsig;
   const uint32_t idesc = tc_idesc(npad, kTcRows);
   const uint32_t sbo = (uint32_t)kpad * 32u;
-  // gather mapping: warp w covers parents 8w..8w+7 (lane & 7) and, per item
-  // q, the 4 consecutive k = 4q + (lane >> 3) (conflict-free stores of the
-  // core-matrix layout)
-  const int kq = lane >> 3, j = warp * 8 + (lane & 7);
-  const int ngrp = kpad >> 2;
-  uint32_t phase = 0;
-  // staging of the result (reuses A_lo once the MMAs are done): per parent
-  // 4p floats (child 2P then 2P+1, interleaved re/im), row stride 4p + 1
-  float* S = Alo;
+  const int ngrp = kpad >> 2;             // k groups of 4
+  const int nquad = (ngrp + 3) >> 2;      // k-group quads per row group
   const int srow = 4 * p + 1;
+  // A-build mapping: lane -> parent row jj = lane & 7 of a group of 8 and
+  // k group 4 qq + (lane >> 3): 16-byte stores, 512 contiguous bytes per warp
+  const int jj = lane & 7, kg = lane >> 3;
+  // accumulator rows / columns of this thread (epilogue)
+  const int arow = 32 * (warp & 3) + lane;
+  const int ari = arow >> 6, aj = arow & 63;
+  const int ac0 = (warp >> 2) * (npad >> 1);
+  float acc[32];
+  uint32_t ph_raw = 0, ph_mma = 0;
+  TcTile prev{0, 0, 0};
+  bool have_prev = false;
 
-  // this thread's A entries of tile t, all loads issued back to back
-  float2 v[kMaxGrp];
-  auto load_tile = [&](int t) {
-    const int sig = t / tiles_per_sig;
-    const int P0 = (t - sig * tiles_per_sig) * kTcParents;
-    const int nval = npar - P0 < kTcParents ? npar - P0 : kTcParents;
-    const float2* ml = mexp + sig * d.mstride + level_off(l) * pm;
-    const float2* lp = lexp + sig * d.lstride + (level_off(l - 1) - 4) * (int64_t)p;
-    const int P = P0 + j;
-    const bool valid = j < nval;
+  // staged result of a finished tile -> the children's locals (contiguous)
+  auto store_prev = [&]() {
 #pragma unroll
-    for (int q = 0; q < kMaxGrp; ++q) {
-      v[q] = make_float2(0.f, 0.f);
-      const int k = 4 * q + kq;
-      if (q < ngrp && valid && k < 5 * p) {
-        const int s = (k >= p) + (k >= 2 * p) + (k >= 3 * p) + (k >= 4 * p);
-        const int m = k - s * p;
-        if (s < 4) {
-          const int off = s == 0 ? -2 : (s == 1 ? -1 : s);  // 2P-2, 2P-1, 2P+2, 2P+3
-          const int box = (2 * P + off + nb) & (nb - 1);
-          v[q] = ml[(int64_t)box * pm + m];
-        } else {
-          v[q] = lp[(int64_t)P * p + m];
-        }
+    for (int e = 0; e < 32; ++e) {
+      const int c = ac0 + e;
+      if (e < (npad >> 1) && c < 2 * p) {
+        const int h = c >= p, n = c - h * p;
+        S[aj * srow + h * 2 * p + 2 * n + ari] = acc[e];
       }
+    }
+    __syncthreads();
+    float4* dst = reinterpret_cast<float4*>(lexp + prev.sig * d.lstride +
+                                            (level_off(l) - 4 + 2 * (int64_t)prev.P0) * p);
+    const int nf4 = p * prev.nval;  // 4 p nval floats
+    for (int e = tid; e < nf4; e += kTcThreads) {
+      const int f = 4 * e;
+      const int jr = f / (4 * p), w = f - jr * 4 * p;
+      const float* src = S + jr * srow + w;
+      dst[e] = make_float4(src[0], src[1], src[2], src[3]);
     }
   };
 
-  int t = blockIdx.x;
-  if (t < ntiles) load_tile(t);
-  for (; ok && t < ntiles; t += gridDim.x) {
-    const int sig = t / tiles_per_sig;
-    const int P0 = (t - sig * tiles_per_sig) * kTcParents;
-    const int nval = npar - P0 < kTcParents ? npar - P0 : kTcParents;
-    // A (hi and lo) from the registers; rows j (real) and j + 64 (imaginary)
+  for (int t = blockIdx.x; ok && t < ntiles; t += G) {
+    const TcTile tl = tc_tile(t, tiles_per_sig, npar);
+    int got = 1;
+    if (tid == 0) got = mbar_wait(bar_raw, ph_raw) ? 1 : 0;
+    ph_raw ^= 1u;
+    if (!__syncthreads_and(got)) { ok = 0; break; }
+    // A (hi, lo) from the raw operands; rows j (real part), j + 64 (imaginary)
+    for (int it = warp; it < 8 * nquad; it += kTcThreads / 32) {
+      const int j = (it & 7) * 8 + jj;
+      const int gk = (it >> 3) * 4 + kg;  // k group
+      if (gk >= ngrp) continue;
+      float re[4], im[4];
 #pragma unroll
-    for (int q = 0; q < kMaxGrp; ++q) {
-      if (q < ngrp) {
-        const int k = 4 * q + kq;
-        float h, r;
-        split_tf32(v[q].x, h, r);
-        Ahi[tc_off(j, k, kpad)] = h;
-        Alo[tc_off(j, k, kpad)] = r;
-        split_tf32(v[q].y, h, r);
-        Ahi[tc_off(j + kTcParents, k, kpad)] = h;
-        Alo[tc_off(j + kTcParents, k, kpad)] = r;
+      for (int i = 0; i < 4; ++i) {
+        const int k = 4 * gk + i;
+        float2 v = make_float2(0.f, 0.f);
+        if (j < tl.nval && k < 5 * p) {
+          const int s = (k >= p) + (k >= 2 * p) + (k >= 3 * p) + (k >= 4 * p);
+          const int m = k - s * p;
+          if (s < 4) {
+            const int bs = s < 2 ? s : s + 2;  // box slots 2j + {0, 1, 4, 5}
+            v = rawM[(2 * j + bs) * pm + m];
+          } else {
+            v = rawL[j * p + m];
+          }
+        }
+        re[i] = v.x;
+        im[i] = v.y;
       }
+      float4 h, r;
+      split_tf32(re[0], h.x, r.x); split_tf32(re[1], h.y, r.y);
+      split_tf32(re[2], h.z, r.z); split_tf32(re[3], h.w, r.w);
+      *reinterpret_cast<float4*>(Ahi + tc_off(j, 4 * gk, kpad)) = h;
+      *reinterpret_cast<float4*>(Alo + tc_off(j, 4 * gk, kpad)) = r;
+      split_tf32(im[0], h.x, r.x); split_tf32(im[1], h.y, r.y);
+      split_tf32(im[2], h.z, r.z); split_tf32(im[3], h.w, r.w);
+      *reinterpret_cast<float4*>(Ahi + tc_off(j + kTcParents, 4 * gk, kpad)) = h;
+      *reinterpret_cast<float4*>(Alo + tc_off(j + kTcParents, 4 * gk, kpad)) = r;
     }
     fence_async_smem();
     tc_fence_before();
@@ -298,57 +378,42 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                  (pass | kk) ? 1u : 0u);
       }
       tc_commit(bar_mma);
+      // the raw operands are consumed: fetch the next tile's meanwhile
+      if (t + G < ntiles)
+        tc_issue_raw(d, l, tc_tile(t + G, tiles_per_sig, npar), mexp, lexp, raw_m_u, raw_l_u,
+                     bar_raw);
     }
-    // the next tile's loads are in flight during the MMAs and the epilogue
-    if (t + (int)gridDim.x < ntiles) load_tile(t + gridDim.x);
+    // the previous tile's epilogue overlaps these MMAs
+    if (have_prev) store_prev();
     int done = 1;
-    if (tid == 0) done = mbar_wait(bar_mma, phase) ? 1 : 0;
-    phase ^= 1u;
+    if (tid == 0) done = mbar_wait(bar_mma, ph_mma) ? 1 : 0;
+    ph_mma ^= 1u;
     if (!__syncthreads_and(done)) { ok = 0; break; }
     tc_fence_after();
-    // accumulator -> staging: warp quadrant (warp & 3) holds rows 32*(warp & 3)
-    // ..+31; warps 0-3 read columns [0, npad/2), warps 4-7 [npad/2, npad)
-    {
-      const int row = 32 * (warp & 3) + lane;
-      const int ri = row >> 6, jr = row & 63;
-      const int c0 = (warp >> 2) * (npad >> 1);
-      for (int cb = 0; cb < (npad >> 1); cb += 8) {
-        float acc[8];
-        tc_ld8(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(c0 + cb), acc);
-        tc_wait_ld();
+    for (int cb = 0; cb < (npad >> 1); cb += 8) {
+      float v[8];
+      tc_ld8(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(ac0 + cb), v);
+      tc_wait_ld();
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          const int c = c0 + cb + e;
-          if (c < 2 * p) {
-            const int h = c >= p, n = c - h * p;
-            S[jr * srow + h * 2 * p + 2 * n + ri] = acc[e];
-          }
-        }
+      for (int e = 0; e < 8; ++e) {
+        // acc index cb + e (cb is a multiple of 8 below 32)
+#pragma unroll
+        for (int z = 0; z < 4; ++z)
+          if (cb == 8 * z) acc[8 * z + e] = v[e];
       }
     }
     tc_fence_before();
     __syncthreads();
-    // children 2P0 .. 2P0 + 2 nval - 1 are contiguous: 2 nval p complex,
-    // written as float4 (16-byte aligned: the offset is an even box index)
-    {
-      float4* dst = reinterpret_cast<float4*>(lexp + sig * d.lstride +
-                                              (level_off(l) - 4 + 2 * (int64_t)P0) * p);
-      const int nf4 = p * nval;  // (4 p nval) / 4
-      for (int e = tid; e < nf4; e += kTcThreads) {
-        const int f = 4 * e;
-        const int jr = f / (4 * p), w = f - jr * 4 * p;
-        const float* src = S + jr * srow + w;  // 4p divisible by 4: no row crossing
-        dst[e] = make_float4(src[0], src[1], src[2], src[3]);
-      }
-    }
-    __syncthreads();
+    prev = tl;
+    have_prev = true;
   }
+  if (ok && have_prev) store_prev();
   if (!ok && tid == 0) atomicOr(status, kDevTimeout);
-  // leave only with the tensor memory freed; a timed-out MMA gets one more
-  // bounded wait first
+  // leave only with the copies and MMAs finished and the tensor memory freed
   if (tid == 0 && !ok) {
     mbar_wait(bar_b, 0);
-    mbar_wait(bar_mma, phase ^ 1u);
+    mbar_wait(bar_raw, ph_raw);
+    mbar_wait(bar_mma, ph_mma);
   }
   tc_fence_before();
   __syncthreads();
@@ -366,9 +431,8 @@ int g_num_sms = 0;
 
 using namespace nufft;
 
-bool m2l_tc_supported(int p) {
-  return tc_npad(p) <= kTcTmemCols && (tc_kpad(p) >> 2) <= kMaxGrp &&
-         tc_smem_floats(p) * 4 + 64 <= 227 * 1024;
+bool m2l_tc_supported(int p, int pm) {
+  return tc_npad(p) <= kTcTmemCols && tc_npad(p) / 2 <= 32 && tc_smem(p, pm).total <= 227 * 1024;
 }
 
 size_t m2l_tc_table_floats(int p) { return (size_t)2 * tc_npad(p) * tc_kpad(p); }
@@ -420,11 +484,12 @@ int m2l_tc_configure() {
 // Launch the level-l M2L + L2L (l >= 4) for all signals of a plan.
 int m2l_tc_level(const TreeDims& d, int l, int nsig, const float* bops, const float2* mexp,
                  float2* lexp, int* status, cudaStream_t st) {
+  if (l < 4 || l > d.L || nsig < 1 || !m2l_tc_supported(d.p, d.pm)) return NUFFT_EINVAL;
   const int npar = 1 << (l - 1);
   const int ntiles = ((npar + kTcParents - 1) / kTcParents) * nsig;
   const int nsm = g_num_sms > 0 ? g_num_sms : 1;
   const int grid = ntiles < nsm ? ntiles : nsm;
-  const size_t smem = tc_smem_floats(d.p) * sizeof(float) + 64;
+  const size_t smem = tc_smem(d.p, d.pm).total;
   k_m2l_tc<<<grid, kTcThreads, smem, st>>>(d, l, nsig, bops, mexp, lexp, status);
   return cudaGetLastError() == cudaSuccess ? NUFFT_OK : NUFFT_ECUDA;
 }

@@ -22,7 +22,7 @@ template <class T>
 int fft_run(const void* in, int in_f64, void* out, int out_f64, cplx<T>* buf, cplx<T>* buf2,
             int64_t N, int batch, int sign, const cplx<T>* tw, cudaStream_t st);
 template <class T> int fmm_configure();
-bool m2l_tc_supported(int p);
+bool m2l_tc_supported(int p, int pm);
 size_t m2l_tc_table_floats(int p);
 void m2l_tc_table(int p, const long double* m2l, const long double* l2l, float* out);
 int m2l_tc_configure();
@@ -323,7 +323,7 @@ int nufft_choose_params(int64_t N, int64_t M, double eps, int prec, nufft_params
   if (batch > 4096) return NUFFT_EINVAL;
   int tc = prm->tc_level;
   if (tc != -1 && tc != 0 && (tc < 4 || tc > 30)) return NUFFT_EINVAL;
-  if (prec != NUFFT_MIXED || !m2l_tc_supported(p)) tc = -1;
+  if (prec != NUFFT_MIXED || !m2l_tc_supported(p, p > 2 * q + 1 ? p : 2 * q + 1)) tc = -1;
   if (tc == 0) {
     // finest levels with at least 2048 parents over all signals (32 tiles)
     tc = -1;

@@ -13,9 +13,13 @@
 //   3. q lowered in steps of 1 likewise;
 //   4. mixed precision: the first tensor-core level (tc_level), every level
 //      from max(4, l_max - 9) to l_max and "never".
-// A candidate is accurate when its relative L2 difference to the reference
-// is at most max(eps / 4, 1.5 x that of the formula's parameters), so tuning
-// never makes a plan less accurate than eps / 4 or than the paper's choice.
+// A candidate is accurate when every output's relative L2 error is at most
+// max(eps / 4, 1.5 x that of the formula's parameters), so tuning never makes
+// a plan less accurate than eps / 4 or than the paper's choice.  Errors: the
+// forward and adjoint against the reference FMM; the inverse, when timed
+// with the forward, as the round trip inv(fwd(c)) against c itself (the
+// pipeline's error, including the inverse's conditioning), else against the
+// reference inverse.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -108,7 +112,8 @@ struct Tuner {
   cudaStream_t st;
   Buffers buf;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
-  double err_default = -1;
+  double def_err[3] = {0, 0, 0};   // errors of the formula parameters (fwd, adj, inv)
+  double last_err[3] = {0, 0, 0};  // errors of the last candidate evaluated
   std::vector<nufft_tune_trial> log;
 
   ~Tuner() {
@@ -118,6 +123,9 @@ struct Tuner {
 
   bool io64() const { return !(flags & NUFFT_IO_C64); }
 
+  // The exec sequence.  A candidate's inverse, timed together with its
+  // forward, takes that forward's output (the round trip of the pipeline);
+  // otherwise it takes the reference forward's samples of the probe series.
   int run(nufft_plan pl, bool reference, void* og, void* oa, void* oi) {
     const bool d = reference || io64();
     int rc = NUFFT_OK;
@@ -125,19 +133,25 @@ struct Tuner {
       rc = nufft_plan_exec_fwd(pl, d ? (void*)buf.c_d : (void*)buf.c_f, og);
     if (!rc && (ops & NUFFT_OP_ADJ))
       rc = nufft_plan_exec_adj(pl, d ? (void*)buf.g_d : (void*)buf.g_f, oa);
-    if (!rc && (ops & NUFFT_OP_INV))
-      rc = nufft_plan_exec_inv(pl, d ? (void*)buf.gi_d : (void*)buf.gi_f, oi);
+    if (!rc && (ops & NUFFT_OP_INV)) {
+      const void* gin = (!reference && (ops & NUFFT_OP_FWD)) ? og
+                        : (d ? (void*)buf.gi_d : (void*)buf.gi_f);
+      rc = nufft_plan_exec_inv(pl, gin, oi);
+    }
     return rc;
   }
 
-  int rel_err(const void* a, int a64, const double2* ref, int64_t n, double* e2, double* r2) {
+  // relative L2 difference of a (complex64 or complex128) to ref
+  int rel_err(const void* a, int a64, const double2* ref, int64_t n, double* err) {
     k_err_partial<<<kErrBlocks, 256, 0, st>>>(a, a64, ref, n, buf.partial);
     std::vector<double2> h(kErrBlocks);
     if (cudaMemcpyAsync(h.data(), buf.partial, kErrBlocks * sizeof(double2), cudaMemcpyDeviceToHost,
                         st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
       return NUFFT_ECUDA;
-    for (const double2& v : h) { *e2 += v.x; *r2 += v.y; }
+    double e2 = 0, r2 = 0;
+    for (const double2& v : h) { e2 += v.x; r2 += v.y; }
+    *err = r2 > 0 ? std::sqrt(e2 / r2) : std::sqrt(e2);
     return NUFFT_OK;
   }
 
@@ -196,24 +210,32 @@ struct Tuner {
       ms.push_back(t);
     }
     if (!rc) rc = nufft_plan_sync(pl);
-    double e2 = 0, r2 = 0;
+    // per output: forward vs the reference forward, adjoint vs the reference
+    // adjoint, inverse vs the probe coefficients themselves (round trip, when
+    // timed with the forward) or vs the reference inverse
     const int a64 = io64();
     const int64_t nc = (int64_t)batch * N, ng = (int64_t)batch * M;
-    if (!rc && (ops & NUFFT_OP_FWD)) rc = rel_err(buf.out_g, a64, buf.ref_g, ng, &e2, &r2);
-    if (!rc && (ops & NUFFT_OP_ADJ)) rc = rel_err(buf.out_a, a64, buf.ref_a, nc, &e2, &r2);
-    if (!rc && (ops & NUFFT_OP_INV)) rc = rel_err(buf.out_i, a64, buf.ref_i, nc, &e2, &r2);
+    double e[3] = {0, 0, 0};
+    if (!rc && (ops & NUFFT_OP_FWD)) rc = rel_err(buf.out_g, a64, buf.ref_g, ng, &e[0]);
+    if (!rc && (ops & NUFFT_OP_ADJ)) rc = rel_err(buf.out_a, a64, buf.ref_a, nc, &e[1]);
+    if (!rc && (ops & NUFFT_OP_INV))
+      rc = rel_err(buf.out_i, a64, (ops & NUFFT_OP_FWD) ? buf.c_d : buf.ref_i, nc, &e[2]);
     nufft_plan_destroy(pl);
     if (rc) return rc;
     std::sort(ms.begin(), ms.end());
     out->ms = ms[ms.size() / 2];
-    out->err = r2 > 0 ? std::sqrt(e2 / r2) : std::sqrt(e2);
+    out->err = std::max(e[0], std::max(e[1], e[2]));
+    for (int i = 0; i < 3; ++i) last_err[i] = e[i];
     out->accepted = 0;
     *valid = true;
     return NUFFT_OK;
   }
 
-  bool accurate(const nufft_tune_trial& t) const {
-    return t.err <= std::max(0.25 * eps, 1.5 * err_default);
+  // every output within max(eps / 4, 1.5 x the formula parameters' error)
+  bool accurate() const {
+    for (int i = 0; i < 3; ++i)
+      if (last_err[i] > std::max(0.25 * eps, 1.5 * def_err[i])) return false;
+    return true;
   }
 
   // evaluate, log, and keep if accurate and faster than *best
@@ -224,7 +246,7 @@ struct Tuner {
     if (acc) *acc = false;
     int rc = eval(prm, &t, &valid);
     if (rc || !valid) return rc;
-    const bool ok = accurate(t);
+    const bool ok = accurate();
     if (acc) *acc = ok;
     if (ok && (best->ms <= 0 || t.ms < best->ms)) {
       *best = t;
@@ -258,7 +280,7 @@ extern "C" int nufft_autotune(int64_t N, int64_t M, const double* y, double eps,
   bool valid = false, took = false, acc = false;
   if ((rc = tu.eval(d0, &cur, &valid))) return rc;
   if (!valid) return NUFFT_EINVAL;
-  tu.err_default = cur.err;
+  for (int i = 0; i < 3; ++i) tu.def_err[i] = tu.last_err[i];
   cur.accepted = 1;
   tu.log.push_back(cur);
   nufft_tune_trial bestt = cur;

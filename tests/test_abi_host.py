@@ -106,7 +106,7 @@ def test_tc_level_choice(nf):
     assert nf.choose_params_full(1 << 20, 1 << 20, 1e-6, nf.MIXED, tc_level=-1)["tc_level"] == -1
     assert nf.choose_params_full(1 << 20, 1 << 20, 1e-6, nf.MIXED, tc_level=9)["tc_level"] == 9
     assert nf.choose_params_full(1 << 20, 1 << 20, 1e-6, nf.MIXED, tc_level=20)["tc_level"] == -1
-    # p above the kernel's limit (28): no tensor-core levels
+    # p above the kernel's limit (24): no tensor-core levels
     assert nf.choose_params_full(1 << 20, 1 << 20, 1e-6, nf.MIXED, p=30)["tc_level"] == -1
     for bad in (1, 2, 3, 31, -2):
         with pytest.raises(nf.NufftError):
