@@ -12,7 +12,7 @@
 
 namespace nufft {
 
-constexpr int kFftSmemElems = 4096;  // R * J complex elements staged per CTA
+constexpr int kFftSmemElems = 4096;  // R * J complex elements staged per CTA (at most)
 
 __global__ void k_fft_tables(double2* __restrict__ tw, int64_t N, int lo_bits) {
   int64_t nlo = int64_t(1) << lo_bits, nhi = N >> lo_bits;
@@ -57,64 +57,112 @@ __device__ inline void store_c(void* p, int64_t i, int f64, cplx<T> v) {
   else reinterpret_cast<float2*>(p)[i] = make_float2((float)v.x, (float)v.y);
 }
 
-template <class T>
-__global__ void __launch_bounds__(256) k_fft_pass(const void* __restrict__ in, int in_f64,
-                                                  void* __restrict__ out, int out_f64, int64_t N,
-                                                  int logR, int64_t Ns, int J, int sign,
-                                                  const cplx<T>* __restrict__ tw, int lo_bits) {
+// Size-S DFT of v[0..S) in registers (S = 2^LOGS <= 32), radix-2
+// decimation in time: v holds the input in bit-reversed order and receives
+// the output in natural order.  Twiddles w_S^e = wR[e * (R / S)] from the
+// pass's table in shared memory (broadcast reads).
+template <class T, int LOGS>
+__device__ inline void dft_reg(cplx<T>* v, const cplx<T>* __restrict__ wR, int rs) {
+  constexpr int S = 1 << LOGS;
+#pragma unroll
+  for (int h = 1; h < S; h <<= 1) {
+#pragma unroll
+    for (int grp = 0; grp < S; grp += 2 * h) {
+#pragma unroll
+      for (int pos = 0; pos < h; ++pos) {
+        cplx<T> a = v[grp + pos], bb = v[grp + pos + h];
+        if (pos != 0) bb = cmul(bb, wR[pos * (S / (2 * h)) * rs]);
+        v[grp + pos] = cadd(a, bb);
+        v[grp + pos + h] = csub(a, bb);
+      }
+    }
+  }
+}
+
+template <int LOG> __device__ constexpr int brev_c(int x) {
+  int r = 0;
+  for (int i = 0; i < LOG; ++i) r |= ((x >> i) & 1) << (LOG - 1 - i);
+  return r;
+}
+
+// One radix-R Stockham pass, R = R1 R2 (R1 = 2^LOG1 >= R2 = 2^LOG2), for J
+// columns j per CTA (blockDim = J R2 threads; thread (c, t) = (tid mod J,
+// tid / J)).  Column j transforms a_r = in[j + r N/R] w^{sign r (j mod Ns) /
+// (Ns R)}, r = t + R2 m, as
+//   X[k1 + R1 k2] = sum_t w_R2^{t k2} w_R^{t k1} sum_m a[t + R2 m] w_R1^{m k1}:
+// thread t does the inner size-R1 DFT over m in registers, multiplies by
+// w_R^{t k1} and writes Y[k1][t] to shared memory; then thread u does the
+// size-R2 DFTs over t for k1 = u, u + R2, ...; the result goes back through
+// shared memory to out[(j / Ns) Ns R + (j mod Ns) + r' Ns] with contiguous
+// runs (J per r' for Ns >= J, else R per j).
+template <class T, int LOG1, int LOG2>
+__global__ void __launch_bounds__(256) k_fft_reg(const void* __restrict__ in, int in_f64,
+                                                 void* __restrict__ out, int out_f64, int64_t N,
+                                                 int64_t Ns, int J, int logJ, int sign,
+                                                 const cplx<T>* __restrict__ tw, int lo_bits) {
+  constexpr int R1 = 1 << LOG1, R2 = 1 << LOG2, R = R1 * R2, LOGR = LOG1 + LOG2;
   extern __shared__ unsigned char smraw[];
-  cplx<T>* sm = reinterpret_cast<cplx<T>*>(smraw);     // [R][J]
-  const int R = 1 << logR;
-  cplx<T>* twR = sm + R * J;                           // [R/2] e^{sign 2 pi i m / R}
-  const int64_t NR = N >> logR;
+  cplx<T>* wR = reinterpret_cast<cplx<T>*>(smraw);  // [R] w_R^e
+  cplx<T>* S = wR + R;                              // [R][J] (Y[k1][t] / X[r'] by column)
+  const int64_t NR = N >> LOGR;
   const int64_t j0 = (int64_t)blockIdx.x * J;
-  const int nth = blockDim.x;
-  // signal blockIdx.y of a batch: vectors at stride N elements
+  const int tid = threadIdx.x, nth = blockDim.x;
   in = (const char*)in + (size_t)blockIdx.y * N * (in_f64 ? 16 : 8);
   out = (char*)out + (size_t)blockIdx.y * N * (out_f64 ? 16 : 8);
-
-  for (int m = threadIdx.x; m < R / 2; m += nth)
-    twR[m] = twiddle_t<T>(tw, (int64_t)m * (N >> logR), lo_bits, sign);
-
-  // load with pass twiddle into bit-reversed position
-  const int64_t tstep = N / (Ns << logR);
-  for (int e = threadIdx.x; e < R * J; e += nth) {
-    int r = e / J, jj = e - r * J;
-    int64_t j = j0 + jj;
-    cplx<T> v = load_c<T>(in, j + (int64_t)r * NR, in_f64);
-    int64_t jm = j & (Ns - 1);
-    if (jm != 0 && r != 0) {
-      // w^{r jm / (Ns R)} = e^{2 pi i m / N} with m = r jm (N / (Ns R))
-      int64_t m = ((int64_t)r * jm) * tstep;
-      v = cmul(v, twiddle_t<T>(tw, m & (N - 1), lo_bits, sign));
-    }
-    int rb = logR ? (int)(__brev((unsigned)r) >> (32 - logR)) : 0;
-    sm[rb * J + jj] = v;
+  for (int e = tid; e < R; e += nth) wR[e] = twiddle_t<T>(tw, (int64_t)e * NR, lo_bits, sign);
+  const int c = tid & (J - 1), t = tid >> logJ;
+  const int64_t j = j0 + c;
+  const int64_t jm = j & (Ns - 1);
+  const int64_t tstep = N / (Ns << LOGR);
+  // load (columns fastest: J contiguous elements per r) with the pass twiddle
+  cplx<T> v[R1];
+#pragma unroll
+  for (int m = 0; m < R1; ++m) {
+    const int r = t + R2 * m;
+    cplx<T> x = load_c<T>(in, j + (int64_t)r * NR, in_f64);
+    if (jm != 0 && r != 0) x = cmul(x, twiddle_t<T>(tw, ((int64_t)r * jm * tstep) & (N - 1), lo_bits, sign));
+    v[brev_c<LOG1>(m)] = x;
+  }
+  __syncthreads();  // wR ready
+  dft_reg<T, LOG1>(v, wR, R / R1);
+  // Y[k1][t] = v[k1] w_R^{t k1}
+#pragma unroll
+  for (int k1 = 0; k1 < R1; ++k1) {
+    cplx<T> y = v[k1];
+    if (LOG2 > 0 && k1 != 0 && t != 0) y = cmul(y, wR[(t * k1) & (R - 1)]);
+    S[(k1 * R2 + t) * J + c] = y;
   }
   __syncthreads();
-  // radix-2 decimation-in-time butterflies
-  for (int h = 1; h < R; h <<= 1) {
-    int stride = R / (2 * h);
-    for (int e = threadIdx.x; e < (R / 2) * J; e += nth) {
-      int bf = e / J, jj = e - bf * J;
-      int grp = bf / h, pos = bf - grp * h;
-      int i0 = grp * 2 * h + pos, i1 = i0 + h;
-      cplx<T> w = twR[pos * stride];
-      cplx<T> a = sm[i0 * J + jj], b = cmul(sm[i1 * J + jj], w);
-      sm[i0 * J + jj] = cadd(a, b);
-      sm[i1 * J + jj] = csub(a, b);
+  if (LOG2 > 0) {
+    // thread u = t: size-R2 DFTs over t for k1 = u + R2 i, i < R1 / R2
+#pragma unroll
+    for (int i = 0; i < R1 / R2; ++i) {
+      const int k1 = t + R2 * i;
+      cplx<T> w[R2];
+#pragma unroll
+      for (int tt = 0; tt < R2; ++tt) w[brev_c<LOG2>(tt)] = S[(k1 * R2 + tt) * J + c];
+      dft_reg<T, LOG2>(w, wR, R / R2);
+#pragma unroll
+      for (int k2 = 0; k2 < R2; ++k2) v[i * R2 + k2] = w[k2];
+    }
+    __syncthreads();  // all reads of Y done
+#pragma unroll
+    for (int i = 0; i < R1 / R2; ++i) {
+      const int k1 = t + R2 * i;
+#pragma unroll
+      for (int k2 = 0; k2 < R2; ++k2) S[(k1 + R1 * k2) * J + c] = v[i * R2 + k2];
     }
     __syncthreads();
   }
-  // store: out[(j/Ns) Ns R + j%Ns + r Ns]
-  for (int e = threadIdx.x; e < R * J; e += nth) {
+  // S[r'][c] = X_{r'} of column c -> out
+  for (int e = tid; e < R * J; e += nth) {
     int r, jj;
-    if (Ns >= J) { r = e / J; jj = e - r * J; }   // J contiguous per r
-    else { jj = e / R; r = e - jj * R; }          // small Ns: R contiguous per j
-    int64_t j = j0 + jj;
-    int64_t jm = j & (Ns - 1);
-    int64_t dst = (j / Ns) * Ns * R + jm + (int64_t)r * Ns;
-    store_c<T>(out, dst, out_f64, sm[r * J + jj]);
+    if (Ns >= J) { r = e >> logJ; jj = e & (J - 1); }  // J contiguous per r
+    else { jj = e >> LOGR; r = e & (R - 1); }           // small Ns: R contiguous per j
+    const int64_t jg = j0 + jj;
+    const int64_t jmg = jg & (Ns - 1);
+    const int64_t dst = (jg / Ns) * Ns * R + jmg + (int64_t)r * Ns;
+    store_c<T>(out, dst, out_f64, S[r * J + jj]);
   }
 }
 
@@ -167,6 +215,49 @@ int fft_num_passes(int64_t N) {
 // (signal-major); in / out are complex128 (f64 = 1) or complex64.  Intermediate passes alternate between the scratch vectors buf
 // and buf2 (batch x N cplx<T> each; buf2 is used only with three or more passes), so
 // they keep T precision and never touch `out`.  `in` is only read.
+using FftKernel = void (*)(const void*, int, void*, int, int64_t, int64_t, int, int, int,
+                          const void*, int);
+
+template <class T, int LOG1, int LOG2>
+static void fft_launch(dim3 grid, int threads, size_t smem, cudaStream_t st, const void* in,
+                       int in_f64, void* out, int out_f64, int64_t N, int64_t Ns, int J, int logJ,
+                       int sign, const cplx<T>* tw, int lo_bits) {
+  k_fft_reg<T, LOG1, LOG2><<<grid, threads, smem, st>>>(in, in_f64, out, out_f64, N, Ns, J, logJ,
+                                                         sign, tw, lo_bits);
+}
+
+// the pass kernel for logR = LOG1 + LOG2 (LOG1 = ceil(logR / 2))
+template <class T>
+static int fft_pass(int logR, dim3 grid, int threads, size_t smem, cudaStream_t st,
+                    const void* in, int in_f64, void* out, int out_f64, int64_t N, int64_t Ns,
+                    int J, int logJ, int sign, const cplx<T>* tw, int lo_bits) {
+#define NUFFT_FFT_CASE(L1, L2)                                                                 \
+  case L1 + L2:                                                                                \
+    fft_launch<T, L1, L2>(grid, threads, smem, st, in, in_f64, out, out_f64, N, Ns, J, logJ, \
+                          sign, tw, lo_bits);                                                  \
+    return NUFFT_OK;
+  switch (logR) {
+    NUFFT_FFT_CASE(1, 0)
+    NUFFT_FFT_CASE(1, 1)
+    NUFFT_FFT_CASE(2, 1)
+    NUFFT_FFT_CASE(2, 2)
+    NUFFT_FFT_CASE(3, 2)
+    NUFFT_FFT_CASE(3, 3)
+    NUFFT_FFT_CASE(4, 3)
+    NUFFT_FFT_CASE(4, 4)
+    NUFFT_FFT_CASE(5, 4)
+    NUFFT_FFT_CASE(5, 5)
+    default: return NUFFT_EINVAL;
+  }
+#undef NUFFT_FFT_CASE
+}
+
+static int g_fft_sms = 0;
+
+// out = FFT(in) in arithmetic T for `batch` signals of N elements each
+// (signal-major); in / out are complex128 (f64 = 1) or complex64.  Intermediate passes alternate between the scratch vectors buf
+// and buf2 (batch x N cplx<T> each; buf2 is used only with three or more passes), so
+// they keep T precision and never touch `out`.  `in` is only read.
 template <class T>
 int fft_run(const void* in, int in_f64, void* out, int out_f64, cplx<T>* buf, cplx<T>* buf2,
             int64_t N, int batch, int sign, const cplx<T>* tw, cudaStream_t st) {
@@ -180,34 +271,65 @@ int fft_run(const void* in, int in_f64, void* out, int out_f64, cplx<T>* buf, cp
   const void* src = in;
   int src_f64 = in_f64;
   int64_t Ns = 1;
+  const int64_t target = 2 * (int64_t)(g_fft_sms > 0 ? g_fft_sms : 152);
   for (int i = 0; i < np; ++i) {
     bool last = (i == np - 1);
     void* dst = last ? out : (void*)((i & 1) ? buf2 : buf);
     int dst_f64 = last ? out_f64 : tf64;
-    int R = 1 << logR[i];
-    int J = kFftSmemElems / R;
-    if (J > (int)(N >> logR[i])) J = (int)(N >> logR[i]);
-    if (J < 1) J = 1;
-    size_t smem = (size_t)(R * J + R / 2) * sizeof(cplx<T>);
-    unsigned grid = (unsigned)((N >> logR[i]) / J);
-    k_fft_pass<T><<<dim3(grid, (unsigned)batch), 256, smem, st>>>(src, src_f64, dst, dst_f64, N,
-                                                                  logR[i], Ns, J, sign, tw, b);
+    const int lr = logR[i];
+    const int R = 1 << lr, R2 = 1 << (lr / 2);
+    const int64_t NR = N >> lr;
+    // columns per CTA: at most 256 threads and kFftSmemElems staged
+    // elements, at least 4 (contiguous runs), fewer while the grid is small
+    int J = 256 / R2;
+    while (J > 1 && (int64_t)R * J > kFftSmemElems) J >>= 1;
+    while (J > 4 && (NR / J) * batch < target) J >>= 1;
+    if (J > NR) J = (int)NR;
+    int logJ = 0;
+    while ((1 << logJ) < J) ++logJ;
+    size_t smem = (size_t)(R + R * J) * sizeof(cplx<T>);
+    unsigned grid = (unsigned)(NR / J);
+    int rc = fft_pass<T>(lr, dim3(grid, (unsigned)batch), J * R2, smem, st, src, src_f64, dst,
+                         dst_f64, N, Ns, J, logJ, sign, tw, b);
+    if (rc) return rc;
     src = dst;
     src_f64 = dst_f64;
-    Ns <<= logR[i];
+    Ns <<= lr;
   }
   return cudaGetLastError() == cudaSuccess ? NUFFT_OK : NUFFT_ECUDA;
 }
 
+template <class T, int LOG1, int LOG2>
+static int fft_attr() {
+  const int big = (int)((kFftSmemElems + 1024) * sizeof(cplx<T>));
+  return cudaFuncSetAttribute(k_fft_reg<T, LOG1, LOG2>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, big) == cudaSuccess
+             ? NUFFT_OK : NUFFT_ECUDA;
+}
+
+template <class T>
+static int fft_attrs() {
+  int rc = fft_attr<T, 1, 0>();
+  if (!rc) rc = fft_attr<T, 1, 1>();
+  if (!rc) rc = fft_attr<T, 2, 1>();
+  if (!rc) rc = fft_attr<T, 2, 2>();
+  if (!rc) rc = fft_attr<T, 3, 2>();
+  if (!rc) rc = fft_attr<T, 3, 3>();
+  if (!rc) rc = fft_attr<T, 4, 3>();
+  if (!rc) rc = fft_attr<T, 4, 4>();
+  if (!rc) rc = fft_attr<T, 5, 4>();
+  if (!rc) rc = fft_attr<T, 5, 5>();
+  return rc;
+}
+
 int fft_configure() {
-  size_t big = (size_t)(kFftSmemElems + 512) * sizeof(double2);
-  if (cudaFuncSetAttribute(k_fft_pass<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)big) != cudaSuccess)
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&g_fft_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return NUFFT_ECUDA;
-  if (cudaFuncSetAttribute(k_fft_pass<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)big) != cudaSuccess)
-    return NUFFT_ECUDA;
-  return NUFFT_OK;
+  int rc = fft_attrs<double>();
+  if (!rc) rc = fft_attrs<float>();
+  return rc;
 }
 
 template int fft_run<double>(const void*, int, void*, int, double2*, double2*, int64_t, int, int,
