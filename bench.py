@@ -42,6 +42,9 @@ EPS_MIXED = 1e-6
 EPS_FP64 = 1e-12
 JITTER = 0.4
 METRIC = "NUFFT points/s (forward + square inverse, N=M=2^20, mixed eps=1e-6)"
+STAGE_KERNELS = {"targets": "k_targets_fwd + k_targets_grid", "fft": "k_fft_reg",
+                 "m2l": "k_down_top + k_down_sub (+ k_m2l_tc)", "p2m": "k_p2m_* + k_charges",
+                 "m2m": "k_up_sub + k_up_top", "level2": "k_level2"}
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -116,29 +119,59 @@ class ClockSampler:
 
 # ---------------------------------------------------------------- roofline model
 
-def stage_work(stage: str, N: int, M: int, info: dict, prec: int):
-    """Algorithmic work of one launch sequence of a stage for one transform:
-    (flops, bytes, bound).  Counted from the method, not from the code:
-    targets: near field (3s-1) pairs x 4 flops (2 complex-real FMA) + far
-    field p complex-real FMA + regular part 2q complex-real FMA, per target;
-    bytes: read y-data (k0, delta, perm: 16 B) + F, E (32 B) + write g (16 B)."""
+def stage_work(stage: str, N: int, M: int, info: dict, io_bytes: int, fwd: int, bwd: int):
+    """Algorithmic work of a stage per step of `fwd` forward and `bwd`
+    adjoint / inverse sequences (each N grid points, M points, one signal):
+    (flops, bytes, bound), counted from the method, not from the code.
+      fft:     one read and one write of the N values per transform (io_bytes
+               per complex value at the interface, 8 inside the FP32 path)
+      p2m:     N pm (forward) or M pm (adjoint / inverse) complex-real FMA
+               (4 flops each)
+      m2m:     ~B parents x pm^2 complex-real FMA per pass
+      m2l:     ~2B boxes x (3 p^2 + p^2 / 2) complex-real FMA per pass
+      targets: per target (3s - 1) near pairs x 4 flops (the reciprocal
+               counted as one flop) + p + 2q complex-real FMA (far field,
+               regular part)"""
     L, p, q = info["lmax"], info["p"], info["q"]
+    pm = max(p, 2 * q + 1)
     s = N >> L
     B = 1 << L
-    csz = 16
-    if stage == "targets":
-        flops = M * ((3 * s - 1) * 4 + p * 4 + 2 * q * 4)
-        byts = M * (16 + 32 + csz) + B * p * (8 if prec else 16) + N * csz
-        return flops, byts
+    nseq = fwd + bwd
     if stage == "fft":
-        return 5 * N * N_LOG2, 2 * N * csz * 2  # two passes, read + write
-    if stage == "m2l":
-        nb = 2 * B
-        return nb * (3 * p * p * 4 + p * p * 2), nb * p * (8 if prec else 16) * 3
+        return 5 * N * math.log2(N) * nseq, (io_bytes + 8) * N * nseq, "hbm"
     if stage == "p2m":
-        pm = max(p, 2 * q + 1)
-        return N * pm * 4, N * csz + B * pm * (8 if prec else 16)
-    return 0, 0
+        return 4 * (N * fwd + M * bwd) * pm, 0, "alu"
+    if stage == "m2m":
+        return 4 * B * pm * pm * nseq, 0, "alu"
+    if stage == "m2l":
+        return 4 * 2 * B * 3.5 * p * p * nseq, 0, "alu"
+    if stage == "targets":
+        per = (3 * s - 1) * 4 + 4 * p + 8 * q
+        return per * (M * fwd + N * bwd), 0, "alu"
+    return 0, 0, "other"
+
+
+def stage_roofline(stages_ms: dict, N: int, M: int, info: dict, io_bytes: int, fwd: int, bwd: int,
+                   peaks: dict) -> dict:
+    """Per-stage achieved rate against its bound: FP32 ALU (152 SMs x 128
+    lanes x 2 flops x max clock) or HBM (measured copy bandwidth)."""
+    out = {}
+    for st, ms in stages_ms.items():
+        if ms <= 0:
+            continue
+        fl, by, bound = stage_work(st, N, M, info, io_bytes, fwd, bwd)
+        if bound == "hbm":
+            ach = by / (ms / 1e3) / 1e9
+            out[st] = {"ms": ms, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"],
+                       "unit": "GB/s", "frac": ach / peaks["hbm_gbs"]}
+        elif bound == "alu":
+            ach = fl / (ms / 1e3) / 1e12
+            pk = fp32_peak_tflops(peaks)
+            out[st] = {"ms": ms, "bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
+                       "frac": ach / pk}
+        else:
+            out[st] = {"ms": ms, "bound": None}
+    return out
 
 
 def fp32_peak_tflops(peaks):
@@ -288,19 +321,12 @@ def run_ours(args):
     per = {k: v[0] / steps for k, v in stats.items()}
     dom = max(per, key=per.get)
     info = mx["info"]
-    fl, by = stage_work(dom, N, M, info, 1)
-    nseq = 2  # forward + inverse per step
-    t_dom = per[dom] / 1e3
-    if dom == "fft":
-        achieved = by * nseq / t_dom / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s"}
-    else:
-        achieved = fl * nseq / t_dom / 1e12
-        pk = fp32_peak_tflops(peaks)
-        roof = {"bound": "alu", "achieved": achieved, "peak": pk, "unit": "TFLOP/s"}
-    roof["frac"] = roof["achieved"] / roof["peak"]
+    sroof = stage_roofline(per, N, M, info, 16, 1, 1, peaks)
+    r = sroof[dom]
+    roof = {k: r[k] for k in ("bound", "achieved", "peak", "unit", "frac")}
     roof["traffic"] = None
     roof["kernel_stage"] = dom
+    roof["kernels"] = STAGE_KERNELS.get(dom)
     roof["peak_source"] = (f"{peak_src}: " + ("MEASURED_PEAKS hbm_gbs" if roof["bound"] == "hbm" else
                                              "152 SM x 128 FP32 lanes x 2 x sm_max_mhz"))
 
@@ -331,6 +357,7 @@ def run_ours(args):
                    "parallelism": "replicas" if ws > 1 else "1 gpu",
                    "plan_s": mx["t_plan_s"]},
         "stages_ms_per_step": {k: round(v, 5) for k, v in per.items()},
+        "stage_roofline": sroof,
         "fp64": {"eps": EPS_FP64, "ms_per_step": ms_fp64, "value": ws * 2 * M / (ms_fp64 / 1e3),
                  "params": fp["info"], "stages_ms_per_step":
                      {k: round(v[0] / steps, 5) for k, v in fp["stats"].items()},
@@ -346,6 +373,8 @@ def run_ours(args):
     }
     if not args.no_batched:
         out["batched"] = run_batched(tune_params=not args.no_tune)
+    if not args.no_large:
+        out["large"] = run_large(tune_params=not args.no_tune)
     if args.lsq:
         out["inufft_lsq"] = run_lsq()
     print(json.dumps(out))
@@ -428,6 +457,58 @@ def run_batched(steps: int = 5, warmup: int = 3, tune_params: bool = True):
                         "launch": "one CUDA graph (16 forked streams)"}
     multi.close()
     return out
+
+
+def run_large(steps: int = 5, warmup: int = 3, tune_params: bool = True):
+    """Large workload: N = M = 2^24, complex64 data, uniform points, forward
+    + adjoint at eps = 1e-6 (mixed precision), per-stage roofline."""
+    import torch
+
+    import paper_1611_09379_gb300 as nf
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    N = M = 1 << 24
+    y = workloads.points("uniform", M, seed=1238)
+    c = workloads.coeffs(N, seed=34).astype(np.complex64)
+    gin = workloads.samples(M, seed=35).astype(np.complex64)
+    yd = torch.from_numpy(y).cuda()
+    prm, tuned = {}, None
+    if tune_params:
+        from paper_1611_09379_gb300 import tune
+        ent = tune.autotune(N, yd, 1e-6, prec=nf.MIXED, io="c64", ops="fwd+adj", reps=3,
+                            tag="uniform")
+        prm = {k: ent["params"][k] for k in ("lmax", "p", "q", "tc_level")}
+        tuned = {"seconds": ent["seconds"], "formula_ms": ent["trials"][0]["ms"],
+                 "formula_params": ent["trials"][0]["params"]}
+    plan = nf.Plan(N, yd, eps=1e-6, prec=nf.MIXED, io="c64", **prm)
+    cd, gd = torch.from_numpy(c).cuda(), torch.from_numpy(gin).cuda()
+    g = torch.empty(M, dtype=torch.complex64, device="cuda")
+    a = torch.empty(N, dtype=torch.complex64, device="cuda")
+
+    def step():
+        plan.forward(cd, out=g)
+        plan.adjoint(gd, out=a)
+
+    plan.profile(True)
+    ms = _timed(step, flush, stream, steps, warmup)
+    per = {k: v[0] / (steps + warmup) for k, v in plan.stats().items()}
+    peaks, _ = _peaks()
+    info = plan.params()
+    acc = None
+    try:
+        import oracle
+        idx = workloads.sample_index(M, 64)
+        kdx = workloads.sample_index(N, 64, seed=6)
+        acc = {"fwd_rel_l2_sampled": oracle.rel_l2(g.cpu().numpy()[idx],
+                                                   oracle.nudft_fwd(c.astype(complex), y, idx)),
+               "adj_rel_l2_sampled": oracle.rel_l2(a.cpu().numpy()[kdx],
+                                                   oracle.nudft_adj(gin.astype(complex), y, N, kdx))}
+    except Exception as e:
+        acc = repr(e)
+    return {"workload": "forward + adjoint NUFFT, N=M=2^24, complex64, uniform y, mixed eps=1e-6",
+            "ms": ms, "value": 2 * M / (ms / 1e3), "unit": "points/s", "params": info,
+            "tuning": tuned, "stage_roofline": stage_roofline(per, N, M, info, 8, 1, 1, peaks),
+            "accuracy": acc}
 
 
 def run_lsq(maxit: int = 60000):
@@ -529,6 +610,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched workloads")
     ap.add_argument("--no-tune", action="store_true",
                     help="use the formula parameters (Eq. 18.2, 25) instead of the autotuner's")
+    ap.add_argument("--no-large", action="store_true", help="skip the 2^24 forward + adjoint")
     ap.add_argument("--batched-only", action="store_true",
                     help="only the batched workloads (steps / warmup as given)")
     args = ap.parse_args()

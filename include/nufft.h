@@ -302,7 +302,7 @@ enum {
   NUFFT_STAGE_LEVEL2 = 3,   /* regular-part coefficients (Eq. p20) */
   NUFFT_STAGE_M2L = 4,      /* M2L + L2L, levels 3..lmax */
   NUFFT_STAGE_TARGETS = 5,  /* L2P + near field + regular part + F_j / C_k */
-  NUFFT_STAGE_OTHER = 6,    /* type conversions */
+  NUFFT_STAGE_OTHER = 6,    /* self terms of the adjoint / inverse, packing, conversions */
   NUFFT_NSTAGES = 7
 };
 

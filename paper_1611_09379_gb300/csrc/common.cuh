@@ -119,6 +119,7 @@ struct nufft_plan_s {
   float2 *lvl2f = nullptr;        // level-2 coefficients
   // inverse coefficients (Eq. p8), scaled by a common factor
   double2 *Dt = nullptr;          // [M] D_j e^{-Lambda}
+  float2 *Dtf = nullptr;          // [M] FP32 copy (mixed path)
   double *Ct = nullptr;           // [N] real C_k e^{+Lambda} / N
   float *Ctf = nullptr;           // [N] FP32 copy (mixed path)
   double *Lambda = nullptr;       // [1] common scale of C and D

@@ -8,6 +8,8 @@
 // multiply Ns by R until it reaches N.  Twiddles come from two small tables,
 // w^{m/N} = T_hi[m >> b] * T_lo[m & (2^b - 1)], filled once per plan with
 // sincospi of exact arguments.
+#include <cstdint>
+
 #include "common.cuh"
 
 namespace nufft {
@@ -95,35 +97,66 @@ template <int LOG> __device__ constexpr int brev_c(int x) {
 // size-R2 DFTs over t for k1 = u, u + R2, ...; the result goes back through
 // shared memory to out[(j / Ns) Ns R + (j mod Ns) + r' Ns] with contiguous
 // runs (J per r' for Ns >= J, else R per j).
+__device__ inline void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                   (uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
+}
+
 template <class T, int LOG1, int LOG2>
 __global__ void __launch_bounds__(256) k_fft_reg(const void* __restrict__ in, int in_f64,
                                                  void* __restrict__ out, int out_f64, int64_t N,
                                                  int64_t Ns, int J, int logJ, int sign,
-                                                 const cplx<T>* __restrict__ tw, int lo_bits) {
+                                                 const cplx<T>* __restrict__ tw, int lo_bits,
+                                                 int staged) {
   constexpr int R1 = 1 << LOG1, R2 = 1 << LOG2, R = R1 * R2, LOGR = LOG1 + LOG2;
-  extern __shared__ unsigned char smraw[];
+  extern __shared__ __align__(16) unsigned char smraw[];
   cplx<T>* wR = reinterpret_cast<cplx<T>*>(smraw);  // [R] w_R^e
   cplx<T>* S = wR + R;                              // [R][J] (Y[k1][t] / X[r'] by column)
   const int64_t NR = N >> LOGR;
   const int64_t j0 = (int64_t)blockIdx.x * J;
   const int tid = threadIdx.x, nth = blockDim.x;
-  in = (const char*)in + (size_t)blockIdx.y * N * (in_f64 ? 16 : 8);
+  const int esz = in_f64 ? 16 : 8;
+  in = (const char*)in + (size_t)blockIdx.y * N * esz;
   out = (char*)out + (size_t)blockIdx.y * N * (out_f64 ? 16 : 8);
+  // staged: the tile's R rows of J contiguous inputs go to shared memory by
+  // 16-byte asynchronous copies (the whole tile in flight at once); the
+  // region holds R J inputs of esz bytes, reused for Y / X afterwards
+  const int lpr = (J * esz) >> 4;  // 16-byte pieces per row (power of two)
+  if (staged) {
+    int lg = 0;
+    while ((1 << lg) < lpr) ++lg;
+    const char* src = (const char*)in + j0 * esz;
+    char* dstb = reinterpret_cast<char*>(S);
+    for (int e = tid; e < R * lpr; e += nth) {
+      const int r = e >> lg, pc = e & (lpr - 1);
+      cp_async16(dstb + ((size_t)r * J * esz + pc * 16), src + ((size_t)r * NR * esz + pc * 16));
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  }
   for (int e = tid; e < R; e += nth) wR[e] = twiddle_t<T>(tw, (int64_t)e * NR, lo_bits, sign);
   const int c = tid & (J - 1), t = tid >> logJ;
   const int64_t j = j0 + c;
   const int64_t jm = j & (Ns - 1);
-  const int64_t tstep = N / (Ns << LOGR);
+  int logNs = 0;
+  while ((int64_t(1) << logNs) < Ns) ++logNs;
+  int logN = 0;
+  while ((int64_t(1) << logN) < N) ++logN;
+  const int lstep = logN - logNs - LOGR;  // tstep = N / (Ns R) = 2^lstep
+  if (staged) asm volatile("cp.async.wait_group 0;" ::: "memory");
+  __syncthreads();  // wR and the staged tile ready
   // load (columns fastest: J contiguous elements per r) with the pass twiddle
   cplx<T> v[R1];
 #pragma unroll
   for (int m = 0; m < R1; ++m) {
     const int r = t + R2 * m;
-    cplx<T> x = load_c<T>(in, j + (int64_t)r * NR, in_f64);
-    if (jm != 0 && r != 0) x = cmul(x, twiddle_t<T>(tw, ((int64_t)r * jm * tstep) & (N - 1), lo_bits, sign));
+    cplx<T> x = staged ? load_c<T>(S, (int64_t)r * J + c, in_f64)
+                       : load_c<T>(in, j + (int64_t)r * NR, in_f64);
+    if (jm != 0 && r != 0) x = cmul(x, twiddle_t<T>(tw, (((int64_t)r * jm) << lstep) & (N - 1), lo_bits, sign));
     v[brev_c<LOG1>(m)] = x;
   }
-  __syncthreads();  // wR ready
+  __syncthreads();  // all staged inputs read before S is reused
   dft_reg<T, LOG1>(v, wR, R / R1);
   // Y[k1][t] = v[k1] w_R^{t k1}
 #pragma unroll
@@ -161,7 +194,7 @@ __global__ void __launch_bounds__(256) k_fft_reg(const void* __restrict__ in, in
     else { jj = e >> LOGR; r = e & (R - 1); }           // small Ns: R contiguous per j
     const int64_t jg = j0 + jj;
     const int64_t jmg = jg & (Ns - 1);
-    const int64_t dst = (jg / Ns) * Ns * R + jmg + (int64_t)r * Ns;
+    const int64_t dst = ((jg >> logNs) << (logNs + LOGR)) + jmg + ((int64_t)r << logNs);
     store_c<T>(out, dst, out_f64, S[r * J + jj]);
   }
 }
@@ -221,20 +254,20 @@ using FftKernel = void (*)(const void*, int, void*, int, int64_t, int64_t, int, 
 template <class T, int LOG1, int LOG2>
 static void fft_launch(dim3 grid, int threads, size_t smem, cudaStream_t st, const void* in,
                        int in_f64, void* out, int out_f64, int64_t N, int64_t Ns, int J, int logJ,
-                       int sign, const cplx<T>* tw, int lo_bits) {
+                       int sign, const cplx<T>* tw, int lo_bits, int staged) {
   k_fft_reg<T, LOG1, LOG2><<<grid, threads, smem, st>>>(in, in_f64, out, out_f64, N, Ns, J, logJ,
-                                                         sign, tw, lo_bits);
+                                                         sign, tw, lo_bits, staged);
 }
 
 // the pass kernel for logR = LOG1 + LOG2 (LOG1 = ceil(logR / 2))
 template <class T>
 static int fft_pass(int logR, dim3 grid, int threads, size_t smem, cudaStream_t st,
                     const void* in, int in_f64, void* out, int out_f64, int64_t N, int64_t Ns,
-                    int J, int logJ, int sign, const cplx<T>* tw, int lo_bits) {
+                    int J, int logJ, int sign, const cplx<T>* tw, int lo_bits, int staged) {
 #define NUFFT_FFT_CASE(L1, L2)                                                                 \
   case L1 + L2:                                                                                \
     fft_launch<T, L1, L2>(grid, threads, smem, st, in, in_f64, out, out_f64, N, Ns, J, logJ, \
-                          sign, tw, lo_bits);                                                  \
+                          sign, tw, lo_bits, staged);                                          \
     return NUFFT_OK;
   switch (logR) {
     NUFFT_FFT_CASE(1, 0)
@@ -287,10 +320,14 @@ int fft_run(const void* in, int in_f64, void* out, int out_f64, cplx<T>* buf, cp
     if (J > NR) J = (int)NR;
     int logJ = 0;
     while ((1 << logJ) < J) ++logJ;
-    size_t smem = (size_t)(R + R * J) * sizeof(cplx<T>);
+    // staged input: 16-byte aligned rows of at least 16 bytes
+    const size_t esz = src_f64 ? 16 : 8;
+    const int staged = ((uintptr_t)src % 16 == 0) && (J * esz >= 16);
+    const size_t elem = staged && esz > sizeof(cplx<T>) ? esz : sizeof(cplx<T>);
+    size_t smem = (size_t)R * sizeof(cplx<T>) + (size_t)R * J * elem;
     unsigned grid = (unsigned)(NR / J);
     int rc = fft_pass<T>(lr, dim3(grid, (unsigned)batch), J * R2, smem, st, src, src_f64, dst,
-                         dst_f64, N, Ns, J, logJ, sign, tw, b);
+                         dst_f64, N, Ns, J, logJ, sign, tw, b, staged);
     if (rc) return rc;
     src = dst;
     src_f64 = dst_f64;
@@ -301,7 +338,7 @@ int fft_run(const void* in, int in_f64, void* out, int out_f64, cplx<T>* buf, cp
 
 template <class T, int LOG1, int LOG2>
 static int fft_attr() {
-  const int big = (int)((kFftSmemElems + 1024) * sizeof(cplx<T>));
+  const int big = (int)(kFftSmemElems * 16 + 1024 * sizeof(cplx<T>));
   return cudaFuncSetAttribute(k_fft_reg<T, LOG1, LOG2>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize, big) == cudaSuccess
              ? NUFFT_OK : NUFFT_ECUDA;

@@ -62,11 +62,14 @@ __device__ inline void point_local(int k0, double delta, int N, int s, int* leaf
 // q rho^m for 32 consecutive m into shared memory, lanes then reduce rows.
 template <class T> struct P2mWarps { static constexpr int value = sizeof(T) == 8 ? 2 : 4; };
 
+// rho = (o + delta) / s - 1/2 in T: 1/s is a power of two, so the only
+// roundings are of o + delta and of the final subtraction (no division).
 template <class T>
 __global__ void __launch_bounds__(128) k_p2m_nonuniform(TreeDims d,
                                                         const int32_t* __restrict__ start,
                                                         const int32_t* __restrict__ k0,
                                                         const double* __restrict__ delta,
+                                                        const T* __restrict__ delta_t,
                                                         const cplx<T>* __restrict__ charge,
                                                         cplx<T>* __restrict__ mleaf) {
   constexpr int WPB = P2mWarps<T>::value;  // keeps the tile under 48 KB
@@ -79,6 +82,7 @@ __global__ void __launch_bounds__(128) k_p2m_nonuniform(TreeDims d,
   mleaf += blockIdx.y * d.mstride;
   int32_t a = start[b], e = start[b + 1];
   const int N = (int)d.N;
+  const T inv_s = (T)1 / (T)d.s;
   for (int mc = 0; mc < d.pm; mc += 32) {
     T accr = 0, acci = 0;
     for (int c0 = a; c0 < e; c0 += 32) {
@@ -88,7 +92,7 @@ __global__ void __launch_bounds__(128) k_p2m_nonuniform(TreeDims d,
       if (i < e) {
         int lb, o;
         point_local(k0[i], delta[i], N, d.s, &lb, &o);
-        rho = (T)(((double)o + delta[i]) / (double)d.s - 0.5);
+        rho = fma((T)o + delta_t[i], inv_s, (T)-0.5);
         q = charge[i];
       }
       T pw = 1;
@@ -441,7 +445,8 @@ __device__ inline float int_to_t(int D, float) {
 __device__ inline double int_to_t(int D, double) { return (double)D; }
 
 // 1/t: FP32 reciprocal on the special-function unit (rcp.approx, 1 ulp), or
-// FP64 division.
+// FP64 division (measured faster on this GPU than an FP32 estimate refined by
+// Newton steps in FP64, whose two precision conversions run at the FP64 rate).
 __device__ inline float rcp_t(float t) {
   float r;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(t));
@@ -502,15 +507,21 @@ template <class T, int G> struct NearCap {
   static constexpr size_t grid_bytes = (size_t)grid * (1 + 2 * G) * sizeof(cplx<T>);
 };
 
-// Near-field sum of one target over a staged window in chunks of 16 terms
-// folded into the compensated total (NearAcc).  `term(i, acc)` adds term i.
+// Near-field sum of one target over window indices [lo, hi): full chunks of
+// 16 terms (unrolled, no predicates), then the tail, each chunk folded into
+// the compensated total (NearAcc).  term(i, u) adds term i + u; u is a
+// compile-time constant inside full chunks.
 template <class T, int G, class Term>
 __device__ inline void near_window(int lo, int hi, NearAcc<T>* acc, Term term) {
-  for (int i = lo; i < hi; i += 16) {
-    const int n = hi - i < 16 ? hi - i : 16;
+  int i = lo;
+  for (; i + 16 <= hi; i += 16) {
 #pragma unroll
-    for (int u = 0; u < 16; ++u)
-      if (u < n) term(i + u);
+    for (int u = 0; u < 16; ++u) term(i, u);
+#pragma unroll
+    for (int gg = 0; gg < G; ++gg) acc[gg].fold();
+  }
+  if (i < hi) {
+    for (int u = 0; u < hi - i; ++u) term(i, u);
 #pragma unroll
     for (int gg = 0; gg < G; ++gg) acc[gg].fold();
   }
@@ -576,22 +587,23 @@ __global__ void __launch_bounds__(kTgtThreads) k_targets_fwd(
   NearAcc<T> acc[G];
   // c-th sample of the target's 3 leaves: D = k0 - k = (o + s) - c
   const T D0 = (T)(o + s);
+  // per chunk: Di = D0 - i (exact); per term: t0 = Di - u (exact), t = t0 + delta
   if (staged && b >= bl && b <= bh) {
     const cplx<T>* w = sf + (b - bl) * s;  // leaf b - 1 of the window
-    near_window<T, G>(0, 3 * s, acc, [&](int c) {
-      const T t0 = D0 - (T)c;
+    near_window<T, G>(0, 3 * s, acc, [&](int i, int u) {
+      const T t0 = (D0 - (T)i) - (T)u;
       T r = rcp_t(t0 + dt);
       r = t0 == (T)0 ? (T)0 : r;  // the pair with x_k0: E_j carries it
 #pragma unroll
-      for (int gg = 0; gg < G; ++gg) acc[gg].add_r(w[gg * nwin + c], r);
+      for (int gg = 0; gg < G; ++gg) acc[gg].add_r(w[gg * nwin + i + u], r);
     });
   } else {
     const int base = (b - 1) * s;
-    near_window<T, G>(0, 3 * s, acc, [&](int c) {
-      const T t0 = D0 - (T)c;
+    near_window<T, G>(0, 3 * s, acc, [&](int i, int u) {
+      const T t0 = (D0 - (T)i) - (T)u;
       T r = rcp_t(t0 + dt);
       r = t0 == (T)0 ? (T)0 : r;
-      const int k = (base + c + N) & (N - 1);
+      const int k = (base + i + u + N) & (N - 1);
 #pragma unroll
       for (int gg = 0; gg < G; ++gg) acc[gg].add_r(fgrid[(int64_t)gg * N + k], r);
     });
@@ -632,16 +644,16 @@ __global__ void __launch_bounds__(kTgtThreads) k_targets_fwd(
 // Signal blockIdx.y: samples and charges at stride M.
 template <class T, class VI>
 __global__ void k_charges(int64_t M, const int32_t* __restrict__ perm,
-                          const double2* __restrict__ coef, int conj_coef,
+                          const cplx<T>* __restrict__ coef, int conj_coef,
                           const VI* __restrict__ gin, cplx<T>* __restrict__ charge) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= M) return;
   gin += blockIdx.y * M;
   charge += blockIdx.y * M;
-  double2 c = coef[i];
+  cplx<T> c = coef[i];
   if (conj_coef) c.y = -c.y;
-  double2 gv = to_d2(gin[perm[i]]);
-  charge[i] = from_d2<T>(cmul(c, gv));
+  const VI gr = gin[perm[i]];
+  charge[i] = cmul(c, mk<T>((T)gr.x, (T)gr.y));
 }
 
 // The pair (y_j, x_k0) of each source j with its nearest grid point, one
@@ -653,11 +665,14 @@ __global__ void k_charges(int64_t M, const int32_t* __restrict__ perm,
 //            Ct_k0 (i/2) (N/pi) q_j / delta_j, formed in FP64 (finite, as Ct_k0
 //            carries sin((x_k0 - y_j)/2)); g_j / N at an exact hit, where
 //            Ct_k0 = 0 removes every other term.
+//   The FP32 path forms Ct_k0 / delta_j in FP32 when |delta_j| >= 2^-20 and
+//   |Ct_k0| >= 2^-100 (no underflow or overflow on the way), else in FP64.
 template <class T, class VI>
 __global__ void k_self_terms(int M, int inverse, int N, const int32_t* __restrict__ k0s,
                              const double* __restrict__ dels, const int32_t* __restrict__ perm,
                              const cplx<T>* __restrict__ E, const cplx<T>* __restrict__ charge,
                              const VI* __restrict__ gin, const double* __restrict__ Ct,
+                             const T* __restrict__ Ctt, const T* __restrict__ delt,
                              cplx<T>* __restrict__ st) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= M) return;
@@ -668,13 +683,24 @@ __global__ void k_self_terms(int M, int inverse, int N, const int32_t* __restric
     st[i] = cmul(cconj(E[i]), from_d2<T>(to_d2(gin[perm[i]])));
     return;
   }
+  const T dt = delt[i];
+  const int k0 = k0s[i];
+  if (sizeof(T) == 4) {
+    const T ct = Ctt[k0];
+    if (fabs(dt) >= (T)9.5367431640625e-07 && fabs(ct) >= (T)7.888609052210118e-31) {
+      const cplx<T> q = charge[i];
+      const T w = (ct / dt) * (T)(0.5 * (double)N * kInvPi);
+      st[i] = mk<T>(-q.y * w, q.x * w);
+      return;
+    }
+  }
   double d = dels[i];
   double2 v;
   if (d == 0.0) {
     v = cscale(to_d2(gin[perm[i]]), 1.0 / (double)N);
   } else {
     double2 q = to_d2(charge[i]);
-    double w = Ct[k0s[i]] * (0.5 * (double)N * kInvPi) / d;
+    double w = Ct[k0] * (0.5 * (double)N * kInvPi) / d;
     v = make_double2(-q.y * w, q.x * w);
   }
   st[i] = from_d2<T>(v);
@@ -789,17 +815,18 @@ __global__ void __launch_bounds__(kTgtThreads) k_targets_grid(
     __syncthreads();
     const int lo = (wlo > c0 ? wlo : c0) - c0, hi = (whi < c1 ? whi : c1) - c0;
     if (act && lo < hi) {
-      near_window<T, G>(lo, hi, acc, [&](int i) {
-        const cplx<T> rp = srel[i];
+      near_window<T, G>(lo, hi, acc, [&](int i, int u) {
+        const cplx<T> rp = srel[i + u];
         const T t0 = kf - rp.x;
         T r = rcp_t(t0 - rp.y);
-        if (t0 == (T)0) {  // k0_j = k: the pair's self term replaces it
-          r = (T)0;
+        const bool hit = t0 == (T)0;  // k0_j = k: the pair's self term replaces it
+        r = hit ? (T)0 : r;
+        if (hit) {
 #pragma unroll
-          for (int gg = 0; gg < G; ++gg) self[gg] = cadd(self[gg], sst[gg * CAP + i]);
+          for (int gg = 0; gg < G; ++gg) self[gg] = cadd(self[gg], sst[gg * CAP + i + u]);
         }
 #pragma unroll
-        for (int gg = 0; gg < G; ++gg) acc[gg].add_r(sq[gg * CAP + i], r);
+        for (int gg = 0; gg < G; ++gg) acc[gg].add_r(sq[gg * CAP + i + u], r);
       });
     }
   }
@@ -881,6 +908,25 @@ TreeDims dims_of(const nufft_plan_s* pl) {
   return d;
 }
 
+// the plan's per-point data in the arithmetic type T
+template <class T> struct PlanT;
+template <> struct PlanT<double> {
+  static const double* delta(nufft_plan_s* pl) { return pl->delta; }
+  static const double2* D(nufft_plan_s* pl) { return pl->Dt; }
+  static const double2* F(nufft_plan_s* pl) { return pl->F; }
+  static const double2* E(nufft_plan_s* pl) { return pl->E; }
+  static const double2* lvl2(nufft_plan_s* pl) { return pl->lvl2; }
+  static const double* Ct(nufft_plan_s* pl) { return pl->Ct; }
+};
+template <> struct PlanT<float> {
+  static const float* delta(nufft_plan_s* pl) { return pl->delta_f; }
+  static const float2* D(nufft_plan_s* pl) { return pl->Dtf; }
+  static const float2* F(nufft_plan_s* pl) { return pl->Ff; }
+  static const float2* E(nufft_plan_s* pl) { return pl->Ef; }
+  static const float2* lvl2(nufft_plan_s* pl) { return pl->lvl2f; }
+  static const float* Ct(nufft_plan_s* pl) { return pl->Ctf; }
+};
+
 // Upward pass + far field + level-2 coefficients for charges already laid out
 // (uniform: on the grid, `charge` = the grid samples; non-uniform: sorted);
 // all signals of the plan at once (grid y = signal).
@@ -901,7 +947,7 @@ int fmm_upward_downward(nufft_plan_s* pl, const FmmOps& ops, bool uniform_source
   } else {
     constexpr int WPB = P2mWarps<T>::value;
     k_p2m_nonuniform<T><<<dim3(nblk(B, WPB), nsig), 32 * WPB, 0, st>>>(
-        d, pl->leaf_start, pl->k0, pl->delta, charge, mleaf);
+        d, pl->leaf_start, pl->k0, pl->delta, PlanT<T>::delta(pl), charge, mleaf);
   }
   if (ops.leaf_shift)
     k_leaf_shift<T><<<nblk(B * pl->pm, 256), 256, 0, st>>>(B, pl->pm, ops.leaf_shift, mleaf);
@@ -984,21 +1030,6 @@ static FmmOps cot_ops(nufft_plan_s* pl) {
   return o;
 }
 
-// the plan's per-point data in the arithmetic type T
-template <class T> struct PlanT;
-template <> struct PlanT<double> {
-  static const double2* F(nufft_plan_s* pl) { return pl->F; }
-  static const double2* E(nufft_plan_s* pl) { return pl->E; }
-  static const double2* lvl2(nufft_plan_s* pl) { return pl->lvl2; }
-  static const double* Ct(nufft_plan_s* pl) { return pl->Ct; }
-};
-template <> struct PlanT<float> {
-  static const float2* F(nufft_plan_s* pl) { return pl->Ff; }
-  static const float2* E(nufft_plan_s* pl) { return pl->Ef; }
-  static const float2* lvl2(nufft_plan_s* pl) { return pl->lvl2f; }
-  static const float* Ct(nufft_plan_s* pl) { return pl->Ctf; }
-};
-
 template <class T, class VO, int G>
 static void launch_targets_fwd(nufft_plan_s* pl, const TreeDims& d, const cplx<T>* f, void* g) {
   dim3 grid(nblk(pl->M, kTgtThreads), (unsigned)(pl->batch / G));
@@ -1034,7 +1065,7 @@ template <class T>
 int fmm_to_grid(nufft_plan_s* pl, const void* g, int inverse) {
   cudaStream_t st = pl->stream;
   bool c64 = (pl->flags & NUFFT_IO_C64) != 0;
-  const double2* coef = inverse ? pl->Dt : pl->F;
+  const cplx<T>* coef = inverse ? PlanT<T>::D(pl) : PlanT<T>::F(pl);
   cplx<T>* charge = (cplx<T>*)pl->charge;
   const unsigned nsig = (unsigned)pl->batch;
   const dim3 gm(nblk(pl->M, 256), nsig);
@@ -1052,16 +1083,20 @@ int fmm_to_grid(nufft_plan_s* pl, const void* g, int inverse) {
   const TreeDims d = dims_of(pl);
   cplx<T>* stt = (cplx<T>*)pl->selft;
   SrcPos<T>* pos = (SrcPos<T>*)pl->srcpos;
-  prof_begin(pl, NUFFT_STAGE_TARGETS);
+  prof_begin(pl, NUFFT_STAGE_OTHER);
   if (c64)
     k_self_terms<T, float2><<<gm, 256, 0, st>>>((int)pl->M, inverse, (int)pl->N, pl->k0,
                                                pl->delta, pl->perm, PlanT<T>::E(pl), charge,
-                                               (const float2*)g, pl->Ct, stt);
+                                               (const float2*)g, pl->Ct, PlanT<T>::Ct(pl),
+                                               PlanT<T>::delta(pl), stt);
   else
     k_self_terms<T, double2><<<gm, 256, 0, st>>>((int)pl->M, inverse, (int)pl->N, pl->k0,
                                                 pl->delta, pl->perm, PlanT<T>::E(pl), charge,
-                                                (const double2*)g, pl->Ct, stt);
+                                                (const double2*)g, pl->Ct, PlanT<T>::Ct(pl),
+                                                PlanT<T>::delta(pl), stt);
   k_pack_positions<T><<<nblk(pl->M, 256), 256, 0, st>>>((int)pl->M, pl->k0, pl->delta, pos);
+  prof_end(pl, 2);
+  prof_begin(pl, NUFFT_STAGE_TARGETS);
   if (pl->batch % 4 == 0)
     k_targets_grid<T, 4><<<dim3(nblk(pl->N, kTgtThreads), nsig / 4), kTgtThreads,
                            NearCap<T, 4>::grid_bytes, st>>>(
@@ -1072,7 +1107,7 @@ int fmm_to_grid(nufft_plan_s* pl, const void* g, int inverse) {
                            NearCap<T, 1>::grid_bytes, st>>>(
         d, inverse, pl->leaf_start, pos, charge, stt, (const cplx<T>*)pl->lexp,
         PlanT<T>::lvl2(pl), PlanT<T>::Ct(pl), (cplx<T>*)pl->grid);
-  prof_end(pl, 3);
+  prof_end(pl, 1);
   return cudaGetLastError() == cudaSuccess ? NUFFT_OK : NUFFT_ECUDA;
 }
 

@@ -226,7 +226,8 @@ __global__ void k_assemble_C(const double* __restrict__ lamC, const int32_t* __r
 __global__ void k_assemble_D(const double* __restrict__ lamD, const int32_t* __restrict__ nD,
                              const int32_t* __restrict__ k0s, const double* __restrict__ dels,
                              int64_t M, const double* __restrict__ Lam, double elim,
-                             double2* __restrict__ Dt, int* __restrict__ status) {
+                             double2* __restrict__ Dt, float2* __restrict__ Dtf,
+                             int* __restrict__ status) {
   int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= M) return;
   double e = lamD[j] - *Lam;
@@ -237,6 +238,7 @@ __global__ void k_assemble_D(const double* __restrict__ lamD, const int32_t* __r
   sincospi(dels[j], &sn, &cs);
   // i e^{-i N y_j / 2} = (-1)^k0 (sin(pi delta) + i cos(pi delta))
   Dt[j] = make_double2(mag * sn, mag * cs);
+  if (Dtf) Dtf[j] = make_float2((float)(mag * sn), (float)(mag * cs));
 }
 
 inline unsigned nblk(int64_t n, int th) { return (unsigned)((n + th - 1) / th); }
@@ -311,7 +313,8 @@ int inverse_precompute(nufft_plan_s* pl, void* tmp, size_t tmp_bytes) {
   if (cudaMalloc((void**)&pl->Ct, N * 8) != cudaSuccess) return NUFFT_ENOMEM;
   if (cudaMalloc((void**)&pl->Dt, M * 16) != cudaSuccess) return NUFFT_ENOMEM;
   if (cudaMalloc((void**)&pl->Lambda, 8) != cudaSuccess) return NUFFT_ENOMEM;
-  if (pl->prec != NUFFT_FP64 && cudaMalloc((void**)&pl->Ctf, N * 4) != cudaSuccess)
+  if (pl->prec != NUFFT_FP64 && (cudaMalloc((void**)&pl->Ctf, N * 4) != cudaSuccess ||
+                                 cudaMalloc((void**)&pl->Dtf, M * 8) != cudaSuccess))
     return NUFFT_ENOMEM;
   // ---- operators of the log kernel (host, long double)
   Bin C(2 * 64 + 2);
@@ -404,6 +407,6 @@ int inverse_precompute(nufft_plan_s* pl, void* tmp, size_t tmp_bytes) {
   double elim = pl->prec == NUFFT_FP64 ? kExpLimit : 60.0;
   k_assemble_C<<<nblk(N, 256), 256, 0, st>>>(lamC, nC, N, Lam, elim, pl->Ct, pl->Ctf, pl->status);
   k_assemble_D<<<nblk(M, 256), 256, 0, st>>>(lamD, nD, pl->k0, pl->delta, M, Lam, elim, pl->Dt,
-                                             pl->status);
+                                             pl->Dtf, pl->status);
   return cudaGetLastError() == cudaSuccess ? NUFFT_OK : NUFFT_ECUDA;
 }
