@@ -62,6 +62,7 @@ typedef enum {
 /* plan flags */
 #define NUFFT_IO_C64 0x1u        /* caller data are complex64 instead of complex128 */
 #define NUFFT_WANT_INVERSE 0x2u  /* precompute C_k, D_j (Eq. p8) for exec_inv (M == N) */
+#define NUFFT_NO_GRAPH 0x4u      /* launch exec kernels one by one (no CUDA graph replay) */
 
 /* Opaque plan: the "data structure" of the paper (Sec. 3.3): the binned point
  * set, F_j, optionally C_k / D_j, the expansion workspace and the FMM
@@ -161,7 +162,11 @@ int nufft_autotune(int64_t N, int64_t M, const double *y, double eps, int prec,
  *   eps              requested accuracy in [1e-15, 1e-1]
  *   prec             nufft_prec
  *   params  [host]   optional overrides (NULL = automatic)
- *   flags            NUFFT_IO_C64 | NUFFT_WANT_INVERSE
+ *   flags            NUFFT_IO_C64 | NUFFT_WANT_INVERSE | NUFFT_NO_GRAPH
+ * Exec calls replay a CUDA graph of their kernel sequence, captured on the
+ * first call with the same operation and buffer pointers (up to 8 kept per
+ * plan); they launch kernels one by one instead while profiling is enabled,
+ * while the stream is being captured by the caller, or with NUFFT_NO_GRAPH.
  *   stream           cudaStream_t to run on (NULL = legacy default stream)
  * Synchronises the stream (it reads back validation flags).  Errors:
  * EINVAL (bad sizes / eps / y), EILLCOND (inverse requested with duplicate

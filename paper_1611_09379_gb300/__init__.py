@@ -31,6 +31,7 @@ STAGES = ("fft", "p2m", "m2m", "level2", "m2l", "targets", "other")
 FP64, MIXED = 0, 1
 IO_C64 = 0x1
 WANT_INVERSE = 0x2
+NO_GRAPH = 0x4
 
 # every symbol declared in include/nufft.h
 SYMBOLS = [
@@ -178,11 +179,12 @@ class Plan:
     batch: signals sharing the points; exec calls take [batch, N] / [batch, M].
     tc_level: first tree level whose M2L runs on the tensor cores (MIXED only;
     0 = automatic, -1 = never).
+    graphs: replay exec sequences as CUDA graphs (captured per buffer set).
     """
 
     def __init__(self, N: int, y, eps: float = 1e-12, prec: int = FP64, io: str = "c128",
                  inverse: bool = False, lmax: int = 0, p: int = 0, q: int = 0, batch: int = 1,
-                 tc_level: int = 0, stream=None):
+                 tc_level: int = 0, graphs: bool = True, stream=None):
         torch = _torch()
         self.N = int(N)
         self.M = int(y.numel())
@@ -190,7 +192,8 @@ class Plan:
         self.io = io
         self.cdtype = torch.complex64 if io == "c64" else torch.complex128
         self.batch = int(batch)
-        flags = (IO_C64 if io == "c64" else 0) | (WANT_INVERSE if inverse else 0)
+        flags = ((IO_C64 if io == "c64" else 0) | (WANT_INVERSE if inverse else 0) |
+                 (0 if graphs else NO_GRAPH))
         self._stream = stream
         h = _P()
         prm = Params(lmax, p, q, self.batch, tc_level)

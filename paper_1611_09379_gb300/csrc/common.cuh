@@ -149,6 +149,17 @@ struct nufft_plan_s {
   int *seg_overflow = nullptr;
   StageProf *prof = nullptr;
   void *lsq_work = nullptr;  // CG work vectors (created on first least-squares solve)
+  // exec sequences captured as CUDA graphs, keyed by operation and buffers
+  struct GraphEntry {
+    int op = -1;
+    const void* in = nullptr;
+    void* out = nullptr;
+    cudaGraphExec_t exec = nullptr;
+  };
+  static constexpr int kGraphSlots = 8;
+  GraphEntry graphs[kGraphSlots];
+  int graph_next = 0;            // slot replaced next (round robin)
+  cudaStream_t cap = nullptr;    // private capture origin
 };
 
 // Bracket the launches of one stage (no-ops unless profiling is enabled).

@@ -204,6 +204,9 @@ void free_plan(nufft_plan_s* pl) {
                   pl->seg_overflow, pl->lsq_work, pl->op_tc};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  for (auto& gr : pl->graphs)
+    if (gr.exec) cudaGraphExecDestroy(gr.exec);
+  if (pl->cap) cudaStreamDestroy(pl->cap);
   if (pl->prof) {
     for (cudaEvent_t e : pl->prof->ev)
       if (e) cudaEventDestroy(e);
@@ -347,6 +350,7 @@ int nufft_plan_create(nufft_plan* out, int64_t N, int64_t M, const double* y, do
   if (params) prm = *params;
   int rc = nufft_choose_params(N, M, eps, prec, &prm);
   if (rc) return rc;
+  if (flags & ~(NUFFT_IO_C64 | NUFFT_WANT_INVERSE | NUFFT_NO_GRAPH)) return NUFFT_EINVAL;
   if ((flags & NUFFT_WANT_INVERSE) && M != N) return NUFFT_EINVAL;
   const int64_t nb = prm.batch;
   if ((rc = configure_once())) return rc;
@@ -504,8 +508,7 @@ static int fft_plan(nufft_plan_s* pl, const void* in, int in_f64, void* out, int
   return rc;
 }
 
-int nufft_plan_exec_fwd(nufft_plan pl, const void* c, void* g) {
-  if (!pl || !c || !g) return NUFFT_EINVAL;
+static int exec_fwd_direct(nufft_plan_s* pl, const void* c, void* g) {
   const int io64 = (pl->flags & NUFFT_IO_C64) ? 0 : 1;
   const int t64 = pl->prec == NUFFT_FP64;
   // f_k = sum_n c_n e^{+2 pi i n k/N}  (Eq. p1, unscaled inverse DFT)
@@ -520,25 +523,89 @@ static int grid_to_coeffs(nufft_plan_s* pl, void* c) {
   return fft_plan(pl, pl->grid, pl->prec == NUFFT_FP64, c, io64, -1);
 }
 
-int nufft_plan_exec_adj(nufft_plan pl, const void* g, void* c) {
-  if (!pl || !c || !g) return NUFFT_EINVAL;
+static int exec_adj_direct(nufft_plan_s* pl, const void* g, void* c) {
   int rc = pl->prec == NUFFT_FP64 ? fmm_to_grid<double>(pl, g, 0) : fmm_to_grid<float>(pl, g, 0);
   if (rc) return rc;
   return grid_to_coeffs(pl, c);
 }
 
-int nufft_plan_exec_inv(nufft_plan pl, const void* g, void* c) {
-  if (!pl || !c || !g) return NUFFT_EINVAL;
-  if (!(pl->flags & NUFFT_WANT_INVERSE) || !pl->Ct) return NUFFT_EINVAL;
+static int exec_inv_direct(nufft_plan_s* pl, const void* g, void* c) {
   int rc = pl->prec == NUFFT_FP64 ? fmm_to_grid<double>(pl, g, 1) : fmm_to_grid<float>(pl, g, 1);
   if (rc) return rc;
   return grid_to_coeffs(pl, c);  // the 1/N of Eq. p1 is folded into C_k
+}
+
+// Run exec sequence `op` (0 fwd, 1 adj, 2 inv) on the plan's stream: replay
+// the graph captured for (op, in, out) if there is one, else capture it on
+// the private stream, instantiate and launch it; direct launches while
+// profiling, while the plan's stream is itself capturing, or with
+// NUFFT_NO_GRAPH.
+static int exec_op(nufft_plan_s* pl, int op, const void* in, void* out) {
+  auto direct = [&](nufft_plan_s* q) {
+    return op == 0 ? exec_fwd_direct(q, in, out)
+                   : (op == 1 ? exec_adj_direct(q, in, out) : exec_inv_direct(q, in, out));
+  };
+  bool graph = !(pl->flags & NUFFT_NO_GRAPH) && !(pl->prof && pl->prof->enabled);
+  if (graph) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(pl->stream, &cs) != cudaSuccess) return NUFFT_ECUDA;
+    graph = cs == cudaStreamCaptureStatusNone;
+  }
+  if (!graph) return direct(pl);
+  for (auto& gr : pl->graphs)
+    if (gr.exec && gr.op == op && gr.in == in && gr.out == out)
+      return cudaGraphLaunch(gr.exec, pl->stream) == cudaSuccess ? NUFFT_OK : NUFFT_ECUDA;
+  if (!pl->cap && cudaStreamCreateWithFlags(&pl->cap, cudaStreamNonBlocking) != cudaSuccess) {
+    pl->cap = nullptr;
+    return NUFFT_ECUDA;
+  }
+  cudaStream_t user = pl->stream;
+  if (cudaStreamBeginCapture(pl->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+    return NUFFT_ECUDA;
+  pl->stream = pl->cap;
+  int rc = direct(pl);
+  pl->stream = user;
+  cudaGraph_t g = nullptr;
+  cudaError_t ec = cudaStreamEndCapture(pl->cap, &g);
+  if (rc || ec != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return rc ? rc : NUFFT_ECUDA;
+  }
+  cudaGraphExec_t ex = nullptr;
+  ec = cudaGraphInstantiate(&ex, g, 0);
+  cudaGraphDestroy(g);
+  if (ec != cudaSuccess) return NUFFT_ECUDA;
+  auto& slot = pl->graphs[pl->graph_next];
+  pl->graph_next = (pl->graph_next + 1) % nufft_plan_s::kGraphSlots;
+  if (slot.exec) cudaGraphExecDestroy(slot.exec);
+  slot.op = op;
+  slot.in = in;
+  slot.out = out;
+  slot.exec = ex;
+  return cudaGraphLaunch(ex, pl->stream) == cudaSuccess ? NUFFT_OK : NUFFT_ECUDA;
+}
+
+int nufft_plan_exec_fwd(nufft_plan pl, const void* c, void* g) {
+  if (!pl || !c || !g) return NUFFT_EINVAL;
+  return exec_op(pl, 0, c, g);
+}
+
+int nufft_plan_exec_adj(nufft_plan pl, const void* g, void* c) {
+  if (!pl || !c || !g) return NUFFT_EINVAL;
+  return exec_op(pl, 1, g, c);
+}
+
+int nufft_plan_exec_inv(nufft_plan pl, const void* g, void* c) {
+  if (!pl || !c || !g) return NUFFT_EINVAL;
+  if (!(pl->flags & NUFFT_WANT_INVERSE) || !pl->Ct) return NUFFT_EINVAL;
+  return exec_op(pl, 2, g, c);
 }
 
 static int one_shot(int which, const void* in, int64_t N, const double* y, int64_t M, double eps,
                     int prec, unsigned flags, void* out, void* stream) {
   nufft_plan pl = nullptr;
   if (which == 2) flags |= NUFFT_WANT_INVERSE;
+  flags |= NUFFT_NO_GRAPH;  // one exec: capturing a graph would not pay
   int rc = nufft_plan_create(&pl, N, M, y, eps, prec, nullptr, flags, stream);
   if (rc) return rc;
   if (which == 0) rc = nufft_plan_exec_fwd(pl, in, out);
