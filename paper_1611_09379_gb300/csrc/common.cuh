@@ -49,6 +49,22 @@ template <class T> __device__ inline cplx<T> from_d2(double2 a);
 template <> __device__ inline double2 from_d2<double>(double2 a) { return a; }
 template <> __device__ inline float2 from_d2<float>(double2 a) { return make_float2((float)a.x, (float)a.y); }
 
+// complex128 <-> the arithmetic type (hardware conversions: measured faster
+// here than integer-operation versions of the IEEE-754 conversion)
+template <class T> __device__ inline cplx<T> c128_to(double2 a);
+template <> __device__ inline double2 c128_to<double>(double2 a) { return a; }
+template <> __device__ inline float2 c128_to<float>(double2 a) {
+  return make_float2((float)a.x, (float)a.y);
+}
+__device__ inline double2 to_c128(float2 a) { return make_double2(a.x, a.y); }
+__device__ inline double2 to_c128(double2 a) { return a; }
+
+// delta < 0 for a binary64 delta (-0.0 counts as zero), tested on its bits
+__device__ inline bool neg_bits(double d) {
+  const long long b = __double_as_longlong(d);
+  return b < 0 && b != (long long)0x8000000000000000ull;
+}
+
 // Sizes and pointers of one FMM evaluation, passed by value to kernels.
 struct TreeDims {
   int64_t N;   // grid size (power of two)
@@ -60,6 +76,26 @@ struct TreeDims {
   int64_t mstride = 0;  // per-signal strides (batched plans; blockIdx.y = signal)
   int64_t lstride = 0;  //   multipoles, locals (complex elements)
   int64_t M_ = 0;       //   and points (charges per signal)
+  // per-plan constants formed on the host (kernels need no FP64 division):
+  // 2/N, 1/s, N/pi, N/(2 pi) in both precisions
+  double two_n = 0, inv_s = 0, n_pi = 0, n_2pi = 0;
+  float two_n_f = 0, inv_s_f = 0, n_pi_f = 0, n_2pi_f = 0;
+};
+
+template <class T> struct KConst;
+template <> struct KConst<double> {
+  __device__ static double two_n(const TreeDims& d) { return d.two_n; }
+  __device__ static double inv_s(const TreeDims& d) { return d.inv_s; }
+  __device__ static double n_pi(const TreeDims& d) { return d.n_pi; }
+  __device__ static double n_2pi(const TreeDims& d) { return d.n_2pi; }
+  static double n_2pi_h(const TreeDims& d) { return d.n_2pi; }
+};
+template <> struct KConst<float> {
+  __device__ static float two_n(const TreeDims& d) { return d.two_n_f; }
+  __device__ static float inv_s(const TreeDims& d) { return d.inv_s_f; }
+  __device__ static float n_pi(const TreeDims& d) { return d.n_pi_f; }
+  __device__ static float n_2pi(const TreeDims& d) { return d.n_2pi_f; }
+  static float n_2pi_h(const TreeDims& d) { return d.n_2pi_f; }
 };
 
 // Device-side error word (set by kernels, read back by the host).

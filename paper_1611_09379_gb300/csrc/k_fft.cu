@@ -46,16 +46,13 @@ __device__ inline cplx<T> twiddle_t(const cplx<T>* __restrict__ tw, int64_t m, i
 // *_f64 != 0, complex64 otherwise; arithmetic in T.
 template <class T>
 __device__ inline cplx<T> load_c(const void* p, int64_t i, int f64) {
-  if (f64) {
-    double2 v = reinterpret_cast<const double2*>(p)[i];
-    return mk<T>((T)v.x, (T)v.y);
-  }
+  if (f64) return c128_to<T>(reinterpret_cast<const double2*>(p)[i]);
   float2 v = reinterpret_cast<const float2*>(p)[i];
   return mk<T>((T)v.x, (T)v.y);
 }
 template <class T>
 __device__ inline void store_c(void* p, int64_t i, int f64, cplx<T> v) {
-  if (f64) reinterpret_cast<double2*>(p)[i] = make_double2((double)v.x, (double)v.y);
+  if (f64) reinterpret_cast<double2*>(p)[i] = to_c128(v);
   else reinterpret_cast<float2*>(p)[i] = make_float2((float)v.x, (float)v.y);
 }
 

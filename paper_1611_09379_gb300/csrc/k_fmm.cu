@@ -51,7 +51,7 @@ __global__ void k_p2m_uniform(TreeDims d, const cplx<T>* __restrict__ q,
 // Leaf index and offset of a point from its grid coordinates (int32: N <= 2^26):
 // leaf = floor((k0 + delta)/s) mod 2^L, o = k0 - leaf s in [0, s].
 __device__ inline void point_local(int k0, double delta, int N, int s, int* leaf, int* o) {
-  int fl = (delta < 0.0) ? k0 - 1 : k0;
+  int fl = neg_bits(delta) ? k0 - 1 : k0;
   fl &= (N - 1);
   int b = fl / s;
   *leaf = b;
@@ -277,7 +277,7 @@ __global__ void __launch_bounds__(512) k_down_top(TreeDims d, int lt, const T* _
       Ms[e] = ml[(int64_t)i * pm + m];
     }
     __syncthreads();
-    const T lw = (T)level_logw(log_kernel, log2N, l);
+    const T lw = log_kernel ? (T)level_logw(log_kernel, log2N, l) : (T)0;
     cplx<T>* lout = lexp + (level_off(l) - 4) * p;
     for (int e = threadIdx.x; e < nb * p; e += blockDim.x) {
       int i = e / p, n = e - i * p;
@@ -331,7 +331,7 @@ __global__ void __launch_bounds__(512) k_down_sub(TreeDims d, int lt, int lb,
       Ms[e] = ml[(int64_t)box * pm + m];
     }
     __syncthreads();
-    const T lw = (T)level_logw(log_kernel, log2N, l);
+    const T lw = log_kernel ? (T)level_logw(log_kernel, log2N, l) : (T)0;
     for (int e = threadIdx.x; e < nbx * p; e += blockDim.x) {
       int bi = e / p, n = e - bi * p;
       auto msrc = [&](int off) { return Ms + (bi + 3 + off) * p; };
@@ -364,9 +364,11 @@ __global__ void k_level2(TreeDims d, int nq, const double* __restrict__ op, doub
                          float2* __restrict__ outf) {
   __shared__ double2 mu[4][66];
   __shared__ double2 A1[4][66];
+  extern __shared__ double sop[];  // the four weight tables, staged once
   const cplx<T>* m2 = mexp + blockIdx.x * d.mstride;  // level 2 sits at offset 0
   out += blockIdx.x * (4 * nq + 1);
   if (outf) outf += blockIdx.x * (4 * nq + 1);
+  for (int e = threadIdx.x; e < 4 * nq * nq; e += blockDim.x) sop[e] = op[e];
   for (int e = threadIdx.x; e < 4 * nq; e += blockDim.x) {
     int a = e / nq, i = e - a * nq;
     double2 v = to_d2(m2[a * d.pm + i]);
@@ -374,10 +376,10 @@ __global__ void k_level2(TreeDims d, int nq, const double* __restrict__ op, doub
     mu[a][i] = make_double2(v.x * sc, v.y * sc);
   }
   __syncthreads();
-  const double* W1 = op;
-  const double* W2 = op + nq * nq;
-  const double* Sm = op + 2 * nq * nq;
-  const double* Sp = op + 3 * nq * nq;
+  const double* W1 = sop;
+  const double* W2 = sop + nq * nq;
+  const double* Sm = sop + 2 * nq * nq;
+  const double* Sp = sop + 3 * nq * nq;
   for (int e = threadIdx.x; e < 4 * nq; e += blockDim.x) {
     int n = e / nq, i = e - n * nq;
     double2 acc = mu[n][i];
@@ -424,6 +426,12 @@ __device__ inline cplx<T> horner(const cplx<T>* __restrict__ c, int n, T u) {
   }
   return acc;
 }
+
+// store a result in the caller's element type (complex128 by integer widening)
+__device__ inline void store_cplx(double2* p, float2 v) { *p = to_c128(v); }
+__device__ inline void store_cplx(double2* p, double2 v) { *p = v; }
+__device__ inline void store_cplx(float2* p, float2 v) { *p = v; }
+__device__ inline void store_cplx(float2* p, double2 v) { *p = make_float2((float)v.x, (float)v.y); }
 
 template <class V> __device__ inline void store_out(V* p, double2 v);
 template <> __device__ inline void store_out<double2>(double2* p, double2 v) { *p = v; }
@@ -527,6 +535,31 @@ __device__ inline void near_window(int lo, int hi, NearAcc<T>* acc, Term term) {
   }
 }
 
+// near_window with one known excluded index `ex`: term(i, u, check) gets
+// std::true_type only in the chunk holding ex (and in the tail), so the other
+// chunks carry no compare / select.
+template <class T, int G, class Term>
+__device__ inline void near_window_ex(int lo, int hi, int ex, NearAcc<T>* acc, Term term) {
+  int i = lo;
+  for (; i + 16 <= hi; i += 16) {
+    // (several signals per thread: one variant only, the code would not fit)
+    if (G > 1 || (ex - i >= 0 && ex - i < 16)) {
+#pragma unroll
+      for (int u = 0; u < 16; ++u) term(i, u, std::true_type());
+    } else if (G == 1) {
+#pragma unroll
+      for (int u = 0; u < 16; ++u) term(i, u, std::false_type());
+    }
+#pragma unroll
+    for (int gg = 0; gg < G; ++gg) acc[gg].fold();
+  }
+  if (i < hi) {
+    for (int u = 0; u < hi - i; ++u) term(i, u, std::true_type());
+#pragma unroll
+    for (int gg = 0; gg < G; ++gg) acc[gg].fold();
+  }
+}
+
 // One thread per sorted target j and group of G signals (Eq. p4, p5, p20):
 //   g_j = E_j f_{k0} - (F_j/2) (Q + i h'_j),
 //   h'_j = (N/pi) [ (1/s) sum_n L_n u^n + sum_{near, k != k0} f_k / t ]
@@ -545,7 +578,7 @@ __device__ inline void near_window(int lo, int hi, NearAcc<T>* acc, Term term) {
 template <class T, class VO, int G>
 __global__ void __launch_bounds__(kTgtThreads) k_targets_fwd(
     TreeDims d, int M, const int32_t* __restrict__ k0s, const double* __restrict__ dels,
-    const int32_t* __restrict__ perm, const cplx<T>* __restrict__ F,
+    const T* __restrict__ dels_t, const int32_t* __restrict__ perm, const cplx<T>* __restrict__ F,
     const cplx<T>* __restrict__ E, const cplx<T>* __restrict__ fgrid,
     const cplx<T>* __restrict__ lexp, const cplx<T>* __restrict__ lvl2, VO* __restrict__ g) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -560,11 +593,11 @@ __global__ void __launch_bounds__(kTgtThreads) k_targets_fwd(
   const bool act = j < M;
   const int jl = (j0 + kTgtThreads < M ? j0 + kTgtThreads : M) - 1;
   int k0 = 0, b = 0, o = 0;
-  double dl = 0;
+  T dt = 0;
   if (act) {
     k0 = k0s[j];
-    dl = dels[j];
-    point_local(k0, dl, N, s, &b, &o);
+    point_local(k0, dels[j], N, s, &b, &o);
+    dt = dels_t[j];
   }
   if (threadIdx.x == 0) s_lo = b;
   if (j == jl) s_hi = b;
@@ -583,26 +616,27 @@ __global__ void __launch_bounds__(kTgtThreads) k_targets_fwd(
   }
   __syncthreads();
   if (!act) return;
-  const T dt = (T)dl;
   NearAcc<T> acc[G];
   // c-th sample of the target's 3 leaves: D = k0 - k = (o + s) - c
   const T D0 = (T)(o + s);
   // per chunk: Di = D0 - i (exact); per term: t0 = Di - u (exact), t = t0 + delta
+  // the pair with x_k0 (window index o + s, D = 0) is left out: E_j carries it
+  const int ex = o + s;
   if (staged && b >= bl && b <= bh) {
     const cplx<T>* w = sf + (b - bl) * s;  // leaf b - 1 of the window
-    near_window<T, G>(0, 3 * s, acc, [&](int i, int u) {
+    near_window_ex<T, G>(0, 3 * s, ex, acc, [&](int i, int u, auto chk) {
       const T t0 = (D0 - (T)i) - (T)u;
       T r = rcp_t(t0 + dt);
-      r = t0 == (T)0 ? (T)0 : r;  // the pair with x_k0: E_j carries it
+      if (decltype(chk)::value) r = t0 == (T)0 ? (T)0 : r;
 #pragma unroll
       for (int gg = 0; gg < G; ++gg) acc[gg].add_r(w[gg * nwin + i + u], r);
     });
   } else {
     const int base = (b - 1) * s;
-    near_window<T, G>(0, 3 * s, acc, [&](int i, int u) {
+    near_window_ex<T, G>(0, 3 * s, ex, acc, [&](int i, int u, auto chk) {
       const T t0 = (D0 - (T)i) - (T)u;
       T r = rcp_t(t0 + dt);
-      r = t0 == (T)0 ? (T)0 : r;
+      if (decltype(chk)::value) r = t0 == (T)0 ? (T)0 : r;
       const int k = (base + i + u + N) & (N - 1);
 #pragma unroll
       for (int gg = 0; gg < G; ++gg) acc[gg].add_r(fgrid[(int64_t)gg * N + k], r);
@@ -612,9 +646,10 @@ __global__ void __launch_bounds__(kTgtThreads) k_targets_fwd(
   const int Q2 = 2 * d.q;  // cot kernel: degree 2q-1
   const int arc = b >> (d.L - 2);
   const int I = base + o - arc * (N >> 2) - (N >> 3);
-  const T uh = ((T)I + dt) * (T)(2.0 / (double)N);
-  const T u = ((T)o + dt) * (T)(1.0 / s) - (T)0.5;
-  const T cN = (T)((double)N * kInvPi), ts = (T)(1.0 / s), c2 = (T)(2.0 * kInvPi);
+  const T uh = ((T)I + dt) * KConst<T>::two_n(d);
+  const T ts = KConst<T>::inv_s(d);
+  const T u = fma((T)o + dt, ts, (T)-0.5);
+  const T cN = KConst<T>::n_pi(d), c2 = (T)(2.0 * kInvPi);
   const cplx<T> Fj = F[j], Ej = E[j];
   const int pj = perm[j];
 #pragma unroll
@@ -633,7 +668,7 @@ __global__ void __launch_bounds__(kTgtThreads) k_targets_fwd(
     cplx<T> wv = mk<T>(Qs.x - hi, Qs.y + hr);
     cplx<T> res = cscale(cmul(Fj, wv), (T)-0.5);
     res = cadd(res, cmul(Ej, fgrid[(int64_t)gg * N + k0]));
-    store_out<VO>(g + (int64_t)sig * M + pj, to_d2(res));
+    store_cplx(g + (int64_t)sig * M + pj, res);
   }
 }
 
@@ -642,6 +677,13 @@ __global__ void __launch_bounds__(kTgtThreads) k_targets_fwd(
 // Charges in sorted order: adjoint q_i = conj(F_i) g_perm(i);
 // inverse q_i = Dt_i g_perm(i) (Eq. p6: D_j g_j, scaled by e^{-Lambda}).
 // Signal blockIdx.y: samples and charges at stride M.
+// caller samples (complex64 or complex128) in the arithmetic type
+template <class T> __device__ inline cplx<T> load_in(const double2* p) { return c128_to<T>(*p); }
+template <class T> __device__ inline cplx<T> load_in(const float2* p) {
+  const float2 v = *p;
+  return mk<T>((T)v.x, (T)v.y);
+}
+
 template <class T, class VI>
 __global__ void k_charges(int64_t M, const int32_t* __restrict__ perm,
                           const cplx<T>* __restrict__ coef, int conj_coef,
@@ -652,8 +694,7 @@ __global__ void k_charges(int64_t M, const int32_t* __restrict__ perm,
   charge += blockIdx.y * M;
   cplx<T> c = coef[i];
   if (conj_coef) c.y = -c.y;
-  const VI gr = gin[perm[i]];
-  charge[i] = cmul(c, mk<T>((T)gr.x, (T)gr.y));
+  charge[i] = cmul(c, load_in<T>(gin + perm[i]));
 }
 
 // The pair (y_j, x_k0) of each source j with its nearest grid point, one
@@ -672,7 +713,7 @@ __global__ void k_self_terms(int M, int inverse, int N, const int32_t* __restric
                              const double* __restrict__ dels, const int32_t* __restrict__ perm,
                              const cplx<T>* __restrict__ E, const cplx<T>* __restrict__ charge,
                              const VI* __restrict__ gin, const double* __restrict__ Ct,
-                             const T* __restrict__ Ctt, const T* __restrict__ delt,
+                             const T* __restrict__ Ctt, const T* __restrict__ delt, T n_2pi,
                              cplx<T>* __restrict__ st) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= M) return;
@@ -680,7 +721,7 @@ __global__ void k_self_terms(int M, int inverse, int N, const int32_t* __restric
   charge += (int64_t)blockIdx.y * M;
   st += (int64_t)blockIdx.y * M;
   if (!inverse) {
-    st[i] = cmul(cconj(E[i]), from_d2<T>(to_d2(gin[perm[i]])));
+    st[i] = cmul(cconj(E[i]), load_in<T>(gin + perm[i]));
     return;
   }
   const T dt = delt[i];
@@ -689,7 +730,7 @@ __global__ void k_self_terms(int M, int inverse, int N, const int32_t* __restric
     const T ct = Ctt[k0];
     if (fabs(dt) >= (T)9.5367431640625e-07 && fabs(ct) >= (T)7.888609052210118e-31) {
       const cplx<T> q = charge[i];
-      const T w = (ct / dt) * (T)(0.5 * (double)N * kInvPi);
+      const T w = (ct / dt) * n_2pi;
       st[i] = mk<T>(-q.y * w, q.x * w);
       return;
     }
@@ -835,9 +876,10 @@ __global__ void __launch_bounds__(kTgtThreads) k_targets_grid(
   const int Q2 = 2 * d.q;
   const int arc = b >> (d.L - 2);
   const int I = k - arc * (N >> 2) - (N >> 3);
-  const T uh = (T)I * (T)(2.0 / (double)N);
-  const T u = (T)o * (T)(1.0 / s) - (T)0.5;
-  const T cN = (T)((double)N * kInvPi), ts = (T)(1.0 / s), c2 = (T)(2.0 * kInvPi);
+  const T uh = (T)I * KConst<T>::two_n(d);
+  const T ts = KConst<T>::inv_s(d);
+  const T u = fma((T)o, ts, (T)-0.5);
+  const T cN = KConst<T>::n_pi(d), c2 = (T)(2.0 * kInvPi);
 #pragma unroll
   for (int gg = 0; gg < G; ++gg) {
     const int sig = sig0 + gg;
@@ -894,7 +936,9 @@ int fmm_configure() {
       cudaFuncSetAttribute(k_down_top<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big) !=
           cudaSuccess ||
       cudaFuncSetAttribute(k_down_sub<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big) !=
-          cudaSuccess)
+          cudaSuccess ||
+      cudaFuncSetAttribute(k_level2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           4 * 66 * 66 * (int)sizeof(double)) != cudaSuccess)
     return NUFFT_ECUDA;
   return NUFFT_OK;
 }
@@ -905,6 +949,14 @@ TreeDims dims_of(const nufft_plan_s* pl) {
   int64_t nl = (int64_t(2) << pl->L) - 8;
   d.lstride = (nl > 0 ? nl : 1) * pl->p;
   d.M_ = pl->M;
+  d.two_n = 2.0 / (double)pl->N;
+  d.inv_s = 1.0 / (double)pl->s;
+  d.n_pi = (double)pl->N * kInvPi;
+  d.n_2pi = 0.5 * (double)pl->N * kInvPi;
+  d.two_n_f = (float)d.two_n;
+  d.inv_s_f = (float)d.inv_s;
+  d.n_pi_f = (float)d.n_pi;
+  d.n_2pi_f = (float)d.n_2pi;
   return d;
 }
 
@@ -973,7 +1025,8 @@ int fmm_upward_downward(nufft_plan_s* pl, const FmmOps& ops, bool uniform_source
   }
   prof_end(pl, nl);
   prof_begin(pl, NUFFT_STAGE_LEVEL2);
-  k_level2<T><<<nsig, 256, 0, st>>>(d, ops.nq, ops.reg, ops.c1, ops.c2, mexp, lvl2, lvl2f);
+  k_level2<T><<<nsig, 256, (size_t)4 * ops.nq * ops.nq * sizeof(double), st>>>(
+      d, ops.nq, ops.reg, ops.c1, ops.c2, mexp, lvl2, lvl2f);
   prof_end(pl, 1);
   // downward: levels 3..kTopLevel in one CTA, then subtrees; the chunks are
   // cut from the finest level up so the costly fine levels get the most CTAs
@@ -1034,7 +1087,8 @@ template <class T, class VO, int G>
 static void launch_targets_fwd(nufft_plan_s* pl, const TreeDims& d, const cplx<T>* f, void* g) {
   dim3 grid(nblk(pl->M, kTgtThreads), (unsigned)(pl->batch / G));
   k_targets_fwd<T, VO, G><<<grid, kTgtThreads, NearCap<T, G>::fwd_bytes, pl->stream>>>(
-      d, (int)pl->M, pl->k0, pl->delta, pl->perm, PlanT<T>::F(pl), PlanT<T>::E(pl), f,
+      d, (int)pl->M, pl->k0, pl->delta, PlanT<T>::delta(pl), pl->perm, PlanT<T>::F(pl),
+      PlanT<T>::E(pl), f,
       (const cplx<T>*)pl->lexp, PlanT<T>::lvl2(pl), (VO*)g);
 }
 
@@ -1088,14 +1142,13 @@ int fmm_to_grid(nufft_plan_s* pl, const void* g, int inverse) {
     k_self_terms<T, float2><<<gm, 256, 0, st>>>((int)pl->M, inverse, (int)pl->N, pl->k0,
                                                pl->delta, pl->perm, PlanT<T>::E(pl), charge,
                                                (const float2*)g, pl->Ct, PlanT<T>::Ct(pl),
-                                               PlanT<T>::delta(pl), stt);
+                                               PlanT<T>::delta(pl), KConst<T>::n_2pi_h(d), stt);
   else
     k_self_terms<T, double2><<<gm, 256, 0, st>>>((int)pl->M, inverse, (int)pl->N, pl->k0,
                                                 pl->delta, pl->perm, PlanT<T>::E(pl), charge,
                                                 (const double2*)g, pl->Ct, PlanT<T>::Ct(pl),
-                                                PlanT<T>::delta(pl), stt);
-  k_pack_positions<T><<<nblk(pl->M, 256), 256, 0, st>>>((int)pl->M, pl->k0, pl->delta, pos);
-  prof_end(pl, 2);
+                                                PlanT<T>::delta(pl), KConst<T>::n_2pi_h(d), stt);
+  prof_end(pl, 1);
   prof_begin(pl, NUFFT_STAGE_TARGETS);
   if (pl->batch % 4 == 0)
     k_targets_grid<T, 4><<<dim3(nblk(pl->N, kTgtThreads), nsig / 4), kTgtThreads,
@@ -1113,6 +1166,17 @@ int fmm_to_grid(nufft_plan_s* pl, const void* g, int inverse) {
 
 template int fmm_configure<double>();
 template int fmm_configure<float>();
+// Source positions of the adjoint / inverse near field, packed once per plan.
+int fmm_pack_positions(nufft_plan_s* pl) {
+  if (pl->prec == NUFFT_FP64)
+    k_pack_positions<double><<<nblk(pl->M, 256), 256, 0, pl->stream>>>(
+        (int)pl->M, pl->k0, pl->delta, (SrcPos<double>*)pl->srcpos);
+  else
+    k_pack_positions<float><<<nblk(pl->M, 256), 256, 0, pl->stream>>>(
+        (int)pl->M, pl->k0, pl->delta, (SrcPos<float>*)pl->srcpos);
+  return cudaGetLastError() == cudaSuccess ? NUFFT_OK : NUFFT_ECUDA;
+}
+
 template int fmm_forward<double>(nufft_plan_s*, void*);
 template int fmm_forward<float>(nufft_plan_s*, void*);
 template int fmm_to_grid<double>(nufft_plan_s*, const void*, int);

@@ -29,6 +29,7 @@ int m2l_tc_configure();
 template <class T> int fmm_forward(nufft_plan_s* pl, void* g);
 template <class T> int fmm_to_grid(nufft_plan_s* pl, const void* g, int inverse);
 int inverse_precompute(nufft_plan_s* pl, void* tmp, size_t tmp_bytes);
+int fmm_pack_positions(nufft_plan_s* pl);
 size_t inverse_tmp_bytes(const nufft_plan_s* pl);
 
 namespace {
@@ -400,6 +401,7 @@ int nufft_plan_create(nufft_plan* out, int64_t N, int64_t M, const double* y, do
   void* tmp = nullptr;
   if (cudaMalloc(&tmp, tb) != cudaSuccess) { free_plan(pl); return NUFFT_ENOMEM; }
   rc = setup_points(pl, y, tmp);
+  if (!rc) rc = fmm_pack_positions(pl);
   if (!rc && (flags & NUFFT_WANT_INVERSE)) rc = inverse_precompute(pl, tmp, tb);
   int hstat = 0;
   if (!rc) {
