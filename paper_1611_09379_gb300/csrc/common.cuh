@@ -196,7 +196,21 @@ struct nufft_plan_s {
   GraphEntry graphs[kGraphSlots];
   int graph_next = 0;            // slot replaced next (round robin)
   cudaStream_t cap = nullptr;    // private capture origin
+  // side branch: work the main chain does not wait for at once (level-2
+  // coefficients, self terms) runs on `aux`, forked and joined by events
+  cudaStream_t aux = nullptr;
+  cudaEvent_t ev_fork[2] = {}, ev_join[2] = {};
+  int side_ok = 1;               // 0: keep everything on `stream`
 };
+
+// Begin a side branch (slot 0 or 1): returns the stream to launch it on --
+// `aux` after it waits for the work issued so far on the plan's stream, or
+// the plan's stream itself while profiling (per-stage events need one
+// stream order) or when the side stream cannot be made.  side_end marks the
+// branch's end; side_join makes the plan's stream wait for it.
+cudaStream_t side_begin(nufft_plan_s* pl, int slot);
+void side_end(nufft_plan_s* pl, int slot, cudaStream_t s);
+void side_join(nufft_plan_s* pl, int slot);
 
 // Bracket the launches of one stage (no-ops unless profiling is enabled).
 void prof_begin(nufft_plan_s* pl, int stage);

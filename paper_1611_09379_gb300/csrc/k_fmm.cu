@@ -1024,9 +1024,14 @@ int fmm_upward_downward(nufft_plan_s* pl, const FmmOps& ops, bool uniform_source
     ++nl;
   }
   prof_end(pl, nl);
+  // level-2 coefficients on the side branch (only the targets need them)
   prof_begin(pl, NUFFT_STAGE_LEVEL2);
-  k_level2<T><<<nsig, 256, (size_t)4 * ops.nq * ops.nq * sizeof(double), st>>>(
-      d, ops.nq, ops.reg, ops.c1, ops.c2, mexp, lvl2, lvl2f);
+  {
+    cudaStream_t s2 = side_begin(pl, 0);
+    k_level2<T><<<nsig, 256, (size_t)4 * ops.nq * ops.nq * sizeof(double), s2>>>(
+        d, ops.nq, ops.reg, ops.c1, ops.c2, mexp, lvl2, lvl2f);
+    side_end(pl, 0, s2);
+  }
   prof_end(pl, 1);
   // downward: levels 3..kTopLevel in one CTA, then subtrees; the chunks are
   // cut from the finest level up so the costly fine levels get the most CTAs
@@ -1071,6 +1076,7 @@ int fmm_upward_downward(nufft_plan_s* pl, const FmmOps& ops, bool uniform_source
     }
   }
   prof_end(pl, nl);
+  side_join(pl, 0);
   return cudaGetLastError() == cudaSuccess ? NUFFT_OK : NUFFT_ECUDA;
 }
 
@@ -1131,24 +1137,28 @@ int fmm_to_grid(nufft_plan_s* pl, const void* g, int inverse) {
     k_charges<T, double2><<<gm, 256, 0, st>>>(pl->M, pl->perm, coef, !inverse, (const double2*)g,
                                              charge);
   prof_end(pl, 1);
-  int rc = fmm_upward_downward<T>(pl, cot_ops(pl), false, charge, pl->lvl2,
-                                  sizeof(T) == 4 ? pl->lvl2f : nullptr);
-  if (rc) return rc;
+  // self terms on the side branch: only the targets kernel needs them
   const TreeDims d = dims_of(pl);
   cplx<T>* stt = (cplx<T>*)pl->selft;
-  SrcPos<T>* pos = (SrcPos<T>*)pl->srcpos;
   prof_begin(pl, NUFFT_STAGE_OTHER);
+  cudaStream_t s1 = side_begin(pl, 1);
   if (c64)
-    k_self_terms<T, float2><<<gm, 256, 0, st>>>((int)pl->M, inverse, (int)pl->N, pl->k0,
+    k_self_terms<T, float2><<<gm, 256, 0, s1>>>((int)pl->M, inverse, (int)pl->N, pl->k0,
                                                pl->delta, pl->perm, PlanT<T>::E(pl), charge,
                                                (const float2*)g, pl->Ct, PlanT<T>::Ct(pl),
                                                PlanT<T>::delta(pl), KConst<T>::n_2pi_h(d), stt);
   else
-    k_self_terms<T, double2><<<gm, 256, 0, st>>>((int)pl->M, inverse, (int)pl->N, pl->k0,
+    k_self_terms<T, double2><<<gm, 256, 0, s1>>>((int)pl->M, inverse, (int)pl->N, pl->k0,
                                                 pl->delta, pl->perm, PlanT<T>::E(pl), charge,
                                                 (const double2*)g, pl->Ct, PlanT<T>::Ct(pl),
                                                 PlanT<T>::delta(pl), KConst<T>::n_2pi_h(d), stt);
+  side_end(pl, 1, s1);
   prof_end(pl, 1);
+  int rc = fmm_upward_downward<T>(pl, cot_ops(pl), false, charge, pl->lvl2,
+                                  sizeof(T) == 4 ? pl->lvl2f : nullptr);
+  if (rc) return rc;
+  SrcPos<T>* pos = (SrcPos<T>*)pl->srcpos;
+  side_join(pl, 1);
   prof_begin(pl, NUFFT_STAGE_TARGETS);
   if (pl->batch % 4 == 0)
     k_targets_grid<T, 4><<<dim3(nblk(pl->N, kTgtThreads), nsig / 4), kTgtThreads,

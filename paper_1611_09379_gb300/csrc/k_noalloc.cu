@@ -112,6 +112,7 @@ extern "C" int nufft_fwd_noalloc(const void* c, int64_t N, const double* y, int6
   pl.N = N; pl.M = M; pl.L = prm.lmax; pl.B = 1 << prm.lmax; pl.s = (int)(N >> prm.lmax);
   pl.p = prm.p; pl.q = prm.q; pl.pm = prm.p > 2 * prm.q + 1 ? prm.p : 2 * prm.q + 1;
   pl.prec = prec; pl.flags = flags | NUFFT_NO_GRAPH; pl.eps = eps;  // a graph would allocate
+  pl.side_ok = 0;  // so would a side stream
   pl.stream = (cudaStream_t)stream;
   if (pl.p > kMaxP || pl.pm > kMaxPm || 2 * pl.q > kMaxQ2 || pl.s > kMaxS) return NUFFT_EINVAL;
   const int64_t B = pl.B;

@@ -208,6 +208,11 @@ void free_plan(nufft_plan_s* pl) {
   for (auto& gr : pl->graphs)
     if (gr.exec) cudaGraphExecDestroy(gr.exec);
   if (pl->cap) cudaStreamDestroy(pl->cap);
+  if (pl->aux) cudaStreamDestroy(pl->aux);
+  for (int i = 0; i < 2; ++i) {
+    if (pl->ev_fork[i]) cudaEventDestroy(pl->ev_fork[i]);
+    if (pl->ev_join[i]) cudaEventDestroy(pl->ev_join[i]);
+  }
   if (pl->prof) {
     for (cudaEvent_t e : pl->prof->ev)
       if (e) cudaEventDestroy(e);
@@ -223,6 +228,37 @@ int dalloc(X** p, size_t bytes) {
 }
 
 }  // namespace
+
+cudaStream_t side_begin(nufft_plan_s* pl, int slot) {
+  if (!pl->side_ok || (pl->prof && pl->prof->enabled)) return pl->stream;
+  if (!pl->aux) {
+    if (cudaStreamCreateWithFlags(&pl->aux, cudaStreamNonBlocking) != cudaSuccess) {
+      pl->aux = nullptr;
+      pl->side_ok = 0;
+      return pl->stream;
+    }
+    for (int i = 0; i < 2; ++i)
+      if (cudaEventCreateWithFlags(&pl->ev_fork[i], cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&pl->ev_join[i], cudaEventDisableTiming) != cudaSuccess) {
+        pl->side_ok = 0;
+        return pl->stream;
+      }
+  }
+  if (cudaEventRecord(pl->ev_fork[slot], pl->stream) != cudaSuccess ||
+      cudaStreamWaitEvent(pl->aux, pl->ev_fork[slot], 0) != cudaSuccess)
+    return pl->stream;
+  return pl->aux;
+}
+
+void side_end(nufft_plan_s* pl, int slot, cudaStream_t s) {
+  if (s != pl->stream) cudaEventRecord(pl->ev_join[slot], s);
+}
+
+void side_join(nufft_plan_s* pl, int slot) {
+  // a no-op unless the branch ran on aux (its join event was recorded)
+  if (pl->aux && pl->side_ok && !(pl->prof && pl->prof->enabled))
+    cudaStreamWaitEvent(pl->stream, pl->ev_join[slot], 0);
+}
 
 void prof_begin(nufft_plan_s* pl, int stage) {
   StageProf* pf = pl->prof;
