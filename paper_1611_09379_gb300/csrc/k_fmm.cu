@@ -529,7 +529,10 @@ __device__ inline void near_window(int lo, int hi, NearAcc<T>* acc, Term term) {
     for (int gg = 0; gg < G; ++gg) acc[gg].fold();
   }
   if (i < hi) {
-    for (int u = 0; u < hi - i; ++u) term(i, u);
+    const int n = hi - i;
+#pragma unroll
+    for (int u = 0; u < 16; ++u)
+      if (u < n) term(i, u);
 #pragma unroll
     for (int gg = 0; gg < G; ++gg) acc[gg].fold();
   }
@@ -766,13 +769,16 @@ __global__ void k_pack_positions(int M, const int32_t* __restrict__ k0s,
 // where h' leaves out the 2/t part of the pairs with k0_j = k (their st_j
 // terms above); Ct_k = C_k e^Lambda / N carries the 1/N of Eq. p1.
 // Near field: the CTA's 256 grid points lie in leaves bl..bh; the sources of
-// leaves bl-1..bh+1 (consecutive in sorted order, leaf by leaf) are staged
-// in shared memory in chunks, each with its position x relative to the
-// CTA's first grid point kb (an exact integer in T, unwrapped through its
-// leaf slot) and offset delta, its charges and self terms.  A grid point in
+// leaves bl-1..bh+1 (consecutive in sorted order, leaf by leaf, inside a
+// leaf by nearest grid point) are staged in shared memory in chunks, each
+// with its position x relative to the CTA's first grid point kb (an exact
+// integer in T, unwrapped through its leaf slot, non-decreasing along the
+// window) and offset delta, its charges and self terms.  A grid point in
 // leaf b sums over the sources of leaves b-1, b, b+1: t = (k - kb - x) -
-// delta with the first difference exact.  The reciprocals 1/t are shared by
-// the G signals.  All arithmetic in T (Ct in FP32 for the mixed path).
+// delta with the first difference exact; the run of sources with x = k - kb
+// (found by binary search) contributes its self terms instead.  The
+// reciprocals 1/t are shared by the G signals.  All arithmetic in T (Ct in
+// FP32 for the mixed path).
 template <class T, int G>
 __global__ void __launch_bounds__(kTgtThreads) k_targets_grid(
     TreeDims d, int inverse, const int32_t* __restrict__ start,
@@ -856,19 +862,27 @@ __global__ void __launch_bounds__(kTgtThreads) k_targets_grid(
     __syncthreads();
     const int lo = (wlo > c0 ? wlo : c0) - c0, hi = (whi < c1 ? whi : c1) - c0;
     if (act && lo < hi) {
-      near_window<T, G>(lo, hi, acc, [&](int i, int u) {
-        const cplx<T> rp = srel[i + u];
-        const T t0 = kf - rp.x;
-        T r = rcp_t(t0 - rp.y);
-        const bool hit = t0 == (T)0;  // k0_j = k: the pair's self term replaces it
-        r = hit ? (T)0 : r;
-        if (hit) {
+      // sources with k0_j = k (x = k - kb) form one run of the window, which
+      // is sorted by x: their self terms replace their pairs
+      int ha = lo, hb = hi;
+      while (ha < hb) {
+        const int mid = (ha + hb) >> 1;
+        if (srel[mid].x < kf) ha = mid + 1; else hb = mid;
+      }
+      int he = ha;
+      while (he < hi && srel[he].x == kf) {
 #pragma unroll
-          for (int gg = 0; gg < G; ++gg) self[gg] = cadd(self[gg], sst[gg * CAP + i + u]);
-        }
+        for (int gg = 0; gg < G; ++gg) self[gg] = cadd(self[gg], sst[gg * CAP + he]);
+        ++he;
+      }
+      auto term = [&](int i, int u) {
+        const cplx<T> rp = srel[i + u];
+        const T r = rcp_t((kf - rp.x) - rp.y);
 #pragma unroll
         for (int gg = 0; gg < G; ++gg) acc[gg].add_r(sq[gg * CAP + i + u], r);
-      });
+      };
+      near_window<T, G>(lo, ha, acc, term);
+      near_window<T, G>(he, hi, acc, term);
     }
   }
   if (!act) return;
@@ -895,6 +909,164 @@ __global__ void __launch_bounds__(kTgtThreads) k_targets_grid(
     cplx<T> res = mk<T>((T)-0.5 * (Qs.x - hi), (T)-0.5 * (Qs.y + hr));
     if (inverse) res = cscale(res, Ct[k]);
     out[(int64_t)sig * N + k] = cadd(res, self[gg]);
+  }
+}
+
+// k_targets_grid for one signal with two adjacent grid points k, k + 1 per
+// thread (same leaf: s is even): every staged source is read once for both
+// points, which halves the shared-memory traffic of the pair loop.  The
+// window is sorted by x, so the sources with k0 = k and those with
+// k0 = k + 1 are two consecutive runs: each point takes the self terms of its
+// own run and the pair of the other's.  Same arithmetic per pair as
+// k_targets_grid.
+template <class T>
+__global__ void __launch_bounds__(kTgtThreads) k_targets_grid2(
+    TreeDims d, int inverse, const int32_t* __restrict__ start,
+    const SrcPos<T>* __restrict__ pos, const cplx<T>* __restrict__ charge,
+    const cplx<T>* __restrict__ st, const cplx<T>* __restrict__ lexp,
+    const cplx<T>* __restrict__ lvl2, const T* __restrict__ Ct, cplx<T>* __restrict__ out) {
+  constexpr int CAP = NearCap<T, 1>::grid;
+  constexpr int kPts = 2 * kTgtThreads;
+  constexpr int kMaxSlots = kTgtThreads + 3;  // kPts / s + 3 with s >= 2
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cplx<T>* srel = reinterpret_cast<cplx<T>*>(smraw);  // [CAP] (x, delta)
+  cplx<T>* sq = srel + CAP;                            // [CAP] charges
+  cplx<T>* sst = sq + CAP;                             // [CAP] self terms
+  __shared__ int s_off[kMaxSlots + 1];
+  const int N = (int)d.N;
+  const int s = d.s;
+  const int B = 1 << d.L;
+  const int kb = blockIdx.x * kPts;
+  const int k = kb + 2 * threadIdx.x;  // and k + 1
+  const bool act = k < N;
+  const int bl = kb / s;
+  const int bh = ((kb + kPts < N ? kb + kPts : N) - 1) / s;
+  const int nslot = bh - bl + 3;
+  if (threadIdx.x < 32) {
+    int carry = 0;
+    for (int c0 = 0; c0 < nslot; c0 += 32) {
+      const int js = c0 + threadIdx.x;
+      int cnt = 0;
+      if (js < nslot) {
+        const int bb = (bl - 1 + js + B) & (B - 1);
+        cnt = start[bb + 1] - start[bb];
+      }
+      int v = cnt;
+#pragma unroll
+      for (int sh = 1; sh < 32; sh <<= 1) {
+        int n = __shfl_up_sync(0xffffffffu, v, sh);
+        if ((int)threadIdx.x >= sh) v += n;
+      }
+      if (js < nslot) s_off[js + 1] = carry + v;
+      carry += __shfl_sync(0xffffffffu, v, 31);
+    }
+    if (threadIdx.x == 0) s_off[0] = 0;
+  }
+  __syncthreads();
+  const int total = s_off[nslot];
+  const int b = act ? k / s : bl;
+  const int wlo = s_off[b - bl], whi = s_off[b - bl + 3];
+  const T kf0 = (T)(k - kb), kf1 = kf0 + (T)1;
+  NearAcc<T> acc0, acc1;
+  cplx<T> self0 = mk<T>(0, 0), self1 = mk<T>(0, 0);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // both points' pairs with source i
+  auto both = [&](int i) {
+    const cplx<T> rp = srel[i];
+    const T e0 = kf0 - rp.x;
+    const T r0 = rcp_t(e0 - rp.y), r1 = rcp_t((e0 + (T)1) - rp.y);
+    const cplx<T> q = sq[i];
+    acc0.add_r(q, r0);
+    acc1.add_r(q, r1);
+  };
+  auto span = [&](int lo, int hi) {  // [lo, hi): chunks of 16, folded
+    int i = lo;
+    for (; i + 16 <= hi; i += 16) {
+#pragma unroll
+      for (int u = 0; u < 16; ++u) both(i + u);
+      acc0.fold();
+      acc1.fold();
+    }
+    if (i < hi) {
+      const int n = hi - i;
+#pragma unroll
+      for (int u = 0; u < 16; ++u)
+        if (u < n) both(i + u);
+      acc0.fold();
+      acc1.fold();
+    }
+  };
+  for (int c0 = 0; c0 < total; c0 += CAP) {
+    const int c1 = total - c0 < CAP ? total : c0 + CAP;
+    __syncthreads();
+    for (int js = warp; js < nslot; js += kTgtThreads / 32) {
+      const int lo = s_off[js] > c0 ? s_off[js] : c0;
+      const int hi = s_off[js + 1] < c1 ? s_off[js + 1] : c1;
+      if (lo >= hi) continue;
+      const int bu = bl - 1 + js;
+      const int bb = (bu + B) & (B - 1);
+      const int g0 = start[bb] - s_off[js];
+      for (int e = lo + lane; e < hi; e += 32) {
+        const int gi = g0 + e;
+        const SrcPos<T> ps = pos[gi];
+        const int xu = bu * s + (((int)ps.k0 - bb * s) & (N - 1)) - kb;
+        srel[e - c0] = mk<T>((T)xu, ps.dl);
+        sq[e - c0] = charge[gi];
+        sst[e - c0] = st[gi];
+      }
+    }
+    __syncthreads();
+    const int lo = (wlo > c0 ? wlo : c0) - c0, hi = (whi < c1 ? whi : c1) - c0;
+    if (act && lo < hi) {
+      // runs x = k - kb and x = k + 1 - kb: [ha, h1), [h1, h2)
+      int ha = lo, hb = hi;
+      while (ha < hb) {
+        const int mid = (ha + hb) >> 1;
+        if (srel[mid].x < kf0) ha = mid + 1; else hb = mid;
+      }
+      int h1 = ha;
+      for (; h1 < hi && srel[h1].x == kf0; ++h1) {
+        self0 = cadd(self0, sst[h1]);
+        const cplx<T> rp = srel[h1];
+        acc1.add_r(sq[h1], rcp_t((T)1 - rp.y));
+      }
+      int h2 = h1;
+      for (; h2 < hi && srel[h2].x == kf1; ++h2) {
+        self1 = cadd(self1, sst[h2]);
+        const cplx<T> rp = srel[h2];
+        acc0.add_r(sq[h2], rcp_t((T)-1 - rp.y));
+      }
+      acc0.fold();
+      acc1.fold();
+      span(lo, ha);
+      span(h2, hi);
+    }
+  }
+  if (!act) return;
+  const int Q2 = 2 * d.q;
+  const int arc = b >> (d.L - 2);
+  const T ts = KConst<T>::inv_s(d);
+  const T cN = KConst<T>::n_pi(d), c2 = (T)(2.0 * kInvPi);
+  const cplx<T>* l2 = lvl2;
+  const cplx<T> Qs = l2[4 * Q2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int kk = k + h;
+    if (kk >= N) break;
+    const int o = kk - b * s;
+    const int I = kk - arc * (N >> 2) - (N >> 3);
+    const T uh = (T)I * KConst<T>::two_n(d);
+    const T u = fma((T)o, ts, (T)-0.5);
+    cplx<T> far = mk<T>(0, 0);
+    if (d.L >= 3)
+      far = horner<T>(lexp + ((int64_t)(level_off(d.L) - 4) + b) * d.p, d.p, u);
+    const cplx<T> reg = horner<T>(l2 + arc * Q2, Q2, uh);
+    const cplx<T> nr = h ? acc1.get() : acc0.get();
+    const T hr = cN * fma(far.x, ts, nr.x) - c2 * reg.x;
+    const T hi = cN * fma(far.y, ts, nr.y) - c2 * reg.y;
+    cplx<T> res = mk<T>((T)-0.5 * (Qs.x - hi), (T)-0.5 * (Qs.y + hr));
+    if (inverse) res = cscale(res, Ct[kk]);
+    out[kk] = cadd(res, h ? self1 : self0);
   }
 }
 
@@ -1165,6 +1337,11 @@ int fmm_to_grid(nufft_plan_s* pl, const void* g, int inverse) {
                            NearCap<T, 4>::grid_bytes, st>>>(
         d, inverse, pl->leaf_start, pos, charge, stt, (const cplx<T>*)pl->lexp,
         PlanT<T>::lvl2(pl), PlanT<T>::Ct(pl), (cplx<T>*)pl->grid);
+  else if (nsig == 1 && pl->s >= 2)
+    k_targets_grid2<T><<<nblk(pl->N, 2 * kTgtThreads), kTgtThreads, NearCap<T, 1>::grid_bytes,
+                         st>>>(d, inverse, pl->leaf_start, pos, charge, stt,
+                               (const cplx<T>*)pl->lexp, PlanT<T>::lvl2(pl), PlanT<T>::Ct(pl),
+                               (cplx<T>*)pl->grid);
   else
     k_targets_grid<T, 1><<<dim3(nblk(pl->N, kTgtThreads), nsig), kTgtThreads,
                            NearCap<T, 1>::grid_bytes, st>>>(

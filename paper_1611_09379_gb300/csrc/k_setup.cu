@@ -112,10 +112,15 @@ __global__ void k_scatter(const int32_t* __restrict__ leafo, int64_t M,
 
 constexpr int kSegMax = 8192;  // largest leaf population the segment sort handles
 
-// One CTA per leaf: bitonic sort of perm[start, end) in shared memory.
+// One CTA per leaf b: bitonic sort of perm[start, end) in shared memory by
+// the key (k0 - b s mod N, original index): inside a leaf the points follow
+// their nearest grid points (0..s from the leaf's first one), ties in the
+// original order.  Sources that share a nearest grid point are then
+// contiguous, which the adjoint / inverse target kernel uses.
 __global__ void k_segment_sort(int32_t* __restrict__ perm, const int32_t* __restrict__ start,
+                               const int32_t* __restrict__ k0o, int N, int s,
                                int* __restrict__ status) {
-  __shared__ int32_t sh[kSegMax];
+  extern __shared__ unsigned long long shk[];  // [kSegMax]
   int b = blockIdx.x;
   int32_t a = start[b], e = start[b + 1];
   int n = e - a;
@@ -126,7 +131,15 @@ __global__ void k_segment_sort(int32_t* __restrict__ perm, const int32_t* __rest
   }
   int P = 1;
   while (P < n) P <<= 1;
-  for (int i = threadIdx.x; i < P; i += blockDim.x) sh[i] = (i < n) ? perm[a + i] : INT32_MAX;
+  for (int i = threadIdx.x; i < P; i += blockDim.x) {
+    unsigned long long key = ~0ull;
+    if (i < n) {
+      const int32_t j = perm[a + i];
+      const unsigned krel = (unsigned)((k0o[j] - b * s) & (N - 1));
+      key = ((unsigned long long)krel << 32) | (unsigned)j;
+    }
+    shk[i] = key;
+  }
   __syncthreads();
   for (int k = 2; k <= P; k <<= 1) {
     for (int j = k >> 1; j > 0; j >>= 1) {
@@ -134,14 +147,14 @@ __global__ void k_segment_sort(int32_t* __restrict__ perm, const int32_t* __rest
         int ixj = i ^ j;
         if (ixj > i) {
           bool up = ((i & k) == 0);
-          int32_t u = sh[i], v = sh[ixj];
-          if ((u > v) == up) { sh[i] = v; sh[ixj] = u; }
+          unsigned long long u = shk[i], v = shk[ixj];
+          if ((u > v) == up) { shk[i] = v; shk[ixj] = u; }
         }
       }
       __syncthreads();
     }
   }
-  for (int i = threadIdx.x; i < n; i += blockDim.x) perm[a + i] = sh[i];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) perm[a + i] = (int32_t)(shk[i] & 0xFFFFFFFFull);
 }
 
 // Gather the sorted point data and form F_j (Eq. p5) and
@@ -177,6 +190,13 @@ __global__ void k_points_finalize(const int32_t* __restrict__ perm, int64_t M, i
 
 using namespace nufft;
 
+int setup_configure() {
+  return cudaFuncSetAttribute(k_segment_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              kSegMax * (int)sizeof(unsigned long long)) == cudaSuccess
+             ? NUFFT_OK : NUFFT_ECUDA;
+}
+
+
 // Host driver: returns a nufft_status.  Temporary buffers come from tmp
 // (caller-owned device memory of at least setup_tmp_bytes(M, B) bytes).
 static inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -209,7 +229,8 @@ int setup_points(nufft_plan_s* pl, const double* y, void* tmp) {
   if (cudaMemcpyAsync(cursor, pl->leaf_start, (B + 1) * 4, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
     return NUFFT_ECUDA;
   k_scatter<<<(unsigned)gb, th, 0, st>>>(leafo, M, cursor, pl->perm);
-  k_segment_sort<<<(unsigned)B, 256, 0, st>>>(pl->perm, pl->leaf_start, pl->status);
+  k_segment_sort<<<(unsigned)B, 256, kSegMax * sizeof(unsigned long long), st>>>(
+      pl->perm, pl->leaf_start, k0o, (int)N, pl->s, pl->status);
   k_points_finalize<<<(unsigned)gb, th, 0, st>>>(pl->perm, M, N, k0o, delo, pl->k0, pl->delta,
                                                  pl->F, pl->E, pl->delta_f, pl->Ff, pl->Ef);
   return cudaGetLastError() == cudaSuccess ? NUFFT_OK : NUFFT_ECUDA;

@@ -17,6 +17,7 @@ int setup_points(nufft_plan_s* pl, const double* y, void* tmp);
 int fft_init_tables(double2* tw, float2* twf, int64_t N, cudaStream_t st);
 size_t fft_table_elems(int64_t N);
 int fft_configure();
+int setup_configure();
 int fft_num_passes(int64_t N);
 template <class T>
 int fft_run(const void* in, int in_f64, void* out, int out_f64, cplx<T>* buf, cplx<T>* buf2,
@@ -83,6 +84,7 @@ int configure_once() {
   if (!rc) rc = fmm_configure<double>();
   if (!rc) rc = fmm_configure<float>();
   if (!rc) rc = m2l_tc_configure();
+  if (!rc) rc = setup_configure();
   if (!rc) g_configured = 1;
   return rc;
 }

@@ -264,15 +264,26 @@ def test_exact_grid_boundaries_and_hits(orc):
 
 
 def test_binning_is_stable_counting_sort(orc):
+    """Leaves in order; inside a leaf, points by nearest grid point (every
+    k0 lies in [leaf s, leaf s + s], the top end for points rounding up to the
+    next leaf's first grid point), equal k0 by original index."""
     N, B = 1 << 10, 1 << 6
+    s = N // B
     y = workloads.points("clustered", 3000, seed=4)
     perm, start, leaf = orc.binning(y, N, B)
+    _, k0, delta = orc.exact_grid(y, N, B)
     assert np.array_equal(np.sort(perm), np.arange(y.size))
     assert np.all(np.diff(leaf[perm]) >= 0)
     for bb in range(B):
         seg = perm[start[bb]:start[bb + 1]]
-        assert np.all(np.diff(seg) > 0)
         assert np.all(leaf[seg] == bb)
+        krel = (k0[seg] - bb * s) % N
+        assert np.all((krel >= 0) & (krel <= s))
+        key = krel * (1 << 40) + seg
+        assert np.all(np.diff(key) > 0)
+        # the grid coordinate k0 + delta lies in the leaf's arc [bb s, bb s + s)
+        Y = bb * s + krel + delta[seg]
+        assert np.all((Y >= bb * s) & (Y < bb * s + s))
     assert start[0] == 0 and start[-1] == y.size
 
 
