@@ -42,7 +42,12 @@ EPS_MIXED = 1e-6
 EPS_FP64 = 1e-12
 JITTER = 0.4
 METRIC = "NUFFT points/s (forward + square inverse, N=M=2^20, mixed eps=1e-6)"
-STAGE_KERNELS = {"targets": "k_targets_fwd + k_targets_grid", "fft": "k_fft_reg",
+# DRAM bytes (read + write) of the target-evaluation kernels per step (one
+# k_targets_fwd + one k_targets_grid2 launch), from the ncu capture summarised
+# in profiles/targets_fft_N2p20_mixed.md; reported only while the kernels'
+# source text still hashes to `sha1` (a changed kernel reports null)
+TARGETS_TRAFFIC = {"bytes_per_step": 79158016, "sha1": "5d6eb3024f13c34cb7fb142b15913f071ce2dce0"}
+STAGE_KERNELS = {"targets": "k_targets_fwd + k_targets_grid2", "fft": "k_fft_reg",
                  "m2l": "k_down_top + k_down_sub (+ k_m2l_tc)", "p2m": "k_p2m_* + k_charges",
                  "m2m": "k_up_sub + k_up_top", "level2": "k_level2"}
 L2_FLUSH_BYTES = 512 << 20
@@ -172,6 +177,16 @@ def stage_roofline(stages_ms: dict, N: int, M: int, info: dict, io_bytes: int, f
         else:
             out[st] = {"ms": ms, "bound": None}
     return out
+
+
+def targets_source_sha1() -> str:
+    """SHA-1 of the near-field / target-kernel section of k_fmm.cu."""
+    import hashlib
+    path = os.path.join(ROOT, "paper_1611_09379_gb300", "csrc", "k_fmm.cu")
+    src = open(path).read()
+    a = src.index("// 1/t: FP32 reciprocal")
+    e = src.index("}  // namespace nufft\n\nusing namespace nufft;")
+    return hashlib.sha1(src[a:e].encode()).hexdigest()
 
 
 def fp32_peak_tflops(peaks):
@@ -331,6 +346,10 @@ def run_ours(args):
     r = sroof[dom]
     roof = {k: r[k] for k in ("bound", "achieved", "peak", "unit", "frac")}
     roof["traffic"] = None
+    if dom == "targets" and TARGETS_TRAFFIC["bytes_per_step"] and \
+            TARGETS_TRAFFIC["sha1"] == targets_source_sha1():
+        roof["traffic"] = TARGETS_TRAFFIC["bytes_per_step"]
+        roof["traffic_unit"] = "DRAM bytes per step (ncu, profiles/targets_fft_N2p20_mixed.md)"
     roof["kernel_stage"] = dom
     roof["kernels"] = STAGE_KERNELS.get(dom)
     roof["peak_source"] = (f"{peak_src}: " + ("MEASURED_PEAKS hbm_gbs" if roof["bound"] == "hbm" else
