@@ -248,7 +248,58 @@ __device__ inline double level_logw(int log_kernel, int log2N, int l) {
 
 // Top of the downward pass in one CTA: levels 3..lt (2^lt <= 32 boxes), each
 // level's multipoles and the locals staged in shared memory.
+// L2L of the parent's local expansion into output n of a child (odd: which
+// child): sum_{k >= n} Tl[odd][k][n] lpar[k]
 template <class T>
+__device__ inline cplx<T> l2l_one(const T* __restrict__ Tl, int p, int n, int odd,
+                                  const cplx<T>* __restrict__ lpar) {
+  T ar = 0, ai = 0;
+  const T* Tt = Tl + odd * p * p + n;
+  for (int k = n; k < p; ++k) {
+    T w = Tt[k * p];
+    cplx<T> x = lpar[k];
+    ar = fma(w, x.x, ar);
+    ai = fma(w, x.y, ai);
+  }
+  return mk<T>(ar, ai);
+}
+
+// M2L of every box of levels l0..l1 at once (no level waits for another):
+//   lexp[l][i][n] = sum over the interaction list of T[slot][m][n] M_l[i+o][m]
+// (+ M_0 log W_l per interacting box for the log kernel); the L2L chain then
+// adds the parents' locals (k_down_top / k_down_sub with PRE).  One thread
+// per output (box, n), the operator in shared memory.
+template <class T>
+__global__ void __launch_bounds__(256) k_m2l_all(TreeDims d, int l0, int l1,
+                                                 const T* __restrict__ op_m2l,
+                                                 const cplx<T>* __restrict__ mexp,
+                                                 cplx<T>* __restrict__ lexp, int log_kernel,
+                                                 int log2N) {
+  extern __shared__ unsigned char smraw[];
+  T* Tm = reinterpret_cast<T*>(smraw);
+  const int p = d.p, pm = d.pm;
+  for (int i = threadIdx.x; i < 4 * p * p; i += blockDim.x) Tm[i] = op_m2l[i];
+  __syncthreads();
+  mexp += blockIdx.y * d.mstride;
+  lexp += blockIdx.y * d.lstride;
+  const int64_t e0 = level_off(l0) * (int64_t)p, e1 = level_off(l1 + 1) * (int64_t)p;
+  for (int64_t e = e0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < e1;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t gb = e / p;  // level_off(l) + i
+    const int n = (int)(e - gb * p);
+    const int l = 63 - __clzll((unsigned long long)(gb + 4));
+    const int64_t nb = int64_t(1) << l;
+    const int64_t i = gb + 4 - nb;
+    const cplx<T>* ml = mexp + level_off(l) * pm;
+    auto msrc = [&](int off) { return ml + ((i + off + nb) & (nb - 1)) * pm; };
+    const T lw = log_kernel ? (T)level_logw(log_kernel, log2N, l) : (T)0;
+    lexp[(gb - 4) * p + n] = m2l_one<T>(Tm, nullptr, p, n, (int)(i & 1), msrc, nullptr, lw);
+  }
+}
+
+// PRE: the M2L parts are already in lexp (k_m2l_all); only the L2L chain
+// runs here, adding the parents' locals in place.
+template <class T, bool PRE>
 __global__ void __launch_bounds__(512) k_down_top(TreeDims d, int lt, const T* __restrict__ op_m2l,
                                                   const T* __restrict__ op_l2l,
                                                   const cplx<T>* __restrict__ mexp,
@@ -270,21 +321,32 @@ __global__ void __launch_bounds__(512) k_down_top(TreeDims d, int lt, const T* _
   cplx<T>* cur = Lb;
   for (int l = 3; l <= lt; ++l) {
     const int nb = 1 << l;
-    const cplx<T>* ml = mexp + level_off(l) * pm;
-    __syncthreads();
-    for (int e = threadIdx.x; e < nb * p; e += blockDim.x) {
-      int i = e / p, m = e - i * p;
-      Ms[e] = ml[(int64_t)i * pm + m];
-    }
-    __syncthreads();
-    const T lw = log_kernel ? (T)level_logw(log_kernel, log2N, l) : (T)0;
     cplx<T>* lout = lexp + (level_off(l) - 4) * p;
-    for (int e = threadIdx.x; e < nb * p; e += blockDim.x) {
-      int i = e / p, n = e - i * p;
-      auto msrc = [&](int off) { return Ms + ((i + off + nb) & (nb - 1)) * p; };
-      cplx<T> v = m2l_one<T>(Tm, Tl, p, n, i & 1, msrc, l > 3 ? par + (i >> 1) * p : nullptr, lw);
-      cur[e] = v;
-      lout[e] = v;
+    if (PRE) {
+      __syncthreads();  // the parent level is complete
+      for (int e = threadIdx.x; e < nb * p; e += blockDim.x) {
+        int i = e / p, n = e - i * p;
+        cplx<T> v = lout[e];
+        if (l > 3) v = cadd(v, l2l_one<T>(Tl, p, n, i & 1, par + (i >> 1) * p));
+        cur[e] = v;
+        lout[e] = v;
+      }
+    } else {
+      const cplx<T>* ml = mexp + level_off(l) * pm;
+      __syncthreads();
+      for (int e = threadIdx.x; e < nb * p; e += blockDim.x) {
+        int i = e / p, m = e - i * p;
+        Ms[e] = ml[(int64_t)i * pm + m];
+      }
+      __syncthreads();
+      const T lw = log_kernel ? (T)level_logw(log_kernel, log2N, l) : (T)0;
+      for (int e = threadIdx.x; e < nb * p; e += blockDim.x) {
+        int i = e / p, n = e - i * p;
+        auto msrc = [&](int off) { return Ms + ((i + off + nb) & (nb - 1)) * p; };
+        cplx<T> v = m2l_one<T>(Tm, Tl, p, n, i & 1, msrc, l > 3 ? par + (i >> 1) * p : nullptr, lw);
+        cur[e] = v;
+        lout[e] = v;
+      }
     }
     cplx<T>* t = par; par = cur; cur = t;
   }
@@ -295,7 +357,7 @@ __global__ void __launch_bounds__(512) k_down_top(TreeDims d, int lt, const T* _
 // formed in shared memory: the multipoles of the boxes and their +-3
 // neighbours are staged per level, the parents' locals stay on chip.  Only
 // level lb is written back.
-template <class T>
+template <class T, bool PRE>
 __global__ void __launch_bounds__(512) k_down_sub(TreeDims d, int lt, int lb,
                                                   const T* __restrict__ op_m2l,
                                                   const T* __restrict__ op_l2l,
@@ -323,19 +385,28 @@ __global__ void __launch_bounds__(512) k_down_sub(TreeDims d, int lt, int lb,
     const int nbx = 1 << (l - lt);          // boxes of this subtree at level l
     const int nb = 1 << l;
     const int c0 = blockIdx.x << (l - lt);  // first box
-    const cplx<T>* ml = mexp + level_off(l) * pm;
-    __syncthreads();  // previous level finished with Ms
-    for (int e = threadIdx.x; e < (nbx + 6) * p; e += blockDim.x) {
-      int bi = e / p, m = e - bi * p;
-      int box = (c0 - 3 + bi + nb) & (nb - 1);
-      Ms[e] = ml[(int64_t)box * pm + m];
-    }
-    __syncthreads();
-    const T lw = log_kernel ? (T)level_logw(log_kernel, log2N, l) : (T)0;
-    for (int e = threadIdx.x; e < nbx * p; e += blockDim.x) {
-      int bi = e / p, n = e - bi * p;
-      auto msrc = [&](int off) { return Ms + (bi + 3 + off) * p; };
-      cur[e] = m2l_one<T>(Tm, Tl, p, n, (c0 + bi) & 1, msrc, par + (bi >> 1) * p, lw);
+    if (PRE) {
+      const cplx<T>* lm = lexp + (level_off(l) - 4 + (int64_t)c0) * p;
+      __syncthreads();  // the parent level is complete
+      for (int e = threadIdx.x; e < nbx * p; e += blockDim.x) {
+        int bi = e / p, n = e - bi * p;
+        cur[e] = cadd(lm[e], l2l_one<T>(Tl, p, n, (c0 + bi) & 1, par + (bi >> 1) * p));
+      }
+    } else {
+      const cplx<T>* ml = mexp + level_off(l) * pm;
+      __syncthreads();  // previous level finished with Ms
+      for (int e = threadIdx.x; e < (nbx + 6) * p; e += blockDim.x) {
+        int bi = e / p, m = e - bi * p;
+        int box = (c0 - 3 + bi + nb) & (nb - 1);
+        Ms[e] = ml[(int64_t)box * pm + m];
+      }
+      __syncthreads();
+      const T lw = log_kernel ? (T)level_logw(log_kernel, log2N, l) : (T)0;
+      for (int e = threadIdx.x; e < nbx * p; e += blockDim.x) {
+        int bi = e / p, n = e - bi * p;
+        auto msrc = [&](int off) { return Ms + (bi + 3 + off) * p; };
+        cur[e] = m2l_one<T>(Tm, Tl, p, n, (c0 + bi) & 1, msrc, par + (bi >> 1) * p, lw);
+      }
     }
     cplx<T>* t = par; par = cur; cur = t;
   }
@@ -1105,10 +1176,16 @@ int fmm_configure() {
           cudaSuccess ||
       cudaFuncSetAttribute(k_up_top<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big) !=
           cudaSuccess ||
-      cudaFuncSetAttribute(k_down_top<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big) !=
-          cudaSuccess ||
-      cudaFuncSetAttribute(k_down_sub<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big) !=
-          cudaSuccess ||
+      cudaFuncSetAttribute(k_down_top<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           big) != cudaSuccess ||
+      cudaFuncSetAttribute(k_down_top<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           big) != cudaSuccess ||
+      cudaFuncSetAttribute(k_down_sub<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           big) != cudaSuccess ||
+      cudaFuncSetAttribute(k_m2l_all<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           4 * 64 * 64 * (int)sizeof(T)) != cudaSuccess ||
+      cudaFuncSetAttribute(k_down_sub<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           big) != cudaSuccess ||
       cudaFuncSetAttribute(k_level2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            4 * 66 * 66 * (int)sizeof(double)) != cudaSuccess)
     return NUFFT_ECUDA;
@@ -1218,14 +1295,27 @@ int fmm_upward_downward(nufft_plan_s* pl, const FmmOps& ops, bool uniform_source
     };
     while (top > 3 && top_smem(top) > kSmemBudget) --top;
     size_t smt = top_smem(top);
-    k_down_top<T><<<dim3(1, nsig), 512, smt, st>>>(
-        d, top, (const T*)ops.m2l, (const T*)ops.l2l, mexp, lexp, ops.log_kernel, log2N);
-    ++nl;
     // levels lc..L as one tensor-core GEMM each (FP32 data, cot kernel only)
     int lc = L + 1;
     if constexpr (std::is_same<T, float>::value)
       if (!ops.log_kernel && pl->op_tc && pl->tc_level >= 4 && pl->tc_level <= L)
         lc = pl->tc_level > top + 1 ? pl->tc_level : top + 1;
+    // without tensor-core levels: every level's M2L in one parallel launch,
+    // then the L2L chain through the subtree kernels
+    const bool pre = lc > L;
+    if (pre) {
+      const int64_t nout = (level_off(L + 1) - level_off(3)) * (int64_t)p;
+      const unsigned nbk = (unsigned)((nout + 255) / 256);
+      k_m2l_all<T><<<dim3(nbk, nsig), 256, (size_t)4 * p * p * sizeof(T), st>>>(
+          d, 3, L, (const T*)ops.m2l, mexp, lexp, ops.log_kernel, log2N);
+      ++nl;
+      k_down_top<T, true><<<dim3(1, nsig), 512, smt, st>>>(
+          d, top, (const T*)ops.m2l, (const T*)ops.l2l, mexp, lexp, ops.log_kernel, log2N);
+    } else {
+      k_down_top<T, false><<<dim3(1, nsig), 512, smt, st>>>(
+          d, top, (const T*)ops.m2l, (const T*)ops.l2l, mexp, lexp, ops.log_kernel, log2N);
+    }
+    ++nl;
     int dep = kSubDepth;
     while (dep > 1 && down_sub_smem<T>(p, dep) > kSmemBudget) --dep;
     int cuts[32], nc = 0;
@@ -1233,8 +1323,12 @@ int fmm_upward_downward(nufft_plan_s* pl, const FmmOps& ops, bool uniform_source
     int lt = top;
     for (int c = nc - 1; c >= 0; --c) {
       int lb = cuts[c];
-      k_down_sub<T><<<dim3(1u << lt, nsig), 512, down_sub_smem<T>(p, lb - lt), st>>>(
-          d, lt, lb, (const T*)ops.m2l, (const T*)ops.l2l, mexp, lexp, ops.log_kernel, log2N);
+      if (pre)
+        k_down_sub<T, true><<<dim3(1u << lt, nsig), 512, down_sub_smem<T>(p, lb - lt), st>>>(
+            d, lt, lb, (const T*)ops.m2l, (const T*)ops.l2l, mexp, lexp, ops.log_kernel, log2N);
+      else
+        k_down_sub<T, false><<<dim3(1u << lt, nsig), 512, down_sub_smem<T>(p, lb - lt), st>>>(
+            d, lt, lb, (const T*)ops.m2l, (const T*)ops.l2l, mexp, lexp, ops.log_kernel, log2N);
       ++nl;
       lt = lb;
     }
