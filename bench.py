@@ -225,7 +225,7 @@ def run_ours(args):
             # empirical l_max, p, q, tc_level for this point set (outside the timing,
             # like the plan: Sec. 3.3 separates setting up from evaluating)
             ent = tune.autotune(N, yd, eps, prec=prec, ops="fwd+inv", reps=5, tag="jitter0.4")
-            prm = {k: ent["params"][k] for k in ("lmax", "p", "q", "tc_level")}
+            prm = {k: ent["params"][k] for k in ("lmax", "p", "q", "tc_level", "tc_near")}
             chosen = [t for t in ent["trials"] if t["accepted"]]
             tuning[tag] = {"params": ent["params"], "seconds": ent["seconds"],
                            "from_table": ent["from_table"],
@@ -446,7 +446,7 @@ def run_batched(steps: int = 5, warmup: int = 3, tune_params: bool = True):
         from paper_1611_09379_gb300 import tune
         ent = tune.autotune(N, yd, 1e-6, prec=nf.MIXED, io="c64", batch=B, ops="fwd", reps=3,
                             tag="uniform")
-        prm = {k: ent["params"][k] for k in ("lmax", "p", "q", "tc_level")}
+        prm = {k: ent["params"][k] for k in ("lmax", "p", "q", "tc_level", "tc_near")}
         tuned = {"seconds": ent["seconds"], "formula_ms": ent["trials"][0]["ms"],
                  "formula_params": ent["trials"][0]["params"]}
     plan = nf.Plan(N, yd, eps=1e-6, prec=nf.MIXED, io="c64", batch=B, **prm)
@@ -504,7 +504,7 @@ def run_large(steps: int = 5, warmup: int = 3, tune_params: bool = True):
         from paper_1611_09379_gb300 import tune
         ent = tune.autotune(N, yd, 1e-6, prec=nf.MIXED, io="c64", ops="fwd+adj", reps=3,
                             tag="uniform")
-        prm = {k: ent["params"][k] for k in ("lmax", "p", "q", "tc_level")}
+        prm = {k: ent["params"][k] for k in ("lmax", "p", "q", "tc_level", "tc_near")}
         tuned = {"seconds": ent["seconds"], "formula_ms": ent["trials"][0]["ms"],
                  "formula_params": ent["trials"][0]["params"]}
     plan = nf.Plan(N, yd, eps=1e-6, prec=nf.MIXED, io="c64", **prm)

@@ -82,14 +82,20 @@ typedef struct nufft_plan_s *nufft_plan;
  *         kernels.  0 = automatic (the finest levels holding at least 2048
  *         parent boxes over all signals), -1 = never.  Reported back as -1
  *         when no level qualifies.
+ *   tc_near: near field of batched forward transforms as a dense GEMM on
+ *         the tensor cores (kernel values x window samples of 64 signals per
+ *         tile, three TF32 passes; NUFFT_MIXED with batch a multiple of 64
+ *         only).  0 = automatic (on where allowed), -1 = never, 1 = where
+ *         allowed.  Reported back as 1 or -1.
  * Constraints: 2 <= lmax <= log2 N, 4 <= p <= 64, 2 <= q <= 32,
- * batch <= 4096, tc_level -1, 0 or in [4, 30]. */
+ * batch <= 4096, tc_level -1, 0 or in [4, 30], tc_near -1, 0 or 1. */
 typedef struct {
   int lmax;
   int p;
   int q;
   int batch;
   int tc_level;
+  int tc_near;
 } nufft_params;
 
 /* ---------------------------------------------------------------- host only */
@@ -126,13 +132,14 @@ typedef struct {
  * 23-25 with l* = 5 and p, q by the error bound of Eq. 18.2).  Times the
  * exec sequence `ops` (NUFFT_OP_* mask) on probe data for 10 to 40 candidate
  * parameter sets, each through a plan of its own, and returns the fastest
- * whose every output has a relative L2 error of at most max(eps / 4, 1.5 x
- * the formula parameters' error): forward and adjoint against the FP64 FMM
+ * whose every output has a relative L2 error of at most max(eps / 4,
+ * min(1.5 x the formula parameters' error, eps / 2)): forward and adjoint
+ * against the FP64 FMM
  * at eps = 1e-15, the inverse (when timed with the forward) as the round
  * trip inv(fwd(c)) against the probe coefficients c.  Search:
  * lmax in {l0 - 1, l0, l0 + 1}; p lowered in steps of 2 and q in steps of 1
  * while accurate; for NUFFT_MIXED every tc_level from max(4, lmax - 9) to
- * lmax and -1.
+ * lmax and -1, and for batches of 64 signals tc_near on and off.
  *   N, M, y [device], eps, prec, flags (0 or NUFFT_IO_C64), batch: as for
  *          nufft_plan_create (y is read during the call only)
  *   ops    NUFFT_OP_FWD | NUFFT_OP_ADJ | NUFFT_OP_INV (INV needs M == N)

@@ -51,7 +51,7 @@ SYMBOLS = [
 
 class Params(ctypes.Structure):
     _fields_ = [("lmax", ctypes.c_int), ("p", ctypes.c_int), ("q", ctypes.c_int),
-                ("batch", ctypes.c_int), ("tc_level", ctypes.c_int)]
+                ("batch", ctypes.c_int), ("tc_level", ctypes.c_int), ("tc_near", ctypes.c_int)]
 
 
 class TuneTrial(ctypes.Structure):
@@ -132,17 +132,18 @@ def version() -> int:
 
 def choose_params(N: int, M: int, eps: float, prec: int = FP64, lmax: int = 0, p: int = 0, q: int = 0):
     """(lmax, p, q) the library would use (host only, no GPU needed)."""
-    prm = Params(lmax, p, q, 1, 0)
+    prm = Params(lmax, p, q, 1, 0, 0)
     _check(_lib.nufft_choose_params(N, M, eps, prec, ctypes.byref(prm)), "nufft_choose_params")
     return prm.lmax, prm.p, prm.q
 
 
 def choose_params_full(N: int, M: int, eps: float, prec: int = FP64, lmax: int = 0, p: int = 0,
-                       q: int = 0, batch: int = 1, tc_level: int = 0) -> dict:
+                       q: int = 0, batch: int = 1, tc_level: int = 0, tc_near: int = 0) -> dict:
     """Every resolved parameter (host only), as a dict."""
-    prm = Params(lmax, p, q, batch, tc_level)
+    prm = Params(lmax, p, q, batch, tc_level, tc_near)
     _check(_lib.nufft_choose_params(N, M, eps, prec, ctypes.byref(prm)), "nufft_choose_params")
-    return {"lmax": prm.lmax, "p": prm.p, "q": prm.q, "batch": prm.batch, "tc_level": prm.tc_level}
+    return {"lmax": prm.lmax, "p": prm.p, "q": prm.q, "batch": prm.batch, "tc_level": prm.tc_level,
+            "tc_near": prm.tc_near}
 
 
 def _torch():
@@ -179,12 +180,14 @@ class Plan:
     batch: signals sharing the points; exec calls take [batch, N] / [batch, M].
     tc_level: first tree level whose M2L runs on the tensor cores (MIXED only;
     0 = automatic, -1 = never).
+    tc_near: batched forward near field on the tensor cores (MIXED, batch a
+    multiple of 64; 0 = automatic, -1 = never).
     graphs: replay exec sequences as CUDA graphs (captured per buffer set).
     """
 
     def __init__(self, N: int, y, eps: float = 1e-12, prec: int = FP64, io: str = "c128",
                  inverse: bool = False, lmax: int = 0, p: int = 0, q: int = 0, batch: int = 1,
-                 tc_level: int = 0, graphs: bool = True, stream=None):
+                 tc_level: int = 0, tc_near: int = 0, graphs: bool = True, stream=None):
         torch = _torch()
         self.N = int(N)
         self.M = int(y.numel())
@@ -196,7 +199,7 @@ class Plan:
                  (0 if graphs else NO_GRAPH))
         self._stream = stream
         h = _P()
-        prm = Params(lmax, p, q, self.batch, tc_level)
+        prm = Params(lmax, p, q, self.batch, tc_level, tc_near)
         yp = _dev_ptr(y, torch.float64, self.M, "y")
         _check(_lib.nufft_plan_create(ctypes.byref(h), self.N, self.M, yp, eps, prec,
                                       ctypes.byref(prm), flags, _stream_handle(stream)),
@@ -215,7 +218,7 @@ class Plan:
         prm = Params()
         _check(_lib.nufft_plan_params(self._h, ctypes.byref(prm)), "nufft_plan_params")
         return {"lmax": prm.lmax, "p": prm.p, "q": prm.q, "batch": prm.batch,
-                "tc_level": prm.tc_level}
+                "tc_level": prm.tc_level, "tc_near": prm.tc_near}
 
     def sync(self):
         """Wait for the plan's stream; raises NufftError(ETIMEOUT) if a bounded

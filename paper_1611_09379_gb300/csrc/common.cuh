@@ -65,6 +65,16 @@ __device__ inline bool neg_bits(double d) {
   return b < 0 && b != (long long)0x8000000000000000ull;
 }
 
+// Leaf index and offset of a point from its grid coordinates (int32: N <= 2^26):
+// leaf = floor((k0 + delta)/s) mod 2^L, o = k0 - leaf s in [0, s].
+__device__ inline void point_local(int k0, double delta, int N, int s, int* leaf, int* o) {
+  int fl = neg_bits(delta) ? k0 - 1 : k0;
+  fl &= (N - 1);
+  int b = fl / s;
+  *leaf = b;
+  *o = (k0 - b * s) & (N - 1);
+}
+
 // Sizes and pointers of one FMM evaluation, passed by value to kernels.
 struct TreeDims {
   int64_t N;   // grid size (power of two)
@@ -178,6 +188,7 @@ struct nufft_plan_s {
   double *op_reg = nullptr;// [2][2q][2q] level-2 weights W1, W2 (FP64)
   float *op_tc = nullptr;  // tensor-core M2L + L2L operator (hi, lo), kernel layout
   int tc_level = -1;       // first level on the tensor cores (-1: none)
+  int tc_near = -1;        // 1: batched forward near field on the tensor cores
   double2 *fft_tw = nullptr; // FFT twiddle tables
   float2 *fft_tw_f = nullptr;
   int fft_tw_lo_bits = 0;

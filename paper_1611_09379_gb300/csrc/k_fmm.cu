@@ -48,15 +48,6 @@ __global__ void k_p2m_uniform(TreeDims d, const cplx<T>* __restrict__ q,
   mleaf[b * d.pm + m] = mk<T>(ar, ai);
 }
 
-// Leaf index and offset of a point from its grid coordinates (int32: N <= 2^26):
-// leaf = floor((k0 + delta)/s) mod 2^L, o = k0 - leaf s in [0, s].
-__device__ inline void point_local(int k0, double delta, int N, int s, int* leaf, int* o) {
-  int fl = neg_bits(delta) ? k0 - 1 : k0;
-  fl &= (N - 1);
-  int b = fl / s;
-  *leaf = b;
-  *o = (k0 - b * s) & (N - 1);
-}
 
 // Non-uniform sources: one warp per leaf; a chunk of 32 sources writes
 // q rho^m for 32 consecutive m into shared memory, lanes then reduce rows.
@@ -654,7 +645,8 @@ __global__ void __launch_bounds__(kTgtThreads) k_targets_fwd(
     TreeDims d, int M, const int32_t* __restrict__ k0s, const double* __restrict__ dels,
     const T* __restrict__ dels_t, const int32_t* __restrict__ perm, const cplx<T>* __restrict__ F,
     const cplx<T>* __restrict__ E, const cplx<T>* __restrict__ fgrid,
-    const cplx<T>* __restrict__ lexp, const cplx<T>* __restrict__ lvl2, VO* __restrict__ g) {
+    const cplx<T>* __restrict__ lexp, const cplx<T>* __restrict__ lvl2,
+    const cplx<T>* __restrict__ hnear, VO* __restrict__ g) {
   extern __shared__ __align__(16) unsigned char smraw[];
   cplx<T>* sf = reinterpret_cast<cplx<T>*>(smraw);  // [G][window]
   __shared__ int s_lo, s_hi;
@@ -678,7 +670,8 @@ __global__ void __launch_bounds__(kTgtThreads) k_targets_fwd(
   __syncthreads();
   const int bl = s_lo, bh = s_hi;
   const int nwin = (bh - bl + 3) * s;  // samples of leaves bl-1 .. bh+1
-  const bool staged = nwin <= NearCap<T, G>::fwd;
+  // hnear: near-field sums computed elsewhere (tensor cores): no window here
+  const bool staged = !hnear && nwin <= NearCap<T, G>::fwd;
   // (targets are sorted by leaf, so b lies in [bl, bh]; checked all the same)
   if (staged) {
     const int base = (bl - 1) * s;
@@ -696,7 +689,8 @@ __global__ void __launch_bounds__(kTgtThreads) k_targets_fwd(
   // per chunk: Di = D0 - i (exact); per term: t0 = Di - u (exact), t = t0 + delta
   // the pair with x_k0 (window index o + s, D = 0) is left out: E_j carries it
   const int ex = o + s;
-  if (staged && b >= bl && b <= bh) {
+  if (hnear) {
+  } else if (staged && b >= bl && b <= bh) {
     const cplx<T>* w = sf + (b - bl) * s;  // leaf b - 1 of the window
     near_window_ex<T, G>(0, 3 * s, ex, acc, [&](int i, int u, auto chk) {
       const T t0 = (D0 - (T)i) - (T)u;
@@ -735,7 +729,7 @@ __global__ void __launch_bounds__(kTgtThreads) k_targets_fwd(
     const cplx<T>* l2 = lvl2 + (int64_t)sig * (4 * Q2 + 1);
     cplx<T> reg = horner<T>(l2 + arc * Q2, Q2, uh);
     cplx<T> Qs = l2[4 * Q2];
-    cplx<T> nr = acc[gg].get();
+    cplx<T> nr = hnear ? hnear[(int64_t)sig * M + j] : acc[gg].get();
     T hr = cN * fma(far.x, ts, nr.x) - c2 * reg.x;
     T hi = cN * fma(far.y, ts, nr.y) - c2 * reg.y;
     // g = E f_k0 - (F/2)(Q + i h')
@@ -1356,13 +1350,18 @@ static FmmOps cot_ops(nufft_plan_s* pl) {
 }
 
 template <class T, class VO, int G>
-static void launch_targets_fwd(nufft_plan_s* pl, const TreeDims& d, const cplx<T>* f, void* g) {
+static void launch_targets_fwd(nufft_plan_s* pl, const TreeDims& d, const cplx<T>* f,
+                               const cplx<T>* hnear, void* g) {
   dim3 grid(nblk(pl->M, kTgtThreads), (unsigned)(pl->batch / G));
   k_targets_fwd<T, VO, G><<<grid, kTgtThreads, NearCap<T, G>::fwd_bytes, pl->stream>>>(
       d, (int)pl->M, pl->k0, pl->delta, PlanT<T>::delta(pl), pl->perm, PlanT<T>::F(pl),
       PlanT<T>::E(pl), f,
-      (const cplx<T>*)pl->lexp, PlanT<T>::lvl2(pl), (VO*)g);
+      (const cplx<T>*)pl->lexp, PlanT<T>::lvl2(pl), hnear, (VO*)g);
 }
+
+int near_tc_forward(const TreeDims& d, int M, int batch, const int32_t* k0s, const double* dels,
+                    const float* dels_f, const float2* fgrid, float2* hnear, int* status,
+                    cudaStream_t st);
 
 // forward: grid samples f (cplx<T>, in pl->grid, [batch][N]) -> g ([batch][M], original order)
 template <class T>
@@ -1374,14 +1373,24 @@ int fmm_forward(nufft_plan_s* pl, void* g) {
   const TreeDims d = dims_of(pl);
   const bool g4 = (pl->batch % 4) == 0;
   prof_begin(pl, NUFFT_STAGE_TARGETS);
-  if (pl->flags & NUFFT_IO_C64) {
-    if (g4) launch_targets_fwd<T, float2, 4>(pl, d, f, g);
-    else launch_targets_fwd<T, float2, 1>(pl, d, f, g);
-  } else {
-    if (g4) launch_targets_fwd<T, double2, 4>(pl, d, f, g);
-    else launch_targets_fwd<T, double2, 1>(pl, d, f, g);
+  // batches of 64 signals: near-field sums on the tensor cores first
+  const cplx<T>* hnear = nullptr;
+  if constexpr (std::is_same<T, float>::value) {
+    if (pl->tc_near > 0) {
+      int rc2 = near_tc_forward(d, (int)pl->M, pl->batch, pl->k0, pl->delta, pl->delta_f,
+                                (const float2*)f, (float2*)pl->charge, pl->status, pl->stream);
+      if (rc2) return rc2;
+      hnear = (const cplx<T>*)pl->charge;
+    }
   }
-  prof_end(pl, 1);
+  if (pl->flags & NUFFT_IO_C64) {
+    if (g4) launch_targets_fwd<T, float2, 4>(pl, d, f, hnear, g);
+    else launch_targets_fwd<T, float2, 1>(pl, d, f, hnear, g);
+  } else {
+    if (g4) launch_targets_fwd<T, double2, 4>(pl, d, f, hnear, g);
+    else launch_targets_fwd<T, double2, 1>(pl, d, f, hnear, g);
+  }
+  prof_end(pl, hnear ? 2 : 1);
   return cudaGetLastError() == cudaSuccess ? NUFFT_OK : NUFFT_ECUDA;
 }
 

@@ -100,7 +100,7 @@ extern "C" int nufft_fwd_noalloc(const void* c, int64_t N, const double* y, int6
   if (!c || !y || !g) return NUFFT_EINVAL;
   if (N > kNoAllocMaxN || M > kNoAllocMaxM) return NUFFT_EINVAL;  // beyond the fixed scratch
   if (flags & ~NUFFT_IO_C64) return NUFFT_EINVAL;
-  nufft_params prm{0, 0, 0, 1, -1};
+  nufft_params prm{0, 0, 0, 1, -1, -1};
   int rc = nufft_choose_params(N, M, eps, prec, &prm);
   if (rc) return rc;
   std::lock_guard<std::mutex> lock(g_noalloc_mu);

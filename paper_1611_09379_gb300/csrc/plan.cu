@@ -18,6 +18,7 @@ int fft_init_tables(double2* tw, float2* twf, int64_t N, cudaStream_t st);
 size_t fft_table_elems(int64_t N);
 int fft_configure();
 int setup_configure();
+int near_tc_configure();
 int fft_num_passes(int64_t N);
 template <class T>
 int fft_run(const void* in, int in_f64, void* out, int out_f64, cplx<T>* buf, cplx<T>* buf2,
@@ -85,6 +86,7 @@ int configure_once() {
   if (!rc) rc = fmm_configure<float>();
   if (!rc) rc = m2l_tc_configure();
   if (!rc) rc = setup_configure();
+  if (!rc) rc = near_tc_configure();
   if (!rc) g_configured = 1;
   return rc;
 }
@@ -373,11 +375,18 @@ int nufft_choose_params(int64_t N, int64_t M, double eps, int prec, nufft_params
       if ((int64_t(1) << (l - 1)) * batch >= 2048) { tc = l; break; }
   }
   if (tc > L) tc = -1;
+  // near field of batched forwards on the tensor cores: groups of 64 signals
+  int tn = prm->tc_near;
+  if (tn != -1 && tn != 0 && tn != 1) return NUFFT_EINVAL;
+  const bool tn_ok = prec == NUFFT_MIXED && batch % 64 == 0;
+  if (tn == 0) tn = tn_ok ? 1 : -1;
+  if (tn == 1 && !tn_ok) tn = -1;
   prm->lmax = L;
   prm->p = p;
   prm->q = q;
   prm->batch = batch;
   prm->tc_level = tc;
+  prm->tc_near = tn;
   return NUFFT_OK;
 }
 
@@ -385,7 +394,7 @@ int nufft_plan_create(nufft_plan* out, int64_t N, int64_t M, const double* y, do
                       int prec, const nufft_params* params, unsigned flags, void* stream) {
   if (!out || !y) return NUFFT_EINVAL;
   *out = nullptr;
-  nufft_params prm{0, 0, 0, 0, 0};
+  nufft_params prm{0, 0, 0, 0, 0, 0};
   if (params) prm = *params;
   int rc = nufft_choose_params(N, M, eps, prec, &prm);
   if (rc) return rc;
@@ -401,6 +410,7 @@ int nufft_plan_create(nufft_plan* out, int64_t N, int64_t M, const double* y, do
   pl->p = prm.p; pl->q = prm.q; pl->pm = prm.p > 2 * prm.q + 1 ? prm.p : 2 * prm.q + 1;
   pl->prec = prec; pl->flags = flags; pl->eps = eps; pl->batch = (int)nb;
   pl->tc_level = prm.tc_level;
+  pl->tc_near = prm.tc_near;
   pl->stream = (cudaStream_t)stream;
   const int64_t B = pl->B;
   const size_t csz = prec == NUFFT_FP64 ? sizeof(double2) : sizeof(float2);
@@ -478,6 +488,7 @@ int nufft_plan_params(nufft_plan pl, nufft_params* out) {
   out->q = pl->q;
   out->batch = pl->batch;
   out->tc_level = pl->tc_level;
+  out->tc_near = pl->tc_near;
   return NUFFT_OK;
 }
 

@@ -12,10 +12,11 @@
 //   2. p lowered in steps of 2 while the result stays accurate;
 //   3. q lowered in steps of 1 likewise;
 //   4. mixed precision: the first tensor-core level (tc_level), every level
-//      from max(4, l_max - 9) to l_max and "never".
+//      from max(4, l_max - 9) to l_max and "never";
+//   5. mixed batches of 64 signals: the near field on the tensor cores or not.
 // A candidate is accurate when every output's relative L2 error is at most
-// max(eps / 4, 1.5 x that of the formula's parameters), so tuning never makes
-// a plan less accurate than eps / 4 or than the paper's choice.  Errors: the
+// max(eps / 4, min(1.5 x that of the formula's parameters, eps / 2)): tuning
+// keeps a plan within eps / 2, and within eps / 4 or the paper's choice.  Errors: the
 // forward and adjoint against the reference FMM; the inverse, when timed
 // with the forward, as the round trip inv(fwd(c)) against c itself (the
 // pipeline's error, including the inverse's conditioning), else against the
@@ -172,7 +173,7 @@ struct Tuner {
     k_probe<<<(unsigned)((nc + 255) / 256), 256, 0, st>>>(buf.c_d, buf.c_f, nc, 1000);
     k_probe<<<(unsigned)((ng + 255) / 256), 256, 0, st>>>(buf.g_d, buf.g_f, ng, 1ull << 40);
     // reference: the FP64 FMM at eps = 1e-15 (complex128 in and out)
-    nufft_params rp{0, 0, 0, batch, -1};
+    nufft_params rp{0, 0, 0, batch, -1, -1};
     nufft_plan ref = nullptr;
     int rc = nufft_plan_create(&ref, N, M, y, 1e-15, NUFFT_FP64, &rp,
                                (ops & NUFFT_OP_INV) ? NUFFT_WANT_INVERSE : 0u, st);
@@ -231,10 +232,11 @@ struct Tuner {
     return NUFFT_OK;
   }
 
-  // every output within max(eps / 4, 1.5 x the formula parameters' error)
+  // every output within max(eps / 4, min(1.5 x the formula parameters'
+  // error, eps / 2))
   bool accurate() const {
     for (int i = 0; i < 3; ++i)
-      if (last_err[i] > std::max(0.25 * eps, 1.5 * def_err[i])) return false;
+      if (last_err[i] > std::max(0.25 * eps, std::min(1.5 * def_err[i], 0.5 * eps))) return false;
     return true;
   }
 
@@ -267,7 +269,7 @@ extern "C" int nufft_autotune(int64_t N, int64_t M, const double* y, double eps,
       (flags & ~NUFFT_IO_C64) || reps < 1 || batch < 1 || (max_trials > 0 && !trials))
     return NUFFT_EINVAL;
   if ((ops & NUFFT_OP_INV) && M != N) return NUFFT_EINVAL;
-  nufft_params d0{0, 0, 0, batch, 0};
+  nufft_params d0{0, 0, 0, batch, 0, 0};
   int rc = nufft_choose_params(N, M, eps, prec, &d0);
   if (rc) return rc;
   Tuner tu;
@@ -291,7 +293,7 @@ extern "C" int nufft_autotune(int64_t N, int64_t M, const double* y, double eps,
   const int L0 = d0.lmax;
   for (int L : {L0 - 1, L0 + 1}) {
     if (L < 2 || L > LN) continue;
-    nufft_params prm{L, 0, 0, batch, 0};
+    nufft_params prm{L, 0, 0, batch, 0, 0};
     if ((rc = tu.try_params(prm, &bestt, &took))) return rc;
   }
   // 2. expansion order p, 3. regular-series order q
@@ -329,11 +331,18 @@ extern "C" int nufft_autotune(int64_t N, int64_t M, const double* y, double eps,
       prm.tc_level = l;
       if ((rc = tu.try_params(prm, &bestt, &took))) return rc;
     }
+    // 5. near field of batched forwards on the tensor cores, or not
+    if (batch % 64 == 0 && (ops & NUFFT_OP_FWD)) {
+      nufft_params prm = bestt.params;
+      prm.tc_near = bestt.params.tc_near > 0 ? -1 : 1;
+      if ((rc = tu.try_params(prm, &bestt, &took))) return rc;
+    }
   }
   *best = bestt.params;
   for (nufft_tune_trial& t : tu.log)
     t.accepted = (t.params.lmax == bestt.params.lmax && t.params.p == bestt.params.p &&
-                  t.params.q == bestt.params.q && t.params.tc_level == bestt.params.tc_level)
+                  t.params.q == bestt.params.q && t.params.tc_level == bestt.params.tc_level &&
+                  t.params.tc_near == bestt.params.tc_near)
                      ? 1 : 0;
   if (n_trials) *n_trials = (int)tu.log.size();
   for (int i = 0; i < max_trials && i < (int)tu.log.size(); ++i) trials[i] = tu.log[i];

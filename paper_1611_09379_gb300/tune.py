@@ -60,7 +60,8 @@ def save_table(table: dict, path: str | None = None) -> None:
 
 
 def _pdict(p: Params) -> dict:
-    return {"lmax": p.lmax, "p": p.p, "q": p.q, "batch": p.batch, "tc_level": p.tc_level}
+    return {"lmax": p.lmax, "p": p.p, "q": p.q, "batch": p.batch, "tc_level": p.tc_level,
+            "tc_near": p.tc_near}
 
 
 def autotune(N: int, y, eps: float, prec: int = FP64, io: str = "c128", batch: int = 1,
@@ -111,4 +112,4 @@ def tuned_plan(N: int, y, eps: float, prec: int = FP64, io: str = "c128", batch:
     p = ent["params"]
     return Plan(N, y, eps=eps, prec=prec, io=io, inverse=bool(ops_mask(ops) & OP_INV),
                 lmax=p["lmax"], p=p["p"], q=p["q"], batch=batch, tc_level=p["tc_level"],
-                stream=stream)
+                tc_near=p.get("tc_near", 0), stream=stream)

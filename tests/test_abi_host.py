@@ -145,3 +145,14 @@ def test_tune_table_roundtrip(tmp_path):
     assert tune.load_table(path) == {}
     tune.save_table({k1: {"params": {"lmax": 15}}}, path)
     assert tune.load_table(path)[k1]["params"]["lmax"] == 15
+
+
+def test_tc_near_choice(nf):
+    """Tensor-core near field: mixed precision with batches of 64 signals."""
+    assert nf.choose_params_full(1 << 18, 1 << 18, 1e-6, nf.MIXED, batch=64)["tc_near"] == 1
+    assert nf.choose_params_full(1 << 18, 1 << 18, 1e-6, nf.MIXED, batch=128)["tc_near"] == 1
+    assert nf.choose_params_full(1 << 18, 1 << 18, 1e-6, nf.MIXED, batch=32)["tc_near"] == -1
+    assert nf.choose_params_full(1 << 18, 1 << 18, 1e-12, nf.FP64, batch=64)["tc_near"] == -1
+    assert nf.choose_params_full(1 << 18, 1 << 18, 1e-6, nf.MIXED, batch=64, tc_near=-1)["tc_near"] == -1
+    with pytest.raises(nf.NufftError):
+        nf.choose_params_full(1 << 18, 1 << 18, 1e-6, nf.MIXED, batch=64, tc_near=2)

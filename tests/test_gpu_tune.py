@@ -40,7 +40,8 @@ def test_autotune_choice_is_accurate(nf, orc, tmp_path, prec, eps, ops):
     # the choice is at least as fast as the formula's parameters (trial 0)
     assert min(t["ms"] for t in chosen) <= trials[0]["ms"] * 1.0001
     # and within the accuracy rule
-    assert all(t["err"] <= max(0.25 * eps, 1.5 * trials[0]["err"]) for t in chosen)
+    assert all(t["err"] <= max(0.25 * eps, min(1.5 * trials[0]["err"], 0.5 * eps))
+               or t["params"] == trials[0]["params"] for t in chosen)
     plan = tune.tuned_plan(N, _dev(y), eps, prec=prec, ops=ops, tag="jitter", path=path)
     assert plan.params()["lmax"] == ent["params"]["lmax"]
     g = plan.forward(_dev(c)).cpu().numpy()
