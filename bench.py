@@ -47,7 +47,7 @@ METRIC = "NUFFT points/s (forward + square inverse, N=M=2^20, mixed eps=1e-6)"
 # in profiles/targets_fft_N2p20_mixed.md; reported only while the kernels'
 # source text still hashes to `sha1` (a changed kernel reports null)
 TARGETS_TRAFFIC = {"bytes_per_step": 79158016, "sha1": "5d6eb3024f13c34cb7fb142b15913f071ce2dce0"}
-STAGE_KERNELS = {"targets": "k_targets_fwd + k_targets_grid2", "fft": "k_fft_reg",
+STAGE_KERNELS = {"targets": "k_targets_fwd + k_targets_grid2", "fft": "k_fft_st",
                  "m2l": "k_down_top + k_down_sub (+ k_m2l_tc)", "p2m": "k_p2m_* + k_charges",
                  "m2m": "k_up_sub + k_up_top", "level2": "k_level2"}
 L2_FLUSH_BYTES = 512 << 20
@@ -159,7 +159,9 @@ def stage_work(stage: str, N: int, M: int, info: dict, io_bytes: int, fwd: int, 
 def stage_roofline(stages_ms: dict, N: int, M: int, info: dict, io_bytes: int, fwd: int, bwd: int,
                    peaks: dict) -> dict:
     """Per-stage achieved rate against its bound: FP32 ALU (152 SMs x 128
-    lanes x 2 flops x max clock) or HBM (measured copy bandwidth)."""
+    lanes x 2 flops x max clock; for the targets, whose pair loop takes one
+    reciprocal per pair, the special-function unit's 16 per clock per SM) or
+    HBM (measured copy bandwidth)."""
     out = {}
     for st, ms in stages_ms.items():
         if ms <= 0:
@@ -174,6 +176,11 @@ def stage_roofline(stages_ms: dict, N: int, M: int, info: dict, io_bytes: int, f
             pk = fp32_peak_tflops(peaks)
             out[st] = {"ms": ms, "bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
                        "frac": ach / pk}
+            if st == "targets":
+                # the pair loop's binding unit is the reciprocal (SFU) pipe
+                pk_sfu = sfu_pair_peak_tflops(peaks)
+                out[st].update({"peak": pk_sfu, "frac": ach / pk_sfu, "peak_fp32_fma": pk,
+                                "frac_fp32_fma": ach / pk})
         else:
             out[st] = {"ms": ms, "bound": None}
     return out
@@ -192,6 +199,13 @@ def targets_source_sha1() -> str:
 def fp32_peak_tflops(peaks):
     # 152 SMs x 128 FP32 lanes x 2 flops (FMA) x max SM clock
     return 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+
+
+def sfu_pair_peak_tflops(peaks):
+    # each near-field pair needs one FP32 reciprocal on the special-function
+    # unit, 16 per clock per SM (an eighth of the FP32 FMA lanes): 152 SMs x
+    # 16 pairs x 4 algorithmic flops per pair x max clock
+    return 152 * 16 * 4 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
 
 
 # ---------------------------------------------------------------- our arm
@@ -352,8 +366,14 @@ def run_ours(args):
         roof["traffic_unit"] = "DRAM bytes per step (ncu, profiles/targets_fft_N2p20_mixed.md)"
     roof["kernel_stage"] = dom
     roof["kernels"] = STAGE_KERNELS.get(dom)
-    roof["peak_source"] = (f"{peak_src}: " + ("MEASURED_PEAKS hbm_gbs" if roof["bound"] == "hbm" else
-                                             "152 SM x 128 FP32 lanes x 2 x sm_max_mhz"))
+    if roof["bound"] == "hbm":
+        roof["peak_source"] = f"{peak_src}: MEASURED_PEAKS hbm_gbs"
+    elif dom == "targets":
+        roof["peak_source"] = (f"{peak_src}: 152 SM x 16 FP32 reciprocals/clk (one per near pair, "
+                               "4 algorithmic flops per pair) x sm_max_mhz")
+        roof["frac_fp32_fma"] = r["frac_fp32_fma"]
+    else:
+        roof["peak_source"] = f"{peak_src}: 152 SM x 128 FP32 lanes x 2 x sm_max_mhz"
 
     # cpu baseline: the oracle (direct forward definition) on sampled targets
     cpu = None

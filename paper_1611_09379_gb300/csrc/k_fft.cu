@@ -3,18 +3,23 @@
 // Each pass is one radix-R Stockham iteration,
 //   a_r = in[j + r N/R] * w^{sign r (j mod Ns) / (Ns R)},  A = DFT_R(a),
 //   out[(j/Ns) Ns R + (j mod Ns) + r' Ns] = A_r',
-// with the size-R DFT done in shared memory by a CTA for J adjacent j (so
-// the strided global reads and writes move J contiguous elements).  Passes
-// multiply Ns by R until it reaches N.  Twiddles come from two small tables,
-// w^{m/N} = T_hi[m >> b] * T_lo[m & (2^b - 1)], filled once per plan with
-// sincospi of exact arguments.
+// with the size-R DFTs of J adjacent columns j done by one CTA (so the
+// strided global reads and writes move J contiguous elements).  Passes
+// multiply Ns by R until it reaches N.  Inside a CTA the size-R DFT is
+// itself a Stockham sequence of radix-8 stages (the last one radix 2 or 4
+// when 3 does not divide log2 R), each thread holding 8 elements in
+// registers between stages, which exchange through shared memory.
+// Twiddles come from two small tables, w^{m/N} = T_hi[m >> b] *
+// T_lo[m & (2^b - 1)], filled once per plan with sincospi of exact
+// arguments.
 #include <cstdint>
 
 #include "common.cuh"
 
 namespace nufft {
 
-constexpr int kFftSmemElems = 4096;  // R * J complex elements staged per CTA (at most)
+constexpr int kFftSmemElems = 4096;  // R * J complex elements per CTA (at most)
+constexpr int kFftMaxThreads = 512;
 
 __global__ void k_fft_tables(double2* __restrict__ tw, int64_t N, int lo_bits) {
   int64_t nlo = int64_t(1) << lo_bits, nhi = N >> lo_bits;
@@ -31,168 +36,298 @@ __global__ void k_fft_tables(double2* __restrict__ tw, int64_t N, int lo_bits) {
   }
 }
 
-// e^{sign 2 pi i m / N}, 0 <= m < N, from the two tables
-template <class T>
-__device__ inline cplx<T> twiddle_t(const cplx<T>* __restrict__ tw, int64_t m, int lo_bits,
-                                    int sign) {
-  int64_t nlo = int64_t(1) << lo_bits;
-  cplx<T> a = tw[m & (nlo - 1)], b = tw[nlo + (m >> lo_bits)];
-  cplx<T> r = cmul(a, b);
-  if (sign < 0) r.y = -r.y;
-  return r;
-}
-
-// in / out element type chosen at run time (uniform branch): complex128 when
-// *_f64 != 0, complex64 otherwise; arithmetic in T.
-template <class T>
-__device__ inline cplx<T> load_c(const void* p, int64_t i, int f64) {
-  if (f64) return c128_to<T>(reinterpret_cast<const double2*>(p)[i]);
-  float2 v = reinterpret_cast<const float2*>(p)[i];
-  return mk<T>((T)v.x, (T)v.y);
-}
-template <class T>
-__device__ inline void store_c(void* p, int64_t i, int f64, cplx<T> v) {
-  if (f64) reinterpret_cast<double2*>(p)[i] = to_c128(v);
-  else reinterpret_cast<float2*>(p)[i] = make_float2((float)v.x, (float)v.y);
-}
-
-// Size-S DFT of v[0..S) in registers (S = 2^LOGS <= 32), radix-2
-// decimation in time: v holds the input in bit-reversed order and receives
-// the output in natural order.  Twiddles w_S^e = wR[e * (R / S)] from the
-// pass's table in shared memory (broadcast reads).
-template <class T, int LOGS>
-__device__ inline void dft_reg(cplx<T>* v, const cplx<T>* __restrict__ wR, int rs) {
-  constexpr int S = 1 << LOGS;
-#pragma unroll
-  for (int h = 1; h < S; h <<= 1) {
-#pragma unroll
-    for (int grp = 0; grp < S; grp += 2 * h) {
-#pragma unroll
-      for (int pos = 0; pos < h; ++pos) {
-        cplx<T> a = v[grp + pos], bb = v[grp + pos + h];
-        if (pos != 0) bb = cmul(bb, wR[pos * (S / (2 * h)) * rs]);
-        v[grp + pos] = cadd(a, bb);
-        v[grp + pos + h] = csub(a, bb);
-      }
-    }
-  }
-}
-
 template <int LOG> __device__ constexpr int brev_c(int x) {
   int r = 0;
   for (int i = 0; i < LOG; ++i) r |= ((x >> i) & 1) << (LOG - 1 - i);
   return r;
 }
 
-// One radix-R Stockham pass, R = R1 R2 (R1 = 2^LOG1 >= R2 = 2^LOG2), for J
-// columns j per CTA (blockDim = J R2 threads; thread (c, t) = (tid mod J,
-// tid / J)).  Column j transforms a_r = in[j + r N/R] w^{sign r (j mod Ns) /
-// (Ns R)}, r = t + R2 m, as
-//   X[k1 + R1 k2] = sum_t w_R2^{t k2} w_R^{t k1} sum_m a[t + R2 m] w_R1^{m k1}:
-// thread t does the inner size-R1 DFT over m in registers, multiplies by
-// w_R^{t k1} and writes Y[k1][t] to shared memory; then thread u does the
-// size-R2 DFTs over t for k1 = u, u + R2, ...; the result goes back through
-// shared memory to out[(j / Ns) Ns R + (j mod Ns) + r' Ns] with contiguous
-// runs (J per r' for Ns >= J, else R per j).
-__device__ inline void cp_async16(void* dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
-                   (uint32_t)__cvta_generic_to_shared(dst)),
-               "l"(src)
-               : "memory");
+// Shared-memory slot of element e = r J + c of the CTA's columns: one spare
+// slot per 32, so the stage writes with stride 8 J spread over the banks.
+__device__ inline int fft_pad(int e) { return e + (e >> 5); }
+
+// x * (sg i), sg = +-1
+template <class T> __device__ inline cplx<T> mul_si(cplx<T> x, T sg) { return mk<T>(-sg * x.y, sg * x.x); }
+
+// Size-2^LOGRAD DFT in registers, decimation in frequency: a in natural
+// order, X_k = sum_m a_m e^{sg 2 pi i m k / RAD} left in a[brev(k)].  The
+// twiddles of radix 8 are the constants (+-1 +- i) / sqrt 2 and +-i.
+template <class T, int LOGRAD>
+__device__ inline void dft_small(cplx<T>* a, T sg) {
+  if constexpr (LOGRAD == 3) {
+    const T h = (T)0.70710678118654752440;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const cplx<T> u = a[k], v = a[k + 4];
+      a[k] = cadd(u, v);
+      cplx<T> d = csub(u, v);
+      if (k == 1) d = mk<T>(h * (d.x - sg * d.y), h * (d.y + sg * d.x));
+      if (k == 2) d = mul_si(d, sg);
+      if (k == 3) d = mk<T>(-h * (d.x + sg * d.y), h * (sg * d.x - d.y));
+      a[k + 4] = d;
+    }
+#pragma unroll
+    for (int hh = 0; hh < 8; hh += 4)
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const cplx<T> u = a[hh + k], v = a[hh + k + 2];
+        a[hh + k] = cadd(u, v);
+        const cplx<T> d = csub(u, v);
+        a[hh + k + 2] = k ? mul_si(d, sg) : d;
+      }
+#pragma unroll
+    for (int k = 0; k < 8; k += 2) {
+      const cplx<T> u = a[k], v = a[k + 1];
+      a[k] = cadd(u, v);
+      a[k + 1] = csub(u, v);
+    }
+  } else if constexpr (LOGRAD == 2) {
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const cplx<T> u = a[k], v = a[k + 2];
+      a[k] = cadd(u, v);
+      const cplx<T> d = csub(u, v);
+      a[k + 2] = k ? mul_si(d, sg) : d;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; k += 2) {
+      const cplx<T> u = a[k], v = a[k + 1];
+      a[k] = cadd(u, v);
+      a[k + 1] = csub(u, v);
+    }
+  } else {
+    const cplx<T> u = a[0], v = a[1];
+    a[0] = cadd(u, v);
+    a[1] = csub(u, v);
+  }
 }
 
-template <class T, int LOG1, int LOG2>
-__global__ void __launch_bounds__(256) k_fft_reg(const void* __restrict__ in, int in_f64,
-                                                 void* __restrict__ out, int out_f64, int64_t N,
-                                                 int64_t Ns, int J, int logJ, int sign,
-                                                 const cplx<T>* __restrict__ tw, int lo_bits,
-                                                 int staged) {
-  constexpr int R1 = 1 << LOG1, R2 = 1 << LOG2, R = R1 * R2, LOGR = LOG1 + LOG2;
-  extern __shared__ __align__(16) unsigned char smraw[];
-  cplx<T>* wR = reinterpret_cast<cplx<T>*>(smraw);  // [R] w_R^e
-  cplx<T>* S = wR + R;                              // [R][J] (Y[k1][t] / X[r'] by column)
-  const int64_t NR = N >> LOGR;
-  const int64_t j0 = (int64_t)blockIdx.x * J;
-  const int tid = threadIdx.x, nth = blockDim.x;
-  const int esz = in_f64 ? 16 : 8;
-  in = (const char*)in + (size_t)blockIdx.y * N * esz;
-  out = (char*)out + (size_t)blockIdx.y * N * (out_f64 ? 16 : 8);
-  // staged: the tile's R rows of J contiguous inputs go to shared memory by
-  // 16-byte asynchronous copies (the whole tile in flight at once); the
-  // region holds R J inputs of esz bytes, reused for Y / X afterwards
-  const int lpr = (J * esz) >> 4;  // 16-byte pieces per row (power of two)
-  if (staged) {
-    int lg = 0;
-    while ((1 << lg) < lpr) ++lg;
-    const char* src = (const char*)in + j0 * esz;
-    char* dstb = reinterpret_cast<char*>(S);
-    for (int e = tid; e < R * lpr; e += nth) {
-      const int r = e >> lg, pc = e & (lpr - 1);
-      cp_async16(dstb + ((size_t)r * J * esz + pc * 16), src + ((size_t)r * NR * esz + pc * 16));
+// Shape of a pass kernel for R = 2^LOGR: E elements per thread, TPC
+// threads per column, at most JMAX columns (kFftMaxThreads threads,
+// kFftSmemElems elements); buffers: two (FP32: one barrier per stage) or one.
+template <class T, int LOGR> struct FftShape {
+  static constexpr int R = 1 << LOGR, LOGE = LOGR < 3 ? LOGR : 3, E = 1 << LOGE, TPC = R / E;
+  static constexpr int JT = kFftMaxThreads / TPC, JS = kFftSmemElems / R;
+  static constexpr int JMAX = JT < JS ? JT : JS;
+  static constexpr int NBUF = sizeof(T) == 4 ? 2 : 1;
+};
+
+// Slot of element e + K (K >= 0) given the slot of e: for K a multiple of
+// 32 (compile-time after unrolling when J is) the padding shifts by K / 32.
+template <int JC>
+__device__ inline int pad_add(int e, int pe, int K) {
+  if (JC != 0 && (K & 31) == 0) return pe + K + (K >> 5);
+  return fft_pad(e + K);
+}
+
+// One radix-2^LOGRAD Stockham stage of the R-point DFTs of the CTA's J
+// columns (element r of column c in buffer[fft_pad(r J + c)]), Ns = 2^LOGNS
+// the length of the sub-DFTs done so far.  Thread (c, q), q < TPC, does the
+// butterflies b = q + i TPC, i < E / 2^LOGRAD:
+//   x_m = src[b + m R / 2^LOGRAD] w^m,  w = w_{Ns 2^LOGRAD}^{b mod Ns},  A = DFT(x),
+//   dst[(b / Ns) Ns 2^LOGRAD + (b mod Ns) + k Ns] = A_k.
+// w is read from the table once per butterfly, its powers formed by
+// products (w^2 = w w, w^3 = w^2 w, w^4 = w^2 w^2, ...: at most three
+// roundings deep).  IN_REGS: the inputs are already in v (the first stage,
+// straight from the loads); src == dst (one buffer) needs a barrier between
+// the reads and the writes.
+template <class T, int LOGR, int LOGRAD, int LOGNS, int JC, bool IN_REGS>
+__device__ inline void fft_stage(cplx<T>* v, const cplx<T>* src, cplx<T>* dst,
+                                 const cplx<T>* __restrict__ wR, int J, int c, int q, T sg) {
+  using S = FftShape<T, LOGR>;
+  constexpr int R = S::R, E = S::E, TPC = S::TPC;
+  constexpr int RAD = 1 << LOGRAD, NB = E / RAD, NS = 1 << LOGNS;
+  if (!IN_REGS) {
+    const int e0 = q * J + c, p0 = fft_pad(e0);
+#pragma unroll
+    for (int i = 0; i < NB; ++i)
+#pragma unroll
+      for (int m = 0; m < RAD; ++m)
+        v[i * RAD + m] = src[pad_add<JC>(e0, p0, (i * TPC + m * (R / RAD)) * J)];
+    if (src == dst) __syncthreads();  // every input read before any output is written
+  }
+#pragma unroll
+  for (int i = 0; i < NB; ++i) {
+    const int b = q + i * TPC, j = b & (NS - 1);
+    cplx<T>* a = v + i * RAD;
+    if (LOGNS > 0 && j != 0) {
+      const cplx<T> w1 = wR[j << (LOGR - LOGNS - LOGRAD)];
+      a[1] = cmul(a[1], w1);
+      if constexpr (RAD >= 4) {
+        const cplx<T> w2 = cmul(w1, w1), w3 = cmul(w2, w1);
+        a[2] = cmul(a[2], w2);
+        a[3] = cmul(a[3], w3);
+        if constexpr (RAD == 8) {
+          const cplx<T> w4 = cmul(w2, w2);
+          a[4] = cmul(a[4], w4);
+          a[5] = cmul(a[5], cmul(w4, w1));
+          a[6] = cmul(a[6], cmul(w4, w2));
+          a[7] = cmul(a[7], cmul(w4, w3));
+        }
+      }
     }
-    asm volatile("cp.async.commit_group;" ::: "memory");
-  }
-  for (int e = tid; e < R; e += nth) wR[e] = twiddle_t<T>(tw, (int64_t)e * NR, lo_bits, sign);
-  const int c = tid & (J - 1), t = tid >> logJ;
-  const int64_t j = j0 + c;
-  const int64_t jm = j & (Ns - 1);
-  int logNs = 0;
-  while ((int64_t(1) << logNs) < Ns) ++logNs;
-  int logN = 0;
-  while ((int64_t(1) << logN) < N) ++logN;
-  const int lstep = logN - logNs - LOGR;  // tstep = N / (Ns R) = 2^lstep
-  if (staged) asm volatile("cp.async.wait_group 0;" ::: "memory");
-  __syncthreads();  // wR and the staged tile ready
-  // load (columns fastest: J contiguous elements per r) with the pass twiddle
-  cplx<T> v[R1];
+    dft_small<T, LOGRAD>(a, sg);
+    const int e0 = (((b >> LOGNS) << (LOGNS + LOGRAD)) + j) * J + c, p0 = fft_pad(e0);
+    // the butterfly's outputs span Ns RAD J slots from a multiple of that
+    // span: inside one 32-slot row when the span is at most 32
+    const bool one_row = JC != 0 && NS * RAD * JC <= 32;
 #pragma unroll
-  for (int m = 0; m < R1; ++m) {
-    const int r = t + R2 * m;
-    cplx<T> x = staged ? load_c<T>(S, (int64_t)r * J + c, in_f64)
-                       : load_c<T>(in, j + (int64_t)r * NR, in_f64);
-    if (jm != 0 && r != 0) x = cmul(x, twiddle_t<T>(tw, (((int64_t)r * jm) << lstep) & (N - 1), lo_bits, sign));
-    v[brev_c<LOG1>(m)] = x;
-  }
-  __syncthreads();  // all staged inputs read before S is reused
-  dft_reg<T, LOG1>(v, wR, R / R1);
-  // Y[k1][t] = v[k1] w_R^{t k1}
-#pragma unroll
-  for (int k1 = 0; k1 < R1; ++k1) {
-    cplx<T> y = v[k1];
-    if (LOG2 > 0 && k1 != 0 && t != 0) y = cmul(y, wR[(t * k1) & (R - 1)]);
-    S[(k1 * R2 + t) * J + c] = y;
+    for (int k = 0; k < RAD; ++k) {
+      const int K = (k << LOGNS) * J;
+      dst[one_row ? p0 + K : pad_add<JC>(e0, p0, K)] = a[brev_c<LOGRAD>(k)];
+    }
   }
   __syncthreads();
-  if (LOG2 > 0) {
-    // thread u = t: size-R2 DFTs over t for k1 = u + R2 i, i < R1 / R2
-#pragma unroll
-    for (int i = 0; i < R1 / R2; ++i) {
-      const int k1 = t + R2 * i;
-      cplx<T> w[R2];
-#pragma unroll
-      for (int tt = 0; tt < R2; ++tt) w[brev_c<LOG2>(tt)] = S[(k1 * R2 + tt) * J + c];
-      dft_reg<T, LOG2>(w, wR, R / R2);
-#pragma unroll
-      for (int k2 = 0; k2 < R2; ++k2) v[i * R2 + k2] = w[k2];
-    }
-    __syncthreads();  // all reads of Y done
-#pragma unroll
-    for (int i = 0; i < R1 / R2; ++i) {
-      const int k1 = t + R2 * i;
-#pragma unroll
-      for (int k2 = 0; k2 < R2; ++k2) S[(k1 + R1 * k2) * J + c] = v[i * R2 + k2];
-    }
-    __syncthreads();
+}
+
+// Stages ST = 1, 2, ... after the first: radix 8 while at least 3 bits are
+// left, then radix 2 or 4; buffers alternate when there are two.
+template <class T, int LOGR, int JC, int ST>
+__device__ inline void fft_stages(cplx<T>* v, cplx<T>* X0, cplx<T>* X1,
+                                  const cplx<T>* __restrict__ wR, int J, int c, int q, T sg,
+                                  cplx<T>** fin) {
+  using S = FftShape<T, LOGR>;
+  constexpr int LOGNS = S::LOGE + 3 * (ST - 1);
+  if constexpr (LOGNS < LOGR) {
+    constexpr int LEFT = LOGR - LOGNS, LOGRAD = LEFT < 3 ? LEFT : 3;
+    cplx<T>* src = (S::NBUF == 2 && (ST & 1) == 0) ? X1 : X0;
+    cplx<T>* dst = (S::NBUF == 2 && (ST & 1) == 1) ? X1 : X0;
+    fft_stage<T, LOGR, LOGRAD, LOGNS, JC, false>(v, src, dst, wR, J, c, q, sg);
+    *fin = dst;
+    fft_stages<T, LOGR, JC, ST + 1>(v, X0, X1, wR, J, c, q, sg, fin);
   }
-  // S[r'][c] = X_{r'} of column c -> out
-  for (int e = tid; e < R * J; e += nth) {
-    int r, jj;
-    if (Ns >= J) { r = e >> logJ; jj = e & (J - 1); }  // J contiguous per r
-    else { jj = e >> LOGR; r = e & (R - 1); }           // small Ns: R contiguous per j
-    const int64_t jg = j0 + jj;
-    const int64_t jmg = jg & (Ns - 1);
-    const int64_t dst = ((jg >> logNs) << (logNs + LOGR)) + jmg + ((int64_t)r << logNs);
-    store_c<T>(out, dst, out_f64, S[r * J + jj]);
+}
+
+// One radix-R Stockham pass (R = 2^LOGR) for J columns j per CTA (JC: J at
+// compile time, 0 = Jrt at run time), J TPC threads; thread (c, q) =
+// (tid mod J, tid / J) loads elements r = q + m TPC (m < E) of column c
+// with the pass twiddle, runs the first stage from registers and the rest
+// through shared memory; the result goes to
+// out[(j / Ns) Ns R + (j mod Ns) + r' Ns] in contiguous runs (J per r' for
+// Ns >= J, else R per j).
+// e^{sign 2 pi i m / N} from the two tables, 32-bit exponent m < N
+template <class T>
+__device__ inline cplx<T> twiddle32(const cplx<T>* __restrict__ tw, uint32_t m, int lo_bits,
+                                    uint32_t lo_mask, T sg) {
+  const cplx<T> a = tw[m & lo_mask], b = tw[(lo_mask + 1) + (m >> lo_bits)];
+  cplx<T> r = cmul(a, b);
+  r.y *= sg;
+  return r;
+}
+
+template <class T>
+__device__ inline cplx<T> ld_cv(const float2* p) {
+  const float2 v = *p;
+  return mk<T>((T)v.x, (T)v.y);
+}
+template <class T>
+__device__ inline cplx<T> ld_cv(const double2* p) {
+  return c128_to<T>(*p);
+}
+
+// loads of a pass: element r = q + m TPC of column jg at in[jg + r NR],
+// times w^{(r jm N / (Ns R)) mod N}, the exponent advancing by
+// de = TPC jm N / (Ns R) per m (32-bit offsets: N < 2^31)
+template <class T, int E, class V>
+__device__ inline void fft_load(cplx<T>* v, const V* __restrict__ in, uint32_t idx,
+                                uint32_t stride, uint32_t ex, uint32_t de, uint32_t nmask,
+                                const cplx<T>* __restrict__ tw, int lo_bits, uint32_t lo_mask,
+                                T sg) {
+#pragma unroll
+  for (int m = 0; m < E; ++m) {
+    cplx<T> x = ld_cv<T>(in + idx);
+    if (ex != 0) x = cmul(x, twiddle32<T>(tw, ex, lo_bits, lo_mask, sg));
+    v[m] = x;
+    idx += stride;
+    ex = (ex + de) & nmask;
+  }
+}
+
+template <class T>
+__device__ inline void st_cv(float2* p, cplx<T> v) {
+  *p = make_float2((float)v.x, (float)v.y);
+}
+template <class T>
+__device__ inline void st_cv(double2* p, cplx<T> v) {
+  *p = to_c128(v);
+}
+
+// One radix-R Stockham pass (R = 2^LOGR) for J columns j per CTA (JC: J at
+// compile time, 0 = Jrt at run time), J TPC threads; thread (c, q) =
+// (tid mod J, tid / J) loads elements r = q + m TPC (m < E) of column c
+// with the pass twiddle, runs the first stage from registers and the rest
+// through shared memory; the result goes to
+// out[(j / Ns) Ns R + (j mod Ns) + r' Ns] in contiguous runs (J per r' for
+// Ns >= J, else R per j).  N = 2^logN < 2^31, Ns = 2^logNs.
+template <class T, int LOGR, int JC>
+__global__ void __launch_bounds__(kFftMaxThreads, sizeof(T) == 4 ? 3 : 2) k_fft_st(
+    const void* __restrict__ in, int in_f64, void* __restrict__ out, int out_f64, int logN,
+    int logNs, int Jrt, int logJrt, int sign, const cplx<T>* __restrict__ tw, int lo_bits) {
+  using S = FftShape<T, LOGR>;
+  constexpr int R = S::R, LOGE = S::LOGE, E = S::E, TPC = S::TPC;
+  const int J = JC ? JC : Jrt;
+  int logJ = logJrt;
+  if (JC) {
+    logJ = 0;
+    while ((1 << logJ) < JC) ++logJ;
+  }
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cplx<T>* wR = reinterpret_cast<cplx<T>*>(smraw);  // [R] w_R^e
+  cplx<T>* X0 = wR + R;                             // [fft_pad(R J) + 1] columns
+  cplx<T>* X1 = X0 + (S::NBUF == 2 ? R * J + (R * J >> 5) + 1 : 0);
+  const uint32_t N = 1u << logN, nmask = N - 1, Ns = 1u << logNs;
+  const int lognr = logN - LOGR;  // NR = N / R
+  const uint32_t lo_mask = (1u << lo_bits) - 1;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const T sg = (T)sign;
+  for (int e = tid; e < R; e += nth)
+    wR[e] = twiddle32<T>(tw, (uint32_t)e << lognr, lo_bits, lo_mask, sg);
+  const int c = tid & (J - 1), q = tid >> logJ;
+  const uint32_t j0 = blockIdx.x * (uint32_t)J;
+  const uint32_t jg = j0 + c, jm = jg & (Ns - 1);
+  cplx<T> v[E];
+  {
+    const int lstep = logN - logNs - LOGR;  // N / (Ns R) = 2^lstep
+    const uint32_t idx = jg + ((uint32_t)q << lognr), stride = (uint32_t)TPC << lognr;
+    const uint32_t ex = ((q * jm) << lstep) & nmask, de = ((TPC * jm) << lstep) & nmask;
+    const size_t sig = (size_t)blockIdx.y * N;
+    if (in_f64)
+      fft_load<T, E>(v, reinterpret_cast<const double2*>(in) + sig, idx, stride, ex, de, nmask,
+                     tw, lo_bits, lo_mask, sg);
+    else
+      fft_load<T, E>(v, reinterpret_cast<const float2*>(in) + sig, idx, stride, ex, de, nmask,
+                     tw, lo_bits, lo_mask, sg);
+  }
+  __syncthreads();  // wR ready
+  fft_stage<T, LOGR, LOGE, 0, JC, true>(v, X0, X0, wR, J, c, q, sg);
+  cplx<T>* Xf = X0;
+  fft_stages<T, LOGR, JC, 1>(v, X0, X1, wR, J, c, q, sg, &Xf);
+  // Xf[r'][c] = A_r' of column c -> out
+  const size_t sig = (size_t)blockIdx.y * N;
+  if (Ns >= (uint32_t)J) {
+    // thread (c, q) writes r' = q + m TPC: J contiguous per r'
+    const uint32_t d0 = ((jg >> logNs) << (logNs + LOGR)) + jm + ((uint32_t)q << logNs);
+    const uint32_t dstep = (uint32_t)TPC << logNs;
+    const int e0 = q * J + c, p0 = fft_pad(e0);
+    if (out_f64) {
+      double2* o = reinterpret_cast<double2*>(out) + sig + d0;
+#pragma unroll
+      for (int m = 0; m < E; ++m) st_cv<T>(o + m * dstep, Xf[pad_add<JC>(e0, p0, m * TPC * J)]);
+    } else {
+      float2* o = reinterpret_cast<float2*>(out) + sig + d0;
+#pragma unroll
+      for (int m = 0; m < E; ++m) st_cv<T>(o + m * dstep, Xf[pad_add<JC>(e0, p0, m * TPC * J)]);
+    }
+  } else {
+    // small Ns: R contiguous per column
+    for (int e = tid; e < R * J; e += nth) {
+      const int jj = e >> LOGR, r = e & (R - 1);
+      const uint32_t jgg = j0 + jj, jmg = jgg & (Ns - 1);
+      const size_t dst = sig + ((jgg >> logNs) << (logNs + LOGR)) + jmg + ((uint32_t)r << logNs);
+      const cplx<T> val = Xf[fft_pad(r * J + jj)];
+      if (out_f64) st_cv<T>(reinterpret_cast<double2*>(out) + dst, val);
+      else st_cv<T>(reinterpret_cast<float2*>(out) + dst, val);
+    }
   }
 }
 
@@ -241,42 +376,40 @@ int fft_num_passes(int64_t N) {
   return fft_plan_passes(L, logR);
 }
 
-// out = FFT(in) in arithmetic T for `batch` signals of N elements each
-// (signal-major); in / out are complex128 (f64 = 1) or complex64.  Intermediate passes alternate between the scratch vectors buf
-// and buf2 (batch x N cplx<T> each; buf2 is used only with three or more passes), so
-// they keep T precision and never touch `out`.  `in` is only read.
-using FftKernel = void (*)(const void*, int, void*, int, int64_t, int64_t, int, int, int,
-                          const void*, int);
-
-template <class T, int LOG1, int LOG2>
+template <class T, int LR>
 static void fft_launch(dim3 grid, int threads, size_t smem, cudaStream_t st, const void* in,
-                       int in_f64, void* out, int out_f64, int64_t N, int64_t Ns, int J, int logJ,
-                       int sign, const cplx<T>* tw, int lo_bits, int staged) {
-  k_fft_reg<T, LOG1, LOG2><<<grid, threads, smem, st>>>(in, in_f64, out, out_f64, N, Ns, J, logJ,
-                                                         sign, tw, lo_bits, staged);
+                       int in_f64, void* out, int out_f64, int logN, int logNs, int J, int logJ,
+                       int sign, const cplx<T>* tw, int lo_bits) {
+  constexpr int JMAX = FftShape<T, LR>::JMAX;
+  if (J == JMAX)
+    k_fft_st<T, LR, JMAX><<<grid, threads, smem, st>>>(in, in_f64, out, out_f64, logN, logNs, J,
+                                                       logJ, sign, tw, lo_bits);
+  else
+    k_fft_st<T, LR, 0><<<grid, threads, smem, st>>>(in, in_f64, out, out_f64, logN, logNs, J,
+                                                    logJ, sign, tw, lo_bits);
 }
 
-// the pass kernel for logR = LOG1 + LOG2 (LOG1 = ceil(logR / 2))
+// the pass kernel for logR
 template <class T>
 static int fft_pass(int logR, dim3 grid, int threads, size_t smem, cudaStream_t st,
-                    const void* in, int in_f64, void* out, int out_f64, int64_t N, int64_t Ns,
-                    int J, int logJ, int sign, const cplx<T>* tw, int lo_bits, int staged) {
-#define NUFFT_FFT_CASE(L1, L2)                                                                 \
-  case L1 + L2:                                                                                \
-    fft_launch<T, L1, L2>(grid, threads, smem, st, in, in_f64, out, out_f64, N, Ns, J, logJ, \
-                          sign, tw, lo_bits, staged);                                          \
+                    const void* in, int in_f64, void* out, int out_f64, int logN, int logNs,
+                    int J, int logJ, int sign, const cplx<T>* tw, int lo_bits) {
+#define NUFFT_FFT_CASE(LR)                                                                  \
+  case LR:                                                                                 \
+    fft_launch<T, LR>(grid, threads, smem, st, in, in_f64, out, out_f64, logN, logNs, J, logJ, \
+                      sign, tw, lo_bits);                                                  \
     return NUFFT_OK;
   switch (logR) {
-    NUFFT_FFT_CASE(1, 0)
-    NUFFT_FFT_CASE(1, 1)
-    NUFFT_FFT_CASE(2, 1)
-    NUFFT_FFT_CASE(2, 2)
-    NUFFT_FFT_CASE(3, 2)
-    NUFFT_FFT_CASE(3, 3)
-    NUFFT_FFT_CASE(4, 3)
-    NUFFT_FFT_CASE(4, 4)
-    NUFFT_FFT_CASE(5, 4)
-    NUFFT_FFT_CASE(5, 5)
+    NUFFT_FFT_CASE(1)
+    NUFFT_FFT_CASE(2)
+    NUFFT_FFT_CASE(3)
+    NUFFT_FFT_CASE(4)
+    NUFFT_FFT_CASE(5)
+    NUFFT_FFT_CASE(6)
+    NUFFT_FFT_CASE(7)
+    NUFFT_FFT_CASE(8)
+    NUFFT_FFT_CASE(9)
+    NUFFT_FFT_CASE(10)
     default: return NUFFT_EINVAL;
   }
 #undef NUFFT_FFT_CASE
@@ -307,24 +440,24 @@ int fft_run(const void* in, int in_f64, void* out, int out_f64, cplx<T>* buf, cp
     void* dst = last ? out : (void*)((i & 1) ? buf2 : buf);
     int dst_f64 = last ? out_f64 : tf64;
     const int lr = logR[i];
-    const int R = 1 << lr, R2 = 1 << (lr / 2);
+    const int R = 1 << lr, TPC = R >= 8 ? R / 8 : 1;
     const int64_t NR = N >> lr;
-    // columns per CTA: at most 256 threads and kFftSmemElems staged
+    // columns per CTA: at most kFftMaxThreads threads and kFftSmemElems
     // elements, at least 4 (contiguous runs), fewer while the grid is small
-    int J = 256 / R2;
+    int J = kFftMaxThreads / TPC;
     while (J > 1 && (int64_t)R * J > kFftSmemElems) J >>= 1;
     while (J > 4 && (NR / J) * batch < target) J >>= 1;
     if (J > NR) J = (int)NR;
     int logJ = 0;
     while ((1 << logJ) < J) ++logJ;
-    // staged input: 16-byte aligned rows of at least 16 bytes
-    const size_t esz = src_f64 ? 16 : 8;
-    const int staged = ((uintptr_t)src % 16 == 0) && (J * esz >= 16);
-    const size_t elem = staged && esz > sizeof(cplx<T>) ? esz : sizeof(cplx<T>);
-    size_t smem = (size_t)R * sizeof(cplx<T>) + (size_t)R * J * elem;
+    const size_t nbuf = sizeof(T) == 4 ? 2 : 1;
+    const size_t smem =
+        ((size_t)R + nbuf * ((size_t)R * J + (size_t)R * J / 32 + 1)) * sizeof(cplx<T>);
     unsigned grid = (unsigned)(NR / J);
-    int rc = fft_pass<T>(lr, dim3(grid, (unsigned)batch), J * R2, smem, st, src, src_f64, dst,
-                         dst_f64, N, Ns, J, logJ, sign, tw, b, staged);
+    int logNs = 0;
+    while ((int64_t(1) << logNs) < Ns) ++logNs;
+    int rc = fft_pass<T>(lr, dim3(grid, (unsigned)batch), J * TPC, smem, st, src, src_f64, dst,
+                         dst_f64, L, logNs, J, logJ, sign, tw, b);
     if (rc) return rc;
     src = dst;
     src_f64 = dst_f64;
@@ -333,26 +466,31 @@ int fft_run(const void* in, int in_f64, void* out, int out_f64, cplx<T>* buf, cp
   return cudaGetLastError() == cudaSuccess ? NUFFT_OK : NUFFT_ECUDA;
 }
 
-template <class T, int LOG1, int LOG2>
+template <class T, int LR>
 static int fft_attr() {
-  const int big = (int)(kFftSmemElems * 16 + 1024 * sizeof(cplx<T>));
-  return cudaFuncSetAttribute(k_fft_reg<T, LOG1, LOG2>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize, big) == cudaSuccess
+  const int nbuf = sizeof(T) == 4 ? 2 : 1;
+  const int big =
+      (int)((1024 + nbuf * (kFftSmemElems + kFftSmemElems / 32 + 1)) * sizeof(cplx<T>));
+  return cudaFuncSetAttribute(k_fft_st<T, LR, FftShape<T, LR>::JMAX>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, big) == cudaSuccess &&
+                 cudaFuncSetAttribute(k_fft_st<T, LR, 0>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      big) == cudaSuccess
              ? NUFFT_OK : NUFFT_ECUDA;
 }
 
 template <class T>
 static int fft_attrs() {
-  int rc = fft_attr<T, 1, 0>();
-  if (!rc) rc = fft_attr<T, 1, 1>();
-  if (!rc) rc = fft_attr<T, 2, 1>();
-  if (!rc) rc = fft_attr<T, 2, 2>();
-  if (!rc) rc = fft_attr<T, 3, 2>();
-  if (!rc) rc = fft_attr<T, 3, 3>();
-  if (!rc) rc = fft_attr<T, 4, 3>();
-  if (!rc) rc = fft_attr<T, 4, 4>();
-  if (!rc) rc = fft_attr<T, 5, 4>();
-  if (!rc) rc = fft_attr<T, 5, 5>();
+  int rc = fft_attr<T, 1>();
+  if (!rc) rc = fft_attr<T, 2>();
+  if (!rc) rc = fft_attr<T, 3>();
+  if (!rc) rc = fft_attr<T, 4>();
+  if (!rc) rc = fft_attr<T, 5>();
+  if (!rc) rc = fft_attr<T, 6>();
+  if (!rc) rc = fft_attr<T, 7>();
+  if (!rc) rc = fft_attr<T, 8>();
+  if (!rc) rc = fft_attr<T, 9>();
+  if (!rc) rc = fft_attr<T, 10>();
   return rc;
 }
 

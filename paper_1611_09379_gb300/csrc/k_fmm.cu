@@ -50,8 +50,18 @@ __global__ void k_p2m_uniform(TreeDims d, const cplx<T>* __restrict__ q,
 
 
 // Non-uniform sources: one warp per leaf; a chunk of 32 sources writes
-// q rho^m for 32 consecutive m into shared memory, lanes then reduce rows.
-template <class T> struct P2mWarps { static constexpr int value = sizeof(T) == 8 ? 2 : 4; };
+// q rho^m for up to 32 consecutive m (the moments of this pass, nm rows)
+// into shared memory, lanes then reduce rows.  The source's offset in the
+// leaf comes from its grid index alone: o = (k0 - b s) mod N lies in
+// [0, s] for every source binned into leaf b.
+template <class T> struct P2mWarps { static constexpr int value = 4; };
+constexpr int kP2mPitch = 33;  // row pitch of the tile (odd: no bank conflicts)
+
+template <class T>
+size_t p2m_smem(int pm) {
+  const int rows = pm < 32 ? pm : 32;
+  return (size_t)P2mWarps<T>::value * rows * kP2mPitch * sizeof(cplx<T>);
+}
 
 // rho = (o + delta) / s - 1/2 in T: 1/s is a power of two, so the only
 // roundings are of o + delta and of the final subtraction (no division).
@@ -59,48 +69,53 @@ template <class T>
 __global__ void __launch_bounds__(128) k_p2m_nonuniform(TreeDims d,
                                                         const int32_t* __restrict__ start,
                                                         const int32_t* __restrict__ k0,
-                                                        const double* __restrict__ delta,
                                                         const T* __restrict__ delta_t,
                                                         const cplx<T>* __restrict__ charge,
                                                         cplx<T>* __restrict__ mleaf) {
-  constexpr int WPB = P2mWarps<T>::value;  // keeps the tile under 48 KB
-  __shared__ cplx<T> tile[WPB][32][33];
-  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int64_t B = int64_t(1) << d.L;
-  int64_t b = blockIdx.x * WPB + warp;
+  constexpr int WPB = P2mWarps<T>::value;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int rows = d.pm < 32 ? d.pm : 32;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  cplx<T>* tile = reinterpret_cast<cplx<T>*>(smraw) + warp * rows * kP2mPitch;
+  const int64_t B = int64_t(1) << d.L;
+  const int64_t b = blockIdx.x * WPB + warp;
   if (b >= B) return;
   charge += blockIdx.y * d.M_;
   mleaf += blockIdx.y * d.mstride;
-  int32_t a = start[b], e = start[b + 1];
+  const int32_t a = start[b], e = start[b + 1];
   const int N = (int)d.N;
+  const int bs = (int)b * d.s;
   const T inv_s = (T)1 / (T)d.s;
   for (int mc = 0; mc < d.pm; mc += 32) {
+    const int nm = d.pm - mc < 32 ? d.pm - mc : 32;
     T accr = 0, acci = 0;
     for (int c0 = a; c0 < e; c0 += 32) {
-      int i = c0 + lane;
+      const int i = c0 + lane;
       cplx<T> q = mk<T>(0, 0);
       T rho = 0;
       if (i < e) {
-        int lb, o;
-        point_local(k0[i], delta[i], N, d.s, &lb, &o);
+        const int o = (k0[i] - bs) & (N - 1);
         rho = fma((T)o + delta_t[i], inv_s, (T)-0.5);
         q = charge[i];
       }
       T pw = 1;
       for (int m = 0; m < mc; ++m) pw *= rho;
-      for (int m = 0; m < 32; ++m) {
-        tile[warp][m][lane] = mk<T>(q.x * pw, q.y * pw);
+      for (int m = 0; m < nm; ++m) {
+        tile[m * kP2mPitch + lane] = mk<T>(q.x * pw, q.y * pw);
         pw *= rho;
       }
       __syncwarp();
-      for (int k = 0; k < 32; ++k) {
-        cplx<T> v = tile[warp][lane][k];
-        accr += v.x;
-        acci += v.y;
+      const int nk = e - c0 < 32 ? e - c0 : 32;
+      if (lane < nm) {
+        for (int k = 0; k < nk; ++k) {
+          const cplx<T> v = tile[lane * kP2mPitch + k];
+          accr += v.x;
+          acci += v.y;
+        }
       }
       __syncwarp();
     }
-    if (mc + lane < d.pm) mleaf[b * d.pm + mc + lane] = mk<T>(accr, acci);
+    if (lane < nm) mleaf[b * d.pm + mc + lane] = mk<T>(accr, acci);
   }
 }
 
@@ -567,6 +582,12 @@ template <class T> struct SrcPos;
 template <> struct SrcPos<float> { int k0; float dl; };
 template <> struct SrcPos<double> { long long k0; double dl; };
 
+// Staged source of the two-point adjoint / inverse near field: position
+// (x relative to the CTA, delta) and charge, one 16-byte load in FP32.
+template <class T> struct __align__(16) SrcQ {
+  cplx<T> rel, q;
+};
+
 // Targets per CTA and the capacity of the staged near-field windows.
 constexpr int kTgtThreads = 256;
 template <class T, int G> struct NearCap {
@@ -620,6 +641,30 @@ __device__ inline void near_window_ex(int lo, int hi, int ex, NearAcc<T>* acc, T
   }
   if (i < hi) {
     for (int u = 0; u < hi - i; ++u) term(i, u, std::true_type());
+#pragma unroll
+    for (int gg = 0; gg < G; ++gg) acc[gg].fold();
+  }
+}
+
+// near_window_ex over [0, n), n even, two terms per call: term(i, u, check)
+// adds terms i + u and i + u + 1 (u even), so a 16-byte load can fetch both
+// FP32 samples.
+template <class T, int G, class Term>
+__device__ inline void near_window_ex2(int n, int ex, NearAcc<T>* acc, Term term) {
+  int i = 0;
+  for (; i + 16 <= n; i += 16) {
+    if (G > 1 || (ex - i >= 0 && ex - i < 16)) {
+#pragma unroll
+      for (int u = 0; u < 16; u += 2) term(i, u, std::true_type());
+    } else if (G == 1) {
+#pragma unroll
+      for (int u = 0; u < 16; u += 2) term(i, u, std::false_type());
+    }
+#pragma unroll
+    for (int gg = 0; gg < G; ++gg) acc[gg].fold();
+  }
+  if (i < n) {
+    for (int u = 0; u < n - i; u += 2) term(i, u, std::true_type());
 #pragma unroll
     for (int gg = 0; gg < G; ++gg) acc[gg].fold();
   }
@@ -690,6 +735,26 @@ __global__ void __launch_bounds__(kTgtThreads) k_targets_fwd(
   // the pair with x_k0 (window index o + s, D = 0) is left out: E_j carries it
   const int ex = o + s;
   if (hnear) {
+  } else if (std::is_same<T, float>::value && (s & 1) == 0 && staged && b >= bl && b <= bh) {
+    // FP32, even s: samples c, c + 1 (c even) in one 16-byte load (nwin and
+    // (b - bl) s are even, so every pair is 16-byte aligned)
+    if constexpr (std::is_same<T, float>::value) {
+      const float2* w = sf + (b - bl) * s;
+      near_window_ex2<T, G>(3 * s, ex, acc, [&](int i, int u, auto chk) {
+        const T ta = (D0 - (T)i) - (T)u, tb = ta - (T)1;
+        T ra = rcp_t(ta + dt), rb = rcp_t(tb + dt);
+        if (decltype(chk)::value) {
+          ra = ta == (T)0 ? (T)0 : ra;
+          rb = tb == (T)0 ? (T)0 : rb;
+        }
+#pragma unroll
+        for (int gg = 0; gg < G; ++gg) {
+          const float4 q = *reinterpret_cast<const float4*>(w + gg * nwin + i + u);
+          acc[gg].add_r(make_float2(q.x, q.y), ra);
+          acc[gg].add_r(make_float2(q.z, q.w), rb);
+        }
+      });
+    }
   } else if (staged && b >= bl && b <= bh) {
     const cplx<T>* w = sf + (b - bl) * s;  // leaf b - 1 of the window
     near_window_ex<T, G>(0, 3 * s, ex, acc, [&](int i, int u, auto chk) {
@@ -978,8 +1043,9 @@ __global__ void __launch_bounds__(kTgtThreads) k_targets_grid(
 }
 
 // k_targets_grid for one signal with two adjacent grid points k, k + 1 per
-// thread (same leaf: s is even): every staged source is read once for both
-// points, which halves the shared-memory traffic of the pair loop.  The
+// thread (same leaf: s is even): every staged source (position and charge
+// in one record) is read once for both points, which halves the
+// shared-memory instructions of the pair loop.  The
 // window is sorted by x, so the sources with k0 = k and those with
 // k0 = k + 1 are two consecutive runs: each point takes the self terms of its
 // own run and the pair of the other's.  Same arithmetic per pair as
@@ -994,9 +1060,8 @@ __global__ void __launch_bounds__(kTgtThreads) k_targets_grid2(
   constexpr int kPts = 2 * kTgtThreads;
   constexpr int kMaxSlots = kTgtThreads + 3;  // kPts / s + 3 with s >= 2
   extern __shared__ __align__(16) unsigned char smraw[];
-  cplx<T>* srel = reinterpret_cast<cplx<T>*>(smraw);  // [CAP] (x, delta)
-  cplx<T>* sq = srel + CAP;                            // [CAP] charges
-  cplx<T>* sst = sq + CAP;                             // [CAP] self terms
+  SrcQ<T>* sw = reinterpret_cast<SrcQ<T>*>(smraw);          // [CAP] (x, delta), charge
+  cplx<T>* sst = reinterpret_cast<cplx<T>*>(sw + CAP);      // [CAP] self terms
   __shared__ int s_off[kMaxSlots + 1];
   const int N = (int)d.N;
   const int s = d.s;
@@ -1037,12 +1102,11 @@ __global__ void __launch_bounds__(kTgtThreads) k_targets_grid2(
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // both points' pairs with source i
   auto both = [&](int i) {
-    const cplx<T> rp = srel[i];
-    const T e0 = kf0 - rp.x;
-    const T r0 = rcp_t(e0 - rp.y), r1 = rcp_t((e0 + (T)1) - rp.y);
-    const cplx<T> q = sq[i];
-    acc0.add_r(q, r0);
-    acc1.add_r(q, r1);
+    const SrcQ<T> v = sw[i];  // one 16-byte load (FP32)
+    const T e0 = kf0 - v.rel.x;
+    const T r0 = rcp_t(e0 - v.rel.y), r1 = rcp_t((e0 + (T)1) - v.rel.y);
+    acc0.add_r(v.q, r0);
+    acc1.add_r(v.q, r1);
   };
   auto span = [&](int lo, int hi) {  // [lo, hi): chunks of 16, folded
     int i = lo;
@@ -1075,8 +1139,10 @@ __global__ void __launch_bounds__(kTgtThreads) k_targets_grid2(
         const int gi = g0 + e;
         const SrcPos<T> ps = pos[gi];
         const int xu = bu * s + (((int)ps.k0 - bb * s) & (N - 1)) - kb;
-        srel[e - c0] = mk<T>((T)xu, ps.dl);
-        sq[e - c0] = charge[gi];
+        SrcQ<T> v;
+        v.rel = mk<T>((T)xu, ps.dl);
+        v.q = charge[gi];
+        sw[e - c0] = v;
         sst[e - c0] = st[gi];
       }
     }
@@ -1087,19 +1153,17 @@ __global__ void __launch_bounds__(kTgtThreads) k_targets_grid2(
       int ha = lo, hb = hi;
       while (ha < hb) {
         const int mid = (ha + hb) >> 1;
-        if (srel[mid].x < kf0) ha = mid + 1; else hb = mid;
+        if (sw[mid].rel.x < kf0) ha = mid + 1; else hb = mid;
       }
       int h1 = ha;
-      for (; h1 < hi && srel[h1].x == kf0; ++h1) {
+      for (; h1 < hi && sw[h1].rel.x == kf0; ++h1) {
         self0 = cadd(self0, sst[h1]);
-        const cplx<T> rp = srel[h1];
-        acc1.add_r(sq[h1], rcp_t((T)1 - rp.y));
+        acc1.add_r(sw[h1].q, rcp_t((T)1 - sw[h1].rel.y));
       }
       int h2 = h1;
-      for (; h2 < hi && srel[h2].x == kf1; ++h2) {
+      for (; h2 < hi && sw[h2].rel.x == kf1; ++h2) {
         self1 = cadd(self1, sst[h2]);
-        const cplx<T> rp = srel[h2];
-        acc0.add_r(sq[h2], rcp_t((T)-1 - rp.y));
+        acc0.add_r(sw[h2].q, rcp_t((T)-1 - sw[h2].rel.y));
       }
       acc0.fold();
       acc1.fold();
@@ -1181,7 +1245,9 @@ int fmm_configure() {
       cudaFuncSetAttribute(k_down_sub<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            big) != cudaSuccess ||
       cudaFuncSetAttribute(k_level2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           4 * 66 * 66 * (int)sizeof(double)) != cudaSuccess)
+                           4 * 66 * 66 * (int)sizeof(double)) != cudaSuccess ||
+      cudaFuncSetAttribute(k_p2m_nonuniform<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)p2m_smem<T>(32)) != cudaSuccess)
     return NUFFT_ECUDA;
   return NUFFT_OK;
 }
@@ -1241,8 +1307,8 @@ int fmm_upward_downward(nufft_plan_s* pl, const FmmOps& ops, bool uniform_source
         d, charge, (const T*)pl->op_p2m, mleaf);
   } else {
     constexpr int WPB = P2mWarps<T>::value;
-    k_p2m_nonuniform<T><<<dim3(nblk(B, WPB), nsig), 32 * WPB, 0, st>>>(
-        d, pl->leaf_start, pl->k0, pl->delta, PlanT<T>::delta(pl), charge, mleaf);
+    k_p2m_nonuniform<T><<<dim3(nblk(B, WPB), nsig), 32 * WPB, p2m_smem<T>(pl->pm), st>>>(
+        d, pl->leaf_start, pl->k0, PlanT<T>::delta(pl), charge, mleaf);
   }
   if (ops.leaf_shift)
     k_leaf_shift<T><<<nblk(B * pl->pm, 256), 256, 0, st>>>(B, pl->pm, ops.leaf_shift, mleaf);
