@@ -117,6 +117,38 @@ enum DevStatus : int {
   kDevTimeout = 8,      // a bounded wait (tensor-core barrier) gave up
 };
 
+// Programmatic dependent launch.  Kernels of a transform are launched with
+// programmatic stream serialization (launch_pdl), so a kernel's CTAs may
+// start while its predecessor in the stream is still finishing.  Every such
+// kernel calls pdl_wait() before it reads or writes any global data that an
+// earlier kernel of the stream touches (only constant plan tables may be read
+// before it); griddepcontrol.wait returns once the predecessor grid has
+// completed and its writes are visible, and is a no-op for a kernel launched
+// without the attribute.  pdl_trigger() lets the successor's launch begin
+// once every CTA of this grid has started.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+bool pdl_enabled();  // false when the environment sets NUFFT_NO_PDL
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl_enabled() ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 }  // namespace nufft
 
 // One kernel's FMM operator set (device pointers): the cot kernel's 1/t

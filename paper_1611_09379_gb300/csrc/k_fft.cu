@@ -282,6 +282,9 @@ __global__ void __launch_bounds__(kFftMaxThreads, sizeof(T) == 4 ? 3 : 2) k_fft_
   const T sg = (T)sign;
   for (int e = tid; e < R; e += nth)
     wR[e] = twiddle32<T>(tw, (uint32_t)e << lognr, lo_bits, lo_mask, sg);
+  // (the twiddle tables are plan constants: read before the predecessor ends)
+  pdl_wait();
+  pdl_trigger();
   const int c = tid & (J - 1), q = tid >> logJ;
   const uint32_t j0 = blockIdx.x * (uint32_t)J;
   const uint32_t jg = j0 + c, jm = jg & (Ns - 1);
@@ -382,11 +385,11 @@ static void fft_launch(dim3 grid, int threads, size_t smem, cudaStream_t st, con
                        int sign, const cplx<T>* tw, int lo_bits) {
   constexpr int JMAX = FftShape<T, LR>::JMAX;
   if (J == JMAX)
-    k_fft_st<T, LR, JMAX><<<grid, threads, smem, st>>>(in, in_f64, out, out_f64, logN, logNs, J,
-                                                       logJ, sign, tw, lo_bits);
+    launch_pdl(k_fft_st<T, LR, JMAX>, grid, threads, smem, st, in, in_f64, out, out_f64, logN,
+               logNs, J, logJ, sign, tw, lo_bits);
   else
-    k_fft_st<T, LR, 0><<<grid, threads, smem, st>>>(in, in_f64, out, out_f64, logN, logNs, J,
-                                                    logJ, sign, tw, lo_bits);
+    launch_pdl(k_fft_st<T, LR, 0>, grid, threads, smem, st, in, in_f64, out, out_f64, logN, logNs,
+               J, logJ, sign, tw, lo_bits);
 }
 
 // the pass kernel for logR

@@ -30,6 +30,8 @@ namespace nufft {
 template <class T>
 __global__ void k_p2m_uniform(TreeDims d, const cplx<T>* __restrict__ q,
                               const T* __restrict__ rp, cplx<T>* __restrict__ mleaf) {
+  pdl_wait();
+  pdl_trigger();
   int64_t B = int64_t(1) << d.L;
   int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (tid >= B * d.pm) return;
@@ -72,6 +74,8 @@ __global__ void __launch_bounds__(128) k_p2m_nonuniform(TreeDims d,
                                                         const T* __restrict__ delta_t,
                                                         const cplx<T>* __restrict__ charge,
                                                         cplx<T>* __restrict__ mleaf) {
+  pdl_wait();
+  pdl_trigger();
   constexpr int WPB = P2mWarps<T>::value;
   extern __shared__ __align__(16) unsigned char smraw[];
   const int rows = d.pm < 32 ? d.pm : 32;
@@ -123,6 +127,8 @@ __global__ void __launch_bounds__(128) k_p2m_nonuniform(TreeDims d,
 template <class T>
 __global__ void k_leaf_shift(int64_t B, int pm, const double* __restrict__ shift,
                              cplx<T>* __restrict__ mleaf) {
+  pdl_wait();
+  pdl_trigger();
   int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (tid >= B * pm) return;
   int m = (int)(tid % pm);
@@ -159,6 +165,9 @@ __global__ void __launch_bounds__(512) k_up_sub(TreeDims d, int lb, int lt, cons
   const int depth = lb - lt;
   cplx<T>* nxt = cur + (pm << depth);
   for (int i = threadIdx.x; i < 2 * pm * pm; i += blockDim.x) A[i] = op[i];
+  // (operator tables are plan constants: read before the predecessor ends)
+  pdl_wait();
+  pdl_trigger();
   mexp += blockIdx.y * d.mstride;
   const int64_t b0 = (int64_t)blockIdx.x << depth;  // first box at level lb
   const cplx<T>* src = mexp + (level_off(lb) + b0) * pm;
@@ -189,6 +198,9 @@ __global__ void __launch_bounds__(512) k_up_top(TreeDims d, int lb, const T* __r
   cplx<T>* cur = reinterpret_cast<cplx<T>*>(A + 2 * pm * pm);  // [2^lb * pm]
   cplx<T>* nxt = cur + (pm << lb);                             // [2^(lb-1) * pm]
   for (int i = threadIdx.x; i < 2 * pm * pm; i += blockDim.x) A[i] = op[i];
+  // (operator tables are plan constants: read before the predecessor ends)
+  pdl_wait();
+  pdl_trigger();
   mexp += blockIdx.y * d.mstride;
   const cplx<T>* src = mexp + level_off(lb) * pm;
   for (int i = threadIdx.x; i < (pm << lb); i += blockDim.x) cur[i] = src[i];
@@ -281,6 +293,8 @@ __global__ void __launch_bounds__(256) k_m2l_all(TreeDims d, int l0, int l1,
                                                  const cplx<T>* __restrict__ mexp,
                                                  cplx<T>* __restrict__ lexp, int log_kernel,
                                                  int log2N) {
+  pdl_wait();
+  pdl_trigger();
   extern __shared__ unsigned char smraw[];
   T* Tm = reinterpret_cast<T*>(smraw);
   const int p = d.p, pm = d.pm;
@@ -321,6 +335,9 @@ __global__ void __launch_bounds__(512) k_down_top(TreeDims d, int lt, const T* _
   cplx<T>* Lb = La + nmax * p;                               // [nmax * p]
   for (int i = threadIdx.x; i < 4 * p * p; i += blockDim.x) Tm[i] = op_m2l[i];
   for (int i = threadIdx.x; i < 2 * p * p; i += blockDim.x) Tl[i] = op_l2l[i];
+  // (operator tables are plan constants: read before the predecessor ends)
+  pdl_wait();
+  pdl_trigger();
   mexp += blockIdx.y * d.mstride;
   lexp += blockIdx.y * d.lstride;
   cplx<T>* par = La;
@@ -380,6 +397,9 @@ __global__ void __launch_bounds__(512) k_down_sub(TreeDims d, int lt, int lb,
   cplx<T>* Lb = La + (p << depth);                           // [2^depth * p]
   for (int i = threadIdx.x; i < 4 * p * p; i += blockDim.x) Tm[i] = op_m2l[i];
   for (int i = threadIdx.x; i < 2 * p * p; i += blockDim.x) Tl[i] = op_l2l[i];
+  // (operator tables are plan constants: read before the predecessor ends)
+  pdl_wait();
+  pdl_trigger();
   mexp += blockIdx.y * d.mstride;
   lexp += blockIdx.y * d.lstride;
   // root local expansion
@@ -439,6 +459,8 @@ template <class T>
 __global__ void k_level2(TreeDims d, int nq, const double* __restrict__ op, double c1, double c2,
                          const cplx<T>* __restrict__ mexp, double2* __restrict__ out,
                          float2* __restrict__ outf) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ double2 mu[4][66];
   __shared__ double2 A1[4][66];
   extern __shared__ double sop[];  // the four weight tables, staged once
@@ -692,6 +714,8 @@ __global__ void __launch_bounds__(kTgtThreads) k_targets_fwd(
     const cplx<T>* __restrict__ E, const cplx<T>* __restrict__ fgrid,
     const cplx<T>* __restrict__ lexp, const cplx<T>* __restrict__ lvl2,
     const cplx<T>* __restrict__ hnear, VO* __restrict__ g) {
+  pdl_wait();
+  pdl_trigger();
   extern __shared__ __align__(16) unsigned char smraw[];
   cplx<T>* sf = reinterpret_cast<cplx<T>*>(smraw);  // [G][window]
   __shared__ int s_lo, s_hi;
@@ -821,6 +845,8 @@ template <class T, class VI>
 __global__ void k_charges(int64_t M, const int32_t* __restrict__ perm,
                           const cplx<T>* __restrict__ coef, int conj_coef,
                           const VI* __restrict__ gin, cplx<T>* __restrict__ charge) {
+  pdl_wait();
+  pdl_trigger();
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= M) return;
   gin += blockIdx.y * M;
@@ -848,6 +874,8 @@ __global__ void k_self_terms(int M, int inverse, int N, const int32_t* __restric
                              const VI* __restrict__ gin, const double* __restrict__ Ct,
                              const T* __restrict__ Ctt, const T* __restrict__ delt, T n_2pi,
                              cplx<T>* __restrict__ st) {
+  pdl_wait();
+  pdl_trigger();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= M) return;
   gin += (int64_t)blockIdx.y * M;
@@ -915,6 +943,8 @@ __global__ void __launch_bounds__(kTgtThreads) k_targets_grid(
     const SrcPos<T>* __restrict__ pos, const cplx<T>* __restrict__ charge,
     const cplx<T>* __restrict__ st, const cplx<T>* __restrict__ lexp,
     const cplx<T>* __restrict__ lvl2, const T* __restrict__ Ct, cplx<T>* __restrict__ out) {
+  pdl_wait();
+  pdl_trigger();
   constexpr int CAP = NearCap<T, G>::grid;
   constexpr int kMaxSlots = kTgtThreads + 3;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -1056,6 +1086,8 @@ __global__ void __launch_bounds__(kTgtThreads) k_targets_grid2(
     const SrcPos<T>* __restrict__ pos, const cplx<T>* __restrict__ charge,
     const cplx<T>* __restrict__ st, const cplx<T>* __restrict__ lexp,
     const cplx<T>* __restrict__ lvl2, const T* __restrict__ Ct, cplx<T>* __restrict__ out) {
+  pdl_wait();
+  pdl_trigger();
   constexpr int CAP = NearCap<T, 1>::grid;
   constexpr int kPts = 2 * kTgtThreads;
   constexpr int kMaxSlots = kTgtThreads + 3;  // kPts / s + 3 with s >= 2
@@ -1303,15 +1335,16 @@ int fmm_upward_downward(nufft_plan_s* pl, const FmmOps& ops, bool uniform_source
   cplx<T>* mleaf = mexp + level_off(pl->L) * pl->pm;
   prof_begin(pl, NUFFT_STAGE_P2M);
   if (uniform_sources) {
-    k_p2m_uniform<T><<<dim3(nblk(B * pl->pm, 256), nsig), 256, 0, st>>>(
-        d, charge, (const T*)pl->op_p2m, mleaf);
+    launch_pdl(k_p2m_uniform<T>, dim3(nblk(B * pl->pm, 256), nsig), 256, 0, st, d, charge,
+               (const T*)pl->op_p2m, mleaf);
   } else {
     constexpr int WPB = P2mWarps<T>::value;
-    k_p2m_nonuniform<T><<<dim3(nblk(B, WPB), nsig), 32 * WPB, p2m_smem<T>(pl->pm), st>>>(
-        d, pl->leaf_start, pl->k0, PlanT<T>::delta(pl), charge, mleaf);
+    launch_pdl(k_p2m_nonuniform<T>, dim3(nblk(B, WPB), nsig), 32 * WPB, p2m_smem<T>(pl->pm), st,
+               d, pl->leaf_start, pl->k0, PlanT<T>::delta(pl), charge, mleaf);
   }
   if (ops.leaf_shift)
-    k_leaf_shift<T><<<nblk(B * pl->pm, 256), 256, 0, st>>>(B, pl->pm, ops.leaf_shift, mleaf);
+    launch_pdl(k_leaf_shift<T>, nblk(B * pl->pm, 256), 256, 0, st, B, pl->pm, ops.leaf_shift,
+               mleaf);
   prof_end(pl, ops.leaf_shift ? 2 : 1);
   // upward: subtrees of up to kSubDepth levels down to level kTopLevel, then one CTA
   prof_begin(pl, NUFFT_STAGE_M2M);
@@ -1322,14 +1355,14 @@ int fmm_upward_downward(nufft_plan_s* pl, const FmmOps& ops, bool uniform_source
     int dep = kSubDepth;
     while (dep > 1 && up_sub_smem<T>(pm, dep) > kSmemBudget) --dep;
     int lt = lev - dep > kTopLevel ? lev - dep : kTopLevel;
-    k_up_sub<T><<<dim3(1u << lt, nsig), 512, up_sub_smem<T>(pm, lev - lt), st>>>(
-        d, lev, lt, (const T*)pl->op_m2m, mexp);
+    launch_pdl(k_up_sub<T>, dim3(1u << lt, nsig), 512, up_sub_smem<T>(pm, lev - lt), st, d, lev,
+               lt, (const T*)pl->op_m2m, mexp);
     ++nl;
     lev = lt;
   }
   if (lev > 2) {
     size_t sm = (size_t)2 * pm * pm * sizeof(T) + (size_t)3 * ((size_t)pm << lev) / 2 * sizeof(cplx<T>);
-    k_up_top<T><<<dim3(1, nsig), 512, sm, st>>>(d, lev, (const T*)pl->op_m2m, mexp);
+    launch_pdl(k_up_top<T>, dim3(1, nsig), 512, sm, st, d, lev, (const T*)pl->op_m2m, mexp);
     ++nl;
   }
   prof_end(pl, nl);
@@ -1337,8 +1370,8 @@ int fmm_upward_downward(nufft_plan_s* pl, const FmmOps& ops, bool uniform_source
   prof_begin(pl, NUFFT_STAGE_LEVEL2);
   {
     cudaStream_t s2 = side_begin(pl, 0);
-    k_level2<T><<<nsig, 256, (size_t)4 * ops.nq * ops.nq * sizeof(double), s2>>>(
-        d, ops.nq, ops.reg, ops.c1, ops.c2, mexp, lvl2, lvl2f);
+    launch_pdl(k_level2<T>, nsig, 256, (size_t)4 * ops.nq * ops.nq * sizeof(double), s2, d,
+               ops.nq, ops.reg, ops.c1, ops.c2, mexp, lvl2, lvl2f);
     side_end(pl, 0, s2);
   }
   prof_end(pl, 1);
@@ -1366,14 +1399,14 @@ int fmm_upward_downward(nufft_plan_s* pl, const FmmOps& ops, bool uniform_source
     if (pre) {
       const int64_t nout = (level_off(L + 1) - level_off(3)) * (int64_t)p;
       const unsigned nbk = (unsigned)((nout + 255) / 256);
-      k_m2l_all<T><<<dim3(nbk, nsig), 256, (size_t)4 * p * p * sizeof(T), st>>>(
-          d, 3, L, (const T*)ops.m2l, mexp, lexp, ops.log_kernel, log2N);
+      launch_pdl(k_m2l_all<T>, dim3(nbk, nsig), 256, (size_t)4 * p * p * sizeof(T), st, d, 3, L,
+                 (const T*)ops.m2l, mexp, lexp, ops.log_kernel, log2N);
       ++nl;
-      k_down_top<T, true><<<dim3(1, nsig), 512, smt, st>>>(
-          d, top, (const T*)ops.m2l, (const T*)ops.l2l, mexp, lexp, ops.log_kernel, log2N);
+      launch_pdl(k_down_top<T, true>, dim3(1, nsig), 512, smt, st, d, top, (const T*)ops.m2l,
+                 (const T*)ops.l2l, mexp, lexp, ops.log_kernel, log2N);
     } else {
-      k_down_top<T, false><<<dim3(1, nsig), 512, smt, st>>>(
-          d, top, (const T*)ops.m2l, (const T*)ops.l2l, mexp, lexp, ops.log_kernel, log2N);
+      launch_pdl(k_down_top<T, false>, dim3(1, nsig), 512, smt, st, d, top, (const T*)ops.m2l,
+                 (const T*)ops.l2l, mexp, lexp, ops.log_kernel, log2N);
     }
     ++nl;
     int dep = kSubDepth;
@@ -1384,11 +1417,13 @@ int fmm_upward_downward(nufft_plan_s* pl, const FmmOps& ops, bool uniform_source
     for (int c = nc - 1; c >= 0; --c) {
       int lb = cuts[c];
       if (pre)
-        k_down_sub<T, true><<<dim3(1u << lt, nsig), 512, down_sub_smem<T>(p, lb - lt), st>>>(
-            d, lt, lb, (const T*)ops.m2l, (const T*)ops.l2l, mexp, lexp, ops.log_kernel, log2N);
+        launch_pdl(k_down_sub<T, true>, dim3(1u << lt, nsig), 512, down_sub_smem<T>(p, lb - lt),
+                   st, d, lt, lb, (const T*)ops.m2l, (const T*)ops.l2l, mexp, lexp,
+                   ops.log_kernel, log2N);
       else
-        k_down_sub<T, false><<<dim3(1u << lt, nsig), 512, down_sub_smem<T>(p, lb - lt), st>>>(
-            d, lt, lb, (const T*)ops.m2l, (const T*)ops.l2l, mexp, lexp, ops.log_kernel, log2N);
+        launch_pdl(k_down_sub<T, false>, dim3(1u << lt, nsig), 512, down_sub_smem<T>(p, lb - lt),
+                   st, d, lt, lb, (const T*)ops.m2l, (const T*)ops.l2l, mexp, lexp,
+                   ops.log_kernel, log2N);
       ++nl;
       lt = lb;
     }
@@ -1419,10 +1454,9 @@ template <class T, class VO, int G>
 static void launch_targets_fwd(nufft_plan_s* pl, const TreeDims& d, const cplx<T>* f,
                                const cplx<T>* hnear, void* g) {
   dim3 grid(nblk(pl->M, kTgtThreads), (unsigned)(pl->batch / G));
-  k_targets_fwd<T, VO, G><<<grid, kTgtThreads, NearCap<T, G>::fwd_bytes, pl->stream>>>(
-      d, (int)pl->M, pl->k0, pl->delta, PlanT<T>::delta(pl), pl->perm, PlanT<T>::F(pl),
-      PlanT<T>::E(pl), f,
-      (const cplx<T>*)pl->lexp, PlanT<T>::lvl2(pl), hnear, (VO*)g);
+  launch_pdl(k_targets_fwd<T, VO, G>, grid, kTgtThreads, NearCap<T, G>::fwd_bytes, pl->stream, d,
+             (int)pl->M, pl->k0, pl->delta, PlanT<T>::delta(pl), pl->perm, PlanT<T>::F(pl),
+             PlanT<T>::E(pl), f, (const cplx<T>*)pl->lexp, PlanT<T>::lvl2(pl), hnear, (VO*)g);
 }
 
 int near_tc_forward(const TreeDims& d, int M, int batch, const int32_t* k0s, const double* dels,
@@ -1472,11 +1506,11 @@ int fmm_to_grid(nufft_plan_s* pl, const void* g, int inverse) {
   const dim3 gm(nblk(pl->M, 256), nsig);
   prof_begin(pl, NUFFT_STAGE_P2M);
   if (c64)
-    k_charges<T, float2><<<gm, 256, 0, st>>>(pl->M, pl->perm, coef, !inverse, (const float2*)g,
-                                            charge);
+    launch_pdl(k_charges<T, float2>, gm, 256, 0, st, pl->M, pl->perm, coef, (int)!inverse,
+               (const float2*)g, charge);
   else
-    k_charges<T, double2><<<gm, 256, 0, st>>>(pl->M, pl->perm, coef, !inverse, (const double2*)g,
-                                             charge);
+    launch_pdl(k_charges<T, double2>, gm, 256, 0, st, pl->M, pl->perm, coef, (int)!inverse,
+               (const double2*)g, charge);
   prof_end(pl, 1);
   // self terms on the side branch: only the targets kernel needs them
   const TreeDims d = dims_of(pl);
@@ -1484,15 +1518,13 @@ int fmm_to_grid(nufft_plan_s* pl, const void* g, int inverse) {
   prof_begin(pl, NUFFT_STAGE_OTHER);
   cudaStream_t s1 = side_begin(pl, 1);
   if (c64)
-    k_self_terms<T, float2><<<gm, 256, 0, s1>>>((int)pl->M, inverse, (int)pl->N, pl->k0,
-                                               pl->delta, pl->perm, PlanT<T>::E(pl), charge,
-                                               (const float2*)g, pl->Ct, PlanT<T>::Ct(pl),
-                                               PlanT<T>::delta(pl), KConst<T>::n_2pi_h(d), stt);
+    launch_pdl(k_self_terms<T, float2>, gm, 256, 0, s1, (int)pl->M, inverse, (int)pl->N, pl->k0,
+               pl->delta, pl->perm, PlanT<T>::E(pl), charge, (const float2*)g, pl->Ct,
+               PlanT<T>::Ct(pl), PlanT<T>::delta(pl), KConst<T>::n_2pi_h(d), stt);
   else
-    k_self_terms<T, double2><<<gm, 256, 0, s1>>>((int)pl->M, inverse, (int)pl->N, pl->k0,
-                                                pl->delta, pl->perm, PlanT<T>::E(pl), charge,
-                                                (const double2*)g, pl->Ct, PlanT<T>::Ct(pl),
-                                                PlanT<T>::delta(pl), KConst<T>::n_2pi_h(d), stt);
+    launch_pdl(k_self_terms<T, double2>, gm, 256, 0, s1, (int)pl->M, inverse, (int)pl->N, pl->k0,
+               pl->delta, pl->perm, PlanT<T>::E(pl), charge, (const double2*)g, pl->Ct,
+               PlanT<T>::Ct(pl), PlanT<T>::delta(pl), KConst<T>::n_2pi_h(d), stt);
   side_end(pl, 1, s1);
   prof_end(pl, 1);
   int rc = fmm_upward_downward<T>(pl, cot_ops(pl), false, charge, pl->lvl2,
@@ -1501,21 +1533,19 @@ int fmm_to_grid(nufft_plan_s* pl, const void* g, int inverse) {
   SrcPos<T>* pos = (SrcPos<T>*)pl->srcpos;
   side_join(pl, 1);
   prof_begin(pl, NUFFT_STAGE_TARGETS);
+  const cplx<T>* lexp_c = (const cplx<T>*)pl->lexp;
   if (pl->batch % 4 == 0)
-    k_targets_grid<T, 4><<<dim3(nblk(pl->N, kTgtThreads), nsig / 4), kTgtThreads,
-                           NearCap<T, 4>::grid_bytes, st>>>(
-        d, inverse, pl->leaf_start, pos, charge, stt, (const cplx<T>*)pl->lexp,
-        PlanT<T>::lvl2(pl), PlanT<T>::Ct(pl), (cplx<T>*)pl->grid);
+    launch_pdl(k_targets_grid<T, 4>, dim3(nblk(pl->N, kTgtThreads), nsig / 4), kTgtThreads,
+               NearCap<T, 4>::grid_bytes, st, d, inverse, pl->leaf_start, pos, charge, stt,
+               lexp_c, PlanT<T>::lvl2(pl), PlanT<T>::Ct(pl), (cplx<T>*)pl->grid);
   else if (nsig == 1 && pl->s >= 2)
-    k_targets_grid2<T><<<nblk(pl->N, 2 * kTgtThreads), kTgtThreads, NearCap<T, 1>::grid_bytes,
-                         st>>>(d, inverse, pl->leaf_start, pos, charge, stt,
-                               (const cplx<T>*)pl->lexp, PlanT<T>::lvl2(pl), PlanT<T>::Ct(pl),
-                               (cplx<T>*)pl->grid);
+    launch_pdl(k_targets_grid2<T>, nblk(pl->N, 2 * kTgtThreads), kTgtThreads,
+               NearCap<T, 1>::grid_bytes, st, d, inverse, pl->leaf_start, pos, charge, stt,
+               lexp_c, PlanT<T>::lvl2(pl), PlanT<T>::Ct(pl), (cplx<T>*)pl->grid);
   else
-    k_targets_grid<T, 1><<<dim3(nblk(pl->N, kTgtThreads), nsig), kTgtThreads,
-                           NearCap<T, 1>::grid_bytes, st>>>(
-        d, inverse, pl->leaf_start, pos, charge, stt, (const cplx<T>*)pl->lexp,
-        PlanT<T>::lvl2(pl), PlanT<T>::Ct(pl), (cplx<T>*)pl->grid);
+    launch_pdl(k_targets_grid<T, 1>, dim3(nblk(pl->N, kTgtThreads), nsig), kTgtThreads,
+               NearCap<T, 1>::grid_bytes, st, d, inverse, pl->leaf_start, pos, charge, stt,
+               lexp_c, PlanT<T>::lvl2(pl), PlanT<T>::Ct(pl), (cplx<T>*)pl->grid);
   prof_end(pl, 1);
   return cudaGetLastError() == cudaSuccess ? NUFFT_OK : NUFFT_ECUDA;
 }

@@ -113,6 +113,8 @@ __device__ inline void tc_issue_raw(const TreeDims& d, int l, const TcTile& tl,
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_m2l_tc(TreeDims d, int l, int nsig, const float* __restrict__ bops,
              const float2* __restrict__ mexp, float2* __restrict__ lexp, int* __restrict__ status) {
+  pdl_wait();
+  pdl_trigger();
   extern __shared__ __align__(1024) unsigned char smraw[];
   const int p = d.p, pm = d.pm;
   const int kpad = tc_kpad(p), npad = tc_npad(p);
@@ -370,6 +372,6 @@ int m2l_tc_level(const TreeDims& d, int l, int nsig, const float* bops, const fl
   const int nsm = g_num_sms > 0 ? g_num_sms : 1;
   const int grid = ntiles < nsm ? ntiles : nsm;
   const size_t smem = tc_smem(d.p, d.pm).total;
-  k_m2l_tc<<<grid, kTcThreads, smem, st>>>(d, l, nsig, bops, mexp, lexp, status);
+  launch_pdl(k_m2l_tc, grid, kTcThreads, smem, st, d, l, nsig, bops, mexp, lexp, status);
   return cudaGetLastError() == cudaSuccess ? NUFFT_OK : NUFFT_ECUDA;
 }

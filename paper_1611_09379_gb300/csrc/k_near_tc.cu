@@ -50,6 +50,8 @@ __global__ void __launch_bounds__(kNtThreads, 1)
     k_near_tc(TreeDims d, int M, const int32_t* __restrict__ k0s, const double* __restrict__ dels,
               const float* __restrict__ dels_f, const float2* __restrict__ fgrid,
               float2* __restrict__ hnear, int* __restrict__ status) {
+  pdl_wait();
+  pdl_trigger();
   extern __shared__ __align__(1024) unsigned char smraw[];
   float* Ahi = reinterpret_cast<float*>(smraw + NtSmem::a_hi);
   float* Alo = reinterpret_cast<float*>(smraw + NtSmem::a_lo);
@@ -252,7 +254,7 @@ int near_tc_forward(const TreeDims& d, int M, int batch, const int32_t* k0s, con
                     cudaStream_t st) {
   if (batch % kNtSig != 0 || M < 1) return NUFFT_EINVAL;
   dim3 grid((unsigned)((M + kNtRows - 1) / kNtRows), (unsigned)(batch / kNtSig));
-  k_near_tc<<<grid, kNtThreads, NtSmem::total, st>>>(d, M, k0s, dels, dels_f, fgrid, hnear,
-                                                     status);
+  launch_pdl(k_near_tc, grid, kNtThreads, NtSmem::total, st, d, M, k0s, dels, dels_f, fgrid, hnear,
+             status);
   return cudaGetLastError() == cudaSuccess ? NUFFT_OK : NUFFT_ECUDA;
 }

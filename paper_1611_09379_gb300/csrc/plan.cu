@@ -9,6 +9,13 @@
 
 #include "common.cuh"
 
+namespace nufft {
+bool pdl_enabled() {
+  static const bool on = std::getenv("NUFFT_NO_PDL") == nullptr;
+  return on;
+}
+}  // namespace nufft
+
 using namespace nufft;
 
 // kernels and drivers from the other translation units
