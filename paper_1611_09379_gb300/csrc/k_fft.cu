@@ -130,8 +130,10 @@ __device__ inline int pad_add(int e, int pe, int K) {
 // products (w^2 = w w, w^3 = w^2 w, w^4 = w^2 w^2, ...: at most three
 // roundings deep).  IN_REGS: the inputs are already in v (the first stage,
 // straight from the loads); src == dst (one buffer) needs a barrier between
-// the reads and the writes.
-template <class T, int LOGR, int LOGRAD, int LOGNS, int JC, bool IN_REGS>
+// the reads and the writes.  LAST (Ns 2^LOGRAD = R): the outputs stay in
+// registers, v[m] = element q + m TPC (butterfly i, output k: m = i + k E /
+// 2^LOGRAD), which is the thread's share of the pass output.
+template <class T, int LOGR, int LOGRAD, int LOGNS, int JC, bool IN_REGS, bool LAST = false>
 __device__ inline void fft_stage(cplx<T>* v, const cplx<T>* src, cplx<T>* dst,
                                  const cplx<T>* __restrict__ wR, int J, int c, int q, T sg) {
   using S = FftShape<T, LOGR>;
@@ -144,8 +146,9 @@ __device__ inline void fft_stage(cplx<T>* v, const cplx<T>* src, cplx<T>* dst,
 #pragma unroll
       for (int m = 0; m < RAD; ++m)
         v[i * RAD + m] = src[pad_add<JC>(e0, p0, (i * TPC + m * (R / RAD)) * J)];
-    if (src == dst) __syncthreads();  // every input read before any output is written
+    if (!LAST && src == dst) __syncthreads();  // every input read before any output is written
   }
+  cplx<T> o[E];  // LAST: outputs by row
 #pragma unroll
   for (int i = 0; i < NB; ++i) {
     const int b = q + i * TPC, j = b & (NS - 1);
@@ -167,6 +170,11 @@ __device__ inline void fft_stage(cplx<T>* v, const cplx<T>* src, cplx<T>* dst,
       }
     }
     dft_small<T, LOGRAD>(a, sg);
+    if constexpr (LAST) {
+#pragma unroll
+      for (int k = 0; k < RAD; ++k) o[i + k * NB] = a[brev_c<LOGRAD>(k)];
+      continue;
+    }
     const int e0 = (((b >> LOGNS) << (LOGNS + LOGRAD)) + j) * J + c, p0 = fft_pad(e0);
     // the butterfly's outputs span Ns RAD J slots from a multiple of that
     // span: inside one 32-slot row when the span is at most 32
@@ -177,24 +185,28 @@ __device__ inline void fft_stage(cplx<T>* v, const cplx<T>* src, cplx<T>* dst,
       dst[one_row ? p0 + K : pad_add<JC>(e0, p0, K)] = a[brev_c<LOGRAD>(k)];
     }
   }
-  __syncthreads();
+  if constexpr (LAST) {
+#pragma unroll
+    for (int m = 0; m < E; ++m) v[m] = o[m];
+  } else {
+    __syncthreads();
+  }
 }
 
 // Stages ST = 1, 2, ... after the first: radix 8 while at least 3 bits are
 // left, then radix 2 or 4; buffers alternate when there are two.
 template <class T, int LOGR, int JC, int ST>
 __device__ inline void fft_stages(cplx<T>* v, cplx<T>* X0, cplx<T>* X1,
-                                  const cplx<T>* __restrict__ wR, int J, int c, int q, T sg,
-                                  cplx<T>** fin) {
+                                  const cplx<T>* __restrict__ wR, int J, int c, int q, T sg) {
   using S = FftShape<T, LOGR>;
   constexpr int LOGNS = S::LOGE + 3 * (ST - 1);
   if constexpr (LOGNS < LOGR) {
     constexpr int LEFT = LOGR - LOGNS, LOGRAD = LEFT < 3 ? LEFT : 3;
     cplx<T>* src = (S::NBUF == 2 && (ST & 1) == 0) ? X1 : X0;
     cplx<T>* dst = (S::NBUF == 2 && (ST & 1) == 1) ? X1 : X0;
-    fft_stage<T, LOGR, LOGRAD, LOGNS, JC, false>(v, src, dst, wR, J, c, q, sg);
-    *fin = dst;
-    fft_stages<T, LOGR, JC, ST + 1>(v, X0, X1, wR, J, c, q, sg, fin);
+    fft_stage<T, LOGR, LOGRAD, LOGNS, JC, false, LOGNS + LOGRAD == LOGR>(v, src, dst, wR, J, c, q,
+                                                                         sg);
+    fft_stages<T, LOGR, JC, ST + 1>(v, X0, X1, wR, J, c, q, sg);
   }
 }
 
@@ -227,20 +239,29 @@ __device__ inline cplx<T> ld_cv(const double2* p) {
 
 // loads of a pass: element r = q + m TPC of column jg at in[jg + r NR],
 // times w^{(r jm N / (Ns R)) mod N}, the exponent advancing by
-// de = TPC jm N / (Ns R) per m (32-bit offsets: N < 2^31)
+// de = TPC jm N / (Ns R) per m (32-bit offsets: N < 2^31).  All E loads are
+// issued before the first twiddle is applied, so they are in flight together.
 template <class T, int E, class V>
 __device__ inline void fft_load(cplx<T>* v, const V* __restrict__ in, uint32_t idx,
                                 uint32_t stride, uint32_t ex, uint32_t de, uint32_t nmask,
                                 const cplx<T>* __restrict__ tw, int lo_bits, uint32_t lo_mask,
                                 T sg) {
+  V raw[E];
+#pragma unroll
+  for (int m = 0; m < E; ++m) raw[m] = in[idx + m * stride];
+  if (de == 0 && ex == 0) {  // first pass (Ns = 1) and column 0: no twiddles
+#pragma unroll
+    for (int m = 0; m < E; ++m) v[m] = ld_cv<T>(&raw[m]);
+    return;
+  }
+  cplx<T> w[E];
 #pragma unroll
   for (int m = 0; m < E; ++m) {
-    cplx<T> x = ld_cv<T>(in + idx);
-    if (ex != 0) x = cmul(x, twiddle32<T>(tw, ex, lo_bits, lo_mask, sg));
-    v[m] = x;
-    idx += stride;
+    w[m] = twiddle32<T>(tw, ex, lo_bits, lo_mask, sg);  // w^0 = 1 exactly from the tables
     ex = (ex + de) & nmask;
   }
+#pragma unroll
+  for (int m = 0; m < E; ++m) v[m] = cmul(ld_cv<T>(&raw[m]), w[m]);
 }
 
 template <class T>
@@ -302,35 +323,21 @@ __global__ void __launch_bounds__(kFftMaxThreads, sizeof(T) == 4 ? 3 : 2) k_fft_
                      tw, lo_bits, lo_mask, sg);
   }
   __syncthreads();  // wR ready
-  fft_stage<T, LOGR, LOGE, 0, JC, true>(v, X0, X0, wR, J, c, q, sg);
-  cplx<T>* Xf = X0;
-  fft_stages<T, LOGR, JC, 1>(v, X0, X1, wR, J, c, q, sg, &Xf);
-  // Xf[r'][c] = A_r' of column c -> out
+  fft_stage<T, LOGR, LOGE, 0, JC, true, LOGE == LOGR>(v, X0, X0, wR, J, c, q, sg);
+  fft_stages<T, LOGR, JC, 1>(v, X0, X1, wR, J, c, q, sg);
+  // v[m] = A_r' of column c, r' = q + m TPC -> out[(j / Ns) Ns R + (j mod Ns) + r' Ns]
+  // (J contiguous per r' for Ns >= J; runs of TPC per column for Ns = 1)
   const size_t sig = (size_t)blockIdx.y * N;
-  if (Ns >= (uint32_t)J) {
-    // thread (c, q) writes r' = q + m TPC: J contiguous per r'
-    const uint32_t d0 = ((jg >> logNs) << (logNs + LOGR)) + jm + ((uint32_t)q << logNs);
-    const uint32_t dstep = (uint32_t)TPC << logNs;
-    const int e0 = q * J + c, p0 = fft_pad(e0);
-    if (out_f64) {
-      double2* o = reinterpret_cast<double2*>(out) + sig + d0;
+  const uint32_t d0 = ((jg >> logNs) << (logNs + LOGR)) + jm + ((uint32_t)q << logNs);
+  const uint32_t dstep = (uint32_t)TPC << logNs;
+  if (out_f64) {
+    double2* o = reinterpret_cast<double2*>(out) + sig + d0;
 #pragma unroll
-      for (int m = 0; m < E; ++m) st_cv<T>(o + m * dstep, Xf[pad_add<JC>(e0, p0, m * TPC * J)]);
-    } else {
-      float2* o = reinterpret_cast<float2*>(out) + sig + d0;
-#pragma unroll
-      for (int m = 0; m < E; ++m) st_cv<T>(o + m * dstep, Xf[pad_add<JC>(e0, p0, m * TPC * J)]);
-    }
+    for (int m = 0; m < E; ++m) st_cv<T>(o + m * dstep, v[m]);
   } else {
-    // small Ns: R contiguous per column
-    for (int e = tid; e < R * J; e += nth) {
-      const int jj = e >> LOGR, r = e & (R - 1);
-      const uint32_t jgg = j0 + jj, jmg = jgg & (Ns - 1);
-      const size_t dst = sig + ((jgg >> logNs) << (logNs + LOGR)) + jmg + ((uint32_t)r << logNs);
-      const cplx<T> val = Xf[fft_pad(r * J + jj)];
-      if (out_f64) st_cv<T>(reinterpret_cast<double2*>(out) + dst, val);
-      else st_cv<T>(reinterpret_cast<float2*>(out) + dst, val);
-    }
+    float2* o = reinterpret_cast<float2*>(out) + sig + d0;
+#pragma unroll
+    for (int m = 0; m < E; ++m) st_cv<T>(o + m * dstep, v[m]);
   }
 }
 

@@ -1081,7 +1081,7 @@ __global__ void __launch_bounds__(kTgtThreads) k_targets_grid(
 // own run and the pair of the other's.  Same arithmetic per pair as
 // k_targets_grid.
 template <class T>
-__global__ void __launch_bounds__(kTgtThreads) k_targets_grid2(
+__global__ void __launch_bounds__(kTgtThreads, sizeof(T) == 4 ? 5 : 4) k_targets_grid2(
     TreeDims d, int inverse, const int32_t* __restrict__ start,
     const SrcPos<T>* __restrict__ pos, const cplx<T>* __restrict__ charge,
     const cplx<T>* __restrict__ st, const cplx<T>* __restrict__ lexp,
