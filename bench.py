@@ -46,9 +46,9 @@ METRIC = "NUFFT points/s (forward + square inverse, N=M=2^20, mixed eps=1e-6)"
 # k_targets_fwd + one k_targets_grid2 launch), from the ncu capture summarised
 # in profiles/targets_fft_N2p20_mixed.md; reported only while the kernels'
 # source text still hashes to `sha1` (a changed kernel reports null)
-TARGETS_TRAFFIC = {"bytes_per_step": 79042816, "sha1": "471fea14ce792aee6a9d620457ef310f718b9213"}
+TARGETS_TRAFFIC = {"bytes_per_step": 79061248, "sha1": "80d8f9ff6fd923065d12a91b75522ec79d479ce4"}
 STAGE_KERNELS = {"targets": "k_targets_fwd + k_targets_grid2", "fft": "k_fft_st",
-                 "m2l": "k_down_top + k_down_sub (+ k_m2l_tc)", "p2m": "k_p2m_* + k_charges",
+                 "m2l": "k_m2l_all + k_down_chain (tensor-core levels: k_down_top + k_down_sub + k_m2l_tc)", "p2m": "k_p2m_* + k_charges",
                  "m2m": "k_up_sub + k_up_top", "level2": "k_level2"}
 L2_FLUSH_BYTES = 512 << 20
 
@@ -187,12 +187,13 @@ def stage_roofline(stages_ms: dict, N: int, M: int, info: dict, io_bytes: int, f
 
 
 def targets_source_sha1() -> str:
-    """SHA-1 of the near-field / target-kernel section of k_fmm.cu."""
+    """SHA-1 of the near-field / target-kernel section of k_fmm.cu (the
+    device code from the reciprocal helper to the first host function)."""
     import hashlib
     path = os.path.join(ROOT, "paper_1611_09379_gb300", "csrc", "k_fmm.cu")
     src = open(path).read()
     a = src.index("// 1/t: FP32 reciprocal")
-    e = src.index("}  // namespace nufft\n\nusing namespace nufft;")
+    e = src.index("static inline unsigned nblk")
     return hashlib.sha1(src[a:e].encode()).hexdigest()
 
 

@@ -132,6 +132,9 @@ __device__ __forceinline__ void pdl_trigger() {
 }
 
 bool pdl_enabled();  // false when the environment sets NUFFT_NO_PDL
+// false when the environment sets NUFFT_NO_FUSED_UP: the upward pass then
+// runs as one launch per subtree level band (same arithmetic, same results)
+bool fused_up_enabled();
 
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
@@ -226,6 +229,8 @@ struct nufft_plan_s {
   int fft_tw_lo_bits = 0;
   int *status = nullptr;   // device error word
   int *seg_overflow = nullptr;
+  int *upcnt = nullptr;    // [batch][upcnt_n] group counters of the one-launch upward pass
+  int upcnt_n = 0;         //     (zero between launches); null: upward pass in several launches
   StageProf *prof = nullptr;
   void *lsq_work = nullptr;  // CG work vectors (created on first least-squares solve)
   // exec sequences captured as CUDA graphs, keyed by operation and buffers

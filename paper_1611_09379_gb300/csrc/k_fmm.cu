@@ -51,6 +51,51 @@ __global__ void k_p2m_uniform(TreeDims d, const cplx<T>* __restrict__ q,
 }
 
 
+// The same product with the grid samples of kP2mChunk consecutive grid
+// points (chunk / s leaves) staged in shared memory by coalesced loads, one
+// row of s + 1 per leaf (odd pitch: rows of different leaves fall in
+// different banks), and the table rho_o^m beside them; each thread then
+// forms outputs (leaf, m) from shared memory.  For s <= kP2mChunk.
+constexpr int kP2mChunk = 2048;
+template <class T>
+size_t p2m_grid_smem(int s, int pm) {
+  return ((size_t)(kP2mChunk / s) * (s + 1)) * sizeof(cplx<T>) + (size_t)s * pm * sizeof(T);
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_p2m_grid(TreeDims d, const cplx<T>* __restrict__ q,
+                                                  const T* __restrict__ rp,
+                                                  cplx<T>* __restrict__ mleaf) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int s = d.s, pm = d.pm;
+  const int nlf = kP2mChunk / s;  // leaves per CTA
+  cplx<T>* qs = reinterpret_cast<cplx<T>*>(smraw);              // [nlf][s + 1]
+  T* rps = reinterpret_cast<T*>(qs + (size_t)nlf * (s + 1));      // [s][pm]
+  for (int i = threadIdx.x; i < s * pm; i += blockDim.x) rps[i] = rp[i];
+  // (the table is a plan constant: read before the predecessor ends)
+  pdl_wait();
+  pdl_trigger();
+  q += blockIdx.y * d.N + (int64_t)blockIdx.x * kP2mChunk;
+  mleaf += blockIdx.y * d.mstride + (int64_t)blockIdx.x * nlf * pm;
+  for (int i = threadIdx.x; i < kP2mChunk; i += blockDim.x) {
+    const int lf = i / s;  // s is a power of two
+    qs[lf * (s + 1) + (i - lf * s)] = q[i];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < nlf * pm; e += blockDim.x) {
+    const int lf = e / pm, m = e - lf * pm;
+    const cplx<T>* row = qs + lf * (s + 1);
+    T ar = 0, ai = 0;
+    for (int o = 0; o < s; ++o) {
+      const cplx<T> v = row[o];
+      const T w = rps[o * pm + m];
+      ar = fma(v.x, w, ar);
+      ai = fma(v.y, w, ai);
+    }
+    mleaf[e] = mk<T>(ar, ai);
+  }
+}
+
 // Non-uniform sources: one warp per leaf; a chunk of 32 sources writes
 // q rho^m for up to 32 consecutive m (the moments of this pass, nm rows)
 // into shared memory, lanes then reduce rows.  The source's offset in the
@@ -219,6 +264,81 @@ __global__ void __launch_bounds__(512) k_up_top(TreeDims d, int lb, const T* __r
   }
 }
 
+// Upward pass in one launch.  Stage k reduces level lev[k] to lev[k + 1]
+// (lev[0] = L, lev[n] = 2, at most `dmax` levels per stage).  In stage 0 each
+// CTA owns one box of level lev[1] and reduces its descendants' multipoles
+// in shared memory (every level written to global memory: M2L needs them
+// all).  A CTA that has finished stage k counts itself in the counter of
+// its ancestor at level lev[k + 2]; the last CTA of that group (its
+// atomicAdd returns the group size - 1) resets the counter to zero and goes
+// on to reduce the group's boxes in stage k + 1; the others exit.  No CTA
+// ever waits for another.  The writers' results are made visible by
+// __threadfence() before the count, and the last CTA reads them from L2.
+struct UpStages {
+  int n;      // stages
+  int dmax;   // largest depth of a stage
+  int lev[16];
+};
+
+template <class T>
+__global__ void __launch_bounds__(512) k_up_fused(TreeDims d, UpStages sg, const T* __restrict__ op,
+                                                  cplx<T>* __restrict__ mexp, int* __restrict__ cnt,
+                                                  int cstride) {
+  extern __shared__ unsigned char smraw[];
+  __shared__ int s_last;
+  const int pm = d.pm;
+  T* A = reinterpret_cast<T*>(smraw);
+  cplx<T>* cur0 = reinterpret_cast<cplx<T>*>(A + 2 * pm * pm);  // [pm << dmax]
+  cplx<T>* nxt0 = cur0 + (pm << sg.dmax);                       // [pm << (dmax - 1)]
+  for (int i = threadIdx.x; i < 2 * pm * pm; i += blockDim.x) A[i] = op[i];
+  // (operator tables are plan constants: read before the predecessor ends)
+  pdl_wait();
+  pdl_trigger();
+  mexp += blockIdx.y * d.mstride;
+  cnt += blockIdx.y * (int64_t)cstride;
+  int64_t box = blockIdx.x;  // box of level lev[k + 1] reduced in stage k
+  for (int k = 0; k < sg.n; ++k) {
+    const int lb = sg.lev[k], lt = sg.lev[k + 1];
+    const cplx<T>* src = mexp + (level_off(lb) + (box << (lb - lt))) * pm;
+    const int nsrc = pm << (lb - lt);
+    if (k == 0) {
+      for (int i = threadIdx.x; i < nsrc; i += blockDim.x) cur0[i] = src[i];
+    } else {  // written by other CTAs of this grid: read through L2
+      for (int i = threadIdx.x; i < nsrc; i += blockDim.x) cur0[i] = __ldcg(src + i);
+    }
+    __syncthreads();
+    cplx<T>* cur = cur0;
+    cplx<T>* nxt = nxt0;
+    for (int lev = lb; lev > lt; --lev) {
+      const int np = 1 << (lev - 1 - lt);  // parents of this level under `box`
+      cplx<T>* dst = mexp + (level_off(lev - 1) + (box << (lev - 1 - lt))) * pm;
+      for (int e = threadIdx.x; e < np * pm; e += blockDim.x) {
+        int ip = e / pm, m = e - ip * pm;
+        cplx<T> v = m2m_one<T>(A, pm, m, cur + 2 * ip * pm, cur + (2 * ip + 1) * pm);
+        nxt[e] = v;
+        dst[e] = v;
+      }
+      __syncthreads();
+      cplx<T>* t = cur; cur = nxt; nxt = t;
+    }
+    if (k + 1 == sg.n) break;
+    const int lp = sg.lev[k + 2];
+    if (threadIdx.x == 0) {
+      int* c = cnt + level_off(lp) + (box >> (lt - lp));
+      __threadfence();
+      const int last = atomicAdd(c, 1) == (1 << (lt - lp)) - 1;
+      if (last) {
+        atomicExch(c, 0);
+        __threadfence();
+      }
+      s_last = last;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    box >>= lt - lp;
+  }
+}
+
 // ---------------------------------------------------------------- downward pass (M2L + L2L)
 
 // One output L[l][i][n]: sum over the interaction list (even i: d in
@@ -284,9 +404,9 @@ __device__ inline cplx<T> l2l_one(const T* __restrict__ Tl, int p, int n, int od
 
 // M2L of every box of levels l0..l1 at once (no level waits for another):
 //   lexp[l][i][n] = sum over the interaction list of T[slot][m][n] M_l[i+o][m]
-// (+ M_0 log W_l per interacting box for the log kernel); the L2L chain then
-// adds the parents' locals (k_down_top / k_down_sub with PRE).  One thread
-// per output (box, n), the operator in shared memory.
+// (+ M_0 log W_l per interacting box for the log kernel); the L2L chains of
+// k_down_chain then add the ancestors' parts.  One thread per output
+// (box, n), the operator in shared memory.
 template <class T>
 __global__ void __launch_bounds__(256) k_m2l_all(TreeDims d, int l0, int l1,
                                                  const T* __restrict__ op_m2l,
@@ -317,9 +437,70 @@ __global__ void __launch_bounds__(256) k_m2l_all(TreeDims d, int l0, int l1,
   }
 }
 
-// PRE: the M2L parts are already in lexp (k_m2l_all); only the L2L chain
-// runs here, adding the parents' locals in place.
-template <class T, bool PRE>
+// Downward pass in one launch after k_m2l_all (which left every box's M2L
+// part Lambda_l in lexp).  CTA c owns box c of level lt and its subtree down
+// to level lb.  The local expansion of box c is the L2L chain of its
+// ancestors a_l = c >> (lt - l),
+//   Loc_3 = Lambda_3(a_3),  Loc_l = L2L_{a_l & 1}(Loc_{l-1}) + Lambda_l(a_l),
+// which the CTA's first warp evaluates on its own (lt - 3 steps of p^2 / 2
+// complex-real multiply-adds, repeated by every CTA: no CTA waits for
+// another); the subtree's levels lt + 1 .. lb are then formed level by level
+// in shared memory and only level lb is written back.  Same sums in the same
+// order as a pass that stores every level: the L2L part from zero, then
+// + Lambda.
+template <class T>
+__global__ void __launch_bounds__(512) k_down_chain(TreeDims d, int lt, int lb,
+                                                   const T* __restrict__ op_l2l,
+                                                   cplx<T>* __restrict__ lexp) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int p = d.p;
+  const int depth = lb - lt;
+  const int na = lt - 2;  // ancestors' levels 3..lt
+  T* Tl = reinterpret_cast<T*>(smraw);                      // [2][p][p] as [sigma][k][n]
+  cplx<T>* La = reinterpret_cast<cplx<T>*>(Tl + 2 * p * p);  // [2^depth * p]
+  cplx<T>* Lb = La + (p << depth);                           // [2^depth * p]
+  cplx<T>* An = Lb + (p << depth);                           // [na * p]
+  for (int i = threadIdx.x; i < 2 * p * p; i += blockDim.x) Tl[i] = op_l2l[i];
+  // (operator tables are plan constants: read before the predecessor ends)
+  pdl_wait();
+  pdl_trigger();
+  lexp += blockIdx.y * d.lstride;
+  const int64_t c = blockIdx.x;
+  for (int e = threadIdx.x; e < na * p; e += blockDim.x) {
+    const int li = e / p, n = e - li * p;
+    An[e] = lexp[(level_off(3 + li) - 4 + (c >> (lt - 3 - li))) * p + n];
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    for (int li = 1; li < na; ++li) {
+      const int odd = (int)((c >> (lt - 3 - li)) & 1);
+      const cplx<T>* prev = An + (li - 1) * p;
+      cplx<T>* cur = An + li * p;
+      for (int n = threadIdx.x; n < p; n += 32) cur[n] = cadd(cur[n], l2l_one<T>(Tl, p, n, odd, prev));
+      __syncwarp();
+    }
+    for (int n = threadIdx.x; n < p; n += 32) La[n] = An[(na - 1) * p + n];
+  }
+  cplx<T>* par = La;
+  cplx<T>* cur = Lb;
+  for (int l = lt + 1; l <= lb; ++l) {
+    const int nbx = 1 << (l - lt);  // boxes of this subtree at level l
+    const int64_t c0 = c << (l - lt);  // first box
+    const cplx<T>* lm = lexp + (level_off(l) - 4 + c0) * p;
+    __syncthreads();  // the parent level is complete
+    for (int e = threadIdx.x; e < nbx * p; e += blockDim.x) {
+      int bi = e / p, n = e - bi * p;
+      cur[e] = cadd(lm[e], l2l_one<T>(Tl, p, n, (int)((c0 + bi) & 1), par + (bi >> 1) * p));
+    }
+    cplx<T>* t = par; par = cur; cur = t;
+  }
+  __syncthreads();
+  // par holds level lb
+  cplx<T>* dst = lexp + (level_off(lb) - 4 + (c << depth)) * p;
+  for (int i = threadIdx.x; i < (p << depth); i += blockDim.x) dst[i] = par[i];
+}
+
+template <class T>
 __global__ void __launch_bounds__(512) k_down_top(TreeDims d, int lt, const T* __restrict__ op_m2l,
                                                   const T* __restrict__ op_l2l,
                                                   const cplx<T>* __restrict__ mexp,
@@ -345,31 +526,20 @@ __global__ void __launch_bounds__(512) k_down_top(TreeDims d, int lt, const T* _
   for (int l = 3; l <= lt; ++l) {
     const int nb = 1 << l;
     cplx<T>* lout = lexp + (level_off(l) - 4) * p;
-    if (PRE) {
-      __syncthreads();  // the parent level is complete
-      for (int e = threadIdx.x; e < nb * p; e += blockDim.x) {
-        int i = e / p, n = e - i * p;
-        cplx<T> v = lout[e];
-        if (l > 3) v = cadd(v, l2l_one<T>(Tl, p, n, i & 1, par + (i >> 1) * p));
-        cur[e] = v;
-        lout[e] = v;
-      }
-    } else {
-      const cplx<T>* ml = mexp + level_off(l) * pm;
-      __syncthreads();
-      for (int e = threadIdx.x; e < nb * p; e += blockDim.x) {
-        int i = e / p, m = e - i * p;
-        Ms[e] = ml[(int64_t)i * pm + m];
-      }
-      __syncthreads();
-      const T lw = log_kernel ? (T)level_logw(log_kernel, log2N, l) : (T)0;
-      for (int e = threadIdx.x; e < nb * p; e += blockDim.x) {
-        int i = e / p, n = e - i * p;
-        auto msrc = [&](int off) { return Ms + ((i + off + nb) & (nb - 1)) * p; };
-        cplx<T> v = m2l_one<T>(Tm, Tl, p, n, i & 1, msrc, l > 3 ? par + (i >> 1) * p : nullptr, lw);
-        cur[e] = v;
-        lout[e] = v;
-      }
+    const cplx<T>* ml = mexp + level_off(l) * pm;
+    __syncthreads();
+    for (int e = threadIdx.x; e < nb * p; e += blockDim.x) {
+      int i = e / p, m = e - i * p;
+      Ms[e] = ml[(int64_t)i * pm + m];
+    }
+    __syncthreads();
+    const T lw = log_kernel ? (T)level_logw(log_kernel, log2N, l) : (T)0;
+    for (int e = threadIdx.x; e < nb * p; e += blockDim.x) {
+      int i = e / p, n = e - i * p;
+      auto msrc = [&](int off) { return Ms + ((i + off + nb) & (nb - 1)) * p; };
+      cplx<T> v = m2l_one<T>(Tm, Tl, p, n, i & 1, msrc, l > 3 ? par + (i >> 1) * p : nullptr, lw);
+      cur[e] = v;
+      lout[e] = v;
     }
     cplx<T>* t = par; par = cur; cur = t;
   }
@@ -380,7 +550,7 @@ __global__ void __launch_bounds__(512) k_down_top(TreeDims d, int lt, const T* _
 // formed in shared memory: the multipoles of the boxes and their +-3
 // neighbours are staged per level, the parents' locals stay on chip.  Only
 // level lb is written back.
-template <class T, bool PRE>
+template <class T>
 __global__ void __launch_bounds__(512) k_down_sub(TreeDims d, int lt, int lb,
                                                   const T* __restrict__ op_m2l,
                                                   const T* __restrict__ op_l2l,
@@ -411,28 +581,19 @@ __global__ void __launch_bounds__(512) k_down_sub(TreeDims d, int lt, int lb,
     const int nbx = 1 << (l - lt);          // boxes of this subtree at level l
     const int nb = 1 << l;
     const int c0 = blockIdx.x << (l - lt);  // first box
-    if (PRE) {
-      const cplx<T>* lm = lexp + (level_off(l) - 4 + (int64_t)c0) * p;
-      __syncthreads();  // the parent level is complete
-      for (int e = threadIdx.x; e < nbx * p; e += blockDim.x) {
-        int bi = e / p, n = e - bi * p;
-        cur[e] = cadd(lm[e], l2l_one<T>(Tl, p, n, (c0 + bi) & 1, par + (bi >> 1) * p));
-      }
-    } else {
-      const cplx<T>* ml = mexp + level_off(l) * pm;
-      __syncthreads();  // previous level finished with Ms
-      for (int e = threadIdx.x; e < (nbx + 6) * p; e += blockDim.x) {
-        int bi = e / p, m = e - bi * p;
-        int box = (c0 - 3 + bi + nb) & (nb - 1);
-        Ms[e] = ml[(int64_t)box * pm + m];
-      }
-      __syncthreads();
-      const T lw = log_kernel ? (T)level_logw(log_kernel, log2N, l) : (T)0;
-      for (int e = threadIdx.x; e < nbx * p; e += blockDim.x) {
-        int bi = e / p, n = e - bi * p;
-        auto msrc = [&](int off) { return Ms + (bi + 3 + off) * p; };
-        cur[e] = m2l_one<T>(Tm, Tl, p, n, (c0 + bi) & 1, msrc, par + (bi >> 1) * p, lw);
-      }
+    const cplx<T>* ml = mexp + level_off(l) * pm;
+    __syncthreads();  // previous level finished with Ms
+    for (int e = threadIdx.x; e < (nbx + 6) * p; e += blockDim.x) {
+      int bi = e / p, m = e - bi * p;
+      int box = (c0 - 3 + bi + nb) & (nb - 1);
+      Ms[e] = ml[(int64_t)box * pm + m];
+    }
+    __syncthreads();
+    const T lw = log_kernel ? (T)level_logw(log_kernel, log2N, l) : (T)0;
+    for (int e = threadIdx.x; e < nbx * p; e += blockDim.x) {
+      int bi = e / p, n = e - bi * p;
+      auto msrc = [&](int off) { return Ms + (bi + 3 + off) * p; };
+      cur[e] = m2l_one<T>(Tm, Tl, p, n, (c0 + bi) & 1, msrc, par + (bi >> 1) * p, lw);
     }
     cplx<T>* t = par; par = cur; cur = t;
   }
@@ -1250,10 +1411,43 @@ template <class T>
 static size_t up_sub_smem(int pm, int depth) {
   return (size_t)2 * pm * pm * sizeof(T) + (size_t)3 * ((size_t)pm << depth) / 2 * sizeof(cplx<T>);
 }
+// Stages of k_up_fused for a plan (depth per stage as large as shared
+// memory allows, at most kSubDepth); returns the counters it needs per signal.
+template <class T>
+static int up_fused_stages(int pm, int L, UpStages* sg) {
+  int dep = kSubDepth;
+  while (dep > 1 && up_sub_smem<T>(pm, dep) > kSmemBudget) --dep;
+  sg->n = 0;
+  sg->dmax = 0;
+  sg->lev[0] = L;
+  int lev = L;
+  while (lev > 2 && sg->n < 15) {
+    const int lt = lev - dep > 2 ? lev - dep : 2;
+    if (lev - lt > sg->dmax) sg->dmax = lev - lt;
+    sg->lev[++sg->n] = lt;
+    lev = lt;
+  }
+  if (lev > 2) return -1;
+  // counters of the boxes of level lev[2] and coarser (indexed like multipoles)
+  return sg->n >= 2 ? (int)(int64_t(2) << sg->lev[2]) : 0;
+}
+
+int fmm_up_counters(int prec, int pm, int L) {
+  UpStages sg;
+  return prec == NUFFT_FP64 ? up_fused_stages<double>(pm, L, &sg)
+                            : up_fused_stages<float>(pm, L, &sg);
+}
+
 template <class T>
 static size_t down_sub_smem(int p, int depth) {
   size_t nbx = (size_t)1 << depth;
   return (size_t)6 * p * p * sizeof(T) + (nbx + 6 + 2 * nbx) * p * sizeof(cplx<T>);
+}
+
+template <class T>
+static size_t down_chain_smem(int p, int depth, int lt) {
+  return (size_t)2 * p * p * sizeof(T) +
+         ((size_t)2 * ((size_t)p << depth) + (size_t)(lt - 2) * p) * sizeof(cplx<T>);
 }
 
 int m2l_tc_level(const TreeDims& d, int l, int nsig, const float* bops, const float2* mexp,
@@ -1266,15 +1460,17 @@ int fmm_configure() {
           cudaSuccess ||
       cudaFuncSetAttribute(k_up_top<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big) !=
           cudaSuccess ||
-      cudaFuncSetAttribute(k_down_top<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      cudaFuncSetAttribute(k_up_fused<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(k_p2m_grid<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(k_down_top<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            big) != cudaSuccess ||
-      cudaFuncSetAttribute(k_down_top<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           big) != cudaSuccess ||
-      cudaFuncSetAttribute(k_down_sub<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      cudaFuncSetAttribute(k_down_chain<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            big) != cudaSuccess ||
       cudaFuncSetAttribute(k_m2l_all<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            4 * 64 * 64 * (int)sizeof(T)) != cudaSuccess ||
-      cudaFuncSetAttribute(k_down_sub<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      cudaFuncSetAttribute(k_down_sub<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            big) != cudaSuccess ||
       cudaFuncSetAttribute(k_level2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            4 * 66 * 66 * (int)sizeof(double)) != cudaSuccess ||
@@ -1334,7 +1530,11 @@ int fmm_upward_downward(nufft_plan_s* pl, const FmmOps& ops, bool uniform_source
   cplx<T>* lexp = (cplx<T>*)pl->lexp;
   cplx<T>* mleaf = mexp + level_off(pl->L) * pl->pm;
   prof_begin(pl, NUFFT_STAGE_P2M);
-  if (uniform_sources) {
+  if (uniform_sources && pl->N >= kP2mChunk && pl->s <= kP2mChunk &&
+      p2m_grid_smem<T>(pl->s, pl->pm) <= kSmemBudget) {
+    launch_pdl(k_p2m_grid<T>, dim3((unsigned)(pl->N / kP2mChunk), nsig), 256,
+               p2m_grid_smem<T>(pl->s, pl->pm), st, d, charge, (const T*)pl->op_p2m, mleaf);
+  } else if (uniform_sources) {
     launch_pdl(k_p2m_uniform<T>, dim3(nblk(B * pl->pm, 256), nsig), 256, 0, st, d, charge,
                (const T*)pl->op_p2m, mleaf);
   } else {
@@ -1351,6 +1551,16 @@ int fmm_upward_downward(nufft_plan_s* pl, const FmmOps& ops, bool uniform_source
   const int pm = pl->pm, p = pl->p, L = pl->L;
   int nl = 0;
   int lev = L;
+  UpStages sg;
+  const int ncnt = L > 2 && pl->upcnt && fused_up_enabled() ? up_fused_stages<T>(pm, L, &sg) : -1;
+  if (ncnt >= 0 && ncnt <= pl->upcnt_n) {
+    // one launch: P2M's leaves to level 2 (k_up_fused)
+    launch_pdl(k_up_fused<T>, dim3(1u << sg.lev[1], nsig), 512,
+               up_sub_smem<T>(pm, sg.dmax), st, d, sg, (const T*)pl->op_m2m, mexp, pl->upcnt,
+               pl->upcnt_n);
+    ++nl;
+    lev = 2;
+  }
   while (lev > kTopLevel) {
     int dep = kSubDepth;
     while (dep > 1 && up_sub_smem<T>(pm, dep) > kSmemBudget) --dep;
@@ -1375,8 +1585,10 @@ int fmm_upward_downward(nufft_plan_s* pl, const FmmOps& ops, bool uniform_source
     side_end(pl, 0, s2);
   }
   prof_end(pl, 1);
-  // downward: levels 3..kTopLevel in one CTA, then subtrees; the chunks are
-  // cut from the finest level up so the costly fine levels get the most CTAs
+  // downward: without tensor-core levels, all M2L at once and then the L2L
+  // chains in one launch; with them, levels 3..kTopLevel in one CTA, then subtrees (cut
+  // from the finest level up so the costly fine levels get the most CTAs)
+  // down to the first tensor-core level
   prof_begin(pl, NUFFT_STAGE_M2L);
   nl = 0;
   int log2N = 0;
@@ -1393,39 +1605,39 @@ int fmm_upward_downward(nufft_plan_s* pl, const FmmOps& ops, bool uniform_source
     if constexpr (std::is_same<T, float>::value)
       if (!ops.log_kernel && pl->op_tc && pl->tc_level >= 4 && pl->tc_level <= L)
         lc = pl->tc_level > top + 1 ? pl->tc_level : top + 1;
-    // without tensor-core levels: every level's M2L in one parallel launch,
-    // then the L2L chain through the subtree kernels
-    const bool pre = lc > L;
-    if (pre) {
+    if (lc > L) {
+      // no tensor-core levels: every level's M2L in one parallel launch, then
+      // the L2L chains in one launch (k_down_chain)
       const int64_t nout = (level_off(L + 1) - level_off(3)) * (int64_t)p;
       const unsigned nbk = (unsigned)((nout + 255) / 256);
       launch_pdl(k_m2l_all<T>, dim3(nbk, nsig), 256, (size_t)4 * p * p * sizeof(T), st, d, 3, L,
                  (const T*)ops.m2l, mexp, lexp, ops.log_kernel, log2N);
       ++nl;
-      launch_pdl(k_down_top<T, true>, dim3(1, nsig), 512, smt, st, d, top, (const T*)ops.m2l,
-                 (const T*)ops.l2l, mexp, lexp, ops.log_kernel, log2N);
+      if (L >= 4) {
+        int dep = kSubDepth;
+        while (dep > 1 && down_chain_smem<T>(p, dep, L) > kSmemBudget) --dep;
+        const int lt = L - dep > 3 ? L - dep : 3;  // subtree roots
+        launch_pdl(k_down_chain<T>, dim3(1u << lt, nsig), 512, down_chain_smem<T>(p, L - lt, lt),
+                   st, d, lt, L, (const T*)ops.l2l, lexp);
+        ++nl;
+      }
     } else {
-      launch_pdl(k_down_top<T, false>, dim3(1, nsig), 512, smt, st, d, top, (const T*)ops.m2l,
+      launch_pdl(k_down_top<T>, dim3(1, nsig), 512, smt, st, d, top, (const T*)ops.m2l,
                  (const T*)ops.l2l, mexp, lexp, ops.log_kernel, log2N);
-    }
-    ++nl;
-    int dep = kSubDepth;
-    while (dep > 1 && down_sub_smem<T>(p, dep) > kSmemBudget) --dep;
-    int cuts[32], nc = 0;
-    for (int lb = lc - 1; lb > top; lb -= dep) cuts[nc++] = lb;
-    int lt = top;
-    for (int c = nc - 1; c >= 0; --c) {
-      int lb = cuts[c];
-      if (pre)
-        launch_pdl(k_down_sub<T, true>, dim3(1u << lt, nsig), 512, down_sub_smem<T>(p, lb - lt),
-                   st, d, lt, lb, (const T*)ops.m2l, (const T*)ops.l2l, mexp, lexp,
-                   ops.log_kernel, log2N);
-      else
-        launch_pdl(k_down_sub<T, false>, dim3(1u << lt, nsig), 512, down_sub_smem<T>(p, lb - lt),
-                   st, d, lt, lb, (const T*)ops.m2l, (const T*)ops.l2l, mexp, lexp,
-                   ops.log_kernel, log2N);
       ++nl;
-      lt = lb;
+      int dep = kSubDepth;
+      while (dep > 1 && down_sub_smem<T>(p, dep) > kSmemBudget) --dep;
+      int cuts[32], nc = 0;
+      for (int lb = lc - 1; lb > top; lb -= dep) cuts[nc++] = lb;
+      int lt = top;
+      for (int c = nc - 1; c >= 0; --c) {
+        int lb = cuts[c];
+        launch_pdl(k_down_sub<T>, dim3(1u << lt, nsig), 512, down_sub_smem<T>(p, lb - lt), st, d,
+                   lt, lb, (const T*)ops.m2l, (const T*)ops.l2l, mexp, lexp, ops.log_kernel,
+                   log2N);
+        ++nl;
+        lt = lb;
+      }
     }
     if constexpr (std::is_same<T, float>::value) {
       for (int l = lc; l <= L; ++l) {

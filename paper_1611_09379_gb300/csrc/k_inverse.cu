@@ -376,6 +376,7 @@ int inverse_precompute(nufft_plan_s* pl, void* tmp, size_t tmp_bytes) {
   nufft_plan_s sh = *pl;
   sh.batch = 1;  // the log-sums are one real "signal" (unit charges)
   sh.side_ok = 0;  // plan time: one stream, no side branch of its own
+  sh.upcnt = nullptr;  // (the plan's counters are sized for its own expansions)
   sh.mexp = base + t.mexp;
   sh.lexp = base + t.lexp;
   sh.op_m2m = base + t.m2m;

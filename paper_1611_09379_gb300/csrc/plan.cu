@@ -14,6 +14,10 @@ bool pdl_enabled() {
   static const bool on = std::getenv("NUFFT_NO_PDL") == nullptr;
   return on;
 }
+bool fused_up_enabled() {
+  static const bool on = std::getenv("NUFFT_NO_FUSED_UP") == nullptr;
+  return on;
+}
 }  // namespace nufft
 
 using namespace nufft;
@@ -39,6 +43,7 @@ template <class T> int fmm_forward(nufft_plan_s* pl, void* g);
 template <class T> int fmm_to_grid(nufft_plan_s* pl, const void* g, int inverse);
 int inverse_precompute(nufft_plan_s* pl, void* tmp, size_t tmp_bytes);
 int fmm_pack_positions(nufft_plan_s* pl);
+int fmm_up_counters(int prec, int pm, int L);
 size_t inverse_tmp_bytes(const nufft_plan_s* pl);
 
 namespace {
@@ -213,7 +218,7 @@ void free_plan(nufft_plan_s* pl) {
                   pl->Ff, pl->Ef, pl->lvl2f, pl->Dt, pl->Dtf, pl->Ct, pl->Ctf, pl->selft, pl->srcpos, pl->Lambda, pl->mexp, pl->lexp,
                   pl->charge, pl->grid, pl->grid2, pl->grid3, pl->lvl2, pl->op_m2m, pl->op_m2l,
                   pl->op_l2l, pl->op_p2m, pl->op_reg, pl->fft_tw, pl->fft_tw_f, pl->status,
-                  pl->seg_overflow, pl->lsq_work, pl->op_tc};
+                  pl->seg_overflow, pl->lsq_work, pl->op_tc, pl->upcnt};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& gr : pl->graphs)
@@ -447,6 +452,14 @@ int nufft_plan_create(nufft_plan* out, int64_t N, int64_t M, const double* y, do
   if ((rc = build_operators(pl))) { free_plan(pl); return rc; }
   cudaStream_t st = pl->stream;
   if (cudaMemsetAsync(pl->status, 0, 16, st) != cudaSuccess) { free_plan(pl); return NUFFT_ECUDA; }
+  // group counters of the one-launch upward pass (start at zero, left at zero)
+  const int ncnt = fmm_up_counters(prec, pl->pm, pl->L);
+  if (ncnt >= 0) {
+    const size_t cb = (size_t)nb * (ncnt > 0 ? ncnt : 1) * 4;
+    if ((rc = dalloc(&pl->upcnt, cb))) { free_plan(pl); return rc; }
+    if (cudaMemsetAsync(pl->upcnt, 0, cb, st) != cudaSuccess) { free_plan(pl); return NUFFT_ECUDA; }
+    pl->upcnt_n = ncnt;
+  }
   if ((rc = fft_init_tables(pl->fft_tw, pl->fft_tw_f, N, st))) { free_plan(pl); return rc; }
   size_t tb = setup_tmp_bytes(M, B);
   if (flags & NUFFT_WANT_INVERSE) {

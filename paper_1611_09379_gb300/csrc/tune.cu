@@ -13,7 +13,10 @@
 //   3. q lowered in steps of 1 likewise;
 //   4. mixed precision: the first tensor-core level (tc_level), every level
 //      from max(4, l_max - 9) to l_max and "never";
-//   5. mixed batches of 64 signals: the near field on the tensor cores or not.
+//   5. l_max again, one level at a time away from the best depth while that
+//      gains, at the lowered p (or p + 2) and q and the chosen tensor-core
+//      level's distance from the leaves;
+//   6. mixed batches of 64 signals: the near field on the tensor cores or not.
 // A candidate is accurate when every output's relative L2 error is at most
 // max(eps / 4, min(1.5 x that of the formula's parameters, eps / 2)): tuning
 // keeps a plan within eps / 2, and within eps / 4 or the paper's choice.  Errors: the
@@ -331,7 +334,35 @@ extern "C" int nufft_autotune(int64_t N, int64_t M, const double* y, double eps,
       prm.tc_level = l;
       if ((rc = tu.try_params(prm, &bestt, &took))) return rc;
     }
-    // 5. near field of batched forwards on the tensor cores, or not
+  }
+  // 5. tree depth again at the lowered orders (the formula's p grows with
+  // the depth, so step 1 compared depths at orders that steps 2-3 then
+  // lowered): one level at a time away from the best depth while that
+  // gains, with the chosen tensor-core level kept at the same distance from
+  // the leaves (or none), and p + 2 when p alone is not accurate there
+  {
+    const nufft_params b0 = bestt.params;
+    for (int dir : {+1, -1}) {
+      bool gained = false;
+      for (int L = b0.lmax + dir; L >= 2 && L <= LN; L += dir) {
+        bool any = false;
+        for (int dp = 0; dp <= 2 && !any; dp += 2) {
+          nufft_params prm = bestt.params;
+          prm.lmax = L;
+          prm.p = bestt.params.p + dp;
+          if (prm.tc_level > 0) prm.tc_level += L - bestt.params.lmax;
+          if ((rc = tu.try_params(prm, &bestt, &took, &acc))) return rc;
+          any = took;
+          if (acc) break;  // accurate but slower: a larger p will not be faster
+        }
+        if (!any) break;
+        gained = true;
+      }
+      if (gained) break;
+    }
+  }
+  if (prec == NUFFT_MIXED) {
+    // 6. near field of batched forwards on the tensor cores, or not
     if (batch % 64 == 0 && (ops & NUFFT_OP_FWD)) {
       nufft_params prm = bestt.params;
       prm.tc_near = bestt.params.tc_near > 0 ? -1 : 1;
