@@ -15,6 +15,7 @@
 //   M2L  source box at offset d (in box widths) from the target box:
 //        L_n += sum_m C(m+n,n) (-1)^(m+1) d^-(m+n+1) M_m
 //   L2L  parent -> child: L'_k = 1/2 sum_n C(n,k) 2^-k (sigma/4)^(n-k) L_n
+#include <climits>
 #include <cmath>
 
 #include <type_traits>
@@ -679,6 +680,7 @@ __global__ void k_level2(TreeDims d, int nq, const double* __restrict__ op, doub
 template <class T>
 __device__ inline cplx<T> horner(const cplx<T>* __restrict__ c, int n, T u) {
   cplx<T> acc = c[n - 1];
+#pragma unroll 4
   for (int k = n - 2; k >= 0; --k) {
     cplx<T> v = c[k];
     acc.x = fma(acc.x, u, v.x);
@@ -756,6 +758,28 @@ template <> struct NearAcc<float> {
   __device__ inline float2 get() { fold(); return s; }
 };
 
+// Two FP32 partial sums (the even and the odd term of each pair of terms),
+// added together and folded into the compensated total after every chunk of
+// 32 terms, so each partial holds 16 terms, as NearAcc's single partial does
+// with chunks of 16.
+struct NearAcc2f {
+  float2 f = make_float2(0, 0), g = make_float2(0, 0);
+  float2 s = make_float2(0, 0), c = make_float2(0, 0);
+  __device__ inline void add0(float2 q, float r) {
+    f.x = fmaf(q.x, r, f.x);
+    f.y = fmaf(q.y, r, f.y);
+  }
+  __device__ inline void add1(float2 q, float r) {
+    g.x = fmaf(q.x, r, g.x);
+    g.y = fmaf(q.y, r, g.y);
+  }
+  __device__ inline void fold() {
+    NearAcc<float>::kahan(s.x, c.x, f.x + g.x);
+    NearAcc<float>::kahan(s.y, c.y, f.y + g.y);
+    f = g = make_float2(0, 0);
+  }
+};
+
 // ---------------------------------------------------------------- forward targets
 
 // Packed source position for the adjoint / inverse near field: grid index k0
@@ -805,14 +829,17 @@ __device__ inline void near_window(int lo, int hi, NearAcc<T>* acc, Term term) {
 }
 
 // near_window with one known excluded index `ex`: term(i, u, check) gets
-// std::true_type only in the chunk holding ex (and in the tail), so the other
-// chunks carry no compare / select.
+// std::true_type only in chunks holding the ex of some lane of the warp (a
+// warp vote: lo and hi are the same for every lane, so the warp never runs
+// both variants of a chunk) and in the tail; the other chunks carry no
+// compare / select.
 template <class T, int G, class Term>
 __device__ inline void near_window_ex(int lo, int hi, int ex, NearAcc<T>* acc, Term term) {
+  const unsigned mask = __activemask();
   int i = lo;
   for (; i + 16 <= hi; i += 16) {
     // (several signals per thread: one variant only, the code would not fit)
-    if (G > 1 || (ex - i >= 0 && ex - i < 16)) {
+    if (G > 1 || __any_sync(mask, ex - i >= 0 && ex - i < 16)) {
 #pragma unroll
       for (int u = 0; u < 16; ++u) term(i, u, std::true_type());
     } else if (G == 1) {
@@ -850,6 +877,30 @@ __device__ inline void near_window_ex2(int n, int ex, NearAcc<T>* acc, Term term
     for (int u = 0; u < n - i; u += 2) term(i, u, std::true_type());
 #pragma unroll
     for (int gg = 0; gg < G; ++gg) acc[gg].fold();
+  }
+}
+
+// near_window_ex2 for one signal: chunks of 32 terms (16 calls), the
+// compare variant taken by the whole warp whenever the chunk holds the
+// excluded index of any of its lanes (a warp vote; n is the same for every
+// lane), so a warp never runs the two variants one after the other.
+template <class Term>
+__device__ inline void near_window_ex2w(int n, int ex, NearAcc2f& acc, Term term) {
+  const unsigned mask = __activemask();
+  int i = 0;
+  for (; i + 32 <= n; i += 32) {
+    if (__any_sync(mask, ex - i >= 0 && ex - i < 32)) {
+#pragma unroll
+      for (int u = 0; u < 32; u += 2) term(i, u, std::true_type());
+    } else {
+#pragma unroll
+      for (int u = 0; u < 32; u += 2) term(i, u, std::false_type());
+    }
+    acc.fold();
+  }
+  if (i < n) {
+    for (int u = 0; u < n - i; u += 2) term(i, u, std::true_type());
+    acc.fold();
   }
 }
 
@@ -923,7 +974,23 @@ __global__ void __launch_bounds__(kTgtThreads) k_targets_fwd(
   } else if (std::is_same<T, float>::value && (s & 1) == 0 && staged && b >= bl && b <= bh) {
     // FP32, even s: samples c, c + 1 (c even) in one 16-byte load (nwin and
     // (b - bl) s are even, so every pair is 16-byte aligned)
-    if constexpr (std::is_same<T, float>::value) {
+    if constexpr (std::is_same<T, float>::value && G == 1) {
+      const float2* w = sf + (b - bl) * s;
+      NearAcc2f a2;
+      near_window_ex2w(3 * s, ex, a2, [&](int i, int u, auto chk) {
+        const T ta = (D0 - (T)i) - (T)u, tb = ta - (T)1;
+        T ra = rcp_t(ta + dt), rb = rcp_t(tb + dt);
+        if (decltype(chk)::value) {
+          ra = ta == (T)0 ? (T)0 : ra;
+          rb = tb == (T)0 ? (T)0 : rb;
+        }
+        const float4 q = *reinterpret_cast<const float4*>(w + i + u);
+        a2.add0(make_float2(q.x, q.y), ra);
+        a2.add1(make_float2(q.z, q.w), rb);
+      });
+      acc[0].s = a2.s;
+      acc[0].c = a2.c;
+    } else if constexpr (std::is_same<T, float>::value) {
       const float2* w = sf + (b - bl) * s;
       near_window_ex2<T, G>(3 * s, ex, acc, [&](int i, int u, auto chk) {
         const T ta = (D0 - (T)i) - (T)u, tb = ta - (T)1;
@@ -1301,22 +1368,18 @@ __global__ void __launch_bounds__(kTgtThreads, sizeof(T) == 4 ? 5 : 4) k_targets
     acc0.add_r(v.q, r0);
     acc1.add_r(v.q, r1);
   };
-  auto span = [&](int lo, int hi) {  // [lo, hi): chunks of 16, folded
-    int i = lo;
-    for (; i + 16 <= hi; i += 16) {
-#pragma unroll
-      for (int u = 0; u < 16; ++u) both(i + u);
-      acc0.fold();
-      acc1.fold();
-    }
-    if (i < hi) {
-      const int n = hi - i;
-#pragma unroll
-      for (int u = 0; u < 16; ++u)
-        if (u < n) both(i + u);
-      acc0.fold();
-      acc1.fold();
-    }
+  // the same for a source that may lie outside the lane's window [lo, hi)
+  // (no pairs) or in one of its own runs (e0 = 0: no pair with k; e0 = -1:
+  // no pair with k + 1; those enter through the self terms)
+  auto both_checked = [&](int i, int lo, int hi) {
+    const SrcQ<T> v = sw[i];
+    const T e0 = kf0 - v.rel.x;
+    T r0 = rcp_t(e0 - v.rel.y), r1 = rcp_t((e0 + (T)1) - v.rel.y);
+    const bool in = i >= lo && i < hi;
+    r0 = in && e0 != (T)0 ? r0 : (T)0;
+    r1 = in && e0 != (T)-1 ? r1 : (T)0;
+    acc0.add_r(v.q, r0);
+    acc1.add_r(v.q, r1);
   };
   for (int c0 = 0; c0 < total; c0 += CAP) {
     const int c1 = total - c0 < CAP ? total : c0 + CAP;
@@ -1341,27 +1404,38 @@ __global__ void __launch_bounds__(kTgtThreads, sizeof(T) == 4 ? 5 : 4) k_targets
     }
     __syncthreads();
     const int lo = (wlo > c0 ? wlo : c0) - c0, hi = (whi < c1 ? whi : c1) - c0;
-    if (act && lo < hi) {
-      // runs x = k - kb and x = k + 1 - kb: [ha, h1), [h1, h2)
-      int ha = lo, hb = hi;
+    const bool has = act && lo < hi;
+    int ha = lo, h2 = lo;
+    if (has) {
+      // runs x = k - kb and x = k + 1 - kb: [ha, h1), [h1, h2): self terms
+      int hb = hi;
       while (ha < hb) {
         const int mid = (ha + hb) >> 1;
         if (sw[mid].rel.x < kf0) ha = mid + 1; else hb = mid;
       }
-      int h1 = ha;
-      for (; h1 < hi && sw[h1].rel.x == kf0; ++h1) {
-        self0 = cadd(self0, sst[h1]);
-        acc1.add_r(sw[h1].q, rcp_t((T)1 - sw[h1].rel.y));
-      }
-      int h2 = h1;
-      for (; h2 < hi && sw[h2].rel.x == kf1; ++h2) {
-        self1 = cadd(self1, sst[h2]);
-        acc0.add_r(sw[h2].q, rcp_t((T)-1 - sw[h2].rel.y));
+      h2 = ha;
+      for (; h2 < hi && sw[h2].rel.x == kf0; ++h2) self0 = cadd(self0, sst[h2]);
+      for (; h2 < hi && sw[h2].rel.x == kf1; ++h2) self1 = cadd(self1, sst[h2]);
+    }
+    // pairs: the warp walks the union of its lanes' windows in chunks of 16
+    // sources; a chunk that is not inside every active lane's window, or
+    // that meets a lane's own runs, is taken by the whole warp in the checked
+    // form (a warp vote), so no lane waits on another's different bounds
+    const int ulo = __reduce_min_sync(0xffffffffu, has ? lo : INT_MAX);
+    const int uhi = __reduce_max_sync(0xffffffffu, has ? hi : INT_MIN);
+    for (int i = ulo; i < uhi; i += 16) {
+      const int n = uhi - i < 16 ? uhi - i : 16;
+      const bool bad = act && (i < lo || i + 16 > hi || (i < h2 && i + 16 > ha));
+      if (n == 16 && !__any_sync(0xffffffffu, bad)) {
+#pragma unroll
+        for (int u = 0; u < 16; ++u) both(i + u);
+      } else {
+#pragma unroll
+        for (int u = 0; u < 16; ++u)
+          if (u < n) both_checked(i + u, lo, hi);
       }
       acc0.fold();
       acc1.fold();
-      span(lo, ha);
-      span(h2, hi);
     }
   }
   if (!act) return;
