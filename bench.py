@@ -48,8 +48,10 @@ METRIC = "NUFFT points/s (forward + square inverse, N=M=2^20, mixed eps=1e-6)"
 # source text still hashes to `sha1` (a changed kernel reports null)
 TARGETS_TRAFFIC = {"bytes_per_step": 78863360, "sha1": "f96e75843410fdbbe9b0e07b7a460cce0df26537"}
 STAGE_KERNELS = {"targets": "k_targets_fwd + k_targets_grid2", "fft": "k_fft_st",
-                 "m2l": "k_m2l_all + k_down_chain (tensor-core levels: k_down_top + k_down_sub + k_m2l_tc)", "p2m": "k_p2m_* + k_charges",
-                 "m2m": "k_up_sub + k_up_top", "level2": "k_level2"}
+                 "m2l": "k_down_fused (tensor-core levels: k_down_top + k_down_sub + k_m2l_tc)",
+                 "p2m": "k_p2m_* + k_charges (when not inside k_up_fused)",
+                 "m2m": "k_up_fused (with P2M and the charges when they fit)",
+                 "level2": "k_level2"}
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -163,10 +165,13 @@ def stage_roofline(stages_ms: dict, N: int, M: int, info: dict, io_bytes: int, f
     reciprocal per pair, the special-function unit's 16 per clock per SM) or
     HBM (measured copy bandwidth)."""
     out = {}
+    p2m_fused = stages_ms.get("p2m", 0.0) <= 0
     for st, ms in stages_ms.items():
         if ms <= 0:
             continue
         fl, by, bound = stage_work(st, N, M, info, io_bytes, fwd, bwd)
+        if st == "m2m" and p2m_fused:  # the upward kernel formed the leaf multipoles too
+            fl += stage_work("p2m", N, M, info, io_bytes, fwd, bwd)[0]
         if bound == "hbm":
             ach = by / (ms / 1e3) / 1e9
             out[st] = {"ms": ms, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"],

@@ -24,6 +24,13 @@
 
 namespace nufft {
 
+// caller samples (complex64 or complex128) in the arithmetic type
+template <class T> __device__ inline cplx<T> load_in(const double2* p) { return c128_to<T>(*p); }
+template <class T> __device__ inline cplx<T> load_in(const float2* p) {
+  const float2 v = *p;
+  return mk<T>((T)v.x, (T)v.y);
+}
+
 // ---------------------------------------------------------------- P2M
 
 // Uniform sources (the grid): every leaf holds s points at the same relative
@@ -111,8 +118,55 @@ size_t p2m_smem(int pm) {
   return (size_t)P2mWarps<T>::value * rows * kP2mPitch * sizeof(cplx<T>);
 }
 
-// rho = (o + delta) / s - 1/2 in T: 1/s is a power of two, so the only
-// roundings are of o + delta and of the final subtraction (no division).
+// P2M of leaf b by one warp (tile: rows x kP2mPitch of shared memory): a
+// chunk of 32 sources writes q rho^m for up to 32 consecutive m into the
+// tile, lanes then reduce rows.  rho = (o + delta) / s - 1/2 in T: 1/s is a
+// power of two, so the only roundings are of o + delta and of the final
+// subtraction (no division).  qget(i, first) returns the charge of sorted
+// source i (first: in the first pass over the moments); out(m, v) stores
+// moment m.
+template <class T, class QGet, class Out>
+__device__ inline void p2m_leaf_warp(const TreeDims& d, int64_t b, int lane, cplx<T>* tile,
+                                     const int32_t* __restrict__ start,
+                                     const int32_t* __restrict__ k0,
+                                     const T* __restrict__ delta_t, QGet qget, Out out) {
+  const int32_t a = start[b], e = start[b + 1];
+  const int N = (int)d.N;
+  const int bs = (int)b * d.s;
+  const T inv_s = (T)1 / (T)d.s;
+  for (int mc = 0; mc < d.pm; mc += 32) {
+    const int nm = d.pm - mc < 32 ? d.pm - mc : 32;
+    T accr = 0, acci = 0;
+    for (int c0 = a; c0 < e; c0 += 32) {
+      const int i = c0 + lane;
+      cplx<T> q = mk<T>(0, 0);
+      T rho = 0;
+      if (i < e) {
+        const int o = (k0[i] - bs) & (N - 1);
+        rho = fma((T)o + delta_t[i], inv_s, (T)-0.5);
+        q = qget(i, mc == 0);
+      }
+      T pw = 1;
+      for (int m = 0; m < mc; ++m) pw *= rho;
+      for (int m = 0; m < nm; ++m) {
+        tile[m * kP2mPitch + lane] = mk<T>(q.x * pw, q.y * pw);
+        pw *= rho;
+      }
+      __syncwarp();
+      const int nk = e - c0 < 32 ? e - c0 : 32;
+      if (lane < nm) {
+        for (int k = 0; k < nk; ++k) {
+          const cplx<T> v = tile[lane * kP2mPitch + k];
+          accr += v.x;
+          acci += v.y;
+        }
+      }
+      __syncwarp();
+    }
+    if (lane < nm) out(mc + lane, mk<T>(accr, acci));
+  }
+}
+
 template <class T>
 __global__ void __launch_bounds__(128) k_p2m_nonuniform(TreeDims d,
                                                         const int32_t* __restrict__ start,
@@ -132,41 +186,9 @@ __global__ void __launch_bounds__(128) k_p2m_nonuniform(TreeDims d,
   if (b >= B) return;
   charge += blockIdx.y * d.M_;
   mleaf += blockIdx.y * d.mstride;
-  const int32_t a = start[b], e = start[b + 1];
-  const int N = (int)d.N;
-  const int bs = (int)b * d.s;
-  const T inv_s = (T)1 / (T)d.s;
-  for (int mc = 0; mc < d.pm; mc += 32) {
-    const int nm = d.pm - mc < 32 ? d.pm - mc : 32;
-    T accr = 0, acci = 0;
-    for (int c0 = a; c0 < e; c0 += 32) {
-      const int i = c0 + lane;
-      cplx<T> q = mk<T>(0, 0);
-      T rho = 0;
-      if (i < e) {
-        const int o = (k0[i] - bs) & (N - 1);
-        rho = fma((T)o + delta_t[i], inv_s, (T)-0.5);
-        q = charge[i];
-      }
-      T pw = 1;
-      for (int m = 0; m < mc; ++m) pw *= rho;
-      for (int m = 0; m < nm; ++m) {
-        tile[m * kP2mPitch + lane] = mk<T>(q.x * pw, q.y * pw);
-        pw *= rho;
-      }
-      __syncwarp();
-      const int nk = e - c0 < 32 ? e - c0 : 32;
-      if (lane < nm) {
-        for (int k = 0; k < nk; ++k) {
-          const cplx<T> v = tile[lane * kP2mPitch + k];
-          accr += v.x;
-          acci += v.y;
-        }
-      }
-      __syncwarp();
-    }
-    if (lane < nm) mleaf[b * d.pm + mc + lane] = mk<T>(accr, acci);
-  }
+  p2m_leaf_warp<T>(
+      d, b, lane, tile, start, k0, delta_t, [&](int i, bool) { return charge[i]; },
+      [&](int m, cplx<T> v) { mleaf[b * d.pm + m] = v; });
 }
 
 // mleaf[b][m] -= shift[m]: charges of a fixed pattern repeated in every leaf
@@ -267,31 +289,61 @@ __global__ void __launch_bounds__(512) k_up_top(TreeDims d, int lb, const T* __r
 
 // Upward pass in one launch.  Stage k reduces level lev[k] to lev[k + 1]
 // (lev[0] = L, lev[n] = 2, at most `dmax` levels per stage).  In stage 0 each
-// CTA owns one box of level lev[1] and reduces its descendants' multipoles
-// in shared memory (every level written to global memory: M2L needs them
-// all).  A CTA that has finished stage k counts itself in the counter of
-// its ancestor at level lev[k + 2]; the last CTA of that group (its
-// atomicAdd returns the group size - 1) resets the counter to zero and goes
-// on to reduce the group's boxes in stage k + 1; the others exit.  No CTA
-// ever waits for another.  The writers' results are made visible by
-// __threadfence() before the count, and the last CTA reads them from L2.
+// CTA owns one box of level lev[1]: it forms or loads the multipoles of its
+// leaves (see UpSrc) and reduces them level by level in shared memory
+// (every level written to global memory: M2L needs them all).  A CTA that
+// has finished stage k counts itself in the counter of its ancestor at
+// level lev[k + 2]; the last CTA of that group (its atomicAdd returns the
+// group size - 1) resets the counter to zero and goes on to reduce the
+// group's boxes in stage k + 1; the others exit.  No CTA ever waits for
+// another.  The writers' results are made visible by __threadfence() before
+// the count, and the last CTA reads them from L2.
 struct UpStages {
   int n;      // stages
   int dmax;   // largest depth of a stage
   int lev[16];
 };
 
-template <class T>
-__global__ void __launch_bounds__(512) k_up_fused(TreeDims d, UpStages sg, const T* __restrict__ op,
-                                                  cplx<T>* __restrict__ mexp, int* __restrict__ cnt,
-                                                  int cstride) {
-  extern __shared__ unsigned char smraw[];
+// Leaf multipoles of k_up_fused.  SRC 0: already in mexp (a P2M kernel ran
+// before); SRC 1: P2M of the grid samples q (uniform sources), the CTA's
+// samples staged in shared memory (one row of s + 1 per leaf), with the
+// table rp = rho_o^m; SRC 2: P2M of the sorted non-uniform sources, one warp
+// per leaf (p2m_leaf_warp), their charges read from q or, with gin set,
+// formed here as coef_i g_perm(i) (conj(coef_i) when conj) and stored to
+// `charge` for the near field.  Per signal: q, gin and charge at stride N
+// (SRC 1) or M (SRC 2).
+template <class T, class VI> struct UpSrc {
+  const cplx<T>* q = nullptr;
+  const T* rp = nullptr;
+  const int32_t* start = nullptr;
+  const int32_t* k0 = nullptr;
+  const T* delta_t = nullptr;
+  const int32_t* perm = nullptr;
+  const cplx<T>* coef = nullptr;
+  const VI* gin = nullptr;
+  cplx<T>* charge = nullptr;
+  int conj = 0;
+};
+constexpr int kUpThreads = 512;
+
+template <class T, int SRC, class VI>
+__global__ void __launch_bounds__(kUpThreads) k_up_fused(TreeDims d, UpStages sg,
+                                                         const T* __restrict__ op,
+                                                         cplx<T>* __restrict__ mexp,
+                                                         int* __restrict__ cnt, int cstride,
+                                                         UpSrc<T, VI> src) {
+  extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ int s_last;
   const int pm = d.pm;
   T* A = reinterpret_cast<T*>(smraw);
   cplx<T>* cur0 = reinterpret_cast<cplx<T>*>(A + 2 * pm * pm);  // [pm << dmax]
   cplx<T>* nxt0 = cur0 + (pm << sg.dmax);                       // [pm << (dmax - 1)]
+  cplx<T>* xtra = nxt0 + (pm << (sg.dmax - 1));                 // SRC 1 / 2 work area
   for (int i = threadIdx.x; i < 2 * pm * pm; i += blockDim.x) A[i] = op[i];
+  const int nl0 = 1 << (sg.lev[0] - sg.lev[1]);  // leaves per CTA in stage 0
+  T* rps = reinterpret_cast<T*>(xtra + (size_t)nl0 * (d.s + 1));  // SRC 1: [s][pm]
+  if constexpr (SRC == 1)
+    for (int i = threadIdx.x; i < d.s * pm; i += blockDim.x) rps[i] = src.rp[i];
   // (operator tables are plan constants: read before the predecessor ends)
   pdl_wait();
   pdl_trigger();
@@ -300,12 +352,60 @@ __global__ void __launch_bounds__(512) k_up_fused(TreeDims d, UpStages sg, const
   int64_t box = blockIdx.x;  // box of level lev[k + 1] reduced in stage k
   for (int k = 0; k < sg.n; ++k) {
     const int lb = sg.lev[k], lt = sg.lev[k + 1];
-    const cplx<T>* src = mexp + (level_off(lb) + (box << (lb - lt))) * pm;
+    cplx<T>* lvl = mexp + (level_off(lb) + (box << (lb - lt))) * pm;
     const int nsrc = pm << (lb - lt);
-    if (k == 0) {
-      for (int i = threadIdx.x; i < nsrc; i += blockDim.x) cur0[i] = src[i];
-    } else {  // written by other CTAs of this grid: read through L2
-      for (int i = threadIdx.x; i < nsrc; i += blockDim.x) cur0[i] = __ldcg(src + i);
+    if (k > 0) {  // written by other CTAs of this grid: read through L2
+      for (int i = threadIdx.x; i < nsrc; i += blockDim.x) cur0[i] = __ldcg(lvl + i);
+    } else if constexpr (SRC == 0) {
+      for (int i = threadIdx.x; i < nsrc; i += blockDim.x) cur0[i] = lvl[i];
+    } else if constexpr (SRC == 1) {
+      const int sN = d.s;
+      cplx<T>* qs = xtra;  // [nl0][s + 1]
+      const cplx<T>* q = src.q + blockIdx.y * d.N + (box << (lb - lt)) * sN;
+      for (int i = threadIdx.x; i < nl0 * sN; i += blockDim.x) {
+        const int lf = i / sN;
+        qs[lf * (sN + 1) + (i - lf * sN)] = q[i];
+      }
+      __syncthreads();
+      for (int e = threadIdx.x; e < nsrc; e += blockDim.x) {
+        const int lf = e / pm, m = e - lf * pm;
+        const cplx<T>* row = qs + lf * (sN + 1);
+        T ar = 0, ai = 0;
+        for (int o = 0; o < sN; ++o) {
+          const cplx<T> v = row[o];
+          const T w = rps[o * pm + m];
+          ar = fma(v.x, w, ar);
+          ai = fma(v.y, w, ai);
+        }
+        const cplx<T> v = mk<T>(ar, ai);
+        cur0[e] = v;
+        lvl[e] = v;
+      }
+    } else {
+      const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+      const int rows = pm < 32 ? pm : 32;
+      cplx<T>* tile = xtra + warp * rows * kP2mPitch;
+      const int64_t b0 = box << (lb - lt);
+      const int64_t so = (int64_t)blockIdx.y * d.M_;
+      const cplx<T>* chg = src.q ? src.q + so : nullptr;
+      const VI* gin = src.gin ? src.gin + so : nullptr;
+      cplx<T>* cout = src.charge ? src.charge + so : nullptr;
+      for (int lf = warp; lf < nl0; lf += kUpThreads / 32) {
+        p2m_leaf_warp<T>(
+            d, b0 + lf, lane, tile, src.start, src.k0, src.delta_t,
+            [&](int i, bool first) {
+              if (!gin) return chg[i];
+              cplx<T> c = src.coef[i];
+              if (src.conj) c.y = -c.y;
+              c = cmul(c, load_in<T>(gin + src.perm[i]));
+              if (first) cout[i] = c;
+              return c;
+            },
+            [&](int m, cplx<T> v) {
+              cur0[lf * pm + m] = v;
+              lvl[lf * pm + m] = v;
+            });
+      }
     }
     __syncthreads();
     cplx<T>* cur = cur0;
@@ -338,6 +438,17 @@ __global__ void __launch_bounds__(512) k_up_fused(TreeDims d, UpStages sg, const
     if (!s_last) return;
     box >>= lt - lp;
   }
+}
+
+// shared memory of k_up_fused: the M2M tables and the two level buffers,
+// plus the grid samples and table (SRC 1) or the warps' P2M tiles (SRC 2)
+template <class T>
+size_t up_fused_smem(int pm, const UpStages& sg, int src, int s) {
+  size_t b = (size_t)2 * pm * pm * sizeof(T) + (size_t)3 * ((size_t)pm << sg.dmax) / 2 * sizeof(cplx<T>);
+  const size_t nl0 = (size_t)1 << (sg.lev[0] - sg.lev[1]);
+  if (src == 1) b += nl0 * (s + 1) * sizeof(cplx<T>) + (size_t)s * pm * sizeof(T);
+  if (src == 2) b += (size_t)(kUpThreads / 32) * (pm < 32 ? pm : 32) * kP2mPitch * sizeof(cplx<T>);
+  return b;
 }
 
 // ---------------------------------------------------------------- downward pass (M2L + L2L)
@@ -401,104 +512,6 @@ __device__ inline cplx<T> l2l_one(const T* __restrict__ Tl, int p, int n, int od
     ai = fma(w, x.y, ai);
   }
   return mk<T>(ar, ai);
-}
-
-// M2L of every box of levels l0..l1 at once (no level waits for another):
-//   lexp[l][i][n] = sum over the interaction list of T[slot][m][n] M_l[i+o][m]
-// (+ M_0 log W_l per interacting box for the log kernel); the L2L chains of
-// k_down_chain then add the ancestors' parts.  One thread per output
-// (box, n), the operator in shared memory.
-template <class T>
-__global__ void __launch_bounds__(256) k_m2l_all(TreeDims d, int l0, int l1,
-                                                 const T* __restrict__ op_m2l,
-                                                 const cplx<T>* __restrict__ mexp,
-                                                 cplx<T>* __restrict__ lexp, int log_kernel,
-                                                 int log2N) {
-  pdl_wait();
-  pdl_trigger();
-  extern __shared__ unsigned char smraw[];
-  T* Tm = reinterpret_cast<T*>(smraw);
-  const int p = d.p, pm = d.pm;
-  for (int i = threadIdx.x; i < 4 * p * p; i += blockDim.x) Tm[i] = op_m2l[i];
-  __syncthreads();
-  mexp += blockIdx.y * d.mstride;
-  lexp += blockIdx.y * d.lstride;
-  const int64_t e0 = level_off(l0) * (int64_t)p, e1 = level_off(l1 + 1) * (int64_t)p;
-  for (int64_t e = e0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < e1;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t gb = e / p;  // level_off(l) + i
-    const int n = (int)(e - gb * p);
-    const int l = 63 - __clzll((unsigned long long)(gb + 4));
-    const int64_t nb = int64_t(1) << l;
-    const int64_t i = gb + 4 - nb;
-    const cplx<T>* ml = mexp + level_off(l) * pm;
-    auto msrc = [&](int off) { return ml + ((i + off + nb) & (nb - 1)) * pm; };
-    const T lw = log_kernel ? (T)level_logw(log_kernel, log2N, l) : (T)0;
-    lexp[(gb - 4) * p + n] = m2l_one<T>(Tm, nullptr, p, n, (int)(i & 1), msrc, nullptr, lw);
-  }
-}
-
-// Downward pass in one launch after k_m2l_all (which left every box's M2L
-// part Lambda_l in lexp).  CTA c owns box c of level lt and its subtree down
-// to level lb.  The local expansion of box c is the L2L chain of its
-// ancestors a_l = c >> (lt - l),
-//   Loc_3 = Lambda_3(a_3),  Loc_l = L2L_{a_l & 1}(Loc_{l-1}) + Lambda_l(a_l),
-// which the CTA's first warp evaluates on its own (lt - 3 steps of p^2 / 2
-// complex-real multiply-adds, repeated by every CTA: no CTA waits for
-// another); the subtree's levels lt + 1 .. lb are then formed level by level
-// in shared memory and only level lb is written back.  Same sums in the same
-// order as a pass that stores every level: the L2L part from zero, then
-// + Lambda.
-template <class T>
-__global__ void __launch_bounds__(512) k_down_chain(TreeDims d, int lt, int lb,
-                                                   const T* __restrict__ op_l2l,
-                                                   cplx<T>* __restrict__ lexp) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  const int p = d.p;
-  const int depth = lb - lt;
-  const int na = lt - 2;  // ancestors' levels 3..lt
-  T* Tl = reinterpret_cast<T*>(smraw);                      // [2][p][p] as [sigma][k][n]
-  cplx<T>* La = reinterpret_cast<cplx<T>*>(Tl + 2 * p * p);  // [2^depth * p]
-  cplx<T>* Lb = La + (p << depth);                           // [2^depth * p]
-  cplx<T>* An = Lb + (p << depth);                           // [na * p]
-  for (int i = threadIdx.x; i < 2 * p * p; i += blockDim.x) Tl[i] = op_l2l[i];
-  // (operator tables are plan constants: read before the predecessor ends)
-  pdl_wait();
-  pdl_trigger();
-  lexp += blockIdx.y * d.lstride;
-  const int64_t c = blockIdx.x;
-  for (int e = threadIdx.x; e < na * p; e += blockDim.x) {
-    const int li = e / p, n = e - li * p;
-    An[e] = lexp[(level_off(3 + li) - 4 + (c >> (lt - 3 - li))) * p + n];
-  }
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    for (int li = 1; li < na; ++li) {
-      const int odd = (int)((c >> (lt - 3 - li)) & 1);
-      const cplx<T>* prev = An + (li - 1) * p;
-      cplx<T>* cur = An + li * p;
-      for (int n = threadIdx.x; n < p; n += 32) cur[n] = cadd(cur[n], l2l_one<T>(Tl, p, n, odd, prev));
-      __syncwarp();
-    }
-    for (int n = threadIdx.x; n < p; n += 32) La[n] = An[(na - 1) * p + n];
-  }
-  cplx<T>* par = La;
-  cplx<T>* cur = Lb;
-  for (int l = lt + 1; l <= lb; ++l) {
-    const int nbx = 1 << (l - lt);  // boxes of this subtree at level l
-    const int64_t c0 = c << (l - lt);  // first box
-    const cplx<T>* lm = lexp + (level_off(l) - 4 + c0) * p;
-    __syncthreads();  // the parent level is complete
-    for (int e = threadIdx.x; e < nbx * p; e += blockDim.x) {
-      int bi = e / p, n = e - bi * p;
-      cur[e] = cadd(lm[e], l2l_one<T>(Tl, p, n, (int)((c0 + bi) & 1), par + (bi >> 1) * p));
-    }
-    cplx<T>* t = par; par = cur; cur = t;
-  }
-  __syncthreads();
-  // par holds level lb
-  cplx<T>* dst = lexp + (level_off(lb) - 4 + (c << depth)) * p;
-  for (int i = threadIdx.x; i < (p << depth); i += blockDim.x) dst[i] = par[i];
 }
 
 template <class T>
@@ -602,6 +615,117 @@ __global__ void __launch_bounds__(512) k_down_sub(TreeDims d, int lt, int lb,
   // par holds level lb
   cplx<T>* dst = lexp + (level_off(lb) - 4 + ((int64_t)blockIdx.x << depth)) * p;
   for (int i = threadIdx.x; i < (p << depth); i += blockDim.x) dst[i] = par[i];
+}
+
+// Downward pass in one launch: CTA c owns box c of level lt and its subtree
+// down to level lb.  The M2L parts of every box it needs -- the subtree's
+// boxes of levels lt + 1 .. lb and the ancestors a_l = c >> (lt - l),
+// l = 3 .. lt -- depend on multipoles only, so they are formed at once by
+// all threads from multipoles staged in shared memory.  Then the L2L chain:
+// the ancestors' in one warp,
+//   Loc_3 = Lambda_3(a_3),  Loc_l = Lambda_l(a_l) + L2L_{a_l & 1}(Loc_{l-1}),
+// (every CTA repeats its own ancestors' chain, (lt - 2)(3 p^2 + p^2 / 2)
+// multiply-adds, so no CTA waits for another), then the subtree's levels in
+// place.  Only level lb is written back.
+template <class T>
+__global__ void __launch_bounds__(512) k_down_fused(TreeDims d, int lt, int lb,
+                                                    const T* __restrict__ op_m2l,
+                                                    const T* __restrict__ op_l2l,
+                                                    const cplx<T>* __restrict__ mexp,
+                                                    cplx<T>* __restrict__ lexp, int log_kernel,
+                                                    int log2N) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int p = d.p, pm = d.pm;
+  const int depth = lb - lt;
+  const int na = lt - 2;  // ancestors' levels 3..lt
+  // level l = lt + j (j = 1..depth): its 2^j boxes' parts at Lam + (2^j - 2) p,
+  // its staged multipoles (boxes -3 .. 2^j + 2) at Ms + (2^j - 2 + 6 (j - 1)) p
+  const int nlam = ((2 << depth) - 2) * p;
+  T* Tm = reinterpret_cast<T*>(smraw);
+  T* Tl = Tm + 4 * p * p;
+  cplx<T>* Ms = reinterpret_cast<cplx<T>*>(Tl + 2 * p * p);  // [nlam + 6 depth p]
+  cplx<T>* Lam = Ms + nlam + 6 * depth * p;                  // [nlam]
+  cplx<T>* An = Lam + nlam;                                  // [na][3][p]
+  cplx<T>* AL = An + na * 3 * p;                             // [na][p]
+  for (int i = threadIdx.x; i < 4 * p * p; i += blockDim.x) Tm[i] = op_m2l[i];
+  for (int i = threadIdx.x; i < 2 * p * p; i += blockDim.x) Tl[i] = op_l2l[i];
+  // (operator tables are plan constants: read before the predecessor ends)
+  pdl_wait();
+  pdl_trigger();
+  mexp += blockIdx.y * d.mstride;
+  lexp += blockIdx.y * d.lstride;
+  const int64_t c = blockIdx.x;
+  // slot t of the interaction list: even box {-2, +2, +3}, odd {-3, -2, +2}
+  auto list_off = [](int odd, int t) {
+    return odd ? (t == 0 ? -3 : (t == 1 ? -2 : 2)) : (t == 0 ? -2 : (t == 1 ? 2 : 3));
+  };
+  for (int e = threadIdx.x; e < na * 3 * p; e += blockDim.x) {
+    const int li = e / (3 * p), r = e - li * 3 * p, t = r / p, m = r - t * p;
+    const int l = 3 + li;
+    const int64_t a = c >> (lt - l), nb = int64_t(1) << l;
+    const int64_t box = (a + list_off((int)(a & 1), t) + nb) & (nb - 1);
+    An[e] = mexp[(level_off(l) + box) * pm + m];
+  }
+  for (int j = 1; j <= depth; ++j) {
+    const int l = lt + j, nbx = 1 << j;
+    const int64_t nb = int64_t(1) << l, c0 = c << j;
+    cplx<T>* ms = Ms + (nbx - 2 + 6 * (j - 1)) * p;
+    for (int e = threadIdx.x; e < (nbx + 6) * p; e += blockDim.x) {
+      const int bi = e / p, m = e - bi * p;
+      const int64_t box = (c0 - 3 + bi + nb) & (nb - 1);
+      ms[e] = mexp[(level_off(l) + box) * pm + m];
+    }
+  }
+  __syncthreads();
+  // M2L parts: the ancestors' (outputs 0 .. na p) and the subtree's
+  for (int e = threadIdx.x; e < na * p + nlam; e += blockDim.x) {
+    if (e < na * p) {
+      const int li = e / p, n = e - li * p;
+      const int l = 3 + li;
+      const int odd = (int)((c >> (lt - l)) & 1);
+      const cplx<T>* mv = An + li * 3 * p;
+      auto msrc = [&](int off) {
+        const int t = odd ? (off == -3 ? 0 : (off == -2 ? 1 : 2)) : (off == -2 ? 0 : (off == 2 ? 1 : 2));
+        return mv + t * p;
+      };
+      const T lw = log_kernel ? (T)level_logw(log_kernel, log2N, l) : (T)0;
+      AL[e] = m2l_one<T>(Tm, Tl, p, n, odd, msrc, nullptr, lw);
+    } else {
+      const int f = e - na * p;
+      int j = 1;
+      while (((2 << j) - 2) * p <= f) ++j;  // level lt + j holds f
+      const int nbx = 1 << j;
+      const int r = f - (nbx - 2) * p, bi = r / p, n = r - bi * p;
+      const cplx<T>* ms = Ms + (nbx - 2 + 6 * (j - 1)) * p;
+      auto msrc = [&](int off) { return ms + (bi + 3 + off) * p; };
+      const T lw = log_kernel ? (T)level_logw(log_kernel, log2N, lt + j) : (T)0;
+      Lam[f] = m2l_one<T>(Tm, Tl, p, n, (int)(((c << j) + bi) & 1), msrc, nullptr, lw);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    for (int li = 1; li < na; ++li) {
+      const int odd = (int)((c >> (lt - 3 - li)) & 1);
+      for (int n = threadIdx.x; n < p; n += 32)
+        AL[li * p + n] = cadd(AL[li * p + n], l2l_one<T>(Tl, p, n, odd, AL + (li - 1) * p));
+      __syncwarp();
+    }
+  }
+  // the subtree's levels in place, from the root's local AL[na - 1]
+  for (int j = 1; j <= depth; ++j) {
+    __syncthreads();  // the parent level is complete
+    const int nbx = 1 << j;
+    cplx<T>* cur = Lam + (nbx - 2) * p;
+    const cplx<T>* par = j == 1 ? AL + (na - 1) * p : Lam + (nbx / 2 - 2) * p;
+    for (int e = threadIdx.x; e < nbx * p; e += blockDim.x) {
+      const int bi = e / p, n = e - bi * p;
+      cur[e] = cadd(cur[e], l2l_one<T>(Tl, p, n, bi & 1, par + (bi >> 1) * p));
+    }
+  }
+  __syncthreads();
+  const cplx<T>* fin = Lam + ((1 << depth) - 2) * p;
+  cplx<T>* dst = lexp + (level_off(lb) - 4 + (c << depth)) * p;
+  for (int i = threadIdx.x; i < (p << depth); i += blockDim.x) dst[i] = fin[i];
 }
 
 // ---------------------------------------------------------------- level 2
@@ -1062,12 +1186,6 @@ __global__ void __launch_bounds__(kTgtThreads) k_targets_fwd(
 // Charges in sorted order: adjoint q_i = conj(F_i) g_perm(i);
 // inverse q_i = Dt_i g_perm(i) (Eq. p6: D_j g_j, scaled by e^{-Lambda}).
 // Signal blockIdx.y: samples and charges at stride M.
-// caller samples (complex64 or complex128) in the arithmetic type
-template <class T> __device__ inline cplx<T> load_in(const double2* p) { return c128_to<T>(*p); }
-template <class T> __device__ inline cplx<T> load_in(const float2* p) {
-  const float2 v = *p;
-  return mk<T>((T)v.x, (T)v.y);
-}
 
 template <class T, class VI>
 __global__ void k_charges(int64_t M, const int32_t* __restrict__ perm,
@@ -1519,9 +1637,10 @@ static size_t down_sub_smem(int p, int depth) {
 }
 
 template <class T>
-static size_t down_chain_smem(int p, int depth, int lt) {
-  return (size_t)2 * p * p * sizeof(T) +
-         ((size_t)2 * ((size_t)p << depth) + (size_t)(lt - 2) * p) * sizeof(cplx<T>);
+static size_t down_fused_smem(int p, int depth, int lt) {
+  const size_t nlam = (((size_t)2 << depth) - 2) * p;
+  return (size_t)6 * p * p * sizeof(T) +
+         (2 * nlam + (size_t)6 * depth * p + (size_t)(lt - 2) * 4 * p) * sizeof(cplx<T>);
 }
 
 int m2l_tc_level(const TreeDims& d, int l, int nsig, const float* bops, const float2* mexp,
@@ -1534,16 +1653,24 @@ int fmm_configure() {
           cudaSuccess ||
       cudaFuncSetAttribute(k_up_top<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big) !=
           cudaSuccess ||
-      cudaFuncSetAttribute(k_up_fused<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big) !=
-          cudaSuccess ||
+      cudaFuncSetAttribute(k_up_fused<T, 0, float2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           big) != cudaSuccess ||
+      cudaFuncSetAttribute(k_up_fused<T, 1, float2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           big) != cudaSuccess ||
+      cudaFuncSetAttribute(k_up_fused<T, 2, float2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           big) != cudaSuccess ||
+      cudaFuncSetAttribute(k_up_fused<T, 0, double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           big) != cudaSuccess ||
+      cudaFuncSetAttribute(k_up_fused<T, 1, double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           big) != cudaSuccess ||
+      cudaFuncSetAttribute(k_up_fused<T, 2, double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           big) != cudaSuccess ||
       cudaFuncSetAttribute(k_p2m_grid<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big) !=
           cudaSuccess ||
       cudaFuncSetAttribute(k_down_top<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            big) != cudaSuccess ||
-      cudaFuncSetAttribute(k_down_chain<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      cudaFuncSetAttribute(k_down_fused<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            big) != cudaSuccess ||
-      cudaFuncSetAttribute(k_m2l_all<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           4 * 64 * 64 * (int)sizeof(T)) != cudaSuccess ||
       cudaFuncSetAttribute(k_down_sub<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            big) != cudaSuccess ||
       cudaFuncSetAttribute(k_level2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1590,66 +1717,113 @@ template <> struct PlanT<float> {
   static const float* Ct(nufft_plan_s* pl) { return pl->Ctf; }
 };
 
-// Upward pass + far field + level-2 coefficients for charges already laid out
-// (uniform: on the grid, `charge` = the grid samples; non-uniform: sorted);
-// all signals of the plan at once (grid y = signal).
-template <class T>
-int fmm_upward_downward(nufft_plan_s* pl, const FmmOps& ops, bool uniform_sources,
-                        const cplx<T>* charge, double2* lvl2, float2* lvl2f) {
+// Upward pass (P2M, M2M) for all signals of the plan at once (grid y =
+// signal), then the level-2 coefficients on a side branch.  Sources:
+// uniform (the grid samples `charge`, [batch][N]) or the sorted non-uniform
+// points (`charge`, [batch][M]); with `gin` set (non-uniform sources only),
+// the charges are formed from the caller's samples as coef_i g_perm(i)
+// (conj(coef_i) when conj) and stored to `charge`: inside the upward kernel
+// where it forms the leaves' multipoles itself, else by k_charges first;
+// *charges_done then reports that the charges are in place.
+template <class T, class VI>
+int fmm_upward(nufft_plan_s* pl, const FmmOps& ops, bool uniform_sources, const cplx<T>* charge,
+               const cplx<T>* coef, int conj, const VI* gin, bool* charges_done, double2* lvl2,
+               float2* lvl2f) {
   cudaStream_t st = pl->stream;
   const TreeDims d = dims_of(pl);
   const unsigned nsig = (unsigned)pl->batch;
   int64_t B = pl->B;
   cplx<T>* mexp = (cplx<T>*)pl->mexp;
-  cplx<T>* lexp = (cplx<T>*)pl->lexp;
   cplx<T>* mleaf = mexp + level_off(pl->L) * pl->pm;
-  prof_begin(pl, NUFFT_STAGE_P2M);
-  if (uniform_sources && pl->N >= kP2mChunk && pl->s <= kP2mChunk &&
-      p2m_grid_smem<T>(pl->s, pl->pm) <= kSmemBudget) {
-    launch_pdl(k_p2m_grid<T>, dim3((unsigned)(pl->N / kP2mChunk), nsig), 256,
-               p2m_grid_smem<T>(pl->s, pl->pm), st, d, charge, (const T*)pl->op_p2m, mleaf);
-  } else if (uniform_sources) {
-    launch_pdl(k_p2m_uniform<T>, dim3(nblk(B * pl->pm, 256), nsig), 256, 0, st, d, charge,
-               (const T*)pl->op_p2m, mleaf);
-  } else {
-    constexpr int WPB = P2mWarps<T>::value;
-    launch_pdl(k_p2m_nonuniform<T>, dim3(nblk(B, WPB), nsig), 32 * WPB, p2m_smem<T>(pl->pm), st,
-               d, pl->leaf_start, pl->k0, PlanT<T>::delta(pl), charge, mleaf);
-  }
-  if (ops.leaf_shift)
-    launch_pdl(k_leaf_shift<T>, nblk(B * pl->pm, 256), 256, 0, st, B, pl->pm, ops.leaf_shift,
-               mleaf);
-  prof_end(pl, ops.leaf_shift ? 2 : 1);
-  // upward: subtrees of up to kSubDepth levels down to level kTopLevel, then one CTA
-  prof_begin(pl, NUFFT_STAGE_M2M);
-  const int pm = pl->pm, p = pl->p, L = pl->L;
-  int nl = 0;
-  int lev = L;
+  const int pm = pl->pm, L = pl->L;
+  // the one-launch upward pass, with P2M inside where shared memory allows
   UpStages sg;
-  const int ncnt = L > 2 && pl->upcnt && fused_up_enabled() ? up_fused_stages<T>(pm, L, &sg) : -1;
-  if (ncnt >= 0 && ncnt <= pl->upcnt_n) {
-    // one launch: P2M's leaves to level 2 (k_up_fused)
-    launch_pdl(k_up_fused<T>, dim3(1u << sg.lev[1], nsig), 512,
-               up_sub_smem<T>(pm, sg.dmax), st, d, sg, (const T*)pl->op_m2m, mexp, pl->upcnt,
-               pl->upcnt_n);
-    ++nl;
-    lev = 2;
+  const int ncnt = L > 2 && pl->upcnt && fused_up_enabled() && !ops.leaf_shift
+                       ? up_fused_stages<T>(pm, L, &sg) : -1;
+  const bool fused = ncnt >= 0 && ncnt <= pl->upcnt_n;
+  int src = 0;
+  if (fused) {
+    if (uniform_sources && up_fused_smem<T>(pm, sg, 1, pl->s) <= kSmemBudget) src = 1;
+    if (!uniform_sources && up_fused_smem<T>(pm, sg, 2, pl->s) <= kSmemBudget) src = 2;
   }
-  while (lev > kTopLevel) {
-    int dep = kSubDepth;
-    while (dep > 1 && up_sub_smem<T>(pm, dep) > kSmemBudget) --dep;
-    int lt = lev - dep > kTopLevel ? lev - dep : kTopLevel;
-    launch_pdl(k_up_sub<T>, dim3(1u << lt, nsig), 512, up_sub_smem<T>(pm, lev - lt), st, d, lev,
-               lt, (const T*)pl->op_m2m, mexp);
-    ++nl;
-    lev = lt;
+  if (gin && src != 2) {  // charges first, by their own kernel
+    prof_begin(pl, NUFFT_STAGE_P2M);
+    launch_pdl(k_charges<T, VI>, dim3(nblk(pl->M, 256), nsig), 256, 0, st, pl->M, pl->perm, coef,
+               conj, gin, (cplx<T>*)charge);
+    prof_end(pl, 1);
   }
-  if (lev > 2) {
-    size_t sm = (size_t)2 * pm * pm * sizeof(T) + (size_t)3 * ((size_t)pm << lev) / 2 * sizeof(cplx<T>);
-    launch_pdl(k_up_top<T>, dim3(1, nsig), 512, sm, st, d, lev, (const T*)pl->op_m2m, mexp);
-    ++nl;
+  if (charges_done) *charges_done = gin != nullptr;
+  if (src) {
+    prof_begin(pl, NUFFT_STAGE_M2M);
+    UpSrc<T, VI> us;
+    us.q = charge;
+    us.rp = (const T*)pl->op_p2m;
+    us.start = pl->leaf_start;
+    us.k0 = pl->k0;
+    us.delta_t = PlanT<T>::delta(pl);
+    if (src == 2 && gin) {
+      us.perm = pl->perm;
+      us.coef = coef;
+      us.conj = conj;
+      us.gin = gin;
+      us.charge = (cplx<T>*)charge;
+    }
+    const size_t sm = up_fused_smem<T>(pm, sg, src, pl->s);
+    const dim3 grid(1u << sg.lev[1], nsig);
+    if (src == 1)
+      launch_pdl(k_up_fused<T, 1, VI>, grid, kUpThreads, sm, st, d, sg, (const T*)pl->op_m2m,
+                 mexp, pl->upcnt, pl->upcnt_n, us);
+    else
+      launch_pdl(k_up_fused<T, 2, VI>, grid, kUpThreads, sm, st, d, sg, (const T*)pl->op_m2m,
+                 mexp, pl->upcnt, pl->upcnt_n, us);
+    prof_end(pl, 1);
+  } else {
+    prof_begin(pl, NUFFT_STAGE_P2M);
+    if (uniform_sources && pl->N >= kP2mChunk && pl->s <= kP2mChunk &&
+        p2m_grid_smem<T>(pl->s, pl->pm) <= kSmemBudget) {
+      launch_pdl(k_p2m_grid<T>, dim3((unsigned)(pl->N / kP2mChunk), nsig), 256,
+                 p2m_grid_smem<T>(pl->s, pl->pm), st, d, charge, (const T*)pl->op_p2m, mleaf);
+    } else if (uniform_sources) {
+      launch_pdl(k_p2m_uniform<T>, dim3(nblk(B * pl->pm, 256), nsig), 256, 0, st, d, charge,
+                 (const T*)pl->op_p2m, mleaf);
+    } else {
+      constexpr int WPB = P2mWarps<T>::value;
+      launch_pdl(k_p2m_nonuniform<T>, dim3(nblk(B, WPB), nsig), 32 * WPB, p2m_smem<T>(pl->pm),
+                 st, d, pl->leaf_start, pl->k0, PlanT<T>::delta(pl), charge, mleaf);
+    }
+    if (ops.leaf_shift)
+      launch_pdl(k_leaf_shift<T>, nblk(B * pl->pm, 256), 256, 0, st, B, pl->pm, ops.leaf_shift,
+                 mleaf);
+    prof_end(pl, ops.leaf_shift ? 2 : 1);
+    // upward: one launch, or subtrees of up to kSubDepth levels down to level
+    // kTopLevel, then one CTA
+    prof_begin(pl, NUFFT_STAGE_M2M);
+    int nl = 0;
+    int lev = L;
+    if (fused) {
+      launch_pdl(k_up_fused<T, 0, VI>, dim3(1u << sg.lev[1], nsig), kUpThreads,
+                 up_fused_smem<T>(pm, sg, 0, pl->s), st, d, sg, (const T*)pl->op_m2m, mexp,
+                 pl->upcnt, pl->upcnt_n, UpSrc<T, VI>());
+      ++nl;
+      lev = 2;
+    }
+    while (lev > kTopLevel) {
+      int dep = kSubDepth;
+      while (dep > 1 && up_sub_smem<T>(pm, dep) > kSmemBudget) --dep;
+      int lt = lev - dep > kTopLevel ? lev - dep : kTopLevel;
+      launch_pdl(k_up_sub<T>, dim3(1u << lt, nsig), 512, up_sub_smem<T>(pm, lev - lt), st, d,
+                 lev, lt, (const T*)pl->op_m2m, mexp);
+      ++nl;
+      lev = lt;
+    }
+    if (lev > 2) {
+      size_t sm = (size_t)2 * pm * pm * sizeof(T) +
+                  (size_t)3 * ((size_t)pm << lev) / 2 * sizeof(cplx<T>);
+      launch_pdl(k_up_top<T>, dim3(1, nsig), 512, sm, st, d, lev, (const T*)pl->op_m2m, mexp);
+      ++nl;
+    }
+    prof_end(pl, nl);
   }
-  prof_end(pl, nl);
   // level-2 coefficients on the side branch (only the targets need them)
   prof_begin(pl, NUFFT_STAGE_LEVEL2);
   {
@@ -1659,12 +1833,25 @@ int fmm_upward_downward(nufft_plan_s* pl, const FmmOps& ops, bool uniform_source
     side_end(pl, 0, s2);
   }
   prof_end(pl, 1);
-  // downward: without tensor-core levels, all M2L at once and then the L2L
-  // chains in one launch; with them, levels 3..kTopLevel in one CTA, then subtrees (cut
-  // from the finest level up so the costly fine levels get the most CTAs)
-  // down to the first tensor-core level
+  return cudaGetLastError() == cudaSuccess ? NUFFT_OK : NUFFT_ECUDA;
+}
+
+// Downward pass (M2L, L2L) to the leaves' local expansions, then joins the
+// level-2 side branch.
+template <class T>
+int fmm_downward(nufft_plan_s* pl, const FmmOps& ops) {
+  cudaStream_t st = pl->stream;
+  const TreeDims d = dims_of(pl);
+  const unsigned nsig = (unsigned)pl->batch;
+  cplx<T>* mexp = (cplx<T>*)pl->mexp;
+  cplx<T>* lexp = (cplx<T>*)pl->lexp;
+  const int p = pl->p, L = pl->L;
+  int nl = 0;
+  // without tensor-core levels the whole pass in one launch; with them,
+  // levels 3..kTopLevel in one CTA, then subtrees (cut from the finest level
+  // up so the costly fine levels get the most CTAs) down to the first
+  // tensor-core level
   prof_begin(pl, NUFFT_STAGE_M2L);
-  nl = 0;
   int log2N = 0;
   while ((int64_t(1) << log2N) < pl->N) ++log2N;
   if (L >= 3) {
@@ -1680,21 +1867,19 @@ int fmm_upward_downward(nufft_plan_s* pl, const FmmOps& ops, bool uniform_source
       if (!ops.log_kernel && pl->op_tc && pl->tc_level >= 4 && pl->tc_level <= L)
         lc = pl->tc_level > top + 1 ? pl->tc_level : top + 1;
     if (lc > L) {
-      // no tensor-core levels: every level's M2L in one parallel launch, then
-      // the L2L chains in one launch (k_down_chain)
-      const int64_t nout = (level_off(L + 1) - level_off(3)) * (int64_t)p;
-      const unsigned nbk = (unsigned)((nout + 255) / 256);
-      launch_pdl(k_m2l_all<T>, dim3(nbk, nsig), 256, (size_t)4 * p * p * sizeof(T), st, d, 3, L,
-                 (const T*)ops.m2l, mexp, lexp, ops.log_kernel, log2N);
-      ++nl;
-      if (L >= 4) {
-        int dep = kSubDepth;
-        while (dep > 1 && down_chain_smem<T>(p, dep, L) > kSmemBudget) --dep;
-        const int lt = L - dep > 3 ? L - dep : 3;  // subtree roots
-        launch_pdl(k_down_chain<T>, dim3(1u << lt, nsig), 512, down_chain_smem<T>(p, L - lt, lt),
-                   st, d, lt, L, (const T*)ops.l2l, lexp);
-        ++nl;
+      // no tensor-core levels: the whole downward pass in one launch
+      int dep = kSubDepth;
+      while (dep > 1 && down_fused_smem<T>(p, dep, L) > kSmemBudget) --dep;
+      const int lt = L - dep > 3 ? L - dep : 3;  // subtree roots
+      if (L > 3) {
+        launch_pdl(k_down_fused<T>, dim3(1u << lt, nsig), 512, down_fused_smem<T>(p, L - lt, lt),
+                   st, d, lt, L, (const T*)ops.m2l, (const T*)ops.l2l, mexp, lexp,
+                   ops.log_kernel, log2N);
+      } else {  // L = 3: level 3 alone
+        launch_pdl(k_down_top<T>, dim3(1, nsig), 512, smt, st, d, 3, (const T*)ops.m2l,
+                   (const T*)ops.l2l, mexp, lexp, ops.log_kernel, log2N);
       }
+      ++nl;
     } else {
       launch_pdl(k_down_top<T>, dim3(1, nsig), 512, smt, st, d, top, (const T*)ops.m2l,
                  (const T*)ops.l2l, mexp, lexp, ops.log_kernel, log2N);
@@ -1725,6 +1910,14 @@ int fmm_upward_downward(nufft_plan_s* pl, const FmmOps& ops, bool uniform_source
   prof_end(pl, nl);
   side_join(pl, 0);
   return cudaGetLastError() == cudaSuccess ? NUFFT_OK : NUFFT_ECUDA;
+}
+
+template <class T>
+int fmm_upward_downward(nufft_plan_s* pl, const FmmOps& ops, bool uniform_sources,
+                        const cplx<T>* charge, double2* lvl2, float2* lvl2f) {
+  int rc = fmm_upward<T, float2>(pl, ops, uniform_sources, charge, nullptr, 0,
+                                 (const float2*)nullptr, nullptr, lvl2, lvl2f);
+  return rc ? rc : fmm_downward<T>(pl, ops);
 }
 
 static FmmOps cot_ops(nufft_plan_s* pl) {
@@ -1790,15 +1983,21 @@ int fmm_to_grid(nufft_plan_s* pl, const void* g, int inverse) {
   cplx<T>* charge = (cplx<T>*)pl->charge;
   const unsigned nsig = (unsigned)pl->batch;
   const dim3 gm(nblk(pl->M, 256), nsig);
-  prof_begin(pl, NUFFT_STAGE_P2M);
-  if (c64)
-    launch_pdl(k_charges<T, float2>, gm, 256, 0, st, pl->M, pl->perm, coef, (int)!inverse,
-               (const float2*)g, charge);
-  else
-    launch_pdl(k_charges<T, double2>, gm, 256, 0, st, pl->M, pl->perm, coef, (int)!inverse,
-               (const double2*)g, charge);
-  prof_end(pl, 1);
-  // self terms on the side branch: only the targets kernel needs them
+  // charges q_i = coef_i g_perm(i) (conj(F_i) for the adjoint) and the
+  // upward pass; the charges are formed inside the upward kernel when it
+  // forms the leaf multipoles itself
+  const FmmOps ops = cot_ops(pl);
+  double2* l2 = pl->lvl2;
+  float2* l2f = sizeof(T) == 4 ? pl->lvl2f : nullptr;
+  bool done = false;
+  int rc = c64 ? fmm_upward<T, float2>(pl, ops, false, charge, coef, (int)!inverse,
+                                       (const float2*)g, &done, l2, l2f)
+               : fmm_upward<T, double2>(pl, ops, false, charge, coef, (int)!inverse,
+                                        (const double2*)g, &done, l2, l2f);
+  if (rc) return rc;
+  if (!done) return NUFFT_ECUDA;
+  // self terms on the side branch (they need the charges; only the targets
+  // kernel needs them), overlapping the downward pass
   const TreeDims d = dims_of(pl);
   cplx<T>* stt = (cplx<T>*)pl->selft;
   prof_begin(pl, NUFFT_STAGE_OTHER);
@@ -1813,8 +2012,7 @@ int fmm_to_grid(nufft_plan_s* pl, const void* g, int inverse) {
                PlanT<T>::Ct(pl), PlanT<T>::delta(pl), KConst<T>::n_2pi_h(d), stt);
   side_end(pl, 1, s1);
   prof_end(pl, 1);
-  int rc = fmm_upward_downward<T>(pl, cot_ops(pl), false, charge, pl->lvl2,
-                                  sizeof(T) == 4 ? pl->lvl2f : nullptr);
+  rc = fmm_downward<T>(pl, ops);
   if (rc) return rc;
   SrcPos<T>* pos = (SrcPos<T>*)pl->srcpos;
   side_join(pl, 1);
