@@ -514,6 +514,23 @@ __device__ inline cplx<T> l2l_one(const T* __restrict__ Tl, int p, int n, int od
   return mk<T>(ar, ai);
 }
 
+// l2l_one over all k (the table is zero for k < n, and fma(0, x, a) = a
+// for finite x): the same value, with a loop length that is the same for
+// every lane
+template <class T>
+__device__ inline cplx<T> l2l_full(const T* __restrict__ Tl, int p, int n, int odd,
+                                   const cplx<T>* __restrict__ lpar) {
+  T ar = 0, ai = 0;
+  const T* Tt = Tl + odd * p * p + n;
+  for (int k = 0; k < p; ++k) {
+    T w = Tt[k * p];
+    cplx<T> x = lpar[k];
+    ar = fma(w, x.x, ar);
+    ai = fma(w, x.y, ai);
+  }
+  return mk<T>(ar, ai);
+}
+
 template <class T>
 __global__ void __launch_bounds__(512) k_down_top(TreeDims d, int lt, const T* __restrict__ op_m2l,
                                                   const T* __restrict__ op_l2l,
@@ -677,29 +694,33 @@ __global__ void __launch_bounds__(512) k_down_fused(TreeDims d, int lt, int lb,
     }
   }
   __syncthreads();
-  // M2L parts: the ancestors' (outputs 0 .. na p) and the subtree's
-  for (int e = threadIdx.x; e < na * p + nlam; e += blockDim.x) {
-    if (e < na * p) {
-      const int li = e / p, n = e - li * p;
-      const int l = 3 + li;
-      const int odd = (int)((c >> (lt - l)) & 1);
-      const cplx<T>* mv = An + li * 3 * p;
-      auto msrc = [&](int off) {
-        const int t = odd ? (off == -3 ? 0 : (off == -2 ? 1 : 2)) : (off == -2 ? 0 : (off == 2 ? 1 : 2));
-        return mv + t * p;
-      };
-      const T lw = log_kernel ? (T)level_logw(log_kernel, log2N, l) : (T)0;
-      AL[e] = m2l_one<T>(Tm, Tl, p, n, odd, msrc, nullptr, lw);
-    } else {
-      const int f = e - na * p;
-      int j = 1;
-      while (((2 << j) - 2) * p <= f) ++j;  // level lt + j holds f
-      const int nbx = 1 << j;
-      const int r = f - (nbx - 2) * p, bi = r / p, n = r - bi * p;
-      const cplx<T>* ms = Ms + (nbx - 2 + 6 * (j - 1)) * p;
+  // M2L parts: the ancestors' and, level by level, the subtree's; a thread's
+  // outputs (box bi, coefficient n) advance by blockDim.x = sb p + sn
+  const int sb = (int)blockDim.x / p, sn = (int)blockDim.x - sb * p;
+  for (int e = threadIdx.x; e < na * p; e += blockDim.x) {
+    const int li = e / p, n = e - li * p;
+    const int l = 3 + li;
+    const int odd = (int)((c >> (lt - l)) & 1);
+    const cplx<T>* mv = An + li * 3 * p;
+    auto msrc = [&](int off) {
+      const int t = odd ? (off == -3 ? 0 : (off == -2 ? 1 : 2)) : (off == -2 ? 0 : (off == 2 ? 1 : 2));
+      return mv + t * p;
+    };
+    const T lw = log_kernel ? (T)level_logw(log_kernel, log2N, l) : (T)0;
+    AL[e] = m2l_one<T>(Tm, Tl, p, n, odd, msrc, nullptr, lw);
+  }
+  const int bi0 = (int)threadIdx.x / p, n0 = (int)threadIdx.x - bi0 * p;
+  for (int j = 1; j <= depth; ++j) {
+    const int nbx = 1 << j;
+    const cplx<T>* ms = Ms + (nbx - 2 + 6 * (j - 1)) * p;
+    cplx<T>* lam = Lam + (nbx - 2) * p;
+    const T lw = log_kernel ? (T)level_logw(log_kernel, log2N, lt + j) : (T)0;
+    for (int bi = bi0, n = n0; bi < nbx;) {
       auto msrc = [&](int off) { return ms + (bi + 3 + off) * p; };
-      const T lw = log_kernel ? (T)level_logw(log_kernel, log2N, lt + j) : (T)0;
-      Lam[f] = m2l_one<T>(Tm, Tl, p, n, (int)(((c << j) + bi) & 1), msrc, nullptr, lw);
+      lam[bi * p + n] = m2l_one<T>(Tm, Tl, p, n, bi & 1, msrc, nullptr, lw);
+      bi += sb;
+      n += sn;
+      if (n >= p) { n -= p; ++bi; }
     }
   }
   __syncthreads();
@@ -707,7 +728,7 @@ __global__ void __launch_bounds__(512) k_down_fused(TreeDims d, int lt, int lb,
     for (int li = 1; li < na; ++li) {
       const int odd = (int)((c >> (lt - 3 - li)) & 1);
       for (int n = threadIdx.x; n < p; n += 32)
-        AL[li * p + n] = cadd(AL[li * p + n], l2l_one<T>(Tl, p, n, odd, AL + (li - 1) * p));
+        AL[li * p + n] = cadd(AL[li * p + n], l2l_full<T>(Tl, p, n, odd, AL + (li - 1) * p));
       __syncwarp();
     }
   }
@@ -717,9 +738,11 @@ __global__ void __launch_bounds__(512) k_down_fused(TreeDims d, int lt, int lb,
     const int nbx = 1 << j;
     cplx<T>* cur = Lam + (nbx - 2) * p;
     const cplx<T>* par = j == 1 ? AL + (na - 1) * p : Lam + (nbx / 2 - 2) * p;
-    for (int e = threadIdx.x; e < nbx * p; e += blockDim.x) {
-      const int bi = e / p, n = e - bi * p;
-      cur[e] = cadd(cur[e], l2l_one<T>(Tl, p, n, bi & 1, par + (bi >> 1) * p));
+    for (int bi = bi0, n = n0; bi < nbx;) {
+      cur[bi * p + n] = cadd(cur[bi * p + n], l2l_full<T>(Tl, p, n, bi & 1, par + (bi >> 1) * p));
+      bi += sb;
+      n += sn;
+      if (n >= p) { n -= p; ++bi; }
     }
   }
   __syncthreads();
@@ -1738,6 +1761,8 @@ int fmm_upward(nufft_plan_s* pl, const FmmOps& ops, bool uniform_sources, const 
   const int pm = pl->pm, L = pl->L;
   // the one-launch upward pass, with P2M inside where shared memory allows
   UpStages sg;
+  // (non-uniform sources: a shallower first stage, one leaf per warp, so
+  // the per-leaf P2M loops run on as many warps as a separate P2M would)
   const int ncnt = L > 2 && pl->upcnt && fused_up_enabled() && !ops.leaf_shift
                        ? up_fused_stages<T>(pm, L, &sg) : -1;
   const bool fused = ncnt >= 0 && ncnt <= pl->upcnt_n;
