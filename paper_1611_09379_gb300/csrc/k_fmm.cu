@@ -324,11 +324,10 @@ template <class T, class VI> struct UpSrc {
   cplx<T>* charge = nullptr;
   int conj = 0;
 };
-// threads of k_up_fused (1024 for the source modes measured slower)
-template <int SRC> struct UpThreads { static constexpr int value = 512; };
+constexpr int kUpThreads = 512;  // (1024 for the P2M source modes measured slower)
 
 template <class T, int SRC, class VI>
-__global__ void __launch_bounds__(UpThreads<SRC>::value) k_up_fused(TreeDims d, UpStages sg,
+__global__ void __launch_bounds__(kUpThreads) k_up_fused(TreeDims d, UpStages sg,
                                                          const T* __restrict__ op,
                                                          cplx<T>* __restrict__ mexp,
                                                          int* __restrict__ cnt, int cstride,
@@ -391,7 +390,7 @@ __global__ void __launch_bounds__(UpThreads<SRC>::value) k_up_fused(TreeDims d, 
       const cplx<T>* chg = src.q ? src.q + so : nullptr;
       const VI* gin = src.gin ? src.gin + so : nullptr;
       cplx<T>* cout = src.charge ? src.charge + so : nullptr;
-      for (int lf = warp; lf < nl0; lf += UpThreads<SRC>::value / 32) {
+      for (int lf = warp; lf < nl0; lf += kUpThreads / 32) {
         p2m_leaf_warp<T>(
             d, b0 + lf, lane, tile, src.start, src.k0, src.delta_t,
             [&](int i, bool first) {
@@ -448,7 +447,7 @@ size_t up_fused_smem(int pm, const UpStages& sg, int src, int s) {
   size_t b = (size_t)2 * pm * pm * sizeof(T) + (size_t)3 * ((size_t)pm << sg.dmax) / 2 * sizeof(cplx<T>);
   const size_t nl0 = (size_t)1 << (sg.lev[0] - sg.lev[1]);
   if (src == 1) b += nl0 * (s + 1) * sizeof(cplx<T>) + (size_t)s * pm * sizeof(T);
-  if (src == 2) b += (size_t)(UpThreads<2>::value / 32) * (pm < 32 ? pm : 32) * kP2mPitch * sizeof(cplx<T>);
+  if (src == 2) b += (size_t)(kUpThreads / 32) * (pm < 32 ? pm : 32) * kP2mPitch * sizeof(cplx<T>);
   return b;
 }
 
@@ -1797,10 +1796,10 @@ int fmm_upward(nufft_plan_s* pl, const FmmOps& ops, bool uniform_sources, const 
     const size_t sm = up_fused_smem<T>(pm, sg, src, pl->s);
     const dim3 grid(1u << sg.lev[1], nsig);
     if (src == 1)
-      launch_pdl(k_up_fused<T, 1, VI>, grid, UpThreads<1>::value, sm, st, d, sg, (const T*)pl->op_m2m,
+      launch_pdl(k_up_fused<T, 1, VI>, grid, kUpThreads, sm, st, d, sg, (const T*)pl->op_m2m,
                  mexp, pl->upcnt, pl->upcnt_n, us);
     else
-      launch_pdl(k_up_fused<T, 2, VI>, grid, UpThreads<2>::value, sm, st, d, sg, (const T*)pl->op_m2m,
+      launch_pdl(k_up_fused<T, 2, VI>, grid, kUpThreads, sm, st, d, sg, (const T*)pl->op_m2m,
                  mexp, pl->upcnt, pl->upcnt_n, us);
     prof_end(pl, 1);
   } else {
@@ -1827,7 +1826,7 @@ int fmm_upward(nufft_plan_s* pl, const FmmOps& ops, bool uniform_sources, const 
     int nl = 0;
     int lev = L;
     if (fused) {
-      launch_pdl(k_up_fused<T, 0, VI>, dim3(1u << sg.lev[1], nsig), UpThreads<0>::value,
+      launch_pdl(k_up_fused<T, 0, VI>, dim3(1u << sg.lev[1], nsig), kUpThreads,
                  up_fused_smem<T>(pm, sg, 0, pl->s), st, d, sg, (const T*)pl->op_m2m, mexp,
                  pl->upcnt, pl->upcnt_n, UpSrc<T, VI>());
       ++nl;
