@@ -1509,9 +1509,18 @@ __global__ void __launch_bounds__(kTgtThreads, sizeof(T) == 4 ? 5 : 4) k_targets
     acc0.add_r(v.q, r0);
     acc1.add_r(v.q, r1);
   };
-  // the same for a source that may lie outside the lane's window [lo, hi)
-  // (no pairs) or in one of its own runs (e0 = 0: no pair with k; e0 = -1:
-  // no pair with k + 1; those enter through the self terms)
+  // the same for a source that may lie in one of the lane's own runs (e0 =
+  // 0: no pair with k; e0 = -1: no pair with k + 1; those enter through the
+  // self terms), and (both_checked) also outside its window [lo, hi)
+  auto both_own = [&](int i) {
+    const SrcQ<T> v = sw[i];
+    const T e0 = kf0 - v.rel.x;
+    T r0 = rcp_t(e0 - v.rel.y), r1 = rcp_t((e0 + (T)1) - v.rel.y);
+    r0 = e0 != (T)0 ? r0 : (T)0;
+    r1 = e0 != (T)-1 ? r1 : (T)0;
+    acc0.add_r(v.q, r0);
+    acc1.add_r(v.q, r1);
+  };
   auto both_checked = [&](int i, int lo, int hi) {
     const SrcQ<T> v = sw[i];
     const T e0 = kf0 - v.rel.x;
@@ -1560,20 +1569,26 @@ __global__ void __launch_bounds__(kTgtThreads, sizeof(T) == 4 ? 5 : 4) k_targets
     }
     // pairs: the warp walks the union of its lanes' windows in chunks of 16
     // sources; a chunk that is not inside every active lane's window, or
-    // that meets a lane's own runs, is taken by the whole warp in the checked
-    // form (a warp vote), so no lane waits on another's different bounds
+    // that meets a lane's own runs, is taken by the whole warp in the
+    // corresponding checked form (warp votes), so no lane waits on another's
+    // different bounds
     const int ulo = __reduce_min_sync(0xffffffffu, has ? lo : INT_MAX);
     const int uhi = __reduce_max_sync(0xffffffffu, has ? hi : INT_MIN);
     for (int i = ulo; i < uhi; i += 16) {
       const int n = uhi - i < 16 ? uhi - i : 16;
-      const bool bad = act && (i < lo || i + 16 > hi || (i < h2 && i + 16 > ha));
-      if (n == 16 && !__any_sync(0xffffffffu, bad)) {
-#pragma unroll
-        for (int u = 0; u < 16; ++u) both(i + u);
-      } else {
+      const bool edge = act && (i < lo || i + 16 > hi);
+      const bool own = act && i < h2 && i + 16 > ha;
+      if (n < 16 || __any_sync(0xffffffffu, edge)) {
 #pragma unroll
         for (int u = 0; u < 16; ++u)
           if (u < n) both_checked(i + u, lo, hi);
+      } else if (__any_sync(0xffffffffu, own)) {
+        // inside every active lane's window: only the own runs are left out
+#pragma unroll
+        for (int u = 0; u < 16; ++u) both_own(i + u);
+      } else {
+#pragma unroll
+        for (int u = 0; u < 16; ++u) both(i + u);
       }
       acc0.fold();
       acc1.fold();
