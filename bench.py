@@ -214,6 +214,26 @@ def sfu_pair_peak_tflops(peaks):
     return 152 * 16 * 4 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
 
 
+# ---------------------------------------------------------------- replicas
+
+def ranks_max(x: float, ws: int, dev) -> float:
+    """Largest value of x over the ranks (the slowest replica's time); the
+    tensor lives on `dev` (the rank's GPU under NCCL, the CPU under gloo)."""
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(points_per_replica: int, ms_slowest: float, ws: int) -> float:
+    """Whole-job points/s of ws independent replicas: the points of all ranks
+    over the slowest rank's time per step."""
+    return ws * points_per_replica / (ms_slowest / 1e3)
+
+
 # ---------------------------------------------------------------- our arm
 
 def run_ours(args):
@@ -320,20 +340,12 @@ def run_ours(args):
             results[tag]["e2e_bytes"] = (N * 16, M * 16 + N * 16)
         plan.close()
 
-    # max over ranks of the timed totals
-    def ranks_max(x):
-        if ws == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
     mx = results["mixed"]
-    ms_step = ranks_max(sum(mx["ms"]) / len(mx["ms"]))
-    value = ws * 2 * M / (ms_step / 1e3)
+    ms_step = ranks_max(sum(mx["ms"]) / len(mx["ms"]), ws, dev)
+    value = replica_throughput(2 * M, ms_step, ws)
     fp = results["fp64"]
-    ms_fp64 = ranks_max(sum(fp["ms"]) / len(fp["ms"]))
-    e2e_ms = ranks_max(sum(mx["e2e_ms"]) / len(mx["e2e_ms"]))
+    ms_fp64 = ranks_max(sum(fp["ms"]) / len(fp["ms"]), ws, dev)
+    e2e_ms = ranks_max(sum(mx["e2e_ms"]) / len(mx["e2e_ms"]), ws, dev)
 
     if rank != 0:
         if ws > 1:
@@ -409,7 +421,7 @@ def run_ours(args):
                    "plan_s": mx["t_plan_s"]},
         "stages_ms_per_step": {k: round(v, 5) for k, v in per.items()},
         "stage_roofline": sroof,
-        "fp64": {"eps": EPS_FP64, "ms_per_step": ms_fp64, "value": ws * 2 * M / (ms_fp64 / 1e3),
+        "fp64": {"eps": EPS_FP64, "ms_per_step": ms_fp64, "value": replica_throughput(2 * M, ms_fp64, ws),
                  "params": fp["info"], "stages_ms_per_step":
                      {k: round(v[0] / steps, 5) for k, v in fp["stats"].items()},
                  "plan_s": fp["t_plan_s"]},
@@ -417,7 +429,7 @@ def run_ours(args):
         "tuning": tuning or None,
         "roofline": roof,
         "cpu_baseline": cpu,
-        "e2e": {"value": ws * 2 * M / (e2e_ms / 1e3), "unit": "points/s",
+        "e2e": {"value": replica_throughput(2 * M, e2e_ms, ws), "unit": "points/s",
                 "h2d_bytes_per_step": mx["e2e_bytes"][0], "d2h_bytes_per_step": mx["e2e_bytes"][1]},
         "gpu_launches": launches,
         "clocks": mx["clocks"],
