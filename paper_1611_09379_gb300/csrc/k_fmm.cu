@@ -137,31 +137,43 @@ __device__ inline void p2m_leaf_warp(const TreeDims& d, int64_t b, int lane, cpl
   for (int mc = 0; mc < d.pm; mc += 32) {
     const int nm = d.pm - mc < 32 ? d.pm - mc : 32;
     T accr = 0, acci = 0;
-    for (int c0 = a; c0 < e; c0 += 32) {
-      const int i = c0 + lane;
-      cplx<T> q = mk<T>(0, 0);
-      T rho = 0;
-      if (i < e) {
-        const int o = (k0[i] - bs) & (N - 1);
-        rho = fma((T)o + delta_t[i], inv_s, (T)-0.5);
-        q = qget(i, mc == 0);
-      }
-      T pw = 1;
-      for (int m = 0; m < mc; ++m) pw *= rho;
-      for (int m = 0; m < nm; ++m) {
-        tile[m * kP2mPitch + lane] = mk<T>(q.x * pw, q.y * pw);
-        pw *= rho;
-      }
-      __syncwarp();
-      const int nk = e - c0 < 32 ? e - c0 : 32;
-      if (lane < nm) {
-        for (int k = 0; k < nk; ++k) {
-          const cplx<T> v = tile[lane * kP2mPitch + k];
-          accr += v.x;
-          acci += v.y;
+    // two chunks of 32 sources per step: both chunks' loads (and charge
+    // gathers) are issued before either is reduced
+    for (int c0 = a; c0 < e; c0 += 64) {
+      cplx<T> q[2];
+      T rho[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int i = c0 + 32 * h + lane;
+        q[h] = mk<T>(0, 0);
+        rho[h] = 0;
+        if (i < e) {
+          const int o = (k0[i] - bs) & (N - 1);
+          rho[h] = fma((T)o + delta_t[i], inv_s, (T)-0.5);
+          q[h] = qget(i, mc == 0);
         }
       }
-      __syncwarp();
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int cb = c0 + 32 * h;
+        if (cb >= e) break;
+        T pw = 1;
+        for (int m = 0; m < mc; ++m) pw *= rho[h];
+        for (int m = 0; m < nm; ++m) {
+          tile[m * kP2mPitch + lane] = mk<T>(q[h].x * pw, q[h].y * pw);
+          pw *= rho[h];
+        }
+        __syncwarp();
+        const int nk = e - cb < 32 ? e - cb : 32;
+        if (lane < nm) {
+          for (int k = 0; k < nk; ++k) {
+            const cplx<T> v = tile[lane * kP2mPitch + k];
+            accr += v.x;
+            acci += v.y;
+          }
+        }
+        __syncwarp();
+      }
     }
     if (lane < nm) out(mc + lane, mk<T>(accr, acci));
   }
