@@ -13,6 +13,7 @@
 // T_lo[m & (2^b - 1)], filled once per plan with sincospi of exact
 // arguments.
 #include <cstdint>
+#include <cstdlib>
 
 #include "common.cuh"
 
@@ -391,8 +392,12 @@ static void fft_launch(dim3 grid, int threads, size_t smem, cudaStream_t st, con
                        int in_f64, void* out, int out_f64, int logN, int logNs, int J, int logJ,
                        int sign, const cplx<T>* tw, int lo_bits) {
   constexpr int JMAX = FftShape<T, LR>::JMAX;
+  constexpr int JHALF = JMAX > 1 ? JMAX / 2 : JMAX;
   if (J == JMAX)
     launch_pdl(k_fft_st<T, LR, JMAX>, grid, threads, smem, st, in, in_f64, out, out_f64, logN,
+               logNs, J, logJ, sign, tw, lo_bits);
+  else if (J == JHALF)
+    launch_pdl(k_fft_st<T, LR, JHALF>, grid, threads, smem, st, in, in_f64, out, out_f64, logN,
                logNs, J, logJ, sign, tw, lo_bits);
   else
     launch_pdl(k_fft_st<T, LR, 0>, grid, threads, smem, st, in, in_f64, out, out_f64, logN, logNs,
@@ -427,6 +432,18 @@ static int fft_pass(int logR, dim3 grid, int threads, size_t smem, cudaStream_t 
 
 static int g_fft_sms = 0;
 
+// Fewest columns per CTA the pass planner goes down to when the grid of
+// CTAs is small (4: every strided row is a full 32-byte sector of complex64);
+// NUFFT_FFT_MIN_COLS (1, 2, 4 or 8) overrides it for measurements.
+static int fft_min_cols() {
+  static const int v = [] {
+    const char* e = std::getenv("NUFFT_FFT_MIN_COLS");
+    const int x = e ? std::atoi(e) : 4;
+    return (x == 1 || x == 2 || x == 4 || x == 8) ? x : 4;
+  }();
+  return v;
+}
+
 // out = FFT(in) in arithmetic T for `batch` signals of N elements each
 // (signal-major); in / out are complex128 (f64 = 1) or complex64.  Intermediate passes alternate between the scratch vectors buf
 // and buf2 (batch x N cplx<T> each; buf2 is used only with three or more passes), so
@@ -453,10 +470,11 @@ int fft_run(const void* in, int in_f64, void* out, int out_f64, cplx<T>* buf, cp
     const int R = 1 << lr, TPC = R >= 8 ? R / 8 : 1;
     const int64_t NR = N >> lr;
     // columns per CTA: at most kFftMaxThreads threads and kFftSmemElems
-    // elements, at least 4 (contiguous runs), fewer while the grid is small
+    // elements, at least fft_min_cols() (contiguous runs), fewer while the
+    // grid is small
     int J = kFftMaxThreads / TPC;
     while (J > 1 && (int64_t)R * J > kFftSmemElems) J >>= 1;
-    while (J > 4 && (NR / J) * batch < target) J >>= 1;
+    while (J > fft_min_cols() && (NR / J) * batch < target) J >>= 1;
     if (J > NR) J = (int)NR;
     int logJ = 0;
     while ((1 << logJ) < J) ++logJ;
@@ -481,8 +499,13 @@ static int fft_attr() {
   const int nbuf = sizeof(T) == 4 ? 2 : 1;
   const int big =
       (int)((1024 + nbuf * (kFftSmemElems + kFftSmemElems / 32 + 1)) * sizeof(cplx<T>));
-  return cudaFuncSetAttribute(k_fft_st<T, LR, FftShape<T, LR>::JMAX>,
+  constexpr int JMAX = FftShape<T, LR>::JMAX;
+  constexpr int JHALF = JMAX > 1 ? JMAX / 2 : JMAX;
+  return cudaFuncSetAttribute(k_fft_st<T, LR, JMAX>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize, big) == cudaSuccess &&
+                 cudaFuncSetAttribute(k_fft_st<T, LR, JHALF>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      big) == cudaSuccess &&
                  cudaFuncSetAttribute(k_fft_st<T, LR, 0>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       big) == cudaSuccess
