@@ -873,15 +873,26 @@ __device__ inline float int_to_t(int D, float) {
 }
 __device__ inline double int_to_t(int D, double) { return (double)D; }
 
-// 1/t: FP32 reciprocal on the special-function unit (rcp.approx, 1 ulp), or
-// FP64 division (measured faster on this GPU than an FP32 estimate refined by
-// Newton steps in FP64, whose two precision conversions run at the FP64 rate).
+// 1/t: FP32 reciprocal on the special-function unit (rcp.approx, 1 ulp).
+// FP64: the unit's FP64 reciprocal estimate (rcp.approx.ftz.f64, about 20
+// correct bits) refined by two Newton-Raphson steps r <- r + r (1 - t r),
+// each of which squares the relative error, so r is within a few ulp of
+// 1/t (t is never subnormal here).  (An FP32 estimate refined in FP64 was
+// measured slower than a division: its two precision conversions run at the
+// FP64 rate.)  t = 0 gives a NaN; callers that meet t = 0 replace r by 0.
 __device__ inline float rcp_t(float t) {
   float r;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(t));
   return r;
 }
-__device__ inline double rcp_t(double t) { return 1.0 / t; }
+__device__ inline double rcp_t(double t) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(t));
+  double e = fma(-t, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-t, r, 1.0);
+  return fma(r, e, r);
+}
 
 // Near-field accumulation of q / t.  FP64 path: FP64 throughout.  FP32 path:
 // FP32 partial sums of up to 16 terms folded into a compensated (Kahan) FP32
