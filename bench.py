@@ -46,7 +46,7 @@ METRIC = "NUFFT points/s (forward + square inverse, N=M=2^20, mixed eps=1e-6)"
 # k_targets_fwd + one k_targets_grid2 launch), from the ncu capture summarised
 # in profiles/targets_fft_N2p20_mixed.md; reported only while the kernels'
 # source text still hashes to `sha1` (a changed kernel reports null)
-TARGETS_TRAFFIC = {"bytes_per_step": 79026944, "sha1": "7f62c92d6a9f8dc20882a6fb1804e8b9bbefc0c9"}
+TARGETS_TRAFFIC = {"bytes_per_step": 79026944, "sha1": "c5a3ea2716aab91aba53280fb108349e118a4d30"}
 STAGE_KERNELS = {"targets": "k_targets_fwd + k_targets_grid2", "fft": "k_fft_st",
                  "m2l": "k_down_fused (tensor-core levels: k_down_top + k_down_sub + k_m2l_tc)",
                  "p2m": "k_p2m_* + k_charges (when not inside k_up_fused)",
