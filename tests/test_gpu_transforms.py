@@ -158,6 +158,22 @@ def test_adjoint_4096_full(nf, orc, prec, kind):
     assert orc.rel_l2(c, orc.nudft_adj(g, y, N)) < TOL[prec]
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("s", [2, 4, 8])
+def test_adjoint_small_leaves_clustered(nf, orc, prec, s):
+    """Leaves of s grid points: a warp of the two-point kernel covers 64 grid
+    points, i.e. several leaves, so its lanes' windows differ and the chunks
+    at their edges take the checked form; clustered points make the windows
+    uneven."""
+    N, M = 2048, 1777
+    eps = 1e-12 if prec == 0 else 1e-6
+    y = workloads.points("clustered", M, seed=31 + s)
+    g = workloads.samples(M, seed=32 + s)
+    plan = nf.Plan(N, _dev(y), eps=eps, prec=prec, lmax=int(math.log2(N // s)))
+    c = _host(plan.adjoint(_dev(g)))
+    assert orc.rel_l2(c, orc.nudft_adj(g, y, N)) < TOL[prec]
+
+
 def test_adjoint_dot_product(nf):
     N, M = 2048, 5000
     y = workloads.points("uniform", M, seed=21)
@@ -194,6 +210,19 @@ def test_inverse_round_trip(nf, orc, N, jit):
     cref = orc.inufft(g, y, N)
     assert orc.rel_l2(c2, cref) < 1e-12
     assert orc.rel_l2(c2, c) < (1e-12 if jit <= 0.1 else 1e-10)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_inverse_round_trip_small_leaves(nf, orc, prec):
+    """Square inverse with leaves of 2 grid points (the deepest tree)."""
+    N = 1024
+    y = workloads.points("jitter", N, N, seed=41, jitter=0.1)
+    c = workloads.coeffs(N, seed=42)
+    g = orc.nudft_fwd(c, y)
+    plan = nf.Plan(N, _dev(y), eps=1e-12 if prec == 0 else 1e-6, prec=prec, inverse=True,
+                   lmax=9)
+    c2 = _host(plan.inverse(_dev(g)))
+    assert orc.rel_l2(c2, orc.inufft(g, y, N)) < TOL[prec]
 
 
 @pytest.mark.parametrize("N,jit,hit", [(256, 0.1, False), (256, 0.1, True), (4096, 0.4, False),
