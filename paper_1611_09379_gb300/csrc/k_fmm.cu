@@ -1929,15 +1929,16 @@ int fmm_downward(nufft_plan_s* pl, const FmmOps& ops) {
     if constexpr (std::is_same<T, float>::value)
       if (!ops.log_kernel && pl->op_tc && pl->tc_level >= 4 && pl->tc_level <= L)
         lc = pl->tc_level > top + 1 ? pl->tc_level : top + 1;
-    if (lc > L) {
-      // no tensor-core levels: the whole downward pass in one launch
-      int dep = kSubDepth;
-      while (dep > 1 && down_fused_smem<T>(p, dep, L) > kSmemBudget) --dep;
-      const int lt = L - dep > 3 ? L - dep : 3;  // subtree roots
+    // no tensor-core levels: the whole downward pass in one launch, where its
+    // shared memory fits (else, as with tensor-core levels, the banded form)
+    int fdep = kSubDepth;
+    while (fdep > 1 && down_fused_smem<T>(p, fdep, L) > kSmemBudget) --fdep;
+    const int flt = L - fdep > 3 ? L - fdep : 3;  // subtree roots
+    if (lc > L && down_fused_smem<T>(p, L - flt, flt) <= kSmemBudget) {
       if (L > 3) {
-        launch_pdl(k_down_fused<T>, dim3(1u << lt, nsig), 512, down_fused_smem<T>(p, L - lt, lt),
-                   st, d, lt, L, (const T*)ops.m2l, (const T*)ops.l2l, mexp, lexp,
-                   ops.log_kernel, log2N);
+        launch_pdl(k_down_fused<T>, dim3(1u << flt, nsig), 512,
+                   down_fused_smem<T>(p, L - flt, flt), st, d, flt, L, (const T*)ops.m2l,
+                   (const T*)ops.l2l, mexp, lexp, ops.log_kernel, log2N);
       } else {  // L = 3: level 3 alone
         launch_pdl(k_down_top<T>, dim3(1, nsig), 512, smt, st, d, 3, (const T*)ops.m2l,
                    (const T*)ops.l2l, mexp, lexp, ops.log_kernel, log2N);

@@ -98,6 +98,21 @@ def test_forward_constant_function(nf, L, eps):
         assert np.abs(g - 1).max() < eps
 
 
+def test_forward_adjoint_largest_order(nf, orc):
+    """p = 64 (the largest order accepted) in FP64: the downward pass's
+    operators then leave no room for the one-launch form, and the banded
+    form runs instead."""
+    N, M = 4096, 3001
+    y = workloads.points("uniform", M, seed=51)
+    c = workloads.coeffs(N, seed=52)
+    g0 = workloads.samples(M, seed=53)
+    plan = nf.Plan(N, _dev(y), eps=1e-12, lmax=8, p=64)
+    g = _host(plan.forward(_dev(c)))
+    assert orc.rel_l2(g, orc.nudft_fwd(c, y)) < 1e-12
+    a = _host(plan.adjoint(_dev(g0)))
+    assert orc.rel_l2(a, orc.nudft_adj(g0, y, N)) < 1e-12
+
+
 @pytest.mark.parametrize("N,M,lmax", [(8, 5, 2), (16, 40, 2), (64, 1, 3), (256, 255, 4), (1024, 3001, 5)])
 def test_forward_edge_sizes(nf, orc, N, M, lmax):
     y = workloads.points("uniform", M, seed=N + M)
