@@ -139,7 +139,8 @@ typedef struct {
  * trip inv(fwd(c)) against the probe coefficients c.  Search:
  * lmax in {l0 - 1, l0, l0 + 1}; p lowered in steps of 2 and q in steps of 1
  * while accurate; for NUFFT_MIXED every tc_level from max(4, lmax - 9) to
- * lmax and -1, and for batches of 64 signals tc_near on and off.
+ * lmax and -1; lmax again, one level at a time while that gains, at the
+ * lowered p (or p + 2) and q; for batches of 64 signals tc_near on and off.
  *   N, M, y [device], eps, prec, flags (0 or NUFFT_IO_C64), batch: as for
  *          nufft_plan_create (y is read during the call only)
  *   ops    NUFFT_OP_FWD | NUFFT_OP_ADJ | NUFFT_OP_INV (INV needs M == N)
