@@ -305,3 +305,50 @@ def test_mlp_oracle_gradient_matches_finite_differences():
         pm[k] -= h
         fd = (mlp.loss(pp, X, t) - mlp.loss(pm, X, t)) / (2 * h)
         assert abs(fd - g[k]) <= 1e-6 * max(1.0, abs(g[k])), k
+
+
+# ------------------------------------------------------------- symmetries of the sums
+
+@pytest.mark.parametrize("N,m", [(64, 5), (256, 77), (1024, 1000)])
+def test_nudft_grid_shift_theorem(orc, N, m):
+    """Eq. p1 under a shift of the points by m grid steps: g(y + 2 pi m / N)
+    equals the sum with c_n e^(2 pi i n m / N) at y (both routes), checked on
+    points whose shifted copies stay inside [0, 2 pi).  The shifted points are
+    binary64 roundings of y + 2 pi m / N (|error| <= 2^-50 2 pi), which moves
+    term n by a phase of at most n times that: the bound below."""
+    rng = np.random.default_rng(N + m)
+    h = 2 * math.pi / N
+    y = rng.uniform(0, 2 * math.pi - (m + 1) * h, 200)
+    c = workloads.coeffs(N, seed=m)
+    cs = c * np.exp(2j * math.pi * np.arange(N) * m / N)
+    ys = y + m * h
+    for route in ("nudft", "kernel"):
+        lhs = orc.nufft_fwd(c, ys, route=route)
+        rhs = orc.nufft_fwd(cs, y, route=route)
+        assert orc.rel_l2(lhs, rhs) < N * 2.0 ** -50 * 2 * math.pi + 1e-14, route
+
+
+@pytest.mark.parametrize("N", [32, 512])
+def test_nudft_reflection(orc, N):
+    """Eq. p1 at 2 pi - y is the conjugate sum: sum conj(c_n) e^(i n (2 pi - y))
+    = conj(sum c_n e^(i n y)); the adjoint obeys the same reflection."""
+    rng = np.random.default_rng(N)
+    y = rng.uniform(1e-3, 2 * math.pi - 1e-3, 300)
+    c = workloads.coeffs(N, seed=3)
+    g = workloads.samples(300, seed=4)
+    assert orc.rel_l2(orc.nudft_fwd(np.conj(c), 2 * math.pi - y),
+                      np.conj(orc.nudft_fwd(c, y))) < 1e-13
+    assert orc.rel_l2(orc.nudft_adj(np.conj(g), 2 * math.pi - y, N),
+                      np.conj(orc.nudft_adj(g, y, N))) < 1e-13
+
+
+def test_adjoint_is_conjugate_transpose_of_dense_matrix(orc):
+    """The adjoint route equals A^H g for the dense matrix A_jn = e^(i n y_j)
+    built by numpy (brute force at small N)."""
+    N, M = 64, 70
+    rng = np.random.default_rng(9)
+    y = rng.uniform(0, 2 * math.pi, M)
+    g = workloads.samples(M, seed=10)
+    A = np.exp(1j * np.outer(y, np.arange(N)))
+    for route in ("nudft", "kernel"):
+        assert orc.rel_l2(orc.nufft_adj(g, y, N, route=route), A.conj().T @ g) < 1e-12, route
