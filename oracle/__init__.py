@@ -293,13 +293,12 @@ def exact_grid(y, N: int, B: int):
 
 
 def binning(y, N: int, B: int):
-    """Binning reference: (perm, leaf_start, leaf) with points ordered by the
-    exact leaf, within a leaf by the nearest grid point relative to the leaf's
-    first one ((k0 - leaf s) mod N, 0..s), ties by original index."""
-    leaf, k0, _ = exact_grid(y, N, B)
-    s = N // B
-    krel = (k0 - leaf * s) % N
-    perm = np.lexsort((np.arange(leaf.size), krel, leaf)).astype(np.int64)
+    """Binning reference (Sec. 2.1, the "data structure" of Sec. 3.3, reading
+    c3): (perm, leaf_start, leaf) with the points grouped by their exact leaf
+    floor(y B / (2 pi)) and, inside a leaf, kept in their original order (a
+    stable counting sort by leaf)."""
+    leaf, _, _ = exact_grid(y, N, B)
+    perm = np.argsort(leaf, kind="stable").astype(np.int64)
     leaf_start = np.searchsorted(leaf[perm], np.arange(B + 1), side="left").astype(np.int64)
     return perm, leaf_start, leaf
 

@@ -4,7 +4,10 @@ w = softplus(z), z = W3 . gelu(W2 gelu(W1 x + b1) + b2) + b3, gelu(x) =
 x (1 + erf(x / sqrt 2)) / 2; loss = mean_i (log w_i - t_i)^2.  Parameters in
 the library's layout W1[64][8] b1[64] W2[64][64] b2[64] W3[64] b3.  The
 gradient is the chain rule written out; it is pinned by central finite
-differences in tests/test_oracle_pins.py.
+differences, the forward pass by weights with closed-form outputs (tabulated
+normal distribution function), and the density fixed point by a dense
+Frobenius least-squares solve and the equispaced closed form w = 1, all in
+tests/test_oracle_pins.py.
 """
 import numpy as np
 from scipy.special import erf

@@ -42,24 +42,53 @@ def _host(t):
 
 # ------------------------------------------------------------------ binning
 
-@pytest.mark.parametrize("kind,N,M,lmax", [
+_BINNING_CASES = [
     ("uniform", 4096, 5000, 7), ("clustered", 4096, 4096, 7), ("uniform", 64, 33, 2),
     ("uniform", 1 << 14, 1, 9), ("jitter", 2048, 2048, 6),
-])
-def test_binning_bit_exact(nf, orc, kind, N, M, lmax):
+]
+
+
+def _binned(nf, kind, N, M, lmax):
     y = workloads.points(kind, M, N if kind == "jitter" else None, seed=M + lmax, jitter=0.4)
     if kind == "uniform" and M > 10:
         y[:4] = [0.0, np.nextafter(2 * np.pi, 0), np.nextafter(2 * np.pi * 3 / N, 0), 2 * np.pi * 5 / N]
     plan = nf.Plan(N, _dev(y), eps=1e-6, lmax=lmax)
-    perm, start, k0, delta = (_host(t) for t in plan.points())
+    return y, [_host(t) for t in plan.points()]
+
+
+@pytest.mark.parametrize("kind,N,M,lmax", _BINNING_CASES)
+def test_binning_bit_exact(nf, orc, kind, N, M, lmax):
+    """Parity with the paper's binning (Sec. 2.1): every point in its exact
+    leaf, leaf_start bit for bit, the same set of points in every leaf, and
+    k0 / delta of every point equal to the exact-rational grid coordinates."""
+    y, (perm, start, k0, delta) = _binned(nf, kind, N, M, lmax)
     B = 1 << lmax
-    operm, ostart, _ = orc.binning(y, N, B)
+    operm, ostart, oleaf = orc.binning(y, N, B)
     _, ok0, odel = orc.exact_grid(y, N, B)
-    assert np.array_equal(perm, operm)
     assert np.array_equal(start, ostart)
+    assert np.array_equal(np.sort(perm), np.arange(M))
+    assert np.array_equal(oleaf[perm], np.repeat(np.arange(B), np.diff(ostart)))
+    for b in range(B):
+        assert np.array_equal(np.sort(perm[start[b]:start[b + 1]]), operm[ostart[b]:ostart[b + 1]])
     assert np.array_equal(k0, ok0[perm])
     ref = odel[perm]
     assert np.all(np.abs(delta - ref) <= 2 * np.spacing(np.abs(ref)) + 1e-300)
+
+
+@pytest.mark.parametrize("kind,N,M,lmax", _BINNING_CASES)
+def test_binning_layout_inside_leaves(nf, orc, kind, N, M, lmax):
+    """Layout, not parity: inside a leaf the library orders its points by the
+    nearest grid point relative to the leaf's first one, (k0 - leaf s) mod N,
+    then by original index (the staged near-field windows rely on it).  The
+    key is formed here from the oracle's exact k0."""
+    y, (perm, start, _, _) = _binned(nf, kind, N, M, lmax)
+    B = 1 << lmax
+    s = N // B
+    _, ok0, _ = orc.exact_grid(y, N, B)
+    for b in range(B):
+        seg = perm[start[b]:start[b + 1]].astype(np.int64)
+        key = ((ok0[seg] - b * s) % N) * (1 << 40) + seg
+        assert np.all(np.diff(key) > 0), b
 
 
 # ------------------------------------------------------------------ forward

@@ -264,9 +264,11 @@ def test_exact_grid_boundaries_and_hits(orc):
 
 
 def test_binning_is_stable_counting_sort(orc):
-    """Leaves in order; inside a leaf, points by nearest grid point (every
-    k0 lies in [leaf s, leaf s + s], the top end for points rounding up to the
-    next leaf's first grid point), equal k0 by original index."""
+    """Leaves in order; inside a leaf, the points keep their original order
+    (a stable counting sort by leaf, Sec. 2.1); every point's grid coordinate
+    y N / (2 pi) = k0 + delta lies in its leaf's half-open arc; the result
+    equals numpy's stable argsort of the exact leaf index and a plain Python
+    bucket sort of the points."""
     N, B = 1 << 10, 1 << 6
     s = N // B
     y = workloads.points("clustered", 3000, seed=4)
@@ -274,17 +276,22 @@ def test_binning_is_stable_counting_sort(orc):
     _, k0, delta = orc.exact_grid(y, N, B)
     assert np.array_equal(np.sort(perm), np.arange(y.size))
     assert np.all(np.diff(leaf[perm]) >= 0)
+    buckets = [[] for _ in range(B)]
+    for j, b in enumerate(leaf.tolist()):
+        buckets[b].append(j)
+    assert np.array_equal(perm, np.array([j for bk in buckets for j in bk]))
     for bb in range(B):
         seg = perm[start[bb]:start[bb + 1]]
         assert np.all(leaf[seg] == bb)
+        assert np.all(np.diff(seg) > 0)  # original order inside the leaf
         krel = (k0[seg] - bb * s) % N
-        assert np.all((krel >= 0) & (krel <= s))
-        key = krel * (1 << 40) + seg
-        assert np.all(np.diff(key) > 0)
-        # the grid coordinate k0 + delta lies in the leaf's arc [bb s, bb s + s)
         Y = bb * s + krel + delta[seg]
         assert np.all((Y >= bb * s) & (Y < bb * s + s))
     assert start[0] == 0 and start[-1] == y.size
+    # the leaf of an ordinary (non-edge) point is what floating point says
+    Yf = y * (N / (2 * math.pi)) / s
+    safe = np.abs(Yf - np.round(Yf)) > 1e-6
+    assert np.array_equal(leaf[safe], np.floor(Yf[safe]).astype(np.int64) % B)
 
 
 # ------------------------------------------------------------- density-compensation network
@@ -305,6 +312,121 @@ def test_mlp_oracle_gradient_matches_finite_differences():
         pm[k] -= h
         fd = (mlp.loss(pp, X, t) - mlp.loss(pm, X, t)) / (2 * h)
         assert abs(fd - g[k]) <= 1e-6 * max(1.0, abs(g[k])), k
+
+
+def test_mlp_oracle_forward_closed_forms():
+    """Forward pass of the DCF network at weights where it has a closed form:
+    with W1 = W2 = 0 the output is softplus(W3 . gelu(b2) + b3), and
+    gelu(x) = x Phi(x) with the tabulated normal distribution function
+    (tests/golden/normal_cdf_as26.txt); softplus(0) = log 2 and
+    softplus(log(e - 1)) = 1.  One nonzero W2[u, v] checks that the hidden
+    layer is h1 @ W2^T (not W2 h1 transposed) and that the layers nest."""
+    from oracle import mlp
+    table = {float(x): float(v) for x, v in _golden_lines("normal_cdf_as26.txt")}
+    X = np.random.default_rng(1).standard_normal((5, 8))
+    base = np.zeros(mlp.NPARAM)
+    q = mlp.unpack(base)  # views into base
+    # zero network: w = softplus(0) = log 2 for every point
+    assert np.allclose(mlp.forward(base, X), math.log(2.0), rtol=0, atol=1e-15)
+    # output bias alone
+    q["b3"] = math.log(math.e - 1.0)
+    p = base.copy()
+    p[-1] = math.log(math.e - 1.0)
+    assert np.allclose(mlp.forward(p, X), 1.0, rtol=0, atol=1e-15)
+    # W1 = W2 = 0: z = sum_u W3_u gelu(b2_u) + b3, gelu from the table
+    p = np.zeros(mlp.NPARAM)
+    pq = mlp.unpack(p)
+    pq["b2"][:3] = list(table)           # 0.5, 1.0, 2.0
+    pq["W3"][:3] = [1.0, -2.0, 0.5]
+    z = sum(wt * x * table[x] for wt, x in zip([1.0, -2.0, 0.5], table))
+    assert np.allclose(mlp.forward(p, X), math.log1p(math.exp(z)), rtol=1e-14, atol=0)
+    # one path through W2: b1_v = 1, W2[u, v] = 1, W3_u = 1 (u != v)
+    u, v = 7, 40
+    p = np.zeros(mlp.NPARAM)
+    pq = mlp.unpack(p)
+    pq["b1"][v] = 1.0
+    pq["W2"][u, v] = 1.0
+    pq["W3"][u] = 1.0
+    h1 = 1.0 * table[1.0]
+    h2 = h1 * 0.5 * (1.0 + math.erf(h1 / math.sqrt(2.0)))
+    assert np.allclose(mlp.forward(p, X), math.log1p(math.exp(h2)), rtol=1e-14, atol=0)
+    # the input layer reads feature k through W1[u, k]
+    p = np.zeros(mlp.NPARAM)
+    pq = mlp.unpack(p)
+    pq["W1"][3, 5] = 1.0
+    pq["W2"][0, 3] = 1.0
+    pq["W3"][0] = 1.0
+    X2 = np.zeros((3, 8))
+    X2[:, 5] = [0.5, 1.0, 2.0]
+    a1 = X2[:, 5]
+    h1 = a1 * np.array([table[x] for x in (0.5, 1.0, 2.0)])
+    h2 = h1 * 0.5 * (1.0 + np.array([math.erf(x / math.sqrt(2.0)) for x in h1]))
+    assert np.allclose(mlp.forward(p, X2), np.log1p(np.exp(h2)), rtol=1e-14, atol=0)
+
+
+def _frobenius_dcf(y, N):
+    """Density-compensation weights minimising ||A^H W A - I||_F (reading c13)
+    by a dense linear least-squares solve over the M columns vec(a_j a_j^H),
+    a_j the j-th row of A_jn = e^{i n y_j}; no kernel formula involved."""
+    A = np.exp(1j * np.outer(y, np.arange(N)))
+    cols = np.stack([np.outer(A[j].conj(), A[j]).ravel() for j in range(y.size)], axis=1)
+    rhs = np.eye(N).ravel().astype(complex)
+    w, *_ = np.linalg.lstsq(np.vstack([cols.real, cols.imag]),
+                            np.concatenate([rhs.real, rhs.imag]), rcond=None)
+    return w
+
+
+def test_dcf_fixed_point_equispaced_closed_form():
+    """On equispaced points with M a multiple of N every row of |D_N|^2 sums
+    to N M, so the fixed point is w = 1 / M everywhere: log(w / mean w) = 0."""
+    from oracle import mlp
+    for N, M in ((16, 64), (32, 96)):
+        y = 2 * np.pi * np.arange(M) / M + 0.1
+        y = np.mod(y, 2 * np.pi)
+        assert np.abs(mlp.dcf_fixed_point(y, N, iters=50)).max() < 1e-12
+
+
+def _frobenius_objective(y, N, w):
+    A = np.exp(1j * np.outer(y, np.arange(N)))
+    return float(np.linalg.norm((A.conj().T * w) @ A - np.eye(N)))
+
+
+def test_dcf_fixed_point_is_frobenius_optimum():
+    """The fixed point solves the normal equations of min ||A^H W A - I||_F
+    (reading c13).  With M <= 2N - 1 the minimiser is unique and, on these
+    jittered points, positive: the iteration converges to it (up to the
+    normalisation to mean 1), compared with a dense least-squares solve that
+    never forms |D_N|^2.  With M > 2N - 1 the minimiser is not unique; the
+    objective at the fixed point, rescaled, still equals the least-squares
+    minimum."""
+    from oracle import mlp
+    rng = np.random.default_rng(21)
+    N, M = 32, 60
+    y = np.sort(np.mod(2 * np.pi * np.arange(M) / M + rng.uniform(-0.3, 0.3, M) * 2 * np.pi / M,
+                       2 * np.pi))
+    w_ref = _frobenius_dcf(y, N)
+    assert np.all(w_ref > 0)
+    lw = mlp.dcf_fixed_point(y, N, iters=3000)
+    assert np.abs(lw - np.log(w_ref / w_ref.mean())).max() < 1e-9
+    # a slip that keeps translation invariance (|D_N| not squared) is caught
+    t = y[:, None] - y[None, :]
+    sn = np.sin(0.5 * t)
+    K1 = np.abs(np.sin(0.5 * N * t) / np.where(np.abs(sn) < 1e-12, 1.0, sn))
+    K1[np.abs(sn) < 1e-12] = N
+    w1 = np.ones(M)
+    for _ in range(3000):
+        w1 = w1 * N / (K1 @ w1)
+    assert np.abs(np.log(w1 / w1.mean()) - np.log(w_ref / w_ref.mean())).max() > 1e-3
+    # rank-deficient case: same optimal objective
+    N, M = 16, 48
+    y = np.sort(np.mod(2 * np.pi * np.arange(M) / M + rng.uniform(-0.3, 0.3, M) * 2 * np.pi / M,
+                       2 * np.pi))
+    w_ref = _frobenius_dcf(y, N)
+    w = np.exp(mlp.dcf_fixed_point(y, N, iters=3000))
+    A = np.exp(1j * np.outer(y, np.arange(N)))
+    Bw = (A.conj().T * w) @ A
+    sc = np.trace(Bw).real / np.linalg.norm(Bw) ** 2  # best scale of the normalised weights
+    assert _frobenius_objective(y, N, sc * w) <= _frobenius_objective(y, N, w_ref) * (1 + 1e-8)
 
 
 # ------------------------------------------------------------- symmetries of the sums
