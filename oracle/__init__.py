@@ -9,10 +9,15 @@ What it computes (each a definition evaluated directly, see oracle.c):
 
 * ``nudft_fwd``   g_j = sum_n c_n e^{i n y_j}                     (Eq. p1)
 * ``kernel_fwd``  g_j = sum_k F_j G(y_j - x_k) f_k                 (Eq. p2, p4, p5)
+* ``kernel_fwd_plain``  the same sum with Eq. p4 in plain binary64, the
+                  paper's straightforward method, whose error for f = 1 is
+                  the threshold error eps_th(N)            (Sec. 3.1)
 * ``nudft_adj``   c'_n = sum_j e^{-i n y_j} g_j                    (adjoint of Eq. p1)
 * ``kernel_adj``  u_k = sum_j conj(F_j) G(x_k - y_j) g_j           (adjoint of Eq. p4)
 * ``logsin_C/D``  log-sums behind C_k and D_j                      (Eq. p8, reading c4)
 * ``inverse_f``   f_k = sum_j C_k G(x_k - y_j) D_j g_j              (Eq. p6)
+* ``inverse_absf`` a_k = sum_j |L_kj| |g_j|, the modulus sum of inverse_f
+                  (normaliser of reading c16)
 * ``inufft``      c = (1/N) DFT(inverse_f(g))                       (Eq. p1, p6)
 * ``fft`` / ``dft``  radix-2 FFT and direct DFT                     (Eq. p1)
 * ``exact_grid``  leaf index, nearest grid index k0 and offset delta of
@@ -66,12 +71,14 @@ def _load():
         sig = {
             "orc_nudft_fwd": [P, I, P, I, P, I, P],
             "orc_kernel_fwd": [P, I, P, I, P, I, P],
+            "orc_kernel_fwd_plain": [P, I, P, I, P, I, P],
             "orc_cot_sum": [P, I, P, I, P],
             "orc_nudft_adj": [P, P, I, I, P, I, P],
             "orc_kernel_adj": [P, P, I, I, P, I, P],
             "orc_logsin_C": [P, I, I, P, I, P, P],
             "orc_logsin_D": [P, I, P, I, P, P],
             "orc_inverse_f": [P, P, I, I, P, P, P, P, P, I, P],
+            "orc_inverse_absf": [P, P, I, I, P, P, P, I, P],
             "orc_dft": [P, I, ctypes.c_int, P],
             "orc_fft": [P, I, ctypes.c_int, P],
         }
@@ -126,6 +133,18 @@ def kernel_fwd(f, y, idx=None) -> np.ndarray:
     g = np.empty(n, np.complex128)
     _load().orc_kernel_fwd(_ptr(f), f.size, _ptr(y), y.size,
                            _ptr(ia) if ia is not None else None, n, _ptr(g))
+    return g
+
+
+def kernel_fwd_plain(f, y, idx=None) -> np.ndarray:
+    """The paper's straightforward method (Sec. 3.1): g_j = sum_k K_jk f_k with
+    K_jk of Eq. p4 evaluated literally in plain binary64 (no compensation);
+    its error for f = 1 is the threshold error eps_th(N)."""
+    f, y = _c128(f), _f64(y)
+    ia, n = _idx(idx, y.size)
+    g = np.empty(n, np.complex128)
+    _load().orc_kernel_fwd_plain(_ptr(f), f.size, _ptr(y), y.size,
+                                 _ptr(ia) if ia is not None else None, n, _ptr(g))
     return g
 
 
@@ -212,6 +231,24 @@ def inverse_f(g, y, N: int, idx=None, lamD=None) -> np.ndarray:
                           _ptr(lD), _ptr(nD), _ptr(ia) if ia is not None else None,
                           n, _ptr(f))
     return f
+
+
+def inverse_absf(g, y, N: int, idx=None, lamD=None) -> np.ndarray:
+    """a_k = sum_j |C_k G(x_k - y_j) D_j| |g_j| (the modulus of every term of
+    inverse_f): the scale against which the inverse's matrix-vector product
+    is compared on ill-conditioned point sets (reading c16)."""
+    g, y = _c128(g), _f64(y)
+    if y.size != N:
+        raise ValueError("the Lagrange form needs M == N")
+    ia, n = _idx(idx, N)
+    lamC, _ = logsin_C(y, N, ia)
+    if lamD is None:
+        lamD = logsin_D(y)
+    lD = _f64(lamD[0])
+    a = np.empty(n, np.float64)
+    _load().orc_inverse_absf(_ptr(g), _ptr(y), y.size, N, _ptr(lamC), _ptr(lD),
+                             _ptr(ia) if ia is not None else None, n, _ptr(a))
+    return a
 
 
 def inufft(g, y, N: int) -> np.ndarray:

@@ -27,6 +27,13 @@
  *   orc_kernel_adj   pinned: agreement with orc_nudft_adj
  *   orc_logsin_*     pinned: equispaced product identity
  *   orc_inverse_f    pinned: round trip and dense solve at N <= 256
+ *   orc_kernel_fwd_plain  the paper's "straightforward method" of Sec. 3.1
+ *                    (Eq. p4 in plain binary64, no compensation), the
+ *                    measuring stick of the threshold error eps_th(N);
+ *                    pinned: agrees with orc_kernel_fwd within the rounding
+ *                    bound of its uncompensated differences
+ *   orc_inverse_absf pinned: equals sum_j |L_kj| |g_j| of the dense Lagrange
+ *                    matrix at N <= 64 (inverse of the dense A, numpy)
  *   orc_fft          pinned: direct DFT and numpy.fft
  */
 #include <math.h>
@@ -163,6 +170,42 @@ void orc_kernel_fwd(const double *f, int64_t N, const double *y, int64_t M,
     }
     g[2 * i] = nval(&sr);
     g[2 * i + 1] = nval(&si);
+  }
+}
+
+/* The paper's "straightforward method" (Sec. 3.1): g_j = sum_k K_jk f_k with
+ * the matrix entry of Eq. p4 evaluated literally in binary64,
+ *   K_jk = ((e^{i N y_j} - 1) / N) / (e^{i (y_j - x_k)} - 1),
+ * x_k = k fl(2 pi / N), the difference y_j - x_k, both exponentials (libm
+ * cos / sin), the complex quotient and the sum all in plain binary64, no
+ * compensation.  Its error for f = 1 is what the paper calls the machine
+ * precision threshold eps_th(N).  A point that hits a grid point exactly
+ * (t == 0) takes K = 1 (reading c7). */
+void orc_kernel_fwd_plain(const double *f, int64_t N, const double *y, int64_t M,
+                          const int64_t *idx, int64_t nidx, double *g) {
+  (void)M;
+  const double h = TWO_PI_HI / (double)N;
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int64_t i = 0; i < nidx; ++i) {
+    double yj = y[IDX(i)];
+    double a = (double)N * yj;
+    double nr = (cos(a) - 1.0) / (double)N, ni = sin(a) / (double)N;
+    double sr = 0.0, si = 0.0;
+    for (int64_t k = 0; k < N; ++k) {
+      double t = yj - (double)k * h;
+      double Kr, Ki;
+      if (t == 0.0) { Kr = 1.0; Ki = 0.0; }
+      else {
+        double dr = cos(t) - 1.0, di = sin(t);
+        double den = dr * dr + di * di;
+        Kr = (nr * dr + ni * di) / den;
+        Ki = (ni * dr - nr * di) / den;
+      }
+      sr += Kr * f[2 * k] - Ki * f[2 * k + 1];
+      si += Kr * f[2 * k + 1] + Ki * f[2 * k];
+    }
+    g[2 * i] = sr;
+    g[2 * i + 1] = si;
   }
 }
 
@@ -367,4 +410,29 @@ int orc_num_threads(void) {
 #else
   return 1;
 #endif
+}
+
+/* Normaliser of the square inverse's matrix-vector product (reading c16):
+ *   a_k = sum_j |C_k G(x_k - y_j) D_j| |g_j|,
+ * the same terms as orc_inverse_f with every factor replaced by its
+ * modulus, |i e^{-i N y_j / 2}| = 1.  An exact hit y_j = x_k gives |g_j|. */
+void orc_inverse_absf(const double *g, const double *y, int64_t M, int64_t N,
+                      const double *lamC, const double *lamD, const int64_t *idx,
+                      int64_t nidx, double *a) {
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int64_t i = 0; i < nidx; ++i) {
+    int64_t k = IDX(i);
+    int64_t hitj = -1;
+    for (int64_t j = 0; j < M; ++j)
+      if (diff_y_xk(y[j], k, N) == 0.0) { hitj = j; break; }
+    if (hitj >= 0) { a[i] = hypot(g[2 * hitj], g[2 * hitj + 1]); continue; }
+    nsum s = {0, 0};
+    for (int64_t j = 0; j < M; ++j) {
+      double t = -diff_y_xk(y[j], k, N);
+      double Gr, Gi;
+      G_of_t(t, &Gr, &Gi);
+      nadd(&s, exp(lamC[i] + lamD[j]) * hypot(Gr, Gi) * hypot(g[2 * j], g[2 * j + 1]));
+    }
+    a[i] = nval(&s);
+  }
 }

@@ -189,6 +189,51 @@ def test_fft_matches_dft_and_numpy(orc):
         assert orc.rel_l2(orc.dft(x, -1), np.fft.fft(x)) < 1e-14
 
 
+# ------------------------------------------------------------- threshold error (Sec. 3.1)
+
+def test_straightforward_method_close_to_compensated_at_small_n(orc):
+    """The plain-binary64 Eq. p4 product (the paper's straightforward method)
+    equals the compensated oracle to within its own rounding: each term's
+    uncompensated difference y - k fl(2 pi/N) is off by at most ~2 ulp(2 pi),
+    which moves K_jk by at most that times |dK/dt| ~ 1/(N t^2) -- small for
+    points away from the grid, as here."""
+    N, M = 64, 200
+    y = workloads.rng(3).uniform(0, 2 * math.pi, M)
+    x = 2 * math.pi * np.arange(N) / N
+    dist = np.abs(np.angle(np.exp(1j * (y[:, None] - x[None, :])))).min(1)
+    y = y[dist > 1e-3]
+    f = workloads.coeffs(N, seed=4)
+    gp = orc.kernel_fwd_plain(f, y)
+    gc = orc.kernel_fwd(f, y)
+    bound = 4 * 2.0 ** -52 * 2 * math.pi / (N * dist[dist > 1e-3] ** 2) * np.abs(f).sum() + 1e-13
+    assert np.all(np.abs(gp - gc) <= bound)
+    # the f = 1 sum reproduces 1 up to the same rounding
+    g1 = orc.kernel_fwd_plain(np.ones(N, complex), y)
+    assert np.abs(g1 - 1).max() < 1e-11
+
+
+def test_threshold_error_grows_with_n(orc):
+    """The paper's threshold phenomenon (Sec. 3.1): the straightforward
+    method's error for f = 1 grows with N, while the compensated oracle stays
+    at the rounding level; and the committed table (written by
+    oracle/eps_threshold.py) reproduces for the small sizes, within a factor
+    2 (its maxima depend on single roundings of libm)."""
+    rows = [list(map(float, r)) for r in _golden_lines("eps_threshold_straightforward.txt")]
+    table = {int(r[0]): r for r in rows}
+    assert table[1 << 20][2] > 100 * table[1 << 8][2]
+    assert all(r[6] <= 32 and r[7] <= 24 for r in rows)           # p_th, q_th bounded
+    assert table[1 << 20][7] < table[1 << 8][7]                     # q_th decays
+    from oracle import eps_threshold
+    for L in (6, 9, 12):
+        N, nt, e1, er = eps_threshold.measure(L, 1024)
+        assert 0.5 * table[N][2] <= e1 <= 2.0 * table[N][2]
+        g = orc.kernel_fwd(np.ones(N, complex), workloads.points("uniform", N, seed=500 + L),
+                           workloads.sample_index(N, 1024, seed=L))
+        assert np.abs(g - 1).max() < 1e-13
+        if L >= 9:
+            assert e1 > 1e-11
+
+
 # ------------------------------------------------------------- inverse
 
 @pytest.mark.parametrize("N", [16, 256])
@@ -219,6 +264,28 @@ def test_inverse_round_trip_and_dense_solve(orc, N, jit):
     tol = 1e-12 if jit <= 0.1 else 1e-10
     assert orc.rel_l2(c2, c) < tol
     assert orc.rel_l2(c2, cs) < tol
+
+
+@pytest.mark.parametrize("N,kind", [(128, "jitter"), (16, "clustered")])
+def test_inverse_modulus_sum_is_dense_lagrange_matrix(orc, N, kind):
+    """sum_j |L_kj| |g_j| of the Lagrange form equals |B A^-1| |g| for the
+    dense matrices A_jn = e^(i n y_j), B_kn = e^(i n x_k) built by numpy (L
+    maps the samples to the grid values of their band-limited interpolant),
+    and the signed sum is (B A^-1) g.  The clustered case is small (cond(A)
+    ~ 7e5) so that numpy's dense inverse is itself accurate to ~1e-10."""
+    y = workloads.points(kind, N, N if kind == "jitter" else None, seed=N, jitter=0.4)
+    y = np.sort(y)
+    g = workloads.samples(N, seed=3)
+    n = np.arange(N)
+    A = np.exp(1j * np.outer(y, n))
+    Bm = np.exp(1j * np.outer(2 * np.pi * n / N, n))
+    L = Bm @ np.linalg.inv(A)
+    a_ref = np.abs(L) @ np.abs(g)
+    a = orc.inverse_absf(g, y, N)
+    tol = 1e-13 if kind == "jitter" else 1e-9
+    assert np.abs(a - a_ref).max() <= tol * a_ref.max()
+    f = orc.inverse_f(g, y, N)
+    assert np.abs(f - L @ g).max() <= tol * a_ref.max()
 
 
 def test_inverse_exact_hit(orc):
