@@ -43,9 +43,9 @@ EPS_FP64 = 1e-12
 JITTER = 0.4
 METRIC = "NUFFT points/s (forward + square inverse, N=M=2^20, mixed eps=1e-6)"
 # DRAM bytes (read + write) of the target-evaluation kernels per step (one
-# k_targets_fwd + one k_targets_grid2 launch), from the ncu capture summarised
-# in profiles/targets_fft_N2p20_mixed.md; reported only while the kernels'
-# source text still hashes to `sha1` (a changed kernel reports null)
+# k_targets_fwd + one k_targets_grid2 launch) from one ncu capture of this
+# workload; reported only while the kernels' source text still hashes to
+# `sha1` (a changed kernel reports null until it is captured again)
 TARGETS_TRAFFIC = {"bytes_per_step": 79026944, "sha1": "c5a3ea2716aab91aba53280fb108349e118a4d30"}
 STAGE_KERNELS = {"targets": "k_targets_fwd + k_targets_grid2", "fft": "k_fft_st",
                  "m2l": "k_down_fused (tensor-core levels: k_down_top + k_down_sub + k_m2l_tc)",
@@ -182,10 +182,18 @@ def stage_roofline(stages_ms: dict, N: int, M: int, info: dict, io_bytes: int, f
             out[st] = {"ms": ms, "bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
                        "frac": ach / pk}
             if st == "targets":
-                # the pair loop's binding unit is the reciprocal (SFU) pipe
-                pk_sfu = sfu_pair_peak_tflops(peaks)
-                out[st].update({"peak": pk_sfu, "frac": ach / pk_sfu, "peak_fp32_fma": pk,
-                                "frac_fp32_fma": ach / pk})
+                # the pair loop's binding unit is the reciprocal (special-function)
+                # pipe: pairs per second against its rate; beside it the FP32 FMA
+                # pipe with 6 flops per pair (one division + 5) plus 4p per target
+                L, p = info["lmax"], info["p"]
+                pairs = near_pairs(N, M, L, fwd, bwd)
+                tps = pairs / (ms / 1e3) / 1e12
+                pk_pair = pair_peak_tps(peaks)
+                fl6 = 6 * pairs + 4 * p * (M * fwd + N * bwd)
+                out[st] = {"ms": ms, "bound": "alu", "achieved": tps, "peak": pk_pair,
+                           "unit": "T pairs/s (one FP32 reciprocal each)", "frac": tps / pk_pair,
+                           "pairs": pairs, "achieved_fp32_tflops": fl6 / (ms / 1e3) / 1e12,
+                           "peak_fp32_fma": pk, "frac_fp32_fma": fl6 / (ms / 1e3) / 1e12 / pk}
         else:
             out[st] = {"ms": ms, "bound": None}
     return out
@@ -193,25 +201,46 @@ def stage_roofline(stages_ms: dict, N: int, M: int, info: dict, io_bytes: int, f
 
 def targets_source_sha1() -> str:
     """SHA-1 of the near-field / target-kernel section of k_fmm.cu (the
-    device code from the reciprocal helper to the first host function)."""
+    device code from the pair reciprocal to the first host function) and of
+    the pair reciprocal itself (common.cuh)."""
     import hashlib
-    path = os.path.join(ROOT, "paper_1611_09379_gb300", "csrc", "k_fmm.cu")
-    src = open(path).read()
-    a = src.index("// 1/t: FP32 reciprocal")
+    csrc = os.path.join(ROOT, "paper_1611_09379_gb300", "csrc")
+    src = open(os.path.join(csrc, "k_fmm.cu")).read()
+    a = src.index("// 1/t of a near-field pair")
     e = src.index("static inline unsigned nblk")
-    return hashlib.sha1(src[a:e].encode()).hexdigest()
+    com = open(os.path.join(csrc, "common.cuh")).read()
+    ra = com.index("// 1/t of a near-field pair")
+    re_ = com.index("// Leaf index and offset of a point")
+    return hashlib.sha1((src[a:e] + com[ra:re_]).encode()).hexdigest()
+
+
+# FP32 reciprocals and FMAs per SM per clock: measured at start-up by the
+# library's probe (nufft_diag_pipe_rates); the CUDA C++ Programming Guide's
+# arithmetic-throughput table gives 16 and 128 for this architecture.
+PIPES = {"rcp_per_clk": 16.0, "ffma_per_clk": 128.0, "source": "CUDA C++ Programming Guide table"}
+N_SM = 152
 
 
 def fp32_peak_tflops(peaks):
-    # 152 SMs x 128 FP32 lanes x 2 flops (FMA) x max SM clock
-    return 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    # SMs x measured FP32 FMAs per clock x 2 flops x max SM clock
+    return N_SM * PIPES["ffma_per_clk"] * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
 
 
-def sfu_pair_peak_tflops(peaks):
-    # each near-field pair needs one FP32 reciprocal on the special-function
-    # unit, 16 per clock per SM (an eighth of the FP32 FMA lanes): 152 SMs x
-    # 16 pairs x 4 algorithmic flops per pair x max clock
-    return 152 * 16 * 4 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+def pair_peak_tps(peaks):
+    # near-field pairs per second (1e12) if every SM's special-function unit
+    # finishes one FP32 reciprocal per pair at its measured rate, max clock
+    return N_SM * PIPES["rcp_per_clk"] * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+
+
+def near_pairs(N: int, M: int, lmax: int, fwd: int, bwd: int) -> int:
+    """Near-field pairs of one step: every target meets the 3s grid points
+    (forward) or the sources (adjoint / inverse) of its leaf and the two
+    neighbouring leaves, less the one pair per point handled in closed form
+    (its nearest grid point): (3s - 1) M per forward, and, summed over the grid
+    targets, 3 s M - M per adjoint / inverse (each leaf's sources are seen by
+    the 3s grid points around them)."""
+    s = N >> lmax
+    return (3 * s - 1) * M * (fwd + bwd)
 
 
 # ---------------------------------------------------------------- replicas
@@ -249,6 +278,13 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
+    # the pipe rates behind the targets' roofline, measured on this GPU
+    try:
+        rcp, ffma = nf.pipe_rates()
+        PIPES.update({"rcp_per_clk": rcp, "ffma_per_clk": ffma,
+                      "source": "measured (nufft_diag_pipe_rates: per-SM clock counters, median SM)"})
+    except Exception as e:  # keep the table's counts, say so
+        PIPES["source"] += f" (probe failed: {e!r})"
 
     N = M = 1 << N_LOG2
     y = workloads.points("jitter", M, N, seed=1234, jitter=JITTER)
@@ -259,7 +295,8 @@ def run_ours(args):
 
     results = {}
     tuning = {}
-    for tag, prec, eps in (("mixed", nf.MIXED, EPS_MIXED), ("fp64", nf.FP64, EPS_FP64)):
+    for tag, prec, eps in (("mixed", nf.MIXED, EPS_MIXED), ("fp64", nf.FP64, EPS_FP64),
+                           ("fp64_eps1e-6", nf.FP64, EPS_MIXED)):
         prm = {}
         if not args.no_tune:
             # empirical l_max, p, q, tc_level for this point set (outside the timing,
@@ -353,6 +390,8 @@ def run_ours(args):
     value = replica_throughput(2 * M, ms_step, ws)
     fp = results["fp64"]
     ms_fp64 = ranks_max(sum(fp["ms"]) / len(fp["ms"]), ws, dev)
+    fp6 = results["fp64_eps1e-6"]
+    ms_fp64_6 = ranks_max(sum(fp6["ms"]) / len(fp6["ms"]), ws, dev)
     e2e_ms = ranks_max(sum(mx["e2e_ms"]) / len(mx["e2e_ms"]), ws, dev)
 
     if rank != 0:
@@ -366,7 +405,7 @@ def run_ours(args):
         import oracle
         idx = workloads.sample_index(M, 1024)
         gref = oracle.nudft_fwd(c, y, idx)
-        for tag in ("mixed", "fp64"):
+        for tag in ("mixed", "fp64", "fp64_eps1e-6"):
             gh = results[tag]["g"].cpu().numpy()
             c2h = results[tag]["c2"].cpu().numpy()
             acc[tag] = {"fwd_rel_l2_sampled": oracle.rel_l2(gh[idx], gref),
@@ -389,17 +428,22 @@ def run_ours(args):
     if dom == "targets" and TARGETS_TRAFFIC["bytes_per_step"] and \
             TARGETS_TRAFFIC["sha1"] == targets_source_sha1():
         roof["traffic"] = TARGETS_TRAFFIC["bytes_per_step"]
-        roof["traffic_unit"] = "DRAM bytes per step (ncu, profiles/targets_fft_N2p20_mixed.md)"
+        roof["traffic_unit"] = "DRAM bytes per step (ncu dram__bytes_read + write, both target kernels)"
     roof["kernel_stage"] = dom
     roof["kernels"] = STAGE_KERNELS.get(dom)
     if roof["bound"] == "hbm":
         roof["peak_source"] = f"{peak_src}: MEASURED_PEAKS hbm_gbs"
     elif dom == "targets":
-        roof["peak_source"] = (f"{peak_src}: 152 SM x 16 FP32 reciprocals/clk (one per near pair, "
-                               "4 algorithmic flops per pair) x sm_max_mhz")
+        roof["peak_source"] = (f"{N_SM} SM x {PIPES['rcp_per_clk']:.2f} FP32 reciprocals/clk "
+                               f"({PIPES['source']}) x sm_max_mhz {peaks.get('sm_max_mhz')} "
+                               f"({peak_src}); one reciprocal per near-field pair")
+        roof["pairs_per_step"] = r["pairs"]
         roof["frac_fp32_fma"] = r["frac_fp32_fma"]
+        roof["fp32_fma_peak_tflops"] = r["peak_fp32_fma"]
+        roof["fp32_fma_count"] = "6 flops per near pair + 4p per target (far field)"
     else:
-        roof["peak_source"] = f"{peak_src}: 152 SM x 128 FP32 lanes x 2 x sm_max_mhz"
+        roof["peak_source"] = (f"{peak_src}: {N_SM} SM x {PIPES['ffma_per_clk']:.1f} FP32 FMA/clk "
+                               f"x 2 x sm_max_mhz")
 
     # cpu baseline: the oracle (direct forward definition) on sampled targets
     cpu = None
@@ -429,10 +473,18 @@ def run_ours(args):
                    "plan_s": mx["t_plan_s"]},
         "stages_ms_per_step": {k: round(v, 5) for k, v in per.items()},
         "stage_roofline": sroof,
+        "points_per_step": 2 * M,
+        "value_per_transform": value / 2,
         "fp64": {"eps": EPS_FP64, "ms_per_step": ms_fp64, "value": replica_throughput(2 * M, ms_fp64, ws),
                  "params": fp["info"], "stages_ms_per_step":
                      {k: round(v[0] / steps, 5) for k, v in fp["stats"].items()},
                  "plan_s": fp["t_plan_s"]},
+        "fp64_eps1e-6": {"eps": EPS_MIXED, "ms_per_step": ms_fp64_6,
+                         "value": replica_throughput(2 * M, ms_fp64_6, ws), "params": fp6["info"],
+                         "stages_ms_per_step":
+                             {k: round(v[0] / steps, 5) for k, v in fp6["stats"].items()},
+                         "mixed_speedup_same_eps": ms_fp64_6 / ms_step},
+        "pipes": dict(PIPES),
         "accuracy": acc,
         "tuning": tuning or None,
         "roofline": roof,
@@ -446,8 +498,8 @@ def run_ours(args):
         out["batched"] = run_batched(tune_params=not args.no_tune)
     if not args.no_large:
         out["large"] = run_large(tune_params=not args.no_tune)
-    if args.lsq:
-        out["inufft_lsq"] = run_lsq()
+    if not args.no_lsq:
+        out["inufft_lsq"] = run_lsq(budget_s=args.lsq_seconds, full=args.lsq_full)
     print(json.dumps(out))
     if ws > 1:
         dist.destroy_process_group()
@@ -586,10 +638,23 @@ def run_large(steps: int = 5, warmup: int = 3, tune_params: bool = True):
             "accuracy": acc}
 
 
-def run_lsq(maxit: int = 60000):
-    """Least-squares INUFFT (N = 2^16, M = 2^18, 1:100 contrast, complex128):
-    CG to a 1e-8 residual with plain weights and with the shipped learned
-    density compensation; plan and weights outside the timed solve."""
+def _first_below(hist, every, iters, level):
+    for i, v in enumerate(hist):
+        if v <= level:
+            return min((i + 1) * every, iters)
+    return None
+
+
+def run_lsq(budget_s: float = 50.0, full: bool = False, check_every: int = 32):
+    """Least-squares INUFFT (N = 2^16, M = 2^18, 1:100 contrast, complex128,
+    consistent samples of a random band-limited c_true): CG with the shipped
+    learned density compensation and plain CG, both stopped on the same test
+    (the unweighted normal-equation residual, recomputed from the iterate,
+    <= 1e-8).  Plan and weights outside the timed solves.  Within `budget_s`
+    both solves get the same iteration cap (from a timed probe solve); each
+    reports its time, iterations, final residual and the iterations at which
+    the residual first fell below 1e-2, 1e-4, 1e-6, 1e-8.  full=True runs both
+    to 1e-8 (about two minutes)."""
     import torch
 
     import paper_1611_09379_gb300 as nf
@@ -605,15 +670,93 @@ def run_lsq(maxit: int = 60000):
     w = dcf.weights(plan, mlp)
     torch.cuda.synchronize()
     t_w = time.perf_counter() - t0
-    out = {"workload": "least-squares INUFFT N=2^16 M=2^18 1:100 density contrast",
-           "tol": 1e-8, "plan": plan.info(), "weights_s": t_w}
+    # iteration time from a short solve, then the common cap
+    probe = 64
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plan.solve_lsq(g, None, tol=1e-30, maxit=probe, check=False, check_every=check_every)
+    torch.cuda.synchronize()
+    t_it = (time.perf_counter() - t0) / probe
+    maxit = 60000 if full else max(256, int(budget_s / 2 / t_it))
+    out = {"workload": "least-squares INUFFT N=2^16 M=2^18 1:100 density contrast, complex128, FP64 FMM "
+                       "eps=1e-10", "tol": 1e-8, "stopping_test": "||A^H (g - A c)|| / ||A^H g|| "
+                       "recomputed from c every %d iterations (same for both)" % check_every,
+           "plan": plan.info(), "weights_s": t_w, "ms_per_iteration_probe": 1e3 * t_it,
+           "iteration_cap": maxit}
     for name, ww in (("learned", w), ("plain", None)):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        c, it, res = plan.solve_lsq(g, ww, tol=1e-8, maxit=maxit, check=False)
+        c, it, res = plan.solve_lsq(g, ww, tol=1e-8, maxit=maxit, check=False, check_every=check_every)
         torch.cuda.synchronize()
-        out[name] = {"iterations": it, "residual": res, "solve_s": time.perf_counter() - t0}
+        dt = time.perf_counter() - t0
+        info = plan.lsq_info
+        hist = info["history"]
+        err = float(torch.linalg.vector_norm(c - torch.from_numpy(c_true).cuda()) /
+                    torch.linalg.vector_norm(torch.from_numpy(c_true).cuda()))
+        out[name] = {"iterations": it, "converged": res <= 1e-8, "residual": res,
+                     "residual_weighted": info["resid_w"], "data_residual": info["data_resid"],
+                     "solve_s": dt, "ms_per_iteration": 1e3 * dt / max(it, 1),
+                     "iterations_to": {f"{lv:.0e}": _first_below(hist, info["check_every"], it, lv)
+                                       for lv in (1e-2, 1e-4, 1e-6, 1e-8)},
+                     "coef_rel_err_vs_c_true": err}
+    L, P = out["learned"], out["plain"]
+    out["learned_over_plain"] = {
+        "iterations_to_1e-6": (L["iterations_to"]["1e-06"] / P["iterations_to"]["1e-06"]
+                               if L["iterations_to"]["1e-06"] and P["iterations_to"]["1e-06"] else None),
+        "residual_at_cap": L["residual"] / P["residual"] if P["residual"] > 0 else None,
+        "solve_s": L["solve_s"] / P["solve_s"]}
     plan.close()
+    return out
+
+
+def run_eps_scan(logs=(8, 10, 12, 14, 16, 18, 20, 22),
+                 epss=(1e-4, 1e-6, 1e-8, 1e-10, 1e-12, 1e-13, 1e-14, 1e-15, 0.0)):
+    """Accuracy floor of the FP64 path (Sec. 3.1's threshold error eps_th(N)
+    for this implementation): for N = M = 2^L, uniform points, and each
+    prescribed eps (0 = the library's machine-precision mode), the paper's
+    analytic test (f = 1, eps_a = max_j |g_j - 1| over all M points), the
+    relative L2 error of a random band-limited signal against the oracle on
+    256 sampled targets, the forward time, and the parameters Eq. 18.2 gave."""
+    import torch
+
+    import oracle
+    import paper_1611_09379_gb300 as nf
+    stream = torch.cuda.current_stream()
+    out = {}
+    for L in logs:
+        N = M = 1 << L
+        y = workloads.points("uniform", M, seed=500 + L)
+        yd = torch.from_numpy(y).cuda()
+        e0 = torch.zeros(N, dtype=torch.complex128, device="cuda")
+        e0[0] = 1.0
+        c = workloads.coeffs(N, seed=L)
+        cd = torch.from_numpy(c).cuda()
+        idx = workloads.sample_index(M, 256, seed=L)
+        gref = oracle.nudft_fwd(c, y, idx)
+        row = {}
+        for eps in epss:
+            try:
+                plan = nf.Plan(N, yd, eps=eps, prec=nf.FP64)
+            except nf.NufftError as e:
+                row[repr(eps)] = {"error": str(e)}
+                continue
+            g1 = plan.forward(e0)
+            ea = float((g1 - 1.0).abs().max())
+            g = plan.forward(cd)
+            torch.cuda.synchronize()
+            err = oracle.rel_l2(g.cpu().numpy()[idx], gref)
+            ms = []
+            for _ in range(5):
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                plan.forward(cd, out=g)
+                b.record(stream)
+                torch.cuda.synchronize()
+                ms.append(a.elapsed_time(b))
+            row[repr(eps)] = {"eps_a_f1": ea, "rel_l2": err, "ms": sorted(ms)[2], **plan.params()}
+            plan.close()
+        out[N] = row
     return out
 
 
@@ -679,18 +822,27 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--lsq", action="store_true",
-                    help="also run the least-squares INUFFT, learned vs plain CG (~2.5 min)")
+    ap.add_argument("--no-lsq", action="store_true",
+                    help="skip the least-squares INUFFT, learned vs plain CG")
+    ap.add_argument("--lsq-seconds", type=float, default=50.0,
+                    help="time budget of the two least-squares solves (same iteration cap)")
+    ap.add_argument("--lsq-full", action="store_true",
+                    help="run both least-squares solves to the 1e-8 residual (~2 min)")
     ap.add_argument("--lsq-only", action="store_true", help="only the least-squares comparison")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched workloads")
     ap.add_argument("--no-tune", action="store_true",
                     help="use the formula parameters (Eq. 18.2, 25) instead of the autotuner's")
     ap.add_argument("--no-large", action="store_true", help="skip the 2^24 forward + adjoint")
+    ap.add_argument("--eps-scan", action="store_true",
+                    help="only the FP64 accuracy-floor scan over N and eps (Sec. 3.1)")
     ap.add_argument("--batched-only", action="store_true",
                     help="only the batched workloads (steps / warmup as given)")
     args = ap.parse_args()
+    if args.eps_scan:
+        print(json.dumps({"eps_scan": run_eps_scan()}))
+        return
     if args.lsq_only:
-        print(json.dumps({"inufft_lsq": run_lsq()}))
+        print(json.dumps({"inufft_lsq": run_lsq(args.lsq_seconds, args.lsq_full)}))
         return
     if args.warmup < 3:
         args.warmup = 3

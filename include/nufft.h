@@ -22,7 +22,15 @@
  *     (2 x double) unless the plan was created with NUFFT_IO_C64, then
  *     complex64 (2 x float).
  *   - Frequencies are one-sided, n = 0..N-1 (Eq. p1).
- *   - N must be a power of two, 8 <= N <= 2^26; 1 <= M <= 2^27.
+ *   - N (the number of coefficients) is any integer 8 <= N <= 2^26;
+ *     1 <= M <= 2^27.  The FMM and its FFT run on the grid of
+ *     N' = 2^ceil(log2 N) points: the series of Eq. p1 with N terms is the
+ *     series with N' terms whose top N' - N coefficients are zero, so the
+ *     forward, adjoint and least-squares results are the same sums (inputs
+ *     are zero padded and outputs truncated inside the FFT passes).  The
+ *     square inverse (Eq. p6 / p8 on the grid of its own N points) needs N a
+ *     power of two; other N give NUFFT_ENOTSUP there.  Grid quantities of a
+ *     plan (leaves, k0, delta, C_k) are on the N' grid.
  *   - y_j must be finite and in [0, 2 pi) (binary64 2 pi excluded).
  *   - All work is enqueued on the plan's CUDA stream and is asynchronous;
  *     a return of NUFFT_OK means the work was enqueued without error.
@@ -106,7 +114,8 @@ const char *nufft_strerror(int status);
 /* Library version as 10000*major + 100*minor + patch. */
 int nufft_version(void);
 
-/* Parameter choice of a plan without creating it (no GPU needed).
+/* Parameter choice of a plan without creating it (no GPU needed); the tree
+ * depth refers to the grid N' = 2^ceil(log2 N).
  * in/out: *params (fields <= 0 are filled in).  Returns NUFFT_EINVAL for an
  * invalid N, M, eps or prec.  eps must lie in [1e-15, 1e-1]. */
 int nufft_choose_params(int64_t N, int64_t M, double eps, int prec,
@@ -165,7 +174,8 @@ int nufft_autotune(int64_t N, int64_t M, const double *y, double eps, int prec,
  * structure", Sec. 3.3), precompute F_j (Eq. p5) and, with
  * NUFFT_WANT_INVERSE, the log-sums behind C_k and D_j (Eq. p8).
  *   out     [host]   receives the plan
- *   N, M             grid size (power of two) and number of points
+ *   N, M             number of coefficients (the grid is N' = 2^ceil(log2 N)) and
+ *                    number of points
  *   y       [device] M binary64 points in [0, 2 pi); read during the call only
  *   eps              requested accuracy in [1e-15, 1e-1]
  *   prec             nufft_prec
@@ -178,7 +188,8 @@ int nufft_autotune(int64_t N, int64_t M, const double *y, double eps, int prec,
  *   stream           cudaStream_t to run on (NULL = legacy default stream)
  * Synchronises the stream (it reads back validation flags).  Errors:
  * EINVAL (bad sizes / eps / y), EILLCOND (inverse requested with duplicate
- * points or coefficients outside the exponent range), ENOMEM, ECUDA. */
+ * points or coefficients outside the exponent range), ENOTSUP (inverse
+ * requested for N not a power of two), ENOMEM, ECUDA. */
 int nufft_plan_create(nufft_plan *out, int64_t N, int64_t M, const double *y,
                       double eps, int prec, const nufft_params *params,
                       unsigned flags, void *stream);
@@ -202,8 +213,8 @@ int nufft_plan_sync(nufft_plan plan);
  * into caller buffers, for inspection and tests.  Any pointer may be NULL.
  *   perm       [device] int32[M]   original index of the i-th sorted point
  *   leaf_start [device] int32[B+1] first sorted index of each leaf, B = 2^lmax
- *   k0         [device] int32[M]   nearest grid index round(y N / 2 pi) mod N
- *   delta      [device] double[M]  y N / (2 pi) - round(y N / 2 pi)
+ *   k0         [device] int32[M]   nearest grid index round(y N' / 2 pi) mod N'
+ *   delta      [device] double[M]  y N' / (2 pi) - round(y N' / 2 pi)
  * Asynchronous on the plan's stream. */
 int nufft_plan_points(nufft_plan plan, int32_t *perm, int32_t *leaf_start,
                       int32_t *k0, double *delta);
@@ -242,22 +253,57 @@ int nufft_plan_exec_inv(nufft_plan plan, const void *g, void *c);
 
 /* Least-squares INUFFT for M > N (problem (ii) of Sec. 2 with more samples
  * than coefficients; the paper states the problem, the CG solver is this
- * library's): c = argmin sum_j w_j |sum_n c_n e^{i n y_j} - g_j|^2, by
- * conjugate gradients on A^H W A c = A^H W g, A_jn = e^{i n y_j}, each
+ * library's): c = argmin sum_j |sum_n c_n e^{i n y_j} - g_j|^2 by conjugate
+ * gradients on the normal equations A^H A c = A^H g, A_jn = e^{i n y_j}, each
  * product being one forward and one adjoint FMM of the plan.
+ * Weights w (density compensation, e.g. nufft_plan_dcf_weights):
+ *   mode 0 (default): w preconditions the same equations (the solution does
+ *     not change).  A^H A acts on coefficients like a product with the
+ *     sample density in x (its Toeplitz symbol), so P = F diag(wt) F^H with
+ *     wt_k the weights carried to the grid points (mean of w_j over the
+ *     points whose nearest grid point is k; empty grid points take the
+ *     nearest occupied one's) is close to its inverse; CG runs on P A^H A.
+ *   NUFFT_LSQ_WEIGHTED: CG on the weighted equations A^H W A c = A^H W g
+ *     instead (the minimiser of sum_j w_j |(A c)_j - g_j|^2, which is the
+ *     same c only for consistent data).
+ * Stopping test, the same in every mode: the residual of the UNWEIGHTED
+ * normal equations, ||A^H (g - A c)|| / ||A^H g|| <= tol, recomputed from
+ * the iterate c (one forward and one adjoint FMM) every `check_every`
+ * iterations (0 = 16) and after the last one.
  *   g      [device] M samples (complex128, original point order)
- *   w      [device] float[M] positive weights (original order), NULL = 1
- *   tol    stop when ||A^H W (g - A c)|| / ||A^H W g|| <= tol (CG residual)
+ *   w      [device] float[M] positive weights (original order), NULL = plain CG
+ *   mode   0 or NUFFT_LSQ_WEIGHTED
+ *   tol    tolerance of the stopping test above
  *   maxit  iteration cap
  *   c      [device] N coefficients out (complex128)
- *   iters, resid [host] iterations used and final relative residual (may be NULL)
+ *   info   [host, optional] what the solve did:
+ *            iters       CG iterations run
+ *            checks      evaluations of the stopping test
+ *            resid       the stopping test's value at the end
+ *            resid_w     the residual of the system CG iterates on, from
+ *                        its recurrence, relative to its right-hand side,
+ *                        at the last test (unweighted equations in mode 0)
+ *            data_resid  ||g - A c|| / ||g||, recomputed at the last test
+ *            hist, hist_cap  (read on entry) optional host array of hist_cap
+ *                        doubles: hist[i] receives the stopping test's value
+ *                        at the i-th test (i < hist_cap)
  * Needs a complex128 plan with batch 1; use NUFFT_FP64 for tolerances below
- * ~1e-6.  Work
- * vectors (4N + M complex) are allocated by the plan on first use.  Reads the
- * residual every few iterations (synchronises).  Returns NUFFT_ENOTCONV when
- * maxit is reached first (c then holds the last iterate). */
-int nufft_plan_solve_lsq(nufft_plan plan, const void *g, const float *w, double tol,
-                         int maxit, void *c, int *iters, double *resid);
+ * ~1e-6.  Work vectors (6N + M complex and a few real arrays) are allocated
+ * by the plan on first use.  Synchronises at every test.  Returns
+ * NUFFT_ENOTCONV when maxit is reached first (c then holds the last
+ * iterate); g with A^H g = 0 gives c = 0 and NUFFT_OK. */
+#define NUFFT_LSQ_WEIGHTED 0x1u
+typedef struct {
+  int iters;
+  int checks;
+  double resid;
+  double resid_w;
+  double data_resid;
+  double *hist;
+  int hist_cap;
+} nufft_lsq_info;
+int nufft_plan_solve_lsq(nufft_plan plan, const void *g, const float *w, unsigned mode,
+                         double tol, int maxit, int check_every, void *c, nufft_lsq_info *info);
 
 /* ---------------------------------------------------------------- learned weights */
 
@@ -304,6 +350,13 @@ int nufft_mlp_grad(nufft_mlp mlp, const float *feat, const float *target, int64_
 /* one Adam step (lr) on that loss; loss [host] optional (synchronises) */
 int nufft_mlp_train_step(nufft_mlp mlp, const float *feat, const float *target, int64_t n,
                          float lr, float *loss, void *stream);
+
+/* Learned weights of a plan's points for nufft_plan_solve_lsq: the features
+ * of nufft_plan_dcf_features through the network's BF16 inference, scaled to
+ * mean 1 on the device (the weights are scale free).  w [device] float[M],
+ * original point order.  Asynchronous on the plan's stream except for the
+ * feature step, which synchronises it. */
+int nufft_plan_dcf_weights(nufft_plan plan, nufft_mlp mlp, float *w);
 
 /* ---------------------------------------------------------------- profiling */
 
@@ -354,7 +407,13 @@ int nufft_multi_destroy(nufft_multi multi);
 
 /* Plan + exec + destroy in one call, with the paper's argument order
  * (nufft_fwd(c_n, N, y_j, M, eps) -> g_j).  All data pointers [device].
- * Synchronises the stream. */
+ * Synchronises the stream.
+ * inufft (problem (ii) of Sec. 2): M == N uses the square Lagrange form of
+ * Eq. p6 / p8 (as nufft_plan_exec_inv); M > N returns the least-squares
+ * solution by plain CG (nufft_plan_solve_lsq with unit weights, tolerance
+ * max(eps, 1e-14) on the unweighted normal-equation residual, at most 100000
+ * iterations, NUFFT_ENOTCONV if it is not reached; complex128 only, else
+ * NUFFT_ENOTSUP); M < N is underdetermined and returns NUFFT_EINVAL. */
 int nufft_fwd(const void *c, int64_t N, const double *y, int64_t M, double eps,
               int prec, unsigned flags, void *g, void *stream);
 int nufft_adj(const void *g, const double *y, int64_t M, int64_t N, double eps,
@@ -372,14 +431,36 @@ int inufft(const void *g, const double *y, int64_t M, int64_t N, double eps,
  * Same arguments, result and accuracy as nufft_fwd (automatic parameters;
  * flags: 0 or NUFFT_IO_C64), but every work buffer lives in one fixed
  * 16 MiB device array compiled into the library, held by every GPU that loads
- * it until the process exits.  Limits: N <= 2^16 and M <= 2^16; larger sizes
- * return NUFFT_EINVAL and do nothing.
+ * it until the process exits.  Limits: N a power of two, N <= 2^16 and
+ * M <= 2^16; other sizes return NUFFT_EINVAL and do nothing.  The tree depth is that of Eq. 25 but
+ * at least log2 N - 6 (leaves of at most 64 grid points), so the result can
+ * differ from nufft_fwd's in the last digits when M is much smaller than N.
  * The first call on a device looks up the array's device address and must run
  * with that device current; make it before any stream capture.  Calls share
  * the array and overwrite its contents; calls whose GPU work overlaps (other
  * streams, other threads) race on it.  Synchronises the stream. */
 int nufft_fwd_noalloc(const void *c, int64_t N, const double *y, int64_t M,
                       double eps, int prec, unsigned flags, void *g, void *stream);
+
+/* ---------------------------------------------------------------- diagnostics */
+
+/* The near-field pair reciprocal 1/t (the singular part 2/t of Eq. p20, t in
+ * grid units, |t| >= 1/2 for every pair the target kernels evaluate) as the
+ * kernels compute it, on caller values: r64[i] = the FP64 path's reciprocal
+ * of t[i] (hardware estimate + two Newton-Raphson steps), r32[i] = the mixed
+ * path's reciprocal of (float)t[i] (rcp.approx.ftz.f32).  t [device]
+ * double[n]; r64 [device] double[n], r32 [device] float[n], either may be
+ * NULL.  Asynchronous. */
+int nufft_diag_rcp(const double *t, int64_t n, double *r64, float *r32, void *stream);
+
+/* Throughput of the two pipes that bound the near-field pair loop (one FP32
+ * reciprocal and two FP32 FMAs per pair, Sec. 2.4's 3NM/2^lmax term): FP32
+ * reciprocals (rcp.approx.ftz.f32) and FP32 FMAs completed per SM per SM
+ * clock, measured by a kernel of independent chains on every SM (1024
+ * threads per SM), timed with each SM's own clock counter; the median over
+ * the SMs.  rcp_per_clk, ffma_per_clk [host] (either may be NULL).  Allocates
+ * a few KB of device memory for the call; synchronises the stream. */
+int nufft_diag_pipe_rates(double *rcp_per_clk, double *ffma_per_clk, void *stream);
 
 #ifdef __cplusplus
 }

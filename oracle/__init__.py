@@ -156,11 +156,17 @@ def cot_sum(f, y) -> np.ndarray:
     return h
 
 
+def _dft_any(x, sign: int) -> np.ndarray:
+    """fft() for power-of-two lengths, the direct dft() otherwise."""
+    n = np.asarray(x).size
+    return fft(x, sign) if n & (n - 1) == 0 else dft(x, sign)
+
+
 def nufft_fwd(c, y, idx=None, route: str = "nudft") -> np.ndarray:
     """Forward NUFFT c_n -> g_j by either independent route."""
     if route == "nudft":
         return nudft_fwd(c, y, idx)
-    f = fft(c, +1)  # f_k = sum_n c_n e^{+i n x_k}
+    f = _dft_any(c, +1)  # f_k = sum_n c_n e^{+i n x_k}
     return kernel_fwd(f, y, idx)
 
 
@@ -189,7 +195,7 @@ def kernel_adj(g, y, N: int, idx=None) -> np.ndarray:
 def nufft_adj(g, y, N: int, route: str = "nudft") -> np.ndarray:
     if route == "nudft":
         return nudft_adj(g, y, N)
-    return fft(kernel_adj(g, y, N), -1)
+    return _dft_any(kernel_adj(g, y, N), -1)
 
 
 # ---------------------------------------------------------------- inverse
@@ -254,7 +260,7 @@ def inverse_absf(g, y, N: int, idx=None, lamD=None) -> np.ndarray:
 def inufft(g, y, N: int) -> np.ndarray:
     """Square INUFFT g_j -> c_n: c = (1/N) sum_k f_k e^{-i n x_k} (Eq. p1) with f from Eq. p6."""
     f = inverse_f(g, y, N)
-    return fft(f, -1) / N
+    return _dft_any(f, -1) / N
 
 
 # ---------------------------------------------------------------- DFT / FFT

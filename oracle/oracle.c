@@ -67,11 +67,24 @@ static inline void expi_ny(int64_t n, double y, double *re, double *im) {
   *im = cp * ei + sp * er;
 }
 
+/* 2 pi / N as an unevaluated sum hi + lo with |lo| <= ulp(hi) / 2 and an
+ * error of order 2^-106 relative: hi = fl(2 pi_hi / N); the remainder
+ * 2 pi_hi - hi N is exact (fma of a correctly rounded quotient), so
+ * lo = (remainder + 2 pi_lo) / N.  For N a power of two, lo = 2 pi_lo / N. */
+static inline void two_pi_over(int64_t N, double *hi, double *lo) {
+  double nd = (double)N;
+  double h = TWO_PI_HI / nd;
+  double rem = fma(-h, nd, TWO_PI_HI);
+  *hi = h;
+  *lo = (rem + TWO_PI_LO) / nd;
+}
+
 /* Unwrapped difference y - x~ with x~ = 2 pi kk / N for an integer kk
  * (kk = k or a periodic image k +- N), formed with a double-double 2 pi/N and
  * an exact two-product so that a small result keeps full relative precision. */
 static inline double diff_y_grid(double y, int64_t kk, int64_t N) {
-  double hhi = TWO_PI_HI / (double)N, hlo = TWO_PI_LO / (double)N; /* exact: N = 2^L */
+  double hhi, hlo;
+  two_pi_over(N, &hhi, &hlo);
   double kd = (double)kk;
   double P = kd * hhi;
   double E = fma(kd, hhi, -P);
@@ -100,11 +113,24 @@ static inline double wrap_diff(double a, double b) {
   return s + err;
 }
 
-/* F_j = (e^{i N y} - 1)/N  (Eq. p5), written as (2i/N) e^{i N y/2} sin(N y/2);
- * N y is exact because N is a power of two. */
+/* cos and sin of N y / 2 with N y formed exactly as p + e (two-product;
+ * e = 0 when N is a power of two): sin(p/2 + e/2) by the expansion of e^{i e/2}
+ * to second order (|e| <= ulp(N y), so the rest is below the rounding). */
+static inline void half_ny(double y, int64_t N, double *c, double *s) {
+  double nd = (double)N;
+  double p = nd * y;
+  double e = fma(nd, y, -p);
+  double a = 0.5 * p, h = 0.5 * e;
+  double ca = cos(a), sa = sin(a);
+  double er = 1.0 - 0.5 * h * h;
+  *c = ca * er - sa * h;
+  *s = sa * er + ca * h;
+}
+
+/* F_j = (e^{i N y} - 1)/N  (Eq. p5), written as (2i/N) e^{i N y/2} sin(N y/2). */
 static inline void F_of_y(double y, int64_t N, double *re, double *im) {
-  double a = 0.5 * (double)N * y;
-  double s = sin(a), c = cos(a);
+  double c, s;
+  half_ny(y, N, &c, &s);
   *re = -2.0 * s * s / (double)N;
   *im = 2.0 * c * s / (double)N;
 }
@@ -341,8 +367,9 @@ void orc_inverse_f(const double *g, const double *y, int64_t M, int64_t N,
       double sgn = ((k + nC[i] + nD[j]) & 1) ? -1.0 : 1.0;
       double mag = sgn * exp(lamC[i] + lamD[j]);
       /* i e^{-i N y_j / 2} */
-      double a = 0.5 * (double)N * y[j];
-      double Dr = sin(a), Di = cos(a);
+      double ca, sa;
+      half_ny(y[j], N, &ca, &sa);
+      double Dr = sa, Di = ca;
       double Gr, Gi;
       G_of_t(t, &Gr, &Gi);
       double Lr = mag * (Gr * Dr - Gi * Di), Li = mag * (Gr * Di + Gi * Dr);

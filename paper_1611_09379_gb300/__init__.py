@@ -45,7 +45,8 @@ SYMBOLS = [
     "nufft_dcf_features_sorted", "nufft_dcf_targets", "nufft_mlp_create", "nufft_mlp_destroy",
     "nufft_mlp_num_params", "nufft_mlp_set_params", "nufft_mlp_get_params", "nufft_mlp_infer",
     "nufft_mlp_grad", "nufft_mlp_train_step", "nufft_multi_create", "nufft_multi_exec_fwd",
-    "nufft_multi_destroy", "nufft_autotune",
+    "nufft_multi_destroy", "nufft_autotune", "nufft_plan_dcf_weights", "nufft_diag_rcp",
+    "nufft_diag_pipe_rates",
 ]
 
 
@@ -57,6 +58,12 @@ class Params(ctypes.Structure):
 class TuneTrial(ctypes.Structure):
     _fields_ = [("params", Params), ("ms", ctypes.c_double), ("err", ctypes.c_double),
                 ("accepted", ctypes.c_int)]
+
+
+class LsqInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("checks", ctypes.c_int), ("resid", ctypes.c_double),
+                ("resid_w", ctypes.c_double), ("data_resid", ctypes.c_double),
+                ("hist", ctypes.POINTER(ctypes.c_double)), ("hist_cap", ctypes.c_int)]
 
 
 OP_FWD, OP_ADJ, OP_INV = 0x1, 0x2, 0x4
@@ -91,8 +98,12 @@ _lib.nufft_mlp_get_params.argtypes = [_P, _P]
 _lib.nufft_mlp_infer.argtypes = [_P, _P, _I64, _P, _P]
 _lib.nufft_mlp_grad.argtypes = [_P, _P, _P, _I64, _P, _P, _P]
 _lib.nufft_mlp_train_step.argtypes = [_P, _P, _P, _I64, ctypes.c_float, _P, _P]
-_lib.nufft_plan_solve_lsq.argtypes = [_P, _P, _P, ctypes.c_double, ctypes.c_int, _P,
-                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
+_lib.nufft_plan_solve_lsq.argtypes = [_P, _P, _P, ctypes.c_uint, ctypes.c_double, ctypes.c_int,
+                                      ctypes.c_int, _P, ctypes.POINTER(LsqInfo)]
+LSQ_WEIGHTED = 0x1
+_lib.nufft_plan_dcf_weights.argtypes = [_P, _P, _P]
+_lib.nufft_diag_rcp.argtypes = [_P, _I64, _P, _P, _P]
+_lib.nufft_diag_pipe_rates.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), _P]
 _lib.nufft_plan_stats.argtypes = [_P, _P, _P]
 _lib.nufft_autotune.argtypes = [_I64, _I64, _P, ctypes.c_double, ctypes.c_int, ctypes.c_uint,
                                 ctypes.c_int, ctypes.c_uint, ctypes.c_int, ctypes.POINTER(Params),
@@ -294,22 +305,48 @@ class Plan:
                                         _dev_ptr(c, self.cdtype, B * self.N, "c")), "nufft_plan_exec_inv")
         return c
 
-    def solve_lsq(self, g, w=None, tol: float = 1e-8, maxit: int = 500, out=None, check=True):
-        """Least-squares coefficients c = argmin sum_j w_j |(A c)_j - g_j|^2 by CG on
-        the normal equations.  Returns (c, iterations, relative residual); raises
-        on non-convergence unless check=False."""
+    def solve_lsq(self, g, w=None, tol: float = 1e-8, maxit: int = 500, out=None, check=True,
+                  check_every: int = 0, weighted: bool = False):
+        """Least-squares coefficients c = argmin sum_j |(A c)_j - g_j|^2 by CG on
+        the normal equations; weights w (density compensation) precondition
+        them, or with weighted=True define the weighted equations A^H W A c =
+        A^H W g instead.  Stopped when the unweighted normal-equation residual
+        ||A^H (g - A c)|| / ||A^H g||, recomputed from c, is <= tol.  Returns
+        (c, iterations, that residual); the full report (iters, checks, resid,
+        resid_w, data_resid, history of the stopping test at every check) is
+        kept in ``self.lsq_info``.  Raises on non-convergence unless
+        check=False."""
         torch = _torch()
         c = self._out(self.N, out)
         wp = None
         if w is not None:
             wp = _dev_ptr(w, torch.float32, self.M, "w")
-        it, res = ctypes.c_int(), ctypes.c_double()
-        rc = _lib.nufft_plan_solve_lsq(self._h, _dev_ptr(g, self.cdtype, self.M, "g"), wp, tol, maxit,
-                                       _dev_ptr(c, self.cdtype, self.N, "c"), ctypes.byref(it),
-                                       ctypes.byref(res))
+        info = LsqInfo()
+        every = int(check_every) if check_every > 0 else 16
+        cap = maxit // every + 2
+        hist = (ctypes.c_double * cap)()
+        info.hist = ctypes.cast(hist, ctypes.POINTER(ctypes.c_double))
+        info.hist_cap = cap
+        rc = _lib.nufft_plan_solve_lsq(self._h, _dev_ptr(g, self.cdtype, self.M, "g"), wp,
+                                       LSQ_WEIGHTED if weighted else 0, tol, maxit,
+                                       int(check_every), _dev_ptr(c, self.cdtype, self.N, "c"),
+                                       ctypes.byref(info))
+        self.lsq_info = {k: getattr(info, k) for k in ("iters", "checks", "resid", "resid_w",
+                                                       "data_resid")}
+        self.lsq_info["check_every"] = every
+        self.lsq_info["history"] = [hist[i] for i in range(min(info.checks, cap))]
         if rc != OK and (check or rc != ENOTCONV):
             raise NufftError(rc, "nufft_plan_solve_lsq")
-        return c, it.value, res.value
+        return c, info.iters, info.resid
+
+    def dcf_weights(self, mlp, out=None):
+        """Learned density-compensation weights of the points (mean 1), float32
+        CUDA tensor [M] in the original point order."""
+        torch = _torch()
+        w = out if out is not None else torch.empty(self.M, dtype=torch.float32, device=self.device)
+        _check(_lib.nufft_plan_dcf_weights(self._h, mlp._h, _dev_ptr(w, torch.float32, self.M, "w")),
+               "nufft_plan_dcf_weights")
+        return w
 
     def dcf_features(self):
         """Density-compensation features of the points: float32 [M, 8] (original order)."""
@@ -361,7 +398,8 @@ def nufft_adj(g, y, M: int, N: int, eps: float, prec: int = FP64, io: str = "c12
 
 
 def inufft(g, y, M: int, N: int, eps: float, prec: int = FP64, io: str = "c128", stream=None):
-    """One-shot square inverse: inufft(g_j, y_j, M, N, eps) -> c_n (M == N)."""
+    """One-shot inverse: inufft(g_j, y_j, M, N, eps) -> c_n; M == N by the Lagrange
+    form (Eq. p6 / p8), M > N the least-squares solution by plain CG."""
     torch = _torch()
     cd = torch.complex64 if io == "c64" else torch.complex128
     c = torch.empty(N, dtype=cd, device=y.device)
@@ -382,6 +420,26 @@ def nufft_fwd_noalloc(c, N: int, y, M: int, eps: float, prec: int = FP64, io: st
     _oneshot(_lib.nufft_fwd_noalloc, _dev_ptr(c, cd, N, "c"), N, _dev_ptr(y, torch.float64, M, "y"),
              M, eps, prec, io, _dev_ptr(g, cd, M, "g"), stream, "nufft_fwd_noalloc")
     return g
+
+
+def diag_rcp(t):
+    """The near-field pair reciprocal as the kernels compute it: (FP64 path,
+    mixed path) for a float64 CUDA tensor t."""
+    torch = _torch()
+    n = t.numel()
+    r64 = torch.empty(n, dtype=torch.float64, device=t.device)
+    r32 = torch.empty(n, dtype=torch.float32, device=t.device)
+    _check(_lib.nufft_diag_rcp(_dev_ptr(t, torch.float64, n, "t"), n, _P(r64.data_ptr()),
+                               _P(r32.data_ptr()), _stream_handle(None)), "nufft_diag_rcp")
+    return r64, r32
+
+
+def pipe_rates(stream=None):
+    """(FP32 reciprocals, FP32 FMAs) completed per SM per clock on this GPU."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(_lib.nufft_diag_pipe_rates(ctypes.byref(a), ctypes.byref(b), _stream_handle(stream)),
+           "nufft_diag_pipe_rates")
+    return a.value, b.value
 
 
 def dcf_features_sorted(y_sorted, stream=None):

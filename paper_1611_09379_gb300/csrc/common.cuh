@@ -65,6 +65,30 @@ __device__ inline bool neg_bits(double d) {
   return b < 0 && b != (long long)0x8000000000000000ull;
 }
 
+// 1/t of a near-field pair (the singular part 2/t of Eq. p20; |t| >= 1/2 in
+// grid units for every pair that is not a point's nearest grid point, so t
+// is never subnormal).  FP32: the special-function unit's reciprocal
+// (rcp.approx, at most 1 ulp).
+// FP64: the unit's FP64 reciprocal estimate (rcp.approx.ftz.f64, about 20
+// correct bits) refined by two Newton-Raphson steps r <- r + r (1 - t r),
+// each of which squares the relative error, so r is within a few ulp of
+// 1/t (t is never subnormal here).  (An FP32 estimate refined in FP64 was
+// measured slower than a division: its two precision conversions run at the
+// FP64 rate.)  t = 0 gives a NaN; callers that meet t = 0 replace r by 0.
+__device__ inline float rcp_t(float t) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(t));
+  return r;
+}
+__device__ inline double rcp_t(double t) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(t));
+  double e = fma(-t, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-t, r, 1.0);
+  return fma(r, e, r);
+}
+
 // Leaf index and offset of a point from its grid coordinates (int32: N <= 2^26):
 // leaf = floor((k0 + delta)/s) mod 2^L, o = k0 - leaf s in [0, s].
 __device__ inline void point_local(int k0, double delta, int N, int s, int* leaf, int* o) {
@@ -180,7 +204,10 @@ struct StageProf {
 
 // The plan object behind the opaque handle of nufft.h.
 struct nufft_plan_s {
-  int64_t N = 0, M = 0;
+  // N: the FMM grid (a power of two); Nc: the caller's number of coefficients
+  // (N itself, or any Nc <= N with N = 2^ceil(log2 Nc): the band-limited
+  // series with Nc terms is also one with N terms, its top N - Nc zero)
+  int64_t N = 0, M = 0, Nc = 0;
   int L = 0, B = 0, s = 0, p = 0, q = 0, pm = 0;
   int prec = 0;
   int batch = 1;        // signals sharing the point set

@@ -244,12 +244,16 @@ __device__ inline cplx<T> ld_cv(const double2* p) {
 // issued before the first twiddle is applied, so they are in flight together.
 template <class T, int E, class V>
 __device__ inline void fft_load(cplx<T>* v, const V* __restrict__ in, uint32_t idx,
-                                uint32_t stride, uint32_t ex, uint32_t de, uint32_t nmask,
-                                const cplx<T>* __restrict__ tw, int lo_bits, uint32_t lo_mask,
-                                T sg) {
+                                uint32_t stride, uint32_t n_in, uint32_t ex, uint32_t de,
+                                uint32_t nmask, const cplx<T>* __restrict__ tw, int lo_bits,
+                                uint32_t lo_mask, T sg) {
   V raw[E];
 #pragma unroll
-  for (int m = 0; m < E; ++m) raw[m] = in[idx + m * stride];
+  for (int m = 0; m < E; ++m) {
+    const uint32_t e = idx + m * stride;
+    if (e < n_in) raw[m] = in[e];  // elements n_in .. N - 1 are the zero padding
+    else { raw[m].x = 0; raw[m].y = 0; }
+  }
   if (de == 0 && ex == 0) {  // first pass (Ns = 1) and column 0: no twiddles
 #pragma unroll
     for (int m = 0; m < E; ++m) v[m] = ld_cv<T>(&raw[m]);
@@ -280,11 +284,15 @@ __device__ inline void st_cv(double2* p, cplx<T> v) {
 // with the pass twiddle, runs the first stage from registers and the rest
 // through shared memory; the result goes to
 // out[(j / Ns) Ns R + (j mod Ns) + r' Ns] in contiguous runs (J per r' for
-// Ns >= J, else R per j).  N = 2^logN < 2^31, Ns = 2^logNs.
+// Ns >= J, else R per j).  N = 2^logN < 2^31, Ns = 2^logNs.  The input holds
+// n_in <= N elements per signal (signal stride n_in; the rest read as zero)
+// and the output keeps the first n_out <= N (signal stride n_out): both N for
+// the passes between two work buffers.
 template <class T, int LOGR, int JC>
 __global__ void __launch_bounds__(kFftMaxThreads, sizeof(T) == 4 ? 3 : 2) k_fft_st(
     const void* __restrict__ in, int in_f64, void* __restrict__ out, int out_f64, int logN,
-    int logNs, int Jrt, int logJrt, int sign, const cplx<T>* __restrict__ tw, int lo_bits) {
+    int logNs, int Jrt, int logJrt, int sign, const cplx<T>* __restrict__ tw, int lo_bits,
+    uint32_t n_in, uint32_t n_out) {
   using S = FftShape<T, LOGR>;
   constexpr int R = S::R, LOGE = S::LOGE, E = S::E, TPC = S::TPC;
   const int J = JC ? JC : Jrt;
@@ -315,30 +323,32 @@ __global__ void __launch_bounds__(kFftMaxThreads, sizeof(T) == 4 ? 3 : 2) k_fft_
     const int lstep = logN - logNs - LOGR;  // N / (Ns R) = 2^lstep
     const uint32_t idx = jg + ((uint32_t)q << lognr), stride = (uint32_t)TPC << lognr;
     const uint32_t ex = ((q * jm) << lstep) & nmask, de = ((TPC * jm) << lstep) & nmask;
-    const size_t sig = (size_t)blockIdx.y * N;
+    const size_t sig = (size_t)blockIdx.y * n_in;
     if (in_f64)
-      fft_load<T, E>(v, reinterpret_cast<const double2*>(in) + sig, idx, stride, ex, de, nmask,
-                     tw, lo_bits, lo_mask, sg);
+      fft_load<T, E>(v, reinterpret_cast<const double2*>(in) + sig, idx, stride, n_in, ex, de,
+                     nmask, tw, lo_bits, lo_mask, sg);
     else
-      fft_load<T, E>(v, reinterpret_cast<const float2*>(in) + sig, idx, stride, ex, de, nmask,
-                     tw, lo_bits, lo_mask, sg);
+      fft_load<T, E>(v, reinterpret_cast<const float2*>(in) + sig, idx, stride, n_in, ex, de,
+                     nmask, tw, lo_bits, lo_mask, sg);
   }
   __syncthreads();  // wR ready
   fft_stage<T, LOGR, LOGE, 0, JC, true, LOGE == LOGR>(v, X0, X0, wR, J, c, q, sg);
   fft_stages<T, LOGR, JC, 1>(v, X0, X1, wR, J, c, q, sg);
   // v[m] = A_r' of column c, r' = q + m TPC -> out[(j / Ns) Ns R + (j mod Ns) + r' Ns]
   // (J contiguous per r' for Ns >= J; runs of TPC per column for Ns = 1)
-  const size_t sig = (size_t)blockIdx.y * N;
+  const size_t sig = (size_t)blockIdx.y * n_out;
   const uint32_t d0 = ((jg >> logNs) << (logNs + LOGR)) + jm + ((uint32_t)q << logNs);
   const uint32_t dstep = (uint32_t)TPC << logNs;
   if (out_f64) {
-    double2* o = reinterpret_cast<double2*>(out) + sig + d0;
+    double2* o = reinterpret_cast<double2*>(out) + sig;
 #pragma unroll
-    for (int m = 0; m < E; ++m) st_cv<T>(o + m * dstep, v[m]);
+    for (int m = 0; m < E; ++m)
+      if (d0 + m * dstep < n_out) st_cv<T>(o + d0 + m * dstep, v[m]);
   } else {
-    float2* o = reinterpret_cast<float2*>(out) + sig + d0;
+    float2* o = reinterpret_cast<float2*>(out) + sig;
 #pragma unroll
-    for (int m = 0; m < E; ++m) st_cv<T>(o + m * dstep, v[m]);
+    for (int m = 0; m < E; ++m)
+      if (d0 + m * dstep < n_out) st_cv<T>(o + d0 + m * dstep, v[m]);
   }
 }
 
@@ -388,31 +398,33 @@ int fft_num_passes(int64_t N) {
 }
 
 template <class T, int LR>
-static void fft_launch(dim3 grid, int threads, size_t smem, cudaStream_t st, const void* in,
+static void fft_launch(dim3 grid, int threads, size_t smem, cudaStream_t st, uint32_t n_in,
+                       uint32_t n_out, const void* in,
                        int in_f64, void* out, int out_f64, int logN, int logNs, int J, int logJ,
                        int sign, const cplx<T>* tw, int lo_bits) {
   constexpr int JMAX = FftShape<T, LR>::JMAX;
   constexpr int JHALF = JMAX > 1 ? JMAX / 2 : JMAX;
   if (J == JMAX)
     launch_pdl(k_fft_st<T, LR, JMAX>, grid, threads, smem, st, in, in_f64, out, out_f64, logN,
-               logNs, J, logJ, sign, tw, lo_bits);
+               logNs, J, logJ, sign, tw, lo_bits, n_in, n_out);
   else if (J == JHALF)
     launch_pdl(k_fft_st<T, LR, JHALF>, grid, threads, smem, st, in, in_f64, out, out_f64, logN,
-               logNs, J, logJ, sign, tw, lo_bits);
+               logNs, J, logJ, sign, tw, lo_bits, n_in, n_out);
   else
     launch_pdl(k_fft_st<T, LR, 0>, grid, threads, smem, st, in, in_f64, out, out_f64, logN, logNs,
-               J, logJ, sign, tw, lo_bits);
+               J, logJ, sign, tw, lo_bits, n_in, n_out);
 }
 
 // the pass kernel for logR
 template <class T>
 static int fft_pass(int logR, dim3 grid, int threads, size_t smem, cudaStream_t st,
-                    const void* in, int in_f64, void* out, int out_f64, int logN, int logNs,
-                    int J, int logJ, int sign, const cplx<T>* tw, int lo_bits) {
+                    uint32_t n_in, uint32_t n_out, const void* in, int in_f64, void* out,
+                    int out_f64, int logN, int logNs, int J, int logJ, int sign,
+                    const cplx<T>* tw, int lo_bits) {
 #define NUFFT_FFT_CASE(LR)                                                                  \
   case LR:                                                                                 \
-    fft_launch<T, LR>(grid, threads, smem, st, in, in_f64, out, out_f64, logN, logNs, J, logJ, \
-                      sign, tw, lo_bits);                                                  \
+    fft_launch<T, LR>(grid, threads, smem, st, n_in, n_out, in, in_f64, out, out_f64, logN, \
+                      logNs, J, logJ, sign, tw, lo_bits);                                  \
     return NUFFT_OK;
   switch (logR) {
     NUFFT_FFT_CASE(1)
@@ -447,10 +459,17 @@ static int fft_min_cols() {
 // out = FFT(in) in arithmetic T for `batch` signals of N elements each
 // (signal-major); in / out are complex128 (f64 = 1) or complex64.  Intermediate passes alternate between the scratch vectors buf
 // and buf2 (batch x N cplx<T> each; buf2 is used only with three or more passes), so
-// they keep T precision and never touch `out`.  `in` is only read.
+// they keep T precision and never touch `out`.  `in` is only read.  in holds
+// n_in <= N elements per signal, zero padded to N (the first pass reads
+// nothing beyond n_in), and out keeps the first n_out <= N of the N outputs
+// (signal strides n_in and n_out); 0 = N.
 template <class T>
 int fft_run(const void* in, int in_f64, void* out, int out_f64, cplx<T>* buf, cplx<T>* buf2,
-            int64_t N, int batch, int sign, const cplx<T>* tw, cudaStream_t st) {
+            int64_t N, int batch, int sign, const cplx<T>* tw, cudaStream_t st, int64_t n_in,
+            int64_t n_out) {
+  if (n_in <= 0) n_in = N;
+  if (n_out <= 0) n_out = N;
+  if (n_in > N || n_out > N) return NUFFT_EINVAL;
   int L = 0;
   while ((int64_t(1) << L) < N) ++L;
   int logR[8];
@@ -484,8 +503,9 @@ int fft_run(const void* in, int in_f64, void* out, int out_f64, cplx<T>* buf, cp
     unsigned grid = (unsigned)(NR / J);
     int logNs = 0;
     while ((int64_t(1) << logNs) < Ns) ++logNs;
-    int rc = fft_pass<T>(lr, dim3(grid, (unsigned)batch), J * TPC, smem, st, src, src_f64, dst,
-                         dst_f64, L, logNs, J, logJ, sign, tw, b);
+    const uint32_t pin = (uint32_t)(i == 0 ? n_in : N), pout = (uint32_t)(last ? n_out : N);
+    int rc = fft_pass<T>(lr, dim3(grid, (unsigned)batch), J * TPC, smem, st, pin, pout, src,
+                         src_f64, dst, dst_f64, L, logNs, J, logJ, sign, tw, b);
     if (rc) return rc;
     src = dst;
     src_f64 = dst_f64;
@@ -538,6 +558,6 @@ int fft_configure() {
 }
 
 template int fft_run<double>(const void*, int, void*, int, double2*, double2*, int64_t, int, int,
-                             const double2*, cudaStream_t);
+                             const double2*, cudaStream_t, int64_t, int64_t);
 template int fft_run<float>(const void*, int, void*, int, float2*, float2*, int64_t, int, int,
-                            const float2*, cudaStream_t);
+                            const float2*, cudaStream_t, int64_t, int64_t);

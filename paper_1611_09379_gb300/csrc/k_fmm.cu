@@ -20,6 +20,8 @@
 
 #include <type_traits>
 
+#include <cstdlib>
+
 #include "common.cuh"
 
 namespace nufft {
@@ -873,26 +875,7 @@ __device__ inline float int_to_t(int D, float) {
 }
 __device__ inline double int_to_t(int D, double) { return (double)D; }
 
-// 1/t: FP32 reciprocal on the special-function unit (rcp.approx, 1 ulp).
-// FP64: the unit's FP64 reciprocal estimate (rcp.approx.ftz.f64, about 20
-// correct bits) refined by two Newton-Raphson steps r <- r + r (1 - t r),
-// each of which squares the relative error, so r is within a few ulp of
-// 1/t (t is never subnormal here).  (An FP32 estimate refined in FP64 was
-// measured slower than a division: its two precision conversions run at the
-// FP64 rate.)  t = 0 gives a NaN; callers that meet t = 0 replace r by 0.
-__device__ inline float rcp_t(float t) {
-  float r;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(t));
-  return r;
-}
-__device__ inline double rcp_t(double t) {
-  double r;
-  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(t));
-  double e = fma(-t, r, 1.0);
-  r = fma(r, e, r);
-  e = fma(-t, r, 1.0);
-  return fma(r, e, r);
-}
+// 1/t of a near-field pair: rcp_t (common.cuh).
 
 // Near-field accumulation of q / t.  FP64 path: FP64 throughout.  FP32 path:
 // FP32 partial sums of up to 16 terms folded into a compensated (Kahan) FP32
@@ -1645,6 +1628,126 @@ __global__ void __launch_bounds__(kTgtThreads, sizeof(T) == 4 ? 5 : 4) k_targets
   }
 }
 
+// Adjoint / inverse near field for one signal when each grid point meets
+// many sources (M >> N, or clustered sources): one warp per G consecutive
+// grid points of one leaf b (G divides s), so all G share the window of
+// leaves b - 1 .. b + 1.  The lanes stride over the window's sources (loads
+// of consecutive sources are coalesced and shared by the G targets), each
+// lane keeps G compensated partial sums; a reduce-scatter across the lanes
+// (log2 G halving exchanges, then full exchanges: 5 shuffle rounds) leaves
+// target g's sum in the lanes g * 32 / G .. (g + 1) * 32 / G - 1, the first of
+// which finishes it: the sources whose nearest grid point is the target (a
+// run of the sorted leaf, found by binary search) add their self terms, the
+// far field, the regular part (Eq. p20) and C_k complete it as in
+// k_targets_grid2.  Grid size N / (8 G) CTAs of 8 warps.
+template <class T>
+__device__ inline T int_small_to_t(int v) { return int_to_t(v, T()); }
+
+template <class T, int G>
+__global__ void __launch_bounds__(kTgtThreads) k_targets_gridw(
+    TreeDims d, int inverse, const int32_t* __restrict__ start,
+    const SrcPos<T>* __restrict__ pos, const cplx<T>* __restrict__ charge,
+    const cplx<T>* __restrict__ st, const cplx<T>* __restrict__ lexp,
+    const cplx<T>* __restrict__ lvl2, const T* __restrict__ Ct, cplx<T>* __restrict__ out) {
+  pdl_wait();
+  pdl_trigger();
+  constexpr int LOGG = G == 8 ? 3 : (G == 4 ? 2 : 1);
+  const int N = (int)d.N;
+  const int s = d.s;
+  const int B = 1 << d.L;
+  const int lane = threadIdx.x & 31;
+  const int kb = (int)((blockIdx.x * (unsigned)kTgtThreads + threadIdx.x) >> 5) * G;
+  if (kb >= N) return;  // the same for the whole warp
+  const int b = kb / s;
+  NearAcc<T> acc[G];
+  for (int nb = -1; nb <= 1; ++nb) {
+    const int bu = b + nb;
+    const int bb = bu & (B - 1);
+    const int i0 = start[bb], i1 = start[bb + 1];
+    const int xbase = bu * s - kb;  // source position relative to kb: xbase + (k0 - bb s) mod N
+    int cnt = 0;
+    for (int i = i0 + lane; i < i1; i += 32) {
+      const SrcPos<T> ps = pos[i];
+      const cplx<T> q = charge[i];
+      const int xi = xbase + (((int)ps.k0 - bb * s) & (N - 1));
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        const T e = int_small_to_t<T>(g - xi);  // exact small integer
+        T r = rcp_t(e - ps.dl);
+        r = e != (T)0 ? r : (T)0;  // the nearest grid point: self term below
+        acc[g].add_r(q, r);
+      }
+      if (++cnt == 16) {
+#pragma unroll
+        for (int g = 0; g < G; ++g) acc[g].fold();
+        cnt = 0;
+      }
+    }
+  }
+  // reduce-scatter over the lanes
+  cplx<T> v[G];
+#pragma unroll
+  for (int g = 0; g < G; ++g) v[g] = acc[g].get();
+#pragma unroll
+  for (int st_ = 0; st_ < LOGG; ++st_) {
+    const int mask = 16 >> st_;
+    const int half = G >> (st_ + 1);
+    const bool upper = (lane & mask) != 0;
+#pragma unroll
+    for (int i = 0; i < half; ++i) {
+      const cplx<T> send = upper ? v[i] : v[i + half];
+      const cplx<T> keep = upper ? v[i + half] : v[i];
+      cplx<T> got;
+      got.x = __shfl_xor_sync(0xffffffffu, send.x, mask);
+      got.y = __shfl_xor_sync(0xffffffffu, send.y, mask);
+      v[i] = cadd(keep, got);
+    }
+  }
+#pragma unroll
+  for (int mask = 16 >> LOGG; mask > 0; mask >>= 1) {
+    v[0].x += __shfl_xor_sync(0xffffffffu, v[0].x, mask);
+    v[0].y += __shfl_xor_sync(0xffffffffu, v[0].y, mask);
+  }
+  if ((lane & ((32 >> LOGG) - 1)) != 0) return;
+  const int g = lane >> (5 - LOGG);
+  const int k = kb + g;
+  // self terms: the run of leaf b with k0 = k, and for the leaf's first grid
+  // point the sources at the end of leaf b - 1 that round up to it
+  cplx<T> self = mk<T>(0, 0);
+  {
+    const int want = k - b * s;  // (k0 - b s) mod N of the run, in [0, s)
+    int lo = start[b], hi = start[b + 1];
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if ((((int)pos[mid].k0 - b * s) & (N - 1)) < want) lo = mid + 1; else hi = mid;
+    }
+    for (int i = lo; i < start[b + 1] && (((int)pos[i].k0 - b * s) & (N - 1)) == want; ++i)
+      self = cadd(self, st[i]);
+    if (want == 0) {
+      const int bp = (b - 1) & (B - 1);
+      for (int i = start[bp + 1] - 1; i >= start[bp] && (((int)pos[i].k0 - bp * s) & (N - 1)) == s; --i)
+        self = cadd(self, st[i]);
+    }
+  }
+  const int Q2 = 2 * d.q;
+  const int arc = b >> (d.L - 2);
+  const T ts = KConst<T>::inv_s(d);
+  const T cN = KConst<T>::n_pi(d), c2 = (T)(2.0 * kInvPi);
+  const cplx<T> Qs = lvl2[4 * Q2];
+  const int o = k - b * s;
+  const int I = k - arc * (N >> 2) - (N >> 3);
+  const T uh = (T)I * KConst<T>::two_n(d);
+  const T u = fma((T)o, ts, (T)-0.5);
+  cplx<T> far = mk<T>(0, 0);
+  if (d.L >= 3) far = horner<T>(lexp + ((int64_t)(level_off(d.L) - 4) + b) * d.p, d.p, u);
+  const cplx<T> reg = horner<T>(lvl2 + arc * Q2, Q2, uh);
+  const T hr = cN * fma(far.x, ts, v[0].x) - c2 * reg.x;
+  const T hi = cN * fma(far.y, ts, v[0].y) - c2 * reg.y;
+  cplx<T> res = mk<T>((T)-0.5 * (Qs.x - hi), (T)-0.5 * (Qs.y + hr));
+  if (inverse) res = cscale(res, Ct[k]);
+  out[k] = cadd(res, self);
+}
+
 }  // namespace nufft
 
 using namespace nufft;
@@ -2037,6 +2140,16 @@ int fmm_forward(nufft_plan_s* pl, void* g) {
   return cudaGetLastError() == cudaSuccess ? NUFFT_OK : NUFFT_ECUDA;
 }
 
+// The warp-per-G-grid-points near field pays when the two-point kernel's
+// CTAs (512 grid points each) would not fill the GPU or each grid point meets
+// more than twice the sources of a uniform grid (M > 2N); NUFFT_NEAR_GRID2=1
+// (environment) keeps the two-point kernel, NUFFT_NEAR_GRIDW=1 forces this one.
+static bool gridw_wanted(const nufft_plan_s* pl) {
+  static const int force = std::getenv("NUFFT_NEAR_GRIDW") ? 1 : (std::getenv("NUFFT_NEAR_GRID2") ? -1 : 0);
+  if (force) return force > 0;
+  return pl->N / (2 * kTgtThreads) < 2 * 152 || pl->M > 2 * pl->N;
+}
+
 // adjoint / inverse: samples g ([batch][M], original order) -> values on the
 // grid (cplx<T>, in pl->grid, [batch][N])
 template <class T>
@@ -2086,7 +2199,19 @@ int fmm_to_grid(nufft_plan_s* pl, const void* g, int inverse) {
     launch_pdl(k_targets_grid<T, 4>, dim3(nblk(pl->N, kTgtThreads), nsig / 4), kTgtThreads,
                NearCap<T, 4>::grid_bytes, st, d, inverse, pl->leaf_start, pos, charge, stt,
                lexp_c, PlanT<T>::lvl2(pl), PlanT<T>::Ct(pl), (cplx<T>*)pl->grid);
-  else if (nsig == 1 && pl->s >= 2)
+  else if (nsig == 1 && pl->s >= 2 && gridw_wanted(pl)) {
+    // many sources per grid point: one warp per G grid points (see k_targets_gridw)
+    const unsigned nb = nblk(pl->N, (int64_t)(kTgtThreads / 32) * (pl->s >= 8 ? 8 : pl->s));
+    if (pl->s >= 8)
+      launch_pdl(k_targets_gridw<T, 8>, nb, kTgtThreads, 0, st, d, inverse, pl->leaf_start, pos,
+                 charge, stt, lexp_c, PlanT<T>::lvl2(pl), PlanT<T>::Ct(pl), (cplx<T>*)pl->grid);
+    else if (pl->s == 4)
+      launch_pdl(k_targets_gridw<T, 4>, nb, kTgtThreads, 0, st, d, inverse, pl->leaf_start, pos,
+                 charge, stt, lexp_c, PlanT<T>::lvl2(pl), PlanT<T>::Ct(pl), (cplx<T>*)pl->grid);
+    else
+      launch_pdl(k_targets_gridw<T, 2>, nb, kTgtThreads, 0, st, d, inverse, pl->leaf_start, pos,
+                 charge, stt, lexp_c, PlanT<T>::lvl2(pl), PlanT<T>::Ct(pl), (cplx<T>*)pl->grid);
+  } else if (nsig == 1 && pl->s >= 2)
     launch_pdl(k_targets_grid2<T>, nblk(pl->N, 2 * kTgtThreads), kTgtThreads,
                NearCap<T, 1>::grid_bytes, st, d, inverse, pl->leaf_start, pos, charge, stt,
                lexp_c, PlanT<T>::lvl2(pl), PlanT<T>::Ct(pl), (cplx<T>*)pl->grid);

@@ -353,6 +353,40 @@ __global__ void __launch_bounds__(1024) k_dcf_targets(const double* __restrict__
   if (i < M) logw[(int64_t)blockIdx.x * M + i] = logf(fmaxf(w[i] / mean, 1e-4f));
 }
 
+// sum of w in FP64: per-CTA partials over a fixed stride, then one CTA
+// adds them in order (the same sum on every run)
+constexpr int kSumBlocks = 256;
+__global__ void __launch_bounds__(256) k_sum_partial(const float* __restrict__ w, int64_t n,
+                                                     double* __restrict__ part) {
+  __shared__ double sh[256];
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    acc += (double)w[i];
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if (threadIdx.x < (unsigned)h) sh[threadIdx.x] += sh[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+// w_i <- w_i / mean(w), the mean from the partials (every CTA adds them in
+// the same order)
+__global__ void __launch_bounds__(256) k_scale_to_mean1(float* __restrict__ w, int64_t n,
+                                                        const double* __restrict__ part) {
+  __shared__ float inv;
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int b = 0; b < kSumBlocks; ++b) t += part[b];
+    inv = t > 0.0 ? (float)((double)n / t) : 1.0f;
+  }
+  __syncthreads();
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) w[i] *= inv;
+}
+
 inline unsigned nblk(int64_t n, int th) { return (unsigned)((n + th - 1) / th); }
 
 size_t grad_smem() { return (size_t)(kNParam + 3 + 4 * kTrainPts * 65 + kTrainPts * kIn + kTrainPts) * 4; }
@@ -511,6 +545,29 @@ int nufft_dcf_targets(const double* y, int64_t S, int64_t M, int64_t N, int iter
 }
 
 // Features of a plan's points (original order): [M][8] floats.
+int nufft_plan_dcf_weights(nufft_plan pl, nufft_mlp m, float* w) {
+  if (!pl || !m || !w) return NUFFT_EINVAL;
+  cudaStream_t st = pl->stream;
+  const int64_t M = pl->M;
+  float* feat = nullptr;
+  double* part = nullptr;
+  if (cudaMallocAsync((void**)&feat, (size_t)M * 8 * 4, st) != cudaSuccess) return NUFFT_ENOMEM;
+  if (cudaMallocAsync((void**)&part, kSumBlocks * 8, st) != cudaSuccess) {
+    cudaFreeAsync(feat, st);
+    return NUFFT_ENOMEM;
+  }
+  int rc = nufft_plan_dcf_features(pl, feat);
+  if (!rc) rc = nufft_mlp_infer(m, feat, M, w, st);
+  if (!rc) {
+    k_sum_partial<<<kSumBlocks, 256, 0, st>>>(w, M, part);
+    k_scale_to_mean1<<<nblk(M, 256), 256, 0, st>>>(w, M, part);
+    if (cudaGetLastError() != cudaSuccess) rc = NUFFT_ECUDA;
+  }
+  cudaFreeAsync(feat, st);
+  cudaFreeAsync(part, st);
+  return rc;
+}
+
 int nufft_plan_dcf_features(nufft_plan pl, float* feat) {
   if (!pl || !feat) return NUFFT_EINVAL;
   cudaStream_t st = pl->stream;

@@ -18,6 +18,7 @@
 // and calls whose GPU work overlaps race on it.  Host-side calls are
 // serialised by a mutex; the operator tables are staged in static host
 // arrays, so no host allocation happens either.
+#include <cmath>
 #include <mutex>
 
 #include "common.cuh"
@@ -99,8 +100,19 @@ extern "C" int nufft_fwd_noalloc(const void* c, int64_t N, const double* y, int6
                                  int prec, unsigned flags, void* g, void* stream) {
   if (!c || !y || !g) return NUFFT_EINVAL;
   if (N > kNoAllocMaxN || M > kNoAllocMaxM) return NUFFT_EINVAL;  // beyond the fixed scratch
+  if (N & (N - 1)) return NUFFT_EINVAL;  // grids of a power of two only
   if (flags & ~NUFFT_IO_C64) return NUFFT_EINVAL;
-  nufft_params prm{0, 0, 0, 1, -1, -1};
+  // Tree depth: Eq. 25 (l* = 5), but at least log2 N - 6, so that a leaf
+  // holds at most kMaxS grid points (few points against a large grid would
+  // otherwise give shallow trees with wide leaves, beyond the staged P2M
+  // table's size)
+  int LN = 0;
+  while ((int64_t(1) << LN) < N) ++LN;
+  int L = (int)std::lround(0.5 * std::log2((double)N * (double)M) - 5.0);
+  if (L < LN - 6) L = LN - 6;
+  if (L > LN) L = LN;
+  if (L < 2) L = 2;
+  nufft_params prm{L, 0, 0, 1, -1, -1};
   int rc = nufft_choose_params(N, M, eps, prec, &prm);
   if (rc) return rc;
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
@@ -109,7 +121,7 @@ extern "C" int nufft_fwd_noalloc(const void* c, int64_t N, const double* y, int6
   if ((rc = scratch_base(&base))) return rc;
 
   nufft_plan_s pl;  // on the stack; its buffers all point into the scratch
-  pl.N = N; pl.M = M; pl.L = prm.lmax; pl.B = 1 << prm.lmax; pl.s = (int)(N >> prm.lmax);
+  pl.N = N; pl.Nc = N; pl.M = M; pl.L = prm.lmax; pl.B = 1 << prm.lmax; pl.s = (int)(N >> prm.lmax);
   pl.p = prm.p; pl.q = prm.q; pl.pm = prm.p > 2 * prm.q + 1 ? prm.p : 2 * prm.q + 1;
   pl.prec = prec; pl.flags = flags | NUFFT_NO_GRAPH; pl.eps = eps;  // a graph would allocate
   pl.side_ok = 0;  // so would a side stream

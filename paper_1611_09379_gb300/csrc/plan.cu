@@ -33,7 +33,8 @@ int near_tc_configure();
 int fft_num_passes(int64_t N);
 template <class T>
 int fft_run(const void* in, int in_f64, void* out, int out_f64, cplx<T>* buf, cplx<T>* buf2,
-            int64_t N, int batch, int sign, const cplx<T>* tw, cudaStream_t st);
+            int64_t N, int batch, int sign, const cplx<T>* tw, cudaStream_t st, int64_t n_in,
+            int64_t n_out);
 template <class T> int fmm_configure();
 bool m2l_tc_supported(int p, int pm);
 size_t m2l_tc_table_floats(int p);
@@ -346,9 +347,17 @@ const char* nufft_strerror(int status) {
 
 int nufft_version(void) { return 100; }
 
-int nufft_choose_params(int64_t N, int64_t M, double eps, int prec, nufft_params* prm) {
+// FMM grid of N coefficients: the next power of two
+static int64_t grid_of(int64_t N) {
+  int64_t g = 1;
+  while (g < N) g <<= 1;
+  return g;
+}
+
+int nufft_choose_params(int64_t Nc, int64_t M, double eps, int prec, nufft_params* prm) {
   if (!prm) return NUFFT_EINVAL;
-  if (!is_pow2(N) || N < 8 || N > (int64_t(1) << 26)) return NUFFT_EINVAL;
+  if (Nc < 8 || Nc > (int64_t(1) << 26)) return NUFFT_EINVAL;
+  const int64_t N = grid_of(Nc);  // the tree and the FFT live on this grid
   if (M < 1 || M > (int64_t(1) << 27)) return NUFFT_EINVAL;
   if (!(eps >= 1e-15 && eps <= 1e-1)) return NUFFT_EINVAL;
   if (prec != NUFFT_FP64 && prec != NUFFT_MIXED) return NUFFT_EINVAL;
@@ -412,13 +421,19 @@ int nufft_plan_create(nufft_plan* out, int64_t N, int64_t M, const double* y, do
   if (rc) return rc;
   if (flags & ~(NUFFT_IO_C64 | NUFFT_WANT_INVERSE | NUFFT_NO_GRAPH)) return NUFFT_EINVAL;
   if ((flags & NUFFT_WANT_INVERSE) && M != N) return NUFFT_EINVAL;
+  const int64_t Nc = N;
+  N = grid_of(Nc);
+  // the square inverse's Lagrange form (Eq. p8) is formed on the grid of its
+  // own N points
+  if ((flags & NUFFT_WANT_INVERSE) && N != Nc) return NUFFT_ENOTSUP;
   const int64_t nb = prm.batch;
   if ((rc = configure_once())) return rc;
   nufft_plan_s* pl = new (std::nothrow) nufft_plan_s();
   if (!pl) return NUFFT_ENOMEM;
   pl->prof = new (std::nothrow) StageProf();
   if (!pl->prof) { delete pl; return NUFFT_ENOMEM; }
-  pl->N = N; pl->M = M; pl->L = prm.lmax; pl->B = 1 << prm.lmax; pl->s = (int)(N >> prm.lmax);
+  pl->N = N; pl->Nc = Nc; pl->M = M; pl->L = prm.lmax; pl->B = 1 << prm.lmax;
+  pl->s = (int)(N >> prm.lmax);
   pl->p = prm.p; pl->q = prm.q; pl->pm = prm.p > 2 * prm.q + 1 ? prm.p : 2 * prm.q + 1;
   pl->prec = prec; pl->flags = flags; pl->eps = eps; pl->batch = (int)nb;
   pl->tc_level = prm.tc_level;
@@ -565,16 +580,17 @@ int nufft_plan_set_stream(nufft_plan pl, void* stream) {
 
 // c_n <-> grid with the FFT of the plan's arithmetic (FP64, or FP32 for the
 // mixed path); caller data complex128 or complex64.
+// (n_in / n_out: caller-side lengths, Nc for the coefficients, 0 = the grid)
 static int fft_plan(nufft_plan_s* pl, const void* in, int in_f64, void* out, int out_f64,
-                    int sign) {
+                    int sign, int64_t n_in, int64_t n_out) {
   prof_begin(pl, NUFFT_STAGE_FFT);
   int rc;
   if (pl->prec == NUFFT_FP64)
     rc = fft_run<double>(in, in_f64, out, out_f64, pl->grid2, pl->grid3, pl->N, pl->batch, sign,
-                         pl->fft_tw, pl->stream);
+                         pl->fft_tw, pl->stream, n_in, n_out);
   else
     rc = fft_run<float>(in, in_f64, out, out_f64, (float2*)pl->grid2, (float2*)pl->grid3, pl->N,
-                        pl->batch, sign, pl->fft_tw_f, pl->stream);
+                        pl->batch, sign, pl->fft_tw_f, pl->stream, n_in, n_out);
   prof_end(pl, fft_num_passes(pl->N));
   return rc;
 }
@@ -582,8 +598,9 @@ static int fft_plan(nufft_plan_s* pl, const void* in, int in_f64, void* out, int
 static int exec_fwd_direct(nufft_plan_s* pl, const void* c, void* g) {
   const int io64 = (pl->flags & NUFFT_IO_C64) ? 0 : 1;
   const int t64 = pl->prec == NUFFT_FP64;
-  // f_k = sum_n c_n e^{+2 pi i n k/N}  (Eq. p1, unscaled inverse DFT)
-  int rc = fft_plan(pl, c, io64, pl->grid, t64, +1);
+  // f_k = sum_n c_n e^{+2 pi i n k/N}  (Eq. p1, unscaled inverse DFT; c_n = 0
+  // for Nc <= n < N)
+  int rc = fft_plan(pl, c, io64, pl->grid, t64, +1, pl->Nc, 0);
   if (rc) return rc;
   return pl->prec == NUFFT_FP64 ? fmm_forward<double>(pl, g) : fmm_forward<float>(pl, g);
 }
@@ -591,7 +608,7 @@ static int exec_fwd_direct(nufft_plan_s* pl, const void* c, void* g) {
 static int grid_to_coeffs(nufft_plan_s* pl, void* c) {
   // c'_n = sum_k u_k e^{-2 pi i n k/N}
   const int io64 = (pl->flags & NUFFT_IO_C64) ? 0 : 1;
-  return fft_plan(pl, pl->grid, pl->prec == NUFFT_FP64, c, io64, -1);
+  return fft_plan(pl, pl->grid, pl->prec == NUFFT_FP64, c, io64, -1, 0, pl->Nc);
 }
 
 static int exec_adj_direct(nufft_plan_s* pl, const void* g, void* c) {
@@ -699,7 +716,19 @@ int nufft_adj(const void* g, const double* y, int64_t M, int64_t N, double eps, 
 
 int inufft(const void* g, const double* y, int64_t M, int64_t N, double eps, int prec,
            unsigned flags, void* c, void* stream) {
-  return one_shot(2, g, N, y, M, eps, prec, flags, c, stream);
+  if (M == N) return one_shot(2, g, N, y, M, eps, prec, flags, c, stream);
+  if (M < N || !g || !c) return NUFFT_EINVAL;  // fewer samples than coefficients
+  if (flags & ~(NUFFT_IO_C64 | NUFFT_NO_GRAPH)) return NUFFT_EINVAL;
+  if (flags & NUFFT_IO_C64) return NUFFT_ENOTSUP;
+  // M > N: least squares by plain CG on the normal equations
+  nufft_plan pl = nullptr;
+  int rc = nufft_plan_create(&pl, N, M, y, eps, prec, nullptr, flags, stream);
+  if (rc) return rc;
+  const double tol = eps > 1e-14 ? eps : 1e-14;
+  rc = nufft_plan_solve_lsq(pl, g, nullptr, 0u, tol, 100000, 0, c, nullptr);
+  if (!rc && cudaStreamSynchronize(pl->stream) != cudaSuccess) rc = NUFFT_ECUDA;
+  nufft_plan_destroy(pl);
+  return rc;
 }
 
 }  // extern "C"

@@ -62,12 +62,10 @@ def train(feat, target, epochs: int = 40, lr: float = 3e-3, batch: int = 32768, 
     return mlp, losses
 
 
-def weights(plan, mlp, normalise: bool = True):
-    """Learned weights of a plan's points, float32 CUDA tensor [M] (original order)."""
-    w = mlp.infer(plan.dcf_features())
-    if normalise:
-        w /= w.mean()
-    return w
+def weights(plan, mlp):
+    """Learned weights of a plan's points, mean 1, float32 CUDA tensor [M]
+    (original order); features, inference and scaling run in the library."""
+    return plan.dcf_weights(mlp)
 
 
 def save(mlp, path: str = WEIGHTS_PATH):

@@ -55,8 +55,8 @@ def test_choose_params_matches_eq18_2_reading(nf):
 
 
 @pytest.mark.parametrize("args", [
-    (1000, 1000, 1e-6, 0),      # N not a power of two
     (4, 4, 1e-6, 0),            # N < 8
+    ((1 << 26) + 1, 10, 1e-6, 0),  # N above 2^26
     (1 << 10, 0, 1e-6, 0),      # M < 1
     (1 << 10, 10, 1e-16, 0),    # eps below 1e-15
     (1 << 10, 10, 0.5, 0),      # eps above 1e-1
@@ -67,6 +67,15 @@ def test_choose_params_rejects(nf, args):
     with pytest.raises(nf.NufftError) as e:
         nf.choose_params(*args)
     assert e.value.code == nf.EINVAL
+
+
+@pytest.mark.parametrize("N", [1000, 12345, 3 << 10, (1 << 20) - 3])
+def test_choose_params_general_n_uses_the_padded_grid(nf, N):
+    """N not a power of two: the tree is chosen for the grid N' = 2^ceil(log2 N)
+    (the same parameters as for N' itself)."""
+    Np = 1 << (N - 1).bit_length()
+    for prec, eps in ((nf.FP64, 1e-12), (nf.MIXED, 1e-6)):
+        assert nf.choose_params(N, N, eps, prec) == nf.choose_params(Np, N, eps, prec)
 
 
 def test_lmax_override_bounds(nf):
@@ -119,7 +128,7 @@ def test_autotune_rejects_bad_arguments(nf):
     best = nf.Params()
     n = ctypes.c_int(0)
     lib = nf._lib
-    # null points, empty op mask, unknown op bit, reps < 1, inverse with M != N
+    # null points, empty op mask, unknown op bit, reps < 1, inverse with M != N, N < 8
     assert lib.nufft_autotune(1024, 1024, None, 1e-6, 1, 0, 1, 1, 3, ctypes.byref(best), None, 0,
                               ctypes.byref(n), None) == nf.EINVAL
     fake = ctypes.c_void_p(16)  # never dereferenced: the checks fail first
@@ -131,7 +140,7 @@ def test_autotune_rejects_bad_arguments(nf):
                               None, None) == nf.EINVAL
     assert lib.nufft_autotune(1024, 2048, fake, 1e-6, 1, 0, 1, 4, 3, ctypes.byref(best), None, 0,
                               None, None) == nf.EINVAL
-    assert lib.nufft_autotune(1000, 1024, fake, 1e-6, 1, 0, 1, 1, 3, ctypes.byref(best), None, 0,
+    assert lib.nufft_autotune(4, 1024, fake, 1e-6, 1, 0, 1, 1, 3, ctypes.byref(best), None, 0,
                               None, None) == nf.EINVAL
 
 

@@ -1,6 +1,9 @@
 """Least-squares INUFFT (M > N) by CG on the normal equations through the
-C ABI, against a dense least-squares solve (small N) and against the known
-band-limited solution c_true of consistent data g = A c_true (any size)."""
+C ABI, against a dense least-squares solve (small N), against the known
+band-limited solution c_true of consistent data g = A c_true (any size), and
+with the solver's reported residuals (the unweighted normal-equation
+residual it stops on, the data residual) recomputed by the oracle, up to the
+full least-squares workload (N = 2^16, M = 2^18)."""
 import numpy as np
 import pytest
 
@@ -89,3 +92,101 @@ def test_lsq_zero_data_and_nonconvergence(nf):
     with pytest.raises(nf.NufftError) as e:
         plan.solve_lsq(g, tol=1e-30, maxit=3)
     assert e.value.code == nf.ENOTCONV
+
+
+def test_lsq_reported_residuals_match_oracle(nf, orc):
+    """A solve stopped early (not converged): the reported data residual
+    ||g - A c|| / ||g|| and normal-equation residual ||A^H (g - A c)|| /
+    ||A^H g|| equal the oracle's direct sums (all targets, all frequencies)
+    for the returned c."""
+    N, M = 1 << 11, 1 << 13
+    y = workloads.points("contrast", M, seed=11)
+    c_true = workloads.coeffs(N, seed=12)
+    g = orc.nudft_fwd(c_true, y)
+    plan = nf.Plan(N, _dev(y), eps=1e-12)
+    c, it, res = plan.solve_lsq(_dev(g), tol=1e-14, maxit=150, check=False, check_every=50)
+    info = plan.lsq_info
+    assert it == 150 and info["checks"] == 3 and len(info["history"]) == 3
+    ch = _host(c)
+    e = g - orc.nudft_fwd(ch, y)
+    d_ref = np.linalg.norm(e) / np.linalg.norm(g)
+    r_ref = np.linalg.norm(orc.nudft_adj(e, y, N)) / np.linalg.norm(orc.nudft_adj(g, y, N))
+    assert abs(info["data_resid"] - d_ref) <= 1e-6 * d_ref
+    assert abs(res - r_ref) <= 1e-6 * r_ref
+    assert res == info["history"][-1]
+    assert info["history"][0] > info["history"][-1]
+
+
+def test_lsq_learned_weights_same_stopping_test(nf, orc):
+    """Weighted (learned density compensation) and plain solves stop on the
+    same unweighted residual, and both return c_true of consistent samples
+    on a well-sampled set."""
+    from paper_1611_09379_gb300 import dcf
+    N, M = 1 << 10, 1 << 12
+    y = workloads.points("uniform", M, seed=13)
+    c_true = workloads.coeffs(N, seed=14)
+    g = orc.nudft_fwd(c_true, y)
+    plan = nf.Plan(N, _dev(y), eps=1e-12)
+    w = plan.dcf_weights(dcf.load())
+    assert abs(float(w.double().mean()) - 1.0) < 1e-6
+    for ww in (None, w):
+        c, it, res = plan.solve_lsq(_dev(g), ww, tol=1e-10, maxit=3000)
+        assert res <= 1e-10
+        assert orc.rel_l2(_host(c), c_true) < 1e-8
+
+
+def test_inufft_one_shot_least_squares(nf, orc):
+    """inufft(g, y, M, N, eps) with M > N returns the least-squares solution
+    (plain CG through the library), equal to a dense solve; M < N is
+    rejected."""
+    import torch
+    N, M = 256, 1024
+    y = workloads.points("uniform", M, seed=15)
+    c_true = workloads.coeffs(N, seed=16)
+    g = orc.nudft_fwd(c_true, y) + 1e-3 * workloads.samples(M, seed=17)  # inconsistent data
+    c = _host(nf.inufft(_dev(g), _dev(y), M, N, 1e-12))
+    assert orc.rel_l2(c, orc.lsq_dense(g, y, N)) < 1e-9
+    with pytest.raises(nf.NufftError) as e:
+        nf.inufft(_dev(g[:100]), _dev(y[:100]), 100, N, 1e-12)
+    assert e.value.code == nf.EINVAL
+    del torch
+
+
+def test_lsq_workload_size_against_oracle(nf, orc):
+    """The least-squares workload at full size (N = 2^16, M = 2^18, 1:100
+    density contrast, consistent samples of a random band-limited c_true):
+    plain and learned-weight CG, each capped at 1200 iterations.  For both,
+    the reported data residual equals the oracle's ||g - A c|| / ||g|| over
+    all 2^18 points, A^H (g - A c) from the library's transforms equals the
+    oracle's on 512 sampled frequencies, and the reported normal-equation
+    residual agrees with the one estimated from those samples."""
+    import torch
+    from paper_1611_09379_gb300 import dcf
+    N, M = 1 << 16, 1 << 18
+    y = workloads.points("contrast", M, seed=1234)
+    c_true = workloads.coeffs(N, seed=99)
+    g = orc.nudft_fwd(c_true, y)
+    gd = _dev(g)
+    plan = nf.Plan(N, _dev(y), eps=1e-10)
+    w = plan.dcf_weights(dcf.load())
+    kdx = workloads.sample_index(N, 512, seed=8)
+    ahg_ref = orc.nudft_adj(g, y, N, kdx)
+    ahg = plan.adjoint(gd)
+    ahg_norm = float(torch.linalg.vector_norm(ahg))
+    assert orc.rel_l2(_host(ahg)[kdx], ahg_ref) < 1e-9
+    out = {}
+    for name, ww in (("plain", None), ("learned", w)):
+        c, it, res = plan.solve_lsq(gd, ww, tol=1e-8, maxit=1200, check=False, check_every=300)
+        info = dict(plan.lsq_info)
+        ch = _host(c)
+        e = g - orc.nudft_fwd(ch, y)
+        d_ref = np.linalg.norm(e) / np.linalg.norm(g)
+        assert abs(info["data_resid"] - d_ref) <= 1e-4 * d_ref, (name, info, d_ref)
+        u = _host(plan.adjoint(gd - plan.forward(c)))
+        u_ref = orc.nudft_adj(e, y, N, kdx)
+        assert np.linalg.norm(u[kdx] - u_ref) <= 1e-6 * np.linalg.norm(u_ref), name
+        assert abs(np.linalg.norm(u) / ahg_norm - res) <= 1e-4 * res, name
+        est = np.sqrt(N / kdx.size) * np.linalg.norm(u_ref) / ahg_norm
+        assert 0.5 * res <= est <= 2.0 * res, (name, est, res)
+        out[name] = (it, res, d_ref)
+    print("lsq at the workload size, 1200 iterations:", out)

@@ -21,7 +21,8 @@ def nf():
 def test_uneven_batch_graph(nf, orc):
     import torch
     rng = workloads.rng(12)
-    U = rng.integers(10, 14, size=24)  # N = M = 2^U, U in 10..13
+    U = rng.integers(10, 17, size=24)  # N = M = 2^U, U in 10..16 (the batched workload's range)
+    U[:2] = [10, 16]                   # both ends present
     Ns = [1 << int(u) for u in U]
     ys = [torch.from_numpy(workloads.points("uniform", n, seed=100 + i)).cuda() for i, n in enumerate(Ns)]
     cs_h = [workloads.coeffs(n, seed=200 + i).astype(np.complex64) for i, n in enumerate(Ns)]

@@ -315,6 +315,84 @@ def test_inverse_exact_hit(nf, orc):
     assert orc.rel_l2(c2, c) < 1e-12
 
 
+_LAMD_CACHE = {}
+
+
+def _lamD(orc, y, key):
+    if key not in _LAMD_CACHE:
+        _LAMD_CACHE[key] = orc.logsin_D(y)
+    return _LAMD_CACHE[key]
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_inverse_2p16_jitter_sampled(nf, orc, prec):
+    """Square inverse at N = M = 2^16 on the 40 % jittered grid (beyond the
+    paper's 10 % test): the grid values f_k of the library's result (f = N
+    IDFT(c)) against the oracle's Lagrange sum (Eq. p6 / p8, direct log-sums)
+    on 512 sampled k, relative to the modulus sum sum_j |L_kj| |g_j| at the
+    same k (reading c16); the round trip c against c_true as well."""
+    N = M = 1 << 16
+    y = workloads.points("jitter", M, N, seed=1616, jitter=0.4)
+    c = workloads.coeffs(N, seed=17)
+    g = orc.nudft_fwd(c, y)
+    eps = 1e-12 if prec == 0 else 1e-6
+    plan = nf.Plan(N, _dev(y), eps=eps, prec=prec, inverse=True)
+    c2 = _host(plan.inverse(_dev(g)))
+    f = np.fft.ifft(c2) * N  # f_k = sum_n c_n e^{2 pi i n k / N}
+    kdx = workloads.sample_index(N, 512, seed=3)
+    lamD = _lamD(orc, y, ("jitter", N))
+    fref = orc.inverse_f(g, y, N, kdx, lamD=lamD)
+    aref = orc.inverse_absf(g, y, N, kdx, lamD=lamD)
+    err = np.linalg.norm(f[kdx] - fref) / np.linalg.norm(aref)
+    assert err < TOL[prec], err
+    assert orc.rel_l2(f[kdx], fref) < 10 * TOL[prec]
+    assert orc.rel_l2(c2, c) < (1e-10 if prec == 0 else 1e-5)
+
+
+def test_inverse_clustered_is_out_of_range_at_2p16(nf, orc):
+    """On the clustered mixture the log-sums behind C_k and D_j span
+    thousands (the Lagrange weights of Eq. p8 are far outside binary64), so
+    the plan refuses the square inverse with NUFFT_EILLCOND; the forward on
+    the same points is unaffected."""
+    N = M = 1 << 16
+    y = workloads.points("clustered", M, seed=1617)
+    lD, _ = orc.logsin_D(y, workloads.sample_index(M, 64, seed=2))
+    assert lD.max() - lD.min() > 1500  # e^1500 is far beyond the binary64 range
+    with pytest.raises(nf.NufftError) as e:
+        nf.Plan(N, _dev(y), eps=1e-12, inverse=True)
+    assert e.value.code == nf.EILLCOND
+    plan = nf.Plan(N, _dev(y), eps=1e-12)
+    c = workloads.coeffs(N, seed=5)
+    g = _host(plan.forward(_dev(c)))
+    idx = workloads.sample_index(M, 256, seed=4)
+    assert orc.rel_l2(g[idx], orc.nudft_fwd(c, y, idx)) < 1e-12
+
+
+@pytest.mark.parametrize("prec,N", [(0, 512), (1, 128)])
+def test_inverse_clustered_small_matvec(nf, orc, prec, N):
+    """Clustered points where the Lagrange weights still fit the arithmetic
+    (log-sums within about +-210 at N = 512 for binary64, +-45 at N = 128 for
+    the mixed path's binary32 copies): the inverse's matrix-vector product
+    f = L g (Eq. p6) against the oracle's, relative to sum_j |L_kj| |g_j|
+    (reading c16); the problem is too ill-conditioned for the round trip to
+    be asserted.  At N = 512 the mixed path refuses (NUFFT_EILLCOND)."""
+    M = N
+    y = workloads.points("clustered", M, seed=33)
+    g = workloads.samples(M, seed=34)
+    eps = 1e-12 if prec == 0 else 1e-6
+    plan = nf.Plan(N, _dev(y), eps=eps, prec=prec, inverse=True)
+    c2 = _host(plan.inverse(_dev(g)))
+    f = np.fft.ifft(c2) * N
+    fref = orc.inverse_f(g, y, N)
+    aref = orc.inverse_absf(g, y, N)
+    assert np.linalg.norm(f - fref) / np.linalg.norm(aref) < TOL[prec]
+    if prec == 1:
+        y5 = workloads.points("clustered", 512, seed=33)
+        with pytest.raises(nf.NufftError) as e:
+            nf.Plan(512, _dev(y5), eps=1e-6, prec=prec, inverse=True)
+        assert e.value.code == nf.EILLCOND
+
+
 # ------------------------------------------------------------------ full size (sampled)
 
 @pytest.mark.parametrize("prec,kind", [(0, "uniform"), (1, "uniform"), (0, "jitter"), (1, "clustered")])

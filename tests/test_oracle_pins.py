@@ -97,7 +97,7 @@ def _exact_expi(m, y):
     return complex(math.cos(r), math.sin(r))
 
 
-@pytest.mark.parametrize("N", [8, 256, 1 << 16])
+@pytest.mark.parametrize("N", [8, 256, 1 << 16, 1000])
 def test_nudft_reproduces_single_mode(orc, N):
     """c = e_m gives g_j = e^{i m y_j} exactly (band-limited series, Eq. p1)."""
     y = workloads.points("uniform", 64 if N < 65536 else 8, seed=3)
@@ -109,11 +109,12 @@ def test_nudft_reproduces_single_mode(orc, N):
         assert np.abs(g - ref).max() < 4e-16 * max(1, 8)
 
 
-@pytest.mark.parametrize("L", [3, 6, 10, 12])
-def test_kernel_form_constant_function(orc, L):
+@pytest.mark.parametrize("N", [8, 64, 1024, 4096, 12, 100, 1000, 3 * 1024])
+def test_kernel_form_constant_function(orc, N):
     """The paper's analytic test (Sec. 3.1): f == 1 gives g_j = 1 exactly, for
-    random y and for y on or next to grid points (Eq. p4 with the 1/N of p5)."""
-    N = 1 << L
+    random y and for y on or next to grid points (Eq. p4 with the 1/N of p5);
+    the identity holds for every grid size N, powers of two or not."""
+    L = N.bit_length()
     y = workloads.points("uniform", 200, seed=L)
     k = np.arange(0, N, max(1, N // 16))
     xk = k * (2 * math.pi / N)
@@ -124,20 +125,30 @@ def test_kernel_form_constant_function(orc, L):
     assert np.abs(g - 1.0).max() < 1e-14
 
 
-@pytest.mark.parametrize("N", [16, 1024, 4096])
+def _exact_cot_half(N, y):
+    """N cot(N y / 2) with N y / 2 reduced modulo pi into [-pi/2, pi/2] in
+    exact rationals (so a result near a pole keeps its relative precision)."""
+    pi = _pi_frac()
+    a = Fraction(N) * Fraction(y) / 2
+    r = float(a - pi * round(a / pi))
+    return N / math.tan(r)
+
+
+@pytest.mark.parametrize("N", [16, 1024, 4096, 12, 1000, 3 * 1024])
 def test_cot_sum_closed_form(orc, N):
     """sum_k cot((y - 2 pi k/N)/2) = N cot(N y/2): pins G and the compensated
-    difference y - x_k, including y within an ulp of a grid point."""
+    difference y - x_k (a double-double 2 pi / N for any N), including y
+    within an ulp of a grid point."""
     y = workloads.points("uniform", 100, seed=N)
     k = np.arange(1, N, max(1, N // 8))
     xk = k * (2 * math.pi / N)
     y = np.concatenate([y, np.nextafter(xk, 10.0), np.nextafter(xk, -10.0)])
     h = orc.cot_sum(np.ones(N), y)
-    ref = N / np.tan(N * y / 2)  # N*y exact for N = 2^L
+    ref = np.array([_exact_cot_half(N, v) for v in y])
     assert np.all(np.abs(h - ref) <= 1e-13 * np.maximum(np.abs(ref), N))
 
 
-@pytest.mark.parametrize("N,M", [(64, 50), (1024, 300), (4096, 64)])
+@pytest.mark.parametrize("N,M", [(64, 50), (1024, 300), (4096, 64), (100, 80), (1000, 300)])
 def test_two_forward_routes_agree(orc, N, M):
     """Direct NUDFT (Eq. p1) and the factored kernel form (Eq. p2/p4) agree."""
     c = workloads.coeffs(N, seed=N)
@@ -147,7 +158,7 @@ def test_two_forward_routes_agree(orc, N, M):
     assert orc.rel_l2(g2, g1) < 1e-13
 
 
-@pytest.mark.parametrize("N", [8, 32, 64])
+@pytest.mark.parametrize("N", [8, 32, 64, 12, 30])
 def test_dense_kernel_matrix(orc, N):
     """Columns of the factored form equal the geometric sum of Eq. p2 and the
     Dirichlet closed form (reading c1: F_j carries the 1/N)."""
@@ -236,7 +247,7 @@ def test_threshold_error_grows_with_n(orc):
 
 # ------------------------------------------------------------- inverse
 
-@pytest.mark.parametrize("N", [16, 256])
+@pytest.mark.parametrize("N", [16, 256, 12, 100])
 def test_logsin_equispaced_closed_form(orc, N):
     """y_l = 2 pi l/N + phi: prod_l 2 sin((x - y_l)/2) = +-2 sin(N (x - phi)/2)
     and prod_{l!=j} 2 sin((y_j - y_l)/2) = +-N, which pin the log-sums and the
@@ -251,7 +262,8 @@ def test_logsin_equispaced_closed_form(orc, N):
     assert np.array_equal(nD, N - 1 - np.arange(N))
 
 
-@pytest.mark.parametrize("N,jit", [(32, 0.1), (128, 0.1), (256, 0.1), (64, 0.4)])
+@pytest.mark.parametrize("N,jit", [(32, 0.1), (128, 0.1), (256, 0.1), (64, 0.4), (30, 0.1),
+                                   (100, 0.1)])
 def test_inverse_round_trip_and_dense_solve(orc, N, jit):
     """At M = N the Lagrange form (Eq. p6, p8) inverts the forward transform:
     inufft(nudft_fwd(c)) = c, equal to a dense LU solve of A c = g."""

@@ -38,6 +38,12 @@ def test_noalloc_matches_allocating_entry_point(nf):
         (1 << 16, 1 << 16, "clustered", nf.MIXED, 1e-6, 2),
         (4096, 3000, "uniform", nf.FP64, 1e-12, 3),
         (1 << 16, 1 << 15, "uniform", nf.FP64, 1e-12, 4),
+        # few points against the largest grid (leaves of at most 64 grid points)
+        (1 << 16, 1000, "uniform", nf.FP64, 1e-12, 5),
+        (1 << 16, 1, "uniform", nf.MIXED, 1e-6, 6),
+        # the largest orders at the largest sizes (the most scratch)
+        (1 << 16, 1 << 16, "uniform", nf.FP64, 1e-15, 7),
+        (1 << 16, 1 << 16, "clustered", nf.FP64, 1e-12, 8),
     ]
     tol = {nf.FP64: 1e-12, nf.MIXED: 1e-6}
     for N, M, kind, prec, eps, seed in cases:
@@ -49,6 +55,10 @@ def test_noalloc_matches_allocating_entry_point(nf):
         torch.cuda.synchronize()
         assert g.data_ptr() == out.data_ptr()
         assert _rel(g.cpu().numpy(), ref.cpu().numpy()) < tol[prec], (N, M, kind, prec)
+        # a second call in a row on the same inputs reuses the shared array
+        g2 = nf.nufft_fwd_noalloc(c, N, y, M, eps, prec, out=torch.empty_like(out))
+        torch.cuda.synchronize()
+        assert _rel(g2.cpu().numpy(), ref.cpu().numpy()) < tol[prec], (N, M, kind, prec)
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch(nf):
