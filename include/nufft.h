@@ -28,9 +28,9 @@
  *     series with N' terms whose top N' - N coefficients are zero, so the
  *     forward, adjoint and least-squares results are the same sums (inputs
  *     are zero padded and outputs truncated inside the FFT passes).  The
- *     square inverse (Eq. p6 / p8 on the grid of its own N points) needs N a
- *     power of two; other N give NUFFT_ENOTSUP there.  Grid quantities of a
- *     plan (leaves, k0, delta, C_k) are on the N' grid.
+ *     square inverse evaluates its interpolant (Eq. p6 / p8 with N points)
+ *     at the N' grid points, whose N'-point DFT gives the N coefficients.
+ *     Grid quantities of a plan (leaves, k0, delta, C_k) are on the N' grid.
  *   - y_j must be finite and in [0, 2 pi) (binary64 2 pi excluded).
  *   - All work is enqueued on the plan's CUDA stream and is asynchronous;
  *     a return of NUFFT_OK means the work was enqueued without error.
@@ -117,9 +117,22 @@ int nufft_version(void);
 /* Parameter choice of a plan without creating it (no GPU needed); the tree
  * depth refers to the grid N' = 2^ceil(log2 N).
  * in/out: *params (fields <= 0 are filled in).  Returns NUFFT_EINVAL for an
- * invalid N, M, eps or prec.  eps must lie in [1e-15, 1e-1]. */
+ * invalid N, M, eps or prec.  eps must lie in [1e-15, 1e-1], or be 0 with
+ * NUFFT_FP64: machine precision, the threshold error nufft_eps_threshold(N)
+ * taken as the prescribed accuracy (the second setting of Sec. 3.2); every
+ * call that takes eps accepts the same values. */
 int nufft_choose_params(int64_t N, int64_t M, double eps, int prec,
                         nufft_params *params);
+
+/* Threshold ("machine precision") error eps_th(N) of the FP64 path (Sec.
+ * 3.1): the value at which the error of the paper's f = 1 test, max_j
+ * |g_j - 1|, stops falling as eps is lowered, modelled as log2(N') 2^-53
+ * (measured on GB300 for N = 2^8 .. 2^22 with uniform points: 0.8e-15 ..
+ * 2.2e-15, each within 20 % below the model), at least 1e-15.  The
+ * straightforward method of Sec. 3.1 (Eq. p4 in plain binary64) has a far
+ * larger threshold; this one comes from the exact grid coordinates.  Returns
+ * -1 for N outside [8, 2^26].  Host only. */
+double nufft_eps_threshold(int64_t N);
 
 /* ---------------------------------------------------------------- autotuner */
 
@@ -188,8 +201,7 @@ int nufft_autotune(int64_t N, int64_t M, const double *y, double eps, int prec,
  *   stream           cudaStream_t to run on (NULL = legacy default stream)
  * Synchronises the stream (it reads back validation flags).  Errors:
  * EINVAL (bad sizes / eps / y), EILLCOND (inverse requested with duplicate
- * points or coefficients outside the exponent range), ENOTSUP (inverse
- * requested for N not a power of two), ENOMEM, ECUDA. */
+ * points or coefficients outside the exponent range), ENOMEM, ECUDA. */
 int nufft_plan_create(nufft_plan *out, int64_t N, int64_t M, const double *y,
                       double eps, int prec, const nufft_params *params,
                       unsigned flags, void *stream);
@@ -222,8 +234,10 @@ int nufft_plan_points(nufft_plan plan, int32_t *perm, int32_t *leaf_start,
 /* Copy the inverse coefficients of a plan made with NUFFT_WANT_INVERSE.
  * With lamC_k = sum_l log|2 sin((x_k - y_l)/2)|, lamD_j = -sum_{l!=j}
  * log|2 sin((y_j - y_l)/2)|, nC_k = #{l: y_l > x_k}, nD_j = #{l: y_l > y_j}:
- *   Ct     [device] double[N]   (-1)^(k + nC_k) e^{lamC_k + Lambda} / N
- *                               (0 where a point sits exactly on x_k)
+ *   Ct     [device] double[N']  (-1)^(k + nC_k) e^{lamC_k + Lambda} / N'
+ *                               (0 where a point sits exactly on x_k); for
+ *                               N < N' the sign is (-1)^(nC_k) and C_k has
+ *                               the further phase e^{i pi k N / N'}
  *   Dt     [device] double2[M]  (-1)^nD_j e^{lamD_j - Lambda} i e^{-i N y_j/2}
  *                               (sorted point order, see nufft_plan_points)
  *   Lambda [host]   the common scale, the midpoint of the range of lamD

@@ -46,7 +46,7 @@ SYMBOLS = [
     "nufft_mlp_num_params", "nufft_mlp_set_params", "nufft_mlp_get_params", "nufft_mlp_infer",
     "nufft_mlp_grad", "nufft_mlp_train_step", "nufft_multi_create", "nufft_multi_exec_fwd",
     "nufft_multi_destroy", "nufft_autotune", "nufft_plan_dcf_weights", "nufft_diag_rcp",
-    "nufft_diag_pipe_rates",
+    "nufft_diag_pipe_rates", "nufft_eps_threshold",
 ]
 
 
@@ -102,6 +102,8 @@ _lib.nufft_plan_solve_lsq.argtypes = [_P, _P, _P, ctypes.c_uint, ctypes.c_double
                                       ctypes.c_int, _P, ctypes.POINTER(LsqInfo)]
 LSQ_WEIGHTED = 0x1
 _lib.nufft_plan_dcf_weights.argtypes = [_P, _P, _P]
+_lib.nufft_eps_threshold.argtypes = [_I64]
+_lib.nufft_eps_threshold.restype = ctypes.c_double
 _lib.nufft_diag_rcp.argtypes = [_P, _I64, _P, _P, _P]
 _lib.nufft_diag_pipe_rates.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), _P]
 _lib.nufft_plan_stats.argtypes = [_P, _P, _P]
@@ -117,7 +119,7 @@ for _n in ("nufft_fwd", "nufft_fwd_noalloc"):
 for _n in ("nufft_adj", "inufft"):
     getattr(_lib, _n).argtypes = [_P, _P, _I64, _I64, ctypes.c_double, ctypes.c_int, ctypes.c_uint, _P, _P]
 for _n in SYMBOLS:
-    if _n not in ("nufft_strerror", "nufft_version"):
+    if _n not in ("nufft_strerror", "nufft_version", "nufft_eps_threshold"):
         getattr(_lib, _n).restype = ctypes.c_int
 
 
@@ -139,6 +141,18 @@ def strerror(code: int) -> str:
 
 def version() -> int:
     return _lib.nufft_version()
+
+
+MACHINE_EPS = 0.0  # eps value of the machine-precision mode (FP64)
+
+
+def eps_threshold(N: int) -> float:
+    """Threshold ("machine precision") error of the FP64 path for N coefficients
+    (Sec. 3.1), the accuracy eps = 0 prescribes."""
+    v = _lib.nufft_eps_threshold(int(N))
+    if v < 0:
+        raise NufftError(EINVAL, "nufft_eps_threshold")
+    return v
 
 
 def choose_params(N: int, M: int, eps: float, prec: int = FP64, lmax: int = 0, p: int = 0, q: int = 0):

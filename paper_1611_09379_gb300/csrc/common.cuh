@@ -114,7 +114,20 @@ struct TreeDims {
   // 2/N, 1/s, N/pi, N/(2 pi) in both precisions
   double two_n = 0, inv_s = 0, n_pi = 0, n_2pi = 0;
   float two_n_f = 0, inv_s_f = 0, n_pi_f = 0, n_2pi_f = 0;
+  // square inverse with Nc = nc coefficients on this grid (nc < N): C at the
+  // grid point k carries the phase e^{i pi k nc / N} (0: the phase is the
+  // sign (-1)^k, already in C)
+  int64_t nc = 0;
 };
+
+// e^{i pi (k nc mod 2N) / N}, the phase of C(x_k) of the square inverse on a
+// grid of N > nc points (the argument reduced exactly in integers)
+__device__ inline double2 inv_phase(const TreeDims& d, int64_t k) {
+  const int64_t a = (k * d.nc) % (2 * d.N);
+  double s, c;
+  sincospi((double)a / (double)d.N, &s, &c);
+  return make_double2(c, s);
+}
 
 template <class T> struct KConst;
 template <> struct KConst<double> {
@@ -231,6 +244,7 @@ struct nufft_plan_s {
   double *Ct = nullptr;           // [N] real C_k e^{+Lambda} / N
   float *Ctf = nullptr;           // [N] FP32 copy (mixed path)
   double *Lambda = nullptr;       // [1] common scale of C and D
+  int64_t inv_nc = 0;             // Nc when C carries the phase e^{i pi k Nc / N} (Nc < N)
   // FMM workspace
   void *mexp = nullptr;    // [levels 2..L][box][pm] complex (T)
   void *lexp = nullptr;    // [levels 3..L][box][p] complex (T)
@@ -274,11 +288,14 @@ struct nufft_plan_s {
   // side branch: work the main chain does not wait for at once (level-2
   // coefficients, self terms) runs on `aux`, forked and joined by events
   cudaStream_t aux = nullptr;
-  cudaEvent_t ev_fork[2] = {}, ev_join[2] = {};
+  cudaStream_t aux2 = nullptr;   // slot 2: the near field, beside the tree passes
+  cudaEvent_t ev_fork[3] = {}, ev_join[3] = {};
   int side_ok = 1;               // 0: keep everything on `stream`
+  void *hnear = nullptr;         // near-field sums of one signal (2 max(N, M) complex):
+                                 //     forward [M], adjoint / inverse [N][2] (sum, self terms)
 };
 
-// Begin a side branch (slot 0 or 1): returns the stream to launch it on --
+// Begin a side branch (slot 0, 1 or 2; slot 2 has a stream of its own): returns the stream to launch it on --
 // `aux` after it waits for the work issued so far on the plan's stream, or
 // the plan's stream itself while profiling (per-stage events need one
 // stream order) or when the side stream cannot be made.  side_end marks the

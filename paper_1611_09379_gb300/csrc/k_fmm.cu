@@ -1072,13 +1072,16 @@ __device__ inline void near_window_ex2w(int n, int ex, NearAcc2f& acc, Term term
 // memory instead.  All arithmetic in T (F_j, E_j were formed in FP64 at plan
 // time).  Signal g of the group: blockIdx.y * G + g; per-signal strides N
 // (grid), M (output), d.lstride (locals), 4 (2q) + 1 (level-2 coefficients).
+// Split evaluation: with hout set the kernel forms the near-field sums only
+// and stores them to hout (it needs the grid samples alone, so it can run
+// beside the tree passes); with hnear set it skips them and reads them there.
 template <class T, class VO, int G>
 __global__ void __launch_bounds__(kTgtThreads) k_targets_fwd(
     TreeDims d, int M, const int32_t* __restrict__ k0s, const double* __restrict__ dels,
     const T* __restrict__ dels_t, const int32_t* __restrict__ perm, const cplx<T>* __restrict__ F,
     const cplx<T>* __restrict__ E, const cplx<T>* __restrict__ fgrid,
     const cplx<T>* __restrict__ lexp, const cplx<T>* __restrict__ lvl2,
-    const cplx<T>* __restrict__ hnear, VO* __restrict__ g) {
+    const cplx<T>* __restrict__ hnear, VO* __restrict__ g, cplx<T>* __restrict__ hout) {
   pdl_wait();
   pdl_trigger();
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -1180,6 +1183,11 @@ __global__ void __launch_bounds__(kTgtThreads) k_targets_fwd(
       for (int gg = 0; gg < G; ++gg) acc[gg].add_r(fgrid[(int64_t)gg * N + k], r);
     });
   }
+  if (hout) {  // near field only: the rest runs once the tree passes are done
+#pragma unroll
+    for (int gg = 0; gg < G; ++gg) hout[(int64_t)(sig0 + gg) * M + j] = acc[gg].get();
+    return;
+  }
   const int base = b * s;
   const int Q2 = 2 * d.q;  // cot kernel: degree 2q-1
   const int arc = b >> (d.L - 2);
@@ -1243,7 +1251,7 @@ __global__ void k_charges(int64_t M, const int32_t* __restrict__ perm,
 //   The FP32 path forms Ct_k0 / delta_j in FP32 when |delta_j| >= 2^-20 and
 //   |Ct_k0| >= 2^-100 (no underflow or overflow on the way), else in FP64.
 template <class T, class VI>
-__global__ void k_self_terms(int M, int inverse, int N, const int32_t* __restrict__ k0s,
+__global__ void k_self_terms(int M, int inverse, int N, TreeDims dd, const int32_t* __restrict__ k0s,
                              const double* __restrict__ dels, const int32_t* __restrict__ perm,
                              const cplx<T>* __restrict__ E, const cplx<T>* __restrict__ charge,
                              const VI* __restrict__ gin, const double* __restrict__ Ct,
@@ -1267,7 +1275,9 @@ __global__ void k_self_terms(int M, int inverse, int N, const int32_t* __restric
     if (fabs(dt) >= (T)9.5367431640625e-07 && fabs(ct) >= (T)7.888609052210118e-31) {
       const cplx<T> q = charge[i];
       const T w = (ct / dt) * n_2pi;
-      st[i] = mk<T>(-q.y * w, q.x * w);
+      cplx<T> v = mk<T>(-q.y * w, q.x * w);
+      if (dd.nc) v = cmul(v, from_d2<T>(inv_phase(dd, k0)));
+      st[i] = v;
       return;
     }
   }
@@ -1279,6 +1289,7 @@ __global__ void k_self_terms(int M, int inverse, int N, const int32_t* __restric
     double2 q = to_d2(charge[i]);
     double w = Ct[k0] * (0.5 * (double)N * kInvPi) / d;
     v = make_double2(-q.y * w, q.x * w);
+    if (dd.nc) v = cmul(v, inv_phase(dd, k0));  // an exact hit takes g_j itself, no phase
   }
   st[i] = from_d2<T>(v);
 }
@@ -1442,7 +1453,10 @@ __global__ void __launch_bounds__(kTgtThreads) k_targets_grid(
     T hr = cN * fma(far.x, ts, nr.x) - c2 * reg.x;
     T hi = cN * fma(far.y, ts, nr.y) - c2 * reg.y;
     cplx<T> res = mk<T>((T)-0.5 * (Qs.x - hi), (T)-0.5 * (Qs.y + hr));
-    if (inverse) res = cscale(res, Ct[k]);
+    if (inverse) {
+      res = cscale(res, Ct[k]);
+      if (d.nc) res = cmul(res, from_d2<T>(inv_phase(d, k)));
+    }
     out[(int64_t)sig * N + k] = cadd(res, self[gg]);
   }
 }
@@ -1623,7 +1637,10 @@ __global__ void __launch_bounds__(kTgtThreads, sizeof(T) == 4 ? 5 : 4) k_targets
     const T hr = cN * fma(far.x, ts, nr.x) - c2 * reg.x;
     const T hi = cN * fma(far.y, ts, nr.y) - c2 * reg.y;
     cplx<T> res = mk<T>((T)-0.5 * (Qs.x - hi), (T)-0.5 * (Qs.y + hr));
-    if (inverse) res = cscale(res, Ct[kk]);
+    if (inverse) {
+      res = cscale(res, Ct[kk]);
+      if (d.nc) res = cmul(res, from_d2<T>(inv_phase(d, kk)));
+    }
     out[kk] = cadd(res, h ? self1 : self0);
   }
 }
@@ -1744,7 +1761,10 @@ __global__ void __launch_bounds__(kTgtThreads) k_targets_gridw(
   const T hr = cN * fma(far.x, ts, v[0].x) - c2 * reg.x;
   const T hi = cN * fma(far.y, ts, v[0].y) - c2 * reg.y;
   cplx<T> res = mk<T>((T)-0.5 * (Qs.x - hi), (T)-0.5 * (Qs.y + hr));
-  if (inverse) res = cscale(res, Ct[k]);
+  if (inverse) {
+    res = cscale(res, Ct[k]);
+    if (d.nc) res = cmul(res, from_d2<T>(inv_phase(d, k)));
+  }
   out[k] = cadd(res, self);
 }
 
@@ -1859,6 +1879,7 @@ TreeDims dims_of(const nufft_plan_s* pl) {
   d.inv_s_f = (float)d.inv_s;
   d.n_pi_f = (float)d.n_pi;
   d.n_2pi_f = (float)d.n_2pi;
+  d.nc = pl->inv_nc;
   return d;
 }
 
@@ -2098,11 +2119,21 @@ static FmmOps cot_ops(nufft_plan_s* pl) {
 
 template <class T, class VO, int G>
 static void launch_targets_fwd(nufft_plan_s* pl, const TreeDims& d, const cplx<T>* f,
-                               const cplx<T>* hnear, void* g) {
+                               const cplx<T>* hnear, void* g, cplx<T>* hout = nullptr,
+                               cudaStream_t st = nullptr) {
   dim3 grid(nblk(pl->M, kTgtThreads), (unsigned)(pl->batch / G));
-  launch_pdl(k_targets_fwd<T, VO, G>, grid, kTgtThreads, NearCap<T, G>::fwd_bytes, pl->stream, d,
-             (int)pl->M, pl->k0, pl->delta, PlanT<T>::delta(pl), pl->perm, PlanT<T>::F(pl),
-             PlanT<T>::E(pl), f, (const cplx<T>*)pl->lexp, PlanT<T>::lvl2(pl), hnear, (VO*)g);
+  launch_pdl(k_targets_fwd<T, VO, G>, grid, kTgtThreads, hnear ? 0 : NearCap<T, G>::fwd_bytes,
+             st ? st : pl->stream, d, (int)pl->M, pl->k0, pl->delta, PlanT<T>::delta(pl),
+             pl->perm, PlanT<T>::F(pl), PlanT<T>::E(pl), f, (const cplx<T>*)pl->lexp,
+             PlanT<T>::lvl2(pl), hnear, (VO*)g, hout);
+}
+
+// Split target evaluation: the near-field sums on side branch 2 while the
+// tree passes run (one signal, no tensor-core near field; NUFFT_NO_SPLIT_NEAR
+// keeps the single fused launch after the tree passes).
+static bool split_near(const nufft_plan_s* pl) {
+  static const bool off = std::getenv("NUFFT_NO_SPLIT_NEAR") != nullptr;
+  return !off && pl->batch == 1 && pl->tc_near <= 0 && pl->hnear && pl->side_ok;
 }
 
 int near_tc_forward(const TreeDims& d, int M, int batch, const int32_t* k0s, const double* dels,
@@ -2113,14 +2144,25 @@ int near_tc_forward(const TreeDims& d, int M, int batch, const int32_t* k0s, con
 template <class T>
 int fmm_forward(nufft_plan_s* pl, void* g) {
   const cplx<T>* f = (const cplx<T>*)pl->grid;
+  const TreeDims d = dims_of(pl);
+  const bool split = split_near(pl);
+  const bool c64 = (pl->flags & NUFFT_IO_C64) != 0;
+  if (split) {  // near field beside the tree passes (it needs f only)
+    prof_begin(pl, NUFFT_STAGE_TARGETS);
+    cudaStream_t s2 = side_begin(pl, 2);
+    if (c64) launch_targets_fwd<T, float2, 1>(pl, d, f, nullptr, g, (cplx<T>*)pl->hnear, s2);
+    else launch_targets_fwd<T, double2, 1>(pl, d, f, nullptr, g, (cplx<T>*)pl->hnear, s2);
+    side_end(pl, 2, s2);
+    prof_end(pl, 1);
+  }
   int rc = fmm_upward_downward<T>(pl, cot_ops(pl), true, f, pl->lvl2,
                                   sizeof(T) == 4 ? pl->lvl2f : nullptr);
   if (rc) return rc;
-  const TreeDims d = dims_of(pl);
   const bool g4 = (pl->batch % 4) == 0;
+  if (split) side_join(pl, 2);
   prof_begin(pl, NUFFT_STAGE_TARGETS);
   // batches of 64 signals: near-field sums on the tensor cores first
-  const cplx<T>* hnear = nullptr;
+  const cplx<T>* hnear = split ? (const cplx<T>*)pl->hnear : nullptr;
   if constexpr (std::is_same<T, float>::value) {
     if (pl->tc_near > 0) {
       int rc2 = near_tc_forward(d, (int)pl->M, pl->batch, pl->k0, pl->delta, pl->delta_f,
@@ -2180,11 +2222,11 @@ int fmm_to_grid(nufft_plan_s* pl, const void* g, int inverse) {
   prof_begin(pl, NUFFT_STAGE_OTHER);
   cudaStream_t s1 = side_begin(pl, 1);
   if (c64)
-    launch_pdl(k_self_terms<T, float2>, gm, 256, 0, s1, (int)pl->M, inverse, (int)pl->N, pl->k0,
+    launch_pdl(k_self_terms<T, float2>, gm, 256, 0, s1, (int)pl->M, inverse, (int)pl->N, d, pl->k0,
                pl->delta, pl->perm, PlanT<T>::E(pl), charge, (const float2*)g, pl->Ct,
                PlanT<T>::Ct(pl), PlanT<T>::delta(pl), KConst<T>::n_2pi_h(d), stt);
   else
-    launch_pdl(k_self_terms<T, double2>, gm, 256, 0, s1, (int)pl->M, inverse, (int)pl->N, pl->k0,
+    launch_pdl(k_self_terms<T, double2>, gm, 256, 0, s1, (int)pl->M, inverse, (int)pl->N, d, pl->k0,
                pl->delta, pl->perm, PlanT<T>::E(pl), charge, (const double2*)g, pl->Ct,
                PlanT<T>::Ct(pl), PlanT<T>::delta(pl), KConst<T>::n_2pi_h(d), stt);
   side_end(pl, 1, s1);

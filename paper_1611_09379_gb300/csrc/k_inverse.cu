@@ -16,6 +16,16 @@
 //   sum_l S(x - 2 pi (l + 1/2)/N) = log|2 cos(N x / 2)|
 // (the product identity of equispaced sines), added back at the end.  Box
 // charges are then nearly neutral and the FP64 sums stay at the 1e-14 level.
+//
+// Nc points on a larger grid (Nc < N, N = 2^ceil(log2 Nc): the inverse for
+// Nc coefficients of a general size): the interpolant is the same, and the
+// Lagrange form holds at any x with C(x) = e^{i Nc x / 2} prod_l sin((x -
+// y_l)/2) and D_j = 2i e^{-i Nc y_j / 2} / prod_{l != j} sin((y_j - y_l)/2),
+// so it is evaluated at the N grid points (whose N-point DFT gives the first
+// Nc coefficients exactly).  C keeps its sign (-1)^{nC_k} here and the phase
+// e^{i pi k Nc / N} is applied by the target kernels; the half-grid charges
+// weigh Nc / N each (total -Nc, the boxes stay neutral) and their closed
+// forms scale by the same weight.
 #include <cmath>
 #include <vector>
 
@@ -72,7 +82,7 @@ __device__ inline int64_t kk_of(int32_t k0, double d, int64_t N) {
 __global__ void k_logsum_grid(TreeDims d, const int32_t* __restrict__ start,
                               const int32_t* __restrict__ k0s, const double* __restrict__ dels,
                               const double2* __restrict__ lexp, const double2* __restrict__ lvl2,
-                              const double* __restrict__ hg, int64_t M,
+                              const double* __restrict__ hg, int64_t M, double wc,
                               double* __restrict__ lamC, int32_t* __restrict__ nC) {
   int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t N = d.N;
@@ -98,8 +108,9 @@ __global__ void k_logsum_grid(TreeDims d, const int32_t* __restrict__ start,
   int64_t arc = b >> (d.L - 2);
   double uh = (double)(k - arc * (N >> 2) - (N >> 3)) * (2.0 / (double)N);
   double reg = horner_re(lvl2 + arc * nq, nq, uh);
-  // closed form of the half-grid sum at x_k: log|2 cos(pi k)| = log 2
-  double lam = far + (lp.get() - hg[o]) + reg + 0.6931471805599453;
+  // closed form of the half-grid sum at x_k: log|2 cos(pi k)| = log 2 (times
+  // the half-grid charge weight wc; hg is weighted already)
+  double lam = far + (lp.get() - hg[o]) + reg + wc * 0.6931471805599453;
   lamC[k] = hit ? -INFINITY : lam;
   // nC_k = #{Y_l > k}: all points of later leaves plus those of leaf b above k
   int32_t cnt = (int32_t)(M - start[b + 1]);
@@ -121,8 +132,8 @@ __device__ inline void two_sum(double a, double b, double* hi, double* lo) {
 __global__ void k_logsum_pts(TreeDims d, const int32_t* __restrict__ start,
                              const int32_t* __restrict__ k0s, const double* __restrict__ dels,
                              const double2* __restrict__ lexp, const double2* __restrict__ lvl2,
-                             int64_t M, double* __restrict__ lamD, int32_t* __restrict__ nD,
-                             int* __restrict__ status) {
+                             int64_t M, double wc, double* __restrict__ lamD,
+                             int32_t* __restrict__ nD, int* __restrict__ status) {
   int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= M) return;
   const int64_t N = d.N;
@@ -163,7 +174,7 @@ __global__ void k_logsum_pts(TreeDims d, const int32_t* __restrict__ start,
   // point's own charge added c1 = log(2 pi/N) to the constant term.
   double cf = log(2.0 * cospi(dj));
   double c1 = log(kTwoPiHi / (double)N);
-  double S = far + (lp.get() - lh.get()) + reg + cf - c1;
+  double S = far + (lp.get() - wc * lh.get()) + reg + wc * cf - c1;
   lamD[j] = -S;
   if (dup) atomicOr(status, kDevIllCond);
   // nD_j = #{Y_l > Y_j}
@@ -203,9 +214,11 @@ constexpr double kExpLimit = 700.0;
 
 // Ctf (optional): FP32 copy for the mixed path, whose exponent limit elim
 // keeps C_k e^Lambda / N inside the FP32 range.
+// phase_sep: the phase of C(x_k) is applied by the target kernels (Nc < N),
+// so only the sign of the sine product is kept here.
 __global__ void k_assemble_C(const double* __restrict__ lamC, const int32_t* __restrict__ nC,
                              int64_t N, const double* __restrict__ Lam, double elim,
-                             double* __restrict__ Ct, float* __restrict__ Ctf,
+                             int phase_sep, double* __restrict__ Ct, float* __restrict__ Ctf,
                              int* __restrict__ status) {
   int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (k >= N) return;
@@ -214,7 +227,7 @@ __global__ void k_assemble_C(const double* __restrict__ lamC, const int32_t* __r
   if (l != -INFINITY) {
     double e = l + *Lam;
     if (!(fabs(e) < elim)) atomicOr(status, kDevIllCond);
-    double sg = ((k + nC[k]) & 1) ? -1.0 : 1.0;
+    double sg = (((phase_sep ? 0 : k) + nC[k]) & 1) ? -1.0 : 1.0;
     v = sg * exp(e) / (double)N;  // with the 1/N of Eq. p1
   }
   Ct[k] = v;
@@ -223,20 +236,33 @@ __global__ void k_assemble_C(const double* __restrict__ lamC, const int32_t* __r
 
 // elim: largest |exponent| of D_j e^{-Lambda} (the mixed path forms the
 // charges D_j g_j in FP32, so it allows less than FP64 range).
+// nc, N: the points' count and the grid (nc = N: a power-of-two inverse)
 __global__ void k_assemble_D(const double* __restrict__ lamD, const int32_t* __restrict__ nD,
                              const int32_t* __restrict__ k0s, const double* __restrict__ dels,
-                             int64_t M, const double* __restrict__ Lam, double elim,
-                             double2* __restrict__ Dt, float2* __restrict__ Dtf,
+                             int64_t M, int64_t nc, int64_t N, const double* __restrict__ Lam,
+                             double elim, double2* __restrict__ Dt, float2* __restrict__ Dtf,
                              int* __restrict__ status) {
   int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= M) return;
   double e = lamD[j] - *Lam;
   if (!(fabs(e) < elim)) atomicOr(status, kDevIllCond);
   double mag = exp(e);
-  if ((nD[j] + k0s[j]) & 1) mag = -mag;
   double sn, cs;
-  sincospi(dels[j], &sn, &cs);
-  // i e^{-i N y_j / 2} = (-1)^k0 (sin(pi delta) + i cos(pi delta))
+  if (nc == N) {
+    // i e^{-i N y_j / 2} = (-1)^k0 (sin(pi delta) + i cos(pi delta))
+    if ((nD[j] + k0s[j]) & 1) mag = -mag;
+    sincospi(dels[j], &sn, &cs);
+  } else {
+    // i e^{-i nc y_j / 2} = sin(pi a) + i cos(pi a), a = (nc / N)(k0 + delta):
+    // the integer part (nc k0 mod 2N) / N exactly, the rest (nc / N) delta
+    if (nD[j] & 1) mag = -mag;
+    const int64_t A = ((int64_t)k0s[j] * nc) % (2 * N);
+    double s1, c1, s2, c2;
+    sincospi((double)A / (double)N, &s1, &c1);
+    sincospi(((double)nc / (double)N) * dels[j], &s2, &c2);
+    sn = s1 * c2 + c1 * s2;
+    cs = c1 * c2 - s1 * s2;
+  }
   Dt[j] = make_double2(mag * sn, mag * cs);
   if (Dtf) Dtf[j] = make_float2((float)(mag * sn), (float)(mag * cs));
 }
@@ -356,15 +382,18 @@ int inverse_precompute(nufft_plan_s* pl, void* tmp, size_t tmp_bytes) {
       reg[(size_t)2 * nq * nq + (size_t)i * nq + r] = (double)(((i - r) & 1) ? -c : c);
       reg[(size_t)3 * nq * nq + (size_t)i * nq + r] = (double)c;
     }
+  // half-grid charges of weight wc = Nc / N (1 for a power-of-two inverse)
+  const long double wcl = (long double)pl->Nc / (long double)N;
+  const double wc = (double)wcl;
   for (int m = 0; m < pm; ++m) {
     long double acc = 0;
     for (int o = 0; o < s; ++o) acc += powl(((long double)o + 0.5L) / s - 0.5L, m);
-    shift[m] = (double)acc;
+    shift[m] = (double)(wcl * acc);
   }
   for (int o = 0; o < s; ++o) {
     long double acc = 0;
     for (int r = -s; r < 2 * s; ++r) acc += logl(fabsl((long double)o - r - 0.5L));
-    hg[o] = (double)acc;
+    hg[o] = (double)(wcl * acc);
   }
   auto up = [&](size_t off, const std::vector<double>& v) {
     return cudaMemcpyAsync(base + off, v.data(), v.size() * 8, cudaMemcpyHostToDevice, st) == cudaSuccess;
@@ -402,13 +431,15 @@ int inverse_precompute(nufft_plan_s* pl, void* tmp, size_t tmp_bytes) {
   double* Lam = pl->Lambda;
   const double2* lexp = (const double2*)sh.lexp;
   k_logsum_grid<<<nblk(N, 128), 128, 0, st>>>(d, pl->leaf_start, pl->k0, pl->delta, lexp, lvl2,
-                                              (const double*)(base + t.hg), M, lamC, nC);
+                                              (const double*)(base + t.hg), M, wc, lamC, nC);
   k_logsum_pts<<<nblk(M, 128), 128, 0, st>>>(d, pl->leaf_start, pl->k0, pl->delta, lexp, lvl2, M,
-                                             lamD, nD, pl->status);
+                                             wc, lamD, nD, pl->status);
   k_lambda<<<1, 1024, 0, st>>>(lamD, M, Lam);
   double elim = pl->prec == NUFFT_FP64 ? kExpLimit : 60.0;
-  k_assemble_C<<<nblk(N, 256), 256, 0, st>>>(lamC, nC, N, Lam, elim, pl->Ct, pl->Ctf, pl->status);
-  k_assemble_D<<<nblk(M, 256), 256, 0, st>>>(lamD, nD, pl->k0, pl->delta, M, Lam, elim, pl->Dt,
-                                             pl->Dtf, pl->status);
+  const int sep = pl->Nc != N;
+  k_assemble_C<<<nblk(N, 256), 256, 0, st>>>(lamC, nC, N, Lam, elim, sep, pl->Ct, pl->Ctf,
+                                             pl->status);
+  k_assemble_D<<<nblk(M, 256), 256, 0, st>>>(lamD, nD, pl->k0, pl->delta, M, pl->Nc, N, Lam, elim,
+                                             pl->Dt, pl->Dtf, pl->status);
   return cudaGetLastError() == cudaSuccess ? NUFFT_OK : NUFFT_ECUDA;
 }

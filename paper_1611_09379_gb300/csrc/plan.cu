@@ -219,14 +219,15 @@ void free_plan(nufft_plan_s* pl) {
                   pl->Ff, pl->Ef, pl->lvl2f, pl->Dt, pl->Dtf, pl->Ct, pl->Ctf, pl->selft, pl->srcpos, pl->Lambda, pl->mexp, pl->lexp,
                   pl->charge, pl->grid, pl->grid2, pl->grid3, pl->lvl2, pl->op_m2m, pl->op_m2l,
                   pl->op_l2l, pl->op_p2m, pl->op_reg, pl->fft_tw, pl->fft_tw_f, pl->status,
-                  pl->seg_overflow, pl->lsq_work, pl->op_tc, pl->upcnt};
+                  pl->seg_overflow, pl->lsq_work, pl->op_tc, pl->upcnt, pl->hnear};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& gr : pl->graphs)
     if (gr.exec) cudaGraphExecDestroy(gr.exec);
   if (pl->cap) cudaStreamDestroy(pl->cap);
   if (pl->aux) cudaStreamDestroy(pl->aux);
-  for (int i = 0; i < 2; ++i) {
+  if (pl->aux2) cudaStreamDestroy(pl->aux2);
+  for (int i = 0; i < 3; ++i) {
     if (pl->ev_fork[i]) cudaEventDestroy(pl->ev_fork[i]);
     if (pl->ev_join[i]) cudaEventDestroy(pl->ev_join[i]);
   }
@@ -248,23 +249,25 @@ int dalloc(X** p, size_t bytes) {
 
 cudaStream_t side_begin(nufft_plan_s* pl, int slot) {
   if (!pl->side_ok || (pl->prof && pl->prof->enabled)) return pl->stream;
-  if (!pl->aux) {
-    if (cudaStreamCreateWithFlags(&pl->aux, cudaStreamNonBlocking) != cudaSuccess) {
-      pl->aux = nullptr;
+  cudaStream_t& as = slot == 2 ? pl->aux2 : pl->aux;
+  if (!as) {
+    if (cudaStreamCreateWithFlags(&as, cudaStreamNonBlocking) != cudaSuccess) {
+      as = nullptr;
       pl->side_ok = 0;
       return pl->stream;
     }
-    for (int i = 0; i < 2; ++i)
-      if (cudaEventCreateWithFlags(&pl->ev_fork[i], cudaEventDisableTiming) != cudaSuccess ||
-          cudaEventCreateWithFlags(&pl->ev_join[i], cudaEventDisableTiming) != cudaSuccess) {
-        pl->side_ok = 0;
-        return pl->stream;
-      }
+  }
+  if (!pl->ev_fork[slot]) {
+    if (cudaEventCreateWithFlags(&pl->ev_fork[slot], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&pl->ev_join[slot], cudaEventDisableTiming) != cudaSuccess) {
+      pl->side_ok = 0;
+      return pl->stream;
+    }
   }
   if (cudaEventRecord(pl->ev_fork[slot], pl->stream) != cudaSuccess ||
-      cudaStreamWaitEvent(pl->aux, pl->ev_fork[slot], 0) != cudaSuccess)
+      cudaStreamWaitEvent(as, pl->ev_fork[slot], 0) != cudaSuccess)
     return pl->stream;
-  return pl->aux;
+  return as;
 }
 
 void side_end(nufft_plan_s* pl, int slot, cudaStream_t s) {
@@ -272,8 +275,9 @@ void side_end(nufft_plan_s* pl, int slot, cudaStream_t s) {
 }
 
 void side_join(nufft_plan_s* pl, int slot) {
-  // a no-op unless the branch ran on aux (its join event was recorded)
-  if (pl->aux && pl->side_ok && !(pl->prof && pl->prof->enabled))
+  // a no-op unless the branch ran on its side stream (its join event was recorded)
+  cudaStream_t as = slot == 2 ? pl->aux2 : pl->aux;
+  if (as && pl->side_ok && pl->ev_join[slot] && !(pl->prof && pl->prof->enabled))
     cudaStreamWaitEvent(pl->stream, pl->ev_join[slot], 0);
 }
 
@@ -354,11 +358,31 @@ static int64_t grid_of(int64_t N) {
   return g;
 }
 
+// Threshold ("machine precision") error of the FP64 path on a grid of N
+// points (Sec. 3.1-3.2): the error of the paper's f = 1 test, max_j |g_j - 1|,
+// stops falling as eps is lowered at about log2(N) 2^-53 (measured on GB300
+// for N = 2^8 .. 2^22, uniform points: 0.8e-15 .. 2.2e-15, each within 20 %
+// below this line), at least 1e-15, the smallest eps accepted.
+static double eps_threshold_fp64(int64_t N) {
+  int L = 0;
+  while ((int64_t(1) << L) < N) ++L;
+  const double e = (double)L * 0x1p-53;
+  return e > 1e-15 ? e : 1e-15;
+}
+
+extern "C" double nufft_eps_threshold(int64_t N) {
+  if (N < 8 || N > (int64_t(1) << 26)) return -1.0;
+  return eps_threshold_fp64(grid_of(N));
+}
+
 int nufft_choose_params(int64_t Nc, int64_t M, double eps, int prec, nufft_params* prm) {
   if (!prm) return NUFFT_EINVAL;
   if (Nc < 8 || Nc > (int64_t(1) << 26)) return NUFFT_EINVAL;
   const int64_t N = grid_of(Nc);  // the tree and the FFT live on this grid
   if (M < 1 || M > (int64_t(1) << 27)) return NUFFT_EINVAL;
+  // eps = 0: machine precision (Sec. 3.2's second setting): the threshold
+  // error eps_th(N) as the prescribed accuracy, p and q from Eq. 18.2 at it
+  if (eps == 0.0 && prec == NUFFT_FP64) eps = eps_threshold_fp64(N);
   if (!(eps >= 1e-15 && eps <= 1e-1)) return NUFFT_EINVAL;
   if (prec != NUFFT_FP64 && prec != NUFFT_MIXED) return NUFFT_EINVAL;
   if (prec == NUFFT_MIXED && eps < 1e-7) return NUFFT_EINVAL;
@@ -423,9 +447,6 @@ int nufft_plan_create(nufft_plan* out, int64_t N, int64_t M, const double* y, do
   if ((flags & NUFFT_WANT_INVERSE) && M != N) return NUFFT_EINVAL;
   const int64_t Nc = N;
   N = grid_of(Nc);
-  // the square inverse's Lagrange form (Eq. p8) is formed on the grid of its
-  // own N points
-  if ((flags & NUFFT_WANT_INVERSE) && N != Nc) return NUFFT_ENOTSUP;
   const int64_t nb = prm.batch;
   if ((rc = configure_once())) return rc;
   nufft_plan_s* pl = new (std::nothrow) nufft_plan_s();
@@ -433,6 +454,8 @@ int nufft_plan_create(nufft_plan* out, int64_t N, int64_t M, const double* y, do
   pl->prof = new (std::nothrow) StageProf();
   if (!pl->prof) { delete pl; return NUFFT_ENOMEM; }
   pl->N = N; pl->Nc = Nc; pl->M = M; pl->L = prm.lmax; pl->B = 1 << prm.lmax;
+  // square inverse for Nc < N: C carries the phase e^{i pi k Nc / N}
+  pl->inv_nc = ((flags & NUFFT_WANT_INVERSE) && Nc != N) ? Nc : 0;
   pl->s = (int)(N >> prm.lmax);
   pl->p = prm.p; pl->q = prm.q; pl->pm = prm.p > 2 * prm.q + 1 ? prm.p : 2 * prm.q + 1;
   pl->prec = prec; pl->flags = flags; pl->eps = eps; pl->batch = (int)nb;
@@ -457,6 +480,8 @@ int nufft_plan_create(nufft_plan* out, int64_t N, int64_t M, const double* y, do
     return rc;
   }
   if (fft_num_passes(N) >= 3 && (rc = dalloc(&pl->grid3, nb * N * 16))) { free_plan(pl); return rc; }
+  // near-field sums of the split target evaluation (one signal)
+  if (nb == 1 && (rc = dalloc(&pl->hnear, 2 * big * 16))) { free_plan(pl); return rc; }
   if (prec == NUFFT_MIXED &&
       ((rc = dalloc(&pl->delta_f, M * 4)) || (rc = dalloc(&pl->Ff, M * 8)) ||
        (rc = dalloc(&pl->Ef, M * 8)) || (rc = dalloc(&pl->lvl2f, nb * (8 * pl->q + 1) * 8)) ||

@@ -272,6 +272,8 @@ extern "C" int nufft_autotune(int64_t N, int64_t M, const double* y, double eps,
       (flags & ~NUFFT_IO_C64) || reps < 1 || batch < 1 || (max_trials > 0 && !trials))
     return NUFFT_EINVAL;
   if ((ops & NUFFT_OP_INV) && M != N) return NUFFT_EINVAL;
+  // machine precision (eps = 0, FP64): tune against the threshold error
+  if (eps == 0.0 && prec == NUFFT_FP64) eps = nufft_eps_threshold(N);
   nufft_params d0{0, 0, 0, batch, 0, 0};
   int rc = nufft_choose_params(N, M, eps, prec, &d0);
   if (rc) return rc;

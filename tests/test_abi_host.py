@@ -78,6 +78,23 @@ def test_choose_params_general_n_uses_the_padded_grid(nf, N):
         assert nf.choose_params(N, N, eps, prec) == nf.choose_params(Np, N, eps, prec)
 
 
+def test_machine_precision_mode_parameters(nf):
+    """eps = 0 (FP64) prescribes the threshold error eps_th(N) = log2(N') 2^-53
+    (at least 1e-15) and takes p, q from Eq. 18.2 at it (Sec. 3.2); the mixed
+    path has no such mode."""
+    for N in (8, 1 << 10, 1 << 16, 1 << 20, 12345, 1 << 26):
+        Np = 1 << (N - 1).bit_length()
+        e = nf.eps_threshold(N)
+        assert e == max(1e-15, (Np.bit_length() - 1) * 2.0 ** -53)
+        assert nf.choose_params(N, N, 0.0, nf.FP64) == nf.choose_params(N, N, e, nf.FP64)
+    p20 = nf.choose_params(1 << 20, 1 << 20, 0.0, nf.FP64)
+    assert p20 == (15, 42, 25)  # eps_th(2^20) = 2.2e-15
+    with pytest.raises(nf.NufftError):
+        nf.choose_params(1 << 10, 1 << 10, 0.0, nf.MIXED)
+    with pytest.raises(nf.NufftError):
+        nf.eps_threshold(4)
+
+
 def test_lmax_override_bounds(nf):
     with pytest.raises(nf.NufftError):
         nf.choose_params(1 << 10, 1 << 10, 1e-6, nf.FP64, lmax=11)

@@ -6,7 +6,8 @@ the FMM and its FFT on the N' grid (zero padding on input, truncation on
 output inside the FFT passes).  The oracle evaluates the definitions
 directly at N: the direct NUDFT with exact phases (forward, adjoint) and a
 dense least-squares solve; its grid routes are pinned at non-power-of-two N
-by the closed forms in test_oracle_pins.py."""
+by the closed forms in test_oracle_pins.py (the square inverse by its round
+trip and a dense solve)."""
 import numpy as np
 import pytest
 
@@ -111,12 +112,25 @@ def test_lsq_general_n(nf, orc):
     assert orc.rel_l2(c1, cref) < 1e-9
 
 
-def test_square_inverse_needs_power_of_two(nf):
-    N = 1000
-    y = workloads.points("jitter", N, N, seed=1, jitter=0.1)
-    with pytest.raises(nf.NufftError) as e:
-        nf.Plan(N, _dev(y), eps=1e-12, inverse=True)
-    assert e.value.code == nf.ENOTSUP
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("N,jit", [(1000, 0.1), (3000, 0.4), (12345, 0.1)])
+def test_square_inverse_general_n(nf, orc, prec, N, jit):
+    """Square inverse (M = N points, Eq. p6 / p8) for N not a power of two: the
+    library evaluates the Lagrange form at the N' grid points, C(x) =
+    e^{i N x / 2} prod sin((x - y_l)/2) being complex there; against the
+    oracle's inverse on the N grid itself and the round trip."""
+    y = workloads.points("jitter", N, N, seed=N + 7, jitter=jit)
+    c = workloads.coeffs(N, seed=N + 8)
+    g = orc.nudft_fwd(c, y)
+    eps = 1e-12 if prec == 0 else 1e-6
+    plan = nf.Plan(N, _dev(y), eps=eps, prec=prec, inverse=True)
+    c2 = _host(plan.inverse(_dev(g)))
+    assert c2.shape == (N,)
+    cref = orc.inufft(g, y, N)
+    assert orc.rel_l2(c2, cref) < TOL[prec] * (1 if jit <= 0.1 else 10)
+    assert orc.rel_l2(c2, c) < (1e-11 if prec == 0 else 1e-5)
+    ci = _host(nf.inufft(_dev(g), _dev(y), N, N, eps, prec))
+    assert orc.rel_l2(ci, cref) < TOL[prec] * (1 if jit <= 0.1 else 10)
 
 
 def test_uneven_batch_log_uniform_n(nf, orc):

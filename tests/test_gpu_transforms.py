@@ -385,7 +385,9 @@ def test_inverse_clustered_small_matvec(nf, orc, prec, N):
     f = np.fft.ifft(c2) * N
     fref = orc.inverse_f(g, y, N)
     aref = orc.inverse_absf(g, y, N)
-    assert np.linalg.norm(f - fref) / np.linalg.norm(aref) < TOL[prec]
+    sc = aref.max()  # the sums reach e^200: scale before the norms
+    assert np.all(np.isfinite(f)) and sc < np.inf
+    assert np.linalg.norm((f - fref) / sc) / np.linalg.norm(aref / sc) < TOL[prec]
     if prec == 1:
         y5 = workloads.points("clustered", 512, seed=33)
         with pytest.raises(nf.NufftError) as e:
