@@ -446,9 +446,10 @@ int inufft(const void *g, const double *y, int64_t M, int64_t N, double eps,
  * flags: 0 or NUFFT_IO_C64), but every work buffer lives in one fixed
  * 16 MiB device array compiled into the library, held by every GPU that loads
  * it until the process exits.  Limits: N a power of two, N <= 2^16 and
- * M <= 2^16; other sizes return NUFFT_EINVAL and do nothing.  The tree depth is that of Eq. 25 but
- * at least log2 N - 6 (leaves of at most 64 grid points), so the result can
- * differ from nufft_fwd's in the last digits when M is much smaller than N.
+ * M <= 2^16; other sizes return NUFFT_EINVAL and do nothing.  The tree depth
+ * is that of Eq. 25 but at least log2 N - 6 (leaves of at most 64 grid
+ * points), so the result can differ from nufft_fwd's in the last digits when
+ * M is much smaller than N.
  * The first call on a device looks up the array's device address and must run
  * with that device current; make it before any stream capture.  Calls share
  * the array and overwrite its contents; calls whose GPU work overlaps (other

@@ -173,6 +173,17 @@ bool pdl_enabled();  // false when the environment sets NUFFT_NO_PDL
 // runs as one launch per subtree level band (same arithmetic, same results)
 bool fused_up_enabled();
 
+// Launch priority: kernels on the critical path of an exec sequence run at
+// the device's highest priority, so the CTAs of a side-branch kernel that
+// fills the GPU (the near field beside the tree passes) do not hold them
+// back; a LowPriority scope (the side branch) launches at the default.
+// 0 = no attribute (NUFFT_NO_PRIORITY, or no priority range on the device).
+int launch_priority();
+struct LowPriority {
+  LowPriority();
+  ~LowPriority();
+};
+
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
                               cudaStream_t st, Args... args) {
@@ -181,11 +192,21 @@ inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, siz
   cfg.blockDim = block;
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchAttribute at[2];
+  int na = 0;
+  if (pdl_enabled()) {
+    at[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[na].val.programmaticStreamSerializationAllowed = 1;
+    ++na;
+  }
+  const int prio = launch_priority();
+  if (prio != 0) {
+    at[na].id = cudaLaunchAttributePriority;
+    at[na].val.priority = prio;
+    ++na;
+  }
   cfg.attrs = at;
-  cfg.numAttrs = pdl_enabled() ? 1 : 0;
+  cfg.numAttrs = na;
   return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
 }
 

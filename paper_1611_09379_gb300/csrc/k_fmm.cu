@@ -340,6 +340,27 @@ template <class T, class VI> struct UpSrc {
 };
 constexpr int kUpThreads = 512;  // (1024 for the P2M source modes measured slower)
 
+// dst[e] = src(e) for e < n by the whole CTA, U loads per thread issued
+// before any of them is stored, so a thread waits for one memory latency
+// per U elements rather than per element (the staging loops of the tree
+// passes are latency bound)
+template <int U, class V, class Src>
+__device__ inline void stage_batched(int n, V* __restrict__ dst, Src src) {
+  for (int e0 = threadIdx.x; e0 < n; e0 += U * (int)blockDim.x) {
+    V r[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + u * (int)blockDim.x;
+      if (e < n) r[u] = src(e);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + u * (int)blockDim.x;
+      if (e < n) dst[e] = r[u];
+    }
+  }
+}
+
 template <class T, int SRC, class VI>
 __global__ void __launch_bounds__(kUpThreads) k_up_fused(TreeDims d, UpStages sg,
                                                          const T* __restrict__ op,
@@ -369,16 +390,31 @@ __global__ void __launch_bounds__(kUpThreads) k_up_fused(TreeDims d, UpStages sg
     cplx<T>* lvl = mexp + (level_off(lb) + (box << (lb - lt))) * pm;
     const int nsrc = pm << (lb - lt);
     if (k > 0) {  // written by other CTAs of this grid: read through L2
-      for (int i = threadIdx.x; i < nsrc; i += blockDim.x) cur0[i] = __ldcg(lvl + i);
+      stage_batched<4>(nsrc, cur0, [&](int i) { return __ldcg(lvl + i); });
     } else if constexpr (SRC == 0) {
-      for (int i = threadIdx.x; i < nsrc; i += blockDim.x) cur0[i] = lvl[i];
+      stage_batched<4>(nsrc, cur0, [&](int i) { return lvl[i]; });
     } else if constexpr (SRC == 1) {
       const int sN = d.s;
       cplx<T>* qs = xtra;  // [nl0][s + 1]
       const cplx<T>* q = src.q + blockIdx.y * d.N + (box << (lb - lt)) * sN;
-      for (int i = threadIdx.x; i < nl0 * sN; i += blockDim.x) {
-        const int lf = i / sN;
-        qs[lf * (sN + 1) + (i - lf * sN)] = q[i];
+      {
+        const int tot = nl0 * sN;
+        for (int i0 = threadIdx.x; i0 < tot; i0 += 8 * kUpThreads) {
+          cplx<T> r[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int i = i0 + u * kUpThreads;
+            if (i < tot) r[u] = q[i];
+          }
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int i = i0 + u * kUpThreads;
+            if (i < tot) {
+              const int lf = i / sN;
+              qs[lf * (sN + 1) + (i - lf * sN)] = r[u];
+            }
+          }
+        }
       }
       __syncthreads();
       for (int e = threadIdx.x; e < nsrc; e += blockDim.x) {
@@ -690,23 +726,26 @@ __global__ void __launch_bounds__(512) k_down_fused(TreeDims d, int lt, int lb,
   auto list_off = [](int odd, int t) {
     return odd ? (t == 0 ? -3 : (t == 1 ? -2 : 2)) : (t == 0 ? -2 : (t == 1 ? 2 : 3));
   };
-  for (int e = threadIdx.x; e < na * 3 * p; e += blockDim.x) {
+  stage_batched<4>(na * 3 * p, An, [&](int e) {
     const int li = e / (3 * p), r = e - li * 3 * p, t = r / p, m = r - t * p;
     const int l = 3 + li;
     const int64_t a = c >> (lt - l), nb = int64_t(1) << l;
     const int64_t box = (a + list_off((int)(a & 1), t) + nb) & (nb - 1);
-    An[e] = mexp[(level_off(l) + box) * pm + m];
-  }
-  for (int j = 1; j <= depth; ++j) {
-    const int l = lt + j, nbx = 1 << j;
+    return mexp[(level_off(l) + box) * pm + m];
+  });
+  // the subtree levels' multipoles (boxes -3 .. 2^j + 2 of level lt + j) in
+  // one flat pass: element e of Ms lies in level j with (2^j - 2 + 6 (j - 1)) p
+  // <= e < (2^(j+1) - 2 + 6 j) p
+  stage_batched<4>((((2 << depth) - 2) + 6 * depth) * p, Ms, [&](int e) {
+    int j = 1;
+    while (j < depth && e >= ((2 << j) - 2 + 6 * j) * p) ++j;
+    const int r = e - ((1 << j) - 2 + 6 * (j - 1)) * p;
+    const int bi = r / p, m = r - bi * p;
+    const int l = lt + j;
     const int64_t nb = int64_t(1) << l, c0 = c << j;
-    cplx<T>* ms = Ms + (nbx - 2 + 6 * (j - 1)) * p;
-    for (int e = threadIdx.x; e < (nbx + 6) * p; e += blockDim.x) {
-      const int bi = e / p, m = e - bi * p;
-      const int64_t box = (c0 - 3 + bi + nb) & (nb - 1);
-      ms[e] = mexp[(level_off(l) + box) * pm + m];
-    }
-  }
+    const int64_t box = (c0 - 3 + bi + nb) & (nb - 1);
+    return mexp[(level_off(l) + box) * pm + m];
+  });
   __syncthreads();
   // M2L parts: the ancestors' and, level by level, the subtree's; a thread's
   // outputs (box bi, coefficient n) advance by blockDim.x = sb p + sn
@@ -950,6 +989,8 @@ template <class T> struct __align__(16) SrcQ {
 
 // Targets per CTA and the capacity of the staged near-field windows.
 constexpr int kTgtThreads = 256;
+// leaf locals a far-part CTA stages in shared memory (more: read from global)
+constexpr int kFarLeaves = 16;
 template <class T, int G> struct NearCap {
   // forward: grid samples per signal; adjoint / inverse: sources per chunk
   static constexpr int fwd = (sizeof(T) == 4 ? 2048 : 1024) / G;
@@ -1076,14 +1117,12 @@ __device__ inline void near_window_ex2w(int n, int ex, NearAcc2f& acc, Term term
 // and stores them to hout (it needs the grid samples alone, so it can run
 // beside the tree passes); with hnear set it skips them and reads them there.
 template <class T, class VO, int G>
-__global__ void __launch_bounds__(kTgtThreads) k_targets_fwd(
-    TreeDims d, int M, const int32_t* __restrict__ k0s, const double* __restrict__ dels,
+__device__ inline void targets_fwd_tile(
+    int tile, TreeDims d, int M, const int32_t* __restrict__ k0s, const double* __restrict__ dels,
     const T* __restrict__ dels_t, const int32_t* __restrict__ perm, const cplx<T>* __restrict__ F,
     const cplx<T>* __restrict__ E, const cplx<T>* __restrict__ fgrid,
     const cplx<T>* __restrict__ lexp, const cplx<T>* __restrict__ lvl2,
     const cplx<T>* __restrict__ hnear, VO* __restrict__ g, cplx<T>* __restrict__ hout) {
-  pdl_wait();
-  pdl_trigger();
   extern __shared__ __align__(16) unsigned char smraw[];
   cplx<T>* sf = reinterpret_cast<cplx<T>*>(smraw);  // [G][window]
   __shared__ int s_lo, s_hi;
@@ -1091,7 +1130,7 @@ __global__ void __launch_bounds__(kTgtThreads) k_targets_fwd(
   const int s = d.s;
   const int sig0 = blockIdx.y * G;
   fgrid += (int64_t)sig0 * N;
-  const int j0 = blockIdx.x * kTgtThreads;
+  const int j0 = tile * kTgtThreads;
   const int j = j0 + threadIdx.x;
   const bool act = j < M;
   const int jl = (j0 + kTgtThreads < M ? j0 + kTgtThreads : M) - 1;
@@ -1102,23 +1141,29 @@ __global__ void __launch_bounds__(kTgtThreads) k_targets_fwd(
     point_local(k0, dels[j], N, s, &b, &o);
     dt = dels_t[j];
   }
-  if (threadIdx.x == 0) s_lo = b;
-  if (j == jl) s_hi = b;
-  __syncthreads();
-  const int bl = s_lo, bh = s_hi;
-  const int nwin = (bh - bl + 3) * s;  // samples of leaves bl-1 .. bh+1
-  // hnear: near-field sums computed elsewhere (tensor cores): no window here
-  const bool staged = !hnear && nwin <= NearCap<T, G>::fwd;
-  // (targets are sorted by leaf, so b lies in [bl, bh]; checked all the same)
-  if (staged) {
-    const int base = (bl - 1) * s;
-    for (int e = threadIdx.x; e < nwin; e += kTgtThreads) {
-      const int k = (base + e + N) & (N - 1);
+  // hnear: near-field sums computed elsewhere (side branch or tensor cores):
+  // no window, no barrier, every load of the far part can be in flight at once
+  int bl = b, bh = b, nwin = 0;
+  bool staged = false;
+  if (!hnear) {
+    if (threadIdx.x == 0) s_lo = b;
+    if (j == jl) s_hi = b;
+    __syncthreads();
+    bl = s_lo;
+    bh = s_hi;
+    nwin = (bh - bl + 3) * s;  // samples of leaves bl-1 .. bh+1
+    staged = nwin <= NearCap<T, G>::fwd;
+    // (targets are sorted by leaf, so b lies in [bl, bh]; checked all the same)
+    if (staged) {
+      const int base = (bl - 1) * s;
+      for (int e = threadIdx.x; e < nwin; e += kTgtThreads) {
+        const int k = (base + e + N) & (N - 1);
 #pragma unroll
-      for (int gg = 0; gg < G; ++gg) sf[gg * nwin + e] = fgrid[(int64_t)gg * N + k];
+        for (int gg = 0; gg < G; ++gg) sf[gg * nwin + e] = fgrid[(int64_t)gg * N + k];
+      }
     }
+    __syncthreads();
   }
-  __syncthreads();
   if (!act) return;
   NearAcc<T> acc[G];
   // c-th sample of the target's 3 leaves: D = k0 - k = (o + s) - c
@@ -1218,6 +1263,95 @@ __global__ void __launch_bounds__(kTgtThreads) k_targets_fwd(
   }
 }
 
+// Tiles of 256 sorted targets; a grid of fewer CTAs than tiles loops over
+// them (the near-field pass beside the tree passes runs a few CTAs per SM
+// only, so the tree kernels keep room on every SM).
+template <class T, class VO, int G>
+__global__ void __launch_bounds__(kTgtThreads) k_targets_fwd(
+    TreeDims d, int M, const int32_t* __restrict__ k0s, const double* __restrict__ dels,
+    const T* __restrict__ dels_t, const int32_t* __restrict__ perm, const cplx<T>* __restrict__ F,
+    const cplx<T>* __restrict__ E, const cplx<T>* __restrict__ fgrid,
+    const cplx<T>* __restrict__ lexp, const cplx<T>* __restrict__ lvl2,
+    const cplx<T>* __restrict__ hnear, VO* __restrict__ g, cplx<T>* __restrict__ hout) {
+  pdl_wait();
+  pdl_trigger();
+  const int ntiles = (M + kTgtThreads - 1) / kTgtThreads;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    if (tile != (int)blockIdx.x) __syncthreads();  // the previous tile's shared data are read
+    targets_fwd_tile<T, VO, G>(tile, d, M, k0s, dels, dels_t, perm, F, E, fgrid, lexp, lvl2,
+                               hnear, g, hout);
+  }
+}
+
+// The far part of the forward targets after the near-field sums were formed
+// on the side branch (hnear, sorted order): the same arithmetic as the end of
+// k_targets_fwd for one signal, with the CTA's leaf locals (leaves bl..bh of
+// its sorted targets, up to kFarLeaves of them) and the level-2 coefficients
+// staged in shared memory first, so each target's Horner sums read on-chip
+// data; the per-target loads (F, E, perm, hnear, the sample at k0) are issued
+// before the barrier.  Dynamic shared memory: (kFarLeaves p + 8q + 1) complex.
+template <class T, class VO>
+__global__ void __launch_bounds__(kTgtThreads) k_far_fwd(
+    TreeDims d, int M, const int32_t* __restrict__ k0s, const double* __restrict__ dels,
+    const T* __restrict__ dels_t, const int32_t* __restrict__ perm, const cplx<T>* __restrict__ F,
+    const cplx<T>* __restrict__ E, const cplx<T>* __restrict__ fgrid,
+    const cplx<T>* __restrict__ lexp, const cplx<T>* __restrict__ lvl2,
+    const cplx<T>* __restrict__ hnear, VO* __restrict__ g) {
+  pdl_wait();
+  pdl_trigger();
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cplx<T>* sl = reinterpret_cast<cplx<T>*>(smraw);  // [kFarLeaves][p]
+  const int Q2 = 2 * d.q;
+  cplx<T>* s2 = sl + kFarLeaves * d.p;               // [4 Q2 + 1]
+  __shared__ int s_lo, s_hi;
+  const int N = (int)d.N;
+  const int s = d.s;
+  const int j0 = blockIdx.x * kTgtThreads;
+  const int j = j0 + threadIdx.x;
+  const bool act = j < M;
+  const int jl = (j0 + kTgtThreads < M ? j0 + kTgtThreads : M) - 1;
+  int k0 = 0, b = 0, o = 0, pj = 0;
+  T dt = 0;
+  cplx<T> Fj = mk<T>(0, 0), Ej = mk<T>(0, 0), nr = mk<T>(0, 0), fk = mk<T>(0, 0);
+  if (act) {
+    k0 = k0s[j];
+    point_local(k0, dels[j], N, s, &b, &o);
+    dt = dels_t[j];
+    pj = perm[j];
+    Fj = F[j];
+    Ej = E[j];
+    nr = hnear[j];
+    fk = fgrid[k0];
+  }
+  if (threadIdx.x == 0) s_lo = b;
+  if (j == jl) s_hi = b;
+  __syncthreads();
+  const int bl = s_lo, nlf = s_hi - s_lo + 1;
+  const bool staged = d.L >= 3 && nlf <= kFarLeaves;
+  const cplx<T>* lx = lexp + (int64_t)(level_off(d.L) - 4) * d.p;
+  if (staged)
+    stage_batched<4>(nlf * d.p, sl, [&](int e) { return lx[(int64_t)bl * d.p + e]; });
+  stage_batched<2>(4 * Q2 + 1, s2, [&](int e) { return lvl2[e]; });
+  __syncthreads();
+  if (!act) return;
+  const int arc = b >> (d.L - 2);
+  const int I = b * s + o - arc * (N >> 2) - (N >> 3);
+  const T uh = ((T)I + dt) * KConst<T>::two_n(d);
+  const T ts = KConst<T>::inv_s(d);
+  const T u = fma((T)o + dt, ts, (T)-0.5);
+  const T cN = KConst<T>::n_pi(d), c2 = (T)(2.0 * kInvPi);
+  cplx<T> far = mk<T>(0, 0);
+  if (d.L >= 3) far = horner<T>(staged ? sl + (b - bl) * d.p : lx + (int64_t)b * d.p, d.p, u);
+  const cplx<T> reg = horner<T>(s2 + arc * Q2, Q2, uh);
+  const cplx<T> Qs = s2[4 * Q2];
+  const T hr = cN * fma(far.x, ts, nr.x) - c2 * reg.x;
+  const T hi = cN * fma(far.y, ts, nr.y) - c2 * reg.y;
+  const cplx<T> wv = mk<T>(Qs.x - hi, Qs.y + hr);
+  cplx<T> res = cscale(cmul(Fj, wv), (T)-0.5);
+  res = cadd(res, cmul(Ej, fk));
+  store_cplx(g + pj, res);
+}
+
 // ---------------------------------------------------------------- adjoint / inverse targets
 
 // Charges in sorted order: adjoint q_i = conj(F_i) g_perm(i);
@@ -1250,6 +1384,69 @@ __global__ void k_charges(int64_t M, const int32_t* __restrict__ perm,
 //            Ct_k0 = 0 removes every other term.
 //   The FP32 path forms Ct_k0 / delta_j in FP32 when |delta_j| >= 2^-20 and
 //   |Ct_k0| >= 2^-100 (no underflow or overflow on the way), else in FP64.
+// The same quantities for one sorted source i of one signal (the caller
+// offsets gin by the signal), in a form the near-field kernels can also
+// evaluate while staging their sources: the charge q_i = coef_i g_perm(i)
+// (conj(coef_i) for the adjoint) and its self term.
+struct SelfArgs {
+  int N = 0;
+  int inverse = 0;
+  const int32_t* k0s = nullptr;
+  const double* dels = nullptr;
+  const int32_t* perm = nullptr;
+  const double* Ct = nullptr;
+  const void* gin = nullptr;  // caller samples: double2 (gin64) or float2
+  int gin64 = 1;
+};
+template <class T> __device__ inline cplx<T> sample_in(const SelfArgs& a, int64_t idx) {
+  return a.gin64 ? load_in<T>((const double2*)a.gin + idx) : load_in<T>((const float2*)a.gin + idx);
+}
+template <class T>
+__device__ inline cplx<T> charge_of(const SelfArgs& a, const cplx<T>* __restrict__ coef, int i) {
+  cplx<T> c = coef[i];
+  if (!a.inverse) c.y = -c.y;  // the adjoint's conj(F_i)
+  return cmul(c, sample_in<T>(a, a.perm[i]));
+}
+template <class T>
+__device__ inline cplx<T> self_term_of(const SelfArgs& a, const TreeDims& dd, int i, cplx<T> q,
+                                       const cplx<T>* __restrict__ E, const T* __restrict__ Ctt,
+                                       const T* __restrict__ delt, T n_2pi) {
+  if (!a.inverse) return cmul(cconj(E[i]), sample_in<T>(a, a.perm[i]));
+  const T dt = delt[i];
+  const int k0 = a.k0s[i];
+  if (sizeof(T) == 4) {
+    const T ct = Ctt[k0];
+    if (fabs(dt) >= (T)9.5367431640625e-07 && fabs(ct) >= (T)7.888609052210118e-31) {
+      const T w = (ct / dt) * n_2pi;
+      cplx<T> v = mk<T>(-q.y * w, q.x * w);
+      if (dd.nc) v = cmul(v, from_d2<T>(inv_phase(dd, k0)));
+      return v;
+    }
+  }
+  double d = a.dels[i];
+  double2 v;
+  if (d == 0.0) {
+    v = cscale(to_d2(sample_in<T>(a, a.perm[i])), 1.0 / (double)a.N);
+  } else {
+    double2 q2 = to_d2(q);
+    double w = a.Ct[k0] * (0.5 * (double)a.N * kInvPi) / d;
+    v = make_double2(-q2.y * w, q2.x * w);
+    if (dd.nc) v = cmul(v, inv_phase(dd, k0));  // an exact hit takes g_j itself, no phase
+  }
+  return from_d2<T>(v);
+}
+
+// Charges and self terms formed where they are used (coef non-null), or read
+// from the arrays a charge / self-term kernel wrote.
+template <class T> struct InlineSrc {
+  SelfArgs a;
+  const cplx<T>* coef = nullptr;
+  const cplx<T>* E = nullptr;
+  const T* Ctt = nullptr;
+  const T* delt = nullptr;
+  T n_2pi = 0;
+};
+
 template <class T, class VI>
 __global__ void k_self_terms(int M, int inverse, int N, TreeDims dd, const int32_t* __restrict__ k0s,
                              const double* __restrict__ dels, const int32_t* __restrict__ perm,
@@ -1264,34 +1461,16 @@ __global__ void k_self_terms(int M, int inverse, int N, TreeDims dd, const int32
   gin += (int64_t)blockIdx.y * M;
   charge += (int64_t)blockIdx.y * M;
   st += (int64_t)blockIdx.y * M;
-  if (!inverse) {
-    st[i] = cmul(cconj(E[i]), load_in<T>(gin + perm[i]));
-    return;
-  }
-  const T dt = delt[i];
-  const int k0 = k0s[i];
-  if (sizeof(T) == 4) {
-    const T ct = Ctt[k0];
-    if (fabs(dt) >= (T)9.5367431640625e-07 && fabs(ct) >= (T)7.888609052210118e-31) {
-      const cplx<T> q = charge[i];
-      const T w = (ct / dt) * n_2pi;
-      cplx<T> v = mk<T>(-q.y * w, q.x * w);
-      if (dd.nc) v = cmul(v, from_d2<T>(inv_phase(dd, k0)));
-      st[i] = v;
-      return;
-    }
-  }
-  double d = dels[i];
-  double2 v;
-  if (d == 0.0) {
-    v = cscale(to_d2(gin[perm[i]]), 1.0 / (double)N);
-  } else {
-    double2 q = to_d2(charge[i]);
-    double w = Ct[k0] * (0.5 * (double)N * kInvPi) / d;
-    v = make_double2(-q.y * w, q.x * w);
-    if (dd.nc) v = cmul(v, inv_phase(dd, k0));  // an exact hit takes g_j itself, no phase
-  }
-  st[i] = from_d2<T>(v);
+  SelfArgs a;
+  a.N = N;
+  a.inverse = inverse;
+  a.k0s = k0s;
+  a.dels = dels;
+  a.perm = perm;
+  a.Ct = Ct;
+  a.gin = gin;
+  a.gin64 = sizeof(VI) == sizeof(double2);
+  st[i] = self_term_of<T>(a, dd, i, inverse ? charge[i] : mk<T>(0, 0), E, Ctt, delt, n_2pi);
 }
 
 
@@ -1462,21 +1641,24 @@ __global__ void __launch_bounds__(kTgtThreads) k_targets_grid(
 }
 
 // k_targets_grid for one signal with two adjacent grid points k, k + 1 per
-// thread (same leaf: s is even): every staged source (position and charge
+// thread (same leaf: s is even); isrc.coef set: the staged sources' charges
+// and self terms are formed while staging (from the caller's samples), so
+// no kernel needs to run before this one: every staged source (position and charge
 // in one record) is read once for both points, which halves the
 // shared-memory instructions of the pair loop.  The
 // window is sorted by x, so the sources with k0 = k and those with
 // k0 = k + 1 are two consecutive runs: each point takes the self terms of its
 // own run and the pair of the other's.  Same arithmetic per pair as
 // k_targets_grid.
-template <class T>
-__global__ void __launch_bounds__(kTgtThreads, sizeof(T) == 4 ? 5 : 4) k_targets_grid2(
-    TreeDims d, int inverse, const int32_t* __restrict__ start,
+// MODE 0: the whole evaluation; 1: near field only (to hout), with the
+// charges and self terms formed while staging (isrc); 2: far part only (hin).
+template <class T, int MODE>
+__device__ inline void grid2_tile(
+    int tile, TreeDims d, int inverse, const int32_t* __restrict__ start,
     const SrcPos<T>* __restrict__ pos, const cplx<T>* __restrict__ charge,
     const cplx<T>* __restrict__ st, const cplx<T>* __restrict__ lexp,
-    const cplx<T>* __restrict__ lvl2, const T* __restrict__ Ct, cplx<T>* __restrict__ out) {
-  pdl_wait();
-  pdl_trigger();
+    const cplx<T>* __restrict__ lvl2, const T* __restrict__ Ct, cplx<T>* __restrict__ out,
+    cplx<T>* __restrict__ hout, const cplx<T>* __restrict__ hin, const InlineSrc<T>& isrc) {
   constexpr int CAP = NearCap<T, 1>::grid;
   constexpr int kPts = 2 * kTgtThreads;
   constexpr int kMaxSlots = kTgtThreads + 3;  // kPts / s + 3 with s >= 2
@@ -1487,12 +1669,44 @@ __global__ void __launch_bounds__(kTgtThreads, sizeof(T) == 4 ? 5 : 4) k_targets
   const int N = (int)d.N;
   const int s = d.s;
   const int B = 1 << d.L;
-  const int kb = blockIdx.x * kPts;
+  const int kb = tile * kPts;
   const int k = kb + 2 * threadIdx.x;  // and k + 1
   const bool act = k < N;
   const int bl = kb / s;
   const int bh = ((kb + kPts < N ? kb + kPts : N) - 1) / s;
   const int nslot = bh - bl + 3;
+  const int b = act ? k / s : bl;
+  NearAcc<T> acc0, acc1;
+  cplx<T> self0 = mk<T>(0, 0), self1 = mk<T>(0, 0);
+  cplx<T> nr0 = mk<T>(0, 0), nr1 = mk<T>(0, 0);
+  // the far part's tables: the CTA's leaf locals and the level-2
+  // coefficients, staged in shared memory when only the far part runs here
+  const cplx<T>* lxg = lexp + (int64_t)(level_off(d.L) - 4) * d.p;
+  const cplx<T>* lx = lxg;  // locals of leaf b at lx + (b - lxb) p
+  int lxb = 0;
+  const cplx<T>* l2 = lvl2;
+  if constexpr (MODE == 2) {  // near-field sums and self terms formed by an earlier launch
+    if (act) {
+      nr0 = hin[2 * (int64_t)k];
+      self0 = hin[2 * (int64_t)k + 1];
+      if (k + 1 < N) {
+        nr1 = hin[2 * (int64_t)k + 2];
+        self1 = hin[2 * (int64_t)k + 3];
+      }
+    }
+    cplx<T>* sl = reinterpret_cast<cplx<T>*>(smraw);
+    const int nlf = bh - bl + 1;
+    if (d.L >= 3 && nlf <= kFarLeaves) {
+      stage_batched<4>(nlf * d.p, sl, [&](int e) { return lxg[(int64_t)bl * d.p + e]; });
+      lx = sl;
+      lxb = bl;
+    }
+    cplx<T>* s2 = sl + kFarLeaves * d.p;
+    stage_batched<2>(8 * d.q + 1, s2, [&](int e) { return lvl2[e]; });
+    l2 = s2;
+    __syncthreads();
+    if (!act) return;
+  } else {
   if (threadIdx.x < 32) {
     int carry = 0;
     for (int c0 = 0; c0 < nslot; c0 += 32) {
@@ -1515,11 +1729,8 @@ __global__ void __launch_bounds__(kTgtThreads, sizeof(T) == 4 ? 5 : 4) k_targets
   }
   __syncthreads();
   const int total = s_off[nslot];
-  const int b = act ? k / s : bl;
   const int wlo = s_off[b - bl], whi = s_off[b - bl + 3];
   const T kf0 = (T)(k - kb), kf1 = kf0 + (T)1;
-  NearAcc<T> acc0, acc1;
-  cplx<T> self0 = mk<T>(0, 0), self1 = mk<T>(0, 0);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // both points' pairs with source i
   auto both = [&](int i) {
@@ -1567,9 +1778,15 @@ __global__ void __launch_bounds__(kTgtThreads, sizeof(T) == 4 ? 5 : 4) k_targets
         const int xu = bu * s + (((int)ps.k0 - bb * s) & (N - 1)) - kb;
         SrcQ<T> v;
         v.rel = mk<T>((T)xu, ps.dl);
-        v.q = charge[gi];
+        if constexpr (MODE == 1) {  // charge and self term formed here (no kernel before)
+          v.q = charge_of<T>(isrc.a, isrc.coef, gi);
+          sst[e - c0] = self_term_of<T>(isrc.a, d, gi, v.q, isrc.E, isrc.Ctt, isrc.delt,
+                                         isrc.n_2pi);
+        } else {
+          v.q = charge[gi];
+          sst[e - c0] = st[gi];
+        }
         sw[e - c0] = v;
-        sst[e - c0] = st[gi];
       }
     }
     __syncthreads();
@@ -1615,11 +1832,22 @@ __global__ void __launch_bounds__(kTgtThreads, sizeof(T) == 4 ? 5 : 4) k_targets
     }
   }
   if (!act) return;
+  nr0 = acc0.get();
+  nr1 = acc1.get();
+  if constexpr (MODE == 1) {  // near field only: the far part follows the tree passes
+    hout[2 * (int64_t)k] = nr0;
+    hout[2 * (int64_t)k + 1] = self0;
+    if (k + 1 < N) {
+      hout[2 * (int64_t)k + 2] = nr1;
+      hout[2 * (int64_t)k + 3] = self1;
+    }
+    return;
+  }
+  }
   const int Q2 = 2 * d.q;
   const int arc = b >> (d.L - 2);
   const T ts = KConst<T>::inv_s(d);
   const T cN = KConst<T>::n_pi(d), c2 = (T)(2.0 * kInvPi);
-  const cplx<T>* l2 = lvl2;
   const cplx<T> Qs = l2[4 * Q2];
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
@@ -1630,10 +1858,9 @@ __global__ void __launch_bounds__(kTgtThreads, sizeof(T) == 4 ? 5 : 4) k_targets
     const T uh = (T)I * KConst<T>::two_n(d);
     const T u = fma((T)o, ts, (T)-0.5);
     cplx<T> far = mk<T>(0, 0);
-    if (d.L >= 3)
-      far = horner<T>(lexp + ((int64_t)(level_off(d.L) - 4) + b) * d.p, d.p, u);
+    if (d.L >= 3) far = horner<T>(lx + (int64_t)(b - lxb) * d.p, d.p, u);
     const cplx<T> reg = horner<T>(l2 + arc * Q2, Q2, uh);
-    const cplx<T> nr = h ? acc1.get() : acc0.get();
+    const cplx<T> nr = h ? nr1 : nr0;
     const T hr = cN * fma(far.x, ts, nr.x) - c2 * reg.x;
     const T hi = cN * fma(far.y, ts, nr.y) - c2 * reg.y;
     cplx<T> res = mk<T>((T)-0.5 * (Qs.x - hi), (T)-0.5 * (Qs.y + hr));
@@ -1642,6 +1869,23 @@ __global__ void __launch_bounds__(kTgtThreads, sizeof(T) == 4 ? 5 : 4) k_targets
       if (d.nc) res = cmul(res, from_d2<T>(inv_phase(d, kk)));
     }
     out[kk] = cadd(res, h ? self1 : self0);
+  }
+}
+
+template <class T, int MODE>
+__global__ void __launch_bounds__(kTgtThreads, (sizeof(T) == 4 && MODE == 0) ? 5 : 4) k_targets_grid2(
+    TreeDims d, int inverse, const int32_t* __restrict__ start,
+    const SrcPos<T>* __restrict__ pos, const cplx<T>* __restrict__ charge,
+    const cplx<T>* __restrict__ st, const cplx<T>* __restrict__ lexp,
+    const cplx<T>* __restrict__ lvl2, const T* __restrict__ Ct, cplx<T>* __restrict__ out,
+    cplx<T>* __restrict__ hout, const cplx<T>* __restrict__ hin, InlineSrc<T> isrc) {
+  pdl_wait();
+  pdl_trigger();
+  const int ntiles = (int)((d.N + 2 * kTgtThreads - 1) / (2 * kTgtThreads));
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    if (tile != (int)blockIdx.x) __syncthreads();  // the previous tile's shared data are read
+    grid2_tile<T, MODE>(tile, d, inverse, start, pos, charge, st, lexp, lvl2, Ct, out, hout, hin,
+                        isrc);
   }
 }
 
@@ -1656,7 +1900,9 @@ __global__ void __launch_bounds__(kTgtThreads, sizeof(T) == 4 ? 5 : 4) k_targets
 // which finishes it: the sources whose nearest grid point is the target (a
 // run of the sorted leaf, found by binary search) add their self terms, the
 // far field, the regular part (Eq. p20) and C_k complete it as in
-// k_targets_grid2.  Grid size N / (8 G) CTAs of 8 warps.
+// k_targets_grid2.  Grid size N / (8 G) CTAs of 8 warps.  With hout set
+// only the near-field sums and self terms are formed (two per grid point,
+// the layout k_targets_grid2 reads with hin).
 template <class T>
 __device__ inline T int_small_to_t(int v) { return int_to_t(v, T()); }
 
@@ -1665,7 +1911,8 @@ __global__ void __launch_bounds__(kTgtThreads) k_targets_gridw(
     TreeDims d, int inverse, const int32_t* __restrict__ start,
     const SrcPos<T>* __restrict__ pos, const cplx<T>* __restrict__ charge,
     const cplx<T>* __restrict__ st, const cplx<T>* __restrict__ lexp,
-    const cplx<T>* __restrict__ lvl2, const T* __restrict__ Ct, cplx<T>* __restrict__ out) {
+    const cplx<T>* __restrict__ lvl2, const T* __restrict__ Ct, cplx<T>* __restrict__ out,
+    cplx<T>* __restrict__ hout) {
   pdl_wait();
   pdl_trigger();
   constexpr int LOGG = G == 8 ? 3 : (G == 4 ? 2 : 1);
@@ -1745,6 +1992,11 @@ __global__ void __launch_bounds__(kTgtThreads) k_targets_gridw(
       for (int i = start[bp + 1] - 1; i >= start[bp] && (((int)pos[i].k0 - bp * s) & (N - 1)) == s; --i)
         self = cadd(self, st[i]);
     }
+  }
+  if (hout) {  // near field only (the two-point kernel's far part follows)
+    hout[2 * (int64_t)k] = v[0];
+    hout[2 * (int64_t)k + 1] = self;
+    return;
   }
   const int Q2 = 2 * d.q;
   const int arc = b >> (d.L - 2);
@@ -2117,11 +2369,36 @@ static FmmOps cot_ops(nufft_plan_s* pl) {
   return o;
 }
 
+// CTAs of a near-field pass beside the tree passes: one per target tile (0),
+// or r per SM looping over the tiles (NUFFT_NEAR_FWD_CTAS / NUFFT_NEAR_GRID_CTAS
+// = r), which keeps room for the tree kernels' CTAs on every SM; measured at
+// 2^20: every r tried (2..8) lost more near-field throughput than the tree
+// passes gained, so one CTA per tile is the default.
+static int near_ctas_per_sm(bool grid) {
+  static const int f = [] { const char* e = std::getenv("NUFFT_NEAR_FWD_CTAS"); return e ? std::atoi(e) : 0; }();
+  static const int g = [] { const char* e = std::getenv("NUFFT_NEAR_GRID_CTAS"); return e ? std::atoi(e) : 0; }();
+  return grid ? g : f;
+}
+static unsigned near_grid(int64_t tiles, bool grid) {
+  static const int nsm = [] {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      n = 0;
+    return n;
+  }();
+  const int r = near_ctas_per_sm(grid);
+  if (r <= 0 || nsm <= 0) return (unsigned)tiles;
+  const int64_t cap = (int64_t)r * nsm;
+  return (unsigned)(tiles < cap ? tiles : cap);
+}
+
 template <class T, class VO, int G>
 static void launch_targets_fwd(nufft_plan_s* pl, const TreeDims& d, const cplx<T>* f,
                                const cplx<T>* hnear, void* g, cplx<T>* hout = nullptr,
                                cudaStream_t st = nullptr) {
-  dim3 grid(nblk(pl->M, kTgtThreads), (unsigned)(pl->batch / G));
+  const int64_t tiles = nblk(pl->M, kTgtThreads);
+  dim3 grid(hout ? near_grid(tiles, false) : (unsigned)tiles, (unsigned)(pl->batch / G));
   launch_pdl(k_targets_fwd<T, VO, G>, grid, kTgtThreads, hnear ? 0 : NearCap<T, G>::fwd_bytes,
              st ? st : pl->stream, d, (int)pl->M, pl->k0, pl->delta, PlanT<T>::delta(pl),
              pl->perm, PlanT<T>::F(pl), PlanT<T>::E(pl), f, (const cplx<T>*)pl->lexp,
@@ -2150,8 +2427,11 @@ int fmm_forward(nufft_plan_s* pl, void* g) {
   if (split) {  // near field beside the tree passes (it needs f only)
     prof_begin(pl, NUFFT_STAGE_TARGETS);
     cudaStream_t s2 = side_begin(pl, 2);
-    if (c64) launch_targets_fwd<T, float2, 1>(pl, d, f, nullptr, g, (cplx<T>*)pl->hnear, s2);
-    else launch_targets_fwd<T, double2, 1>(pl, d, f, nullptr, g, (cplx<T>*)pl->hnear, s2);
+    {
+      LowPriority lp;
+      if (c64) launch_targets_fwd<T, float2, 1>(pl, d, f, nullptr, g, (cplx<T>*)pl->hnear, s2);
+      else launch_targets_fwd<T, double2, 1>(pl, d, f, nullptr, g, (cplx<T>*)pl->hnear, s2);
+    }
     side_end(pl, 2, s2);
     prof_end(pl, 1);
   }
@@ -2171,7 +2451,18 @@ int fmm_forward(nufft_plan_s* pl, void* g) {
       hnear = (const cplx<T>*)pl->charge;
     }
   }
-  if (pl->flags & NUFFT_IO_C64) {
+  if (split) {
+    const size_t sm = (size_t)(kFarLeaves * pl->p + 8 * pl->q + 1) * sizeof(cplx<T>);
+    const unsigned nb = nblk(pl->M, kTgtThreads);
+    if (c64)
+      launch_pdl(k_far_fwd<T, float2>, nb, kTgtThreads, sm, pl->stream, d, (int)pl->M, pl->k0,
+                 pl->delta, PlanT<T>::delta(pl), pl->perm, PlanT<T>::F(pl), PlanT<T>::E(pl), f,
+                 (const cplx<T>*)pl->lexp, PlanT<T>::lvl2(pl), hnear, (float2*)g);
+    else
+      launch_pdl(k_far_fwd<T, double2>, nb, kTgtThreads, sm, pl->stream, d, (int)pl->M, pl->k0,
+                 pl->delta, PlanT<T>::delta(pl), pl->perm, PlanT<T>::F(pl), PlanT<T>::E(pl), f,
+                 (const cplx<T>*)pl->lexp, PlanT<T>::lvl2(pl), hnear, (double2*)g);
+  } else if (pl->flags & NUFFT_IO_C64) {
     if (g4) launch_targets_fwd<T, float2, 4>(pl, d, f, hnear, g);
     else launch_targets_fwd<T, float2, 1>(pl, d, f, hnear, g);
   } else {
@@ -2194,6 +2485,54 @@ static bool gridw_wanted(const nufft_plan_s* pl) {
 
 // adjoint / inverse: samples g ([batch][M], original order) -> values on the
 // grid (cplx<T>, in pl->grid, [batch][N])
+// near-field part of the adjoint / inverse targets for one signal (hout: the
+// near-field sums and self terms only), or the whole evaluation (hout null)
+template <class T>
+static void launch_targets_grid1(nufft_plan_s* pl, const TreeDims& d, int inverse,
+                                 const SrcPos<T>* pos, const cplx<T>* charge, const cplx<T>* stt,
+                                 cplx<T>* hout, cudaStream_t st,
+                                 InlineSrc<T> isrc = InlineSrc<T>()) {
+  const cplx<T>* lexp_c = (const cplx<T>*)pl->lexp;
+  if (gridw_wanted(pl)) {
+    // many sources per grid point: one warp per G grid points (see k_targets_gridw)
+    const unsigned nb = nblk(pl->N, (int64_t)(kTgtThreads / 32) * (pl->s >= 8 ? 8 : pl->s));
+    if (pl->s >= 8)
+      launch_pdl(k_targets_gridw<T, 8>, nb, kTgtThreads, 0, st, d, inverse, pl->leaf_start, pos,
+                 charge, stt, lexp_c, PlanT<T>::lvl2(pl), PlanT<T>::Ct(pl), (cplx<T>*)pl->grid,
+                 hout);
+    else if (pl->s == 4)
+      launch_pdl(k_targets_gridw<T, 4>, nb, kTgtThreads, 0, st, d, inverse, pl->leaf_start, pos,
+                 charge, stt, lexp_c, PlanT<T>::lvl2(pl), PlanT<T>::Ct(pl), (cplx<T>*)pl->grid,
+                 hout);
+    else
+      launch_pdl(k_targets_gridw<T, 2>, nb, kTgtThreads, 0, st, d, inverse, pl->leaf_start, pos,
+                 charge, stt, lexp_c, PlanT<T>::lvl2(pl), PlanT<T>::Ct(pl), (cplx<T>*)pl->grid,
+                 hout);
+  } else {
+    if (hout)
+      launch_pdl(k_targets_grid2<T, 1>, near_grid(nblk(pl->N, 2 * kTgtThreads), true), kTgtThreads,
+                 NearCap<T, 1>::grid_bytes, st, d, inverse, pl->leaf_start, pos, charge, stt,
+                 lexp_c, PlanT<T>::lvl2(pl), PlanT<T>::Ct(pl), (cplx<T>*)pl->grid, hout,
+                 (const cplx<T>*)nullptr, isrc);
+    else
+      launch_pdl(k_targets_grid2<T, 0>, nblk(pl->N, 2 * kTgtThreads), kTgtThreads,
+                 NearCap<T, 1>::grid_bytes, st, d, inverse, pl->leaf_start, pos, charge, stt,
+                 lexp_c, PlanT<T>::lvl2(pl), PlanT<T>::Ct(pl), (cplx<T>*)pl->grid, hout,
+                 (const cplx<T>*)nullptr, isrc);
+  }
+}
+
+template <class T, class VI>
+static void launch_self_terms(nufft_plan_s* pl, const TreeDims& d, int inverse, const VI* g,
+                              const cplx<T>* charge, cplx<T>* stt, cudaStream_t s1) {
+  const dim3 gm(nblk(pl->M, 256), (unsigned)pl->batch);
+  launch_pdl(k_self_terms<T, VI>, gm, 256, 0, s1, (int)pl->M, inverse, (int)pl->N, d, pl->k0,
+             pl->delta, pl->perm, PlanT<T>::E(pl), charge, g, pl->Ct, PlanT<T>::Ct(pl),
+             PlanT<T>::delta(pl), KConst<T>::n_2pi_h(d), stt);
+}
+
+// adjoint / inverse: samples g ([batch][M], original order) -> values on the
+// grid (cplx<T>, in pl->grid, [batch][N])
 template <class T>
 int fmm_to_grid(nufft_plan_s* pl, const void* g, int inverse) {
   cudaStream_t st = pl->stream;
@@ -2201,39 +2540,100 @@ int fmm_to_grid(nufft_plan_s* pl, const void* g, int inverse) {
   const cplx<T>* coef = inverse ? PlanT<T>::D(pl) : PlanT<T>::F(pl);
   cplx<T>* charge = (cplx<T>*)pl->charge;
   const unsigned nsig = (unsigned)pl->batch;
-  const dim3 gm(nblk(pl->M, 256), nsig);
+  const TreeDims d = dims_of(pl);
+  cplx<T>* stt = (cplx<T>*)pl->selft;
+  SrcPos<T>* pos = (SrcPos<T>*)pl->srcpos;
   // charges q_i = coef_i g_perm(i) (conj(F_i) for the adjoint) and the
   // upward pass; the charges are formed inside the upward kernel when it
   // forms the leaf multipoles itself
   const FmmOps ops = cot_ops(pl);
   double2* l2 = pl->lvl2;
   float2* l2f = sizeof(T) == 4 ? pl->lvl2f : nullptr;
-  bool done = false;
-  int rc = c64 ? fmm_upward<T, float2>(pl, ops, false, charge, coef, (int)!inverse,
-                                       (const float2*)g, &done, l2, l2f)
+  int rc;
+  const bool split = split_near(pl) && pl->s >= 2;
+  if (split) {
+    // on side branch 2 the near-field sums (with the self terms), which need
+    // nothing from the tree passes: the two-point kernel forms the charges
+    // and self terms of its staged sources itself, so it starts at once
+    // beside the upward pass (which forms the charges it needs too); the
+    // warp-per-grid-points kernel reads them from a charge kernel and a
+    // self-term kernel run first
+    const bool inl = !gridw_wanted(pl);
+    InlineSrc<T> isrc;
+    if (inl) {
+      isrc.a.N = (int)pl->N;
+      isrc.a.inverse = inverse;
+      isrc.a.k0s = pl->k0;
+      isrc.a.dels = pl->delta;
+      isrc.a.perm = pl->perm;
+      isrc.a.Ct = pl->Ct;
+      isrc.a.gin = g;
+      isrc.a.gin64 = c64 ? 0 : 1;
+      isrc.coef = coef;
+      isrc.E = PlanT<T>::E(pl);
+      isrc.Ctt = PlanT<T>::Ct(pl);
+      isrc.delt = PlanT<T>::delta(pl);
+      isrc.n_2pi = KConst<T>::n_2pi_h(d);
+    } else {
+      prof_begin(pl, NUFFT_STAGE_P2M);
+      if (c64)
+        launch_pdl(k_charges<T, float2>, dim3(nblk(pl->M, 256), nsig), 256, 0, st, pl->M,
+                   pl->perm, coef, (int)!inverse, (const float2*)g, charge);
+      else
+        launch_pdl(k_charges<T, double2>, dim3(nblk(pl->M, 256), nsig), 256, 0, st, pl->M,
+                   pl->perm, coef, (int)!inverse, (const double2*)g, charge);
+      prof_end(pl, 1);
+    }
+    prof_begin(pl, NUFFT_STAGE_TARGETS);
+    cudaStream_t s2 = side_begin(pl, 2);
+    {
+      LowPriority lp;
+      if (!inl) {
+        if (c64) launch_self_terms<T, float2>(pl, d, inverse, (const float2*)g, charge, stt, s2);
+        else launch_self_terms<T, double2>(pl, d, inverse, (const double2*)g, charge, stt, s2);
+      }
+      launch_targets_grid1<T>(pl, d, inverse, pos, charge, stt, (cplx<T>*)pl->hnear, s2, isrc);
+    }
+    side_end(pl, 2, s2);
+    prof_end(pl, inl ? 1 : 2);
+    if (inl)
+      rc = c64 ? fmm_upward<T, float2>(pl, ops, false, charge, coef, (int)!inverse,
+                                       (const float2*)g, nullptr, l2, l2f)
                : fmm_upward<T, double2>(pl, ops, false, charge, coef, (int)!inverse,
-                                        (const double2*)g, &done, l2, l2f);
+                                        (const double2*)g, nullptr, l2, l2f);
+    else
+      rc = fmm_upward<T, float2>(pl, ops, false, charge, coef, (int)!inverse,
+                                 (const float2*)nullptr, nullptr, l2, l2f);
+    if (rc) return rc;
+    rc = fmm_downward<T>(pl, ops);
+    if (rc) return rc;
+    side_join(pl, 2);
+    prof_begin(pl, NUFFT_STAGE_TARGETS);
+    launch_pdl(k_targets_grid2<T, 2>, nblk(pl->N, 2 * kTgtThreads), kTgtThreads,
+               (size_t)(kFarLeaves * pl->p + 8 * pl->q + 1) * sizeof(cplx<T>), st, d, inverse,
+               pl->leaf_start, (const SrcPos<T>*)pos, (const cplx<T>*)charge, (const cplx<T>*)stt,
+               (const cplx<T>*)pl->lexp, PlanT<T>::lvl2(pl), PlanT<T>::Ct(pl), (cplx<T>*)pl->grid,
+               (cplx<T>*)nullptr, (const cplx<T>*)pl->hnear, InlineSrc<T>());
+    prof_end(pl, 1);
+    return cudaGetLastError() == cudaSuccess ? NUFFT_OK : NUFFT_ECUDA;
+  }
+  bool done = false;
+  rc = c64 ? fmm_upward<T, float2>(pl, ops, false, charge, coef, (int)!inverse,
+                                   (const float2*)g, &done, l2, l2f)
+           : fmm_upward<T, double2>(pl, ops, false, charge, coef, (int)!inverse,
+                                    (const double2*)g, &done, l2, l2f);
   if (rc) return rc;
   if (!done) return NUFFT_ECUDA;
   // self terms on the side branch (they need the charges; only the targets
   // kernel needs them), overlapping the downward pass
-  const TreeDims d = dims_of(pl);
-  cplx<T>* stt = (cplx<T>*)pl->selft;
   prof_begin(pl, NUFFT_STAGE_OTHER);
   cudaStream_t s1 = side_begin(pl, 1);
-  if (c64)
-    launch_pdl(k_self_terms<T, float2>, gm, 256, 0, s1, (int)pl->M, inverse, (int)pl->N, d, pl->k0,
-               pl->delta, pl->perm, PlanT<T>::E(pl), charge, (const float2*)g, pl->Ct,
-               PlanT<T>::Ct(pl), PlanT<T>::delta(pl), KConst<T>::n_2pi_h(d), stt);
-  else
-    launch_pdl(k_self_terms<T, double2>, gm, 256, 0, s1, (int)pl->M, inverse, (int)pl->N, d, pl->k0,
-               pl->delta, pl->perm, PlanT<T>::E(pl), charge, (const double2*)g, pl->Ct,
-               PlanT<T>::Ct(pl), PlanT<T>::delta(pl), KConst<T>::n_2pi_h(d), stt);
+  if (c64) launch_self_terms<T, float2>(pl, d, inverse, (const float2*)g, charge, stt, s1);
+  else launch_self_terms<T, double2>(pl, d, inverse, (const double2*)g, charge, stt, s1);
   side_end(pl, 1, s1);
   prof_end(pl, 1);
   rc = fmm_downward<T>(pl, ops);
   if (rc) return rc;
-  SrcPos<T>* pos = (SrcPos<T>*)pl->srcpos;
   side_join(pl, 1);
   prof_begin(pl, NUFFT_STAGE_TARGETS);
   const cplx<T>* lexp_c = (const cplx<T>*)pl->lexp;
@@ -2241,22 +2641,8 @@ int fmm_to_grid(nufft_plan_s* pl, const void* g, int inverse) {
     launch_pdl(k_targets_grid<T, 4>, dim3(nblk(pl->N, kTgtThreads), nsig / 4), kTgtThreads,
                NearCap<T, 4>::grid_bytes, st, d, inverse, pl->leaf_start, pos, charge, stt,
                lexp_c, PlanT<T>::lvl2(pl), PlanT<T>::Ct(pl), (cplx<T>*)pl->grid);
-  else if (nsig == 1 && pl->s >= 2 && gridw_wanted(pl)) {
-    // many sources per grid point: one warp per G grid points (see k_targets_gridw)
-    const unsigned nb = nblk(pl->N, (int64_t)(kTgtThreads / 32) * (pl->s >= 8 ? 8 : pl->s));
-    if (pl->s >= 8)
-      launch_pdl(k_targets_gridw<T, 8>, nb, kTgtThreads, 0, st, d, inverse, pl->leaf_start, pos,
-                 charge, stt, lexp_c, PlanT<T>::lvl2(pl), PlanT<T>::Ct(pl), (cplx<T>*)pl->grid);
-    else if (pl->s == 4)
-      launch_pdl(k_targets_gridw<T, 4>, nb, kTgtThreads, 0, st, d, inverse, pl->leaf_start, pos,
-                 charge, stt, lexp_c, PlanT<T>::lvl2(pl), PlanT<T>::Ct(pl), (cplx<T>*)pl->grid);
-    else
-      launch_pdl(k_targets_gridw<T, 2>, nb, kTgtThreads, 0, st, d, inverse, pl->leaf_start, pos,
-                 charge, stt, lexp_c, PlanT<T>::lvl2(pl), PlanT<T>::Ct(pl), (cplx<T>*)pl->grid);
-  } else if (nsig == 1 && pl->s >= 2)
-    launch_pdl(k_targets_grid2<T>, nblk(pl->N, 2 * kTgtThreads), kTgtThreads,
-               NearCap<T, 1>::grid_bytes, st, d, inverse, pl->leaf_start, pos, charge, stt,
-               lexp_c, PlanT<T>::lvl2(pl), PlanT<T>::Ct(pl), (cplx<T>*)pl->grid);
+  else if (nsig == 1 && pl->s >= 2)
+    launch_targets_grid1<T>(pl, d, inverse, pos, charge, stt, nullptr, st);
   else
     launch_pdl(k_targets_grid<T, 1>, dim3(nblk(pl->N, kTgtThreads), nsig), kTgtThreads,
                NearCap<T, 1>::grid_bytes, st, d, inverse, pl->leaf_start, pos, charge, stt,

@@ -18,6 +18,21 @@ bool fused_up_enabled() {
   static const bool on = std::getenv("NUFFT_NO_FUSED_UP") == nullptr;
   return on;
 }
+namespace {
+thread_local int g_low_depth = 0;
+int high_priority() {
+  static const int v = [] {
+    if (std::getenv("NUFFT_NO_PRIORITY")) return 0;
+    int least = 0, greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) return 0;
+    return greatest < least ? greatest : 0;  // numerically lower is higher
+  }();
+  return v;
+}
+}  // namespace
+int launch_priority() { return g_low_depth > 0 ? 0 : high_priority(); }
+LowPriority::LowPriority() { ++g_low_depth; }
+LowPriority::~LowPriority() { --g_low_depth; }
 }  // namespace nufft
 
 using namespace nufft;
@@ -685,7 +700,8 @@ static int exec_op(nufft_plan_s* pl, int op, const void* in, void* out) {
     return rc ? rc : NUFFT_ECUDA;
   }
   cudaGraphExec_t ex = nullptr;
-  ec = cudaGraphInstantiate(&ex, g, 0);
+  // per-node priorities (critical path high, the near-field branch default)
+  ec = cudaGraphInstantiate(&ex, g, cudaGraphInstantiateFlagUseNodePriority);
   cudaGraphDestroy(g);
   if (ec != cudaSuccess) return NUFFT_ECUDA;
   auto& slot = pl->graphs[pl->graph_next];
