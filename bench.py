@@ -42,12 +42,14 @@ EPS_MIXED = 1e-6
 EPS_FP64 = 1e-12
 JITTER = 0.4
 METRIC = "NUFFT points/s (forward + square inverse, N=M=2^20, mixed eps=1e-6)"
-# DRAM bytes (read + write) of the target-evaluation kernels per step (one
-# k_targets_fwd + one k_targets_grid2 launch) from one ncu capture of this
-# workload; reported only while the kernels' source text still hashes to
-# `sha1` (a changed kernel reports null until it is captured again)
-TARGETS_TRAFFIC = {"bytes_per_step": 79026944, "sha1": "c5a3ea2716aab91aba53280fb108349e118a4d30"}
-STAGE_KERNELS = {"targets": "k_targets_fwd + k_targets_grid2", "fft": "k_fft_st",
+# DRAM bytes (read + write) of the target-evaluation kernels per step (the
+# forward's near-field and far-part launches, k_targets_fwd + k_far_fwd, and
+# the inverse's, k_targets_grid2 in its near-field and far-part forms) from
+# one ncu capture of this workload; reported only while the kernels' source
+# text still hashes to `sha1` (a changed kernel reports null until it is
+# captured again)
+TARGETS_TRAFFIC = {"bytes_per_step": 155803136, "sha1": "d6d161cecd99ba1b48154465aa4bbe565ac8bc72"}
+STAGE_KERNELS = {"targets": "k_targets_fwd + k_far_fwd + k_targets_grid2 (near-field and far-part forms)", "fft": "k_fft_st",
                  "m2l": "k_down_fused (tensor-core levels: k_down_top + k_down_sub + k_m2l_tc)",
                  "p2m": "k_p2m_* + k_charges (when not inside k_up_fused)",
                  "m2m": "k_up_fused (with P2M and the charges when they fit)",
@@ -433,7 +435,7 @@ def run_ours(args):
     if dom == "targets" and TARGETS_TRAFFIC["bytes_per_step"] and \
             TARGETS_TRAFFIC["sha1"] == targets_source_sha1():
         roof["traffic"] = TARGETS_TRAFFIC["bytes_per_step"]
-        roof["traffic_unit"] = "DRAM bytes per step (ncu dram__bytes_read + write, both target kernels)"
+        roof["traffic_unit"] = "DRAM bytes per step (ncu dram__bytes_read + write, the four target launches)"
     roof["kernel_stage"] = dom
     roof["kernels"] = STAGE_KERNELS.get(dom)
     if roof["bound"] == "hbm":
