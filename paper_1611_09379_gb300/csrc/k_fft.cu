@@ -22,6 +22,9 @@ namespace nufft {
 constexpr int kFftSmemElems = 4096;  // R * J complex elements per CTA (at most)
 constexpr int kFftMaxThreads = 512;
 
+// Twiddle tables of a plan: w_N^m = T_hi[m >> b] T_lo[m & (2^b - 1)] (T_lo
+// first, 2^b entries, then T_hi, N / 2^b entries), then the radix-1024 pass
+// table w_1024^{ka t} at [ka 32 + t] (ka, t < 32).
 __global__ void k_fft_tables(double2* __restrict__ tw, int64_t N, int lo_bits) {
   int64_t nlo = int64_t(1) << lo_bits, nhi = N >> lo_bits;
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -33,6 +36,10 @@ __global__ void k_fft_tables(double2* __restrict__ tw, int64_t N, int lo_bits) {
     int64_t h = i - nlo;
     // 2 h 2^b / N reduced mod 2 exactly (all powers of two)
     sincospi(2.0 * (double)(h << lo_bits) / (double)N, &s, &c);
+    tw[i] = make_double2(c, s);
+  } else if (i < nlo + nhi + 1024) {
+    const int e = (int)(i - nlo - nhi);
+    sincospi((double)((e >> 5) * (e & 31)) / 512.0, &s, &c);  // exact argument
     tw[i] = make_double2(c, s);
   }
 }
@@ -352,6 +359,192 @@ __global__ void __launch_bounds__(kFftMaxThreads, sizeof(T) == 4 ? 3 : 2) k_fft_
   }
 }
 
+// ------------------------------------------- radix-1024 pass, one warp per column (FP32)
+//
+// The same pass as k_fft_st for R = 1024 = 32 x 32, with r = t + 32 m (t the
+// lane, m a register index) and r' = ka + 32 kb:
+//   A_{ka + 32 kb} = sum_t w_32^{t kb} [ w_1024^{t ka} sum_m a_{t + 32 m} w_32^{m ka} ]:
+// stage A is lane t's 32-point DFT over m in registers, then the twiddle
+// w_1024^{t ka} from a [ka][t] table in shared memory (conflict-free: the
+// lanes read consecutive entries), a transpose through shared memory inside
+// the warp (no CTA barrier), stage B lane ka's 32-point DFT over t.  The
+// CTA's four warps take four adjacent columns j; their strided rows are
+// loaded (and, for Ns > 1, stored) by the whole CTA as runs of four adjacent
+// elements through shared memory.  The pass twiddle w_{Ns R}^{r jm} factors
+// into w^{t jm} (per lane) times w^{32 m jm} (per warp, from shared memory).
+
+constexpr int kW32Cols = 4;      // columns (warps) per CTA
+constexpr int kW32Stride = 1060;  // column stride in shared memory: rows 33 m + t, + 4 (banks)
+constexpr size_t kW32Smem = (size_t)(kW32Cols * kW32Stride + 1024 + kW32Cols * 32) * sizeof(float2);
+
+// cos and sin of 2 pi e / 32 (the exact values rounded to FP32), e in [0, 32)
+__host__ __device__ constexpr float w32_cos(int e) {
+  constexpr float q[9] = {1.0f, 0.98078528040323044913f, 0.92387953251128675613f,
+                          0.83146961230254523708f, 0.70710678118654752440f,
+                          0.55557023301960222474f, 0.38268343236508977173f,
+                          0.19509032201612826785f, 0.0f};
+  return e <= 8 ? q[e] : e <= 16 ? -q[16 - e] : e <= 24 ? -q[e - 16] : q[32 - e];
+}
+__host__ __device__ constexpr float w32_sin(int e) { return w32_cos((e + 24) & 31); }
+
+// x e^{sg 2 pi i e / 32}, e a compile-time constant after unrolling
+__device__ inline float2 w32_mul(float2 x, int e, float sg) {
+  e &= 31;
+  if (e == 0) return x;
+  if (e == 8) return mul_si<float>(x, sg);
+  if (e == 16) return make_float2(-x.x, -x.y);
+  if (e == 24) return mul_si<float>(x, -sg);
+  const float c = w32_cos(e), s = sg * w32_sin(e);
+  return make_float2(x.x * c - x.y * s, x.x * s + x.y * c);
+}
+
+// X_k = sum_n a_n e^{sg 2 pi i n k / 32} in place, natural order in and out:
+// n = n1 + 4 n2, k = 8 k1 + k2, four radix-8 DFTs over n2, the twiddles
+// w_32^{n1 k2}, eight radix-4 DFTs over n1.
+__device__ inline void dft32(float2* a, float sg) {
+  float2 y[32];  // y[n1 8 + k2]
+#pragma unroll
+  for (int n1 = 0; n1 < 4; ++n1) {
+    float2 b[8];
+#pragma unroll
+    for (int n2 = 0; n2 < 8; ++n2) b[n2] = a[n1 + 4 * n2];
+    dft_small<float, 3>(b, sg);
+#pragma unroll
+    for (int k2 = 0; k2 < 8; ++k2) y[n1 * 8 + k2] = w32_mul(b[brev_c<3>(k2)], n1 * k2, sg);
+  }
+#pragma unroll
+  for (int k2 = 0; k2 < 8; ++k2) {
+    float2 c[4];
+#pragma unroll
+    for (int n1 = 0; n1 < 4; ++n1) c[n1] = y[n1 * 8 + k2];
+    dft_small<float, 2>(c, sg);
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) a[8 * k1 + k2] = c[brev_c<2>(k1)];
+  }
+}
+
+// One radix-1024 Stockham pass (the k_fft_st pass with R = 1024) for
+// N = 2^logN >= 4096 and Ns = 1 or Ns >= 4: 128 threads, four columns
+// j = 4 blockIdx.x + warp, signal blockIdx.y.  tw: the two-level FP32
+// twiddle tables of w_N; tw32: w_1024^{ka t} at [ka 32 + t] (sign +1).
+__global__ void __launch_bounds__(128, 4) k_fft_w32(
+    const void* __restrict__ in, int in_f64, void* __restrict__ out, int out_f64, int logN,
+    int logNs, int sign, const float2* __restrict__ tw, const float2* __restrict__ tw32,
+    int lo_bits, uint32_t n_in, uint32_t n_out) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float2* X = reinterpret_cast<float2*>(smraw);  // [4][kW32Stride]
+  float2* TW = X + kW32Cols * kW32Stride;        // [32 ka][32 t]
+  float2* BM = TW + 1024;                        // [4 warps][32 m]
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const float sg = (float)sign;
+  const uint32_t N = 1u << logN, nmask = N - 1, Ns = 1u << logNs;
+  const int lognr = logN - 10;
+  const uint32_t lo_mask = (1u << lo_bits) - 1;
+  for (int e = tid; e < 1024; e += 128) {
+    float2 v = tw32[e];
+    v.y *= sg;
+    TW[e] = v;
+  }
+  const uint32_t j0 = blockIdx.x * (uint32_t)kW32Cols, j = j0 + w, jm = j & (Ns - 1);
+  float2 At = make_float2(1.0f, 0.0f);
+  if (Ns > 1) {  // w_{Ns R}^{e} = w_N^{e N / (Ns R)}, N / (Ns R) = 2^lstep
+    const int lstep = logN - logNs - 10;
+    At = twiddle32<float>(tw, ((lane * jm) << lstep) & nmask, lo_bits, lo_mask, sg);
+    BM[w * 32 + lane] =
+        twiddle32<float>(tw, ((32u * lane * jm) << lstep) & nmask, lo_bits, lo_mask, sg);
+  }
+  // (the twiddle tables are plan constants: read before the predecessor ends)
+  pdl_wait();
+  pdl_trigger();
+  const int c4 = tid & 3, q4 = tid >> 2;  // staging: column j0 + c4, rows q4 + 32 i
+  {
+    float2* xc = X + c4 * kW32Stride + q4;
+    const uint32_t e0 = j0 + c4 + ((uint32_t)q4 << lognr), de = 32u << lognr;
+    if (in_f64) {
+      const double2* src = reinterpret_cast<const double2*>(in) + (size_t)blockIdx.y * n_in;
+#pragma unroll
+      for (int h = 0; h < 32; h += 16) {
+        double2 raw[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const uint32_t e = e0 + (uint32_t)(h + i) * de;
+          if (e < n_in) raw[i] = src[e];  // elements n_in .. N - 1 are the zero padding
+          else raw[i] = make_double2(0.0, 0.0);
+        }
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+          xc[33 * (h + i)] = make_float2((float)raw[i].x, (float)raw[i].y);
+      }
+    } else {
+      const float2* src = reinterpret_cast<const float2*>(in) + (size_t)blockIdx.y * n_in;
+      float2 raw[32];
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        const uint32_t e = e0 + (uint32_t)i * de;
+        raw[i] = e < n_in ? src[e] : make_float2(0.0f, 0.0f);
+      }
+#pragma unroll
+      for (int i = 0; i < 32; ++i) xc[33 * i] = raw[i];
+    }
+  }
+  __syncthreads();
+  float2* xw = X + w * kW32Stride;
+  float2 a[32];
+#pragma unroll
+  for (int m = 0; m < 32; ++m) a[m] = xw[33 * m + lane];
+  if (Ns > 1) {
+#pragma unroll
+    for (int m = 0; m < 32; ++m) a[m] = cmul(a[m], cmul(At, BM[w * 32 + m]));
+  }
+  dft32(a, sg);  // a[ka] = sum_m a_{t + 32 m} w_32^{m ka}
+#pragma unroll
+  for (int ka = 1; ka < 32; ++ka) a[ka] = cmul(a[ka], TW[ka * 32 + lane]);
+  __syncwarp();  // every lane's stage-A reads are done
+#pragma unroll
+  for (int ka = 0; ka < 32; ++ka) xw[33 * ka + lane] = a[ka];
+  __syncwarp();
+#pragma unroll
+  for (int t = 0; t < 32; ++t) a[t] = xw[33 * lane + t];
+  dft32(a, sg);  // a[kb] = A_{lane + 32 kb}
+  const size_t so = (size_t)blockIdx.y * n_out;
+  if (Ns == 1) {  // out[j R + r']: 32 consecutive elements per kb
+    const uint32_t base = (j << 10) + lane;
+    if (out_f64) {
+      double2* o = reinterpret_cast<double2*>(out) + so;
+#pragma unroll
+      for (int kb = 0; kb < 32; ++kb)
+        if (base + 32u * kb < n_out) o[base + 32u * kb] = make_double2(a[kb].x, a[kb].y);
+    } else {
+      float2* o = reinterpret_cast<float2*>(out) + so;
+#pragma unroll
+      for (int kb = 0; kb < 32; ++kb)
+        if (base + 32u * kb < n_out) o[base + 32u * kb] = a[kb];
+    }
+    return;
+  }
+  // out[(j / Ns) Ns R + jm + r' Ns]: rows of the four adjacent columns
+  __syncwarp();
+#pragma unroll
+  for (int kb = 0; kb < 32; ++kb) xw[33 * kb + lane] = a[kb];
+  __syncthreads();
+  const float2* xc = X + c4 * kW32Stride + q4;
+  const uint32_t base = ((j0 >> logNs) << (logNs + 10)) + (j0 & (Ns - 1)) + c4 + q4 * Ns;
+  const uint32_t ds = 32u * Ns;
+  if (out_f64) {
+    double2* o = reinterpret_cast<double2*>(out) + so;
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+      const float2 v = xc[33 * i];
+      if (base + i * ds < n_out) o[base + i * ds] = make_double2(v.x, v.y);
+    }
+  } else {
+    float2* o = reinterpret_cast<float2*>(out) + so;
+#pragma unroll
+    for (int i = 0; i < 32; ++i)
+      if (base + i * ds < n_out) o[base + i * ds] = xc[33 * i];
+  }
+}
+
 __global__ void k_tw_to_float(const double2* __restrict__ a, float2* __restrict__ b, int64_t n) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < n) b[i] = make_float2((float)a[i].x, (float)a[i].y);
@@ -367,15 +560,18 @@ int fft_lo_bits(int64_t N) {
   return (L + 1) / 2;
 }
 
-size_t fft_table_elems(int64_t N) {
+// entries of the two-level tables of w_N (the radix-1024 table follows them)
+static size_t fft_table_base(int64_t N) {
   int b = fft_lo_bits(N);
   return (size_t)(int64_t(1) << b) + (size_t)(N >> b);
 }
 
+size_t fft_table_elems(int64_t N) { return fft_table_base(N) + 1024; }
+
 // tw: double2 tables, twf: float2 copy (may be null)
 int fft_init_tables(double2* tw, float2* twf, int64_t N, cudaStream_t st) {
   int b = fft_lo_bits(N);
-  int64_t n = (int64_t(1) << b) + (N >> b);
+  int64_t n = (int64_t)fft_table_elems(N);
   k_fft_tables<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(tw, N, b);
   if (twf) k_tw_to_float<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(tw, twf, n);
   return cudaGetLastError() == cudaSuccess ? NUFFT_OK : NUFFT_ECUDA;
@@ -444,6 +640,16 @@ static int fft_pass(int logR, dim3 grid, int threads, size_t smem, cudaStream_t 
 
 static int g_fft_sms = 0;
 
+// The one-warp-per-column radix-1024 pass (FP32) where it applies;
+// NUFFT_FFT_NO_W32=1 keeps every pass on k_fft_st, for measurements.
+static bool fft_w32_enabled() {
+  static const bool v = [] {
+    const char* e = std::getenv("NUFFT_FFT_NO_W32");
+    return !(e && std::atoi(e) == 1);
+  }();
+  return v;
+}
+
 // Fewest columns per CTA the pass planner goes down to when the grid of
 // CTAs is small (4: every strided row is a full 32-byte sector of complex64);
 // NUFFT_FFT_MIN_COLS (1, 2, 4 or 8) overrides it for measurements.
@@ -488,6 +694,19 @@ int fft_run(const void* in, int in_f64, void* out, int out_f64, cplx<T>* buf, cp
     const int lr = logR[i];
     const int R = 1 << lr, TPC = R >= 8 ? R / 8 : 1;
     const int64_t NR = N >> lr;
+    const uint32_t pin = (uint32_t)(i == 0 ? n_in : N), pout = (uint32_t)(last ? n_out : N);
+    if (!tf64 && lr == 10 && NR >= kW32Cols && (Ns == 1 || Ns >= kW32Cols) && fft_w32_enabled()) {
+      int logNs = 0;
+      while ((int64_t(1) << logNs) < Ns) ++logNs;
+      launch_pdl(k_fft_w32, dim3((unsigned)(NR / kW32Cols), (unsigned)batch), 128, kW32Smem, st,
+                 src, src_f64, dst, dst_f64, L, logNs, sign,
+                 reinterpret_cast<const float2*>(tw),
+                 reinterpret_cast<const float2*>(tw) + fft_table_base(N), b, pin, pout);
+      src = dst;
+      src_f64 = dst_f64;
+      Ns <<= lr;
+      continue;
+    }
     // columns per CTA: at most kFftMaxThreads threads and kFftSmemElems
     // elements, at least fft_min_cols() (contiguous runs), fewer while the
     // grid is small
@@ -503,7 +722,6 @@ int fft_run(const void* in, int in_f64, void* out, int out_f64, cplx<T>* buf, cp
     unsigned grid = (unsigned)(NR / J);
     int logNs = 0;
     while ((int64_t(1) << logNs) < Ns) ++logNs;
-    const uint32_t pin = (uint32_t)(i == 0 ? n_in : N), pout = (uint32_t)(last ? n_out : N);
     int rc = fft_pass<T>(lr, dim3(grid, (unsigned)batch), J * TPC, smem, st, pin, pout, src,
                          src_f64, dst, dst_f64, L, logNs, J, logJ, sign, tw, b);
     if (rc) return rc;
