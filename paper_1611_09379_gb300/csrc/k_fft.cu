@@ -440,18 +440,25 @@ __global__ void __launch_bounds__(128, 4) k_fft_w32(
   const uint32_t N = 1u << logN, nmask = N - 1, Ns = 1u << logNs;
   const int lognr = logN - 10;
   const uint32_t lo_mask = (1u << lo_bits) - 1;
-  for (int e = tid; e < 1024; e += 128) {
-    float2 v = tw32[e];
-    v.y *= sg;
-    TW[e] = v;
-  }
   const uint32_t j0 = blockIdx.x * (uint32_t)kW32Cols, j = j0 + w, jm = j & (Ns - 1);
   float2 At = make_float2(1.0f, 0.0f);
-  if (Ns > 1) {  // w_{Ns R}^{e} = w_N^{e N / (Ns R)}, N / (Ns R) = 2^lstep
-    const int lstep = logN - logNs - 10;
-    At = twiddle32<float>(tw, ((lane * jm) << lstep) & nmask, lo_bits, lo_mask, sg);
-    BM[w * 32 + lane] =
-        twiddle32<float>(tw, ((32u * lane * jm) << lstep) & nmask, lo_bits, lo_mask, sg);
+  {
+    // all table loads in flight together (a loop of load-store pairs would
+    // wait for each load in turn)
+    float2 tv[1024 / 128];
+#pragma unroll
+    for (int u = 0; u < 1024 / 128; ++u) tv[u] = tw32[tid + 128 * u];
+    if (Ns > 1) {  // w_{Ns R}^{e} = w_N^{e N / (Ns R)}, N / (Ns R) = 2^lstep
+      const int lstep = logN - logNs - 10;
+      At = twiddle32<float>(tw, ((lane * jm) << lstep) & nmask, lo_bits, lo_mask, sg);
+      BM[w * 32 + lane] =
+          twiddle32<float>(tw, ((32u * lane * jm) << lstep) & nmask, lo_bits, lo_mask, sg);
+    }
+#pragma unroll
+    for (int u = 0; u < 1024 / 128; ++u) {
+      tv[u].y *= sg;
+      TW[tid + 128 * u] = tv[u];
+    }
   }
   // (the twiddle tables are plan constants: read before the predecessor ends)
   pdl_wait();

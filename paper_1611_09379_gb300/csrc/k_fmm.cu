@@ -127,7 +127,7 @@ size_t p2m_smem(int pm) {
 // subtraction (no division).  qget(i, first) returns the charge of sorted
 // source i (first: in the first pass over the moments); out(m, v) stores
 // moment m.
-template <class T, class QGet, class Out>
+template <class T, int PM = 0, class QGet, class Out>
 __device__ inline void p2m_leaf_warp(const TreeDims& d, int64_t b, int lane, cplx<T>* tile,
                                      const int32_t* __restrict__ start,
                                      const int32_t* __restrict__ k0,
@@ -136,8 +136,9 @@ __device__ inline void p2m_leaf_warp(const TreeDims& d, int64_t b, int lane, cpl
   const int N = (int)d.N;
   const int bs = (int)b * d.s;
   const T inv_s = (T)1 / (T)d.s;
-  for (int mc = 0; mc < d.pm; mc += 32) {
-    const int nm = d.pm - mc < 32 ? d.pm - mc : 32;
+  const int pmv = PM > 0 ? PM : d.pm;  // (PM <= 32: one pass over the moments)
+  for (int mc = 0; mc < pmv; mc += 32) {
+    const int nm = pmv - mc < 32 ? pmv - mc : 32;
     T accr = 0, acci = 0;
     // two chunks of 32 sources per step: both chunks' loads (and charge
     // gathers) are issued before either is reduced
@@ -161,6 +162,7 @@ __device__ inline void p2m_leaf_warp(const TreeDims& d, int64_t b, int lane, cpl
         if (cb >= e) break;
         T pw = 1;
         for (int m = 0; m < mc; ++m) pw *= rho[h];
+#pragma unroll(PM > 0 ? PM : 1)
         for (int m = 0; m < nm; ++m) {
           tile[m * kP2mPitch + lane] = mk<T>(q[h].x * pw, q[h].y * pw);
           pw *= rho[h];
@@ -226,6 +228,23 @@ __device__ inline cplx<T> m2m_one(const T* __restrict__ A, int pm, int m,
                                   const cplx<T>* __restrict__ c0, const cplx<T>* __restrict__ c1) {
   T ar = 0, ai = 0;
   for (int k = 0; k <= m; ++k) {
+    T w0 = A[k * pm + m], w1 = A[pm * pm + k * pm + m];
+    cplx<T> x0 = c0[k], x1 = c1[k];
+    ar = fma(w0, x0.x, fma(w1, x1.x, ar));
+    ai = fma(w0, x0.y, fma(w1, x1.y, ai));
+  }
+  return mk<T>(ar, ai);
+}
+
+// m2m_one over all k < pm (the table is zero for k > m, and fma(0, x, a) = a
+// for finite x): the same value, with a loop length that is the same for
+// every lane (unrolled where pm is a compile-time constant)
+template <class T>
+__device__ inline cplx<T> m2m_full(const T* __restrict__ A, int pm, int m,
+                                   const cplx<T>* __restrict__ c0, const cplx<T>* __restrict__ c1) {
+  T ar = 0, ai = 0;
+#pragma unroll
+  for (int k = 0; k < pm; ++k) {
     T w0 = A[k * pm + m], w1 = A[pm * pm + k * pm + m];
     cplx<T> x0 = c0[k], x1 = c1[k];
     ar = fma(w0, x0.x, fma(w1, x1.x, ar));
@@ -361,7 +380,10 @@ __device__ inline void stage_batched(int n, V* __restrict__ dst, Src src) {
   }
 }
 
-template <class T, int SRC, class VI>
+// PM > 0: the multipole length pm as a compile-time constant (d.pm == PM),
+// so the M2M and P2M loops over moments are unrolled and their divisions by
+// pm are by a constant; PM = 0: pm from d.
+template <class T, int SRC, class VI, int PM = 0>
 __global__ void __launch_bounds__(kUpThreads) k_up_fused(TreeDims d, UpStages sg,
                                                          const T* __restrict__ op,
                                                          cplx<T>* __restrict__ mexp,
@@ -369,7 +391,7 @@ __global__ void __launch_bounds__(kUpThreads) k_up_fused(TreeDims d, UpStages sg
                                                          UpSrc<T, VI> src) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ int s_last;
-  const int pm = d.pm;
+  const int pm = PM > 0 ? PM : d.pm;
   T* A = reinterpret_cast<T*>(smraw);
   cplx<T>* cur0 = reinterpret_cast<cplx<T>*>(A + 2 * pm * pm);  // [pm << dmax]
   cplx<T>* nxt0 = cur0 + (pm << sg.dmax);                       // [pm << (dmax - 1)]
@@ -421,6 +443,7 @@ __global__ void __launch_bounds__(kUpThreads) k_up_fused(TreeDims d, UpStages sg
         const int lf = e / pm, m = e - lf * pm;
         const cplx<T>* row = qs + lf * (sN + 1);
         T ar = 0, ai = 0;
+#pragma unroll 8
         for (int o = 0; o < sN; ++o) {
           const cplx<T> v = row[o];
           const T w = rps[o * pm + m];
@@ -441,7 +464,7 @@ __global__ void __launch_bounds__(kUpThreads) k_up_fused(TreeDims d, UpStages sg
       const VI* gin = src.gin ? src.gin + so : nullptr;
       cplx<T>* cout = src.charge ? src.charge + so : nullptr;
       for (int lf = warp; lf < nl0; lf += kUpThreads / 32) {
-        p2m_leaf_warp<T>(
+        p2m_leaf_warp<T, PM>(
             d, b0 + lf, lane, tile, src.start, src.k0, src.delta_t,
             [&](int i, bool first) {
               if (!gin) return chg[i];
@@ -465,7 +488,7 @@ __global__ void __launch_bounds__(kUpThreads) k_up_fused(TreeDims d, UpStages sg
       cplx<T>* dst = mexp + (level_off(lev - 1) + (box << (lev - 1 - lt))) * pm;
       for (int e = threadIdx.x; e < np * pm; e += blockDim.x) {
         int ip = e / pm, m = e - ip * pm;
-        cplx<T> v = m2m_one<T>(A, pm, m, cur + 2 * ip * pm, cur + (2 * ip + 1) * pm);
+        cplx<T> v = m2m_full<T>(A, pm, m, cur + 2 * ip * pm, cur + (2 * ip + 1) * pm);
         nxt[e] = v;
         dst[e] = v;
       }
@@ -518,6 +541,7 @@ __device__ inline cplx<T> m2l_one(const T* __restrict__ Tm, const T* __restrict_
     const int slot = odd ? t : t + 1;
     const cplx<T>* mv = msrc(off);
     const T* Tt = Tm + slot * p * p + n;
+#pragma unroll
     for (int m = 0; m < p; ++m) {
       T w = Tt[m * p];
       cplx<T> x = mv[m];
@@ -572,6 +596,7 @@ __device__ inline cplx<T> l2l_full(const T* __restrict__ Tl, int p, int n, int o
                                    const cplx<T>* __restrict__ lpar) {
   T ar = 0, ai = 0;
   const T* Tt = Tl + odd * p * p + n;
+#pragma unroll
   for (int k = 0; k < p; ++k) {
     T w = Tt[k * p];
     cplx<T> x = lpar[k];
@@ -693,16 +718,20 @@ __global__ void __launch_bounds__(512) k_down_sub(TreeDims d, int lt, int lb,
 //   Loc_3 = Lambda_3(a_3),  Loc_l = Lambda_l(a_l) + L2L_{a_l & 1}(Loc_{l-1}),
 // (every CTA repeats its own ancestors' chain, (lt - 2)(3 p^2 + p^2 / 2)
 // multiply-adds, so no CTA waits for another), then the subtree's levels in
-// place.  Only level lb is written back.
-template <class T>
-__global__ void __launch_bounds__(512) k_down_fused(TreeDims d, int lt, int lb,
+// place.  Only level lb is written back.  P > 0: the expansion length p as
+// a compile-time constant (d.p == P), so every loop over coefficients is
+// unrolled and every index into the tables is a constant offset; P = 0:
+// p from d.  512 threads.
+constexpr int kDownThreads = 512;
+template <class T, int P = 0>
+__global__ void __launch_bounds__(kDownThreads) k_down_fused(TreeDims d, int lt, int lb,
                                                     const T* __restrict__ op_m2l,
                                                     const T* __restrict__ op_l2l,
                                                     const cplx<T>* __restrict__ mexp,
                                                     cplx<T>* __restrict__ lexp, int log_kernel,
                                                     int log2N) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int p = d.p, pm = d.pm;
+  const int p = P > 0 ? P : d.p, pm = d.pm;
   const int depth = lb - lt;
   const int na = lt - 2;  // ancestors' levels 3..lt
   // level l = lt + j (j = 1..depth): its 2^j boxes' parts at Lam + (2^j - 2) p,
@@ -748,9 +777,9 @@ __global__ void __launch_bounds__(512) k_down_fused(TreeDims d, int lt, int lb,
   });
   __syncthreads();
   // M2L parts: the ancestors' and, level by level, the subtree's; a thread's
-  // outputs (box bi, coefficient n) advance by blockDim.x = sb p + sn
-  const int sb = (int)blockDim.x / p, sn = (int)blockDim.x - sb * p;
-  for (int e = threadIdx.x; e < na * p; e += blockDim.x) {
+  // outputs (box bi, coefficient n) advance by kDownThreads = sb p + sn
+  const int sb = kDownThreads / p, sn = kDownThreads - sb * p;
+  for (int e = threadIdx.x; e < na * p; e += kDownThreads) {
     const int li = e / p, n = e - li * p;
     const int l = 3 + li;
     const int odd = (int)((c >> (lt - l)) & 1);
@@ -801,8 +830,12 @@ __global__ void __launch_bounds__(512) k_down_fused(TreeDims d, int lt, int lb,
   __syncthreads();
   const cplx<T>* fin = Lam + ((1 << depth) - 2) * p;
   cplx<T>* dst = lexp + (level_off(lb) - 4 + (c << depth)) * p;
-  for (int i = threadIdx.x; i < (p << depth); i += blockDim.x) dst[i] = fin[i];
+  for (int i = threadIdx.x; i < (p << depth); i += kDownThreads) dst[i] = fin[i];
 }
+
+// expansion lengths with a compile-time instance of the one-launch tree
+// passes (FP32); other lengths take the run-time instance
+#define NUFFT_TREE_P_LIST(X) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(16)
 
 // ---------------------------------------------------------------- level 2
 
@@ -1179,8 +1212,12 @@ __device__ inline void targets_fwd_tile(
       const float2* w = sf + (b - bl) * s;
       NearAcc2f a2;
       near_window_ex2w(3 * s, ex, a2, [&](int i, int u, auto chk) {
+        // t_b = t_a - 1 from the rounded t_a: for every included pair
+        // |t_b| >= 1/2 and |t_a| <= |t_b| + 1, so t_b keeps a relative
+        // error of at most two roundings
         const T ta = (D0 - (T)i) - (T)u, tb = ta - (T)1;
-        T ra = rcp_t(ta + dt), rb = rcp_t(tb + dt);
+        const T xa = ta + dt;
+        T ra = rcp_t(xa), rb = rcp_t(xa - (T)1);
         if (decltype(chk)::value) {
           ra = ta == (T)0 ? (T)0 : ra;
           rb = tb == (T)0 ? (T)0 : rb;
@@ -1732,11 +1769,17 @@ __device__ inline void grid2_tile(
   const int wlo = s_off[b - bl], whi = s_off[b - bl + 3];
   const T kf0 = (T)(k - kb), kf1 = kf0 + (T)1;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // both points' pairs with source i
+  // both points' pairs with source i: t0 = (k - x) - delta, t1 = t0 + 1
+  // from the rounded t0 (for every included pair |t1| >= 1/2 and |t0| <=
+  // |t1| + 1, so t1 keeps a relative error of at most two roundings)
+  // (MODE 0, the whole evaluation at five CTAs per SM, keeps the exact
+  // t1 = (e0 + 1) - delta: its register budget has no room for the other form)
   auto both = [&](int i) {
     const SrcQ<T> v = sw[i];  // one 16-byte load (FP32)
     const T e0 = kf0 - v.rel.x;
-    const T r0 = rcp_t(e0 - v.rel.y), r1 = rcp_t((e0 + (T)1) - v.rel.y);
+    const T t0 = e0 - v.rel.y;
+    const T t1 = MODE == 0 ? (e0 + (T)1) - v.rel.y : t0 + (T)1;
+    const T r0 = rcp_t(t0), r1 = rcp_t(t1);
     acc0.add_r(v.q, r0);
     acc1.add_r(v.q, r1);
   };
@@ -1746,7 +1789,9 @@ __device__ inline void grid2_tile(
   auto both_own = [&](int i) {
     const SrcQ<T> v = sw[i];
     const T e0 = kf0 - v.rel.x;
-    T r0 = rcp_t(e0 - v.rel.y), r1 = rcp_t((e0 + (T)1) - v.rel.y);
+    const T t0 = e0 - v.rel.y;
+    const T t1 = MODE == 0 ? (e0 + (T)1) - v.rel.y : t0 + (T)1;
+    T r0 = rcp_t(t0), r1 = rcp_t(t1);
     r0 = e0 != (T)0 ? r0 : (T)0;
     r1 = e0 != (T)-1 ? r1 : (T)0;
     acc0.add_r(v.q, r0);
@@ -1755,7 +1800,9 @@ __device__ inline void grid2_tile(
   auto both_checked = [&](int i, int lo, int hi) {
     const SrcQ<T> v = sw[i];
     const T e0 = kf0 - v.rel.x;
-    T r0 = rcp_t(e0 - v.rel.y), r1 = rcp_t((e0 + (T)1) - v.rel.y);
+    const T t0 = e0 - v.rel.y;
+    const T t1 = MODE == 0 ? (e0 + (T)1) - v.rel.y : t0 + (T)1;
+    T r0 = rcp_t(t0), r1 = rcp_t(t1);
     const bool in = i >= lo && i < hi;
     r0 = in && e0 != (T)0 ? r0 : (T)0;
     r1 = in && e0 != (T)-1 ? r1 : (T)0;
@@ -2083,6 +2130,70 @@ int m2l_tc_level(const TreeDims& d, int l, int nsig, const float* bops, const fl
                  float2* lexp, int* status, cudaStream_t st);
 
 template <class T>
+static cudaError_t down_fused_attrs(int big) {
+  cudaError_t e = cudaSuccess;
+  if constexpr (std::is_same<T, float>::value) {
+#define NUFFT_DOWN_ATTR(PV)                                                                   \
+  if (e == cudaSuccess)                                                                      \
+    e = cudaFuncSetAttribute(k_down_fused<T, PV>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                             big);
+    NUFFT_TREE_P_LIST(NUFFT_DOWN_ATTR)
+#undef NUFFT_DOWN_ATTR
+  }
+  return e;
+}
+
+// the one-launch upward pass (P2M from SRC 1 or 2), at the compile-time
+// instance for pm where there is one
+template <class T, int SRC, class VI, class... A>
+static void launch_up_fused(int pm, dim3 grid, size_t smem, cudaStream_t st, A... args) {
+  if constexpr (std::is_same<T, float>::value) {
+    switch (pm) {
+#define NUFFT_UP_CASE(PV)                                                            \
+  case PV:                                                                          \
+    launch_pdl(k_up_fused<T, SRC, VI, PV>, grid, kUpThreads, smem, st, args...);    \
+    return;
+      NUFFT_TREE_P_LIST(NUFFT_UP_CASE)
+#undef NUFFT_UP_CASE
+      default: break;
+    }
+  }
+  launch_pdl(k_up_fused<T, SRC, VI>, grid, kUpThreads, smem, st, args...);
+}
+
+template <class T, int SRC, class VI>
+static cudaError_t up_fused_attrs(int big) {
+  cudaError_t e = cudaSuccess;
+  if constexpr (std::is_same<T, float>::value) {
+#define NUFFT_UP_ATTR(PV)                                                                  \
+  if (e == cudaSuccess)                                                                   \
+    e = cudaFuncSetAttribute(k_up_fused<T, SRC, VI, PV>,                                  \
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    NUFFT_TREE_P_LIST(NUFFT_UP_ATTR)
+#undef NUFFT_UP_ATTR
+  }
+  return e;
+}
+
+// the one-launch downward pass, at the compile-time instance for p where
+// there is one
+template <class T, class... A>
+static void launch_down_fused(int p, dim3 grid, size_t smem, cudaStream_t st, A... args) {
+  if constexpr (std::is_same<T, float>::value) {
+    switch (p) {
+#define NUFFT_DOWN_CASE(PV)                                                          \
+  case PV:                                                                          \
+    launch_pdl(k_down_fused<T, PV>, grid, kDownThreads, smem, st, args...);         \
+    return;
+      NUFFT_TREE_P_LIST(NUFFT_DOWN_CASE)
+#undef NUFFT_DOWN_CASE
+      default: break;
+    }
+  }
+  launch_pdl(k_down_fused<T>, grid, kDownThreads, smem, st, args...);
+}
+
+template <class T>
 int fmm_configure() {
   int big = 220 * 1024;
   if (cudaFuncSetAttribute(k_up_sub<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big) !=
@@ -2107,6 +2218,10 @@ int fmm_configure() {
                            big) != cudaSuccess ||
       cudaFuncSetAttribute(k_down_fused<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            big) != cudaSuccess ||
+      down_fused_attrs<T>(big) != cudaSuccess ||
+      up_fused_attrs<T, 1, float2>(big) != cudaSuccess ||
+      up_fused_attrs<T, 2, float2>(big) != cudaSuccess ||
+      up_fused_attrs<T, 2, double2>(big) != cudaSuccess ||
       cudaFuncSetAttribute(k_down_sub<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            big) != cudaSuccess ||
       cudaFuncSetAttribute(k_level2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -2209,12 +2324,19 @@ int fmm_upward(nufft_plan_s* pl, const FmmOps& ops, bool uniform_sources, const 
     }
     const size_t sm = up_fused_smem<T>(pm, sg, src, pl->s);
     const dim3 grid(1u << sg.lev[1], nsig);
-    if (src == 1)
-      launch_pdl(k_up_fused<T, 1, VI>, grid, kUpThreads, sm, st, d, sg, (const T*)pl->op_m2m,
-                 mexp, pl->upcnt, pl->upcnt_n, us);
-    else
-      launch_pdl(k_up_fused<T, 2, VI>, grid, kUpThreads, sm, st, d, sg, (const T*)pl->op_m2m,
-                 mexp, pl->upcnt, pl->upcnt_n, us);
+    if (src == 1) {  // (the input type does not enter SRC 1)
+      UpSrc<T, float2> u1;
+      u1.q = us.q;
+      u1.rp = us.rp;
+      u1.start = us.start;
+      u1.k0 = us.k0;
+      u1.delta_t = us.delta_t;
+      launch_up_fused<T, 1, float2>(pm, grid, sm, st, d, sg, (const T*)pl->op_m2m, mexp,
+                                    pl->upcnt, pl->upcnt_n, u1);
+    } else {
+      launch_up_fused<T, 2, VI>(pm, grid, sm, st, d, sg, (const T*)pl->op_m2m, mexp, pl->upcnt,
+                                pl->upcnt_n, us);
+    }
     prof_end(pl, 1);
   } else {
     prof_begin(pl, NUFFT_STAGE_P2M);
@@ -2312,9 +2434,9 @@ int fmm_downward(nufft_plan_s* pl, const FmmOps& ops) {
     const int flt = L - fdep > 3 ? L - fdep : 3;  // subtree roots
     if (lc > L && down_fused_smem<T>(p, L - flt, flt) <= kSmemBudget) {
       if (L > 3) {
-        launch_pdl(k_down_fused<T>, dim3(1u << flt, nsig), 512,
-                   down_fused_smem<T>(p, L - flt, flt), st, d, flt, L, (const T*)ops.m2l,
-                   (const T*)ops.l2l, mexp, lexp, ops.log_kernel, log2N);
+        launch_down_fused<T>(p, dim3(1u << flt, nsig), down_fused_smem<T>(p, L - flt, flt), st,
+                             d, flt, L, (const T*)ops.m2l, (const T*)ops.l2l,
+                             (const cplx<T>*)mexp, lexp, ops.log_kernel, log2N);
       } else {  // L = 3: level 3 alone
         launch_pdl(k_down_top<T>, dim3(1, nsig), 512, smt, st, d, 3, (const T*)ops.m2l,
                    (const T*)ops.l2l, mexp, lexp, ops.log_kernel, log2N);
