@@ -94,7 +94,7 @@ __device__ inline double rcp_t(double t) {
 __device__ inline void point_local(int k0, double delta, int N, int s, int* leaf, int* o) {
   int fl = neg_bits(delta) ? k0 - 1 : k0;
   fl &= (N - 1);
-  int b = fl / s;
+  int b = fl >> (__ffs(s) - 1);  // s is a power of two
   *leaf = b;
   *o = (k0 - b * s) & (N - 1);
 }

@@ -584,10 +584,17 @@ int fft_init_tables(double2* tw, float2* twf, int64_t N, cudaStream_t st) {
   return cudaGetLastError() == cudaSuccess ? NUFFT_OK : NUFFT_ECUDA;
 }
 
-// Split L into passes of at most 10 bits, as evenly as possible.
-static int fft_plan_passes(int L, int* logR) {
+// Split L into the fewest passes of at most 10 bits: as evenly as possible,
+// or (radix10) 10-bit passes first and the remainder last, for the
+// one-warp-per-column radix-1024 pass.
+static int fft_plan_passes(int L, int* logR, bool radix10 = false) {
   int np = (L + 9) / 10;
   if (np == 0) np = 1;
+  if (radix10 && L > 10) {
+    for (int i = 0; i < np - 1; ++i) logR[i] = 10;
+    logR[np - 1] = L - 10 * (np - 1);
+    return np;
+  }
   int base = L / np, extra = L % np;
   for (int i = 0; i < np; ++i) logR[i] = base + (i < extra ? 1 : 0);
   return np;
@@ -685,15 +692,19 @@ int fft_run(const void* in, int in_f64, void* out, int out_f64, cplx<T>* buf, cp
   if (n_in > N || n_out > N) return NUFFT_EINVAL;
   int L = 0;
   while ((int64_t(1) << L) < N) ++L;
+  const int tf64 = sizeof(T) == 8;
+  const int64_t nsm = g_fft_sms > 0 ? g_fft_sms : 152;
+  // the radix-1024 pass where its grid (four columns per CTA) fills every SM
+  const bool w32 = !tf64 && fft_w32_enabled() && L >= 12 &&
+                   ((int64_t(1) << (L - 10)) / kW32Cols) * batch >= nsm;
   int logR[8];
-  int np = fft_plan_passes(L, logR);
+  int np = fft_plan_passes(L, logR, w32);
   if (np >= 3 && !buf2) return NUFFT_EINVAL;
   int b = fft_lo_bits(N);
-  const int tf64 = sizeof(T) == 8;
   const void* src = in;
   int src_f64 = in_f64;
   int64_t Ns = 1;
-  const int64_t target = 2 * (int64_t)(g_fft_sms > 0 ? g_fft_sms : 152);
+  const int64_t target = 2 * nsm;
   for (int i = 0; i < np; ++i) {
     bool last = (i == np - 1);
     void* dst = last ? out : (void*)((i & 1) ? buf2 : buf);
@@ -702,7 +713,7 @@ int fft_run(const void* in, int in_f64, void* out, int out_f64, cplx<T>* buf, cp
     const int R = 1 << lr, TPC = R >= 8 ? R / 8 : 1;
     const int64_t NR = N >> lr;
     const uint32_t pin = (uint32_t)(i == 0 ? n_in : N), pout = (uint32_t)(last ? n_out : N);
-    if (!tf64 && lr == 10 && NR >= kW32Cols && (Ns == 1 || Ns >= kW32Cols) && fft_w32_enabled()) {
+    if (w32 && lr == 10 && NR >= kW32Cols && (Ns == 1 || Ns >= kW32Cols)) {
       int logNs = 0;
       while ((int64_t(1) << logNs) < Ns) ++logNs;
       launch_pdl(k_fft_w32, dim3((unsigned)(NR / kW32Cols), (unsigned)batch), 128, kW32Smem, st,

@@ -922,6 +922,23 @@ __device__ inline cplx<T> horner(const cplx<T>* __restrict__ c, int n, T u) {
   return acc;
 }
 
+// horner with the length n = NN a compile-time constant (NN > 0), else run time
+template <class T, int NN>
+__device__ inline cplx<T> horner_n(const cplx<T>* __restrict__ c, int n, T u) {
+  if constexpr (NN > 0) {
+    cplx<T> acc = c[NN - 1];
+#pragma unroll
+    for (int k = NN - 2; k >= 0; --k) {
+      const cplx<T> v = c[k];
+      acc.x = fma(acc.x, u, v.x);
+      acc.y = fma(acc.y, u, v.y);
+    }
+    return acc;
+  } else {
+    return horner<T>(c, n, u);
+  }
+}
+
 // store a result in the caller's element type (complex128 by integer widening)
 __device__ inline void store_cplx(double2* p, float2 v) { *p = to_c128(v); }
 __device__ inline void store_cplx(double2* p, double2 v) { *p = v; }
@@ -1151,8 +1168,8 @@ __device__ inline void near_window_ex2w(int n, int ex, NearAcc2f& acc, Term term
 // beside the tree passes); with hnear set it skips them and reads them there.
 template <class T, class VO, int G>
 __device__ inline void targets_fwd_tile(
-    int tile, TreeDims d, int M, const int32_t* __restrict__ k0s, const double* __restrict__ dels,
-    const T* __restrict__ dels_t, const int32_t* __restrict__ perm, const cplx<T>* __restrict__ F,
+    int tile, TreeDims d, int M, const SrcPos<T>* __restrict__ pos,
+    const int32_t* __restrict__ perm, const cplx<T>* __restrict__ F,
     const cplx<T>* __restrict__ E, const cplx<T>* __restrict__ fgrid,
     const cplx<T>* __restrict__ lexp, const cplx<T>* __restrict__ lvl2,
     const cplx<T>* __restrict__ hnear, VO* __restrict__ g, cplx<T>* __restrict__ hout) {
@@ -1169,10 +1186,11 @@ __device__ inline void targets_fwd_tile(
   const int jl = (j0 + kTgtThreads < M ? j0 + kTgtThreads : M) - 1;
   int k0 = 0, b = 0, o = 0;
   T dt = 0;
-  if (act) {
-    k0 = k0s[j];
-    point_local(k0, dels[j], N, s, &b, &o);
-    dt = dels_t[j];
+  if (act) {  // (delta in T has the sign of the FP64 offset: the same leaf)
+    const SrcPos<T> ps = pos[j];
+    k0 = (int)ps.k0;
+    dt = ps.dl;
+    point_local(k0, (double)dt, N, s, &b, &o);
   }
   // hnear: near-field sums computed elsewhere (side branch or tensor cores):
   // no window, no barrier, every load of the far part can be in flight at once
@@ -1305,8 +1323,8 @@ __device__ inline void targets_fwd_tile(
 // only, so the tree kernels keep room on every SM).
 template <class T, class VO, int G>
 __global__ void __launch_bounds__(kTgtThreads) k_targets_fwd(
-    TreeDims d, int M, const int32_t* __restrict__ k0s, const double* __restrict__ dels,
-    const T* __restrict__ dels_t, const int32_t* __restrict__ perm, const cplx<T>* __restrict__ F,
+    TreeDims d, int M, const SrcPos<T>* __restrict__ pos,
+    const int32_t* __restrict__ perm, const cplx<T>* __restrict__ F,
     const cplx<T>* __restrict__ E, const cplx<T>* __restrict__ fgrid,
     const cplx<T>* __restrict__ lexp, const cplx<T>* __restrict__ lvl2,
     const cplx<T>* __restrict__ hnear, VO* __restrict__ g, cplx<T>* __restrict__ hout) {
@@ -1315,8 +1333,7 @@ __global__ void __launch_bounds__(kTgtThreads) k_targets_fwd(
   const int ntiles = (M + kTgtThreads - 1) / kTgtThreads;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     if (tile != (int)blockIdx.x) __syncthreads();  // the previous tile's shared data are read
-    targets_fwd_tile<T, VO, G>(tile, d, M, k0s, dels, dels_t, perm, F, E, fgrid, lexp, lvl2,
-                               hnear, g, hout);
+    targets_fwd_tile<T, VO, G>(tile, d, M, pos, perm, F, E, fgrid, lexp, lvl2, hnear, g, hout);
   }
 }
 
@@ -1327,20 +1344,21 @@ __global__ void __launch_bounds__(kTgtThreads) k_targets_fwd(
 // staged in shared memory first, so each target's Horner sums read on-chip
 // data; the per-target loads (F, E, perm, hnear, the sample at k0) are issued
 // before the barrier.  Dynamic shared memory: (kFarLeaves p + 8q + 1) complex.
-template <class T, class VO>
+// P > 0: the local expansion length as a compile-time constant (d.p == P).
+template <class T, class VO, int P = 0>
 __global__ void __launch_bounds__(kTgtThreads) k_far_fwd(
-    TreeDims d, int M, const int32_t* __restrict__ k0s, const double* __restrict__ dels,
-    const T* __restrict__ dels_t, const int32_t* __restrict__ perm, const cplx<T>* __restrict__ F,
+    TreeDims d, int M, const SrcPos<T>* __restrict__ pos,
+    const int32_t* __restrict__ perm, const cplx<T>* __restrict__ F,
     const cplx<T>* __restrict__ E, const cplx<T>* __restrict__ fgrid,
     const cplx<T>* __restrict__ lexp, const cplx<T>* __restrict__ lvl2,
     const cplx<T>* __restrict__ hnear, VO* __restrict__ g) {
   pdl_wait();
   pdl_trigger();
   extern __shared__ __align__(16) unsigned char smraw[];
+  const int p = P > 0 ? P : d.p;
   cplx<T>* sl = reinterpret_cast<cplx<T>*>(smraw);  // [kFarLeaves][p]
   const int Q2 = 2 * d.q;
-  cplx<T>* s2 = sl + kFarLeaves * d.p;               // [4 Q2 + 1]
-  __shared__ int s_lo, s_hi;
+  cplx<T>* s2 = sl + kFarLeaves * p;                 // [4 Q2 + 1]
   const int N = (int)d.N;
   const int s = d.s;
   const int j0 = blockIdx.x * kTgtThreads;
@@ -1351,23 +1369,29 @@ __global__ void __launch_bounds__(kTgtThreads) k_far_fwd(
   T dt = 0;
   cplx<T> Fj = mk<T>(0, 0), Ej = mk<T>(0, 0), nr = mk<T>(0, 0), fk = mk<T>(0, 0);
   if (act) {
-    k0 = k0s[j];
-    point_local(k0, dels[j], N, s, &b, &o);
-    dt = dels_t[j];
+    const SrcPos<T> ps = pos[j];
+    k0 = (int)ps.k0;
+    dt = ps.dl;
+    point_local(k0, (double)dt, N, s, &b, &o);
     pj = perm[j];
     Fj = F[j];
     Ej = E[j];
     nr = hnear[j];
     fk = fgrid[k0];
   }
-  if (threadIdx.x == 0) s_lo = b;
-  if (j == jl) s_hi = b;
-  __syncthreads();
-  const int bl = s_lo, nlf = s_hi - s_lo + 1;
+  // leaves of the CTA's first and last targets (sorted): every thread reads
+  // both positions (one broadcast load each), so no barrier is needed here
+  int bl, bh, ot;
+  {
+    const SrcPos<T> pa = pos[j0], pb = pos[jl];
+    point_local((int)pa.k0, (double)pa.dl, N, s, &bl, &ot);
+    point_local((int)pb.k0, (double)pb.dl, N, s, &bh, &ot);
+  }
+  const int nlf = bh - bl + 1;
   const bool staged = d.L >= 3 && nlf <= kFarLeaves;
-  const cplx<T>* lx = lexp + (int64_t)(level_off(d.L) - 4) * d.p;
+  const cplx<T>* lx = lexp + (int64_t)(level_off(d.L) - 4) * p;
   if (staged)
-    stage_batched<4>(nlf * d.p, sl, [&](int e) { return lx[(int64_t)bl * d.p + e]; });
+    stage_batched<4>(nlf * p, sl, [&](int e) { return lx[(int64_t)bl * p + e]; });
   stage_batched<2>(4 * Q2 + 1, s2, [&](int e) { return lvl2[e]; });
   __syncthreads();
   if (!act) return;
@@ -1378,7 +1402,8 @@ __global__ void __launch_bounds__(kTgtThreads) k_far_fwd(
   const T u = fma((T)o + dt, ts, (T)-0.5);
   const T cN = KConst<T>::n_pi(d), c2 = (T)(2.0 * kInvPi);
   cplx<T> far = mk<T>(0, 0);
-  if (d.L >= 3) far = horner<T>(staged ? sl + (b - bl) * d.p : lx + (int64_t)b * d.p, d.p, u);
+  if (d.L >= 3)
+    far = horner_n<T, P>(staged ? sl + (b - bl) * p : lx + (int64_t)b * p, p, u);
   const cplx<T> reg = horner<T>(s2 + arc * Q2, Q2, uh);
   const cplx<T> Qs = s2[4 * Q2];
   const T hr = cN * fma(far.x, ts, nr.x) - c2 * reg.x;
@@ -1689,7 +1714,7 @@ __global__ void __launch_bounds__(kTgtThreads) k_targets_grid(
 // k_targets_grid.
 // MODE 0: the whole evaluation; 1: near field only (to hout), with the
 // charges and self terms formed while staging (isrc); 2: far part only (hin).
-template <class T, int MODE>
+template <class T, int MODE, int P = 0>
 __device__ inline void grid2_tile(
     int tile, TreeDims d, int inverse, const int32_t* __restrict__ start,
     const SrcPos<T>* __restrict__ pos, const cplx<T>* __restrict__ charge,
@@ -1718,7 +1743,8 @@ __device__ inline void grid2_tile(
   cplx<T> nr0 = mk<T>(0, 0), nr1 = mk<T>(0, 0);
   // the far part's tables: the CTA's leaf locals and the level-2
   // coefficients, staged in shared memory when only the far part runs here
-  const cplx<T>* lxg = lexp + (int64_t)(level_off(d.L) - 4) * d.p;
+  const int p = P > 0 ? P : d.p;  // (P > 0: d.p as a compile-time constant)
+  const cplx<T>* lxg = lexp + (int64_t)(level_off(d.L) - 4) * p;
   const cplx<T>* lx = lxg;  // locals of leaf b at lx + (b - lxb) p
   int lxb = 0;
   const cplx<T>* l2 = lvl2;
@@ -1734,11 +1760,11 @@ __device__ inline void grid2_tile(
     cplx<T>* sl = reinterpret_cast<cplx<T>*>(smraw);
     const int nlf = bh - bl + 1;
     if (d.L >= 3 && nlf <= kFarLeaves) {
-      stage_batched<4>(nlf * d.p, sl, [&](int e) { return lxg[(int64_t)bl * d.p + e]; });
+      stage_batched<4>(nlf * p, sl, [&](int e) { return lxg[(int64_t)bl * p + e]; });
       lx = sl;
       lxb = bl;
     }
-    cplx<T>* s2 = sl + kFarLeaves * d.p;
+    cplx<T>* s2 = sl + kFarLeaves * p;
     stage_batched<2>(8 * d.q + 1, s2, [&](int e) { return lvl2[e]; });
     l2 = s2;
     __syncthreads();
@@ -1905,7 +1931,7 @@ __device__ inline void grid2_tile(
     const T uh = (T)I * KConst<T>::two_n(d);
     const T u = fma((T)o, ts, (T)-0.5);
     cplx<T> far = mk<T>(0, 0);
-    if (d.L >= 3) far = horner<T>(lx + (int64_t)(b - lxb) * d.p, d.p, u);
+    if (d.L >= 3) far = horner_n<T, P>(lx + (int64_t)(b - lxb) * p, p, u);
     const cplx<T> reg = horner<T>(l2 + arc * Q2, Q2, uh);
     const cplx<T> nr = h ? nr1 : nr0;
     const T hr = cN * fma(far.x, ts, nr.x) - c2 * reg.x;
@@ -1919,7 +1945,7 @@ __device__ inline void grid2_tile(
   }
 }
 
-template <class T, int MODE>
+template <class T, int MODE, int P = 0>
 __global__ void __launch_bounds__(kTgtThreads, (sizeof(T) == 4 && MODE == 0) ? 5 : 4) k_targets_grid2(
     TreeDims d, int inverse, const int32_t* __restrict__ start,
     const SrcPos<T>* __restrict__ pos, const cplx<T>* __restrict__ charge,
@@ -1931,7 +1957,7 @@ __global__ void __launch_bounds__(kTgtThreads, (sizeof(T) == 4 && MODE == 0) ? 5
   const int ntiles = (int)((d.N + 2 * kTgtThreads - 1) / (2 * kTgtThreads));
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     if (tile != (int)blockIdx.x) __syncthreads();  // the previous tile's shared data are read
-    grid2_tile<T, MODE>(tile, d, inverse, start, pos, charge, st, lexp, lvl2, Ct, out, hout, hin,
+    grid2_tile<T, MODE, P>(tile, d, inverse, start, pos, charge, st, lexp, lvl2, Ct, out, hout, hin,
                         isrc);
   }
 }
@@ -2515,6 +2541,40 @@ static unsigned near_grid(int64_t tiles, bool grid) {
   return (unsigned)(tiles < cap ? tiles : cap);
 }
 
+// k_targets_grid2's far part (MODE 2) at the compile-time instance for p
+template <class T, class... A>
+static void launch_far_grid2(int p, unsigned nb, size_t sm, cudaStream_t st, A... args) {
+  if constexpr (std::is_same<T, float>::value) {
+    switch (p) {
+#define NUFFT_FARG_CASE(PV)                                                   \
+  case PV:                                                                   \
+    launch_pdl(k_targets_grid2<T, 2, PV>, nb, kTgtThreads, sm, st, args...); \
+    return;
+      NUFFT_TREE_P_LIST(NUFFT_FARG_CASE)
+#undef NUFFT_FARG_CASE
+      default: break;
+    }
+  }
+  launch_pdl(k_targets_grid2<T, 2>, nb, kTgtThreads, sm, st, args...);
+}
+
+// k_far_fwd at the compile-time instance for p where there is one
+template <class T, class VO, class... A>
+static void launch_far_fwd(int p, unsigned nb, size_t sm, cudaStream_t st, A... args) {
+  if constexpr (std::is_same<T, float>::value) {
+    switch (p) {
+#define NUFFT_FAR_CASE(PV)                                                  \
+  case PV:                                                                 \
+    launch_pdl(k_far_fwd<T, VO, PV>, nb, kTgtThreads, sm, st, args...);    \
+    return;
+      NUFFT_TREE_P_LIST(NUFFT_FAR_CASE)
+#undef NUFFT_FAR_CASE
+      default: break;
+    }
+  }
+  launch_pdl(k_far_fwd<T, VO>, nb, kTgtThreads, sm, st, args...);
+}
+
 template <class T, class VO, int G>
 static void launch_targets_fwd(nufft_plan_s* pl, const TreeDims& d, const cplx<T>* f,
                                const cplx<T>* hnear, void* g, cplx<T>* hout = nullptr,
@@ -2522,7 +2582,7 @@ static void launch_targets_fwd(nufft_plan_s* pl, const TreeDims& d, const cplx<T
   const int64_t tiles = nblk(pl->M, kTgtThreads);
   dim3 grid(hout ? near_grid(tiles, false) : (unsigned)tiles, (unsigned)(pl->batch / G));
   launch_pdl(k_targets_fwd<T, VO, G>, grid, kTgtThreads, hnear ? 0 : NearCap<T, G>::fwd_bytes,
-             st ? st : pl->stream, d, (int)pl->M, pl->k0, pl->delta, PlanT<T>::delta(pl),
+             st ? st : pl->stream, d, (int)pl->M, (const SrcPos<T>*)pl->srcpos,
              pl->perm, PlanT<T>::F(pl), PlanT<T>::E(pl), f, (const cplx<T>*)pl->lexp,
              PlanT<T>::lvl2(pl), hnear, (VO*)g, hout);
 }
@@ -2577,13 +2637,15 @@ int fmm_forward(nufft_plan_s* pl, void* g) {
     const size_t sm = (size_t)(kFarLeaves * pl->p + 8 * pl->q + 1) * sizeof(cplx<T>);
     const unsigned nb = nblk(pl->M, kTgtThreads);
     if (c64)
-      launch_pdl(k_far_fwd<T, float2>, nb, kTgtThreads, sm, pl->stream, d, (int)pl->M, pl->k0,
-                 pl->delta, PlanT<T>::delta(pl), pl->perm, PlanT<T>::F(pl), PlanT<T>::E(pl), f,
-                 (const cplx<T>*)pl->lexp, PlanT<T>::lvl2(pl), hnear, (float2*)g);
+      launch_far_fwd<T, float2>(pl->p, nb, sm, pl->stream, d, (int)pl->M,
+                              (const SrcPos<T>*)pl->srcpos, (const int32_t*)pl->perm,
+                              PlanT<T>::F(pl), PlanT<T>::E(pl), f, (const cplx<T>*)pl->lexp,
+                              PlanT<T>::lvl2(pl), hnear, (float2*)g);
     else
-      launch_pdl(k_far_fwd<T, double2>, nb, kTgtThreads, sm, pl->stream, d, (int)pl->M, pl->k0,
-                 pl->delta, PlanT<T>::delta(pl), pl->perm, PlanT<T>::F(pl), PlanT<T>::E(pl), f,
-                 (const cplx<T>*)pl->lexp, PlanT<T>::lvl2(pl), hnear, (double2*)g);
+      launch_far_fwd<T, double2>(pl->p, nb, sm, pl->stream, d, (int)pl->M,
+                              (const SrcPos<T>*)pl->srcpos, (const int32_t*)pl->perm,
+                              PlanT<T>::F(pl), PlanT<T>::E(pl), f, (const cplx<T>*)pl->lexp,
+                              PlanT<T>::lvl2(pl), hnear, (double2*)g);
   } else if (pl->flags & NUFFT_IO_C64) {
     if (g4) launch_targets_fwd<T, float2, 4>(pl, d, f, hnear, g);
     else launch_targets_fwd<T, float2, 1>(pl, d, f, hnear, g);
@@ -2731,11 +2793,12 @@ int fmm_to_grid(nufft_plan_s* pl, const void* g, int inverse) {
     if (rc) return rc;
     side_join(pl, 2);
     prof_begin(pl, NUFFT_STAGE_TARGETS);
-    launch_pdl(k_targets_grid2<T, 2>, nblk(pl->N, 2 * kTgtThreads), kTgtThreads,
-               (size_t)(kFarLeaves * pl->p + 8 * pl->q + 1) * sizeof(cplx<T>), st, d, inverse,
-               pl->leaf_start, (const SrcPos<T>*)pos, (const cplx<T>*)charge, (const cplx<T>*)stt,
-               (const cplx<T>*)pl->lexp, PlanT<T>::lvl2(pl), PlanT<T>::Ct(pl), (cplx<T>*)pl->grid,
-               (cplx<T>*)nullptr, (const cplx<T>*)pl->hnear, InlineSrc<T>());
+    launch_far_grid2<T>(pl->p, nblk(pl->N, 2 * kTgtThreads),
+                        (size_t)(kFarLeaves * pl->p + 8 * pl->q + 1) * sizeof(cplx<T>), st, d,
+                        inverse, (const int32_t*)pl->leaf_start, (const SrcPos<T>*)pos,
+                        (const cplx<T>*)charge, (const cplx<T>*)stt, (const cplx<T>*)pl->lexp,
+                        PlanT<T>::lvl2(pl), PlanT<T>::Ct(pl), (cplx<T>*)pl->grid,
+                        (cplx<T>*)nullptr, (const cplx<T>*)pl->hnear, InlineSrc<T>());
     prof_end(pl, 1);
     return cudaGetLastError() == cudaSuccess ? NUFFT_OK : NUFFT_ECUDA;
   }

@@ -30,6 +30,7 @@ void make_operator_tables(const nufft_plan_s* pl, long double* m2m, long double*
                           long double* l2l, long double* rp, double* reg);
 size_t setup_tmp_bytes(int64_t M, int64_t B);
 int setup_points(nufft_plan_s* pl, const double* y, void* tmp);
+int fmm_pack_positions(nufft_plan_s* pl);
 int fft_init_tables(double2* tw, float2* twf, int64_t N, cudaStream_t st);
 size_t fft_table_elems(int64_t N);
 int fft_num_passes(int64_t N);
@@ -158,6 +159,7 @@ extern "C" int nufft_fwd_noalloc(const void* c, int64_t N, const double* y, int6
     pl.lvl2f = cv.take<float2>((8 * pl.q + 1) * 8);
     pl.fft_tw_f = cv.take<float2>(fft_table_elems(N) * 8);
   }
+  pl.srcpos = cv.take<void>(M * csz);
   void* tmp = cv.take<void>(setup_tmp_bytes(M, B));
   if (!cv.ok) return NUFFT_EINVAL;  // does not fit the fixed scratch
 
@@ -175,6 +177,7 @@ extern "C" int nufft_fwd_noalloc(const void* c, int64_t N, const double* y, int6
                       st) != cudaSuccess)
     return NUFFT_ECUDA;
   if ((rc = setup_points(&pl, y, tmp))) return rc;
+  if ((rc = fmm_pack_positions(&pl))) return rc;
   int hstat = 0;
   if (cudaMemcpyAsync(&hstat, pl.status, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess)

@@ -3,9 +3,10 @@ transforms, against the oracle's radix-2 FFT.  With every y_j on a grid
 point x_k (M = N, y_j = x_j) the forward transform returns the grid samples
 f_k = sum_n c_n e^{i n x_k} (its E_j f_k0 term; F_j vanishes to rounding)
 and the adjoint returns c'_n = sum_k e^{-i n x_k} g_k, so both are the FFT
-pass kernels alone: the Stockham passes of every radix and, at N = 2^19 and
-2^20, the one-warp-per-column radix-1024 passes (FP32), both signs, with the
-FP32 and complex128 loads and stores at the ends."""
+pass kernels alone: the Stockham passes of every radix and, where their grid
+fills the GPU (N >= 2^20 for one signal), the one-warp-per-column radix-1024
+passes (FP32), both signs, with the FP32 and complex128 loads and stores at
+the ends."""
 import numpy as np
 import pytest
 
@@ -61,6 +62,20 @@ def test_grid_points_forward_and_adjoint_are_the_fft(nf, orc, prec, L):
     tol = TOL[1] if prec == 1 else 4e-9
     assert orc.rel_l2(g, orc.fft(c, +1)) < tol
     assert orc.rel_l2(a, orc.fft(c, -1)) < tol
+
+
+@pytest.mark.parametrize("L", [22, 24])
+def test_grid_points_three_passes_mixed(nf, orc, L):
+    """N = 2^22 and 2^24 (mixed): two radix-1024 passes and a radix-4 / radix-16
+    pass."""
+    N = 1 << L
+    y = _grid_points(N)
+    plan = nf.Plan(N, _dev(y), eps=1e-6, prec=1)
+    c = workloads.coeffs(N, seed=100 + L)
+    g = _host(plan.forward(_dev(c)))
+    assert orc.rel_l2(g, orc.fft(c, +1)) < TOL[1]
+    a = _host(plan.adjoint(_dev(c)))
+    assert orc.rel_l2(a, orc.fft(c, -1)) < TOL[1]
 
 
 def test_grid_points_batched_signals(nf, orc):
