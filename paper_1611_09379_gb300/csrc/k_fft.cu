@@ -373,9 +373,16 @@ __global__ void __launch_bounds__(kFftMaxThreads, sizeof(T) == 4 ? 3 : 2) k_fft_
 // elements through shared memory.  The pass twiddle w_{Ns R}^{r jm} factors
 // into w^{t jm} (per lane) times w^{32 m jm} (per warp, from shared memory).
 
-constexpr int kW32Cols = 4;      // columns (warps) per CTA
-constexpr int kW32Stride = 1060;  // column stride in shared memory: rows 33 m + t, + 4 (banks)
-constexpr size_t kW32Smem = (size_t)(kW32Cols * kW32Stride + 1024 + kW32Cols * 32) * sizeof(float2);
+// COLS columns (warps) per CTA: rows of the strided passes move as runs of
+// COLS adjacent elements (32, 64 or 128 bytes)
+template <int COLS> struct W32Shape {
+  static constexpr int threads = 32 * COLS;
+  // column stride in shared memory: rows 33 m + t, then 16 / COLS slots so
+  // the staging accesses (COLS columns x 32 / COLS rows per half-warp) fall
+  // in different banks
+  static constexpr int stride = 1056 + 16 / COLS;
+  static constexpr size_t smem = (size_t)(COLS * stride + 1024 + COLS * 32) * sizeof(float2);
+};
 
 // cos and sin of 2 pi e / 32 (the exact values rounded to FP32), e in [0, 32)
 __host__ __device__ constexpr float w32_cos(int e) {
@@ -427,14 +434,17 @@ __device__ inline void dft32(float2* a, float sg) {
 // N = 2^logN >= 4096 and Ns = 1 or Ns >= 4: 128 threads, four columns
 // j = 4 blockIdx.x + warp, signal blockIdx.y.  tw: the two-level FP32
 // twiddle tables of w_N; tw32: w_1024^{ka t} at [ka 32 + t] (sign +1).
-__global__ void __launch_bounds__(128, 4) k_fft_w32(
+template <int COLS>
+__global__ void __launch_bounds__(32 * COLS, 16 / COLS) k_fft_w32(
     const void* __restrict__ in, int in_f64, void* __restrict__ out, int out_f64, int logN,
     int logNs, int sign, const float2* __restrict__ tw, const float2* __restrict__ tw32,
     int lo_bits, uint32_t n_in, uint32_t n_out) {
+  using S = W32Shape<COLS>;
+  constexpr int kW32Cols = COLS, kW32Stride = S::stride, NT = S::threads;
   extern __shared__ __align__(16) unsigned char smraw[];
-  float2* X = reinterpret_cast<float2*>(smraw);  // [4][kW32Stride]
+  float2* X = reinterpret_cast<float2*>(smraw);  // [COLS][stride]
   float2* TW = X + kW32Cols * kW32Stride;        // [32 ka][32 t]
-  float2* BM = TW + 1024;                        // [4 warps][32 m]
+  float2* BM = TW + 1024;                        // [COLS warps][32 m]
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const float sg = (float)sign;
   const uint32_t N = 1u << logN, nmask = N - 1, Ns = 1u << logNs;
@@ -445,9 +455,9 @@ __global__ void __launch_bounds__(128, 4) k_fft_w32(
   {
     // all table loads in flight together (a loop of load-store pairs would
     // wait for each load in turn)
-    float2 tv[1024 / 128];
+    float2 tv[1024 / NT];
 #pragma unroll
-    for (int u = 0; u < 1024 / 128; ++u) tv[u] = tw32[tid + 128 * u];
+    for (int u = 0; u < 1024 / NT; ++u) tv[u] = tw32[tid + NT * u];
     if (Ns > 1) {  // w_{Ns R}^{e} = w_N^{e N / (Ns R)}, N / (Ns R) = 2^lstep
       const int lstep = logN - logNs - 10;
       At = twiddle32<float>(tw, ((lane * jm) << lstep) & nmask, lo_bits, lo_mask, sg);
@@ -455,15 +465,15 @@ __global__ void __launch_bounds__(128, 4) k_fft_w32(
           twiddle32<float>(tw, ((32u * lane * jm) << lstep) & nmask, lo_bits, lo_mask, sg);
     }
 #pragma unroll
-    for (int u = 0; u < 1024 / 128; ++u) {
+    for (int u = 0; u < 1024 / NT; ++u) {
       tv[u].y *= sg;
-      TW[tid + 128 * u] = tv[u];
+      TW[tid + NT * u] = tv[u];
     }
   }
   // (the twiddle tables are plan constants: read before the predecessor ends)
   pdl_wait();
   pdl_trigger();
-  const int c4 = tid & 3, q4 = tid >> 2;  // staging: column j0 + c4, rows q4 + 32 i
+  const int c4 = tid % COLS, q4 = tid / COLS;  // staging: column j0 + c4, rows q4 + 32 i
   {
     float2* xc = X + c4 * kW32Stride + q4;
     const uint32_t e0 = j0 + c4 + ((uint32_t)q4 << lognr), de = 32u << lognr;
@@ -654,6 +664,24 @@ static int fft_pass(int logR, dim3 grid, int threads, size_t smem, cudaStream_t 
 
 static int g_fft_sms = 0;
 
+// Columns per CTA of the radix-1024 pass: the widest of 16, 8, 4 (longest
+// row runs) that still gives about one CTA per SM (at least 4/5 of the SMs)
+// over the grid: measured at 2^20 (8: 14.4 us per transform, 4: 15.0, 16:
+// 23.3), 2^21 (16: 29.8, 4: 31.3) and 2^24 (16: 276, 4: 292);
+// NUFFT_FFT_W32_COLS (4, 8 or 16) fixes it, for measurements.
+constexpr int kW32MinCols = 4;
+static int w32_cols(int64_t NR, int64_t Ns, int batch, int64_t nsm) {
+  static const int forced = [] {
+    const char* e = std::getenv("NUFFT_FFT_W32_COLS");
+    const int x = e ? std::atoi(e) : 0;
+    return (x == 4 || x == 8 || x == 16) ? x : 0;
+  }();
+  int c = forced ? forced : 16;
+  while (!forced && c > kW32MinCols && 5 * (NR / c) * batch < 4 * nsm) c >>= 1;
+  while (c > kW32MinCols && (NR < c || (Ns > 1 && Ns < c))) c >>= 1;
+  return c;
+}
+
 // The one-warp-per-column radix-1024 pass (FP32) where it applies;
 // NUFFT_FFT_NO_W32=1 keeps every pass on k_fft_st, for measurements.
 static bool fft_w32_enabled() {
@@ -696,7 +724,7 @@ int fft_run(const void* in, int in_f64, void* out, int out_f64, cplx<T>* buf, cp
   const int64_t nsm = g_fft_sms > 0 ? g_fft_sms : 152;
   // the radix-1024 pass where its grid (four columns per CTA) fills every SM
   const bool w32 = !tf64 && fft_w32_enabled() && L >= 12 &&
-                   ((int64_t(1) << (L - 10)) / kW32Cols) * batch >= nsm;
+                   ((int64_t(1) << (L - 10)) / kW32MinCols) * batch >= nsm;
   int logR[8];
   int np = fft_plan_passes(L, logR, w32);
   if (np >= 3 && !buf2) return NUFFT_EINVAL;
@@ -713,13 +741,22 @@ int fft_run(const void* in, int in_f64, void* out, int out_f64, cplx<T>* buf, cp
     const int R = 1 << lr, TPC = R >= 8 ? R / 8 : 1;
     const int64_t NR = N >> lr;
     const uint32_t pin = (uint32_t)(i == 0 ? n_in : N), pout = (uint32_t)(last ? n_out : N);
-    if (w32 && lr == 10 && NR >= kW32Cols && (Ns == 1 || Ns >= kW32Cols)) {
+    if (w32 && lr == 10 && NR >= kW32MinCols && (Ns == 1 || Ns >= kW32MinCols)) {
       int logNs = 0;
       while ((int64_t(1) << logNs) < Ns) ++logNs;
-      launch_pdl(k_fft_w32, dim3((unsigned)(NR / kW32Cols), (unsigned)batch), 128, kW32Smem, st,
-                 src, src_f64, dst, dst_f64, L, logNs, sign,
-                 reinterpret_cast<const float2*>(tw),
-                 reinterpret_cast<const float2*>(tw) + fft_table_base(N), b, pin, pout);
+      const int cols = w32_cols(NR, Ns, batch, nsm);
+      const float2* twf = reinterpret_cast<const float2*>(tw);
+      const float2* tw32 = twf + fft_table_base(N);
+      const dim3 grid((unsigned)(NR / cols), (unsigned)batch);
+      if (cols == 16)
+        launch_pdl(k_fft_w32<16>, grid, W32Shape<16>::threads, W32Shape<16>::smem, st, src,
+                   src_f64, dst, dst_f64, L, logNs, sign, twf, tw32, b, pin, pout);
+      else if (cols == 8)
+        launch_pdl(k_fft_w32<8>, grid, W32Shape<8>::threads, W32Shape<8>::smem, st, src,
+                   src_f64, dst, dst_f64, L, logNs, sign, twf, tw32, b, pin, pout);
+      else
+        launch_pdl(k_fft_w32<4>, grid, W32Shape<4>::threads, W32Shape<4>::smem, st, src,
+                   src_f64, dst, dst_f64, L, logNs, sign, twf, tw32, b, pin, pout);
       src = dst;
       src_f64 = dst_f64;
       Ns <<= lr;
@@ -790,6 +827,11 @@ int fft_configure() {
     return NUFFT_ECUDA;
   int rc = fft_attrs<double>();
   if (!rc) rc = fft_attrs<float>();
+  if (!rc && (cudaFuncSetAttribute(k_fft_w32<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)W32Shape<8>::smem) != cudaSuccess ||
+              cudaFuncSetAttribute(k_fft_w32<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)W32Shape<16>::smem) != cudaSuccess))
+    rc = NUFFT_ECUDA;
   return rc;
 }
 

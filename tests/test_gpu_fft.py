@@ -91,9 +91,10 @@ def test_grid_points_batched_signals(nf, orc):
 
 
 def test_radix1024_passes_match_stockham_passes(nf, orc):
-    """NUFFT_FFT_NO_W32=1 keeps every pass on the Stockham kernel: a child
-    process with it set gives the same forward at N = 2^20 (mixed) to FP32
-    rounding, on jittered points."""
+    """NUFFT_FFT_NO_W32=1 keeps every pass on the Stockham kernel and
+    NUFFT_FFT_W32_COLS fixes the radix-1024 pass's columns per CTA (4, 8,
+    16): child processes with each give the same forward at N = 2^20 (mixed)
+    to FP32 rounding, on jittered points, and each matches the direct sums."""
     import os
     import subprocess
     import sys
@@ -106,15 +107,16 @@ def test_radix1024_passes_match_stockham_passes(nf, orc):
         "np.save(sys.argv[1], p.forward(c).cpu().numpy())")
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     outs = []
-    for flag in ("0", "1"):
-        path = os.path.join(root, "gpurun_out", f"_w32_{flag}.npy")
+    for flag, cols in (("0", ""), ("1", ""), ("0", "4"), ("0", "16")):
+        path = os.path.join(root, "gpurun_out", f"_w32_{flag}_{cols}.npy")
         os.makedirs(os.path.dirname(path), exist_ok=True)
-        env = dict(os.environ, NUFFT_FFT_NO_W32=flag)
+        env = dict(os.environ, NUFFT_FFT_NO_W32=flag, NUFFT_FFT_W32_COLS=cols)
         subprocess.run([sys.executable, "-c", code, path], cwd=root, env=env, check=True,
                        timeout=300)
         outs.append(np.load(path))
         os.remove(path)
-    assert orc.rel_l2(outs[0], outs[1]) < 3e-7
+    for o in outs[1:]:
+        assert orc.rel_l2(outs[0], o) < 3e-7
     idx = workloads.sample_index(1 << 20, 256, seed=5)
     y = workloads.points("jitter", 1 << 20, 1 << 20, seed=31, jitter=0.4)
     ref = orc.nudft_fwd(workloads.coeffs(1 << 20, seed=32), y, idx)
