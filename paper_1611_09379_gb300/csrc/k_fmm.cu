@@ -1509,6 +1509,41 @@ template <class T> struct InlineSrc {
   T n_2pi = 0;
 };
 
+// The charge of staged source i (returned) and, with need_self, its self
+// term (to *st): the same values as charge_of and self_term_of, with the
+// caller's sample read once for both and the grid index and offset taken
+// from the staged position record; the inverse's FP32 self term multiplies
+// by the reciprocal of delta (rcp_t, within 1 ulp) instead of an IEEE
+// division, and falls back to self_term_of where its FP32 range checks fail.
+template <class T>
+__device__ inline cplx<T> stage_charge_self(const InlineSrc<T>& is, const TreeDims& d, int i,
+                                            const SrcPos<T>& ps, bool need_self,
+                                            cplx<T>* st) {
+  const SelfArgs& a = is.a;
+  const cplx<T> gs = sample_in<T>(a, a.perm[i]);
+  cplx<T> c = is.coef[i];
+  if (!a.inverse) c.y = -c.y;  // the adjoint's conj(F_i)
+  const cplx<T> q = cmul(c, gs);
+  if (!need_self) return q;
+  if (!a.inverse) {
+    *st = cmul(cconj(is.E[i]), gs);
+    return q;
+  }
+  if constexpr (sizeof(T) == 4) {
+    const int k0 = (int)ps.k0;
+    const T dt = ps.dl, ct = is.Ctt[k0];
+    if (fabs(dt) >= (T)9.5367431640625e-07 && fabs(ct) >= (T)7.888609052210118e-31) {
+      const T w = (ct * rcp_t(dt)) * is.n_2pi;
+      cplx<T> v = mk<T>(-q.y * w, q.x * w);
+      if (d.nc) v = cmul(v, from_d2<T>(inv_phase(d, k0)));
+      *st = v;
+      return q;
+    }
+  }
+  *st = self_term_of<T>(a, d, i, q, is.E, is.Ctt, is.delt, is.n_2pi);
+  return q;
+}
+
 template <class T, class VI>
 __global__ void k_self_terms(int M, int inverse, int N, TreeDims dd, const int32_t* __restrict__ k0s,
                              const double* __restrict__ dels, const int32_t* __restrict__ perm,
@@ -1852,9 +1887,10 @@ __device__ inline void grid2_tile(
         SrcQ<T> v;
         v.rel = mk<T>((T)xu, ps.dl);
         if constexpr (MODE == 1) {  // charge and self term formed here (no kernel before)
-          v.q = charge_of<T>(isrc.a, isrc.coef, gi);
-          sst[e - c0] = self_term_of<T>(isrc.a, d, gi, v.q, isrc.E, isrc.Ctt, isrc.delt,
-                                         isrc.n_2pi);
+          // (only a source whose nearest grid point lies in this tile's
+          // range can be in a tile point's own run: the halo's sources need
+          // no self term)
+          v.q = stage_charge_self<T>(isrc, d, gi, ps, xu >= 0 && xu < kPts, &sst[e - c0]);
         } else {
           v.q = charge[gi];
           sst[e - c0] = st[gi];
