@@ -1039,8 +1039,6 @@ template <class T> struct __align__(16) SrcQ {
 
 // Targets per CTA and the capacity of the staged near-field windows.
 constexpr int kTgtThreads = 256;
-// leaf locals a far-part CTA stages in shared memory (more: read from global)
-constexpr int kFarLeaves = 16;
 template <class T, int G> struct NearCap {
   // forward: grid samples per signal; adjoint / inverse: sources per chunk
   static constexpr int fwd = (sizeof(T) == 4 ? 2048 : 1024) / G;
@@ -1339,12 +1337,12 @@ __global__ void __launch_bounds__(kTgtThreads) k_targets_fwd(
 
 // The far part of the forward targets after the near-field sums were formed
 // on the side branch (hnear, sorted order): the same arithmetic as the end of
-// k_targets_fwd for one signal, with the CTA's leaf locals (leaves bl..bh of
-// its sorted targets, up to kFarLeaves of them) and the level-2 coefficients
-// staged in shared memory first, so each target's Horner sums read on-chip
-// data; the per-target loads (F, E, perm, hnear, the sample at k0) are issued
-// before the barrier.  Dynamic shared memory: (kFarLeaves p + 8q + 1) complex.
-// P > 0: the local expansion length as a compile-time constant (d.p == P).
+// k_targets_fwd for one signal, one target per thread with no barrier: every
+// load but the target's leaf locals and the sample at k0 is independent of
+// the target's position, and those read through L1 (the targets of a CTA
+// share a few leaves, and the level-2 coefficients are common to all), so a
+// thread waits for two memory latencies.  P > 0: the local expansion length
+// as a compile-time constant (d.p == P).
 template <class T, class VO, int P = 0>
 __global__ void __launch_bounds__(kTgtThreads) k_far_fwd(
     TreeDims d, int M, const SrcPos<T>* __restrict__ pos,
@@ -1354,47 +1352,21 @@ __global__ void __launch_bounds__(kTgtThreads) k_far_fwd(
     const cplx<T>* __restrict__ hnear, VO* __restrict__ g) {
   pdl_wait();
   pdl_trigger();
-  extern __shared__ __align__(16) unsigned char smraw[];
+  const int j = blockIdx.x * kTgtThreads + threadIdx.x;
+  if (j >= M) return;
   const int p = P > 0 ? P : d.p;
-  cplx<T>* sl = reinterpret_cast<cplx<T>*>(smraw);  // [kFarLeaves][p]
   const int Q2 = 2 * d.q;
-  cplx<T>* s2 = sl + kFarLeaves * p;                 // [4 Q2 + 1]
   const int N = (int)d.N;
   const int s = d.s;
-  const int j0 = blockIdx.x * kTgtThreads;
-  const int j = j0 + threadIdx.x;
-  const bool act = j < M;
-  const int jl = (j0 + kTgtThreads < M ? j0 + kTgtThreads : M) - 1;
-  int k0 = 0, b = 0, o = 0, pj = 0;
-  T dt = 0;
-  cplx<T> Fj = mk<T>(0, 0), Ej = mk<T>(0, 0), nr = mk<T>(0, 0), fk = mk<T>(0, 0);
-  if (act) {
-    const SrcPos<T> ps = pos[j];
-    k0 = (int)ps.k0;
-    dt = ps.dl;
-    point_local(k0, (double)dt, N, s, &b, &o);
-    pj = perm[j];
-    Fj = F[j];
-    Ej = E[j];
-    nr = hnear[j];
-    fk = fgrid[k0];
-  }
-  // leaves of the CTA's first and last targets (sorted): every thread reads
-  // both positions (one broadcast load each), so no barrier is needed here
-  int bl, bh, ot;
-  {
-    const SrcPos<T> pa = pos[j0], pb = pos[jl];
-    point_local((int)pa.k0, (double)pa.dl, N, s, &bl, &ot);
-    point_local((int)pb.k0, (double)pb.dl, N, s, &bh, &ot);
-  }
-  const int nlf = bh - bl + 1;
-  const bool staged = d.L >= 3 && nlf <= kFarLeaves;
-  const cplx<T>* lx = lexp + (int64_t)(level_off(d.L) - 4) * p;
-  if (staged)
-    stage_batched<4>(nlf * p, sl, [&](int e) { return lx[(int64_t)bl * p + e]; });
-  stage_batched<2>(4 * Q2 + 1, s2, [&](int e) { return lvl2[e]; });
-  __syncthreads();
-  if (!act) return;
+  const SrcPos<T> ps = pos[j];
+  const int pj = perm[j];
+  const cplx<T> Fj = F[j], Ej = E[j], nr = hnear[j];
+  const cplx<T> Qs = lvl2[4 * Q2];
+  const int k0 = (int)ps.k0;
+  const T dt = ps.dl;
+  int b, o;
+  point_local(k0, (double)dt, N, s, &b, &o);
+  const cplx<T> fk = fgrid[k0];
   const int arc = b >> (d.L - 2);
   const int I = b * s + o - arc * (N >> 2) - (N >> 3);
   const T uh = ((T)I + dt) * KConst<T>::two_n(d);
@@ -1403,9 +1375,8 @@ __global__ void __launch_bounds__(kTgtThreads) k_far_fwd(
   const T cN = KConst<T>::n_pi(d), c2 = (T)(2.0 * kInvPi);
   cplx<T> far = mk<T>(0, 0);
   if (d.L >= 3)
-    far = horner_n<T, P>(staged ? sl + (b - bl) * p : lx + (int64_t)b * p, p, u);
-  const cplx<T> reg = horner<T>(s2 + arc * Q2, Q2, uh);
-  const cplx<T> Qs = s2[4 * Q2];
+    far = horner_n<T, P>(lexp + ((int64_t)(level_off(d.L) - 4) + b) * p, p, u);
+  const cplx<T> reg = horner<T>(lvl2 + arc * Q2, Q2, uh);
   const T hr = cN * fma(far.x, ts, nr.x) - c2 * reg.x;
   const T hi = cN * fma(far.y, ts, nr.y) - c2 * reg.y;
   const cplx<T> wv = mk<T>(Qs.x - hi, Qs.y + hr);
@@ -1784,26 +1755,15 @@ __device__ inline void grid2_tile(
   int lxb = 0;
   const cplx<T>* l2 = lvl2;
   if constexpr (MODE == 2) {  // near-field sums and self terms formed by an earlier launch
-    if (act) {
-      nr0 = hin[2 * (int64_t)k];
-      self0 = hin[2 * (int64_t)k + 1];
-      if (k + 1 < N) {
-        nr1 = hin[2 * (int64_t)k + 2];
-        self1 = hin[2 * (int64_t)k + 3];
-      }
-    }
-    cplx<T>* sl = reinterpret_cast<cplx<T>*>(smraw);
-    const int nlf = bh - bl + 1;
-    if (d.L >= 3 && nlf <= kFarLeaves) {
-      stage_batched<4>(nlf * p, sl, [&](int e) { return lxg[(int64_t)bl * p + e]; });
-      lx = sl;
-      lxb = bl;
-    }
-    cplx<T>* s2 = sl + kFarLeaves * p;
-    stage_batched<2>(8 * d.q + 1, s2, [&](int e) { return lvl2[e]; });
-    l2 = s2;
-    __syncthreads();
+    // (the leaf locals and level-2 coefficients read through L1: every load
+    // of this part is independent of the others, no barrier)
     if (!act) return;
+    nr0 = hin[2 * (int64_t)k];
+    self0 = hin[2 * (int64_t)k + 1];
+    if (k + 1 < N) {
+      nr1 = hin[2 * (int64_t)k + 2];
+      self1 = hin[2 * (int64_t)k + 3];
+    }
   } else {
   if (threadIdx.x < 32) {
     int carry = 0;
@@ -2670,7 +2630,7 @@ int fmm_forward(nufft_plan_s* pl, void* g) {
     }
   }
   if (split) {
-    const size_t sm = (size_t)(kFarLeaves * pl->p + 8 * pl->q + 1) * sizeof(cplx<T>);
+    const size_t sm = 0;
     const unsigned nb = nblk(pl->M, kTgtThreads);
     if (c64)
       launch_far_fwd<T, float2>(pl->p, nb, sm, pl->stream, d, (int)pl->M,
@@ -2830,7 +2790,7 @@ int fmm_to_grid(nufft_plan_s* pl, const void* g, int inverse) {
     side_join(pl, 2);
     prof_begin(pl, NUFFT_STAGE_TARGETS);
     launch_far_grid2<T>(pl->p, nblk(pl->N, 2 * kTgtThreads),
-                        (size_t)(kFarLeaves * pl->p + 8 * pl->q + 1) * sizeof(cplx<T>), st, d,
+                        (size_t)0, st, d,
                         inverse, (const int32_t*)pl->leaf_start, (const SrcPos<T>*)pos,
                         (const cplx<T>*)charge, (const cplx<T>*)stt, (const cplx<T>*)pl->lexp,
                         PlanT<T>::lvl2(pl), PlanT<T>::Ct(pl), (cplx<T>*)pl->grid,
