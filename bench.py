@@ -627,12 +627,42 @@ def run_batched(steps: int = 5, warmup: int = 3, tune_params: bool = True):
     cs = [torch.from_numpy(workloads.coeffs(n, seed=2000 + i).astype(np.complex64)).cuda()
           for i, n in enumerate(Ns)]
     gs = [torch.empty(n, dtype=torch.complex64, device="cuda") for n in Ns]
+    # parameters per size class (outside the timing, like the plans): the
+    # autotuner once per N on the first transform of that size, its choice
+    # used for every transform of the class
     t0 = time.perf_counter()
-    multi = nf.Multi(Ns, ys, eps=1e-6, prec=nf.MIXED, io="c64")
+    per_class = {}
+    if tune_params:
+        from paper_1611_09379_gb300 import tune
+        for n in sorted(set(Ns)):
+            i0 = Ns.index(n)
+            ent = tune.autotune(n, ys[i0], 1e-6, prec=nf.MIXED, io="c64", ops="fwd", reps=3,
+                                tag="uniform")
+            per_class[n] = {k: ent["params"][k] for k in ("lmax", "p", "q", "tc_level", "tc_near")}
+    t_tune = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    multi = nf.Multi(Ns, ys, eps=1e-6, prec=nf.MIXED, io="c64",
+                     params=[per_class.get(n) for n in Ns] if per_class else None)
     t_plan = time.perf_counter() - t0
     ms = _timed(lambda: multi.forward(cs, gs), flush, stream, steps, warmup)
+    acc = None
+    try:
+        import oracle
+        worst = 0.0
+        for i in (0, int(np.argmax(Ns)), 255):
+            idx = workloads.sample_index(Ns[i], 64, seed=i)
+            y_i = ys[i].cpu().numpy()
+            ref = oracle.nudft_fwd(cs[i].cpu().numpy().astype(complex), y_i, idx)
+            worst = max(worst, oracle.rel_l2(gs[i].cpu().numpy()[idx], ref))
+        acc = worst
+    except Exception as e:
+        acc = repr(e)
     out["uneven256"] = {"count": 256, "points": int(sum(Ns)), "ms": ms,
                         "value": sum(Ns) / (ms / 1e3), "unit": "points/s", "plan_s": t_plan,
+                        "tune_s": t_tune,
+                        "params_per_N": {str(n): v for n, v in sorted(per_class.items())} or
+                        "formulas",
+                        "fwd_rel_l2_sampled_max": acc,
                         "launch": "one CUDA graph (16 forked streams)"}
     multi.close()
     return out

@@ -406,14 +406,17 @@ int nufft_plan_stats(nufft_plan plan, double *stage_ms, int64_t *launches);
  * instantiated graph is replayed while the caller's buffers stay the same.
  * The paper treats one transform at a time; this groups many.
  * nufft_multi_create builds one plan per transform (same eps, prec, flags;
- * NUFFT_WANT_INVERSE not supported) and synchronises the stream.
+ * NUFFT_WANT_INVERSE not supported) and synchronises the stream; params
+ * [host] (NULL, or count entries) gives each plan's parameters as
+ * nufft_plan_create's params (zero fields: the formulas), for instance the
+ * autotuner's choice per size class.
  * nufft_multi_exec_fwd: c[i] [device] N[i] coefficients, g[i] [device] M[i]
  * outputs; captures a new graph when the pointers differ from the previous
  * call's, then launches it on the stream (asynchronous). */
 typedef struct nufft_multi_s *nufft_multi;
 int nufft_multi_create(nufft_multi *out, int count, const int64_t *N, const int64_t *M,
-                       const double *const *y, double eps, int prec, unsigned flags,
-                       void *stream);
+                       const double *const *y, double eps, int prec,
+                       const nufft_params *params, unsigned flags, void *stream);
 int nufft_multi_exec_fwd(nufft_multi multi, const void *const *c, void *const *g);
 int nufft_multi_destroy(nufft_multi multi);
 

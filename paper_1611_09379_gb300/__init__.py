@@ -85,7 +85,7 @@ _lib.nufft_plan_set_stream.argtypes = [_P, _P]
 _lib.nufft_plan_points.argtypes = [_P, _P, _P, _P, _P]
 _lib.nufft_plan_profile.argtypes = [_P, ctypes.c_int]
 _lib.nufft_multi_create.argtypes = [ctypes.POINTER(_P), ctypes.c_int, _P, _P, _P, ctypes.c_double,
-                                    ctypes.c_int, ctypes.c_uint, _P]
+                                    ctypes.c_int, _P, ctypes.c_uint, _P]
 _lib.nufft_multi_exec_fwd.argtypes = [_P, _P, _P]
 _lib.nufft_multi_destroy.argtypes = [_P]
 _lib.nufft_plan_dcf_features.argtypes = [_P, _P]
@@ -550,11 +550,14 @@ class MLP:
 class Multi:
     """Independent forward transforms of uneven sizes run as one CUDA graph launch.
 
-    ys: list of CUDA float64 point tensors; Ns: grid sizes.  forward(cs, gs)
-    takes lists of coefficient / output tensors (captures a graph the first
-    time and whenever the tensors change, then replays it)."""
+    ys: list of CUDA float64 point tensors; Ns: grid sizes; params: None or
+    one dict per transform (lmax, p, q, tc_level, tc_near: a plan's
+    parameters, 0 / missing = the formulas).  forward(cs, gs) takes lists of
+    coefficient / output tensors (captures a graph the first time and
+    whenever the tensors change, then replays it)."""
 
-    def __init__(self, Ns, ys, eps: float = 1e-6, prec: int = MIXED, io: str = "c64", stream=None):
+    def __init__(self, Ns, ys, eps: float = 1e-6, prec: int = MIXED, io: str = "c64", stream=None,
+                 params=None):
         import numpy as np
         torch = _torch()
         self.Ns = [int(n) for n in Ns]
@@ -565,9 +568,20 @@ class Multi:
         Na = np.array(self.Ns, dtype=np.int64)
         Ma = np.array(self.Ms, dtype=np.int64)
         yp = (ctypes.c_void_p * n)(*[_dev_ptr(y, torch.float64, m, "y").value for y, m in zip(ys, self.Ms)])
+        prm = None
+        if params is not None:
+            if len(params) != n:
+                raise ValueError("params: one entry per transform")
+            prm = (Params * n)()
+            for i, d in enumerate(params):
+                d = d or {}
+                prm[i] = Params(int(d.get("lmax", 0)), int(d.get("p", 0)), int(d.get("q", 0)), 1,
+                                int(d.get("tc_level", 0)), int(d.get("tc_near", 0)))
         h = _P()
         _check(_lib.nufft_multi_create(ctypes.byref(h), n, Na.ctypes.data_as(_P), Ma.ctypes.data_as(_P),
-                                       ctypes.cast(yp, _P), eps, prec, IO_C64 if io == "c64" else 0,
+                                       ctypes.cast(yp, _P), eps, prec,
+                                       ctypes.cast(prm, _P) if prm is not None else None,
+                                       IO_C64 if io == "c64" else 0,
                                        _stream_handle(stream)), "nufft_multi_create")
         self._h = h
 

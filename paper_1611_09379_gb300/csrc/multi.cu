@@ -43,8 +43,8 @@ static void multi_free(nufft_multi_s* m) {
 extern "C" {
 
 int nufft_multi_create(nufft_multi* out, int count, const int64_t* N, const int64_t* M,
-                       const double* const* y, double eps, int prec, unsigned flags,
-                       void* stream) {
+                       const double* const* y, double eps, int prec,
+                       const nufft_params* params, unsigned flags, void* stream) {
   if (!out || count < 1 || !N || !M || !y) return NUFFT_EINVAL;
   if (flags & NUFFT_WANT_INVERSE) return NUFFT_ENOTSUP;
   *out = nullptr;
@@ -53,7 +53,8 @@ int nufft_multi_create(nufft_multi* out, int count, const int64_t* N, const int6
   m->user = (cudaStream_t)stream;
   m->plans.assign(count, nullptr);
   for (int i = 0; i < count; ++i) {
-    int rc = nufft_plan_create(&m->plans[i], N[i], M[i], y[i], eps, prec, nullptr, flags, stream);
+    int rc = nufft_plan_create(&m->plans[i], N[i], M[i], y[i], eps, prec,
+                               params ? &params[i] : nullptr, flags, stream);
     if (rc) { multi_free(m); return rc; }
   }
   if (cudaEventCreateWithFlags(&m->fork, cudaEventDisableTiming) != cudaSuccess ||
