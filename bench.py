@@ -663,7 +663,7 @@ def run_batched(steps: int = 5, warmup: int = 3, tune_params: bool = True):
                         "params_per_N": {str(n): v for n, v in sorted(per_class.items())} or
                         "formulas",
                         "fwd_rel_l2_sampled_max": acc,
-                        "launch": "one CUDA graph (16 forked streams)"}
+                        "launch": "one CUDA graph (64 forked streams)"}
     multi.close()
     return out
 
