@@ -264,6 +264,8 @@ struct nufft_plan_s {
   float2 *Dtf = nullptr;          // [M] FP32 copy (mixed path)
   double *Ct = nullptr;           // [N] real C_k e^{+Lambda} / N
   float *Ctf = nullptr;           // [N] FP32 copy (mixed path)
+  double2 *Sinv = nullptr;        // [M] sorted: the inverse's self term st_j = q_j S_j
+  float2 *Sinvf = nullptr;        // [M] FP32 copy (mixed path)
   double *Lambda = nullptr;       // [1] common scale of C and D
   int64_t inv_nc = 0;             // Nc when C carries the phase e^{i pi k Nc / N} (Nc < N)
   // FMM workspace

@@ -1478,14 +1478,16 @@ template <class T> struct InlineSrc {
   const T* Ctt = nullptr;
   const T* delt = nullptr;
   T n_2pi = 0;
+  const cplx<T>* S = nullptr;  // the inverse's self-term factors (q_j S_j), when formed
 };
 
 // The charge of staged source i (returned) and, with need_self, its self
 // term (to *st): the same values as charge_of and self_term_of, with the
-// caller's sample read once for both and the grid index and offset taken
-// from the staged position record; the inverse's FP32 self term multiplies
-// by the reciprocal of delta (rcp_t, within 1 ulp) instead of an IEEE
-// division, and falls back to self_term_of where its FP32 range checks fail.
+// caller's sample read once for both; the inverse's self term is q_i S_i
+// with the plan's factor S_i (k_assemble_S) where the plan formed it, else
+// (from the staged position record) its FP32 form multiplies by the
+// reciprocal of delta (rcp_t, within 1 ulp) instead of an IEEE division and
+// falls back to self_term_of where its FP32 range checks fail.
 template <class T>
 __device__ inline cplx<T> stage_charge_self(const InlineSrc<T>& is, const TreeDims& d, int i,
                                             const SrcPos<T>& ps, bool need_self,
@@ -1498,6 +1500,10 @@ __device__ inline cplx<T> stage_charge_self(const InlineSrc<T>& is, const TreeDi
   if (!need_self) return q;
   if (!a.inverse) {
     *st = cmul(cconj(is.E[i]), gs);
+    return q;
+  }
+  if (is.S) {
+    *st = cmul(q, is.S[i]);
     return q;
   }
   if constexpr (sizeof(T) == 4) {
@@ -2281,6 +2287,7 @@ template <> struct PlanT<double> {
   static const double2* E(nufft_plan_s* pl) { return pl->E; }
   static const double2* lvl2(nufft_plan_s* pl) { return pl->lvl2; }
   static const double* Ct(nufft_plan_s* pl) { return pl->Ct; }
+  static const double2* S(nufft_plan_s* pl) { return pl->Sinv; }
 };
 template <> struct PlanT<float> {
   static const float* delta(nufft_plan_s* pl) { return pl->delta_f; }
@@ -2289,6 +2296,7 @@ template <> struct PlanT<float> {
   static const float2* E(nufft_plan_s* pl) { return pl->Ef; }
   static const float2* lvl2(nufft_plan_s* pl) { return pl->lvl2f; }
   static const float* Ct(nufft_plan_s* pl) { return pl->Ctf; }
+  static const float2* S(nufft_plan_s* pl) { return pl->Sinvf; }
 };
 
 // Upward pass (P2M, M2M) for all signals of the plan at once (grid y =
@@ -2754,6 +2762,7 @@ int fmm_to_grid(nufft_plan_s* pl, const void* g, int inverse) {
       isrc.Ctt = PlanT<T>::Ct(pl);
       isrc.delt = PlanT<T>::delta(pl);
       isrc.n_2pi = KConst<T>::n_2pi_h(d);
+      if (inverse) isrc.S = PlanT<T>::S(pl);
     } else {
       prof_begin(pl, NUFFT_STAGE_P2M);
       if (c64)

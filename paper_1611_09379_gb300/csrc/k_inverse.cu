@@ -329,6 +329,36 @@ TmpLayout layout(const nufft_plan_s* pl) {
 
 size_t inverse_tmp_bytes(const nufft_plan_s* pl) { return layout(pl).total; }
 
+// The inverse's self term of sorted point j (the closed form of its pair with
+// the nearest grid point x_k0, Eq. p6 with Eq. p8's factors) is its charge
+// q_j = D~_j g_j times a factor of the points alone:
+//   S_j = i C~_k0 (N / 2pi) / delta_j  (times e^{i pi k0 Nc / N} when the
+//         coefficient count Nc is below the grid size N),
+//   S_j = 1 / (N D~_j) at an exact hit (the grid value there is g_j / N).
+// Formed in FP64 once per plan (with an FP32 copy for the mixed path), so
+// the near-field kernels' staging multiplies instead of dividing.
+__global__ void k_assemble_S(TreeDims d, int64_t M, const int32_t* __restrict__ k0s,
+                             const double* __restrict__ dels, const double* __restrict__ Ct,
+                             const double2* __restrict__ Dt, double2* __restrict__ S,
+                             float2* __restrict__ Sf) {
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= M) return;
+  const double dl = dels[j];
+  double2 v;
+  if (dl == 0.0) {
+    const double2 q = Dt[j];
+    const double n2 = (q.x * q.x + q.y * q.y) * (double)d.N;
+    v = make_double2(q.x / n2, -q.y / n2);
+  } else {
+    const int k0 = k0s[j];
+    const double w = Ct[k0] * (0.5 * (double)d.N * kInvPi) / dl;
+    v = make_double2(0.0, w);
+    if (d.nc) v = cmul(v, inv_phase(d, k0));
+  }
+  S[j] = v;
+  if (Sf) Sf[j] = make_float2((float)v.x, (float)v.y);
+}
+
 int inverse_precompute(nufft_plan_s* pl, void* tmp, size_t tmp_bytes) {
   TmpLayout t = layout(pl);
   if (tmp_bytes < t.total) return NUFFT_EINVAL;
@@ -339,8 +369,10 @@ int inverse_precompute(nufft_plan_s* pl, void* tmp, size_t tmp_bytes) {
   if (cudaMalloc((void**)&pl->Ct, N * 8) != cudaSuccess) return NUFFT_ENOMEM;
   if (cudaMalloc((void**)&pl->Dt, M * 16) != cudaSuccess) return NUFFT_ENOMEM;
   if (cudaMalloc((void**)&pl->Lambda, 8) != cudaSuccess) return NUFFT_ENOMEM;
+  if (cudaMalloc((void**)&pl->Sinv, M * 16) != cudaSuccess) return NUFFT_ENOMEM;
   if (pl->prec != NUFFT_FP64 && (cudaMalloc((void**)&pl->Ctf, N * 4) != cudaSuccess ||
-                                 cudaMalloc((void**)&pl->Dtf, M * 8) != cudaSuccess))
+                                 cudaMalloc((void**)&pl->Dtf, M * 8) != cudaSuccess ||
+                                 cudaMalloc((void**)&pl->Sinvf, M * 8) != cudaSuccess))
     return NUFFT_ENOMEM;
   // ---- operators of the log kernel (host, long double)
   Bin C(2 * 64 + 2);
@@ -441,5 +473,9 @@ int inverse_precompute(nufft_plan_s* pl, void* tmp, size_t tmp_bytes) {
                                              pl->status);
   k_assemble_D<<<nblk(M, 256), 256, 0, st>>>(lamD, nD, pl->k0, pl->delta, M, pl->Nc, N, Lam, elim,
                                              pl->Dt, pl->Dtf, pl->status);
+  TreeDims dn = d;
+  dn.nc = pl->inv_nc;
+  k_assemble_S<<<nblk(M, 256), 256, 0, st>>>(dn, M, pl->k0, pl->delta, pl->Ct, pl->Dt, pl->Sinv,
+                                             pl->Sinvf);
   return cudaGetLastError() == cudaSuccess ? NUFFT_OK : NUFFT_ECUDA;
 }

@@ -231,7 +231,7 @@ int build_operators(nufft_plan_s* pl) {
 
 void free_plan(nufft_plan_s* pl) {
   void* ptrs[] = {pl->perm, pl->leaf_start, pl->k0, pl->delta, pl->F, pl->E, pl->delta_f,
-                  pl->Ff, pl->Ef, pl->lvl2f, pl->Dt, pl->Dtf, pl->Ct, pl->Ctf, pl->selft, pl->srcpos, pl->Lambda, pl->mexp, pl->lexp,
+                  pl->Ff, pl->Ef, pl->lvl2f, pl->Dt, pl->Dtf, pl->Ct, pl->Ctf, pl->Sinv, pl->Sinvf, pl->selft, pl->srcpos, pl->Lambda, pl->mexp, pl->lexp,
                   pl->charge, pl->grid, pl->grid2, pl->grid3, pl->lvl2, pl->op_m2m, pl->op_m2l,
                   pl->op_l2l, pl->op_p2m, pl->op_reg, pl->fft_tw, pl->fft_tw_f, pl->status,
                   pl->seg_overflow, pl->lsq_work, pl->op_tc, pl->upcnt, pl->hnear};
