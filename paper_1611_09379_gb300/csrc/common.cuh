@@ -111,9 +111,9 @@ struct TreeDims {
   int64_t lstride = 0;  //   multipoles, locals (complex elements)
   int64_t M_ = 0;       //   and points (charges per signal)
   // per-plan constants formed on the host (kernels need no FP64 division):
-  // 2/N, 1/s, N/pi, N/(2 pi) in both precisions
-  double two_n = 0, inv_s = 0, n_pi = 0, n_2pi = 0;
-  float two_n_f = 0, inv_s_f = 0, n_pi_f = 0, n_2pi_f = 0;
+  // 2/N, 1/s, N/pi in both precisions
+  double two_n = 0, inv_s = 0, n_pi = 0;
+  float two_n_f = 0, inv_s_f = 0, n_pi_f = 0;
   // square inverse with Nc = nc coefficients on this grid (nc < N): C at the
   // grid point k carries the phase e^{i pi k nc / N} (0: the phase is the
   // sign (-1)^k, already in C)
@@ -134,15 +134,11 @@ template <> struct KConst<double> {
   __device__ static double two_n(const TreeDims& d) { return d.two_n; }
   __device__ static double inv_s(const TreeDims& d) { return d.inv_s; }
   __device__ static double n_pi(const TreeDims& d) { return d.n_pi; }
-  __device__ static double n_2pi(const TreeDims& d) { return d.n_2pi; }
-  static double n_2pi_h(const TreeDims& d) { return d.n_2pi; }
 };
 template <> struct KConst<float> {
   __device__ static float two_n(const TreeDims& d) { return d.two_n_f; }
   __device__ static float inv_s(const TreeDims& d) { return d.inv_s_f; }
   __device__ static float n_pi(const TreeDims& d) { return d.n_pi_f; }
-  __device__ static float n_2pi(const TreeDims& d) { return d.n_2pi_f; }
-  static float n_2pi_h(const TreeDims& d) { return d.n_2pi_f; }
 };
 
 // Device-side error word (set by kernels, read back by the host).

@@ -1407,27 +1407,21 @@ __global__ void k_charges(int64_t M, const int32_t* __restrict__ perm,
 }
 
 // The pair (y_j, x_k0) of each source j with its nearest grid point, one
-// thread per sorted source and signal (uniform work, so the FP64 arithmetic
-// of the inverse does not diverge inside a warp):
+// thread per sorted source and signal:
 //   adjoint: conj(E_j) g_j, the closed form of the pair's 2/t part (and
 //            conj(F_j) G(x_k0 - y_j) -> 1 at an exact hit);
-//   inverse: the pair's 2/t part times the target factor,
-//            Ct_k0 (i/2) (N/pi) q_j / delta_j, formed in FP64 (finite, as Ct_k0
-//            carries sin((x_k0 - y_j)/2)); g_j / N at an exact hit, where
-//            Ct_k0 = 0 removes every other term.
-//   The FP32 path forms Ct_k0 / delta_j in FP32 when |delta_j| >= 2^-20 and
-//   |Ct_k0| >= 2^-100 (no underflow or overflow on the way), else in FP64.
+//   inverse: the pair's 2/t part times the target factor, q_j S_j with the
+//            plan's per-point factor S_j = i C~_k0 (N / 2pi) / delta_j (finite,
+//            as C~_k0 carries sin((x_k0 - y_j)/2); times the general-N phase),
+//            1 / (N D~_j) at an exact hit, where C~_k0 = 0 removes every
+//            other term (k_assemble_S, in FP64 with an FP32 copy).
 // The same quantities for one sorted source i of one signal (the caller
 // offsets gin by the signal), in a form the near-field kernels can also
 // evaluate while staging their sources: the charge q_i = coef_i g_perm(i)
 // (conj(coef_i) for the adjoint) and its self term.
 struct SelfArgs {
-  int N = 0;
   int inverse = 0;
-  const int32_t* k0s = nullptr;
-  const double* dels = nullptr;
   const int32_t* perm = nullptr;
-  const double* Ct = nullptr;
   const void* gin = nullptr;  // caller samples: double2 (gin64) or float2
   int gin64 = 1;
 };
@@ -1435,38 +1429,11 @@ template <class T> __device__ inline cplx<T> sample_in(const SelfArgs& a, int64_
   return a.gin64 ? load_in<T>((const double2*)a.gin + idx) : load_in<T>((const float2*)a.gin + idx);
 }
 template <class T>
-__device__ inline cplx<T> charge_of(const SelfArgs& a, const cplx<T>* __restrict__ coef, int i) {
-  cplx<T> c = coef[i];
-  if (!a.inverse) c.y = -c.y;  // the adjoint's conj(F_i)
-  return cmul(c, sample_in<T>(a, a.perm[i]));
-}
-template <class T>
-__device__ inline cplx<T> self_term_of(const SelfArgs& a, const TreeDims& dd, int i, cplx<T> q,
-                                       const cplx<T>* __restrict__ E, const T* __restrict__ Ctt,
-                                       const T* __restrict__ delt, T n_2pi) {
+__device__ inline cplx<T> self_term_of(const SelfArgs& a, int i, cplx<T> q,
+                                       const cplx<T>* __restrict__ E,
+                                       const cplx<T>* __restrict__ S) {
   if (!a.inverse) return cmul(cconj(E[i]), sample_in<T>(a, a.perm[i]));
-  const T dt = delt[i];
-  const int k0 = a.k0s[i];
-  if (sizeof(T) == 4) {
-    const T ct = Ctt[k0];
-    if (fabs(dt) >= (T)9.5367431640625e-07 && fabs(ct) >= (T)7.888609052210118e-31) {
-      const T w = (ct / dt) * n_2pi;
-      cplx<T> v = mk<T>(-q.y * w, q.x * w);
-      if (dd.nc) v = cmul(v, from_d2<T>(inv_phase(dd, k0)));
-      return v;
-    }
-  }
-  double d = a.dels[i];
-  double2 v;
-  if (d == 0.0) {
-    v = cscale(to_d2(sample_in<T>(a, a.perm[i])), 1.0 / (double)a.N);
-  } else {
-    double2 q2 = to_d2(q);
-    double w = a.Ct[k0] * (0.5 * (double)a.N * kInvPi) / d;
-    v = make_double2(-q2.y * w, q2.x * w);
-    if (dd.nc) v = cmul(v, inv_phase(dd, k0));  // an exact hit takes g_j itself, no phase
-  }
-  return from_d2<T>(v);
+  return cmul(q, S[i]);
 }
 
 // Charges and self terms formed where they are used (coef non-null), or read
@@ -1475,58 +1442,28 @@ template <class T> struct InlineSrc {
   SelfArgs a;
   const cplx<T>* coef = nullptr;
   const cplx<T>* E = nullptr;
-  const T* Ctt = nullptr;
-  const T* delt = nullptr;
-  T n_2pi = 0;
-  const cplx<T>* S = nullptr;  // the inverse's self-term factors (q_j S_j), when formed
+  const cplx<T>* S = nullptr;  // the inverse's self-term factors S_j
 };
 
 // The charge of staged source i (returned) and, with need_self, its self
-// term (to *st): the same values as charge_of and self_term_of, with the
-// caller's sample read once for both; the inverse's self term is q_i S_i
-// with the plan's factor S_i (k_assemble_S) where the plan formed it, else
-// (from the staged position record) its FP32 form multiplies by the
-// reciprocal of delta (rcp_t, within 1 ulp) instead of an IEEE division and
-// falls back to self_term_of where its FP32 range checks fail.
+// term (to *st): the values of k_charges and self_term_of, with the caller's
+// sample read once for both.
 template <class T>
-__device__ inline cplx<T> stage_charge_self(const InlineSrc<T>& is, const TreeDims& d, int i,
-                                            const SrcPos<T>& ps, bool need_self,
+__device__ inline cplx<T> stage_charge_self(const InlineSrc<T>& is, int i, bool need_self,
                                             cplx<T>* st) {
   const SelfArgs& a = is.a;
   const cplx<T> gs = sample_in<T>(a, a.perm[i]);
   cplx<T> c = is.coef[i];
   if (!a.inverse) c.y = -c.y;  // the adjoint's conj(F_i)
   const cplx<T> q = cmul(c, gs);
-  if (!need_self) return q;
-  if (!a.inverse) {
-    *st = cmul(cconj(is.E[i]), gs);
-    return q;
-  }
-  if (is.S) {
-    *st = cmul(q, is.S[i]);
-    return q;
-  }
-  if constexpr (sizeof(T) == 4) {
-    const int k0 = (int)ps.k0;
-    const T dt = ps.dl, ct = is.Ctt[k0];
-    if (fabs(dt) >= (T)9.5367431640625e-07 && fabs(ct) >= (T)7.888609052210118e-31) {
-      const T w = (ct * rcp_t(dt)) * is.n_2pi;
-      cplx<T> v = mk<T>(-q.y * w, q.x * w);
-      if (d.nc) v = cmul(v, from_d2<T>(inv_phase(d, k0)));
-      *st = v;
-      return q;
-    }
-  }
-  *st = self_term_of<T>(a, d, i, q, is.E, is.Ctt, is.delt, is.n_2pi);
+  if (need_self) *st = a.inverse ? cmul(q, is.S[i]) : cmul(cconj(is.E[i]), gs);
   return q;
 }
 
 template <class T, class VI>
-__global__ void k_self_terms(int M, int inverse, int N, TreeDims dd, const int32_t* __restrict__ k0s,
-                             const double* __restrict__ dels, const int32_t* __restrict__ perm,
-                             const cplx<T>* __restrict__ E, const cplx<T>* __restrict__ charge,
-                             const VI* __restrict__ gin, const double* __restrict__ Ct,
-                             const T* __restrict__ Ctt, const T* __restrict__ delt, T n_2pi,
+__global__ void k_self_terms(int M, int inverse, const int32_t* __restrict__ perm,
+                             const cplx<T>* __restrict__ E, const cplx<T>* __restrict__ S,
+                             const cplx<T>* __restrict__ charge, const VI* __restrict__ gin,
                              cplx<T>* __restrict__ st) {
   pdl_wait();
   pdl_trigger();
@@ -1536,15 +1473,11 @@ __global__ void k_self_terms(int M, int inverse, int N, TreeDims dd, const int32
   charge += (int64_t)blockIdx.y * M;
   st += (int64_t)blockIdx.y * M;
   SelfArgs a;
-  a.N = N;
   a.inverse = inverse;
-  a.k0s = k0s;
-  a.dels = dels;
   a.perm = perm;
-  a.Ct = Ct;
   a.gin = gin;
   a.gin64 = sizeof(VI) == sizeof(double2);
-  st[i] = self_term_of<T>(a, dd, i, inverse ? charge[i] : mk<T>(0, 0), E, Ctt, delt, n_2pi);
+  st[i] = self_term_of<T>(a, i, inverse ? charge[i] : mk<T>(0, 0), E, S);
 }
 
 
@@ -1856,7 +1789,7 @@ __device__ inline void grid2_tile(
           // (only a source whose nearest grid point lies in this tile's
           // range can be in a tile point's own run: the halo's sources need
           // no self term)
-          v.q = stage_charge_self<T>(isrc, d, gi, ps, xu >= 0 && xu < kPts, &sst[e - c0]);
+          v.q = stage_charge_self<T>(isrc, gi, xu >= 0 && xu < kPts, &sst[e - c0]);
         } else {
           v.q = charge[gi];
           sst[e - c0] = st[gi];
@@ -2269,11 +2202,9 @@ TreeDims dims_of(const nufft_plan_s* pl) {
   d.two_n = 2.0 / (double)pl->N;
   d.inv_s = 1.0 / (double)pl->s;
   d.n_pi = (double)pl->N * kInvPi;
-  d.n_2pi = 0.5 * (double)pl->N * kInvPi;
   d.two_n_f = (float)d.two_n;
   d.inv_s_f = (float)d.inv_s;
   d.n_pi_f = (float)d.n_pi;
-  d.n_2pi_f = (float)d.n_2pi;
   d.nc = pl->inv_nc;
   return d;
 }
@@ -2714,9 +2645,8 @@ template <class T, class VI>
 static void launch_self_terms(nufft_plan_s* pl, const TreeDims& d, int inverse, const VI* g,
                               const cplx<T>* charge, cplx<T>* stt, cudaStream_t s1) {
   const dim3 gm(nblk(pl->M, 256), (unsigned)pl->batch);
-  launch_pdl(k_self_terms<T, VI>, gm, 256, 0, s1, (int)pl->M, inverse, (int)pl->N, d, pl->k0,
-             pl->delta, pl->perm, PlanT<T>::E(pl), charge, g, pl->Ct, PlanT<T>::Ct(pl),
-             PlanT<T>::delta(pl), KConst<T>::n_2pi_h(d), stt);
+  launch_pdl(k_self_terms<T, VI>, gm, 256, 0, s1, (int)pl->M, inverse, pl->perm, PlanT<T>::E(pl),
+             inverse ? PlanT<T>::S(pl) : (const cplx<T>*)nullptr, charge, g, stt);
 }
 
 // adjoint / inverse: samples g ([batch][M], original order) -> values on the
@@ -2749,19 +2679,12 @@ int fmm_to_grid(nufft_plan_s* pl, const void* g, int inverse) {
     const bool inl = !gridw_wanted(pl);
     InlineSrc<T> isrc;
     if (inl) {
-      isrc.a.N = (int)pl->N;
       isrc.a.inverse = inverse;
-      isrc.a.k0s = pl->k0;
-      isrc.a.dels = pl->delta;
       isrc.a.perm = pl->perm;
-      isrc.a.Ct = pl->Ct;
       isrc.a.gin = g;
       isrc.a.gin64 = c64 ? 0 : 1;
       isrc.coef = coef;
       isrc.E = PlanT<T>::E(pl);
-      isrc.Ctt = PlanT<T>::Ct(pl);
-      isrc.delt = PlanT<T>::delta(pl);
-      isrc.n_2pi = KConst<T>::n_2pi_h(d);
       if (inverse) isrc.S = PlanT<T>::S(pl);
     } else {
       prof_begin(pl, NUFFT_STAGE_P2M);

@@ -315,6 +315,28 @@ def test_inverse_exact_hit(nf, orc):
     assert orc.rel_l2(c2, c) < 1e-12
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("y0", [0.0, 1e-30])
+def test_inverse_near_grid_points(nf, orc, prec, y0):
+    """Points at or next to grid points, where the self term's factor
+    C~_k0 / delta_j is a ratio of two small numbers (C~_k0 carries
+    sin((x_k0 - y_j)/2)): an exact hit at y = 0 or a point 1e-30 from it,
+    and points one ulp either side of grid points, on the 10 % jittered
+    grid.  The round trip meets eps in both precisions."""
+    N = 1024
+    y = workloads.points("jitter", N, N, seed=19, jitter=0.1)
+    xk = 2 * math.pi * np.arange(N) / N
+    y[0] = y0
+    y[37::97] = np.nextafter(xk[37::97], 10.0)
+    y[81::97] = np.nextafter(xk[81::97], -10.0)
+    c = workloads.coeffs(N, seed=20)
+    g = orc.nudft_fwd(c, y)
+    plan = nf.Plan(N, _dev(y), eps=1e-12 if prec == 0 else 1e-6, prec=prec, inverse=True)
+    c2 = _host(plan.inverse(_dev(g)))
+    assert np.all(np.isfinite(c2))
+    assert orc.rel_l2(c2, c) < (1e-11 if prec == 0 else 1e-6)
+
+
 _LAMD_CACHE = {}
 
 
