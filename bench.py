@@ -552,6 +552,8 @@ def run_ours(args):
         out["batched"] = run_batched(tune_params=not args.no_tune)
     if not args.no_large:
         out["large"] = run_large(tune_params=not args.no_tune)
+    if not args.no_adaptive:
+        out["adaptive_forward"] = run_adaptive()
     if not args.no_lsq:
         out["inufft_lsq"] = run_lsq(budget_s=args.lsq_seconds, full=args.lsq_full)
     print(json.dumps(out))
@@ -720,6 +722,52 @@ def run_large(steps: int = 5, warmup: int = 3, tune_params: bool = True):
             "ms": ms, "value": 2 * M / (ms / 1e3), "unit": "points/s", "params": info,
             "tuning": tuned, "stage_roofline": stage_roofline(per, N, M, info, 8, 1, 1, peaks),
             "accuracy": acc}
+
+
+def run_adaptive(steps: int = 10, warmup: int = 3):
+    """Forward NUFFT on clustered points, N = M = 2^20, complex64, mixed
+    eps = 1e-6: the uniform tree against the adaptive tree (NUFFT_ADAPTIVE,
+    leaves refined where they hold more targets than the mean), the same
+    parameters (Eq. 18.2 / 25), for the eight-cluster mixture and for
+    clusters of four widths over a uniform background."""
+    import torch
+
+    import paper_1611_09379_gb300 as nf
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    N = M = 1 << 20
+    c = workloads.coeffs(N, seed=61).astype(np.complex64)
+    cd = torch.from_numpy(c).cuda()
+    out = {"workload": "forward NUFFT, N=M=2^20, complex64, mixed eps=1e-6, clustered y",
+           "unit": "points/s", "cases": {}}
+    for kind, seed in (("clustered", 62), ("multiscale", 63)):
+        y = workloads.points(kind, M, seed=seed)
+        yd = torch.from_numpy(y).cuda()
+        case = {}
+        for name, ad in (("uniform_tree", False), ("adaptive_tree", True)):
+            plan = nf.Plan(N, yd, eps=1e-6, prec=nf.MIXED, io="c64", adaptive=ad)
+            g = torch.empty(M, dtype=torch.complex64, device="cuda")
+            ms = _timed(lambda: plan.forward(cd, out=g), flush, stream, steps, warmup)
+            plan.profile(True)
+            _timed(lambda: plan.forward(cd, out=g), flush, stream, 3, 0)
+            per = {k: round(v[0] / 3, 4) for k, v in plan.stats().items() if v[1]}
+            plan.profile(False)
+            lv, cnt = plan.adaptive()
+            r = {"ms": ms, "value": M / (ms / 1e3), "levels": lv, "class_counts": cnt,
+                 "stage_ms": per}
+            try:
+                import oracle
+                idx = workloads.sample_index(M, 64, seed=7)
+                r["fwd_rel_l2_sampled"] = oracle.rel_l2(
+                    g.cpu().numpy()[idx], oracle.nudft_fwd(c.astype(complex), y, idx))
+            except Exception as e:
+                r["fwd_rel_l2_sampled"] = repr(e)
+            case[name] = r
+            case["params"] = plan.params()
+            del plan
+        case["speedup"] = case["uniform_tree"]["ms"] / case["adaptive_tree"]["ms"]
+        out["cases"][kind] = case
+    return out
 
 
 def _first_below(hist, every, iters, level):
@@ -922,6 +970,10 @@ def main():
                          "repeat it)")
     ap.add_argument("--eps-scan", action="store_true",
                     help="only the FP64 accuracy-floor scan over N and eps (Sec. 3.1)")
+    ap.add_argument("--no-adaptive", action="store_true",
+                    help="skip the clustered forward on the uniform and adaptive trees")
+    ap.add_argument("--adaptive-only", action="store_true",
+                    help="only the clustered forward on the uniform and adaptive trees")
     ap.add_argument("--batched-only", action="store_true",
                     help="only the batched workloads (steps / warmup as given)")
     args = ap.parse_args()
@@ -935,6 +987,9 @@ def main():
         args.warmup = 3
     if args.batched_only:
         print(json.dumps({"batched": run_batched(args.steps, args.warmup, not args.no_tune)}))
+        return
+    if args.adaptive_only:
+        print(json.dumps({"adaptive_forward": run_adaptive(args.steps, args.warmup)}))
         return
     if args.impl == "reference":
         run_reference(args)

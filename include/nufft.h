@@ -71,6 +71,9 @@ typedef enum {
 #define NUFFT_IO_C64 0x1u        /* caller data are complex64 instead of complex128 */
 #define NUFFT_WANT_INVERSE 0x2u  /* precompute C_k, D_j (Eq. p8) for exec_inv (M == N) */
 #define NUFFT_NO_GRAPH 0x4u      /* launch exec kernels one by one (no CUDA graph replay) */
+#define NUFFT_ADAPTIVE 0x8u      /* forward: leaves holding more targets than the mean
+                                    are refined (non-uniform tree depth, see
+                                    nufft_adaptive_depths); one signal (batch 1) */
 
 /* Opaque plan: the "data structure" of the paper (Sec. 3.3): the binned point
  * set, F_j, optionally C_k / D_j, the expansion workspace and the FMM
@@ -134,6 +137,29 @@ int nufft_choose_params(int64_t N, int64_t M, double eps, int prec,
  * -1 for N outside [8, 2^26].  Host only. */
 double nufft_eps_threshold(int64_t N);
 
+/* Adaptive tree depth (plan flag NUFFT_ADAPTIVE).  The tree of Sec. 2.1 is
+ * uniform: every target meets the 3 s grid points of its leaf and the two
+ * adjacent ones (s = N' >> lmax), so the near field (Sec. 2.4, 3 N M / 2^lmax
+ * pairs) costs the same per target however the points cluster, while a
+ * leaf in a cluster holds many more targets than grid points.  A refined
+ * leaf b takes d_b more levels: its targets' local expansions come from the
+ * downward pass continued to level lmax + d_b (L2L of the parent plus the
+ * M2L of the interaction list, whose multipoles are formed from the grid
+ * samples: the sources are the uniform grid at every level) and their near
+ * field from the 3 boxes of that level (3 s / 2^d_b grid points).
+ * The depth of leaf b from its target count n_b and the mean nbar = M / B:
+ *   d_b = the largest d <= dmax with n_b >= 2^d nbar,
+ *   dmax = min(3, log2(s) - 3) (a refined box keeps at least 8 grid points).
+ * in: leaf_start[B + 1] (host; n_b = leaf_start[b + 1] - leaf_start[b]), B a
+ * power of two, M = leaf_start[B], s a power of two.  out: depth[B] (host).
+ * Returns max_b d_b, or -1 for invalid arguments.  Host only. */
+int nufft_adaptive_depths(const int32_t *leaf_start, int64_t B, int64_t M, int s, int *depth);
+
+/* Refinement of a plan created with NUFFT_ADAPTIVE: *levels = max_b d_b (0:
+ * the uniform tree, e.g. for uniform points, or a plan without the flag);
+ * count[d] = the targets whose leaf has d_b = d, d = 0..3.  Host only. */
+int nufft_plan_adaptive(nufft_plan pl, int *levels, int64_t count[4]);
+
 /* ---------------------------------------------------------------- autotuner */
 
 /* Exec calls an autotuning run times together (bit mask). */
@@ -193,7 +219,9 @@ int nufft_autotune(int64_t N, int64_t M, const double *y, double eps, int prec,
  *   eps              requested accuracy in [1e-15, 1e-1]
  *   prec             nufft_prec
  *   params  [host]   optional overrides (NULL = automatic)
- *   flags            NUFFT_IO_C64 | NUFFT_WANT_INVERSE | NUFFT_NO_GRAPH
+ *   flags            NUFFT_IO_C64 | NUFFT_WANT_INVERSE | NUFFT_NO_GRAPH |
+ *                    NUFFT_ADAPTIVE (forward of a one-signal plan; the
+ *                    adjoint and the inverse keep the uniform tree)
  * Exec calls replay a CUDA graph of their kernel sequence, captured on the
  * first call with the same operation and buffer pointers (up to 8 kept per
  * plan); they launch kernels one by one instead while profiling is enabled,
@@ -201,7 +229,8 @@ int nufft_autotune(int64_t N, int64_t M, const double *y, double eps, int prec,
  *   stream           cudaStream_t to run on (NULL = legacy default stream)
  * Synchronises the stream (it reads back validation flags).  Errors:
  * EINVAL (bad sizes / eps / y), EILLCOND (inverse requested with duplicate
- * points or coefficients outside the exponent range), ENOMEM, ECUDA. */
+ * points or coefficients outside the exponent range), ENOTSUP
+ * (NUFFT_ADAPTIVE with batch > 1), ENOMEM, ECUDA. */
 int nufft_plan_create(nufft_plan *out, int64_t N, int64_t M, const double *y,
                       double eps, int prec, const nufft_params *params,
                       unsigned flags, void *stream);

@@ -32,6 +32,7 @@ FP64, MIXED = 0, 1
 IO_C64 = 0x1
 WANT_INVERSE = 0x2
 NO_GRAPH = 0x4
+ADAPTIVE = 0x8
 
 # every symbol declared in include/nufft.h
 SYMBOLS = [
@@ -46,7 +47,8 @@ SYMBOLS = [
     "nufft_mlp_num_params", "nufft_mlp_set_params", "nufft_mlp_get_params", "nufft_mlp_infer",
     "nufft_mlp_grad", "nufft_mlp_train_step", "nufft_multi_create", "nufft_multi_exec_fwd",
     "nufft_multi_destroy", "nufft_autotune", "nufft_plan_dcf_weights", "nufft_diag_rcp",
-    "nufft_diag_pipe_rates", "nufft_eps_threshold",
+    "nufft_diag_pipe_rates", "nufft_eps_threshold", "nufft_adaptive_depths",
+    "nufft_plan_adaptive",
 ]
 
 
@@ -112,6 +114,8 @@ _lib.nufft_autotune.argtypes = [_I64, _I64, _P, ctypes.c_double, ctypes.c_int, c
                                 ctypes.POINTER(TuneTrial), ctypes.c_int,
                                 ctypes.POINTER(ctypes.c_int), _P]
 _lib.nufft_plan_inverse_coeffs.argtypes = [_P, _P, _P, ctypes.POINTER(ctypes.c_double)]
+_lib.nufft_adaptive_depths.argtypes = [_P, _I64, _I64, ctypes.c_int, _P]
+_lib.nufft_plan_adaptive.argtypes = [_P, ctypes.POINTER(ctypes.c_int), _P]
 for _n in ("nufft_plan_exec_fwd", "nufft_plan_exec_adj", "nufft_plan_exec_inv"):
     getattr(_lib, _n).argtypes = [_P, _P, _P]
 for _n in ("nufft_fwd", "nufft_fwd_noalloc"):
@@ -153,6 +157,20 @@ def eps_threshold(N: int) -> float:
     if v < 0:
         raise NufftError(EINVAL, "nufft_eps_threshold")
     return v
+
+
+def adaptive_depths(leaf_start, s: int):
+    """Extra tree levels of each leaf under the adaptive rule (host only):
+    (max depth, int32 array of B depths) from the B + 1 leaf starts (numpy)
+    and the grid points per leaf s."""
+    import numpy as np
+    st = np.ascontiguousarray(leaf_start, dtype=np.int32)
+    B = st.size - 1
+    dep = np.empty(max(B, 1), dtype=np.int32)
+    D = _lib.nufft_adaptive_depths(st.ctypes.data, B, int(st[-1]), int(s), dep.ctypes.data)
+    if D < 0:
+        raise NufftError(EINVAL, "nufft_adaptive_depths")
+    return D, dep[:B]
 
 
 def choose_params(N: int, M: int, eps: float, prec: int = FP64, lmax: int = 0, p: int = 0, q: int = 0):
@@ -208,11 +226,14 @@ class Plan:
     tc_near: batched forward near field on the tensor cores (MIXED, batch a
     multiple of 64; 0 = automatic, -1 = never).
     graphs: replay exec sequences as CUDA graphs (captured per buffer set).
+    adaptive: refine the leaves that hold more targets than the mean for the
+    forward transform (one signal; see :meth:`adaptive`).
     """
 
     def __init__(self, N: int, y, eps: float = 1e-12, prec: int = FP64, io: str = "c128",
                  inverse: bool = False, lmax: int = 0, p: int = 0, q: int = 0, batch: int = 1,
-                 tc_level: int = 0, tc_near: int = 0, graphs: bool = True, stream=None):
+                 tc_level: int = 0, tc_near: int = 0, graphs: bool = True, stream=None,
+                 adaptive: bool = False):
         torch = _torch()
         self.N = int(N)
         self.M = int(y.numel())
@@ -221,7 +242,7 @@ class Plan:
         self.cdtype = torch.complex64 if io == "c64" else torch.complex128
         self.batch = int(batch)
         flags = ((IO_C64 if io == "c64" else 0) | (WANT_INVERSE if inverse else 0) |
-                 (0 if graphs else NO_GRAPH))
+                 (0 if graphs else NO_GRAPH) | (ADAPTIVE if adaptive else 0))
         self._stream = stream
         h = _P()
         prm = Params(lmax, p, q, self.batch, tc_level, tc_near)
@@ -244,6 +265,15 @@ class Plan:
         _check(_lib.nufft_plan_params(self._h, ctypes.byref(prm)), "nufft_plan_params")
         return {"lmax": prm.lmax, "p": prm.p, "q": prm.q, "batch": prm.batch,
                 "tc_level": prm.tc_level, "tc_near": prm.tc_near}
+
+    def adaptive(self):
+        """(levels, counts): the largest extra depth of the adaptive tree (0:
+        uniform) and the number of targets refined by 0..3 levels."""
+        lv = ctypes.c_int()
+        cnt = (ctypes.c_int64 * 4)()
+        _check(_lib.nufft_plan_adaptive(self._h, ctypes.byref(lv), ctypes.cast(cnt, _P)),
+               "nufft_plan_adaptive")
+        return lv.value, [int(v) for v in cnt]
 
     def sync(self):
         """Wait for the plan's stream; raises NufftError(ETIMEOUT) if a bounded

@@ -312,6 +312,21 @@ struct nufft_plan_s {
   int side_ok = 1;               // 0: keep everything on `stream`
   void *hnear = nullptr;         // near-field sums of one signal (2 max(N, M) complex):
                                  //     forward [M], adjoint / inverse [N][2] (sum, self terms)
+  // adaptive tree (NUFFT_ADAPTIVE, forward): leaf b refined by d_b levels;
+  // class d = the targets of leaves with d_b = d, stored class after class
+  static constexpr int kAdMax = 3;
+  int ad_D = 0;                    // max d_b (0: uniform tree)
+  int64_t ad_off[kAdMax + 2] = {}; // class d: [ad_off[d], ad_off[d + 1]) of the ad_ arrays
+  int64_t ad_boff[kAdMax + 1] = {};// boxes of level L + d (d >= 1): ad_box[ad_boff[d-1], ad_boff[d])
+  int64_t ad_toff[kAdMax + 1] = {};// P2M table of level L + d: ad_p2m + ad_toff[d - 1] (s_d x p)
+  int32_t *ad_box = nullptr;       // box indices at their level
+  int32_t *ad_perm = nullptr;      // [M] original index, class-major order
+  void *ad_pos = nullptr;          // [M] packed positions (as srcpos)
+  double2 *ad_F = nullptr, *ad_E = nullptr;   // [M]
+  float2 *ad_Ff = nullptr, *ad_Ef = nullptr;  // [M] (mixed)
+  void *ad_p2m = nullptr;          // rho_o^m of the grid points of a box, per deep level (T)
+  void *ad_lexp = nullptr;         // locals in the lexp layout of levels 3..L + ad_D
+                                   //     (levels L + 1 .. L + ad_D written)
 };
 
 // Begin a side branch (slot 0, 1 or 2; slot 2 has a stream of its own): returns the stream to launch it on --

@@ -833,6 +833,63 @@ __global__ void __launch_bounds__(kDownThreads) k_down_fused(TreeDims d, int lt,
   for (int i = threadIdx.x; i < (p << depth); i += kDownThreads) dst[i] = fin[i];
 }
 
+// The downward pass continued below the leaf level L where the tree is
+// refined (adaptive depth, forward only): one warp per box B of level l > L
+// from the list `box`.  Its local expansion is the L2L of its parent's (level
+// l - 1: the plan's locals for l - 1 = L, else this pass's) plus the M2L of
+// the three boxes of its interaction list.  The sources are the grid at every
+// level, so the warp forms those boxes' multipoles itself from the grid
+// samples: M_m = sum_o f_{I s_l + o} rho_o^m over the s_l = N >> l points of
+// box I (rho_o = o / s_l - 1/2, the table `rp`, [s_l][p]), the P2M of Sec. 2.1
+// at level l.  lexp: the locals in the plan's layout of levels 3..l.
+constexpr int kDeepWarps = 8;
+template <class T>
+__global__ void __launch_bounds__(kDeepWarps * 32) k_down_deep(
+    TreeDims d, int l, int nbox, const int32_t* __restrict__ box, const T* __restrict__ op_m2l,
+    const T* __restrict__ op_l2l, const T* __restrict__ rp, const cplx<T>* __restrict__ f,
+    const cplx<T>* __restrict__ lpar_base, cplx<T>* __restrict__ lexp) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int p = d.p;
+  T* Tm = reinterpret_cast<T*>(smraw);
+  T* Tl = Tm + 4 * p * p;
+  cplx<T>* Mv = reinterpret_cast<cplx<T>*>(Tl + 2 * p * p);  // [kDeepWarps][3 p]
+  for (int i = threadIdx.x; i < 4 * p * p; i += blockDim.x) Tm[i] = op_m2l[i];
+  for (int i = threadIdx.x; i < 2 * p * p; i += blockDim.x) Tl[i] = op_l2l[i];
+  pdl_wait();
+  pdl_trigger();
+  __syncthreads();
+  const int w = (int)threadIdx.x >> 5, lane = (int)threadIdx.x & 31;
+  const int bi = blockIdx.x * kDeepWarps + w;
+  if (bi >= nbox) return;
+  const int64_t B = box[bi], nb = int64_t(1) << l;
+  const int sl = (int)(d.N >> l);
+  const int odd = (int)(B & 1);
+  cplx<T>* mv = Mv + w * 3 * p;
+  // multipoles of the interaction list (slot t: even box {-2, +2, +3}, odd {-3, -2, +2})
+  for (int e = lane; e < 3 * p; e += 32) {
+    const int t = e / p, m = e - t * p;
+    const int off = odd ? (t == 0 ? -3 : (t == 1 ? -2 : 2)) : (t == 0 ? -2 : (t == 1 ? 2 : 3));
+    const int64_t I = (B + off + nb) & (nb - 1);
+    const cplx<T>* fb = f + I * sl;
+    T ar = 0, ai = 0;
+    for (int o = 0; o < sl; ++o) {
+      const cplx<T> v = fb[o];
+      const T wgt = rp[o * p + m];
+      ar = fma(v.x, wgt, ar);
+      ai = fma(v.y, wgt, ai);
+    }
+    mv[e] = mk<T>(ar, ai);
+  }
+  __syncwarp();
+  const cplx<T>* lpar = lpar_base + (level_off(l - 1) - 4 + (B >> 1)) * p;
+  auto msrc = [&](int off) {
+    const int t = odd ? (off == -3 ? 0 : (off == -2 ? 1 : 2)) : (off == -2 ? 0 : (off == 2 ? 1 : 2));
+    return mv + t * p;
+  };
+  for (int n = lane; n < p; n += 32)
+    lexp[(level_off(l) - 4 + B) * p + n] = m2l_one<T>(Tm, Tl, p, n, odd, msrc, lpar, (T)0);
+}
+
 // expansion lengths with a compile-time instance of the one-launch tree
 // passes (FP32); other lengths take the run-time instance
 #define NUFFT_TREE_P_LIST(X) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(16)
@@ -2185,6 +2242,8 @@ int fmm_configure() {
       up_fused_attrs<T, 2, double2>(big) != cudaSuccess ||
       cudaFuncSetAttribute(k_down_sub<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            big) != cudaSuccess ||
+      cudaFuncSetAttribute(k_down_deep<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           big) != cudaSuccess ||
       cudaFuncSetAttribute(k_level2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            4 * 66 * 66 * (int)sizeof(double)) != cudaSuccess ||
       cudaFuncSetAttribute(k_p2m_nonuniform<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -2534,9 +2593,112 @@ int near_tc_forward(const TreeDims& d, int M, int batch, const int32_t* k0s, con
                     const float* dels_f, const float2* fgrid, float2* hnear, int* status,
                     cudaStream_t st);
 
+// the per-point data of the adaptive classes in the arithmetic type T
+template <class T> struct AdT;
+template <> struct AdT<double> {
+  static const double2* F(nufft_plan_s* pl) { return pl->ad_F; }
+  static const double2* E(nufft_plan_s* pl) { return pl->ad_E; }
+};
+template <> struct AdT<float> {
+  static const float2* F(nufft_plan_s* pl) { return pl->ad_Ff; }
+  static const float2* E(nufft_plan_s* pl) { return pl->ad_Ef; }
+};
+
+// The tree of depth class c: leaves at level L + c, s >> c grid points each.
+static TreeDims class_dims(const nufft_plan_s* pl, int c) {
+  TreeDims d = dims_of(pl);
+  d.L += c;
+  d.s >>= c;
+  d.inv_s = 1.0 / (double)d.s;
+  d.inv_s_f = (float)d.inv_s;
+  d.lstride = ((int64_t(2) << d.L) - 8) * d.p;
+  return d;
+}
+
+// Forward with the adaptive tree (one signal): the targets of depth class c
+// (stored class after class) are the uniform tree's targets at depth L + c.
+// Their near-field sums (grid samples only) run on side branch 2 beside the
+// tree passes, class after class; the main chain runs the uniform upward and
+// downward passes, then the deeper levels (k_down_deep, level by level); the
+// far parts of the classes follow the join.
+template <class T>
+static int fmm_forward_adaptive(nufft_plan_s* pl, void* g) {
+  const cplx<T>* f = (const cplx<T>*)pl->grid;
+  const bool c64 = (pl->flags & NUFFT_IO_C64) != 0;
+  const int D = pl->ad_D, p = pl->p;
+  const SrcPos<T>* pos = (const SrcPos<T>*)pl->ad_pos;
+  const cplx<T>* F = AdT<T>::F(pl);
+  const cplx<T>* E = AdT<T>::E(pl);
+  cplx<T>* hn = (cplx<T>*)pl->hnear;
+  const cplx<T>* l2 = PlanT<T>::lvl2(pl);
+  prof_begin(pl, NUFFT_STAGE_TARGETS);
+  cudaStream_t s2 = side_begin(pl, 2);
+  int nn = 0;
+  {
+    LowPriority lp;
+    for (int c = 0; c <= D; ++c) {
+      const int64_t o = pl->ad_off[c], mc = pl->ad_off[c + 1] - o;
+      if (mc == 0) continue;
+      const TreeDims dc = class_dims(pl, c);
+      const unsigned nb = near_grid(nblk(mc, kTgtThreads), false);
+      if (c64)
+        launch_pdl(k_targets_fwd<T, float2, 1>, dim3(nb, 1), kTgtThreads,
+                   NearCap<T, 1>::fwd_bytes, s2, dc, (int)mc, pos + o, pl->ad_perm + o, F + o,
+                   E + o, f, (const cplx<T>*)nullptr, l2, (const cplx<T>*)nullptr,
+                   (float2*)g, hn + o);
+      else
+        launch_pdl(k_targets_fwd<T, double2, 1>, dim3(nb, 1), kTgtThreads,
+                   NearCap<T, 1>::fwd_bytes, s2, dc, (int)mc, pos + o, pl->ad_perm + o, F + o,
+                   E + o, f, (const cplx<T>*)nullptr, l2, (const cplx<T>*)nullptr,
+                   (double2*)g, hn + o);
+      ++nn;
+    }
+  }
+  side_end(pl, 2, s2);
+  prof_end(pl, nn);
+  const FmmOps ops = cot_ops(pl);
+  int rc = fmm_upward_downward<T>(pl, ops, true, f, pl->lvl2,
+                                  sizeof(T) == 4 ? pl->lvl2f : nullptr);
+  if (rc) return rc;
+  prof_begin(pl, NUFFT_STAGE_M2L);
+  const size_t sm = (size_t)6 * p * p * sizeof(T) + (size_t)kDeepWarps * 3 * p * sizeof(cplx<T>);
+  cplx<T>* lad = (cplx<T>*)pl->ad_lexp;
+  for (int c = 1; c <= D; ++c) {
+    const int64_t b0 = pl->ad_boff[c - 1], nbox = pl->ad_boff[c] - b0;
+    const cplx<T>* lpar = c == 1 ? (const cplx<T>*)pl->lexp : lad;
+    launch_pdl(k_down_deep<T>, dim3(nblk(nbox, kDeepWarps)), kDeepWarps * 32, sm,
+               pl->stream, dims_of(pl), pl->L + c, (int)nbox, pl->ad_box + b0,
+               (const T*)ops.m2l, (const T*)ops.l2l, (const T*)pl->ad_p2m + pl->ad_toff[c - 1],
+               f, lpar, lad);
+  }
+  prof_end(pl, D);
+  side_join(pl, 2);
+  prof_begin(pl, NUFFT_STAGE_TARGETS);
+  int nf = 0;
+  for (int c = 0; c <= D; ++c) {
+    const int64_t o = pl->ad_off[c], mc = pl->ad_off[c + 1] - o;
+    if (mc == 0) continue;
+    const TreeDims dc = class_dims(pl, c);
+    const cplx<T>* lx = c == 0 ? (const cplx<T>*)pl->lexp : lad;
+    const unsigned nb = nblk(mc, kTgtThreads);
+    if (c64)
+      launch_far_fwd<T, float2>(p, nb, 0, pl->stream, dc, (int)mc, pos + o,
+                                (const int32_t*)pl->ad_perm + o, F + o, E + o, f, lx, l2,
+                                (const cplx<T>*)hn + o, (float2*)g);
+    else
+      launch_far_fwd<T, double2>(p, nb, 0, pl->stream, dc, (int)mc, pos + o,
+                                 (const int32_t*)pl->ad_perm + o, F + o, E + o, f, lx, l2,
+                                 (const cplx<T>*)hn + o, (double2*)g);
+    ++nf;
+  }
+  prof_end(pl, nf);
+  return cudaGetLastError() == cudaSuccess ? NUFFT_OK : NUFFT_ECUDA;
+}
+
 // forward: grid samples f (cplx<T>, in pl->grid, [batch][N]) -> g ([batch][M], original order)
 template <class T>
 int fmm_forward(nufft_plan_s* pl, void* g) {
+  if (pl->ad_D > 0 && pl->batch == 1 && pl->hnear) return fmm_forward_adaptive<T>(pl, g);
   const cplx<T>* f = (const cplx<T>*)pl->grid;
   const TreeDims d = dims_of(pl);
   const bool split = split_near(pl);

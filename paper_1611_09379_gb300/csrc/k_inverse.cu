@@ -213,7 +213,12 @@ __global__ void k_lambda(const double* __restrict__ lamD, int64_t M, double* __r
 constexpr double kExpLimit = 700.0;
 
 // Ctf (optional): FP32 copy for the mixed path, whose exponent limit elim
-// keeps C_k e^Lambda / N inside the FP32 range.
+// keeps C_k e^Lambda / N below the FP32 overflow threshold.  Below the FP32
+// range only the FP64 limit applies: a tiny C~_k (a point next to x_k: C~_k
+// carries sin((x_k - y_j)/2)) scales sums that are O(1), so its FP32 copy
+// losing digits or vanishing changes f_k by less than rounding, and the one
+// term it does not leave small, the self term of that point, comes from the
+// FP64-formed factor S_j.
 // phase_sep: the phase of C(x_k) is applied by the target kernels (Nc < N),
 // so only the sign of the sine product is kept here.
 __global__ void k_assemble_C(const double* __restrict__ lamC, const int32_t* __restrict__ nC,
@@ -226,7 +231,7 @@ __global__ void k_assemble_C(const double* __restrict__ lamC, const int32_t* __r
   double v = 0.0;
   if (l != -INFINITY) {
     double e = l + *Lam;
-    if (!(fabs(e) < elim)) atomicOr(status, kDevIllCond);
+    if (!(e < elim && e > -kExpLimit)) atomicOr(status, kDevIllCond);
     double sg = (((phase_sep ? 0 : k) + nC[k]) & 1) ? -1.0 : 1.0;
     v = sg * exp(e) / (double)N;  // with the 1/N of Eq. p1
   }

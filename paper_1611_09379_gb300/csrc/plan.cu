@@ -59,6 +59,7 @@ template <class T> int fmm_forward(nufft_plan_s* pl, void* g);
 template <class T> int fmm_to_grid(nufft_plan_s* pl, const void* g, int inverse);
 int inverse_precompute(nufft_plan_s* pl, void* tmp, size_t tmp_bytes);
 int fmm_pack_positions(nufft_plan_s* pl);
+int adaptive_setup(nufft_plan_s* pl);
 int fmm_up_counters(int prec, int pm, int L);
 size_t inverse_tmp_bytes(const nufft_plan_s* pl);
 
@@ -234,7 +235,9 @@ void free_plan(nufft_plan_s* pl) {
                   pl->Ff, pl->Ef, pl->lvl2f, pl->Dt, pl->Dtf, pl->Ct, pl->Ctf, pl->Sinv, pl->Sinvf, pl->selft, pl->srcpos, pl->Lambda, pl->mexp, pl->lexp,
                   pl->charge, pl->grid, pl->grid2, pl->grid3, pl->lvl2, pl->op_m2m, pl->op_m2l,
                   pl->op_l2l, pl->op_p2m, pl->op_reg, pl->fft_tw, pl->fft_tw_f, pl->status,
-                  pl->seg_overflow, pl->lsq_work, pl->op_tc, pl->upcnt, pl->hnear};
+                  pl->seg_overflow, pl->lsq_work, pl->op_tc, pl->upcnt, pl->hnear,
+                  pl->ad_box, pl->ad_perm, pl->ad_pos, pl->ad_F, pl->ad_E, pl->ad_Ff, pl->ad_Ef,
+                  pl->ad_p2m, pl->ad_lexp};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& gr : pl->graphs)
@@ -458,7 +461,9 @@ int nufft_plan_create(nufft_plan* out, int64_t N, int64_t M, const double* y, do
   if (params) prm = *params;
   int rc = nufft_choose_params(N, M, eps, prec, &prm);
   if (rc) return rc;
-  if (flags & ~(NUFFT_IO_C64 | NUFFT_WANT_INVERSE | NUFFT_NO_GRAPH)) return NUFFT_EINVAL;
+  if (flags & ~(NUFFT_IO_C64 | NUFFT_WANT_INVERSE | NUFFT_NO_GRAPH | NUFFT_ADAPTIVE))
+    return NUFFT_EINVAL;
+  if ((flags & NUFFT_ADAPTIVE) && prm.batch != 1) return NUFFT_ENOTSUP;
   if ((flags & NUFFT_WANT_INVERSE) && M != N) return NUFFT_EINVAL;
   const int64_t Nc = N;
   N = grid_of(Nc);
@@ -525,6 +530,7 @@ int nufft_plan_create(nufft_plan* out, int64_t N, int64_t M, const double* y, do
   if (cudaMalloc(&tmp, tb) != cudaSuccess) { free_plan(pl); return NUFFT_ENOMEM; }
   rc = setup_points(pl, y, tmp);
   if (!rc) rc = fmm_pack_positions(pl);
+  if (!rc && (flags & NUFFT_ADAPTIVE)) rc = adaptive_setup(pl);
   if (!rc && (flags & NUFFT_WANT_INVERSE)) rc = inverse_precompute(pl, tmp, tb);
   int hstat = 0;
   if (!rc) {

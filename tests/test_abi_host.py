@@ -182,3 +182,38 @@ def test_tc_near_choice(nf):
     assert nf.choose_params_full(1 << 18, 1 << 18, 1e-6, nf.MIXED, batch=64, tc_near=-1)["tc_near"] == -1
     with pytest.raises(nf.NufftError):
         nf.choose_params_full(1 << 18, 1 << 18, 1e-6, nf.MIXED, batch=64, tc_near=2)
+
+
+def test_adaptive_depths_rule(nf):
+    """The adaptive tree's depth rule (nufft_adaptive_depths): d_b is the
+    largest d <= min(3, log2 s - 3) with n_b >= 2^d * mean count; equal counts
+    refine nothing, the cap follows s, and bad arguments are rejected."""
+    import numpy as np
+
+    def starts(counts):
+        return np.concatenate([[0], np.cumsum(counts)]).astype(np.int32)
+
+    D, dep = nf.adaptive_depths(starts([64] * 16), 64)
+    assert D == 0 and not dep.any()
+    # mean 100 over 64 leaves: counts 199 / 200 / 399 / 400 / 799 / 800 / 1600
+    # straddle 2x, 4x and 8x the mean; the other 57 leaves share the rest
+    c = np.array([199, 200, 399, 400, 799, 800, 1600] + [0] * 57)
+    rest = 6400 - c.sum()
+    c[7:] = rest // 57
+    c[7] += rest - 57 * (rest // 57)
+    assert c.sum() == 6400 and c[7:].max() < 200
+    D, dep = nf.adaptive_depths(starts(c), 1024)
+    assert list(dep[:7]) == [0, 1, 1, 2, 2, 3, 3] and D == 3
+    # the cap: s = 32 allows 2 levels, s = 16 one, s = 8 none
+    assert nf.adaptive_depths(starts(c), 32)[1][5] == 2
+    assert nf.adaptive_depths(starts(c), 16)[0] == 1
+    assert nf.adaptive_depths(starts(c), 8)[0] == 0
+    # no targets: nothing refined
+    assert nf.adaptive_depths(starts([0] * 8), 64)[0] == 0
+    # invalid: B not a power of two, s not a power of two, decreasing starts
+    with pytest.raises(nf.NufftError):
+        nf.adaptive_depths(starts([1, 2, 3]), 64)
+    with pytest.raises(nf.NufftError):
+        nf.adaptive_depths(starts([1, 2, 3, 4]), 48)
+    with pytest.raises(nf.NufftError):
+        nf.adaptive_depths(np.array([0, 5, 3, 6, 10], dtype=np.int32), 64)

@@ -52,6 +52,16 @@ def points(kind: str, M: int, N: int | None = None, seed: int = 1234,
         return _wrap(centres[comp] + 0.05 * g.standard_normal(M))
     if kind == "contrast":
         return _contrast(g, M)
+    if kind == "multiscale":
+        # four Gaussian clusters of widths 0.004 .. 0.15 rad and a uniform
+        # background, a fifth of the points each: densities from the mean to
+        # about 30x it
+        widths = np.array([0.004, 0.02, 0.06, 0.15])
+        comp = g.integers(0, 5, M)
+        ctr = g.random(4) * TWO_PI
+        k = np.minimum(comp, 3)
+        y = np.where(comp < 4, ctr[k] + widths[k] * g.standard_normal(M), g.random(M) * TWO_PI)
+        return _wrap(y)
     raise ValueError(kind)
 
 
