@@ -553,7 +553,7 @@ def run_ours(args):
     if not args.no_large:
         out["large"] = run_large(tune_params=not args.no_tune)
     if not args.no_adaptive:
-        out["adaptive_forward"] = run_adaptive()
+        out["adaptive_tree"] = run_adaptive(tune_params=not args.no_tune)
     if not args.no_lsq:
         out["inufft_lsq"] = run_lsq(budget_s=args.lsq_seconds, full=args.lsq_full)
     print(json.dumps(out))
@@ -724,12 +724,14 @@ def run_large(steps: int = 5, warmup: int = 3, tune_params: bool = True):
             "accuracy": acc}
 
 
-def run_adaptive(steps: int = 10, warmup: int = 3):
-    """Forward NUFFT on clustered points, N = M = 2^20, complex64, mixed
-    eps = 1e-6: the uniform tree against the adaptive tree (NUFFT_ADAPTIVE,
-    leaves refined where they hold more targets than the mean), the same
-    parameters (Eq. 18.2 / 25), for the eight-cluster mixture and for
-    clusters of four widths over a uniform background."""
+def run_adaptive(steps: int = 10, warmup: int = 3, tune_params: bool = True):
+    """Forward and adjoint NUFFT on clustered points, N = M = 2^20,
+    complex64, mixed eps = 1e-6: the uniform tree against the adaptive tree
+    (NUFFT_ADAPTIVE, leaves refined where they hold more points than the
+    mean), both with the parameters the autotuner picks for the uniform tree
+    on these points, and the adaptive tree on a base one level coarser; for
+    the eight-cluster mixture and for clusters of four widths over a uniform
+    background."""
     import torch
 
     import paper_1611_09379_gb300 as nf
@@ -737,35 +739,58 @@ def run_adaptive(steps: int = 10, warmup: int = 3):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     N = M = 1 << 20
     c = workloads.coeffs(N, seed=61).astype(np.complex64)
-    cd = torch.from_numpy(c).cuda()
-    out = {"workload": "forward NUFFT, N=M=2^20, complex64, mixed eps=1e-6, clustered y",
-           "unit": "points/s", "cases": {}}
+    gin = workloads.samples(M, seed=64).astype(np.complex64)
+    cd, gd = torch.from_numpy(c).cuda(), torch.from_numpy(gin).cuda()
+    out = {"workload": "forward and adjoint NUFFT, N=M=2^20, complex64, mixed eps=1e-6, "
+                       "clustered y", "unit": "points/s", "cases": {}}
     for kind, seed in (("clustered", 62), ("multiscale", 63)):
         y = workloads.points(kind, M, seed=seed)
         yd = torch.from_numpy(y).cuda()
+        prm = {}
         case = {}
-        for name, ad in (("uniform_tree", False), ("adaptive_tree", True)):
-            plan = nf.Plan(N, yd, eps=1e-6, prec=nf.MIXED, io="c64", adaptive=ad)
+        if tune_params:
+            from paper_1611_09379_gb300 import tune
+            ent = tune.autotune(N, yd, 1e-6, prec=nf.MIXED, io="c64", ops="fwd+adj", reps=3,
+                                tag=kind)
+            prm = {k: ent["params"][k] for k in ("lmax", "p", "q", "tc_level", "tc_near")}
+            case["tuning_s"] = ent["seconds"]
+        variants = (("uniform_tree", False, 0), ("adaptive_tree", True, 0),
+                    ("adaptive_tree_coarser_base", True, -1))
+        for name, ad, dl in variants:
+            pv = dict(prm)
+            if dl and pv:
+                pv["lmax"] = pv["lmax"] + dl
+            elif dl:
+                continue
+            try:
+                plan = nf.Plan(N, yd, eps=1e-6, prec=nf.MIXED, io="c64", adaptive=ad, **pv)
+            except nf.NufftError as e:  # e.g. a leaf of the coarser base over the binning's cap
+                case[name] = {"refused": str(e), "params": pv}
+                continue
             g = torch.empty(M, dtype=torch.complex64, device="cuda")
-            ms = _timed(lambda: plan.forward(cd, out=g), flush, stream, steps, warmup)
+            a = torch.empty(N, dtype=torch.complex64, device="cuda")
+            fwd = _timed(lambda: plan.forward(cd, out=g), flush, stream, steps, warmup)
+            adj = _timed(lambda: plan.adjoint(gd, out=a), flush, stream, steps, warmup)
             plan.profile(True)
             _timed(lambda: plan.forward(cd, out=g), flush, stream, 3, 0)
             per = {k: round(v[0] / 3, 4) for k, v in plan.stats().items() if v[1]}
             plan.profile(False)
             lv, cnt = plan.adaptive()
-            r = {"ms": ms, "value": M / (ms / 1e3), "levels": lv, "class_counts": cnt,
-                 "stage_ms": per}
+            r = {"fwd_ms": fwd, "adj_ms": adj, "fwd_value": M / (fwd / 1e3),
+                 "adj_value": M / (adj / 1e3), "levels": lv, "class_counts": cnt,
+                 "fwd_stage_ms": per, "params": plan.params()}
             try:
                 import oracle
                 idx = workloads.sample_index(M, 64, seed=7)
+                kdx = workloads.sample_index(N, 64, seed=9)
                 r["fwd_rel_l2_sampled"] = oracle.rel_l2(
                     g.cpu().numpy()[idx], oracle.nudft_fwd(c.astype(complex), y, idx))
+                r["adj_rel_l2_sampled"] = oracle.rel_l2(
+                    a.cpu().numpy()[kdx], oracle.nudft_adj(gin.astype(complex), y, N, kdx))
             except Exception as e:
-                r["fwd_rel_l2_sampled"] = repr(e)
+                r["rel_l2_sampled"] = repr(e)
             case[name] = r
-            case["params"] = plan.params()
             del plan
-        case["speedup"] = case["uniform_tree"]["ms"] / case["adaptive_tree"]["ms"]
         out["cases"][kind] = case
     return out
 
@@ -971,9 +996,9 @@ def main():
     ap.add_argument("--eps-scan", action="store_true",
                     help="only the FP64 accuracy-floor scan over N and eps (Sec. 3.1)")
     ap.add_argument("--no-adaptive", action="store_true",
-                    help="skip the clustered forward on the uniform and adaptive trees")
+                    help="skip the clustered transforms on the uniform and adaptive trees")
     ap.add_argument("--adaptive-only", action="store_true",
-                    help="only the clustered forward on the uniform and adaptive trees")
+                    help="only the clustered transforms on the uniform and adaptive trees")
     ap.add_argument("--batched-only", action="store_true",
                     help="only the batched workloads (steps / warmup as given)")
     args = ap.parse_args()
@@ -989,7 +1014,8 @@ def main():
         print(json.dumps({"batched": run_batched(args.steps, args.warmup, not args.no_tune)}))
         return
     if args.adaptive_only:
-        print(json.dumps({"adaptive_forward": run_adaptive(args.steps, args.warmup)}))
+        print(json.dumps({"adaptive_tree": run_adaptive(args.steps, args.warmup,
+                                                        not args.no_tune)}))
         return
     if args.impl == "reference":
         run_reference(args)

@@ -71,8 +71,8 @@ typedef enum {
 #define NUFFT_IO_C64 0x1u        /* caller data are complex64 instead of complex128 */
 #define NUFFT_WANT_INVERSE 0x2u  /* precompute C_k, D_j (Eq. p8) for exec_inv (M == N) */
 #define NUFFT_NO_GRAPH 0x4u      /* launch exec kernels one by one (no CUDA graph replay) */
-#define NUFFT_ADAPTIVE 0x8u      /* forward: leaves holding more targets than the mean
-                                    are refined (non-uniform tree depth, see
+#define NUFFT_ADAPTIVE 0x8u      /* leaves holding more points than the mean are
+                                    refined (non-uniform tree depth, see
                                     nufft_adaptive_depths); one signal (batch 1) */
 
 /* Opaque plan: the "data structure" of the paper (Sec. 3.3): the binned point
@@ -146,7 +146,12 @@ double nufft_eps_threshold(int64_t N);
  * downward pass continued to level lmax + d_b (L2L of the parent plus the
  * M2L of the interaction list, whose multipoles are formed from the grid
  * samples: the sources are the uniform grid at every level) and their near
- * field from the 3 boxes of that level (3 s / 2^d_b grid points).
+ * field from the 3 boxes of that level (3 s / 2^d_b grid points).  The
+ * adjoint and the inverse take the same leaves' points as sources: near
+ * field from the 3 boxes of level lmax + d_b, and the grid boxes of the
+ * interaction lists of their boxes at levels lmax + 1 .. lmax + d_b through
+ * those boxes' multipoles (M2L into the grid boxes, evaluated at the grid
+ * points).
  * The depth of leaf b from its target count n_b and the mean nbar = M / B:
  *   d_b = the largest d <= dmax with n_b >= 2^d nbar,
  *   dmax = min(3, log2(s) - 3) (a refined box keeps at least 8 grid points).
@@ -157,7 +162,7 @@ int nufft_adaptive_depths(const int32_t *leaf_start, int64_t B, int64_t M, int s
 
 /* Refinement of a plan created with NUFFT_ADAPTIVE: *levels = max_b d_b (0:
  * the uniform tree, e.g. for uniform points, or a plan without the flag);
- * count[d] = the targets whose leaf has d_b = d, d = 0..3.  Host only. */
+ * count[d] = the points whose leaf has d_b = d, d = 0..3.  Host only. */
 int nufft_plan_adaptive(nufft_plan pl, int *levels, int64_t count[4]);
 
 /* ---------------------------------------------------------------- autotuner */
@@ -220,8 +225,8 @@ int nufft_autotune(int64_t N, int64_t M, const double *y, double eps, int prec,
  *   prec             nufft_prec
  *   params  [host]   optional overrides (NULL = automatic)
  *   flags            NUFFT_IO_C64 | NUFFT_WANT_INVERSE | NUFFT_NO_GRAPH |
- *                    NUFFT_ADAPTIVE (forward of a one-signal plan; the
- *                    adjoint and the inverse keep the uniform tree)
+ *                    NUFFT_ADAPTIVE (one-signal plans: forward, adjoint
+ *                    and inverse on the adaptive tree)
  * Exec calls replay a CUDA graph of their kernel sequence, captured on the
  * first call with the same operation and buffer pointers (up to 8 kept per
  * plan); they launch kernels one by one instead while profiling is enabled,

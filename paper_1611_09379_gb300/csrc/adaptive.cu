@@ -11,8 +11,16 @@
 // of the parent plus the M2L of the three boxes of the interaction list,
 // whose multipoles come from the grid samples), and the targets of each
 // depth class are evaluated by the uniform tree's target kernels with the
-// tree depth L + d.  This file chooses the depths (host) and lays out the
-// class-major copies of the target data the class launches read.
+// tree depth L + d.  The adjoint and the inverse (the same sums with the
+// roles of points and grid exchanged) use the same classes as sources:
+// class d, its points sorted by leaf of level L + d, is the uniform tree of
+// that depth for the near field; the pairs a refined leaf's sources no
+// longer meet directly (grid boxes of its interaction lists at levels L + 1
+// .. L + d) go through the multipoles of the deep boxes, M2L into those
+// grid boxes and their evaluation at the grid points.  This file chooses
+// the depths (host) and lays out the class-major copies of the point data
+// and the index lists the class launches read.
+#include <algorithm>
 #include <cstring>
 #include <vector>
 
@@ -25,13 +33,15 @@ namespace {
 // Class-major copies of the sorted target data: slot i takes sorted point
 // idx[i] (packed position of esz bytes, permutation, F and E in FP64 and,
 // when Ff is set, FP32).
+struct GatherPtrs {
+  const double2 *F, *E, *Dt, *S;
+  const float2 *Ff, *Ef, *Dtf, *Sf;
+  double2 *oF, *oE, *oDt, *oS;
+  float2 *oFf, *oEf, *oDtf, *oSf;
+};
 __global__ void k_ad_gather(int64_t M, const int32_t* __restrict__ idx, int esz,
                             const int32_t* __restrict__ perm, const void* __restrict__ pos,
-                            const double2* __restrict__ F, const double2* __restrict__ E,
-                            const float2* __restrict__ Ff, const float2* __restrict__ Ef,
-                            int32_t* __restrict__ operm, void* __restrict__ opos,
-                            double2* __restrict__ oF, double2* __restrict__ oE,
-                            float2* __restrict__ oFf, float2* __restrict__ oEf) {
+                            int32_t* __restrict__ operm, void* __restrict__ opos, GatherPtrs g) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= M) return;
   const int64_t j = idx[i];
@@ -40,11 +50,19 @@ __global__ void k_ad_gather(int64_t M, const int32_t* __restrict__ idx, int esz,
     reinterpret_cast<uint2*>(opos)[i] = reinterpret_cast<const uint2*>(pos)[j];
   else
     reinterpret_cast<uint4*>(opos)[i] = reinterpret_cast<const uint4*>(pos)[j];
-  oF[i] = F[j];
-  oE[i] = E[j];
-  if (oFf) {
-    oFf[i] = Ff[j];
-    oEf[i] = Ef[j];
+  g.oF[i] = g.F[j];
+  g.oE[i] = g.E[j];
+  if (g.oFf) {
+    g.oFf[i] = g.Ff[j];
+    g.oEf[i] = g.Ef[j];
+  }
+  if (g.oDt) {
+    g.oDt[i] = g.Dt[j];
+    g.oS[i] = g.S[j];
+  }
+  if (g.oDtf) {
+    g.oDtf[i] = g.Dtf[j];
+    g.oSf[i] = g.Sf[j];
   }
 }
 
@@ -66,45 +84,122 @@ int ad_alloc(X** p, size_t bytes) {
 using namespace nufft;
 
 int adaptive_setup(nufft_plan_s* pl) {
-  const int64_t B = pl->B, M = pl->M;
+  const int64_t B = pl->B, M = pl->M, N = pl->N;
+  const int L = pl->L, s = pl->s, p = pl->p;
+  cudaStream_t st = pl->stream;
   pl->ad_D = 0;
-  std::vector<int32_t> start((size_t)B + 1);
-  if (cudaMemcpyAsync(start.data(), pl->leaf_start, (B + 1) * 4, cudaMemcpyDeviceToHost,
-                      pl->stream) != cudaSuccess ||
-      cudaStreamSynchronize(pl->stream) != cudaSuccess)
+  std::vector<int32_t> start((size_t)B + 1), k0((size_t)M);
+  std::vector<double> dl((size_t)M);
+  if (cudaMemcpyAsync(start.data(), pl->leaf_start, (B + 1) * 4, cudaMemcpyDeviceToHost, st) !=
+          cudaSuccess ||
+      (M > 0 && (cudaMemcpyAsync(k0.data(), pl->k0, M * 4, cudaMemcpyDeviceToHost, st) !=
+                     cudaSuccess ||
+                 cudaMemcpyAsync(dl.data(), pl->delta, M * 8, cudaMemcpyDeviceToHost, st) !=
+                     cudaSuccess)) ||
+      cudaStreamSynchronize(st) != cudaSuccess)
     return NUFFT_ECUDA;
   // (an invalid point set leaves the tree uniform; plan creation reports it)
   if (start[0] != 0 || start[B] != M) return NUFFT_OK;
   for (int64_t b = 0; b < B; ++b)
     if (start[b + 1] < start[b]) return NUFFT_OK;
   std::vector<int> dep((size_t)B);
-  const int D = nufft_adaptive_depths(start.data(), B, M, pl->s, dep.data());
+  const int D = nufft_adaptive_depths(start.data(), B, M, s, dep.data());
   if (D <= 0) return NUFFT_OK;
-  // class-major order (within a class: the sorted order, leaf by leaf)
+  const int ls = ilog2i(s);
+  // the leaf of level L + c of sorted point j: its position's grid cell
+  // (k0 - 1 below the grid point, k0 from it on) >> log2(s_c)
+  auto deep_leaf = [&](int64_t j, int c) {
+    const int64_t fl = ((dl[j] < 0.0 ? k0[j] - 1 : k0[j]) + N) & (N - 1);
+    return fl >> (ls - c);
+  };
+  // class-major order; within class c: by leaf of level L + c (stable: by
+  // offset from the leaf's first grid point, then as sorted)
   std::vector<int32_t> idx((size_t)M);
+  std::vector<int32_t> sstart;
   int64_t n = 0;
   for (int c = 0; c <= D; ++c) {
     pl->ad_off[c] = n;
     for (int64_t b = 0; b < B; ++b)
-      if (dep[b] == c)
+      if (dep[b] == c) {
+        const int64_t a0 = n;
         for (int32_t j = start[b]; j < start[b + 1]; ++j) idx[n++] = j;
+        std::stable_sort(idx.begin() + a0, idx.begin() + n, [&](int32_t x, int32_t y) {
+          return deep_leaf(x, c) < deep_leaf(y, c);
+        });
+      }
+    // leaf starts of level L + c within the class
+    pl->ad_soff[c] = (int64_t)sstart.size();
+    const int64_t nb = B << c;
+    std::vector<int32_t> cnt((size_t)nb + 1, 0);
+    for (int64_t i = pl->ad_off[c]; i < n; ++i) ++cnt[(size_t)deep_leaf(idx[i], c) + 1];
+    for (int64_t b = 0; b < nb; ++b) cnt[(size_t)b + 1] += cnt[(size_t)b];
+    sstart.insert(sstart.end(), cnt.begin(), cnt.end());
   }
   pl->ad_off[D + 1] = n;
-  // boxes of the deeper levels: the descendants of the leaves refined that far
-  std::vector<int32_t> box;
+  // grid tiles (2 kTgtThreads points) within one leaf of level L + c of a class-c leaf
+  const int64_t tpts = 512, ntile = (N + tpts - 1) / tpts;
+  std::vector<int32_t> tiles;
   for (int c = 1; c <= D; ++c) {
+    pl->ad_tioff[c - 1] = (int64_t)tiles.size();
+    std::vector<char> mark((size_t)ntile, 0);
+    const int64_t sc = s >> c;
     for (int64_t b = 0; b < B; ++b)
-      if (dep[b] >= c)
-        for (int64_t k = 0; k < (int64_t(1) << c); ++k) box.push_back((int32_t)((b << c) + k));
-    pl->ad_boff[c] = (int64_t)box.size();
+      if (dep[b] == c)
+        for (int64_t t = (b * s - sc) >> 9; t <= ((b + 1) * s + sc - 1) >> 9; ++t)
+          mark[(size_t)((t + ntile) % ntile)] = 1;
+    for (int64_t t = 0; t < ntile; ++t)
+      if (mark[(size_t)t]) tiles.push_back((int32_t)t);
   }
+  pl->ad_tioff[D] = (int64_t)tiles.size();
+  // boxes of the deeper levels (the descendants of the leaves refined that
+  // far), their sources (class-major ranges), and the grid boxes whose
+  // interaction lists hold them, with the slots (even box {-2, +2, +3}, odd
+  // {-3, -2, +2}) as indices into the level's box list
+  std::vector<int32_t> box, srange, gbox, gil;
+  for (int c = 1; c <= D; ++c) {
+    const int64_t b0 = (int64_t)box.size(), nbl = B << c;
+    std::vector<int32_t> at((size_t)nbl, -1);
+    for (int64_t b = 0; b < B; ++b) {
+      const int db = dep[b];
+      if (db < c) continue;
+      const int32_t* cs = sstart.data() + pl->ad_soff[db];
+      for (int64_t k = 0; k < (int64_t(1) << c); ++k) {
+        const int64_t S = (b << c) + k;
+        at[(size_t)S] = (int32_t)((int64_t)box.size() - b0);
+        box.push_back((int32_t)S);
+        const int64_t f0 = S << (db - c), f1 = (S + 1) << (db - c);
+        srange.push_back((int32_t)(pl->ad_off[db] + cs[f0]));
+        srange.push_back((int32_t)(pl->ad_off[db] + cs[f1]));
+      }
+    }
+    pl->ad_boff[c] = (int64_t)box.size();
+    pl->ad_goff[c - 1] = (int64_t)gbox.size();
+    std::vector<char> seen((size_t)nbl, 0);
+    for (int64_t i = b0; i < (int64_t)box.size(); ++i) {
+      const int64_t S = box[(size_t)i];
+      const int odd = (int)(S & 1);
+      for (int t = 0; t < 3; ++t) {
+        const int off = odd ? (t == 0 ? -3 : (t == 1 ? -2 : 2)) : (t == 0 ? -2 : (t == 1 ? 2 : 3));
+        seen[(size_t)((S + off + nbl) & (nbl - 1))] = 1;
+      }
+    }
+    for (int64_t I = 0; I < nbl; ++I) {
+      if (!seen[(size_t)I]) continue;
+      gbox.push_back((int32_t)I);
+      const int odd = (int)(I & 1);
+      for (int t = 0; t < 3; ++t) {
+        const int off = odd ? (t == 0 ? -3 : (t == 1 ? -2 : 2)) : (t == 0 ? -2 : (t == 1 ? 2 : 3));
+        gil.push_back(at[(size_t)((I + off + nbl) & (nbl - 1))]);
+      }
+    }
+  }
+  pl->ad_goff[D] = (int64_t)gbox.size();
   // rho_o^m of the s >> c grid points of a box of level L + c: rho_o = o / s_c - 1/2
-  const int p = pl->p;
   const bool f32 = pl->prec != NUFFT_FP64;
   std::vector<double> tab;
   for (int c = 1; c <= D; ++c) {
     pl->ad_toff[c - 1] = (int64_t)tab.size();
-    const int sc = pl->s >> c;
+    const int sc = s >> c;
     for (int o = 0; o < sc; ++o) {
       long double rho = (long double)o / sc - 0.5L, pw = 1;
       for (int m = 0; m < p; ++m) {
@@ -115,31 +210,48 @@ int adaptive_setup(nufft_plan_s* pl) {
   }
   pl->ad_toff[D] = (int64_t)tab.size();
   const size_t csz = f32 ? sizeof(float2) : sizeof(double2);
-  const int64_t nl = (int64_t(2) << (pl->L + D)) - 8;
+  const int64_t nl = (int64_t(2) << (L + D)) - 8;
+  const bool inv = pl->Dt != nullptr && pl->Sinv != nullptr;
   int rc;
   if ((rc = ad_alloc(&pl->ad_box, box.size() * 4)) || (rc = ad_alloc(&pl->ad_perm, M * 4)) ||
       (rc = ad_alloc(&pl->ad_pos, M * csz)) || (rc = ad_alloc(&pl->ad_F, M * 16)) ||
       (rc = ad_alloc(&pl->ad_E, M * 16)) ||
       (rc = ad_alloc(&pl->ad_p2m, tab.size() * (f32 ? 4 : 8))) ||
-      (rc = ad_alloc(&pl->ad_lexp, nl * p * csz)))
+      (rc = ad_alloc(&pl->ad_lexp, nl * p * csz)) ||
+      (rc = ad_alloc(&pl->ad_start, sstart.size() * 4)) ||
+      (rc = ad_alloc(&pl->ad_tiles, tiles.size() * 4)) ||
+      (rc = ad_alloc(&pl->ad_srange, srange.size() * 4)) ||
+      (rc = ad_alloc(&pl->ad_gbox, gbox.size() * 4)) ||
+      (rc = ad_alloc(&pl->ad_gil, gil.size() * 4)) ||
+      (rc = ad_alloc(&pl->ad_mexp, box.size() * p * csz)))
     return rc;
   if (f32 && ((rc = ad_alloc(&pl->ad_Ff, M * 8)) || (rc = ad_alloc(&pl->ad_Ef, M * 8)))) return rc;
+  if (inv && ((rc = ad_alloc(&pl->ad_Dt, M * 16)) || (rc = ad_alloc(&pl->ad_S, M * 16))))
+    return rc;
+  if (inv && f32 && ((rc = ad_alloc(&pl->ad_Dtf, M * 8)) || (rc = ad_alloc(&pl->ad_Sf, M * 8))))
+    return rc;
   std::vector<float> tabf;
   if (f32) tabf.assign(tab.begin(), tab.end());
   int32_t* didx = nullptr;
   if ((rc = ad_alloc(&didx, M * 4))) return rc;
-  cudaStream_t st = pl->stream;
-  bool ok = cudaMemcpyAsync(didx, idx.data(), M * 4, cudaMemcpyHostToDevice, st) == cudaSuccess &&
-            cudaMemcpyAsync(pl->ad_box, box.data(), box.size() * 4, cudaMemcpyHostToDevice, st) ==
-                cudaSuccess &&
-            (f32 ? cudaMemcpyAsync(pl->ad_p2m, tabf.data(), tabf.size() * 4,
-                                   cudaMemcpyHostToDevice, st)
-                 : cudaMemcpyAsync(pl->ad_p2m, tab.data(), tab.size() * 8,
-                                   cudaMemcpyHostToDevice, st)) == cudaSuccess;
+  auto up = [&](void* dst, const void* src, size_t bytes) {
+    return bytes == 0 || cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st) == cudaSuccess;
+  };
+  bool ok = up(didx, idx.data(), M * 4) && up(pl->ad_box, box.data(), box.size() * 4) &&
+            up(pl->ad_start, sstart.data(), sstart.size() * 4) &&
+            up(pl->ad_tiles, tiles.data(), tiles.size() * 4) &&
+            up(pl->ad_srange, srange.data(), srange.size() * 4) &&
+            up(pl->ad_gbox, gbox.data(), gbox.size() * 4) &&
+            up(pl->ad_gil, gil.data(), gil.size() * 4) &&
+            (f32 ? up(pl->ad_p2m, tabf.data(), tabf.size() * 4)
+                 : up(pl->ad_p2m, tab.data(), tab.size() * 8));
   if (ok) {
-    k_ad_gather<<<(unsigned)((M + 255) / 256), 256, 0, st>>>(
-        M, didx, (int)csz, pl->perm, pl->srcpos, pl->F, pl->E, pl->Ff, pl->Ef, pl->ad_perm,
-        pl->ad_pos, pl->ad_F, pl->ad_E, pl->ad_Ff, pl->ad_Ef);
+    GatherPtrs g{pl->F,     pl->E,     inv ? pl->Dt : nullptr,  inv ? pl->Sinv : nullptr,
+                 pl->Ff,    pl->Ef,    inv ? pl->Dtf : nullptr, inv ? pl->Sinvf : nullptr,
+                 pl->ad_F,  pl->ad_E,  pl->ad_Dt,               pl->ad_S,
+                 pl->ad_Ff, pl->ad_Ef, pl->ad_Dtf,              pl->ad_Sf};
+    k_ad_gather<<<(unsigned)((M + 255) / 256), 256, 0, st>>>(M, didx, (int)csz, pl->perm,
+                                                             pl->srcpos, pl->ad_perm, pl->ad_pos, g);
     // (the host vectors are read by the copies: wait before they go)
     ok = cudaGetLastError() == cudaSuccess && cudaStreamSynchronize(st) == cudaSuccess;
   }

@@ -327,6 +327,19 @@ struct nufft_plan_s {
   void *ad_p2m = nullptr;          // rho_o^m of the grid points of a box, per deep level (T)
   void *ad_lexp = nullptr;         // locals in the lexp layout of levels 3..L + ad_D
                                    //     (levels L + 1 .. L + ad_D written)
+  // adjoint / inverse on the same classes (sources): class d as the uniform
+  // tree of depth L + d (its points sorted by leaf of that level)
+  int32_t *ad_start = nullptr;     // class d: leaf starts of level L + d (within the class) at ad_soff[d]
+  int64_t ad_soff[kAdMax + 1] = {};
+  int32_t *ad_tiles = nullptr;     // class d >= 1: the grid tiles (2 kTgtThreads points) its sources reach
+  int64_t ad_tioff[kAdMax + 1] = {};
+  int32_t *ad_srange = nullptr;    // [ad_boff[D]][2] source range of each deep box (class-major indices)
+  int32_t *ad_gbox = nullptr;      // grid boxes of level L + d with a deep box in their interaction list
+  int32_t *ad_gil = nullptr;       //     [][3]: that list's slots as deep-box indices of the level (-1: none)
+  int64_t ad_goff[kAdMax + 1] = {};
+  void *ad_mexp = nullptr;         // [ad_boff[D]][p] multipoles of the deep boxes (T)
+  double2 *ad_Dt = nullptr, *ad_S = nullptr;   // [M] inverse coefficients / self-term factors (class order)
+  float2 *ad_Dtf = nullptr, *ad_Sf = nullptr;  // [M] (mixed)
 };
 
 // Begin a side branch (slot 0, 1 or 2; slot 2 has a stream of its own): returns the stream to launch it on --

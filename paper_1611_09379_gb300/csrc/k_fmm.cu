@@ -1538,6 +1538,118 @@ __global__ void k_self_terms(int M, int inverse, const int32_t* __restrict__ per
 }
 
 
+// Adaptive tree, adjoint / inverse: the multipoles of the deep boxes of
+// level l (one warp per box S of the list; its sources are the class-major
+// points [range[2i], range[2i + 1])): M_m = sum q rho^m, m < p, with
+// rho = (o + delta) / s_l - 1/2 and o = (k0 - S s_l) mod N, the charges formed
+// from the caller's samples as in the near-field staging (coef_i g_perm(i),
+// conj(coef_i) for the adjoint).  A chunk of 32 sources writes q rho^m for up
+// to 32 consecutive m into the warp's tile of shared memory, lanes then
+// reduce rows (the P2M of the uniform tree's leaves, on a range).
+template <class T>
+__global__ void __launch_bounds__(kDeepWarps * 32) k_deep_p2m(
+    TreeDims d, int l, int nbox, const int32_t* __restrict__ box,
+    const int32_t* __restrict__ range, const SrcPos<T>* __restrict__ pos, InlineSrc<T> isrc,
+    cplx<T>* __restrict__ mexp) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  pdl_wait();
+  pdl_trigger();
+  const int w = (int)threadIdx.x >> 5, lane = (int)threadIdx.x & 31;
+  const int bi = blockIdx.x * kDeepWarps + w;
+  if (bi >= nbox) return;
+  cplx<T>* tile = reinterpret_cast<cplx<T>*>(smraw) + w * 32 * kP2mPitch;
+  const int N = (int)d.N, p = d.p;
+  const int sl = (int)(d.N >> l);
+  const int bs = box[bi] * sl;
+  const int a = range[2 * bi], e = range[2 * bi + 1];
+  const T inv_s = (T)1 / (T)sl;
+  const SelfArgs& sa = isrc.a;
+  for (int mc = 0; mc < p; mc += 32) {
+    const int nm = p - mc < 32 ? p - mc : 32;
+    T accr = 0, acci = 0;
+    for (int c0 = a; c0 < e; c0 += 32) {
+      const int i = c0 + lane;
+      cplx<T> q = mk<T>(0, 0);
+      T rho = 0;
+      if (i < e) {
+        const SrcPos<T> ps = pos[i];
+        rho = fma((T)(((int)ps.k0 - bs) & (N - 1)) + ps.dl, inv_s, (T)-0.5);
+        cplx<T> c = isrc.coef[i];
+        if (!sa.inverse) c.y = -c.y;  // the adjoint's conj(F_i)
+        q = cmul(c, sample_in<T>(sa, sa.perm[i]));
+      }
+      T pw = 1;
+      for (int m = 0; m < mc; ++m) pw *= rho;
+      for (int m = 0; m < nm; ++m) {
+        tile[m * kP2mPitch + lane] = mk<T>(q.x * pw, q.y * pw);
+        pw *= rho;
+      }
+      __syncwarp();
+      const int nk = e - c0 < 32 ? e - c0 : 32;
+      if (lane < nm)
+        for (int k = 0; k < nk; ++k) {
+          const cplx<T> v = tile[lane * kP2mPitch + k];
+          accr += v.x;
+          acci += v.y;
+        }
+      __syncwarp();
+    }
+    if (lane < nm) mexp[(int64_t)bi * p + mc + lane] = mk<T>(accr, acci);
+  }
+}
+
+// Adaptive tree, adjoint / inverse: grid box I of level l (one warp per box
+// of the list `gbox`) receives the M2L of the deep boxes of its interaction
+// list (gil: their indices among the level's deep boxes, -1 for a box that
+// is not refined that far), and the local expansion is evaluated at its
+// s_l grid points and added to their near-field sums in the units the far
+// part reads them ((1/s_l) sum_n L_n u^n, u = o / s_l - 1/2): the pairs of
+// grid points and sources that the sources' deeper near field no longer
+// holds.  Levels run one launch after another, so the additions are ordered.
+template <class T>
+__global__ void __launch_bounds__(kDeepWarps * 32) k_deep_m2l_grid(
+    TreeDims d, int l, int ngbox, const int32_t* __restrict__ gbox,
+    const int32_t* __restrict__ gil, const T* __restrict__ op_m2l, const T* __restrict__ op_l2l,
+    const cplx<T>* __restrict__ mexp, cplx<T>* __restrict__ hout) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int p = d.p;
+  T* Tm = reinterpret_cast<T*>(smraw);
+  T* Tl = Tm + 4 * p * p;
+  cplx<T>* Lw = reinterpret_cast<cplx<T>*>(Tl + 2 * p * p);  // [kDeepWarps][p]
+  cplx<T>* Z = Lw + kDeepWarps * p;                            // [p] zeros
+  for (int i = threadIdx.x; i < 4 * p * p; i += blockDim.x) Tm[i] = op_m2l[i];
+  for (int i = threadIdx.x; i < 2 * p * p; i += blockDim.x) Tl[i] = op_l2l[i];
+  for (int i = threadIdx.x; i < p; i += blockDim.x) Z[i] = mk<T>(0, 0);
+  pdl_wait();
+  pdl_trigger();
+  __syncthreads();
+  const int w = (int)threadIdx.x >> 5, lane = (int)threadIdx.x & 31;
+  const int gi = blockIdx.x * kDeepWarps + w;
+  if (gi >= ngbox) return;
+  const int64_t I = gbox[gi];
+  const int odd = (int)(I & 1);
+  const int s0 = gil[3 * gi], s1 = gil[3 * gi + 1], s2 = gil[3 * gi + 2];
+  auto msrc = [&](int off) {
+    const int t = odd ? (off == -3 ? 0 : (off == -2 ? 1 : 2)) : (off == -2 ? 0 : (off == 2 ? 1 : 2));
+    const int si = t == 0 ? s0 : (t == 1 ? s1 : s2);
+    return si >= 0 ? mexp + (int64_t)si * p : (const cplx<T>*)Z;
+  };
+  cplx<T>* lw = Lw + w * p;
+  for (int n = lane; n < p; n += 32) lw[n] = m2l_one<T>(Tm, Tl, p, n, odd, msrc, nullptr, (T)0);
+  __syncwarp();
+  const int sl = (int)(d.N >> l);
+  const T ts = (T)1 / (T)sl;
+  for (int o = lane; o < sl; o += 32) {
+    const T u = fma((T)o, ts, (T)-0.5);
+    const cplx<T> v = horner<T>(lw, p, u);
+    const int64_t k = I * sl + o;
+    cplx<T> h = hout[2 * k];
+    h.x = fma(v.x, ts, h.x);
+    h.y = fma(v.y, ts, h.y);
+    hout[2 * k] = h;
+  }
+}
+
 template <class T>
 __global__ void k_pack_positions(int M, const int32_t* __restrict__ k0s,
                                  const double* __restrict__ dels, SrcPos<T>* __restrict__ pos) {
@@ -1716,7 +1828,7 @@ __global__ void __launch_bounds__(kTgtThreads) k_targets_grid(
 // k_targets_grid.
 // MODE 0: the whole evaluation; 1: near field only (to hout), with the
 // charges and self terms formed while staging (isrc); 2: far part only (hin).
-template <class T, int MODE, int P = 0>
+template <class T, int MODE, int P = 0, int AD = 0>
 __device__ inline void grid2_tile(
     int tile, TreeDims d, int inverse, const int32_t* __restrict__ start,
     const SrcPos<T>* __restrict__ pos, const cplx<T>* __restrict__ charge,
@@ -1900,6 +2012,14 @@ __device__ inline void grid2_tile(
   nr0 = acc0.get();
   nr1 = acc1.get();
   if constexpr (MODE == 1) {  // near field only: the far part follows the tree passes
+    if constexpr (AD) {  // a deeper class of the adaptive tree: added to the earlier classes'
+      nr0 = cadd(nr0, hout[2 * (int64_t)k]);
+      self0 = cadd(self0, hout[2 * (int64_t)k + 1]);
+      if (k + 1 < N) {
+        nr1 = cadd(nr1, hout[2 * (int64_t)k + 2]);
+        self1 = cadd(self1, hout[2 * (int64_t)k + 3]);
+      }
+    }
     hout[2 * (int64_t)k] = nr0;
     hout[2 * (int64_t)k + 1] = self0;
     if (k + 1 < N) {
@@ -1952,6 +2072,20 @@ __global__ void __launch_bounds__(kTgtThreads, (sizeof(T) == 4 && MODE == 0) ? 5
     grid2_tile<T, MODE, P>(tile, d, inverse, start, pos, charge, st, lexp, lvl2, Ct, out, hout, hin,
                         isrc);
   }
+}
+
+// The near-field sums of one depth class of the adaptive tree (its sources
+// alone, the tree of depth d.L), added to those of the earlier classes, on
+// the grid tiles of the list `tiles` (one per CTA).
+template <class T>
+__global__ void __launch_bounds__(kTgtThreads, 4) k_targets_grid2_ad(
+    TreeDims d, int inverse, const int32_t* __restrict__ tiles, const int32_t* __restrict__ start,
+    const SrcPos<T>* __restrict__ pos, const cplx<T>* __restrict__ lexp,
+    const cplx<T>* __restrict__ lvl2, cplx<T>* __restrict__ hout, InlineSrc<T> isrc) {
+  pdl_wait();
+  pdl_trigger();
+  grid2_tile<T, 1, 0, 1>(tiles[blockIdx.x], d, inverse, start, pos, nullptr, nullptr, lexp, lvl2,
+                         nullptr, nullptr, hout, nullptr, isrc);
 }
 
 // Adjoint / inverse near field for one signal when each grid point meets
@@ -2243,6 +2377,10 @@ int fmm_configure() {
       cudaFuncSetAttribute(k_down_sub<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            big) != cudaSuccess ||
       cudaFuncSetAttribute(k_down_deep<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           big) != cudaSuccess ||
+      cudaFuncSetAttribute(k_deep_p2m<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           big) != cudaSuccess ||
+      cudaFuncSetAttribute(k_deep_m2l_grid<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            big) != cudaSuccess ||
       cudaFuncSetAttribute(k_level2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            4 * 66 * 66 * (int)sizeof(double)) != cudaSuccess ||
@@ -2811,10 +2949,117 @@ static void launch_self_terms(nufft_plan_s* pl, const TreeDims& d, int inverse, 
              inverse ? PlanT<T>::S(pl) : (const cplx<T>*)nullptr, charge, g, stt);
 }
 
+template <class T> struct AdInvT;
+template <> struct AdInvT<double> {
+  static const double2* D(nufft_plan_s* pl) { return pl->ad_Dt; }
+  static const double2* S(nufft_plan_s* pl) { return pl->ad_S; }
+};
+template <> struct AdInvT<float> {
+  static const float2* D(nufft_plan_s* pl) { return pl->ad_Dtf; }
+  static const float2* S(nufft_plan_s* pl) { return pl->ad_Sf; }
+};
+
+// Adjoint / inverse with the adaptive tree (one signal).  Side branch 2,
+// beside the uniform tree passes (which take every source, as before): the
+// near-field sums of class 0 on every grid tile, those of each deeper class
+// (the uniform tree of depth L + d over its own sources, charges and self
+// terms formed inline) added on the tiles it reaches, then level by level the
+// deep boxes' multipoles and their M2L into the grid boxes of their
+// interaction lists, added at those grid points.  After the join the far
+// part reads the sums as with the uniform tree.
+template <class T>
+static int fmm_to_grid_adaptive(nufft_plan_s* pl, const void* g, int inverse) {
+  cudaStream_t st = pl->stream;
+  const bool c64 = (pl->flags & NUFFT_IO_C64) != 0;
+  const int D = pl->ad_D, p = pl->p;
+  const TreeDims d = dims_of(pl);
+  const SrcPos<T>* pos = (const SrcPos<T>*)pl->ad_pos;
+  const cplx<T>* coef = inverse ? AdInvT<T>::D(pl) : AdT<T>::F(pl);
+  const cplx<T>* E = AdT<T>::E(pl);
+  const cplx<T>* S = inverse ? AdInvT<T>::S(pl) : (const cplx<T>*)nullptr;
+  if (inverse && !S) return NUFFT_EINVAL;
+  cplx<T>* hn = (cplx<T>*)pl->hnear;
+  const cplx<T>* l2 = PlanT<T>::lvl2(pl);
+  const cplx<T>* lad = (const cplx<T>*)pl->ad_lexp;
+  const FmmOps ops = cot_ops(pl);
+  auto isrc_of = [&](int64_t o) {
+    InlineSrc<T> is;
+    is.a.inverse = inverse;
+    is.a.perm = pl->ad_perm + o;
+    is.a.gin = g;
+    is.a.gin64 = c64 ? 0 : 1;
+    is.coef = coef + o;
+    is.E = E + o;
+    if (S) is.S = S + o;
+    return is;
+  };
+  prof_begin(pl, NUFFT_STAGE_TARGETS);
+  cudaStream_t s2 = side_begin(pl, 2);
+  int nn = 0;
+  {
+    LowPriority lp;
+    const int64_t o0 = pl->ad_off[0];
+    launch_pdl(k_targets_grid2<T, 1>, near_grid(nblk(pl->N, 2 * kTgtThreads), true), kTgtThreads,
+               NearCap<T, 1>::grid_bytes, s2, d, inverse,
+               (const int32_t*)pl->ad_start + pl->ad_soff[0], pos + o0, (const cplx<T>*)nullptr,
+               (const cplx<T>*)nullptr, (const cplx<T>*)pl->lexp, l2, PlanT<T>::Ct(pl),
+               (cplx<T>*)pl->grid, hn, (const cplx<T>*)nullptr, isrc_of(o0));
+    ++nn;
+    for (int c = 1; c <= D; ++c) {
+      const int64_t o = pl->ad_off[c], nt = pl->ad_tioff[c] - pl->ad_tioff[c - 1];
+      if (nt == 0) continue;
+      launch_pdl(k_targets_grid2_ad<T>, dim3((unsigned)nt), kTgtThreads,
+                 NearCap<T, 1>::grid_bytes, s2, class_dims(pl, c), inverse,
+                 (const int32_t*)pl->ad_tiles + pl->ad_tioff[c - 1],
+                 (const int32_t*)pl->ad_start + pl->ad_soff[c], pos + o, lad, l2, hn, isrc_of(o));
+      ++nn;
+    }
+    const size_t smp = (size_t)kDeepWarps * 32 * kP2mPitch * sizeof(cplx<T>);
+    const size_t sml = (size_t)6 * p * p * sizeof(T) + (size_t)(kDeepWarps + 1) * p * sizeof(cplx<T>);
+    for (int c = 1; c <= D; ++c) {
+      const int64_t b0 = pl->ad_boff[c - 1], nbox = pl->ad_boff[c] - b0;
+      const int64_t g0 = pl->ad_goff[c - 1], ng = pl->ad_goff[c] - g0;
+      cplx<T>* mx = (cplx<T>*)pl->ad_mexp + b0 * p;
+      launch_pdl(k_deep_p2m<T>, dim3(nblk(nbox, kDeepWarps)), kDeepWarps * 32, smp, s2, d,
+                 pl->L + c, (int)nbox, (const int32_t*)pl->ad_box + b0,
+                 (const int32_t*)pl->ad_srange + 2 * b0, pos, isrc_of(0), mx);
+      if (ng > 0)
+        launch_pdl(k_deep_m2l_grid<T>, dim3(nblk(ng, kDeepWarps)), kDeepWarps * 32, sml, s2, d,
+                   pl->L + c, (int)ng, (const int32_t*)pl->ad_gbox + g0,
+                   (const int32_t*)pl->ad_gil + 3 * g0, (const T*)ops.m2l, (const T*)ops.l2l,
+                   (const cplx<T>*)mx, hn);
+      nn += 2;
+    }
+  }
+  side_end(pl, 2, s2);
+  prof_end(pl, nn);
+  cplx<T>* charge = (cplx<T>*)pl->charge;
+  const cplx<T>* coef_u = inverse ? PlanT<T>::D(pl) : PlanT<T>::F(pl);
+  double2* lv2 = pl->lvl2;
+  float2* lv2f = sizeof(T) == 4 ? pl->lvl2f : nullptr;
+  int rc = c64 ? fmm_upward<T, float2>(pl, ops, false, charge, coef_u, (int)!inverse,
+                                       (const float2*)g, nullptr, lv2, lv2f)
+               : fmm_upward<T, double2>(pl, ops, false, charge, coef_u, (int)!inverse,
+                                        (const double2*)g, nullptr, lv2, lv2f);
+  if (rc) return rc;
+  rc = fmm_downward<T>(pl, ops);
+  if (rc) return rc;
+  side_join(pl, 2);
+  prof_begin(pl, NUFFT_STAGE_TARGETS);
+  launch_far_grid2<T>(pl->p, nblk(pl->N, 2 * kTgtThreads), (size_t)0, st, d, inverse,
+                      (const int32_t*)pl->leaf_start, (const SrcPos<T>*)pl->srcpos,
+                      (const cplx<T>*)charge, (const cplx<T>*)pl->selft,
+                      (const cplx<T>*)pl->lexp, l2, PlanT<T>::Ct(pl), (cplx<T>*)pl->grid,
+                      (cplx<T>*)nullptr, (const cplx<T>*)hn, InlineSrc<T>());
+  prof_end(pl, 1);
+  return cudaGetLastError() == cudaSuccess ? NUFFT_OK : NUFFT_ECUDA;
+}
+
 // adjoint / inverse: samples g ([batch][M], original order) -> values on the
 // grid (cplx<T>, in pl->grid, [batch][N])
 template <class T>
 int fmm_to_grid(nufft_plan_s* pl, const void* g, int inverse) {
+  if (pl->ad_D > 0 && pl->batch == 1 && pl->hnear) return fmm_to_grid_adaptive<T>(pl, g, inverse);
   cudaStream_t st = pl->stream;
   bool c64 = (pl->flags & NUFFT_IO_C64) != 0;
   const cplx<T>* coef = inverse ? PlanT<T>::D(pl) : PlanT<T>::F(pl);

@@ -237,7 +237,9 @@ void free_plan(nufft_plan_s* pl) {
                   pl->op_l2l, pl->op_p2m, pl->op_reg, pl->fft_tw, pl->fft_tw_f, pl->status,
                   pl->seg_overflow, pl->lsq_work, pl->op_tc, pl->upcnt, pl->hnear,
                   pl->ad_box, pl->ad_perm, pl->ad_pos, pl->ad_F, pl->ad_E, pl->ad_Ff, pl->ad_Ef,
-                  pl->ad_p2m, pl->ad_lexp};
+                  pl->ad_p2m, pl->ad_lexp, pl->ad_start, pl->ad_tiles, pl->ad_srange,
+                  pl->ad_gbox, pl->ad_gil, pl->ad_mexp, pl->ad_Dt, pl->ad_S, pl->ad_Dtf,
+                  pl->ad_Sf};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& gr : pl->graphs)
@@ -530,8 +532,8 @@ int nufft_plan_create(nufft_plan* out, int64_t N, int64_t M, const double* y, do
   if (cudaMalloc(&tmp, tb) != cudaSuccess) { free_plan(pl); return NUFFT_ENOMEM; }
   rc = setup_points(pl, y, tmp);
   if (!rc) rc = fmm_pack_positions(pl);
-  if (!rc && (flags & NUFFT_ADAPTIVE)) rc = adaptive_setup(pl);
   if (!rc && (flags & NUFFT_WANT_INVERSE)) rc = inverse_precompute(pl, tmp, tb);
+  if (!rc && (flags & NUFFT_ADAPTIVE)) rc = adaptive_setup(pl);
   int hstat = 0;
   if (!rc) {
     if (cudaMemcpyAsync(&hstat, pl->status, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||

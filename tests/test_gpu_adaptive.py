@@ -1,9 +1,11 @@
-"""Forward transform on the adaptive tree (plan flag NUFFT_ADAPTIVE): leaves
-holding more targets than the mean are refined by up to three levels, their
+"""Transforms on the adaptive tree (plan flag NUFFT_ADAPTIVE): leaves holding
+more points than the mean are refined by up to three levels.  Forward: their
 targets evaluated at the deeper level (local expansions from the downward
 pass continued with grid multipoles, near field over the 3 deeper boxes).
-Compared with the oracle's direct sums (Eq. p1) element by element, and with
-the uniform tree's result on the same points."""
+Adjoint / inverse: their sources as a deeper uniform tree for the near field,
+the pairs that leaves through the deep boxes' multipoles and M2L into the
+grid boxes.  Compared with the oracle's direct sums (Eq. p1, its adjoint,
+Eq. p6) element by element, and with the uniform tree's results."""
 import numpy as np
 import pytest
 
@@ -140,3 +142,75 @@ def test_adaptive_rejects_batches(nf):
     with pytest.raises(nf.NufftError) as e:
         nf.Plan(1024, _dev(y), eps=1e-6, prec=1, batch=2, adaptive=True)
     assert e.value.code == nf.ENOTSUP
+
+
+def _adj(nf, N, y, gs, prec, adaptive):
+    import torch
+    eps = 1e-12 if prec == 0 else 1e-6
+    plan = nf.Plan(N, _dev(y), eps=eps, prec=prec, adaptive=adaptive)
+    c = plan.adjoint(_dev(gs))
+    torch.cuda.synchronize()
+    return c.cpu().numpy(), plan
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_adaptive_adjoint_clustered_full(nf, orc, prec):
+    """Adjoint, N = M = 4096 on the eight-cluster mixture (two extra levels):
+    every coefficient against the direct sums; a replay gives the same bits."""
+    N = M = 4096
+    y = workloads.points("clustered", M, seed=41)
+    gs = workloads.samples(M, seed=55)
+    c, plan = _adj(nf, N, y, gs, prec, True)
+    assert plan.adaptive()[0] == 2
+    assert orc.rel_l2(c, orc.nudft_adj(gs, y, N)) < TOL[prec]
+    import torch
+    c2 = plan.adjoint(_dev(gs))
+    torch.cuda.synchronize()
+    assert np.array_equal(c2.cpu().numpy(), c)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_adaptive_adjoint_three_levels_sampled(nf, orc, prec):
+    """Adjoint, N = 2^16, M = 2^14 on clusters of four widths (every depth
+    class present): sampled coefficients against the direct sums, and the
+    uniform tree's result on the same points."""
+    N, M = 1 << 16, 1 << 14
+    y = workloads.points("multiscale", M, seed=45)
+    gs = workloads.samples(M, seed=56)
+    c, plan = _adj(nf, N, y, gs, prec, True)
+    lv, cnt = plan.adaptive()
+    assert lv == 3 and all(v > 0 for v in cnt), cnt
+    kdx = workloads.sample_index(N, 512, seed=8)
+    assert orc.rel_l2(c[kdx], orc.nudft_adj(gs, y, N, kdx)) < TOL[prec]
+    cu, _ = _adj(nf, N, y, gs, prec, False)
+    assert orc.rel_l2(c, cu) < 2 * TOL[prec]
+
+
+def _two_density(N):
+    """N points equispaced at two densities: 48 % of them on [0, 0.4 pi)."""
+    n1 = int(N * 0.48)
+    a = 0.4 * np.pi
+    return np.concatenate([(np.arange(n1) + 0.5) * a / n1,
+                           a + (np.arange(N - n1) + 0.5) * (2 * np.pi - a) / (N - n1)])
+
+
+@pytest.mark.parametrize("prec,N,kind", [(0, 128, "two"), (1, 128, "two"), (0, 512, "clustered")])
+def test_adaptive_inverse_matvec(nf, orc, prec, N, kind):
+    """Square inverse on point sets whose density varies enough to refine a
+    leaf while the Lagrange weights (Eq. p8) still fit the arithmetic: the
+    matrix-vector product f = L g (Eq. p6) against the oracle's, relative to
+    sum_j |L_kj| |g_j| (reading c16), as on the uniform tree."""
+    y = _two_density(N) if kind == "two" else workloads.points("clustered", N, seed=33)
+    g = workloads.samples(N, seed=34)
+    eps = 1e-12 if prec == 0 else 1e-6
+    plan = nf.Plan(N, _dev(y), eps=eps, prec=prec, inverse=True, adaptive=True)
+    assert plan.adaptive()[0] >= 1
+    import torch
+    c2 = plan.inverse(_dev(g))
+    torch.cuda.synchronize()
+    f = np.fft.ifft(c2.cpu().numpy()) * N
+    fref = orc.inverse_f(g, y, N)
+    aref = orc.inverse_absf(g, y, N)
+    sc = aref.max()
+    assert np.all(np.isfinite(f)) and sc < np.inf
+    assert np.linalg.norm((f - fref) / sc) / np.linalg.norm(aref / sc) < TOL[prec]
