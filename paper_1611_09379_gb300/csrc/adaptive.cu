@@ -155,7 +155,13 @@ int adaptive_setup(nufft_plan_s* pl) {
   // far), their sources (class-major ranges), and the grid boxes whose
   // interaction lists hold them, with the slots (even box {-2, +2, +3}, odd
   // {-3, -2, +2}) as indices into the level's box list
-  std::vector<int32_t> box, srange, gbox, gil;
+  std::vector<int32_t> box, srange, gbox, gil, rleaf;
+  for (int64_t b = 0; b < B; ++b)
+    if (dep[b] > 0) {
+      rleaf.push_back((int32_t)b);
+      rleaf.push_back(dep[b]);
+    }
+  pl->ad_nrleaf = (int64_t)rleaf.size() / 2;
   for (int c = 1; c <= D; ++c) {
     const int64_t b0 = (int64_t)box.size(), nbl = B << c;
     std::vector<int32_t> at((size_t)nbl, -1);
@@ -223,7 +229,9 @@ int adaptive_setup(nufft_plan_s* pl) {
       (rc = ad_alloc(&pl->ad_srange, srange.size() * 4)) ||
       (rc = ad_alloc(&pl->ad_gbox, gbox.size() * 4)) ||
       (rc = ad_alloc(&pl->ad_gil, gil.size() * 4)) ||
-      (rc = ad_alloc(&pl->ad_mexp, box.size() * p * csz)))
+      (rc = ad_alloc(&pl->ad_mexp, box.size() * p * csz)) ||
+      (rc = ad_alloc(&pl->ad_charge, M * csz)) || (rc = ad_alloc(&pl->ad_st, M * csz)) ||
+      (rc = ad_alloc(&pl->ad_rleaf, rleaf.size() * 4)))
     return rc;
   if (f32 && ((rc = ad_alloc(&pl->ad_Ff, M * 8)) || (rc = ad_alloc(&pl->ad_Ef, M * 8)))) return rc;
   if (inv && ((rc = ad_alloc(&pl->ad_Dt, M * 16)) || (rc = ad_alloc(&pl->ad_S, M * 16))))
@@ -243,6 +251,7 @@ int adaptive_setup(nufft_plan_s* pl) {
             up(pl->ad_srange, srange.data(), srange.size() * 4) &&
             up(pl->ad_gbox, gbox.data(), gbox.size() * 4) &&
             up(pl->ad_gil, gil.data(), gil.size() * 4) &&
+            up(pl->ad_rleaf, rleaf.data(), rleaf.size() * 4) &&
             (f32 ? up(pl->ad_p2m, tabf.data(), tabf.size() * 4)
                  : up(pl->ad_p2m, tab.data(), tab.size() * 8));
   if (ok) {

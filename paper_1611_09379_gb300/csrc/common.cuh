@@ -310,6 +310,7 @@ struct nufft_plan_s {
   cudaStream_t aux2 = nullptr;   // slot 2: the near field, beside the tree passes
   cudaEvent_t ev_fork[3] = {}, ev_join[3] = {};
   int side_ok = 1;               // 0: keep everything on `stream`
+  int max_leaf = 0;              // most points in one leaf (host copy, set at plan creation)
   void *hnear = nullptr;         // near-field sums of one signal (2 max(N, M) complex):
                                  //     forward [M], adjoint / inverse [N][2] (sum, self terms)
   // adaptive tree (NUFFT_ADAPTIVE, forward): leaf b refined by d_b levels;
@@ -320,6 +321,8 @@ struct nufft_plan_s {
   int64_t ad_boff[kAdMax + 1] = {};// boxes of level L + d (d >= 1): ad_box[ad_boff[d-1], ad_boff[d])
   int64_t ad_toff[kAdMax + 1] = {};// P2M table of level L + d: ad_p2m + ad_toff[d - 1] (s_d x p)
   int32_t *ad_box = nullptr;       // box indices at their level
+  int32_t *ad_rleaf = nullptr;     // [ad_nrleaf][2] the refined leaves and their depths d_b
+  int64_t ad_nrleaf = 0;
   int32_t *ad_perm = nullptr;      // [M] original index, class-major order
   void *ad_pos = nullptr;          // [M] packed positions (as srcpos)
   double2 *ad_F = nullptr, *ad_E = nullptr;   // [M]
@@ -338,6 +341,7 @@ struct nufft_plan_s {
   int32_t *ad_gil = nullptr;       //     [][3]: that list's slots as deep-box indices of the level (-1: none)
   int64_t ad_goff[kAdMax + 1] = {};
   void *ad_mexp = nullptr;         // [ad_boff[D]][p] multipoles of the deep boxes (T)
+  void *ad_charge = nullptr, *ad_st = nullptr; // [M] charges / self terms of the deeper classes (T, class order)
   double2 *ad_Dt = nullptr, *ad_S = nullptr;   // [M] inverse coefficients / self-term factors (class order)
   float2 *ad_Dtf = nullptr, *ad_Sf = nullptr;  // [M] (mixed)
 };

@@ -834,20 +834,27 @@ __global__ void __launch_bounds__(kDownThreads) k_down_fused(TreeDims d, int lt,
 }
 
 // The downward pass continued below the leaf level L where the tree is
-// refined (adaptive depth, forward only): one warp per box B of level l > L
-// from the list `box`.  Its local expansion is the L2L of its parent's (level
-// l - 1: the plan's locals for l - 1 = L, else this pass's) plus the M2L of
-// the three boxes of its interaction list.  The sources are the grid at every
-// level, so the warp forms those boxes' multipoles itself from the grid
-// samples: M_m = sum_o f_{I s_l + o} rho_o^m over the s_l = N >> l points of
-// box I (rho_o = o / s_l - 1/2, the table `rp`, [s_l][p]), the P2M of Sec. 2.1
-// at level l.  lexp: the locals in the plan's layout of levels 3..l.
+// refined (adaptive depth, forward only): one CTA per refined leaf b (the
+// list `rleaf`: leaf, depth d_b), which runs the levels L + 1 .. L + d_b of its
+// subtree one after the other, a warp per box.  The local expansion of box B
+// of level l is the L2L of its parent's (level l - 1: the plan's locals
+// `lmain` for l - 1 = L, else this pass's `lad`) plus the M2L of the three
+// boxes of its interaction list.  The sources are the grid at every level,
+// so the warp forms those boxes' multipoles itself from the grid samples:
+// M_m = sum_o f_{I s_l + o} rho_o^m over the s_l = N >> l points of box I
+// (rho_o = o / s_l - 1/2, the table rp[l - L - 1], [s_l][p]), the P2M of
+// Sec. 2.1 at level l.  A subtree needs nothing from another leaf's, so one
+// launch covers every level.  lad: the locals in the plan's layout of levels
+// 3..L + 3.
 constexpr int kDeepWarps = 8;
+template <class T> struct DeepTabs {
+  const T* rp[3];
+};
 template <class T>
 __global__ void __launch_bounds__(kDeepWarps * 32) k_down_deep(
-    TreeDims d, int l, int nbox, const int32_t* __restrict__ box, const T* __restrict__ op_m2l,
-    const T* __restrict__ op_l2l, const T* __restrict__ rp, const cplx<T>* __restrict__ f,
-    const cplx<T>* __restrict__ lpar_base, cplx<T>* __restrict__ lexp) {
+    TreeDims d, const int32_t* __restrict__ rleaf, DeepTabs<T> tabs,
+    const T* __restrict__ op_m2l, const T* __restrict__ op_l2l, const cplx<T>* __restrict__ f,
+    const cplx<T>* __restrict__ lmain, cplx<T>* __restrict__ lad) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int p = d.p;
   T* Tm = reinterpret_cast<T*>(smraw);
@@ -859,35 +866,45 @@ __global__ void __launch_bounds__(kDeepWarps * 32) k_down_deep(
   pdl_trigger();
   __syncthreads();
   const int w = (int)threadIdx.x >> 5, lane = (int)threadIdx.x & 31;
-  const int bi = blockIdx.x * kDeepWarps + w;
-  if (bi >= nbox) return;
-  const int64_t B = box[bi], nb = int64_t(1) << l;
-  const int sl = (int)(d.N >> l);
-  const int odd = (int)(B & 1);
+  const int64_t b = rleaf[2 * blockIdx.x];
+  const int db = rleaf[2 * blockIdx.x + 1];
   cplx<T>* mv = Mv + w * 3 * p;
-  // multipoles of the interaction list (slot t: even box {-2, +2, +3}, odd {-3, -2, +2})
-  for (int e = lane; e < 3 * p; e += 32) {
-    const int t = e / p, m = e - t * p;
-    const int off = odd ? (t == 0 ? -3 : (t == 1 ? -2 : 2)) : (t == 0 ? -2 : (t == 1 ? 2 : 3));
-    const int64_t I = (B + off + nb) & (nb - 1);
-    const cplx<T>* fb = f + I * sl;
-    T ar = 0, ai = 0;
-    for (int o = 0; o < sl; ++o) {
-      const cplx<T> v = fb[o];
-      const T wgt = rp[o * p + m];
-      ar = fma(v.x, wgt, ar);
-      ai = fma(v.y, wgt, ai);
+  for (int c = 1; c <= db; ++c) {
+    const int l = d.L + c;
+    const int64_t nb = int64_t(1) << l;
+    const int sl = (int)(d.N >> l);
+    const T* __restrict__ rp = tabs.rp[c - 1];
+    const cplx<T>* lpb = c == 1 ? lmain : lad;
+    for (int j = w; j < (1 << c); j += kDeepWarps) {
+      const int64_t B = (b << c) + j;
+      const int odd = (int)(B & 1);
+      // multipoles of the interaction list (slot t: even box {-2, +2, +3}, odd {-3, -2, +2})
+      for (int e = lane; e < 3 * p; e += 32) {
+        const int t = e / p, m = e - t * p;
+        const int off = odd ? (t == 0 ? -3 : (t == 1 ? -2 : 2)) : (t == 0 ? -2 : (t == 1 ? 2 : 3));
+        const int64_t I = (B + off + nb) & (nb - 1);
+        const cplx<T>* fb = f + I * sl;
+        T ar = 0, ai = 0;
+        for (int o = 0; o < sl; ++o) {
+          const cplx<T> v = fb[o];
+          const T wgt = rp[o * p + m];
+          ar = fma(v.x, wgt, ar);
+          ai = fma(v.y, wgt, ai);
+        }
+        mv[e] = mk<T>(ar, ai);
+      }
+      __syncwarp();
+      const cplx<T>* lpar = lpb + (level_off(l - 1) - 4 + (B >> 1)) * p;
+      auto msrc = [&](int off) {
+        const int t = odd ? (off == -3 ? 0 : (off == -2 ? 1 : 2)) : (off == -2 ? 0 : (off == 2 ? 1 : 2));
+        return mv + t * p;
+      };
+      for (int n = lane; n < p; n += 32)
+        lad[(level_off(l) - 4 + B) * p + n] = m2l_one<T>(Tm, Tl, p, n, odd, msrc, lpar, (T)0);
+      __syncwarp();  // (mv is rewritten by the warp's next box)
     }
-    mv[e] = mk<T>(ar, ai);
+    __syncthreads();  // level l complete: the parents of level l + 1
   }
-  __syncwarp();
-  const cplx<T>* lpar = lpar_base + (level_off(l - 1) - 4 + (B >> 1)) * p;
-  auto msrc = [&](int off) {
-    const int t = odd ? (off == -3 ? 0 : (off == -2 ? 1 : 2)) : (off == -2 ? 0 : (off == 2 ? 1 : 2));
-    return mv + t * p;
-  };
-  for (int n = lane; n < p; n += 32)
-    lexp[(level_off(l) - 4 + B) * p + n] = m2l_one<T>(Tm, Tl, p, n, odd, msrc, lpar, (T)0);
 }
 
 // expansion lengths with a compile-time instance of the one-launch tree
@@ -1196,6 +1213,19 @@ __device__ inline void near_window_ex2w(int n, int ex, NearAcc2f& acc, Term term
       for (int u = 0; u < 32; u += 2) term(i, u, std::false_type());
     }
     acc.fold();
+  }
+  // (3s = 48 or 24 terms, the deeper classes of the adaptive tree: a half
+  // chunk, voted the same way, before the tail)
+  if (i + 16 <= n) {
+    if (__any_sync(mask, ex - i >= 0 && ex - i < 16)) {
+#pragma unroll
+      for (int u = 0; u < 16; u += 2) term(i, u, std::true_type());
+    } else {
+#pragma unroll
+      for (int u = 0; u < 16; u += 2) term(i, u, std::false_type());
+    }
+    acc.fold();
+    i += 16;
   }
   if (i < n) {
     for (int u = 0; u < n - i; u += 2) term(i, u, std::true_type());
@@ -1828,7 +1858,7 @@ __global__ void __launch_bounds__(kTgtThreads) k_targets_grid(
 // k_targets_grid.
 // MODE 0: the whole evaluation; 1: near field only (to hout), with the
 // charges and self terms formed while staging (isrc); 2: far part only (hin).
-template <class T, int MODE, int P = 0, int AD = 0>
+template <class T, int MODE, int P = 0>
 __device__ inline void grid2_tile(
     int tile, TreeDims d, int inverse, const int32_t* __restrict__ start,
     const SrcPos<T>* __restrict__ pos, const cplx<T>* __restrict__ charge,
@@ -2012,14 +2042,6 @@ __device__ inline void grid2_tile(
   nr0 = acc0.get();
   nr1 = acc1.get();
   if constexpr (MODE == 1) {  // near field only: the far part follows the tree passes
-    if constexpr (AD) {  // a deeper class of the adaptive tree: added to the earlier classes'
-      nr0 = cadd(nr0, hout[2 * (int64_t)k]);
-      self0 = cadd(self0, hout[2 * (int64_t)k + 1]);
-      if (k + 1 < N) {
-        nr1 = cadd(nr1, hout[2 * (int64_t)k + 2]);
-        self1 = cadd(self1, hout[2 * (int64_t)k + 3]);
-      }
-    }
     hout[2 * (int64_t)k] = nr0;
     hout[2 * (int64_t)k + 1] = self0;
     if (k + 1 < N) {
@@ -2074,20 +2096,6 @@ __global__ void __launch_bounds__(kTgtThreads, (sizeof(T) == 4 && MODE == 0) ? 5
   }
 }
 
-// The near-field sums of one depth class of the adaptive tree (its sources
-// alone, the tree of depth d.L), added to those of the earlier classes, on
-// the grid tiles of the list `tiles` (one per CTA).
-template <class T>
-__global__ void __launch_bounds__(kTgtThreads, 4) k_targets_grid2_ad(
-    TreeDims d, int inverse, const int32_t* __restrict__ tiles, const int32_t* __restrict__ start,
-    const SrcPos<T>* __restrict__ pos, const cplx<T>* __restrict__ lexp,
-    const cplx<T>* __restrict__ lvl2, cplx<T>* __restrict__ hout, InlineSrc<T> isrc) {
-  pdl_wait();
-  pdl_trigger();
-  grid2_tile<T, 1, 0, 1>(tiles[blockIdx.x], d, inverse, start, pos, nullptr, nullptr, lexp, lvl2,
-                         nullptr, nullptr, hout, nullptr, isrc);
-}
-
 // Adjoint / inverse near field for one signal when each grid point meets
 // many sources (M >> N, or clustered sources): one warp per G consecutive
 // grid points of one leaf b (G divides s), so all G share the window of
@@ -2105,22 +2113,20 @@ __global__ void __launch_bounds__(kTgtThreads, 4) k_targets_grid2_ad(
 template <class T>
 __device__ inline T int_small_to_t(int v) { return int_to_t(v, T()); }
 
-template <class T, int G>
-__global__ void __launch_bounds__(kTgtThreads) k_targets_gridw(
-    TreeDims d, int inverse, const int32_t* __restrict__ start,
+// One warp's G grid points kb .. kb + G - 1 (AD: the near-field sums of a
+// deeper class of the adaptive tree, added to the earlier classes').
+template <class T, int G, int AD>
+__device__ inline void gridw_group(
+    int kb, const TreeDims& d, int inverse, const int32_t* __restrict__ start,
     const SrcPos<T>* __restrict__ pos, const cplx<T>* __restrict__ charge,
     const cplx<T>* __restrict__ st, const cplx<T>* __restrict__ lexp,
     const cplx<T>* __restrict__ lvl2, const T* __restrict__ Ct, cplx<T>* __restrict__ out,
     cplx<T>* __restrict__ hout) {
-  pdl_wait();
-  pdl_trigger();
   constexpr int LOGG = G == 8 ? 3 : (G == 4 ? 2 : 1);
   const int N = (int)d.N;
   const int s = d.s;
   const int B = 1 << d.L;
   const int lane = threadIdx.x & 31;
-  const int kb = (int)((blockIdx.x * (unsigned)kTgtThreads + threadIdx.x) >> 5) * G;
-  if (kb >= N) return;  // the same for the whole warp
   const int b = kb / s;
   NearAcc<T> acc[G];
   for (int nb = -1; nb <= 1; ++nb) {
@@ -2193,6 +2199,10 @@ __global__ void __launch_bounds__(kTgtThreads) k_targets_gridw(
     }
   }
   if (hout) {  // near field only (the two-point kernel's far part follows)
+    if constexpr (AD) {
+      v[0] = cadd(v[0], hout[2 * (int64_t)k]);
+      self = cadd(self, hout[2 * (int64_t)k + 1]);
+    }
     hout[2 * (int64_t)k] = v[0];
     hout[2 * (int64_t)k + 1] = self;
     return;
@@ -2217,6 +2227,40 @@ __global__ void __launch_bounds__(kTgtThreads) k_targets_gridw(
     if (d.nc) res = cmul(res, from_d2<T>(inv_phase(d, k)));
   }
   out[k] = cadd(res, self);
+}
+
+template <class T, int G>
+__global__ void __launch_bounds__(kTgtThreads) k_targets_gridw(
+    TreeDims d, int inverse, const int32_t* __restrict__ start,
+    const SrcPos<T>* __restrict__ pos, const cplx<T>* __restrict__ charge,
+    const cplx<T>* __restrict__ st, const cplx<T>* __restrict__ lexp,
+    const cplx<T>* __restrict__ lvl2, const T* __restrict__ Ct, cplx<T>* __restrict__ out,
+    cplx<T>* __restrict__ hout) {
+  pdl_wait();
+  pdl_trigger();
+  const int kb = (int)((blockIdx.x * (unsigned)kTgtThreads + threadIdx.x) >> 5) * G;
+  if (kb >= (int)d.N) return;  // the same for the whole warp
+  gridw_group<T, G, 0>(kb, d, inverse, start, pos, charge, st, lexp, lvl2, Ct, out, hout);
+}
+
+// The near-field sums of one deeper class of the adaptive tree (its sources
+// alone, the tree of depth d.L; charges and self terms in class order),
+// added to the earlier classes', on the grid tiles of 2 kTgtThreads points of
+// the list `tiles`: kGridwTileCtas CTAs of 8 warps x 8 grid points per tile.
+constexpr int kGridwTileCtas = 2 * kTgtThreads / (kTgtThreads / 32 * 8);
+template <class T>
+__global__ void __launch_bounds__(kTgtThreads) k_targets_gridw_ad(
+    TreeDims d, int inverse, const int32_t* __restrict__ tiles, const int32_t* __restrict__ start,
+    const SrcPos<T>* __restrict__ pos, const cplx<T>* __restrict__ charge,
+    const cplx<T>* __restrict__ st, cplx<T>* __restrict__ hout) {
+  pdl_wait();
+  pdl_trigger();
+  const int tile = tiles[blockIdx.x / kGridwTileCtas];
+  const int kb = tile * 2 * kTgtThreads +
+                 (int)(((blockIdx.x % kGridwTileCtas) * (unsigned)kTgtThreads + threadIdx.x) >> 5) * 8;
+  if (kb >= (int)d.N) return;  // the same for the whole warp
+  gridw_group<T, 8, 1>(kb, d, inverse, start, pos, charge, st, nullptr, nullptr, nullptr, nullptr,
+                       hout);
 }
 
 }  // namespace nufft
@@ -2801,15 +2845,13 @@ static int fmm_forward_adaptive(nufft_plan_s* pl, void* g) {
   prof_begin(pl, NUFFT_STAGE_M2L);
   const size_t sm = (size_t)6 * p * p * sizeof(T) + (size_t)kDeepWarps * 3 * p * sizeof(cplx<T>);
   cplx<T>* lad = (cplx<T>*)pl->ad_lexp;
-  for (int c = 1; c <= D; ++c) {
-    const int64_t b0 = pl->ad_boff[c - 1], nbox = pl->ad_boff[c] - b0;
-    const cplx<T>* lpar = c == 1 ? (const cplx<T>*)pl->lexp : lad;
-    launch_pdl(k_down_deep<T>, dim3(nblk(nbox, kDeepWarps)), kDeepWarps * 32, sm,
-               pl->stream, dims_of(pl), pl->L + c, (int)nbox, pl->ad_box + b0,
-               (const T*)ops.m2l, (const T*)ops.l2l, (const T*)pl->ad_p2m + pl->ad_toff[c - 1],
-               f, lpar, lad);
-  }
-  prof_end(pl, D);
+  DeepTabs<T> tabs;
+  for (int c = 1; c <= 3; ++c)
+    tabs.rp[c - 1] = (const T*)pl->ad_p2m + pl->ad_toff[c <= D ? c - 1 : 0];
+  launch_pdl(k_down_deep<T>, dim3((unsigned)pl->ad_nrleaf), kDeepWarps * 32, sm, pl->stream,
+             dims_of(pl), (const int32_t*)pl->ad_rleaf, tabs, (const T*)ops.m2l,
+             (const T*)ops.l2l, f, (const cplx<T>*)pl->lexp, lad);
+  prof_end(pl, 1);
   side_join(pl, 2);
   prof_begin(pl, NUFFT_STAGE_TARGETS);
   int nf = 0;
@@ -2899,7 +2941,8 @@ int fmm_forward(nufft_plan_s* pl, void* g) {
 static bool gridw_wanted(const nufft_plan_s* pl) {
   static const int force = std::getenv("NUFFT_NEAR_GRIDW") ? 1 : (std::getenv("NUFFT_NEAR_GRID2") ? -1 : 0);
   if (force) return force > 0;
-  return pl->N / (2 * kTgtThreads) < 2 * 152 || pl->M > 2 * pl->N;
+  return pl->N / (2 * kTgtThreads) < 2 * 152 || pl->M > 2 * pl->N ||
+         (pl->M > 0 && (int64_t)pl->max_leaf * pl->B >= 4 * pl->M);
 }
 
 // adjoint / inverse: samples g ([batch][M], original order) -> values on the
@@ -3005,13 +3048,35 @@ static int fmm_to_grid_adaptive(nufft_plan_s* pl, const void* g, int inverse) {
                (const cplx<T>*)nullptr, (const cplx<T>*)pl->lexp, l2, PlanT<T>::Ct(pl),
                (cplx<T>*)pl->grid, hn, (const cplx<T>*)nullptr, isrc_of(o0));
     ++nn;
+    // the deeper classes' charges and self terms in class order, then their
+    // near fields one warp per 8 grid points (a refined leaf's grid points
+    // each meet many sources)
+    const int64_t o1 = pl->ad_off[1], m1 = pl->M - o1;
+    cplx<T>* qa = (cplx<T>*)pl->ad_charge + o1;
+    cplx<T>* sa = (cplx<T>*)pl->ad_st + o1;
+    if (m1 > 0) {
+      if (c64) {
+        launch_pdl(k_charges<T, float2>, dim3(nblk(m1, 256), 1), 256, 0, s2, m1, pl->ad_perm + o1,
+                   coef + o1, (int)!inverse, (const float2*)g, qa);
+        launch_pdl(k_self_terms<T, float2>, dim3(nblk(m1, 256), 1), 256, 0, s2, (int)m1, inverse,
+                   pl->ad_perm + o1, E + o1, S ? S + o1 : S, (const cplx<T>*)qa,
+                   (const float2*)g, sa);
+      } else {
+        launch_pdl(k_charges<T, double2>, dim3(nblk(m1, 256), 1), 256, 0, s2, m1,
+                   pl->ad_perm + o1, coef + o1, (int)!inverse, (const double2*)g, qa);
+        launch_pdl(k_self_terms<T, double2>, dim3(nblk(m1, 256), 1), 256, 0, s2, (int)m1,
+                   inverse, pl->ad_perm + o1, E + o1, S ? S + o1 : S, (const cplx<T>*)qa,
+                   (const double2*)g, sa);
+      }
+      nn += 2;
+    }
     for (int c = 1; c <= D; ++c) {
       const int64_t o = pl->ad_off[c], nt = pl->ad_tioff[c] - pl->ad_tioff[c - 1];
       if (nt == 0) continue;
-      launch_pdl(k_targets_grid2_ad<T>, dim3((unsigned)nt), kTgtThreads,
-                 NearCap<T, 1>::grid_bytes, s2, class_dims(pl, c), inverse,
-                 (const int32_t*)pl->ad_tiles + pl->ad_tioff[c - 1],
-                 (const int32_t*)pl->ad_start + pl->ad_soff[c], pos + o, lad, l2, hn, isrc_of(o));
+      launch_pdl(k_targets_gridw_ad<T>, dim3((unsigned)(nt * kGridwTileCtas)), kTgtThreads, 0, s2,
+                 class_dims(pl, c), inverse, (const int32_t*)pl->ad_tiles + pl->ad_tioff[c - 1],
+                 (const int32_t*)pl->ad_start + pl->ad_soff[c], pos + o,
+                 (const cplx<T>*)pl->ad_charge + o, (const cplx<T>*)pl->ad_st + o, hn);
       ++nn;
     }
     const size_t smp = (size_t)kDeepWarps * 32 * kP2mPitch * sizeof(cplx<T>);

@@ -239,7 +239,7 @@ void free_plan(nufft_plan_s* pl) {
                   pl->ad_box, pl->ad_perm, pl->ad_pos, pl->ad_F, pl->ad_E, pl->ad_Ff, pl->ad_Ef,
                   pl->ad_p2m, pl->ad_lexp, pl->ad_start, pl->ad_tiles, pl->ad_srange,
                   pl->ad_gbox, pl->ad_gil, pl->ad_mexp, pl->ad_Dt, pl->ad_S, pl->ad_Dtf,
-                  pl->ad_Sf};
+                  pl->ad_Sf, pl->ad_charge, pl->ad_st, pl->ad_rleaf};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& gr : pl->graphs)
@@ -532,6 +532,15 @@ int nufft_plan_create(nufft_plan* out, int64_t N, int64_t M, const double* y, do
   if (cudaMalloc(&tmp, tb) != cudaSuccess) { free_plan(pl); return NUFFT_ENOMEM; }
   rc = setup_points(pl, y, tmp);
   if (!rc) rc = fmm_pack_positions(pl);
+  if (!rc) {  // the fullest leaf (the adjoint's near-field kernel choice)
+    std::vector<int32_t> ls((size_t)B + 1);
+    if (cudaMemcpyAsync(ls.data(), pl->leaf_start, (B + 1) * 4, cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      rc = NUFFT_ECUDA;
+    for (int64_t b = 0; !rc && b < B; ++b)
+      if (ls[b + 1] - ls[b] > pl->max_leaf) pl->max_leaf = ls[b + 1] - ls[b];
+  }
   if (!rc && (flags & NUFFT_WANT_INVERSE)) rc = inverse_precompute(pl, tmp, tb);
   if (!rc && (flags & NUFFT_ADAPTIVE)) rc = adaptive_setup(pl);
   int hstat = 0;
