@@ -771,14 +771,17 @@ def run_adaptive(steps: int = 10, warmup: int = 3, tune_params: bool = True):
             a = torch.empty(N, dtype=torch.complex64, device="cuda")
             fwd = _timed(lambda: plan.forward(cd, out=g), flush, stream, steps, warmup)
             adj = _timed(lambda: plan.adjoint(gd, out=a), flush, stream, steps, warmup)
-            plan.profile(True)
-            _timed(lambda: plan.forward(cd, out=g), flush, stream, 3, 0)
-            per = {k: round(v[0] / 3, 4) for k, v in plan.stats().items() if v[1]}
-            plan.profile(False)
+            per = {}
+            for op, fn in (("fwd", lambda: plan.forward(cd, out=g)),
+                           ("adj", lambda: plan.adjoint(gd, out=a))):
+                plan.profile(True)
+                _timed(fn, flush, stream, 3, 0)
+                per[op] = {k: round(v[0] / 3, 4) for k, v in plan.stats().items() if v[1]}
+                plan.profile(False)
             lv, cnt = plan.adaptive()
             r = {"fwd_ms": fwd, "adj_ms": adj, "fwd_value": M / (fwd / 1e3),
                  "adj_value": M / (adj / 1e3), "levels": lv, "class_counts": cnt,
-                 "fwd_stage_ms": per, "params": plan.params()}
+                 "fwd_stage_ms": per["fwd"], "adj_stage_ms": per["adj"], "params": plan.params()}
             try:
                 import oracle
                 idx = workloads.sample_index(M, 64, seed=7)
