@@ -884,14 +884,18 @@ __global__ void __launch_bounds__(kDeepWarps * 32) k_down_deep(
         const int off = odd ? (t == 0 ? -3 : (t == 1 ? -2 : 2)) : (t == 0 ? -2 : (t == 1 ? 2 : 3));
         const int64_t I = (B + off + nb) & (nb - 1);
         const cplx<T>* fb = f + I * sl;
-        T ar = 0, ai = 0;
-        for (int o = 0; o < sl; ++o) {
-          const cplx<T> v = fb[o];
-          const T wgt = rp[o * p + m];
-          ar = fma(v.x, wgt, ar);
-          ai = fma(v.y, wgt, ai);
+        // (two partial sums, the loads of several steps in flight: s_l >= 8, even)
+        T ar = 0, ai = 0, br = 0, bi = 0;
+#pragma unroll 4
+        for (int o = 0; o < sl; o += 2) {
+          const cplx<T> v0 = fb[o], v1 = fb[o + 1];
+          const T w0 = rp[o * p + m], w1 = rp[(o + 1) * p + m];
+          ar = fma(v0.x, w0, ar);
+          ai = fma(v0.y, w0, ai);
+          br = fma(v1.x, w1, br);
+          bi = fma(v1.y, w1, bi);
         }
-        mv[e] = mk<T>(ar, ai);
+        mv[e] = mk<T>(ar + br, ai + bi);
       }
       __syncwarp();
       const cplx<T>* lpar = lpb + (level_off(l - 1) - 4 + (B >> 1)) * p;
