@@ -311,6 +311,13 @@ struct nufft_plan_s {
   cudaEvent_t ev_fork[3] = {}, ev_join[3] = {};
   int side_ok = 1;               // 0: keep everything on `stream`
   int max_leaf = 0;              // most points in one leaf (host copy, set at plan creation)
+  // chunked P2M of clustered sources (a leaf with >= 4x the mean count):
+  // chunk i = (leaf, first, end) of at most 256 sources; leaf b's chunks are
+  // p2m_cfirst[b] .. p2m_cfirst[b + 1] - 1; their moments in p2m_part
+  int32_t *p2m_chunk = nullptr;  // [p2m_nchunk][3]
+  int32_t *p2m_cfirst = nullptr; // [B + 1]
+  int64_t p2m_nchunk = 0;
+  void *p2m_part = nullptr;      // [batch][p2m_nchunk][pm] complex (T)
   void *hnear = nullptr;         // near-field sums of one signal (2 max(N, M) complex):
                                  //     forward [M], adjoint / inverse [N][2] (sum, self terms)
   // adaptive tree (NUFFT_ADAPTIVE, forward): leaf b refined by d_b levels;

@@ -127,12 +127,12 @@ size_t p2m_smem(int pm) {
 // subtraction (no division).  qget(i, first) returns the charge of sorted
 // source i (first: in the first pass over the moments); out(m, v) stores
 // moment m.
+// The same over the sources [a, e) of leaf b (a part of the leaf: the
+// moments of those sources alone).
 template <class T, int PM = 0, class QGet, class Out>
-__device__ inline void p2m_leaf_warp(const TreeDims& d, int64_t b, int lane, cplx<T>* tile,
-                                     const int32_t* __restrict__ start,
-                                     const int32_t* __restrict__ k0,
-                                     const T* __restrict__ delta_t, QGet qget, Out out) {
-  const int32_t a = start[b], e = start[b + 1];
+__device__ inline void p2m_range_warp(const TreeDims& d, int64_t b, int32_t a, int32_t e,
+                                      int lane, cplx<T>* tile, const int32_t* __restrict__ k0,
+                                      const T* __restrict__ delta_t, QGet qget, Out out) {
   const int N = (int)d.N;
   const int bs = (int)b * d.s;
   const T inv_s = (T)1 / (T)d.s;
@@ -181,6 +181,65 @@ __device__ inline void p2m_leaf_warp(const TreeDims& d, int64_t b, int lane, cpl
     }
     if (lane < nm) out(mc + lane, mk<T>(accr, acci));
   }
+}
+
+template <class T, int PM = 0, class QGet, class Out>
+__device__ inline void p2m_leaf_warp(const TreeDims& d, int64_t b, int lane, cplx<T>* tile,
+                                     const int32_t* __restrict__ start,
+                                     const int32_t* __restrict__ k0,
+                                     const T* __restrict__ delta_t, QGet qget, Out out) {
+  p2m_range_warp<T, PM>(d, b, start[b], start[b + 1], lane, tile, k0, delta_t, qget, out);
+}
+
+// P2M for clustered sources, where one warp per leaf would leave the warps of
+// the dense leaves with nearly all the work: one warp per chunk of at most
+// kP2mChunkSrc sources of one leaf (chunk i: leaf, first, end), its moments
+// to part[i]; k_p2m_chunk_sum then adds each leaf's chunks in chunk order,
+// so the result does not depend on the schedule.
+constexpr int kP2mChunkSrc = 256;
+template <class T>
+__global__ void __launch_bounds__(128) k_p2m_chunks(TreeDims d, int nchunk,
+                                                    const int32_t* __restrict__ chunk,
+                                                    const int32_t* __restrict__ k0,
+                                                    const T* __restrict__ delta_t,
+                                                    const cplx<T>* __restrict__ charge,
+                                                    cplx<T>* __restrict__ part) {
+  pdl_wait();
+  pdl_trigger();
+  constexpr int WPB = P2mWarps<T>::value;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int rows = d.pm < 32 ? d.pm : 32;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  cplx<T>* tile = reinterpret_cast<cplx<T>*>(smraw) + warp * rows * kP2mPitch;
+  const int i = blockIdx.x * WPB + warp;
+  if (i >= nchunk) return;
+  charge += blockIdx.y * d.M_;
+  part += ((int64_t)blockIdx.y * nchunk + i) * d.pm;
+  p2m_range_warp<T>(
+      d, chunk[3 * i], chunk[3 * i + 1], chunk[3 * i + 2], lane, tile, k0, delta_t,
+      [&](int j, bool) { return charge[j]; }, [&](int m, cplx<T> v) { part[m] = v; });
+}
+
+// mleaf[b][m] = sum of the moments of leaf b's chunks cfirst[b] .. cfirst[b + 1] - 1
+template <class T>
+__global__ void k_p2m_chunk_sum(TreeDims d, int nchunk, const int32_t* __restrict__ cfirst,
+                                const cplx<T>* __restrict__ part, cplx<T>* __restrict__ mleaf) {
+  pdl_wait();
+  pdl_trigger();
+  const int64_t B = int64_t(1) << d.L;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= B * d.pm) return;
+  const int64_t b = t / d.pm;
+  const int m = (int)(t - b * d.pm);
+  part += (int64_t)blockIdx.y * nchunk * d.pm;
+  mleaf += blockIdx.y * d.mstride;
+  T ar = 0, ai = 0;
+  for (int c = cfirst[b]; c < cfirst[b + 1]; ++c) {
+    const cplx<T> v = part[(int64_t)c * d.pm + m];
+    ar += v.x;
+    ai += v.y;
+  }
+  mleaf[b * d.pm + m] = mk<T>(ar, ai);
 }
 
 template <class T>
@@ -2432,6 +2491,8 @@ int fmm_configure() {
                            big) != cudaSuccess ||
       cudaFuncSetAttribute(k_level2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            4 * 66 * 66 * (int)sizeof(double)) != cudaSuccess ||
+      cudaFuncSetAttribute(k_p2m_chunks<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)p2m_smem<T>(32)) != cudaSuccess ||
       cudaFuncSetAttribute(k_p2m_nonuniform<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)p2m_smem<T>(32)) != cudaSuccess)
     return NUFFT_ECUDA;
@@ -2502,9 +2563,13 @@ int fmm_upward(nufft_plan_s* pl, const FmmOps& ops, bool uniform_sources, const 
                        ? up_fused_stages<T>(pm, L, &sg) : -1;
   const bool fused = ncnt >= 0 && ncnt <= pl->upcnt_n;
   int src = 0;
+  // (clustered sources: the chunked P2M before the pass instead of one warp
+  // per leaf inside it)
+  const bool chunked = !uniform_sources && pl->p2m_part != nullptr && !ops.leaf_shift;
   if (fused) {
     if (uniform_sources && up_fused_smem<T>(pm, sg, 1, pl->s) <= kSmemBudget) src = 1;
-    if (!uniform_sources && up_fused_smem<T>(pm, sg, 2, pl->s) <= kSmemBudget) src = 2;
+    if (!uniform_sources && !chunked && up_fused_smem<T>(pm, sg, 2, pl->s) <= kSmemBudget)
+      src = 2;
   }
   if (gin && src != 2) {  // charges first, by their own kernel
     prof_begin(pl, NUFFT_STAGE_P2M);
@@ -2553,6 +2618,15 @@ int fmm_upward(nufft_plan_s* pl, const FmmOps& ops, bool uniform_sources, const 
     } else if (uniform_sources) {
       launch_pdl(k_p2m_uniform<T>, dim3(nblk(B * pl->pm, 256), nsig), 256, 0, st, d, charge,
                  (const T*)pl->op_p2m, mleaf);
+    } else if (chunked) {
+      constexpr int WPB = P2mWarps<T>::value;
+      const int nc = (int)pl->p2m_nchunk;
+      cplx<T>* part = (cplx<T>*)pl->p2m_part;
+      launch_pdl(k_p2m_chunks<T>, dim3(nblk(nc, WPB), nsig), 32 * WPB, p2m_smem<T>(pl->pm), st,
+                 d, nc, (const int32_t*)pl->p2m_chunk, (const int32_t*)pl->k0,
+                 PlanT<T>::delta(pl), charge, part);
+      launch_pdl(k_p2m_chunk_sum<T>, dim3(nblk(B * pl->pm, 256), nsig), 256, 0, st, d, nc,
+                 (const int32_t*)pl->p2m_cfirst, (const cplx<T>*)part, mleaf);
     } else {
       constexpr int WPB = P2mWarps<T>::value;
       launch_pdl(k_p2m_nonuniform<T>, dim3(nblk(B, WPB), nsig), 32 * WPB, p2m_smem<T>(pl->pm),
@@ -2561,7 +2635,7 @@ int fmm_upward(nufft_plan_s* pl, const FmmOps& ops, bool uniform_sources, const 
     if (ops.leaf_shift)
       launch_pdl(k_leaf_shift<T>, nblk(B * pl->pm, 256), 256, 0, st, B, pl->pm, ops.leaf_shift,
                  mleaf);
-    prof_end(pl, ops.leaf_shift ? 2 : 1);
+    prof_end(pl, ops.leaf_shift || chunked ? 2 : 1);
     // upward: one launch, or subtrees of up to kSubDepth levels down to level
     // kTopLevel, then one CTA
     prof_begin(pl, NUFFT_STAGE_M2M);

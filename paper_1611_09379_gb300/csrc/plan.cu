@@ -239,7 +239,8 @@ void free_plan(nufft_plan_s* pl) {
                   pl->ad_box, pl->ad_perm, pl->ad_pos, pl->ad_F, pl->ad_E, pl->ad_Ff, pl->ad_Ef,
                   pl->ad_p2m, pl->ad_lexp, pl->ad_start, pl->ad_tiles, pl->ad_srange,
                   pl->ad_gbox, pl->ad_gil, pl->ad_mexp, pl->ad_Dt, pl->ad_S, pl->ad_Dtf,
-                  pl->ad_Sf, pl->ad_charge, pl->ad_st, pl->ad_rleaf};
+                  pl->ad_Sf, pl->ad_charge, pl->ad_st, pl->ad_rleaf, pl->p2m_chunk,
+                  pl->p2m_cfirst, pl->p2m_part};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& gr : pl->graphs)
@@ -263,6 +264,31 @@ template <class X>
 int dalloc(X** p, size_t bytes) {
   if (bytes == 0) bytes = 16;
   return cudaMalloc((void**)p, bytes) == cudaSuccess ? NUFFT_OK : NUFFT_ENOMEM;
+}
+
+// Chunks of the P2M of clustered sources: each leaf's sorted sources cut into
+// runs of at most 256 (the chunked kernel's unit), leaf by leaf.
+int build_p2m_chunks(nufft_plan_s* pl, const std::vector<int32_t>& start) {
+  const int64_t B = pl->B;
+  std::vector<int32_t> chunk, cfirst((size_t)B + 1);
+  for (int64_t b = 0; b < B; ++b) {
+    cfirst[(size_t)b] = (int32_t)(chunk.size() / 3);
+    for (int32_t a = start[(size_t)b]; a < start[(size_t)b + 1]; a += 256) {
+      const int32_t e = a + 256 < start[(size_t)b + 1] ? a + 256 : start[(size_t)b + 1];
+      chunk.push_back((int32_t)b);
+      chunk.push_back(a);
+      chunk.push_back(e);
+    }
+  }
+  cfirst[(size_t)B] = (int32_t)(chunk.size() / 3);
+  pl->p2m_nchunk = (int64_t)chunk.size() / 3;
+  const size_t csz = pl->prec == NUFFT_FP64 ? sizeof(double2) : sizeof(float2);
+  int rc;
+  if ((rc = upload((void**)&pl->p2m_chunk, chunk.data(), chunk.size() * 4)) ||
+      (rc = upload((void**)&pl->p2m_cfirst, cfirst.data(), cfirst.size() * 4)) ||
+      (rc = dalloc(&pl->p2m_part, (size_t)pl->batch * pl->p2m_nchunk * pl->pm * csz)))
+    return rc;
+  return NUFFT_OK;
 }
 
 }  // namespace
@@ -532,8 +558,8 @@ int nufft_plan_create(nufft_plan* out, int64_t N, int64_t M, const double* y, do
   if (cudaMalloc(&tmp, tb) != cudaSuccess) { free_plan(pl); return NUFFT_ENOMEM; }
   rc = setup_points(pl, y, tmp);
   if (!rc) rc = fmm_pack_positions(pl);
+  std::vector<int32_t> ls((size_t)B + 1);
   if (!rc) {  // the fullest leaf (the adjoint's near-field kernel choice)
-    std::vector<int32_t> ls((size_t)B + 1);
     if (cudaMemcpyAsync(ls.data(), pl->leaf_start, (B + 1) * 4, cudaMemcpyDeviceToHost, st) !=
             cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
@@ -542,6 +568,9 @@ int nufft_plan_create(nufft_plan* out, int64_t N, int64_t M, const double* y, do
       if (ls[b + 1] - ls[b] > pl->max_leaf) pl->max_leaf = ls[b + 1] - ls[b];
   }
   if (!rc && (flags & NUFFT_WANT_INVERSE)) rc = inverse_precompute(pl, tmp, tb);
+  // clustered sources (a leaf with at least 4x the mean count): the chunks of
+  // the adjoint / inverse P2M, at most 256 sources of one leaf each
+  if (!rc && M > 0 && (int64_t)pl->max_leaf * B >= 4 * M) rc = build_p2m_chunks(pl, ls);
   if (!rc && (flags & NUFFT_ADAPTIVE)) rc = adaptive_setup(pl);
   int hstat = 0;
   if (!rc) {
