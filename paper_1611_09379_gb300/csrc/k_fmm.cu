@@ -2879,8 +2879,8 @@ static TreeDims class_dims(const nufft_plan_s* pl, int c) {
 // (stored class after class) are the uniform tree's targets at depth L + c.
 // Their near-field sums (grid samples only) run on side branch 2 beside the
 // tree passes, class after class; the main chain runs the uniform upward and
-// downward passes, then the deeper levels (k_down_deep, level by level); the
-// far parts of the classes follow the join.
+// downward passes, then the deeper levels (k_down_deep: one launch, one CTA
+// per refined leaf); the far parts of the classes follow the join.
 template <class T>
 static int fmm_forward_adaptive(nufft_plan_s* pl, void* g) {
   const cplx<T>* f = (const cplx<T>*)pl->grid;
@@ -3082,11 +3082,12 @@ template <> struct AdInvT<float> {
 
 // Adjoint / inverse with the adaptive tree (one signal).  Side branch 2,
 // beside the uniform tree passes (which take every source, as before): the
-// near-field sums of class 0 on every grid tile, those of each deeper class
-// (the uniform tree of depth L + d over its own sources, charges and self
-// terms formed inline) added on the tiles it reaches, then level by level the
-// deep boxes' multipoles and their M2L into the grid boxes of their
-// interaction lists, added at those grid points.  After the join the far
+// near-field sums of class 0 on every grid tile (charges and self terms
+// formed inline), those of each deeper class (the uniform tree of depth
+// L + d over its own sources, one warp per 8 grid points, its charges and
+// self terms formed first in class order) added on the tiles it reaches,
+// then level by level the deep boxes' multipoles and their M2L into the grid
+// boxes of their interaction lists, added at those grid points.  After the join the far
 // part reads the sums as with the uniform tree.
 template <class T>
 static int fmm_to_grid_adaptive(nufft_plan_s* pl, const void* g, int inverse) {
