@@ -442,6 +442,26 @@ def test_adjoint_2p20_sampled(nf, orc, prec):
     assert orc.rel_l2(c[idx], orc.nudft_adj(g, y, N, idx)) < TOL[prec]
 
 
+@pytest.mark.parametrize("prec,kind,lmax", [(0, "multiscale", 17), (1, "multiscale", 17),
+                                          (1, "clustered", 0)])
+def test_adjoint_2p20_clustered_sampled(nf, orc, prec, kind, lmax):
+    """Adjoint on clustered sources at 2^20, where leaves hold up to 30x the
+    mean count: the P2M in chunks of at most 256 sources of one leaf, and the
+    near field one warp per 8 grid points on the tiles next to a dense leaf
+    and the two-point kernel on the others.  Sampled coefficients against
+    the direct sums; a replay gives the same bits.  (The four-width mixture
+    at l_max 17: at the formula's depth a leaf would exceed the binning's
+    2048 points.)"""
+    N = M = 1 << 20
+    y = workloads.points(kind, M, seed=1235)
+    g = workloads.samples(M, seed=78)
+    plan = nf.Plan(N, _dev(y), eps=1e-12 if prec == 0 else 1e-6, prec=prec, lmax=lmax)
+    c = _host(plan.adjoint(_dev(g)))
+    idx = workloads.sample_index(N, 1024, seed=3)
+    assert orc.rel_l2(c[idx], orc.nudft_adj(g, y, N, idx)) < TOL[prec]
+    assert np.array_equal(_host(plan.adjoint(_dev(g))), c)
+
+
 # ------------------------------------------------------------------ errors
 
 def test_rejects_points_outside_circle(nf):
