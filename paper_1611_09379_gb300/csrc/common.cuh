@@ -318,10 +318,6 @@ struct nufft_plan_s {
   int32_t *p2m_cfirst = nullptr; // [B + 1]
   int64_t p2m_nchunk = 0;
   void *p2m_part = nullptr;      // [batch][p2m_nchunk][pm] complex (T)
-  // the adjoint near field's grid tiles (2 x 256 points) of such a plan: the
-  // nctile_dense next to a dense leaf first, then the others
-  int32_t *ctile = nullptr;
-  int64_t nctile = 0, nctile_dense = 0;
   void *hnear = nullptr;         // near-field sums of one signal (2 max(N, M) complex):
                                  //     forward [M], adjoint / inverse [N][2] (sum, self terms)
   // adaptive tree (NUFFT_ADAPTIVE, forward): leaf b refined by d_b levels;

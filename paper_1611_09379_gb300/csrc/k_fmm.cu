@@ -2311,10 +2311,8 @@ __global__ void __launch_bounds__(kTgtThreads) k_targets_gridw(
 // added to the earlier classes', on the grid tiles of 2 kTgtThreads points of
 // the list `tiles`: kGridwTileCtas CTAs of 8 warps x 8 grid points per tile.
 constexpr int kGridwTileCtas = 2 * kTgtThreads / (kTgtThreads / 32 * 8);
-// (AD = 0: the near-field sums of the dense tiles of a plan with clustered
-// sources, stored; the other tiles go to k_targets_grid2_tl.)
-template <class T, int AD>
-__global__ void __launch_bounds__(kTgtThreads) k_targets_gridw_tl(
+template <class T>
+__global__ void __launch_bounds__(kTgtThreads) k_targets_gridw_ad(
     TreeDims d, int inverse, const int32_t* __restrict__ tiles, const int32_t* __restrict__ start,
     const SrcPos<T>* __restrict__ pos, const cplx<T>* __restrict__ charge,
     const cplx<T>* __restrict__ st, cplx<T>* __restrict__ hout) {
@@ -2324,22 +2322,8 @@ __global__ void __launch_bounds__(kTgtThreads) k_targets_gridw_tl(
   const int kb = tile * 2 * kTgtThreads +
                  (int)(((blockIdx.x % kGridwTileCtas) * (unsigned)kTgtThreads + threadIdx.x) >> 5) * 8;
   if (kb >= (int)d.N) return;  // the same for the whole warp
-  gridw_group<T, 8, AD>(kb, d, inverse, start, pos, charge, st, nullptr, nullptr, nullptr, nullptr,
-                        hout);
-}
-
-// The two-point kernel's near-field sums (charges and self terms inline) on
-// the grid tiles of the list `tiles`, one per CTA: the tiles of a plan with
-// clustered sources whose windows hold no dense leaf.
-template <class T>
-__global__ void __launch_bounds__(kTgtThreads, 4) k_targets_grid2_tl(
-    TreeDims d, int inverse, const int32_t* __restrict__ tiles, const int32_t* __restrict__ start,
-    const SrcPos<T>* __restrict__ pos, const cplx<T>* __restrict__ lexp,
-    const cplx<T>* __restrict__ lvl2, cplx<T>* __restrict__ hout, InlineSrc<T> isrc) {
-  pdl_wait();
-  pdl_trigger();
-  grid2_tile<T, 1>(tiles[blockIdx.x], d, inverse, start, pos, nullptr, nullptr, lexp, lvl2,
-                   nullptr, nullptr, hout, nullptr, isrc);
+  gridw_group<T, 8, 1>(kb, d, inverse, start, pos, charge, st, nullptr, nullptr, nullptr, nullptr,
+                       hout);
 }
 
 }  // namespace nufft
@@ -3168,7 +3152,7 @@ static int fmm_to_grid_adaptive(nufft_plan_s* pl, const void* g, int inverse) {
     for (int c = 1; c <= D; ++c) {
       const int64_t o = pl->ad_off[c], nt = pl->ad_tioff[c] - pl->ad_tioff[c - 1];
       if (nt == 0) continue;
-      launch_pdl(k_targets_gridw_tl<T, 1>, dim3((unsigned)(nt * kGridwTileCtas)), kTgtThreads, 0, s2,
+      launch_pdl(k_targets_gridw_ad<T>, dim3((unsigned)(nt * kGridwTileCtas)), kTgtThreads, 0, s2,
                  class_dims(pl, c), inverse, (const int32_t*)pl->ad_tiles + pl->ad_tioff[c - 1],
                  (const int32_t*)pl->ad_start + pl->ad_soff[c], pos + o,
                  (const cplx<T>*)pl->ad_charge + o, (const cplx<T>*)pl->ad_st + o, hn);
@@ -3244,20 +3228,16 @@ int fmm_to_grid(nufft_plan_s* pl, const void* g, int inverse) {
     // warp-per-grid-points kernel reads them from a charge kernel and a
     // self-term kernel run first
     const bool inl = !gridw_wanted(pl);
-    // clustered sources on a grid that fills the GPU: the warp-per-grid-points
-    // kernel on the tiles next to a dense leaf only, the two-point kernel on
-    // the others
-    const bool hybrid = !inl && pl->ctile && pl->M <= 2 * pl->N && pl->s >= 8 &&
-                        pl->N / (2 * kTgtThreads) >= 2 * 152;
     InlineSrc<T> isrc;
-    isrc.a.inverse = inverse;
-    isrc.a.perm = pl->perm;
-    isrc.a.gin = g;
-    isrc.a.gin64 = c64 ? 0 : 1;
-    isrc.coef = coef;
-    isrc.E = PlanT<T>::E(pl);
-    if (inverse) isrc.S = PlanT<T>::S(pl);
-    if (!inl) {
+    if (inl) {
+      isrc.a.inverse = inverse;
+      isrc.a.perm = pl->perm;
+      isrc.a.gin = g;
+      isrc.a.gin64 = c64 ? 0 : 1;
+      isrc.coef = coef;
+      isrc.E = PlanT<T>::E(pl);
+      if (inverse) isrc.S = PlanT<T>::S(pl);
+    } else {
       prof_begin(pl, NUFFT_STAGE_P2M);
       if (c64)
         launch_pdl(k_charges<T, float2>, dim3(nblk(pl->M, 256), nsig), 256, 0, st, pl->M,
@@ -3275,23 +3255,10 @@ int fmm_to_grid(nufft_plan_s* pl, const void* g, int inverse) {
         if (c64) launch_self_terms<T, float2>(pl, d, inverse, (const float2*)g, charge, stt, s2);
         else launch_self_terms<T, double2>(pl, d, inverse, (const double2*)g, charge, stt, s2);
       }
-      if (hybrid) {
-        const int64_t nd = pl->nctile_dense, ns = pl->nctile - nd;
-        if (nd > 0)
-          launch_pdl(k_targets_gridw_tl<T, 0>, dim3((unsigned)(nd * kGridwTileCtas)), kTgtThreads,
-                     0, s2, d, inverse, (const int32_t*)pl->ctile, (const int32_t*)pl->leaf_start,
-                     pos, (const cplx<T>*)charge, (const cplx<T>*)stt, (cplx<T>*)pl->hnear);
-        if (ns > 0)
-          launch_pdl(k_targets_grid2_tl<T>, dim3((unsigned)ns), kTgtThreads,
-                     NearCap<T, 1>::grid_bytes, s2, d, inverse,
-                     (const int32_t*)pl->ctile + nd, (const int32_t*)pl->leaf_start, pos,
-                     (const cplx<T>*)pl->lexp, PlanT<T>::lvl2(pl), (cplx<T>*)pl->hnear, isrc);
-      } else {
-        launch_targets_grid1<T>(pl, d, inverse, pos, charge, stt, (cplx<T>*)pl->hnear, s2, isrc);
-      }
+      launch_targets_grid1<T>(pl, d, inverse, pos, charge, stt, (cplx<T>*)pl->hnear, s2, isrc);
     }
     side_end(pl, 2, s2);
-    prof_end(pl, inl ? 1 : (hybrid ? 3 : 2));
+    prof_end(pl, inl ? 1 : 2);
     if (inl)
       rc = c64 ? fmm_upward<T, float2>(pl, ops, false, charge, coef, (int)!inverse,
                                        (const float2*)g, nullptr, l2, l2f)

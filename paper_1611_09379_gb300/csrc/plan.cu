@@ -240,7 +240,7 @@ void free_plan(nufft_plan_s* pl) {
                   pl->ad_p2m, pl->ad_lexp, pl->ad_start, pl->ad_tiles, pl->ad_srange,
                   pl->ad_gbox, pl->ad_gil, pl->ad_mexp, pl->ad_Dt, pl->ad_S, pl->ad_Dtf,
                   pl->ad_Sf, pl->ad_charge, pl->ad_st, pl->ad_rleaf, pl->p2m_chunk,
-                  pl->p2m_cfirst, pl->p2m_part, pl->ctile};
+                  pl->p2m_cfirst, pl->p2m_part};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& gr : pl->graphs)
@@ -282,28 +282,11 @@ int build_p2m_chunks(nufft_plan_s* pl, const std::vector<int32_t>& start) {
   }
   cfirst[(size_t)B] = (int32_t)(chunk.size() / 3);
   pl->p2m_nchunk = (int64_t)chunk.size() / 3;
-  // grid tiles of 512 points: dense when a leaf of their window (the tile's
-  // leaves and one on each side) holds at least 4x the mean count
-  const int64_t N = pl->N, M = pl->M, s = pl->s, ntile = (N + 511) / 512;
-  std::vector<int32_t> dense, sparse;
-  for (int64_t t = 0; t < ntile; ++t) {
-    const int64_t bl = t * 512 / s, bh = ((t + 1) * 512 - 1 < N ? (t + 1) * 512 - 1 : N - 1) / s;
-    bool d = false;
-    for (int64_t b = bl - 1; b <= bh + 1 && !d; ++b) {
-      const int64_t bb = (b + B) & (B - 1);
-      d = (int64_t)(start[(size_t)bb + 1] - start[(size_t)bb]) * B >= 4 * M;
-    }
-    (d ? dense : sparse).push_back((int32_t)t);
-  }
-  pl->nctile_dense = (int64_t)dense.size();
-  dense.insert(dense.end(), sparse.begin(), sparse.end());
-  pl->nctile = (int64_t)dense.size();
   const size_t csz = pl->prec == NUFFT_FP64 ? sizeof(double2) : sizeof(float2);
   int rc;
   if ((rc = upload((void**)&pl->p2m_chunk, chunk.data(), chunk.size() * 4)) ||
       (rc = upload((void**)&pl->p2m_cfirst, cfirst.data(), cfirst.size() * 4)) ||
-      (rc = dalloc(&pl->p2m_part, (size_t)pl->batch * pl->p2m_nchunk * pl->pm * csz)) ||
-      (rc = upload((void**)&pl->ctile, dense.data(), dense.size() * 4)))
+      (rc = dalloc(&pl->p2m_part, (size_t)pl->batch * pl->p2m_nchunk * pl->pm * csz)))
     return rc;
   return NUFFT_OK;
 }

@@ -446,10 +446,9 @@ def test_adjoint_2p20_sampled(nf, orc, prec):
                                           (1, "clustered", 0)])
 def test_adjoint_2p20_clustered_sampled(nf, orc, prec, kind, lmax):
     """Adjoint on clustered sources at 2^20, where leaves hold up to 30x the
-    mean count: the P2M in chunks of at most 256 sources of one leaf, and the
-    near field one warp per 8 grid points on the tiles next to a dense leaf
-    and the two-point kernel on the others.  Sampled coefficients against
-    the direct sums; a replay gives the same bits.  (The four-width mixture
+    mean count: the P2M in chunks of at most 256 sources of one leaf and the
+    near field one warp per 8 grid points.  Sampled coefficients against the
+    direct sums; a replay gives the same bits.  (The four-width mixture
     at l_max 17: at the formula's depth a leaf would exceed the binning's
     2048 points.)"""
     N = M = 1 << 20
